@@ -1,0 +1,408 @@
+/*
+ * dfpr_oracle.c -- plain, slow, single-threaded FP64 reference for the
+ * Dynamic Frontier (DF) and Dynamic Frontier with Pruning (DF-P) PageRank
+ * update of arXiv 2401.15870 and for its comparators (Static, Naive-dynamic,
+ * Dynamic Traversal).
+ *
+ * TEST INFRASTRUCTURE ONLY.  This file is the oracle that the CUDA library is
+ * checked against.  It shares no code, header, table or helper with the CUDA
+ * path, and nothing in the product path may link, load or call it: only the
+ * tests, the package smoke check and the benchmark's CPU-baseline leg do.
+ *
+ * Everything is written for readability against the paper, not for speed:
+ *   - a graph is the sorted set of its edge keys (src << 32 | dst), with
+ *     exactly one self-loop on every vertex (Sec. 4.1.3, Sec. 4.1.4: self-loops
+ *     are added to all vertices, so there are no dead ends);
+ *   - out- and in-adjacency lists are rebuilt from that set after every batch;
+ *   - every method runs in the synchronous (Jacobi) order: all vertices
+ *     processed in iteration i read the ranks R_i of the start of the iteration
+ *     (Sec. 3.4 runs Alg. 1 asynchronously with one rank vector, which leaves
+ *     the schedule undefined; the synchronous order is one legal interleaving
+ *     of its parallel loop and is reproducible).
+ *
+ * Readings of points where the paper is silent (each is also listed in the
+ * design notes):
+ *   - set semantics for batches: E_t = (E_{t-1} \ D) u I, deletions first,
+ *     duplicate and ineffective entries have no effect (Sec. 2.2 defines the
+ *     deletions and insertions as set differences);
+ *   - a deletion of a self-loop is ignored: self-loops are re-added with every
+ *     batch (Sec. 4.1.4, Sec. 4.2.2);
+ *   - the initial marking of Alg. 1 marks (G_{t-1} u G_t).out(u) for every
+ *     updated edge (u, v); that set contains u itself through its self-loop;
+ *   - Delta r / max(r, R[v]) uses the larger of the new and the old rank
+ *     (Sec. 3.2);
+ *   - prune when the relative change is <= tau_p, expand when it is > tau_f,
+ *     stop when the L-infinity change is <= tau (Alg. 1);
+ *   - when a vertex is pruned and also re-marked by an expansion in the same
+ *     iteration, the mark wins: F_{i+1} = M_i u (F_i \ P_i);
+ *   - Dynamic Traversal marks the union of the vertices reachable from the
+ *     updated sources in G_{t-1} and those reachable in G_t (Sec. 2.3.2).
+ *
+ * Build: gcc -O2 -std=c11 -shared -fPIC dfpr_oracle.c -o liboracle.so
+ * (no -ffast-math: IEEE round-to-nearest FP64 throughout).
+ */
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+#include <math.h>
+
+enum { OR_STATIC = 0, OR_NAIVE_DYNAMIC = 1, OR_DYNAMIC_TRAVERSAL = 2, OR_DF = 3, OR_DFP = 4 };
+enum { OR_OK = 0, OR_EINVAL = 1, OR_ERANGE = 2, OR_ENOMEM = 3, OR_ENORANKS = 4 };
+
+typedef struct {
+  int32_t n;
+  int64_t m;             /* |E_t|, self-loops included */
+  uint64_t *keys;        /* sorted unique edge keys of E_t */
+  int64_t *out_off;      /* n+1: out-rows of E_t, each sorted by target */
+  int32_t *out_adj;
+  int64_t *in_off;       /* n+1: in-rows of E_t, each sorted by source */
+  int32_t *in_adj;
+  int64_t m_prev;        /* E_{t-1} of the last batch */
+  uint64_t *keys_prev;
+  int64_t n_del, n_ins;  /* effective Delta- = E_{t-1} \ E_t, Delta+ = E_t \ E_{t-1} */
+  uint64_t *del, *ins;
+} or_graph;
+
+typedef struct {
+  int32_t iterations, converged;
+  double delta_R;
+  int64_t vertices_ever_affected;
+  int64_t edges_processed;
+  int64_t vertices_processed;
+} or_stats;
+
+static uint64_t key_of(int32_t u, int32_t v) { return ((uint64_t)(uint32_t)u << 32) | (uint32_t)v; }
+static int32_t key_src(uint64_t k) { return (int32_t)(k >> 32); }
+static int32_t key_dst(uint64_t k) { return (int32_t)(k & 0xffffffffu); }
+
+static int cmp_u64(const void *a, const void *b) {
+  uint64_t x = *(const uint64_t *)a, y = *(const uint64_t *)b;
+  return (x > y) - (x < y);
+}
+
+/* sort and drop repeated keys in place; returns the new length */
+static int64_t sort_unique(uint64_t *k, int64_t len) {
+  if (len == 0) return 0;
+  qsort(k, (size_t)len, sizeof(uint64_t), cmp_u64);
+  int64_t w = 1;
+  for (int64_t i = 1; i < len; i++)
+    if (k[i] != k[w - 1]) k[w++] = k[i];
+  return w;
+}
+
+static int contains(const uint64_t *k, int64_t len, uint64_t x) {
+  int64_t lo = 0, hi = len;
+  while (lo < hi) {
+    int64_t mid = lo + (hi - lo) / 2;
+    if (k[mid] < x) lo = mid + 1; else hi = mid;
+  }
+  return lo < len && k[lo] == x;
+}
+
+/* first index with k[i] >= x */
+static int64_t lower_bound(const uint64_t *k, int64_t len, uint64_t x) {
+  int64_t lo = 0, hi = len;
+  while (lo < hi) {
+    int64_t mid = lo + (hi - lo) / 2;
+    if (k[mid] < x) lo = mid + 1; else hi = mid;
+  }
+  return lo;
+}
+
+/* a \ b for sorted unique arrays; out has room for len_a */
+static int64_t set_minus(const uint64_t *a, int64_t la, const uint64_t *b, int64_t lb, uint64_t *out) {
+  int64_t i = 0, j = 0, w = 0;
+  while (i < la) {
+    while (j < lb && b[j] < a[i]) j++;
+    if (j < lb && b[j] == a[i]) { i++; continue; }
+    out[w++] = a[i++];
+  }
+  return w;
+}
+
+/* a u b for sorted unique arrays; out has room for la + lb */
+static int64_t set_union(const uint64_t *a, int64_t la, const uint64_t *b, int64_t lb, uint64_t *out) {
+  int64_t i = 0, j = 0, w = 0;
+  while (i < la || j < lb) {
+    if (j >= lb || (i < la && a[i] < b[j])) out[w++] = a[i++];
+    else if (i >= la || b[j] < a[i]) out[w++] = b[j++];
+    else { out[w++] = a[i++]; j++; }
+  }
+  return w;
+}
+
+/* rebuild out- and in-adjacency (CSR) from the sorted key set */
+static int rebuild_adjacency(or_graph *g) {
+  int32_t n = g->n;
+  int64_t m = g->m;
+  free(g->out_off); free(g->out_adj); free(g->in_off); free(g->in_adj);
+  g->out_off = (int64_t *)calloc((size_t)n + 1, sizeof(int64_t));
+  g->in_off = (int64_t *)calloc((size_t)n + 1, sizeof(int64_t));
+  g->out_adj = (int32_t *)malloc(sizeof(int32_t) * (size_t)(m > 0 ? m : 1));
+  g->in_adj = (int32_t *)malloc(sizeof(int32_t) * (size_t)(m > 0 ? m : 1));
+  if (!g->out_off || !g->in_off || !g->out_adj || !g->in_adj) return OR_ENOMEM;
+  for (int64_t i = 0; i < m; i++) {
+    g->out_off[key_src(g->keys[i]) + 1]++;
+    g->in_off[key_dst(g->keys[i]) + 1]++;
+  }
+  for (int32_t v = 0; v < n; v++) {
+    g->out_off[v + 1] += g->out_off[v];
+    g->in_off[v + 1] += g->in_off[v];
+  }
+  /* keys are sorted by (src, dst): a linear pass gives out-rows sorted by dst
+   * and, bucketing by dst in that order, in-rows sorted by src */
+  int64_t *fill = (int64_t *)malloc(sizeof(int64_t) * (size_t)(n > 0 ? n : 1));
+  if (!fill) return OR_ENOMEM;
+  for (int32_t v = 0; v < n; v++) fill[v] = g->in_off[v];
+  for (int64_t i = 0; i < m; i++) {
+    g->out_adj[i] = key_dst(g->keys[i]);
+    g->in_adj[fill[key_dst(g->keys[i])]++] = key_src(g->keys[i]);
+  }
+  free(fill);
+  return OR_OK;
+}
+
+void or_graph_destroy(or_graph *g) {
+  if (!g) return;
+  free(g->keys); free(g->out_off); free(g->out_adj); free(g->in_off); free(g->in_adj);
+  free(g->keys_prev); free(g->del); free(g->ins);
+  free(g);
+}
+
+/* Graph from a raw edge list (repeats and self-loops allowed): the edge set
+ * with exactly one self-loop per vertex (Sec. 4.1.3). */
+int or_graph_create(int32_t n, int64_t m, const int32_t *src, const int32_t *dst, or_graph **out) {
+  *out = NULL;
+  if (n <= 0 || m < 0) return OR_EINVAL;
+  for (int64_t i = 0; i < m; i++)
+    if (src[i] < 0 || src[i] >= n || dst[i] < 0 || dst[i] >= n) return OR_ERANGE;
+  or_graph *g = (or_graph *)calloc(1, sizeof(or_graph));
+  if (!g) return OR_ENOMEM;
+  g->n = n;
+  g->keys = (uint64_t *)malloc(sizeof(uint64_t) * (size_t)(m + n));
+  if (!g->keys) { free(g); return OR_ENOMEM; }
+  int64_t len = 0;
+  for (int64_t i = 0; i < m; i++) g->keys[len++] = key_of(src[i], dst[i]);
+  for (int32_t v = 0; v < n; v++) g->keys[len++] = key_of(v, v);
+  g->m = sort_unique(g->keys, len);
+  int rc = rebuild_adjacency(g);
+  if (rc != OR_OK) { or_graph_destroy(g); return rc; }
+  *out = g;
+  return OR_OK;
+}
+
+/* Batch update (Sec. 2.2): E_t = (E_{t-1} \ D) u I with self-loop deletions
+ * ignored; records the effective Delta- = E_{t-1} \ E_t and Delta+ = E_t \ E_{t-1}.
+ * Ids are validated before anything changes. */
+int or_apply_batch(or_graph *g, const int32_t *del_src, const int32_t *del_dst, int64_t n_del,
+                   const int32_t *ins_src, const int32_t *ins_dst, int64_t n_ins) {
+  int32_t n = g->n;
+  if (n_del < 0 || n_ins < 0) return OR_EINVAL;
+  for (int64_t i = 0; i < n_del; i++)
+    if (del_src[i] < 0 || del_src[i] >= n || del_dst[i] < 0 || del_dst[i] >= n) return OR_ERANGE;
+  for (int64_t i = 0; i < n_ins; i++)
+    if (ins_src[i] < 0 || ins_src[i] >= n || ins_dst[i] < 0 || ins_dst[i] >= n) return OR_ERANGE;
+
+  uint64_t *D = (uint64_t *)malloc(sizeof(uint64_t) * (size_t)(n_del > 0 ? n_del : 1));
+  uint64_t *I = (uint64_t *)malloc(sizeof(uint64_t) * (size_t)(n_ins > 0 ? n_ins : 1));
+  if (!D || !I) { free(D); free(I); return OR_ENOMEM; }
+  int64_t nd = 0, ni = 0;
+  for (int64_t i = 0; i < n_del; i++)
+    if (del_src[i] != del_dst[i]) D[nd++] = key_of(del_src[i], del_dst[i]);
+  for (int64_t i = 0; i < n_ins; i++) I[ni++] = key_of(ins_src[i], ins_dst[i]);
+  nd = sort_unique(D, nd);
+  ni = sort_unique(I, ni);
+
+  uint64_t *kept = (uint64_t *)malloc(sizeof(uint64_t) * (size_t)(g->m > 0 ? g->m : 1));
+  uint64_t *next = (uint64_t *)malloc(sizeof(uint64_t) * (size_t)(g->m + ni + 1));
+  if (!kept || !next) { free(D); free(I); free(kept); free(next); return OR_ENOMEM; }
+  int64_t nk = set_minus(g->keys, g->m, D, nd, kept);
+  int64_t nn = set_union(kept, nk, I, ni, next);
+  free(kept); free(D); free(I);
+
+  uint64_t *dm = (uint64_t *)malloc(sizeof(uint64_t) * (size_t)(g->m + 1));
+  uint64_t *dp = (uint64_t *)malloc(sizeof(uint64_t) * (size_t)(nn + 1));
+  if (!dm || !dp) { free(dm); free(dp); free(next); return OR_ENOMEM; }
+  int64_t ndm = set_minus(g->keys, g->m, next, nn, dm);
+  int64_t ndp = set_minus(next, nn, g->keys, g->m, dp);
+
+  free(g->keys_prev); free(g->del); free(g->ins);
+  g->keys_prev = g->keys; g->m_prev = g->m;
+  g->keys = next; g->m = nn;
+  g->del = dm; g->n_del = ndm;
+  g->ins = dp; g->n_ins = ndp;
+  return rebuild_adjacency(g);
+}
+
+/* ---- read-only accessors (tests) ---- */
+int32_t or_num_vertices(const or_graph *g) { return g->n; }
+int64_t or_num_edges(const or_graph *g) { return g->m; }
+int64_t or_num_eff_del(const or_graph *g) { return g->n_del; }
+int64_t or_num_eff_ins(const or_graph *g) { return g->n_ins; }
+void or_get_out_csr(const or_graph *g, int64_t *off, int32_t *adj) {
+  memcpy(off, g->out_off, sizeof(int64_t) * ((size_t)g->n + 1));
+  memcpy(adj, g->out_adj, sizeof(int32_t) * (size_t)g->m);
+}
+void or_get_in_csr(const or_graph *g, int64_t *off, int32_t *adj) {
+  memcpy(off, g->in_off, sizeof(int64_t) * ((size_t)g->n + 1));
+  memcpy(adj, g->in_adj, sizeof(int32_t) * (size_t)g->m);
+}
+void or_get_eff_delta(const or_graph *g, uint64_t *del, uint64_t *ins) {
+  if (g->n_del) memcpy(del, g->del, sizeof(uint64_t) * (size_t)g->n_del);
+  if (g->n_ins) memcpy(ins, g->ins, sizeof(uint64_t) * (size_t)g->n_ins);
+}
+
+/* ---- affected sets ---- */
+
+/* Initial marking of DF / DF-P (Alg. 1, initial marking loop): for every
+ * (u, v) in Delta- u Delta+, mark every v' in (G_{t-1} u G_t).out(u). */
+void or_initial_affected(const or_graph *g, uint8_t *flag) {
+  memset(flag, 0, (size_t)g->n);
+  for (int side = 0; side < 2; side++) {
+    const uint64_t *d = side ? g->ins : g->del;
+    int64_t nd = side ? g->n_ins : g->n_del;
+    for (int64_t e = 0; e < nd; e++) {
+      int32_t u = key_src(d[e]);
+      /* G_t.out(u) */
+      for (int64_t j = g->out_off[u]; j < g->out_off[u + 1]; j++) flag[g->out_adj[j]] = 1;
+      /* G_{t-1}.out(u): the key range of source u in the previous edge set */
+      int64_t j = lower_bound(g->keys_prev, g->m_prev, key_of(u, 0));
+      for (; j < g->m_prev && key_src(g->keys_prev[j]) == u; j++) flag[key_dst(g->keys_prev[j])] = 1;
+    }
+  }
+}
+
+/* Vertices reachable from the sources of the updated edges, in G_{t-1} and
+ * in G_t separately, united (Dynamic Traversal, Sec. 2.3.2).  A source reaches
+ * itself. */
+int or_dt_affected(const or_graph *g, uint8_t *flag) {
+  int32_t n = g->n;
+  memset(flag, 0, (size_t)n);
+  int32_t *queue = (int32_t *)malloc(sizeof(int32_t) * (size_t)n);
+  uint8_t *seen = (uint8_t *)malloc((size_t)n);
+  if (!queue || !seen) { free(queue); free(seen); return OR_ENOMEM; }
+  for (int which = 0; which < 2; which++) {   /* 0: G_{t-1}, 1: G_t */
+    memset(seen, 0, (size_t)n);
+    int64_t head = 0, tail = 0;
+    for (int side = 0; side < 2; side++) {
+      const uint64_t *d = side ? g->ins : g->del;
+      int64_t nd = side ? g->n_ins : g->n_del;
+      for (int64_t e = 0; e < nd; e++) {
+        int32_t u = key_src(d[e]);
+        if (!seen[u]) { seen[u] = 1; queue[tail++] = u; }
+      }
+    }
+    while (head < tail) {
+      int32_t x = queue[head++];
+      if (which == 1) {
+        for (int64_t j = g->out_off[x]; j < g->out_off[x + 1]; j++) {
+          int32_t w = g->out_adj[j];
+          if (!seen[w]) { seen[w] = 1; queue[tail++] = w; }
+        }
+      } else {
+        int64_t j = lower_bound(g->keys_prev, g->m_prev, key_of(x, 0));
+        for (; j < g->m_prev && key_src(g->keys_prev[j]) == x; j++) {
+          int32_t w = key_dst(g->keys_prev[j]);
+          if (!seen[w]) { seen[w] = 1; queue[tail++] = w; }
+        }
+      }
+    }
+    for (int32_t v = 0; v < n; v++) flag[v] |= seen[v];
+  }
+  free(queue); free(seen);
+  return OR_OK;
+}
+
+/* ---- rank update ---- */
+
+/* c = sum over u in G_t.in(v) of R[u] / |G_t.out(u)|, in ascending u (Eq. 1) */
+static double in_sum(const or_graph *g, const double *R, int32_t v) {
+  double c = 0.0;
+  for (int64_t j = g->in_off[v]; j < g->in_off[v + 1]; j++) {
+    int32_t u = g->in_adj[j];
+    c += R[u] / (double)(g->out_off[u + 1] - g->out_off[u]);
+  }
+  return c;
+}
+
+/* Eq. 1: r = C0 + alpha * c */
+double or_rank_plain(double alpha, int32_t n, double c) {
+  double C0 = (1.0 - alpha) / (double)n;
+  return C0 + alpha * c;
+}
+
+/* Eq. 2 (closed-loop form used by DF-P, derived in the appendix):
+ * r = 1 / (1 - alpha/d) * (C0 + alpha * (c - R[v]/d)), d = |G_t.out(v)| */
+double or_rank_closed_loop(double alpha, int32_t n, double c, double Rv, int64_t d) {
+  double C0 = (1.0 - alpha) / (double)n;
+  double dd = (double)d;
+  return 1.0 / (1.0 - alpha / dd) * (C0 + alpha * (c - Rv / dd));
+}
+
+/*
+ * One method run (Sec. 2.1, Sec. 2.3, Alg. 1), synchronous order.
+ * r_prev: ranks of the previous snapshot (ignored by Static, required by the
+ * others).  r_out: the updated ranks.  Returns OR_ENORANKS when a dynamic
+ * method has no r_prev.
+ */
+int or_update(const or_graph *g, int method, double alpha, double tau, double tau_f, double tau_p,
+              int32_t max_iter, const double *r_prev, double *r_out, or_stats *st) {
+  int32_t n = g->n;
+  if (method < OR_STATIC || method > OR_DFP || max_iter < 0 || !(alpha >= 0.0 && alpha < 1.0)) return OR_EINVAL;
+  if (method != OR_STATIC && !r_prev) return OR_ENORANKS;
+  double *R = (double *)malloc(sizeof(double) * (size_t)n);
+  double *Rn = (double *)malloc(sizeof(double) * (size_t)n);
+  uint8_t *F = (uint8_t *)calloc((size_t)n, 1);      /* vertices processed in this iteration */
+  uint8_t *Fn = (uint8_t *)calloc((size_t)n, 1);     /* F_{i+1} */
+  uint8_t *ever = (uint8_t *)calloc((size_t)n, 1);
+  if (!R || !Rn || !F || !Fn || !ever) { free(R); free(Rn); free(F); free(Fn); free(ever); return OR_ENOMEM; }
+
+  if (method == OR_STATIC) for (int32_t v = 0; v < n; v++) R[v] = 1.0 / (double)n;
+  else memcpy(R, r_prev, sizeof(double) * (size_t)n);
+
+  if (method == OR_STATIC || method == OR_NAIVE_DYNAMIC) memset(F, 1, (size_t)n);
+  else if (method == OR_DYNAMIC_TRAVERSAL) {
+    if (or_dt_affected(g, F) != OR_OK) { free(R); free(Rn); free(F); free(Fn); free(ever); return OR_ENOMEM; }
+  } else or_initial_affected(g, F);
+  for (int32_t v = 0; v < n; v++) ever[v] = F[v];
+
+  int frontier = (method == OR_DF || method == OR_DFP);
+  int prune = (method == OR_DFP);
+  or_stats s;
+  memset(&s, 0, sizeof(s));
+  for (int32_t i = 0; i < max_iter; i++) {
+    double dR = 0.0;
+    memcpy(Rn, R, sizeof(double) * (size_t)n);
+    if (frontier) memset(Fn, 0, (size_t)n);
+    for (int32_t v = 0; v < n; v++) {
+      if (!F[v]) continue;
+      double c = in_sum(g, R, v);
+      int64_t d = g->out_off[v + 1] - g->out_off[v];
+      double r = prune ? or_rank_closed_loop(alpha, n, c, R[v], d) : or_rank_plain(alpha, n, c);
+      double dr = fabs(r - R[v]);
+      if (dr > dR) dR = dr;
+      Rn[v] = r;
+      s.vertices_processed++;
+      s.edges_processed += g->in_off[v + 1] - g->in_off[v];
+      if (frontier) {
+        double rel = dr / fmax(r, R[v]);
+        if (!(prune && rel <= tau_p)) Fn[v] = 1;          /* v stays unless pruned */
+        if (rel > tau_f)                                    /* expand: mark G_t.out(v) */
+          for (int64_t j = g->out_off[v]; j < g->out_off[v + 1]; j++) Fn[g->out_adj[j]] = 1;
+      }
+    }
+    memcpy(R, Rn, sizeof(double) * (size_t)n);
+    if (frontier) {
+      memcpy(F, Fn, (size_t)n);
+      for (int32_t v = 0; v < n; v++) ever[v] |= F[v];
+    }
+    s.iterations = i + 1;
+    s.delta_R = dR;
+    if (dR <= tau) { s.converged = 1; break; }
+  }
+  for (int32_t v = 0; v < n; v++) s.vertices_ever_affected += ever[v];
+  memcpy(r_out, R, sizeof(double) * (size_t)n);
+  if (st) *st = s;
+  free(R); free(Rn); free(F); free(Fn); free(ever);
+  return OR_OK;
+}
