@@ -1,0 +1,199 @@
+/*
+ * dfpr.h -- C ABI of the GB300 library for the Dynamic Frontier (DF) and
+ * Dynamic Frontier with Pruning (DF-P) PageRank update of arXiv 2401.15870
+ * ("DF* PageRank: Improved Incrementally Expanding Approaches for Updating
+ * PageRank on Dynamic Graphs"), with Static, Naive-dynamic and Dynamic
+ * Traversal PageRank as comparators.
+ *
+ * Conventions for every call:
+ *   - Vertex ids are int32 in [0, n); n is fixed when the graph is created
+ *     (Sec. 4.2.2: batches add or remove no vertices).
+ *   - "host" pointers are ordinary CPU memory; "device" pointers are CUDA
+ *     global memory on the graph's device (for example torch CUDA tensors).
+ *     Input arrays stay owned by the caller and are only read during the call.
+ *     Output arrays are owned by the caller and must hold the stated number of
+ *     elements.
+ *   - The graph owns all of its device memory and enqueues all work on the
+ *     CUDA stream given at creation (pr_set_stream changes it).  Calls return
+ *     after their results are available to the caller (host outputs written,
+ *     device outputs complete on the graph's stream).
+ *   - Inputs are validated before anything is changed: a call that returns an
+ *     error leaves the graph as it was, except PR_ECUDA / PR_ENOMEM raised by
+ *     the device in the middle of an edit, after which the graph must be
+ *     destroyed.  No C++ exception crosses this interface.
+ *   - Ranks are FP64.  Contribution sums inside the rank sweep are exact sums
+ *     of 2^-61 fixed-point terms (every term R[u]/|out(u)| rounded to the
+ *     nearest multiple of 2^-61), so results do not depend on the order of
+ *     additions; the caller's ranks must be finite, non-negative and sum to at
+ *     most 2.
+ *   - One caller at a time per graph (Sec. 2.2: one writer on the graph at
+ *     any given time).  Different graphs may be used from different threads.
+ */
+#ifndef DFPR_H
+#define DFPR_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct pr_graph pr_graph;
+
+/* Update methods (Sec. 2.1, Sec. 2.3, Sec. 3.1). */
+typedef enum {
+  PR_STATIC = 0,            /* power iteration from 1/|V| over all vertices (Sec. 2.1)          */
+  PR_NAIVE_DYNAMIC = 1,     /* all vertices, starting from the current ranks (Sec. 2.3.1)        */
+  PR_DYNAMIC_TRAVERSAL = 2, /* vertices reachable from updated sources in G_{t-1} or G_t (2.3.2) */
+  PR_DF = 3,                /* Dynamic Frontier (Sec. 3.1.1, Alg. 1)                            */
+  PR_DFP = 4                /* Dynamic Frontier with Pruning (Sec. 3.1.2, Alg. 1, Eq. 2)         */
+} pr_method;
+
+typedef enum {
+  PR_OK = 0,
+  PR_EINVAL = 1,    /* bad argument (null pointer, negative size, method, alpha, tolerances) */
+  PR_ERANGE = 2,    /* a vertex id outside [0, n)                                            */
+  PR_ENOMEM = 3,    /* device or host allocation failed                                      */
+  PR_ENORANKS = 4,  /* a dynamic method was asked for before any ranks exist                 */
+  PR_ECUDA = 5,     /* a CUDA call failed; pr_last_error has the text                        */
+  PR_ETIMEOUT = 6   /* a bounded device-side wait gave up                                    */
+} pr_status;
+
+/* Tolerances of Alg. 1; NULL options mean tau_f = tau_p = 1e-6 and 500
+ * iterations (Sec. 4.1.2, Sec. 3.2, Sec. 3.3). */
+typedef struct {
+  double tau_f;       /* frontier tolerance: expand when dr / max(r, R[v]) > tau_f  */
+  double tau_p;       /* prune tolerance (DF-P): drop v when dr / max(r, R[v]) <= tau_p */
+  int32_t max_iter;   /* MAX_ITERATIONS                                              */
+  int32_t flags;      /* reserved, must be 0                                          */
+} pr_options;
+
+/* Outcome of one pr_update (Sec. 4.1.5 measures time and affected vertices). */
+typedef struct {
+  int32_t iterations;              /* sweeps run                                            */
+  int32_t converged;               /* 1 if the last L-inf change was <= tau                 */
+  double delta_R;                  /* L-inf change of the last sweep                        */
+  int64_t vertices_ever_affected;  /* vertices ever marked (Sec. 4.2.3); |V| for Static, ND */
+  int64_t edges_processed;         /* in-edges summed over all sweeps                       */
+  int64_t vertices_processed;      /* vertex updates over all sweeps                        */
+  int64_t eff_deletions;           /* |Delta-| of the last batch                            */
+  int64_t eff_insertions;          /* |Delta+| of the last batch                            */
+  double ms_apply;                 /* device time of the last pr_apply_batch*               */
+  double ms_update;                /* device time of this pr_update                         */
+} pr_stats;
+
+/*
+ * Create a graph from an out-edge CSR in host memory (Sec. 2.1 notation:
+ * G.out(u) = col[row_off[u] .. row_off[u+1])).  row_off has n+1 entries with
+ * row_off[0] = 0 and row_off[n] = m; col has m entries in [0, n).  Repeated
+ * edges are collapsed and every vertex gets exactly one self-loop (Sec. 4.1.3:
+ * self-loops on all vertices remove dead ends).  stream is a cudaStream_t
+ * (NULL = the default stream) on the current device.  On success *out owns a
+ * new graph without ranks.  Errors: PR_EINVAL (n < 1, m < 0, null pointers,
+ * row_off not non-decreasing from 0 to m), PR_ERANGE (a column outside
+ * [0, n)), PR_ENOMEM, PR_ECUDA.
+ */
+pr_status pr_graph_create(int32_t n, int64_t m, const int64_t* row_off, const int32_t* col, void* stream,
+                          pr_graph** out);
+
+/*
+ * Create a graph from an edge list src[i] -> dst[i], i < m, in host memory
+ * (device_ptrs = 0) or device memory (device_ptrs = 1).  Same semantics and
+ * errors as pr_graph_create.  flags: bit 0 set keeps the caller's vertex order
+ * inside the library (by default vertices are renumbered internally by
+ * decreasing out-degree for locality; ranks and batches always use the
+ * caller's ids).
+ */
+pr_status pr_graph_create_edges(int32_t n, int64_t m, const int32_t* src, const int32_t* dst, int32_t device_ptrs,
+                                int32_t flags, void* stream, pr_graph** out);
+
+/* Free the graph and all its device memory (NULL is ignored). */
+void pr_graph_destroy(pr_graph* g);
+
+/* Rebind the graph to another CUDA stream of the same device. */
+pr_status pr_set_stream(pr_graph* g, void* stream);
+
+/*
+ * Apply one batch update (Sec. 2.2): E_t = (E_{t-1} \ D) u I, deletions
+ * first.  D = {(del_src[i], del_dst[i])}, I = {(ins_src[i], ins_dst[i])}, all
+ * in host memory.  Repeats, deletions of absent edges, insertions of present
+ * edges and self-loop deletions have no effect (self-loops are re-added with
+ * every batch, Sec. 4.2.2).  The CSR and its transpose are edited in place on
+ * the device, and the effective change Delta- = E_{t-1} \ E_t, Delta+ =
+ * E_t \ E_{t-1} is kept for the next pr_update.  Contributions of sources
+ * whose out-degree changed are refreshed.  Errors: PR_EINVAL (null pointer
+ * with a positive count, negative count), PR_ERANGE (an id outside [0, n);
+ * nothing is changed), PR_ENOMEM, PR_ECUDA.
+ */
+pr_status pr_apply_batch(pr_graph* g, const int32_t* del_src, const int32_t* del_dst, int64_t n_del,
+                         const int32_t* ins_src, const int32_t* ins_dst, int64_t n_ins);
+
+/* As pr_apply_batch with the four endpoint arrays in device memory. */
+pr_status pr_apply_batch_device(pr_graph* g, const int32_t* del_src, const int32_t* del_dst, int64_t n_del,
+                                const int32_t* ins_src, const int32_t* ins_dst, int64_t n_ins);
+
+/*
+ * Update the ranks with one method (Sec. 2.1, 2.3, Alg. 1) after the last
+ * batch, iterating until the L-inf change of a sweep is <= tau or
+ * opts->max_iter sweeps have run.  alpha in [0, 1) is the damping factor
+ * (0.85 in the paper), tau >= 0 the iteration tolerance (1e-10, L-inf).
+ * Every method runs in the synchronous order: all vertices processed in a
+ * sweep read the ranks of the start of the sweep.  PR_STATIC starts from
+ * 1/|V|; the others from the current ranks (pr_set_ranks or a previous
+ * update; PR_ENORANKS if none).  Not converging is not an error
+ * (stats->converged = 0).  opts and stats may be NULL.  Errors: PR_EINVAL,
+ * PR_ENORANKS, PR_ECUDA.
+ */
+pr_status pr_update(pr_graph* g, pr_method method, double alpha, double tau, const pr_options* opts,
+                    pr_stats* stats);
+
+/* Copy the n ranks (caller's vertex ids) to host memory out[0..n). */
+pr_status pr_ranks(const pr_graph* g, double* out);
+/* Copy the n ranks to device memory out[0..n) (complete on the graph's stream). */
+pr_status pr_ranks_device(const pr_graph* g, double* out);
+
+/*
+ * Set the current ranks R_{t-1} from host memory r[0..n) (caller's ids), for
+ * example to run several methods from the same previous ranks.  Errors:
+ * PR_EINVAL (a rank that is negative or not finite, or a sum above 2).
+ */
+pr_status pr_set_ranks(pr_graph* g, const double* r);
+/* As pr_set_ranks with r in device memory (checked on the device). */
+pr_status pr_set_ranks_device(pr_graph* g, const double* r);
+
+/* n and the current edge count m (self-loops included). */
+pr_status pr_graph_info(const pr_graph* g, int32_t* n, int64_t* m);
+
+/*
+ * Export one direction of the current graph to host memory in the caller's
+ * ids: which = 0 for out-edges, 1 for in-edges.  off[0..n] gets row offsets,
+ * adj[0..m) the neighbours of each row in ascending order.
+ */
+pr_status pr_get_csr(const pr_graph* g, int32_t which, int64_t* off, int32_t* adj);
+
+/* Effective change of the last batch: sizes, then the edges (caller's ids,
+ * each array sorted by (src, dst)).  Any output pointer may be NULL. */
+pr_status pr_last_delta(const pr_graph* g, int64_t* n_del, int64_t* n_ins, int32_t* del_src, int32_t* del_dst,
+                        int32_t* ins_src, int32_t* ins_dst);
+
+/*
+ * Affected sets on the device, written as one byte per vertex (caller's ids)
+ * to host memory flags[0..n):
+ *   which = 0: initial marking of DF / DF-P (Alg. 1): every v' in
+ *              (G_{t-1} u G_t).out(u) for (u, v) in Delta- u Delta+;
+ *   which = 1: Dynamic Traversal (Sec. 2.3.2): vertices reachable from those
+ *              u in G_{t-1}, united with those reachable in G_t.
+ */
+pr_status pr_affected(pr_graph* g, int32_t which, uint8_t* flags);
+
+/* Text of the last error on this graph ("" if none); valid until the next call. */
+const char* pr_last_error(const pr_graph* g);
+
+/* Name of a status code. */
+const char* pr_status_string(pr_status s);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* DFPR_H */

@@ -1,0 +1,344 @@
+"""Python binding of the GB300 DF / DF-P PageRank library (arXiv 2401.15870).
+
+Argument marshalling only: every step of the update runs in the CUDA kernels of
+``libdfpr.so`` behind the C ABI declared in ``include/dfpr.h``; the functions
+below carry the same names as the C entry points.  Host arrays are numpy
+arrays; device arrays are torch CUDA tensors (PyTorch provides device memory
+and streams, nothing else).  There is no CPU fallback: if the library is not
+built, loading fails with an error.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from dataclasses import dataclass
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libdfpr.so")
+
+PR_STATIC, PR_NAIVE_DYNAMIC, PR_DYNAMIC_TRAVERSAL, PR_DF, PR_DFP = 0, 1, 2, 3, 4
+METHODS = {"static": PR_STATIC, "nd": PR_NAIVE_DYNAMIC, "dt": PR_DYNAMIC_TRAVERSAL, "df": PR_DF, "dfp": PR_DFP}
+STATUS = {0: "PR_OK", 1: "PR_EINVAL", 2: "PR_ERANGE", 3: "PR_ENOMEM", 4: "PR_ENORANKS", 5: "PR_ECUDA",
+          6: "PR_ETIMEOUT"}
+
+
+class PRError(RuntimeError):
+    def __init__(self, status: int, msg: str = ""):
+        self.status = status
+        super().__init__("%s%s" % (STATUS.get(status, str(status)), (": " + msg) if msg else ""))
+
+
+class pr_options(ctypes.Structure):
+    _fields_ = [("tau_f", ctypes.c_double), ("tau_p", ctypes.c_double), ("max_iter", ctypes.c_int32),
+                ("flags", ctypes.c_int32)]
+
+
+class pr_stats(ctypes.Structure):
+    _fields_ = [("iterations", ctypes.c_int32), ("converged", ctypes.c_int32), ("delta_R", ctypes.c_double),
+                ("vertices_ever_affected", ctypes.c_int64), ("edges_processed", ctypes.c_int64),
+                ("vertices_processed", ctypes.c_int64), ("eff_deletions", ctypes.c_int64),
+                ("eff_insertions", ctypes.c_int64), ("ms_apply", ctypes.c_double), ("ms_update", ctypes.c_double)]
+
+
+@dataclass
+class Stats:
+    iterations: int
+    converged: bool
+    delta_R: float
+    vertices_ever_affected: int
+    edges_processed: int
+    vertices_processed: int
+    eff_deletions: int
+    eff_insertions: int
+    ms_apply: float
+    ms_update: float
+
+
+_lib = None
+_P = ctypes.c_void_p
+
+
+def load():
+    """Load libdfpr.so (built by build.build()); raises if it is missing."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        raise RuntimeError("libdfpr.so is not built (run __graft_entry__.build() or "
+                           "python paper_2401_15870_gb300/build.py)")
+    lib = ctypes.CDLL(LIB_PATH)
+    i32, i64, f64 = ctypes.c_int32, ctypes.c_int64, ctypes.c_double
+    sig = {
+        "pr_graph_create": ([i32, i64, _P, _P, _P, ctypes.POINTER(_P)], ctypes.c_int),
+        "pr_graph_create_edges": ([i32, i64, _P, _P, i32, i32, _P, ctypes.POINTER(_P)], ctypes.c_int),
+        "pr_graph_destroy": ([_P], None),
+        "pr_set_stream": ([_P, _P], ctypes.c_int),
+        "pr_apply_batch": ([_P, _P, _P, i64, _P, _P, i64], ctypes.c_int),
+        "pr_apply_batch_device": ([_P, _P, _P, i64, _P, _P, i64], ctypes.c_int),
+        "pr_update": ([_P, ctypes.c_int, f64, f64, _P, _P], ctypes.c_int),
+        "pr_ranks": ([_P, _P], ctypes.c_int),
+        "pr_ranks_device": ([_P, _P], ctypes.c_int),
+        "pr_set_ranks": ([_P, _P], ctypes.c_int),
+        "pr_set_ranks_device": ([_P, _P], ctypes.c_int),
+        "pr_graph_info": ([_P, ctypes.POINTER(i32), ctypes.POINTER(i64)], ctypes.c_int),
+        "pr_get_csr": ([_P, i32, _P, _P], ctypes.c_int),
+        "pr_last_delta": ([_P, ctypes.POINTER(i64), ctypes.POINTER(i64), _P, _P, _P, _P], ctypes.c_int),
+        "pr_affected": ([_P, i32, _P], ctypes.c_int),
+        "pr_last_error": ([_P], ctypes.c_char_p),
+        "pr_status_string": ([ctypes.c_int], ctypes.c_char_p),
+    }
+    for name, (args, res) in sig.items():
+        f = getattr(lib, name)
+        f.argtypes = args
+        f.restype = res
+    _lib = lib
+    return lib
+
+
+def _check(rc, h=None):
+    if rc != 0:
+        msg = load().pr_last_error(h).decode() if h else ""
+        raise PRError(rc, msg)
+
+
+def _host_i32(a):
+    a = np.ascontiguousarray(np.asarray(a, dtype=np.int32))
+    return a, (a.ctypes.data if a.size else None)
+
+
+def _dev_ptr(t, dtype_name):
+    if t is None:
+        return None, 0
+    if not (hasattr(t, "is_cuda") and t.is_cuda):
+        raise TypeError("expected a CUDA tensor")
+    if str(t.dtype) != "torch." + dtype_name or not t.is_contiguous():
+        raise TypeError("expected a contiguous %s CUDA tensor" % dtype_name)
+    return t.data_ptr(), t.numel()
+
+
+def _stream_handle(stream):
+    if stream is None:
+        return None
+    if isinstance(stream, int):
+        return stream
+    return stream.cuda_stream
+
+
+# ------------------------------------------------------------------ C-ABI mirrors
+
+def pr_graph_create(n, row_off, col, stream=None):
+    lib = load()
+    ro = np.ascontiguousarray(np.asarray(row_off, dtype=np.int64))
+    c, cp = _host_i32(col)
+    h = _P()
+    rc = lib.pr_graph_create(int(n), int(c.size), ro.ctypes.data, cp, _stream_handle(stream), ctypes.byref(h))
+    _check(rc)
+    return h
+
+
+def pr_graph_create_edges(n, src, dst, device=False, keep_order=False, stream=None):
+    lib = load()
+    flags = 1 if keep_order else 0
+    h = _P()
+    if device:
+        sp, m = _dev_ptr(src, "int32")
+        dp, m2 = _dev_ptr(dst, "int32")
+        if m != m2:
+            raise ValueError("src and dst differ in length")
+        rc = lib.pr_graph_create_edges(int(n), m, sp, dp, 1, flags, _stream_handle(stream), ctypes.byref(h))
+    else:
+        s, sp = _host_i32(src)
+        d, dp = _host_i32(dst)
+        if s.size != d.size:
+            raise ValueError("src and dst differ in length")
+        rc = lib.pr_graph_create_edges(int(n), s.size, sp, dp, 0, flags, _stream_handle(stream), ctypes.byref(h))
+    _check(rc)
+    return h
+
+
+def pr_graph_destroy(h):
+    if h:
+        load().pr_graph_destroy(h)
+
+
+def pr_set_stream(h, stream):
+    _check(load().pr_set_stream(h, _stream_handle(stream)), h)
+
+
+def pr_apply_batch(h, del_src=(), del_dst=(), ins_src=(), ins_dst=()):
+    ds, dsp = _host_i32(del_src)
+    dd, ddp = _host_i32(del_dst)
+    is_, isp = _host_i32(ins_src)
+    id_, idp = _host_i32(ins_dst)
+    if ds.size != dd.size or is_.size != id_.size:
+        raise ValueError("endpoint arrays differ in length")
+    _check(load().pr_apply_batch(h, dsp, ddp, ds.size, isp, idp, is_.size), h)
+
+
+def pr_apply_batch_device(h, del_src=None, del_dst=None, ins_src=None, ins_dst=None):
+    dsp, nd = _dev_ptr(del_src, "int32")
+    ddp, nd2 = _dev_ptr(del_dst, "int32")
+    isp, ni = _dev_ptr(ins_src, "int32")
+    idp, ni2 = _dev_ptr(ins_dst, "int32")
+    if nd != nd2 or ni != ni2:
+        raise ValueError("endpoint arrays differ in length")
+    _check(load().pr_apply_batch_device(h, dsp, ddp, nd, isp, idp, ni), h)
+
+
+def pr_update(h, method, alpha=0.85, tau=1e-10, tau_f=1e-6, tau_p=1e-6, max_iter=500) -> Stats:
+    m = METHODS[method] if isinstance(method, str) else int(method)
+    opts = pr_options(tau_f, tau_p, int(max_iter), 0)
+    st = pr_stats()
+    _check(load().pr_update(h, m, float(alpha), float(tau), ctypes.byref(opts), ctypes.byref(st)), h)
+    return Stats(st.iterations, bool(st.converged), st.delta_R, st.vertices_ever_affected, st.edges_processed,
+                 st.vertices_processed, st.eff_deletions, st.eff_insertions, st.ms_apply, st.ms_update)
+
+
+def pr_graph_info(h):
+    n = ctypes.c_int32()
+    m = ctypes.c_int64()
+    _check(load().pr_graph_info(h, ctypes.byref(n), ctypes.byref(m)), h)
+    return n.value, m.value
+
+
+def pr_ranks(h, out=None):
+    n, _ = pr_graph_info(h)
+    if out is None:
+        out = np.empty(n, np.float64)
+    if out.dtype != np.float64 or out.size != n or not out.flags["C_CONTIGUOUS"]:
+        raise ValueError("out must be a contiguous float64 array of n elements")
+    _check(load().pr_ranks(h, out.ctypes.data), h)
+    return out
+
+
+def pr_ranks_device(h, out):
+    p, k = _dev_ptr(out, "float64")
+    n, _ = pr_graph_info(h)
+    if k != n:
+        raise ValueError("out must hold n elements")
+    _check(load().pr_ranks_device(h, p), h)
+    return out
+
+
+def pr_set_ranks(h, r):
+    a = np.ascontiguousarray(np.asarray(r, dtype=np.float64))
+    n, _ = pr_graph_info(h)
+    if a.size != n:
+        raise ValueError("ranks must hold n elements")
+    _check(load().pr_set_ranks(h, a.ctypes.data), h)
+
+
+def pr_set_ranks_device(h, r):
+    p, k = _dev_ptr(r, "float64")
+    n, _ = pr_graph_info(h)
+    if k != n:
+        raise ValueError("ranks must hold n elements")
+    _check(load().pr_set_ranks_device(h, p), h)
+
+
+def pr_get_csr(h, which=0):
+    n, m = pr_graph_info(h)
+    off = np.empty(n + 1, np.int64)
+    adj = np.empty(max(m, 1), np.int32)
+    _check(load().pr_get_csr(h, int(which), off.ctypes.data, adj.ctypes.data), h)
+    return off, adj[: off[-1]]
+
+
+def pr_last_delta(h):
+    nd, ni = ctypes.c_int64(), ctypes.c_int64()
+    lib = load()
+    _check(lib.pr_last_delta(h, ctypes.byref(nd), ctypes.byref(ni), None, None, None, None), h)
+    arrs = [np.empty(max(k, 1), np.int32) for k in (nd.value, nd.value, ni.value, ni.value)]
+    _check(lib.pr_last_delta(h, None, None, *[a.ctypes.data for a in arrs]), h)
+    dm = np.stack([arrs[0][: nd.value], arrs[1][: nd.value]], 1)
+    dp = np.stack([arrs[2][: ni.value], arrs[3][: ni.value]], 1)
+    return dm, dp
+
+
+def pr_affected(h, which):
+    n, _ = pr_graph_info(h)
+    f = np.empty(n, np.uint8)
+    _check(load().pr_affected(h, int(which), f.ctypes.data), h)
+    return f.astype(bool)
+
+
+def pr_last_error(h) -> str:
+    return load().pr_last_error(h).decode()
+
+
+# ------------------------------------------------------------------ convenience wrapper
+
+class Graph:
+    """Owning wrapper around a pr_graph handle."""
+
+    def __init__(self, handle):
+        self._h = handle
+
+    @classmethod
+    def from_csr(cls, n, row_off, col, stream=None):
+        return cls(pr_graph_create(n, row_off, col, stream))
+
+    @classmethod
+    def from_edges(cls, n, src, dst, device=False, keep_order=False, stream=None):
+        return cls(pr_graph_create_edges(n, src, dst, device, keep_order, stream))
+
+    def close(self):
+        if self._h:
+            pr_graph_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    @property
+    def handle(self):
+        return self._h
+
+    @property
+    def n(self):
+        return pr_graph_info(self._h)[0]
+
+    @property
+    def m(self):
+        return pr_graph_info(self._h)[1]
+
+    def apply_batch(self, del_src=(), del_dst=(), ins_src=(), ins_dst=()):
+        pr_apply_batch(self._h, del_src, del_dst, ins_src, ins_dst)
+
+    def apply_batch_device(self, del_src, del_dst, ins_src, ins_dst):
+        pr_apply_batch_device(self._h, del_src, del_dst, ins_src, ins_dst)
+
+    def update(self, method, **kw) -> Stats:
+        return pr_update(self._h, method, **kw)
+
+    def ranks(self, out=None):
+        return pr_ranks(self._h, out)
+
+    def ranks_device(self, out):
+        return pr_ranks_device(self._h, out)
+
+    def set_ranks(self, r):
+        pr_set_ranks(self._h, r)
+
+    def set_ranks_device(self, r):
+        pr_set_ranks_device(self._h, r)
+
+    def out_csr(self):
+        return pr_get_csr(self._h, 0)
+
+    def in_csr(self):
+        return pr_get_csr(self._h, 1)
+
+    def effective_delta(self):
+        return pr_last_delta(self._h)
+
+    def initial_affected(self):
+        return pr_affected(self._h, 0)
+
+    def dt_affected(self):
+        return pr_affected(self._h, 1)

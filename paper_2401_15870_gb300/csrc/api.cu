@@ -1,0 +1,791 @@
+// api.cu -- the C ABI of include/dfpr.h and the method drivers.
+//
+// pr_update drives the iterations of Alg. 1 (and of the comparators) from the
+// host: every iteration enqueues its kernels on the graph's stream and reads
+// back the 100-byte control block, which holds the iteration's L-inf change.
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <vector>
+#include "../../include/dfpr.h"
+#include "batch.cuh"
+#include "frontier.cuh"
+#include "graph.cuh"
+#include "prim.cuh"
+#include "sweep.cuh"
+
+using namespace dfpr;
+
+struct pr_graph {
+  Graph g;
+  cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};
+  double ms_apply = 0.0;
+  int32_t* lbits_tmp = nullptr;   // bits_to_list scratch
+  int64_t* ls_tmp = nullptr;      // list scan scratch
+  int64_t tiles_cap = 0;          // capacity of the tile tables
+  double* vec_tmp = nullptr;      // n doubles (rank import / export)
+};
+
+#define TRY(x)                                          \
+  do {                                                  \
+    cudaError_t _e = (x);                               \
+    if (_e != cudaSuccess) return (pr_status)cuda_fail(g, _e, #x); \
+  } while (0)
+
+#define RC(x)                       \
+  do {                              \
+    int _r = (x);                   \
+    if (_r != OK) return (pr_status)_r; \
+  } while (0)
+
+static int bits_for(int32_t n) {
+  int b = 1;
+  while ((1ll << b) < (int64_t)n) b++;
+  return b;
+}
+
+// ------------------------------------------------------------------ construction helpers
+
+__global__ void k_edge_keys(const int32_t* __restrict__ src, const int32_t* __restrict__ dst, int64_t m, int32_t n,
+                            int bits, uint64_t* __restrict__ keys) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < m + n; i += (int64_t)gridDim.x * blockDim.x) {
+    if (i < m) keys[i] = ((uint64_t)src[i] << bits) | (uint64_t)dst[i];
+    else keys[i] = ((uint64_t)(i - m) << bits) | (uint64_t)(i - m);
+  }
+}
+
+__global__ void k_csr_keys(const int64_t* __restrict__ off, const int32_t* __restrict__ col, int64_t m, int32_t n,
+                           int bits, uint64_t* __restrict__ keys) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < m + n; i += (int64_t)gridDim.x * blockDim.x) {
+    if (i < m) {
+      int32_t lo = 0, hi = n - 1;   // row u with off[u] <= i < off[u+1]
+      while (lo < hi) {
+        int32_t mid = (lo + hi + 1) >> 1;
+        if (off[mid] <= i) lo = mid;
+        else hi = mid - 1;
+      }
+      keys[i] = ((uint64_t)lo << bits) | (uint64_t)col[i];
+    } else {
+      keys[i] = ((uint64_t)(i - m) << bits) | (uint64_t)(i - m);
+    }
+  }
+}
+
+__global__ void k_validate_ids(const int32_t* __restrict__ a, int64_t m, int32_t n, unsigned long long* bad) {
+  unsigned long long c = 0;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < m; i += (int64_t)gridDim.x * blockDim.x)
+    c += (a[i] < 0 || a[i] >= n) ? 1 : 0;
+  if (c) atomicAdd(bad, c);
+}
+
+__global__ void k_check_ranks(const double* __restrict__ r, int32_t n, unsigned long long* bad, double* sum) {
+  double s = 0.0;
+  unsigned long long b = 0;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    double x = r[i];
+    if (!(x >= 0.0) || !isfinite(x)) b++;
+    else s += x;
+  }
+  if (b) atomicAdd(bad, b);
+  atomicAdd(sum, s);
+}
+
+__global__ void k_bits_to_bytes(const uint32_t* __restrict__ a, const uint32_t* __restrict__ b,
+                                const int32_t* __restrict__ perm, int32_t n, uint8_t* __restrict__ out) {
+  for (int64_t u = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; u < n; u += (int64_t)gridDim.x * blockDim.x) {
+    int32_t v = perm[u];
+    uint32_t w = a[v >> 5] | (b ? b[v >> 5] : 0u);
+    out[u] = (w >> (v & 31)) & 1u;
+  }
+}
+
+static pr_status alloc_state(pr_graph* h) {
+  Graph* g = &h->g;
+  int32_t n = g->n;
+  int64_t words = cdiv(n, 32) + 1;
+  TRY(dalloc(g, (void**)&g->R, sizeof(double) * n));
+  for (int i = 0; i < 2; i++) {
+    TRY(dalloc(g, (void**)&g->C[i], sizeof(long long) * (n + 1)));
+    TRY(cudaMemsetAsync(g->C[i], 0, sizeof(long long) * (n + 1), g->stream));
+    TRY(dalloc(g, (void**)&g->bits[i], sizeof(uint32_t) * words));
+    TRY(dalloc(g, (void**)&g->wl[i], sizeof(int32_t) * n));
+  }
+  TRY(dalloc(g, (void**)&g->ever, sizeof(uint32_t) * words));
+  TRY(dalloc(g, (void**)&g->aux, sizeof(uint32_t) * words));
+  TRY(dalloc(g, (void**)&g->aux2, sizeof(uint32_t) * words));
+  TRY(dalloc(g, (void**)&g->xl, sizeof(int32_t) * n));
+  TRY(dalloc(g, (void**)&g->rnew, sizeof(double) * n));
+  TRY(dalloc(g, (void**)&g->qs, sizeof(int64_t) * (n + 1)));
+  TRY(dalloc(g, (void**)&g->xqs, sizeof(int64_t) * (n + 1)));
+  TRY(dalloc(g, (void**)&g->gacc, sizeof(long long) * n));
+  TRY(cudaMemsetAsync(g->gacc, 0, sizeof(long long) * n, g->stream));
+  TRY(dalloc(g, (void**)&g->gcnt, sizeof(int32_t) * n));
+  TRY(cudaMemsetAsync(g->gcnt, 0, sizeof(int32_t) * n, g->stream));
+  TRY(dalloc(g, (void**)&g->tab_sc, sizeof(double) * TAB));
+  TRY(dalloc(g, (void**)&g->tab_cl, sizeof(double) * TAB));
+  TRY(dalloc(g, (void**)&g->ctl, sizeof(Ctl)));
+  TRY(cudaMemsetAsync(g->ctl, 0, sizeof(Ctl), g->stream));
+  TRY(cudaMallocHost((void**)&g->ctl_h, sizeof(Ctl)));
+  TRY(dalloc(g, (void**)&h->lbits_tmp, sizeof(int32_t) * bits_to_list_tmp(n)));
+  TRY(dalloc(g, (void**)&h->ls_tmp, sizeof(int64_t) * list_scan_tmp(n)));
+  TRY(dalloc(g, (void**)&h->vec_tmp, sizeof(double) * (n > 4 ? n : 4)));
+  TRY(launch_tables(g->tab_sc, g->tab_cl, 0.85, g->stream));
+  g->tab_alpha = 0.85;
+  for (int i = 0; i < 4; i++) TRY(cudaEventCreate(&h->ev[i]));
+  return PR_OK;
+}
+
+// grow the tile tables to cover any list of the current graph
+static pr_status ensure_tiles(pr_graph* h) {
+  Graph* g = &h->g;
+  int64_t need = cdiv(g->m / 4 + g->n + 1, SW_TILE_Q) + 2;
+  if (need <= h->tiles_cap) return PR_OK;
+  int64_t cap = need + need / 4 + 16;
+  for (auto& p : g->allocs)
+    if (p == g->tfirst || p == g->xtfirst) {
+      cudaFree(p);
+      p = nullptr;
+    }
+  TRY(dalloc(g, (void**)&g->tfirst, sizeof(int32_t) * cap));
+  TRY(dalloc(g, (void**)&g->xtfirst, sizeof(int32_t) * cap));
+  h->tiles_cap = cap;
+  return PR_OK;
+}
+
+static pr_status finish_create(pr_graph* h, uint64_t* keys, int64_t nkeys, pr_graph** out) {
+  Graph* g = &h->g;
+  RC(build_graph_from_user_keys(g, keys, nkeys));
+  pr_status st = alloc_state(h);
+  if (st != PR_OK) return st;
+  st = ensure_tiles(h);
+  if (st != PR_OK) return st;
+  TRY(cudaStreamSynchronize(g->stream));
+  *out = h;
+  return PR_OK;
+}
+
+static void destroy_handle(pr_graph* h) {
+  if (!h) return;
+  Graph* g = &h->g;
+  if (g->stream) cudaStreamSynchronize(g->stream);
+  dfree_all(g);
+  if (g->dmin) cudaFree(g->dmin);
+  if (g->dplus) cudaFree(g->dplus);
+  if (g->ctl_h) cudaFreeHost(g->ctl_h);
+  for (int i = 0; i < 4; i++)
+    if (h->ev[i]) cudaEventDestroy(h->ev[i]);
+  delete h;
+}
+
+// ------------------------------------------------------------------ drivers
+
+static pr_status read_ctl(Graph* g) {
+  TRY(cudaMemcpyAsync(g->ctl_h, g->ctl, sizeof(Ctl), cudaMemcpyDeviceToHost, g->stream));
+  TRY(cudaStreamSynchronize(g->stream));
+  if (g->ctl_h->status) return (pr_status)set_error(g, ECUDA_, "device reported an inconsistent tile table");
+  return PR_OK;
+}
+
+static double ctl_dR(const Ctl* c) {
+  double d;
+  unsigned long long b = c->dR_last;
+  memcpy(&d, &b, sizeof(d));
+  return d;
+}
+
+static SweepParams base_params(Graph* g, double alpha, double tau_f, double tau_p) {
+  SweepParams p;
+  memset(&p, 0, sizeof(p));
+  p.n = g->n;
+  p.ioff = g->in.off;
+  p.ideg = g->in.deg;
+  p.icol = g->in.col;
+  p.odeg = g->out.deg;
+  p.R = g->R;
+  p.rnew = g->rnew;
+  p.tab_sc = g->tab_sc;
+  p.tab_cl = g->tab_cl;
+  p.alpha = alpha;
+  p.C0 = (1.0 - alpha) / (double)g->n;
+  p.tau_f = tau_f;
+  p.tau_p = tau_p;
+  p.gacc = g->gacc;
+  p.gcnt = g->gcnt;
+  p.ctl = g->ctl;
+  return p;
+}
+
+static ExpandParams expand_params(Graph* g, const int32_t* list, const int32_t* count, uint32_t* bits, uint32_t* ever,
+                                  int32_t* wl, int32_t* cnt) {
+  ExpandParams e;
+  memset(&e, 0, sizeof(e));
+  e.n = g->n;
+  e.ooff = g->out.off;
+  e.ocol = g->out.col;
+  e.list = list;
+  e.count = count;
+  e.qs = g->xqs;
+  e.tfirst = g->xtfirst;
+  e.ntiles_dev = &g->ctl->xntiles;
+  e.bits = bits;
+  e.ever = ever;
+  e.wl = wl;
+  e.cnt = cnt;
+  e.id_bits = g->id_bits;
+  return e;
+}
+
+// expand the listed vertices' out-rows (expander tables)
+static pr_status run_expand(pr_graph* h, const int32_t* list, const int32_t* count, uint32_t* bits, uint32_t* ever,
+                            int32_t* wl, int32_t* cnt, const uint32_t* ins_src_bits) {
+  Graph* g = &h->g;
+  TRY(launch_list_scan(list, count, g->out.deg, g->n, g->xqs, g->xtfirst, &g->ctl->xqtot, &g->ctl->xntiles, h->ls_tmp,
+                       g->stream));
+  ExpandParams e = expand_params(g, list, count, bits, ever, wl, cnt);
+  e.ins_src_bits = ins_src_bits;
+  e.dplus = g->dplus;
+  e.n_dplus = g->n_dplus;
+  TRY(launch_expand(e, g->stream));
+  return PR_OK;
+}
+
+// DF / DF-P initial marking (Alg. 1) into bits[0] / wl[0] / ever
+static pr_status initial_marking(pr_graph* h) {
+  Graph* g = &h->g;
+  cudaStream_t s = g->stream;
+  int64_t words = cdiv(g->n, 32) + 1;
+  for (uint32_t* b : {g->bits[0], g->bits[1], g->ever, g->aux})
+    TRY(cudaMemsetAsync(b, 0, sizeof(uint32_t) * words, s));
+  TRY(cudaMemsetAsync(g->ctl, 0, sizeof(Ctl), s));
+  // sources of the effective change, each once
+  TRY(launch_mark_sources(g->dmin, g->n_dmin, g->dplus, g->n_dplus, g->id_bits, g->aux, g->xl, &g->ctl->nexp, s));
+  // G_t.out(u) for every source u ...
+  pr_status st = run_expand(h, g->xl, &g->ctl->nexp, g->bits[0], g->ever, g->wl[0], &g->ctl->count[0], nullptr);
+  if (st != PR_OK) return st;
+  // ... and the targets of deleted edges, which complete G_{t-1}.out(u)
+  TRY(launch_mark_targets(g->dmin, g->n_dmin, g->id_bits, g->bits[0], g->ever, g->wl[0], &g->ctl->count[0], s));
+  TRY(cudaMemsetAsync(&g->ctl->nexp, 0, sizeof(int32_t), s));
+  return PR_OK;
+}
+
+// Dynamic Traversal affected set: reach(G_t) in aux, reach(G_{t-1}) in aux2;
+// the union as an ascending list in wl[0] / count[0]
+static pr_status dt_affected(pr_graph* h) {
+  Graph* g = &h->g;
+  cudaStream_t s = g->stream;
+  int64_t words = cdiv(g->n, 32) + 1;
+  for (uint32_t* b : {g->aux, g->aux2, g->bits[1]}) TRY(cudaMemsetAsync(b, 0, sizeof(uint32_t) * words, s));
+  TRY(launch_source_bits(g->dplus, g->n_dplus, g->id_bits, g->bits[1], s));
+  for (int which = 0; which < 2; which++) {
+    uint32_t* vis = which == 0 ? g->aux : g->aux2;
+    TRY(cudaMemsetAsync(g->ctl, 0, sizeof(Ctl), s));
+    TRY(launch_mark_sources(g->dmin, g->n_dmin, g->dplus, g->n_dplus, g->id_bits, vis, g->wl[0], &g->ctl->count[0], s));
+    int c = 0;
+    for (;;) {
+      pr_status st = run_expand(h, g->wl[c], &g->ctl->count[c], vis, nullptr, g->wl[1 - c], &g->ctl->count[1 - c],
+                                which == 1 ? g->bits[1] : nullptr);
+      if (st != PR_OK) return st;
+      if (which == 1)
+        TRY(launch_follow_edges(g->dmin, g->n_dmin, g->id_bits, vis, g->wl[1 - c], &g->ctl->count[1 - c], s));
+      TRY(cudaMemsetAsync(&g->ctl->count[c], 0, sizeof(int32_t), s));
+      c ^= 1;
+      st = read_ctl(g);
+      if (st != PR_OK) return st;
+      if (g->ctl_h->count[c] == 0) break;
+    }
+  }
+  TRY(cudaMemsetAsync(g->ctl, 0, sizeof(Ctl), s));
+  TRY(launch_bits_to_list(g->aux, g->aux2, g->n, g->wl[0], &g->ctl->count[0], h->lbits_tmp, s));
+  return PR_OK;
+}
+
+static pr_status run_update(pr_graph* h, int method, double alpha, double tau, double tau_f, double tau_p,
+                            int32_t max_iter, pr_stats* out) {
+  Graph* g = &h->g;
+  cudaStream_t s = g->stream;
+  int32_t n = g->n;
+  TRY(cudaEventRecord(h->ev[2], s));
+  if (g->tab_alpha != alpha) {
+    TRY(launch_tables(g->tab_sc, g->tab_cl, alpha, s));
+    g->tab_alpha = alpha;
+  }
+  SweepParams p = base_params(g, alpha, tau_f, tau_p);
+  int64_t ever = 0;
+  int32_t iters = 0;
+  double dR = 0.0;
+  bool conv = false;
+  if (method == PR_STATIC || method == PR_NAIVE_DYNAMIC) {
+    TRY(cudaMemsetAsync(g->ctl, 0, sizeof(Ctl), s));
+    if (method == PR_STATIC) TRY(launch_init_uniform(g->R, g->C[g->ccur], g->out.deg, g->tab_sc, n, s));
+    p.tfirst = g->full_tfirst;
+    p.ntiles_host = g->full_ntiles;
+    for (int32_t it = 0; it < max_iter; it++) {
+      p.Ccur = g->C[g->ccur];
+      p.Cnext = g->C[1 - g->ccur];
+      TRY(launch_sweep(SWEEP_FULL, p, s));
+      TRY(launch_control(g->ctl, 0, s));
+      g->ccur ^= 1;
+      pr_status st = read_ctl(g);
+      if (st != PR_OK) return st;
+      iters = it + 1;
+      dR = ctl_dR(g->ctl_h);
+      if (dR <= tau) {
+        conv = true;
+        break;
+      }
+    }
+    ever = n;
+  } else if (method == PR_DYNAMIC_TRAVERSAL) {
+    pr_status st = dt_affected(h);
+    if (st != PR_OK) return st;
+    TRY(launch_list_scan(g->wl[0], &g->ctl->count[0], g->in.deg, n, g->qs, g->tfirst, &g->ctl->qtot, &g->ctl->ntiles,
+                         h->ls_tmp, s));
+    p.list = g->wl[0];
+    p.count = &g->ctl->count[0];
+    p.qs = g->qs;
+    p.tfirst = g->tfirst;
+    p.ntiles_dev = &g->ctl->ntiles;
+    p.Ccur = g->C[g->ccur];
+    for (int32_t it = 0; it < max_iter; it++) {
+      TRY(launch_sweep(SWEEP_LIST, p, s));
+      TRY(launch_commit(g->wl[0], &g->ctl->count[0], g->rnew, g->R, g->C[g->ccur], g->out.deg, g->tab_sc, nullptr, n,
+                        s));
+      TRY(launch_control(g->ctl, 0, s));
+      st = read_ctl(g);
+      if (st != PR_OK) return st;
+      iters = it + 1;
+      dR = ctl_dR(g->ctl_h);
+      if (dR <= tau) {
+        conv = true;
+        break;
+      }
+    }
+    if (max_iter == 0) {
+      st = read_ctl(g);
+      if (st != PR_OK) return st;
+    }
+    ever = g->ctl_h->count[0];
+  } else {
+    pr_status st = initial_marking(h);
+    if (st != PR_OK) return st;
+    int mode = method == PR_DF ? SWEEP_DF : SWEEP_DFP;
+    int cur = 0;
+    for (int32_t it = 0; it < max_iter; it++) {
+      TRY(launch_list_scan(g->wl[cur], &g->ctl->count[cur], g->in.deg, n, g->qs, g->tfirst, &g->ctl->qtot,
+                           &g->ctl->ntiles, h->ls_tmp, s));
+      p.list = g->wl[cur];
+      p.count = &g->ctl->count[cur];
+      p.qs = g->qs;
+      p.tfirst = g->tfirst;
+      p.ntiles_dev = &g->ctl->ntiles;
+      p.Ccur = g->C[g->ccur];
+      p.bits_next = g->bits[1 - cur];
+      p.ever = g->ever;
+      p.wl_next = g->wl[1 - cur];
+      p.cnt_next = &g->ctl->count[1 - cur];
+      p.xl = g->xl;
+      p.cnt_x = &g->ctl->nexp;
+      TRY(launch_sweep(mode, p, s));
+      st = run_expand(h, g->xl, &g->ctl->nexp, g->bits[1 - cur], g->ever, g->wl[1 - cur], &g->ctl->count[1 - cur],
+                      nullptr);
+      if (st != PR_OK) return st;
+      TRY(launch_commit(g->wl[cur], &g->ctl->count[cur], g->rnew, g->R, g->C[g->ccur], g->out.deg, g->tab_sc,
+                        g->bits[cur], n, s));
+      TRY(launch_control(g->ctl, 1, s));
+      cur ^= 1;
+      st = read_ctl(g);
+      if (st != PR_OK) return st;
+      iters = it + 1;
+      dR = ctl_dR(g->ctl_h);
+      if (dR <= tau) {
+        conv = true;
+        break;
+      }
+    }
+    long long* cnt = (long long*)h->vec_tmp;
+    TRY(launch_popcount(g->ever, cdiv(n, 32), cnt, s));
+    long long ev = 0;
+    TRY(cudaMemcpyAsync(&ev, cnt, sizeof(ev), cudaMemcpyDeviceToHost, s));
+    TRY(cudaStreamSynchronize(s));
+    ever = ev;
+    if (max_iter == 0) {
+      st = read_ctl(g);
+      if (st != PR_OK) return st;
+    }
+  }
+  TRY(cudaEventRecord(h->ev[3], s));
+  TRY(cudaEventSynchronize(h->ev[3]));
+  float ms = 0.f;
+  TRY(cudaEventElapsedTime(&ms, h->ev[2], h->ev[3]));
+  g->has_ranks = true;
+  if (out) {
+    out->iterations = iters;
+    out->converged = conv ? 1 : 0;
+    out->delta_R = iters ? dR : 0.0;
+    out->vertices_ever_affected = ever;
+    out->edges_processed = g->ctl_h->edges;
+    out->vertices_processed = g->ctl_h->verts;
+    out->eff_deletions = g->n_dmin;
+    out->eff_insertions = g->n_dplus;
+    out->ms_apply = h->ms_apply;
+    out->ms_update = ms;
+  }
+  return PR_OK;
+}
+
+// ------------------------------------------------------------------ C ABI
+
+extern "C" {
+
+static pr_status create_from_keys_host_edges(int32_t n, int64_t m, const int32_t* src, const int32_t* dst,
+                                             bool dev_ptrs, int32_t flags, void* stream, pr_graph** out) {
+  pr_graph* h = new (std::nothrow) pr_graph();
+  if (!h) return PR_ENOMEM;
+  Graph* g = &h->g;
+  g->n = n;
+  g->id_bits = bits_for(n);
+  g->stream = (cudaStream_t)stream;
+  g->relabel = (flags & 1) == 0;
+  cudaGetDevice(&g->dev);
+  uint64_t* keys = nullptr;
+  int32_t *ds = nullptr, *dd = nullptr;
+  pr_status st = PR_OK;
+  do {
+    cudaError_t e = cudaMalloc(&keys, sizeof(uint64_t) * (size_t)(m + n));
+    if (e != cudaSuccess) { st = (pr_status)cuda_fail(g, e, "cudaMalloc(keys)"); break; }
+    const int32_t *s_dev = src, *d_dev = dst;
+    if (!dev_ptrs && m > 0) {
+      if ((e = cudaMalloc(&ds, sizeof(int32_t) * m)) != cudaSuccess ||
+          (e = cudaMalloc(&dd, sizeof(int32_t) * m)) != cudaSuccess ||
+          (e = cudaMemcpyAsync(ds, src, sizeof(int32_t) * m, cudaMemcpyHostToDevice, g->stream)) != cudaSuccess ||
+          (e = cudaMemcpyAsync(dd, dst, sizeof(int32_t) * m, cudaMemcpyHostToDevice, g->stream)) != cudaSuccess) {
+        st = (pr_status)cuda_fail(g, e, "copy edge list");
+        break;
+      }
+      s_dev = ds;
+      d_dev = dd;
+    }
+    if (dev_ptrs && m > 0) {
+      unsigned long long* bad;
+      if ((e = cudaMalloc(&bad, sizeof(*bad))) != cudaSuccess) { st = (pr_status)cuda_fail(g, e, "cudaMalloc"); break; }
+      cudaMemsetAsync(bad, 0, sizeof(*bad), g->stream);
+      k_validate_ids<<<grid_for(m, 256), 256, 0, g->stream>>>(src, m, n, bad);
+      k_validate_ids<<<grid_for(m, 256), 256, 0, g->stream>>>(dst, m, n, bad);
+      unsigned long long hb = 0;
+      cudaMemcpyAsync(&hb, bad, sizeof(hb), cudaMemcpyDeviceToHost, g->stream);
+      e = cudaStreamSynchronize(g->stream);
+      cudaFree(bad);
+      if (e != cudaSuccess) { st = (pr_status)cuda_fail(g, e, "validate"); break; }
+      if (hb) { st = PR_ERANGE; break; }
+    }
+    k_edge_keys<<<grid_for(m + n, 256), 256, 0, g->stream>>>(s_dev, d_dev, m, n, g->id_bits, keys);
+    if ((e = cudaGetLastError()) != cudaSuccess) { st = (pr_status)cuda_fail(g, e, "k_edge_keys"); break; }
+    if (ds) { cudaStreamSynchronize(g->stream); cudaFree(ds); ds = nullptr; }
+    if (dd) { cudaFree(dd); dd = nullptr; }
+    st = finish_create(h, keys, m + n, out);
+  } while (0);
+  if (ds) cudaFree(ds);
+  if (dd) cudaFree(dd);
+  if (keys) cudaFree(keys);
+  if (st != PR_OK) destroy_handle(h);
+  return st;
+}
+
+pr_status pr_graph_create_edges(int32_t n, int64_t m, const int32_t* src, const int32_t* dst, int32_t device_ptrs,
+                                int32_t flags, void* stream, pr_graph** out) {
+  if (!out) return PR_EINVAL;
+  *out = nullptr;
+  if (n < 1 || m < 0 || (m > 0 && (!src || !dst)) || (flags & ~1)) return PR_EINVAL;
+  if ((int64_t)n + m >= (int64_t(1) << 31)) return PR_EINVAL;
+  if (!device_ptrs)
+    for (int64_t i = 0; i < m; i++)
+      if (src[i] < 0 || src[i] >= n || dst[i] < 0 || dst[i] >= n) return PR_ERANGE;
+  return create_from_keys_host_edges(n, m, src, dst, device_ptrs != 0, flags, stream, out);
+}
+
+pr_status pr_graph_create(int32_t n, int64_t m, const int64_t* row_off, const int32_t* col, void* stream,
+                          pr_graph** out) {
+  if (!out) return PR_EINVAL;
+  *out = nullptr;
+  if (n < 1 || m < 0 || !row_off || (m > 0 && !col)) return PR_EINVAL;
+  if ((int64_t)n + m >= (int64_t(1) << 31)) return PR_EINVAL;
+  if (row_off[0] != 0 || row_off[n] != m) return PR_EINVAL;
+  for (int32_t u = 0; u < n; u++)
+    if (row_off[u + 1] < row_off[u]) return PR_EINVAL;
+  for (int64_t i = 0; i < m; i++)
+    if (col[i] < 0 || col[i] >= n) return PR_ERANGE;
+  pr_graph* h = new (std::nothrow) pr_graph();
+  if (!h) return PR_ENOMEM;
+  Graph* g = &h->g;
+  g->n = n;
+  g->id_bits = bits_for(n);
+  g->stream = (cudaStream_t)stream;
+  cudaGetDevice(&g->dev);
+  uint64_t* keys = nullptr;
+  int64_t* doff = nullptr;
+  int32_t* dcol = nullptr;
+  pr_status st = PR_OK;
+  cudaError_t e;
+  if ((e = cudaMalloc(&keys, sizeof(uint64_t) * (size_t)(m + n))) != cudaSuccess ||
+      (e = cudaMalloc(&doff, sizeof(int64_t) * (size_t)(n + 1))) != cudaSuccess ||
+      (e = cudaMalloc(&dcol, sizeof(int32_t) * (size_t)(m > 0 ? m : 1))) != cudaSuccess ||
+      (e = cudaMemcpyAsync(doff, row_off, sizeof(int64_t) * (n + 1), cudaMemcpyHostToDevice, g->stream)) != cudaSuccess ||
+      (m > 0 && (e = cudaMemcpyAsync(dcol, col, sizeof(int32_t) * m, cudaMemcpyHostToDevice, g->stream)) != cudaSuccess)) {
+    st = (pr_status)cuda_fail(g, e, "pr_graph_create copy");
+  } else {
+    k_csr_keys<<<grid_for(m + n, 256), 256, 0, g->stream>>>(doff, dcol, m, n, g->id_bits, keys);
+    e = cudaStreamSynchronize(g->stream);
+    cudaFree(doff);
+    cudaFree(dcol);
+    doff = nullptr;
+    dcol = nullptr;
+    if (e != cudaSuccess) st = (pr_status)cuda_fail(g, e, "k_csr_keys");
+    else st = finish_create(h, keys, m + n, out);
+  }
+  if (doff) cudaFree(doff);
+  if (dcol) cudaFree(dcol);
+  if (keys) cudaFree(keys);
+  if (st != PR_OK) destroy_handle(h);
+  return st;
+}
+
+void pr_graph_destroy(pr_graph* g) { destroy_handle(g); }
+
+pr_status pr_set_stream(pr_graph* h, void* stream) {
+  if (!h) return PR_EINVAL;
+  Graph* g = &h->g;
+  TRY(cudaStreamSynchronize(g->stream));
+  g->stream = (cudaStream_t)stream;
+  return PR_OK;
+}
+
+static pr_status apply_common(pr_graph* h, const int32_t* ds, const int32_t* dd, int64_t nd, const int32_t* is,
+                              const int32_t* id, int64_t ni, bool device) {
+  if (!h || nd < 0 || ni < 0 || (nd > 0 && (!ds || !dd)) || (ni > 0 && (!is || !id))) return PR_EINVAL;
+  Graph* g = &h->g;
+  g->err.clear();
+  cudaStream_t s = g->stream;
+  int32_t n = g->n;
+  TRY(cudaEventRecord(h->ev[0], s));
+  int rc;
+  if (device) {
+    rc = apply_batch_device(g, ds, dd, nd, is, id, ni, false);
+  } else {
+    for (int64_t i = 0; i < nd; i++)
+      if (ds[i] < 0 || ds[i] >= n || dd[i] < 0 || dd[i] >= n)
+        return (pr_status)set_error(g, ERANGE_, "pr_apply_batch: vertex id out of range");
+    for (int64_t i = 0; i < ni; i++)
+      if (is[i] < 0 || is[i] >= n || id[i] < 0 || id[i] >= n)
+        return (pr_status)set_error(g, ERANGE_, "pr_apply_batch: vertex id out of range");
+    int64_t nk = nd + ni;
+    void* stage;
+    TRY(scratch_get(g, 0, sizeof(int32_t) * (size_t)(2 * nk + 4) + 1024, &stage));
+    int32_t* b = (int32_t*)stage;
+    if (nd) {
+      TRY(cudaMemcpyAsync(b, ds, sizeof(int32_t) * nd, cudaMemcpyHostToDevice, s));
+      TRY(cudaMemcpyAsync(b + nd, dd, sizeof(int32_t) * nd, cudaMemcpyHostToDevice, s));
+    }
+    if (ni) {
+      TRY(cudaMemcpyAsync(b + 2 * nd, is, sizeof(int32_t) * ni, cudaMemcpyHostToDevice, s));
+      TRY(cudaMemcpyAsync(b + 2 * nd + ni, id, sizeof(int32_t) * ni, cudaMemcpyHostToDevice, s));
+    }
+    rc = apply_batch_device(g, b, b + nd, nd, b + 2 * nd, b + 2 * nd + ni, ni, true);
+  }
+  if (rc != OK) return (pr_status)rc;
+  g->m += g->n_dplus - g->n_dmin;
+  pr_status st = ensure_tiles(h);
+  if (st != PR_OK) return st;
+  TRY(cudaEventRecord(h->ev[1], s));
+  TRY(cudaEventSynchronize(h->ev[1]));
+  float ms = 0.f;
+  TRY(cudaEventElapsedTime(&ms, h->ev[0], h->ev[1]));
+  h->ms_apply = ms;
+  return PR_OK;
+}
+
+pr_status pr_apply_batch(pr_graph* h, const int32_t* del_src, const int32_t* del_dst, int64_t n_del,
+                         const int32_t* ins_src, const int32_t* ins_dst, int64_t n_ins) {
+  return apply_common(h, del_src, del_dst, n_del, ins_src, ins_dst, n_ins, false);
+}
+
+pr_status pr_apply_batch_device(pr_graph* h, const int32_t* del_src, const int32_t* del_dst, int64_t n_del,
+                                const int32_t* ins_src, const int32_t* ins_dst, int64_t n_ins) {
+  return apply_common(h, del_src, del_dst, n_del, ins_src, ins_dst, n_ins, true);
+}
+
+pr_status pr_update(pr_graph* h, pr_method method, double alpha, double tau, const pr_options* opts,
+                    pr_stats* stats) {
+  if (!h) return PR_EINVAL;
+  Graph* g = &h->g;
+  g->err.clear();
+  double tau_f = 1e-6, tau_p = 1e-6;
+  int32_t max_iter = 500;
+  if (opts) {
+    tau_f = opts->tau_f;
+    tau_p = opts->tau_p;
+    max_iter = opts->max_iter;
+    if (opts->flags != 0) return PR_EINVAL;
+  }
+  if ((int)method < PR_STATIC || (int)method > PR_DFP) return PR_EINVAL;
+  if (!(alpha >= 0.0 && alpha < 1.0) || !(tau >= 0.0) || !(tau_f >= 0.0) || !(tau_p >= 0.0) || max_iter < 0)
+    return PR_EINVAL;
+  if (method != PR_STATIC && !g->has_ranks)
+    return (pr_status)set_error(g, ENORANKS_, "pr_update: a dynamic method needs ranks (pr_set_ranks or a previous update)");
+  return run_update(h, (int)method, alpha, tau, tau_f, tau_p, max_iter, stats);
+}
+
+pr_status pr_ranks_device(const pr_graph* hc, double* out) {
+  pr_graph* h = const_cast<pr_graph*>(hc);
+  if (!h || !out) return PR_EINVAL;
+  Graph* g = &h->g;
+  if (!g->has_ranks) return PR_ENORANKS;
+  TRY(launch_gather_f64(g->R, g->perm, out, g->n, g->stream));
+  TRY(cudaStreamSynchronize(g->stream));
+  return PR_OK;
+}
+
+pr_status pr_ranks(const pr_graph* hc, double* out) {
+  pr_graph* h = const_cast<pr_graph*>(hc);
+  if (!h || !out) return PR_EINVAL;
+  Graph* g = &h->g;
+  if (!g->has_ranks) return PR_ENORANKS;
+  TRY(launch_gather_f64(g->R, g->perm, h->vec_tmp, g->n, g->stream));
+  TRY(cudaMemcpyAsync(out, h->vec_tmp, sizeof(double) * g->n, cudaMemcpyDeviceToHost, g->stream));
+  TRY(cudaStreamSynchronize(g->stream));
+  return PR_OK;
+}
+
+static pr_status set_ranks_from_device(pr_graph* h, const double* dev) {
+  Graph* g = &h->g;
+  cudaStream_t s = g->stream;
+  TRY(launch_scatter_f64(dev, g->perm, g->R, g->n, s));
+  TRY(launch_contrib_all(g->R, g->C[g->ccur], g->out.deg, g->tab_sc, g->n, s));
+  TRY(cudaStreamSynchronize(s));
+  g->has_ranks = true;
+  return PR_OK;
+}
+
+pr_status pr_set_ranks(pr_graph* h, const double* r) {
+  if (!h || !r) return PR_EINVAL;
+  Graph* g = &h->g;
+  double sum = 0.0;
+  for (int32_t i = 0; i < g->n; i++) {
+    if (!(r[i] >= 0.0) || !std::isfinite(r[i])) return (pr_status)set_error(g, EINVAL_, "pr_set_ranks: bad rank");
+    sum += r[i];
+  }
+  if (sum > 2.0) return (pr_status)set_error(g, EINVAL_, "pr_set_ranks: ranks sum above 2");
+  TRY(cudaMemcpyAsync(h->vec_tmp, r, sizeof(double) * g->n, cudaMemcpyHostToDevice, g->stream));
+  return set_ranks_from_device(h, h->vec_tmp);
+}
+
+pr_status pr_set_ranks_device(pr_graph* h, const double* r) {
+  if (!h || !r) return PR_EINVAL;
+  Graph* g = &h->g;
+  cudaStream_t s = g->stream;
+  struct {
+    unsigned long long bad;
+    double sum;
+  } hv, *dv = (decltype(dv))h->vec_tmp;
+  TRY(cudaMemsetAsync(dv, 0, sizeof(hv), s));
+  k_check_ranks<<<grid_for(g->n, 256), 256, 0, s>>>(r, g->n, &dv->bad, &dv->sum);
+  TRY(cudaMemcpyAsync(&hv, dv, sizeof(hv), cudaMemcpyDeviceToHost, s));
+  TRY(cudaStreamSynchronize(s));
+  if (hv.bad || hv.sum > 2.0) return (pr_status)set_error(g, EINVAL_, "pr_set_ranks_device: bad ranks");
+  return set_ranks_from_device(h, r);
+}
+
+pr_status pr_graph_info(const pr_graph* h, int32_t* n, int64_t* m) {
+  if (!h) return PR_EINVAL;
+  if (n) *n = h->g.n;
+  if (m) *m = h->g.m;
+  return PR_OK;
+}
+
+pr_status pr_get_csr(const pr_graph* hc, int32_t which, int64_t* off, int32_t* adj) {
+  pr_graph* h = const_cast<pr_graph*>(hc);
+  if (!h || !off || !adj || (which != 0 && which != 1)) return PR_EINVAL;
+  Graph* g = &h->g;
+  const Csr& c = which == 0 ? g->out : g->in;
+  int32_t n = g->n;
+  std::vector<int64_t> o(n + 1);
+  std::vector<int32_t> d(n), col(c.cap), perm(n), iperm(n);
+  cudaStream_t s = g->stream;
+  TRY(cudaMemcpyAsync(o.data(), c.off, sizeof(int64_t) * (n + 1), cudaMemcpyDeviceToHost, s));
+  TRY(cudaMemcpyAsync(d.data(), c.deg, sizeof(int32_t) * n, cudaMemcpyDeviceToHost, s));
+  TRY(cudaMemcpyAsync(col.data(), c.col, sizeof(int32_t) * c.cap, cudaMemcpyDeviceToHost, s));
+  TRY(cudaMemcpyAsync(perm.data(), g->perm, sizeof(int32_t) * n, cudaMemcpyDeviceToHost, s));
+  TRY(cudaMemcpyAsync(iperm.data(), g->iperm, sizeof(int32_t) * n, cudaMemcpyDeviceToHost, s));
+  TRY(cudaStreamSynchronize(s));
+  int64_t w = 0;
+  for (int32_t u = 0; u < n; u++) {
+    off[u] = w;
+    int32_t r = perm[u];
+    int64_t start = w;
+    for (int32_t x = 0; x < d[r]; x++) adj[w++] = iperm[col[o[r] + x]];
+    std::sort(adj + start, adj + w);
+  }
+  off[n] = w;
+  return PR_OK;
+}
+
+pr_status pr_last_delta(const pr_graph* hc, int64_t* n_del, int64_t* n_ins, int32_t* del_src, int32_t* del_dst,
+                        int32_t* ins_src, int32_t* ins_dst) {
+  pr_graph* h = const_cast<pr_graph*>(hc);
+  if (!h) return PR_EINVAL;
+  Graph* g = &h->g;
+  if (n_del) *n_del = g->n_dmin;
+  if (n_ins) *n_ins = g->n_dplus;
+  int32_t n = g->n;
+  std::vector<int32_t> iperm(n);
+  TRY(cudaMemcpy(iperm.data(), g->iperm, sizeof(int32_t) * n, cudaMemcpyDeviceToHost));
+  uint64_t mask = (1ull << g->id_bits) - 1;
+  for (int side = 0; side < 2; side++) {
+    int64_t k = side ? g->n_dplus : g->n_dmin;
+    int32_t* os = side ? ins_src : del_src;
+    int32_t* od = side ? ins_dst : del_dst;
+    if (!k || !os || !od) continue;
+    std::vector<uint64_t> keys(k);
+    TRY(cudaMemcpy(keys.data(), side ? g->dplus : g->dmin, sizeof(uint64_t) * k, cudaMemcpyDeviceToHost));
+    std::vector<std::pair<int32_t, int32_t>> e(k);
+    for (int64_t i = 0; i < k; i++) e[i] = {iperm[keys[i] >> g->id_bits], iperm[keys[i] & mask]};
+    std::sort(e.begin(), e.end());
+    for (int64_t i = 0; i < k; i++) {
+      os[i] = e[i].first;
+      od[i] = e[i].second;
+    }
+  }
+  return PR_OK;
+}
+
+pr_status pr_affected(pr_graph* h, int32_t which, uint8_t* flags) {
+  if (!h || !flags || (which != 0 && which != 1)) return PR_EINVAL;
+  Graph* g = &h->g;
+  cudaStream_t s = g->stream;
+  pr_status st = which == 0 ? initial_marking(h) : dt_affected(h);
+  if (st != PR_OK) return st;
+  uint8_t* tmp = (uint8_t*)h->vec_tmp;
+  if (which == 0) k_bits_to_bytes<<<grid_for(g->n, 256), 256, 0, s>>>(g->bits[0], nullptr, g->perm, g->n, tmp);
+  else k_bits_to_bytes<<<grid_for(g->n, 256), 256, 0, s>>>(g->aux, g->aux2, g->perm, g->n, tmp);
+  TRY(cudaMemcpyAsync(flags, tmp, g->n, cudaMemcpyDeviceToHost, s));
+  TRY(cudaStreamSynchronize(s));
+  return PR_OK;
+}
+
+const char* pr_last_error(const pr_graph* h) { return h ? h->g.err.c_str() : ""; }
+
+const char* pr_status_string(pr_status s) {
+  switch (s) {
+    case PR_OK: return "PR_OK";
+    case PR_EINVAL: return "PR_EINVAL";
+    case PR_ERANGE: return "PR_ERANGE";
+    case PR_ENOMEM: return "PR_ENOMEM";
+    case PR_ENORANKS: return "PR_ENORANKS";
+    case PR_ECUDA: return "PR_ECUDA";
+    case PR_ETIMEOUT: return "PR_ETIMEOUT";
+  }
+  return "unknown";
+}
+
+}  // extern "C"

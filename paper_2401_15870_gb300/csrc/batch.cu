@@ -1,0 +1,468 @@
+// batch.cu -- a batch of edge deletions and insertions applied to the device
+// CSR and transpose-CSR in place (Sec. 2.2).
+//
+//   E_t = (E_{t-1} \ D) u I      (deletions first; self-loop deletions are
+//                                 ignored because self-loops are re-added with
+//                                 every batch, Sec. 4.1.4 / 4.2.2)
+//   Delta- = E_{t-1} \ E_t,  Delta+ = E_t \ E_{t-1}   (the effective change)
+//
+// Steps: packed keys -> radix sort -> first occurrences -> effective flags by
+// binary search in the sorted rows -> compaction (Delta-, Delta+ sorted by
+// (src, dst)).  Each touched row is rewritten by one warp: the old row is
+// copied to scratch, every surviving element and every insertion computes its
+// output position by counting smaller deletions / insertions / old elements,
+// and is written back in place; padding slots get the sentinel.  A row whose
+// new degree exceeds its capacity triggers a repack of that direction (a full
+// rebuild with fresh slack).
+#include <algorithm>
+#include "batch.cuh"
+#include "frontier.cuh"
+#include "prim.cuh"
+#include "sweep.cuh"
+
+namespace dfpr {
+
+constexpr uint64_t DROP = ~0ull;
+
+struct Carve {
+  char* p;
+  size_t used = 0;
+  explicit Carve(void* base) : p((char*)base) {}
+  template <typename T>
+  T* take(int64_t n) {
+    size_t off = (used + 255) & ~(size_t)255;
+    used = off + sizeof(T) * (size_t)(n > 0 ? n : 1);
+    return (T*)(p + off);
+  }
+};
+
+#define GRID_STRIDE(i, n) \
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < (n); i += (int64_t)gridDim.x * blockDim.x)
+
+#define TRY(x)                                          \
+  do {                                                  \
+    cudaError_t _e = (x);                               \
+    if (_e != cudaSuccess) return cuda_fail(g, _e, #x); \
+  } while (0)
+
+// ------------------------------------------------------------------ kernels
+
+__global__ void k_validate(const int32_t* __restrict__ s, const int32_t* __restrict__ d, int64_t k, int32_t n,
+                           unsigned long long* bad) {
+  unsigned long long c = 0;
+  GRID_STRIDE(i, k) c += (s[i] < 0 || s[i] >= n || d[i] < 0 || d[i] >= n) ? 1 : 0;
+  if (c) atomicAdd(bad, c);
+}
+
+// user ids -> packed internal keys; self-loops become DROP
+__global__ void k_make_keys(const int32_t* __restrict__ s, const int32_t* __restrict__ d, int64_t k,
+                            const int32_t* __restrict__ perm, int bits, uint64_t* __restrict__ out) {
+  GRID_STRIDE(i, k) {
+    int32_t u = s[i], v = d[i];
+    out[i] = (u == v) ? DROP : (((uint64_t)perm[u] << bits) | (uint64_t)perm[v]);
+  }
+}
+
+__device__ __forceinline__ bool in_row(const int32_t* col, int64_t base, int32_t deg, int32_t x) {
+  int32_t lo = 0, hi = deg;
+  while (lo < hi) {
+    int32_t mid = (lo + hi) >> 1;
+    if (col[base + mid] < x) lo = mid + 1;
+    else hi = mid;
+  }
+  return lo < deg && col[base + lo] == x;
+}
+
+__device__ __forceinline__ bool key_in(const uint64_t* k, int64_t len, uint64_t x) {
+  int64_t lo = 0, hi = len;
+  while (lo < hi) {
+    int64_t mid = (lo + hi) >> 1;
+    if (k[mid] < x) lo = mid + 1;
+    else hi = mid;
+  }
+  return lo < len && k[lo] == x;
+}
+
+__device__ __forceinline__ int64_t lower_key(const uint64_t* k, int64_t lo, int64_t hi, uint64_t x) {
+  while (lo < hi) {
+    int64_t mid = (lo + hi) >> 1;
+    if (k[mid] < x) lo = mid + 1;
+    else hi = mid;
+  }
+  return lo;
+}
+
+// effective deletion: first occurrence, present in E_{t-1}, not re-inserted
+__global__ void k_flag_del(const uint64_t* __restrict__ dk, int64_t nd, const uint64_t* __restrict__ ik, int64_t ni,
+                           const int64_t* __restrict__ oo, const int32_t* __restrict__ od,
+                           const int32_t* __restrict__ oc, int bits, uint8_t* __restrict__ f) {
+  uint64_t mask = (1ull << bits) - 1;
+  GRID_STRIDE(i, nd) {
+    uint64_t k = dk[i];
+    bool e = k != DROP && (i == 0 || dk[i - 1] != k);
+    if (e) {
+      int32_t u = (int32_t)(k >> bits), v = (int32_t)(k & mask);
+      e = in_row(oc, oo[u], od[u], v) && !key_in(ik, ni, k);
+    }
+    f[i] = e;
+  }
+}
+
+// effective insertion: first occurrence, absent from E_{t-1}
+__global__ void k_flag_ins(const uint64_t* __restrict__ ik, int64_t ni, const int64_t* __restrict__ oo,
+                           const int32_t* __restrict__ od, const int32_t* __restrict__ oc, int bits,
+                           uint8_t* __restrict__ f) {
+  uint64_t mask = (1ull << bits) - 1;
+  GRID_STRIDE(i, ni) {
+    uint64_t k = ik[i];
+    bool e = k != DROP && (i == 0 || ik[i - 1] != k);
+    if (e) {
+      int32_t u = (int32_t)(k >> bits), v = (int32_t)(k & mask);
+      e = !in_row(oc, oo[u], od[u], v);
+    }
+    f[i] = e;
+  }
+}
+
+__global__ void k_swap_keys(const uint64_t* __restrict__ in, int64_t k, int bits, uint64_t* __restrict__ out) {
+  uint64_t mask = (1ull << bits) - 1;
+  GRID_STRIDE(i, k) out[i] = ((in[i] & mask) << bits) | (in[i] >> bits);
+}
+
+__global__ void k_row_keys(const uint64_t* __restrict__ a, int64_t na, const uint64_t* __restrict__ b, int64_t nb,
+                           int bits, uint64_t* __restrict__ out) {
+  GRID_STRIDE(i, na + nb) out[i] = (i < na ? a[i] : b[i - na]) >> bits;
+}
+
+// per touched row: ranges in the deletion / insertion lists, new degree, overflow
+__global__ void k_row_plan(const uint64_t* __restrict__ rows, int64_t nr, const uint64_t* __restrict__ dl, int64_t nd,
+                           const uint64_t* __restrict__ il, int64_t ni, int bits, const int64_t* __restrict__ off,
+                           const int32_t* __restrict__ deg, int64_t* __restrict__ plan, int64_t* __restrict__ olddeg,
+                           unsigned long long* overflow) {
+  GRID_STRIDE(j, nr) {
+    uint64_t r = rows[j];
+    int64_t d0 = lower_key(dl, 0, nd, r << bits), d1 = lower_key(dl, d0, nd, (r + 1) << bits);
+    int64_t i0 = lower_key(il, 0, ni, r << bits), i1 = lower_key(il, i0, ni, (r + 1) << bits);
+    int64_t dg = deg[r];
+    int64_t nd2 = dg - (d1 - d0) + (i1 - i0);
+    plan[4 * j + 0] = d0;
+    plan[4 * j + 1] = d1;
+    plan[4 * j + 2] = i0;
+    plan[4 * j + 3] = i1;
+    olddeg[j] = dg;
+    if (round4(nd2) > off[r + 1] - off[r]) atomicAdd(overflow, 1ull);
+  }
+}
+
+// one warp per touched row: copy old row to scratch, then write the merged row
+__global__ void k_row_rewrite(const uint64_t* __restrict__ rows, int64_t nr, const int64_t* __restrict__ plan,
+                              const int64_t* __restrict__ sofs, const uint64_t* __restrict__ dl,
+                              const uint64_t* __restrict__ il, int bits, const int64_t* __restrict__ off,
+                              int32_t* __restrict__ deg, int32_t* __restrict__ col, int32_t* __restrict__ scratch,
+                              int32_t sent) {
+  uint64_t mask = (1ull << bits) - 1;
+  int lane = threadIdx.x & 31;
+  int64_t warp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+  int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  for (int64_t j = warp; j < nr; j += nwarps) {
+    int64_t r = (int64_t)rows[j];
+    int64_t base = off[r];
+    int32_t d_old = deg[r];
+    int64_t d0 = plan[4 * j], d1 = plan[4 * j + 1], i0 = plan[4 * j + 2], i1 = plan[4 * j + 3];
+    int32_t* S = scratch + sofs[j];
+    const int64_t cap = off[r + 1] - base;   // every write below is kept inside the row
+    for (int32_t x = lane; x < d_old; x += 32) S[x] = col[base + x];
+    __syncwarp();
+    // survivors
+    for (int32_t x = lane; x < d_old; x += 32) {
+      int32_t v = S[x];
+      uint64_t key = ((uint64_t)r << bits) | (uint64_t)v;
+      int64_t dl_lt = lower_key(dl, d0, d1, key);
+      if (dl_lt < d1 && dl[dl_lt] == key) continue;   // deleted
+      int64_t il_lt = lower_key(il, i0, i1, key);
+      int64_t pos = x - (dl_lt - d0) + (il_lt - i0);
+      if (pos >= 0 && pos < cap) col[base + pos] = v;
+    }
+    // insertions
+    for (int64_t k = i0 + lane; k < i1; k += 32) {
+      int32_t y = (int32_t)(il[k] & mask);
+      int32_t lo = 0, hi = d_old;
+      while (lo < hi) {
+        int32_t mid = (lo + hi) >> 1;
+        if (S[mid] < y) lo = mid + 1;
+        else hi = mid;
+      }
+      uint64_t key = ((uint64_t)r << bits) | (uint64_t)y;
+      int64_t dl_lt = lower_key(dl, d0, d1, key);
+      int64_t pos = (k - i0) + lo - (dl_lt - d0);
+      if (pos >= 0 && pos < cap) col[base + pos] = y;
+    }
+    int32_t d_new = d_old - (int32_t)(d1 - d0) + (int32_t)(i1 - i0);
+    int64_t pad_end = round4(d_old > d_new ? d_old : d_new);
+    for (int64_t x = d_new + lane; x < pad_end && x < cap; x += 32) col[base + x] = sent;
+    if (lane == 0) deg[r] = d_new;
+    __syncwarp();
+  }
+}
+
+// repack: every surviving edge of a direction as a packed key (row << bits | col)
+__global__ void k_materialize(const int64_t* __restrict__ off, const int32_t* __restrict__ deg,
+                              const int32_t* __restrict__ col, int32_t n, const uint64_t* __restrict__ dl, int64_t nd,
+                              int bits, const int64_t* __restrict__ pos, uint64_t* __restrict__ out) {
+  GRID_STRIDE(r, n) {
+    int64_t w = pos[r];
+    uint64_t rk = (uint64_t)r << bits;
+    int64_t d0 = lower_key(dl, 0, nd, rk), d1 = lower_key(dl, d0, nd, rk + (1ull << bits));
+    for (int32_t x = 0; x < deg[r]; x++) {
+      uint64_t key = rk | (uint64_t)col[off[r] + x];
+      if (d1 > d0 && key_in(dl + d0, d1 - d0, key)) continue;
+      out[w++] = key;
+    }
+  }
+}
+
+__global__ void k_surv_count(const int32_t* __restrict__ deg, int32_t n, const uint64_t* __restrict__ dl, int64_t nd,
+                             int bits, int64_t* __restrict__ cnt) {
+  GRID_STRIDE(r, n) {
+    uint64_t rk = (uint64_t)r << bits;
+    int64_t d0 = lower_key(dl, 0, nd, rk), d1 = lower_key(dl, d0, nd, rk + (1ull << bits));
+    cnt[r] = deg[r] - (d1 - d0);
+  }
+}
+
+__global__ void k_u64_to_i32_low(const uint64_t* __restrict__ in, int64_t k, int32_t* __restrict__ out) {
+  GRID_STRIDE(i, k) out[i] = (int32_t)in[i];
+}
+
+// ------------------------------------------------------------------ host
+
+static int edit_direction(Graph* g, Csr* c, const uint64_t* dl, int64_t nd, const uint64_t* il, int64_t ni,
+                          bool* repacked) {
+  cudaStream_t s = g->stream;
+  int bits = g->id_bits;
+  *repacked = false;
+  int64_t nrk = nd + ni;
+  if (nrk == 0) return OK;
+  // touched rows: sorted distinct row ids
+  size_t need = 0;
+  {
+    Carve probe(nullptr);
+    probe.take<uint64_t>(nrk);
+    probe.take<uint64_t>(nrk);
+    probe.take<uint64_t>(nrk);
+    probe.take<uint8_t>(nrk);
+    probe.take<char>((int64_t)std::max(radix_tmp_bytes(nrk), compact_tmp_bytes(nrk)));
+    probe.take<int64_t>(1);
+    need = probe.used + 4096;
+  }
+  void* base;
+  TRY(scratch_get(g, 3, need, &base));
+  Carve cv(base);
+  uint64_t* rk = cv.take<uint64_t>(nrk);
+  uint64_t* alt = cv.take<uint64_t>(nrk);
+  uint64_t* rows = cv.take<uint64_t>(nrk);
+  uint8_t* flag = cv.take<uint8_t>(nrk);
+  void* tmp = cv.take<char>((int64_t)std::max(radix_tmp_bytes(nrk), compact_tmp_bytes(nrk)));
+  int64_t* cnt = cv.take<int64_t>(1);
+  k_row_keys<<<grid_for(nrk, 256), 256, 0, s>>>(dl, nd, il, ni, bits, rk);
+  TRY(radix_sort_u64(rk, alt, nrk, bits, tmp, s));
+  TRY(flag_unique_sorted(rk, nrk, flag, s));
+  TRY(compact_u64(rk, flag, nrk, rows, cnt, tmp, s));
+  int64_t nr = 0;
+  TRY(cudaMemcpyAsync(&nr, cnt, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+  TRY(cudaStreamSynchronize(s));
+
+  void* base2;
+  size_t need2 = 0;
+  {
+    Carve probe(nullptr);
+    probe.take<int64_t>(4 * nr);
+    probe.take<int64_t>(nr + 1);
+    probe.take<int64_t>(scan_tmp_elems(nr));
+    probe.take<unsigned long long>(1);
+    need2 = probe.used + 4096;
+  }
+  TRY(scratch_get(g, 4, need2, &base2));
+  Carve c2(base2);
+  int64_t* plan = c2.take<int64_t>(4 * nr);
+  int64_t* sofs = c2.take<int64_t>(nr + 1);
+  int64_t* sscr = c2.take<int64_t>(scan_tmp_elems(nr));
+  unsigned long long* ovf = c2.take<unsigned long long>(1);
+  TRY(cudaMemsetAsync(ovf, 0, sizeof(unsigned long long), s));
+  k_row_plan<<<grid_for(nr, 256), 256, 0, s>>>(rows, nr, dl, nd, il, ni, bits, c->off, c->deg, plan, sofs, ovf);
+  TRY(scan_excl<int64_t>(sofs, sofs, nr, sscr, s));
+  unsigned long long ovf_h = 0;
+  int64_t stot = 0;
+  TRY(cudaMemcpyAsync(&ovf_h, ovf, sizeof(ovf_h), cudaMemcpyDeviceToHost, s));
+  TRY(cudaMemcpyAsync(&stot, sofs + nr, sizeof(stot), cudaMemcpyDeviceToHost, s));
+  TRY(cudaStreamSynchronize(s));
+
+  if (ovf_h == 0) {
+    void* sp;
+    TRY(scratch_get(g, 5, sizeof(int32_t) * (size_t)(stot + 1), &sp));
+    int64_t warps = nr;
+    int blocks = (int)std::min<int64_t>(cdiv(warps * 32, 256), (int64_t)num_sms() * 16);
+    if (blocks < 1) blocks = 1;
+    k_row_rewrite<<<blocks, 256, 0, s>>>(rows, nr, plan, sofs, dl, il, bits, c->off, c->deg, c->col, (int32_t*)sp,
+                                         g->n);
+    TRY(cudaGetLastError());
+    return OK;
+  }
+
+  // repack this direction: survivors + insertions, sorted, rebuilt with more slack
+  *repacked = true;
+  int32_t n = g->n;
+  int64_t* pos;
+  int64_t* pscr;
+  TRY(cudaMalloc(&pos, sizeof(int64_t) * (n + 1)));
+  TRY(cudaMalloc(&pscr, sizeof(int64_t) * scan_tmp_elems(n)));
+  k_surv_count<<<grid_for(n, 256), 256, 0, s>>>(c->deg, n, dl, nd, bits, pos);
+  TRY(scan_excl<int64_t>(pos, pos, n, pscr, s));
+  int64_t surv = 0;
+  TRY(cudaMemcpyAsync(&surv, pos + n, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+  TRY(cudaStreamSynchronize(s));
+  int64_t mtot = surv + ni;
+  uint64_t *keys, *kalt;
+  void* rtmp;
+  TRY(cudaMalloc(&keys, sizeof(uint64_t) * (mtot + 1)));
+  TRY(cudaMalloc(&kalt, sizeof(uint64_t) * (mtot + 1)));
+  TRY(cudaMalloc(&rtmp, radix_tmp_bytes(mtot)));
+  k_materialize<<<grid_for(n, 128), 128, 0, s>>>(c->off, c->deg, c->col, n, dl, nd, bits, pos, keys);
+  if (ni) TRY(cudaMemcpyAsync(keys + surv, il, sizeof(uint64_t) * ni, cudaMemcpyDeviceToDevice, s));
+  TRY(radix_sort_u64(keys, kalt, mtot, 2 * bits, rtmp, s));
+  int rc = build_csr_from_sorted(g, c, keys, mtot, c == &g->in, 2);
+  cudaFree(pos);
+  cudaFree(pscr);
+  cudaFree(keys);
+  cudaFree(kalt);
+  cudaFree(rtmp);
+  return rc;
+}
+
+int apply_batch_device(Graph* g, const int32_t* ds, const int32_t* dd, int64_t nd, const int32_t* is,
+                       const int32_t* id, int64_t ni, bool validated) {
+  cudaStream_t s = g->stream;
+  int bits = g->id_bits;
+  int32_t n = g->n;
+  int64_t nk = nd + ni;
+  size_t need;
+  {
+    Carve probe(nullptr);
+    probe.take<uint64_t>(nd);
+    probe.take<uint64_t>(ni);
+    probe.take<uint64_t>(nk);
+    probe.take<uint8_t>(nk);
+    probe.take<char>((int64_t)std::max(radix_tmp_bytes(nk), compact_tmp_bytes(nk)));
+    probe.take<unsigned long long>(4);
+    need = probe.used + 4096;
+  }
+  void* base;
+  TRY(scratch_get(g, 2, need, &base));
+  Carve cv(base);
+  uint64_t* dk = cv.take<uint64_t>(nd);
+  uint64_t* ik = cv.take<uint64_t>(ni);
+  uint64_t* alt = cv.take<uint64_t>(nk);
+  uint8_t* flag = cv.take<uint8_t>(nk);
+  void* tmp = cv.take<char>((int64_t)std::max(radix_tmp_bytes(nk), compact_tmp_bytes(nk)));
+  unsigned long long* small = cv.take<unsigned long long>(4);
+  if (!validated && nk) {
+    TRY(cudaMemsetAsync(small, 0, sizeof(unsigned long long), s));
+    if (nd) k_validate<<<grid_for(nd, 256), 256, 0, s>>>(ds, dd, nd, n, small);
+    if (ni) k_validate<<<grid_for(ni, 256), 256, 0, s>>>(is, id, ni, n, small);
+    unsigned long long bad = 0;
+    TRY(cudaMemcpyAsync(&bad, small, sizeof(bad), cudaMemcpyDeviceToHost, s));
+    TRY(cudaStreamSynchronize(s));
+    if (bad) return set_error(g, ERANGE_, "pr_apply_batch: vertex id out of range");
+  }
+  // effective change lists (grow-only buffers owned by the graph)
+  if (g->cap_dmin < nd) {
+    if (g->dmin) cudaFree(g->dmin);
+    g->dmin = nullptr;
+    g->cap_dmin = 0;
+    TRY(cudaMalloc(&g->dmin, sizeof(uint64_t) * (nd + 1)));
+    g->cap_dmin = nd;
+  }
+  if (g->cap_dplus < ni) {
+    if (g->dplus) cudaFree(g->dplus);
+    g->dplus = nullptr;
+    g->cap_dplus = 0;
+    TRY(cudaMalloc(&g->dplus, sizeof(uint64_t) * (ni + 1)));
+    g->cap_dplus = ni;
+  }
+  if (nd) {
+    k_make_keys<<<grid_for(nd, 256), 256, 0, s>>>(ds, dd, nd, g->perm, bits, dk);
+    TRY(radix_sort_u64(dk, alt, nd, 2 * bits, tmp, s));
+  }
+  if (ni) {
+    k_make_keys<<<grid_for(ni, 256), 256, 0, s>>>(is, id, ni, g->perm, bits, ik);
+    TRY(radix_sort_u64(ik, alt, ni, 2 * bits, tmp, s));
+  }
+  int64_t* cnts = (int64_t*)(small + 1);
+  TRY(cudaMemsetAsync(cnts, 0, 2 * sizeof(int64_t), s));
+  if (nd) {
+    k_flag_del<<<grid_for(nd, 256), 256, 0, s>>>(dk, nd, ik, ni, g->out.off, g->out.deg, g->out.col, bits, flag);
+    TRY(compact_u64(dk, flag, nd, g->dmin, cnts, tmp, s));
+  }
+  if (ni) {
+    k_flag_ins<<<grid_for(ni, 256), 256, 0, s>>>(ik, ni, g->out.off, g->out.deg, g->out.col, bits, flag + nd);
+    TRY(compact_u64(ik, flag + nd, ni, g->dplus, cnts + 1, tmp, s));
+  }
+  int64_t hc[2] = {0, 0};
+  TRY(cudaMemcpyAsync(hc, cnts, sizeof(hc), cudaMemcpyDeviceToHost, s));
+  TRY(cudaStreamSynchronize(s));
+  g->n_dmin = hc[0];
+  g->n_dplus = hc[1];
+  if (hc[0] + hc[1] == 0) return OK;
+
+  // out-CSR: lists are sorted by (src, dst)
+  bool rep_out = false, rep_in = false;
+  int rc = edit_direction(g, &g->out, g->dmin, hc[0], g->dplus, hc[1], &rep_out);
+  if (rc) return rc;
+  // in-CSR: the same lists keyed (dst, src)
+  {
+    int64_t a = hc[0], b = hc[1];
+    void* base2;
+    size_t need2;
+    {
+      Carve probe(nullptr);
+      probe.take<uint64_t>(a);
+      probe.take<uint64_t>(b);
+      probe.take<uint64_t>(a + b);
+      probe.take<char>((int64_t)radix_tmp_bytes(a + b));
+      need2 = probe.used + 4096;
+    }
+    TRY(scratch_get(g, 1, need2, &base2));
+    Carve c2(base2);
+    uint64_t* sd = c2.take<uint64_t>(a);
+    uint64_t* si = c2.take<uint64_t>(b);
+    uint64_t* alt2 = c2.take<uint64_t>(a + b);
+    void* tmp2 = c2.take<char>((int64_t)radix_tmp_bytes(a + b));
+    if (a) {
+      k_swap_keys<<<grid_for(a, 256), 256, 0, s>>>(g->dmin, a, bits, sd);
+      TRY(radix_sort_u64(sd, alt2, a, 2 * bits, tmp2, s));
+    }
+    if (b) {
+      k_swap_keys<<<grid_for(b, 256), 256, 0, s>>>(g->dplus, b, bits, si);
+      TRY(radix_sort_u64(si, alt2, b, 2 * bits, tmp2, s));
+    }
+    rc = edit_direction(g, &g->in, sd, a, si, b, &rep_in);
+    if (rc) return rc;
+  }
+  if (rep_in) {
+    rc = refresh_full_tiles(g);
+    if (rc) return rc;
+  }
+  // contributions of sources whose out-degree changed (a3)
+  if (g->has_ranks) {
+    // the sources: reuse worklist 0 and the aux bitset
+    TRY(cudaMemsetAsync(g->aux, 0, sizeof(uint32_t) * (size_t)(cdiv(n, 32) + 1), s));
+    TRY(cudaMemsetAsync(&g->ctl->count[0], 0, sizeof(int32_t), s));
+    TRY(launch_mark_sources(g->dmin, hc[0], g->dplus, hc[1], bits, g->aux, g->wl[0], &g->ctl->count[0], s));
+    TRY(launch_contrib_list(g->wl[0], &g->ctl->count[0], g->R, g->C[g->ccur], g->out.deg, g->tab_sc, n, s));
+    TRY(cudaMemsetAsync(&g->ctl->count[0], 0, sizeof(int32_t), s));
+  }
+  TRY(cudaGetLastError());
+  return OK;
+}
+
+}  // namespace dfpr

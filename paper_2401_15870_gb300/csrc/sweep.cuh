@@ -1,0 +1,86 @@
+// sweep.cuh -- the pull rank sweep and the frontier kernels around it.
+#pragma once
+#include "graph.cuh"
+
+namespace dfpr {
+
+constexpr int SW_THREADS = 256;
+constexpr int SW_QPT = 4;                          // quads per thread per tile
+constexpr int SW_TILE_Q = SW_THREADS * SW_QPT;     // 1024 quads = 4096 edge slots per tile
+constexpr int SW_MAX_ITEMS = SW_TILE_Q + 2;        // items loaded per tile (those touching it, plus one)
+
+enum SweepMode : int {
+  SWEEP_FULL = 0,   // every vertex, Eq. 1, writes R in place and the next contribution buffer (Static, ND)
+  SWEEP_LIST = 1,   // a fixed vertex list, Eq. 1, new ranks to rnew (Dynamic Traversal)
+  SWEEP_DF = 2,     // frontier list, Eq. 1, expand on a large relative change (DF)
+  SWEEP_DFP = 3,    // frontier list, Eq. 2, prune on a small one, expand on a large one (DF-P)
+};
+
+struct SweepParams {
+  int32_t n;
+  const int64_t* ioff;
+  const int32_t* ideg;
+  const int32_t* icol;
+  const int32_t* odeg;
+  const long long* Ccur;
+  long long* Cnext;          // FULL only
+  double* R;
+  double* rnew;              // LIST / DF / DFP
+  const double* tab_sc;      // 2^61 / d
+  const double* tab_cl;      // 1 / (1 - alpha/d)
+  double alpha, C0, tau_f, tau_p;
+  // the swept list: identity (list == nullptr) over in-CSR capacity quads, or
+  // list[0..*count) with quad prefix qs
+  const int32_t* list;
+  const int32_t* count;
+  const int64_t* qs;
+  const int32_t* tfirst;
+  const int64_t* ntiles_dev;  // device tile count (list mode)
+  int64_t ntiles_host;        // identity mode
+  long long* gacc;
+  int32_t* gcnt;
+  // frontier outputs (DF / DFP)
+  uint32_t* bits_next;
+  uint32_t* ever;
+  int32_t* wl_next;
+  int32_t* cnt_next;
+  int32_t* xl;
+  int32_t* cnt_x;
+  Ctl* ctl;
+};
+
+cudaError_t launch_sweep(int mode, const SweepParams& p, cudaStream_t s);
+
+// quad prefix + tile starts of list[0..*count) with quads(v) = ceil(deg[v]/4);
+// writes qs[0..K], tfirst[0..ntiles], *qtot_dev, *ntiles_dev.  tmp: >= list_scan_tmp(n) int64
+int64_t list_scan_tmp(int32_t n);
+cudaError_t launch_list_scan(const int32_t* list, const int32_t* count, const int32_t* deg, int32_t n, int64_t* qs,
+                             int32_t* tfirst, int64_t* qtot_dev, int64_t* ntiles_dev, int64_t* tmp, cudaStream_t s);
+
+struct ExpandParams {
+  int32_t n;
+  const int64_t* ooff;
+  const int32_t* ocol;
+  const int32_t* list;       // expanding vertices
+  const int32_t* count;
+  const int64_t* qs;
+  const int32_t* tfirst;
+  const int64_t* ntiles_dev;
+  uint32_t* bits;            // marks (test-and-set)
+  uint32_t* ever;            // nullable
+  int32_t* wl;               // appended newly marked vertices
+  int32_t* cnt;
+  // previous-snapshot traversal (Dynamic Traversal on G_{t-1}): skip inserted edges
+  const uint32_t* ins_src_bits;   // nullable: sources with effective insertions
+  const uint64_t* dplus;          // sorted packed keys of effective insertions
+  int64_t n_dplus;
+  int id_bits;
+};
+cudaError_t launch_expand(const ExpandParams& p, cudaStream_t s);
+
+// commit ranks of list[0..*count): R[v] = rnew[k], contribution refreshed;
+// clears v's bit in bits_clear when non-null
+cudaError_t launch_commit(const int32_t* list, const int32_t* count, const double* rnew, double* R, long long* C,
+                          const int32_t* odeg, const double* tab_sc, uint32_t* bits_clear, int32_t n, cudaStream_t s);
+
+}  // namespace dfpr

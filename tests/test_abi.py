@@ -1,0 +1,71 @@
+"""The C-ABI library builds for sm_103a, loads, and exports every entry point
+that include/dfpr.h declares (no compute calls: this runs without a GPU)."""
+import ctypes
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def declared_entry_points():
+    names = []
+    for f in sorted(os.listdir(os.path.join(ROOT, "include"))):
+        if f.endswith(".h"):
+            text = open(os.path.join(ROOT, "include", f)).read()
+            text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+            names += re.findall(r"\b(pr_[a-z_0-9]+)\s*\(", text)
+    return sorted(set(names))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_2401_15870_gb300 import build
+    path = build.build()
+    return ctypes.CDLL(path)
+
+
+def test_header_declares_the_boundary():
+    names = declared_entry_points()
+    for need in ("pr_graph_create", "pr_apply_batch", "pr_update", "pr_ranks", "pr_set_ranks", "pr_graph_destroy",
+                 "pr_last_error"):
+        assert need in names
+
+
+def test_library_exports_every_declared_symbol(lib):
+    missing = [n for n in declared_entry_points() if not hasattr(lib, n)]
+    assert not missing, missing
+
+
+def test_status_strings_need_no_gpu(lib):
+    lib.pr_status_string.restype = ctypes.c_char_p
+    lib.pr_status_string.argtypes = [ctypes.c_int]
+    assert lib.pr_status_string(0) == b"PR_OK"
+    assert lib.pr_status_string(4) == b"PR_ENORANKS"
+
+
+def test_argument_errors_are_reported_before_any_device_work(lib):
+    """Invalid arguments are rejected on the host without touching the GPU."""
+    P = ctypes.c_void_p
+    lib.pr_graph_create_edges.argtypes = [ctypes.c_int32, ctypes.c_int64, P, P, ctypes.c_int32, ctypes.c_int32, P,
+                                          ctypes.POINTER(P)]
+    h = P()
+    assert lib.pr_graph_create_edges(0, 0, None, None, 0, 0, None, ctypes.byref(h)) == 1      # n < 1
+    assert lib.pr_graph_create_edges(4, -1, None, None, 0, 0, None, ctypes.byref(h)) == 1     # m < 0
+    src = (ctypes.c_int32 * 2)(0, 7)
+    dst = (ctypes.c_int32 * 2)(1, 2)
+    assert lib.pr_graph_create_edges(4, 2, src, dst, 0, 0, None, ctypes.byref(h)) == 2        # id out of range
+    lib.pr_update.argtypes = [P, ctypes.c_int, ctypes.c_double, ctypes.c_double, P, P]
+    assert lib.pr_update(None, 0, 0.85, 1e-10, None, None) == 1
+
+
+def test_product_path_has_no_oracle_or_cpu_fallback():
+    """The package never imports the oracle, and fails loudly without its library."""
+    pkg = os.path.join(ROOT, "paper_2401_15870_gb300")
+    for dirpath, _, files in os.walk(pkg):
+        for f in files:
+            if f.endswith((".py", ".cu", ".cuh", ".h")):
+                text = open(os.path.join(dirpath, f)).read()
+                assert "import oracle" not in text and "from oracle" not in text
+                assert "dfpr_oracle" not in text and "liboracle" not in text

@@ -1,0 +1,286 @@
+"""Parity of the CUDA library with the CPU oracle, element by element.
+
+Integer work (CSR build, batch edit, effective change, affected sets) must be
+bit-exact; ranks must agree within 1e-9 in L-infinity (the tolerance the
+target states), for every method, from the same previous ranks.
+"""
+import numpy as np
+import pytest
+
+import oracle
+import synth
+
+pytestmark = pytest.mark.gpu
+
+TOL = 1e-9
+
+
+@pytest.fixture(scope="module")
+def lib():
+    import paper_2401_15870_gb300 as pr
+    pr.load()
+    return pr
+
+
+def make_pair(pr, n, src, dst, keep_order=False):
+    return pr.Graph.from_edges(n, src, dst, keep_order=keep_order), oracle.Graph(n, src, dst)
+
+
+def assert_same_graph(G, O):
+    for mine, ref in ((G.out_csr(), O.out_csr()), (G.in_csr(), O.in_csr())):
+        assert np.array_equal(mine[0], ref[0])
+        assert np.array_equal(mine[1], ref[1])
+
+
+# ------------------------------------------------------------- integer parity
+
+
+@pytest.mark.parametrize("keep_order", [False, True])
+@pytest.mark.parametrize("scale,m", [(1, 3), (5, 40), (10, 1 << 13), (14, 1 << 18)])
+def test_build_matches_oracle(lib, scale, m, keep_order):
+    n = 1 << scale
+    src, dst = synth.rmat(scale, m, 100 + scale)
+    G, O = make_pair(lib, n, src, dst, keep_order)
+    assert G.m == O.m
+    assert_same_graph(G, O)
+
+
+def test_build_from_csr_and_ragged_sizes(lib):
+    for n, m, seed in ((1, 0, 1), (3, 5, 2), (37, 300, 3), (1000, 7001, 4)):
+        rng = np.random.default_rng(seed)
+        s = np.sort(rng.integers(0, n, m)).astype(np.int32)
+        d = rng.integers(0, n, m).astype(np.int32)
+        off = np.zeros(n + 1, np.int64)
+        np.add.at(off, s + 1, 1)
+        off = np.cumsum(off)
+        G = lib.Graph.from_csr(n, off, d)
+        O = oracle.Graph(n, s, d)
+        assert_same_graph(G, O)
+
+
+def batches(n, src, dst, count, size, seed):
+    cs, cd = synth.unique_edges(src, dst)
+    out = []
+    for i in range(count):
+        ds, dd, is_, id_ = synth.batch(n, cs, cd, size, seed + i)
+        # repeats, self-loops, a missing-edge deletion, an edge deleted and re-inserted
+        if len(ds):
+            ds = np.concatenate([ds, ds[:1], [3 % n], [(7 * i) % n]]).astype(np.int32)
+            dd = np.concatenate([dd, dd[:1], [3 % n], [(11 * i + 1) % n]]).astype(np.int32)
+            is_ = np.concatenate([is_, is_[:1], [5 % n], ds[:1]]).astype(np.int32)
+            id_ = np.concatenate([id_, id_[:1], [5 % n], dd[:1]]).astype(np.int32)
+        out.append((ds, dd, is_, id_))
+    return out
+
+
+@pytest.mark.parametrize("scale,size", [(6, 20), (10, 300), (14, 262)])
+def test_batch_edit_matches_oracle(lib, scale, size):
+    n = 1 << scale
+    src, dst = synth.rmat(scale, 16 * n, 200 + scale)
+    G, O = make_pair(lib, n, src, dst)
+    for b in batches(n, src, dst, 4, size, 300):
+        G.apply_batch(*b)
+        O.apply_batch(*b)
+        gd, gp = G.effective_delta()
+        od, op = O.effective_delta()
+        assert np.array_equal(gd, od) and np.array_equal(gp, op)
+        assert G.m == O.m
+        assert_same_graph(G, O)
+
+
+def test_batch_overflow_repacks(lib):
+    """Insertions that overflow a row's slack force a rebuild of that direction."""
+    n = 512
+    src, dst = synth.rmat(9, 4000, 7)
+    G, O = make_pair(lib, n, src, dst)
+    hub_ins_s = np.full(300, 17, np.int32)
+    hub_ins_d = np.arange(300, dtype=np.int32) * 1 % n
+    tgt_ins_s = np.arange(300, dtype=np.int32) % n
+    tgt_ins_d = np.full(300, 99, np.int32)
+    for b in ((hub_ins_s, hub_ins_d), (tgt_ins_s, tgt_ins_d)):
+        G.apply_batch(ins_src=b[0], ins_dst=b[1])
+        O.apply_batch(ins_src=b[0], ins_dst=b[1])
+        assert_same_graph(G, O)
+    # and deleting them again
+    G.apply_batch(del_src=hub_ins_s, del_dst=hub_ins_d)
+    O.apply_batch(del_src=hub_ins_s, del_dst=hub_ins_d)
+    assert_same_graph(G, O)
+
+
+def test_batch_out_of_range_changes_nothing(lib):
+    n = 64
+    src, dst = synth.rmat(6, 300, 9)
+    G, O = make_pair(lib, n, src, dst)
+    with pytest.raises(lib.PRError) as e:
+        G.apply_batch(ins_src=[1, 64], ins_dst=[2, 3])
+    assert e.value.status == 2
+    assert_same_graph(G, O)
+
+
+@pytest.mark.parametrize("seed", range(3))
+def test_affected_sets_match_oracle(lib, seed):
+    n = 1 << 11
+    src, dst = synth.rmat(11, 8 * n, 400 + seed)
+    G, O = make_pair(lib, n, src, dst)
+    b = batches(n, src, dst, 1, 5 + 20 * seed, 500 + seed)[0]
+    G.apply_batch(*b)
+    O.apply_batch(*b)
+    assert np.array_equal(G.initial_affected(), O.initial_affected())
+    assert np.array_equal(G.dt_affected(), O.dt_affected())
+
+
+# -------------------------------------------------------------- rank parity
+
+
+def rank_case(lib, scale, ef, bsize, seed, keep_order=False):
+    n = 1 << scale
+    src, dst = synth.rmat(scale, ef * n, seed)
+    G, O = make_pair(lib, n, src, dst, keep_order)
+    r0, _ = O.update("static")
+    b = batches(n, src, dst, 1, bsize, seed + 1)[0]
+    G.apply_batch(*b)
+    O.apply_batch(*b)
+    return G, O, r0
+
+
+@pytest.mark.parametrize("method", ["static", "nd", "dt", "df", "dfp"])
+def test_ranks_tiny_config(lib, method):
+    """R-MAT 2^14 vertices, 2^18 edges, one batch of 1e-3 |E| (80/20)."""
+    G, O, r0 = rank_case(lib, 14, 16, 262, 11)
+    G.set_ranks(r0)
+    st = G.update(method)
+    ref, ost = O.update(method, r_prev=r0)
+    got = G.ranks()
+    assert np.max(np.abs(got - ref)) < TOL
+    assert st.converged and ost.converged
+    assert abs(st.iterations - ost.iterations) <= 1
+    if method in ("static", "nd", "dt"):
+        assert st.vertices_ever_affected == ost.vertices_ever_affected
+        assert st.edges_processed == pytest.approx(ost.edges_processed, rel=0.02)
+
+
+@pytest.mark.parametrize("method", ["static", "nd", "dt", "df", "dfp"])
+@pytest.mark.parametrize("scale,ef,bsize,keep", [(4, 3, 4, False), (9, 8, 50, True), (12, 24, 400, False)])
+def test_ranks_ragged_and_small(lib, method, scale, ef, bsize, keep):
+    G, O, r0 = rank_case(lib, scale, ef, bsize, 20 + scale, keep)
+    G.set_ranks(r0)
+    G.update(method)
+    ref, _ = O.update(method, r_prev=r0)
+    assert np.max(np.abs(G.ranks() - ref)) < TOL
+
+
+def test_ranks_with_hub_rows_spanning_many_tiles(lib):
+    """A vertex with ~20000 in-edges spans several 4096-slot tiles, so its sum
+    is assembled from partial sums of different thread blocks."""
+    n = 30000
+    rng = np.random.default_rng(5)
+    src = np.concatenate([np.arange(n), rng.integers(0, n, 60000)]).astype(np.int32)
+    dst = np.concatenate([np.full(n, 7), rng.integers(0, n, 60000)]).astype(np.int32)
+    src = np.concatenate([src, np.full(20000, 3)]).astype(np.int32)     # out-hub too
+    dst = np.concatenate([dst, rng.integers(0, n, 20000)]).astype(np.int32)
+    G, O = make_pair(lib, n, src, dst)
+    for method in ("static",):
+        G.update(method)
+        ref, _ = O.update(method)
+        assert np.max(np.abs(G.ranks() - ref)) < TOL
+    r0 = ref
+    b = (np.array([3, 11], np.int32), np.array([int(dst[-1]), 7], np.int32),
+         np.array([7, 100, 3], np.int32), np.array([3, 7, 8], np.int32))
+    G.apply_batch(*b)
+    O.apply_batch(*b)
+    for method in ("nd", "dt", "df", "dfp"):
+        G.set_ranks(r0)
+        G.update(method)
+        ref, _ = O.update(method, r_prev=r0)
+        assert np.max(np.abs(G.ranks() - ref)) < TOL, method
+
+
+def test_successive_batches_and_methods_from_same_ranks(lib):
+    n = 1 << 12
+    src, dst = synth.rmat(12, 16 * n, 77)
+    G, O = make_pair(lib, n, src, dst)
+    G.update("static")
+    r_gpu = G.ranks()
+    r_cpu, _ = O.update("static")
+    for i, b in enumerate(batches(n, src, dst, 3, 120, 900)):
+        G.apply_batch(*b)
+        O.apply_batch(*b)
+        for method in ("dfp", "df", "dt", "nd"):
+            G.set_ranks(r_cpu)
+            G.update(method)
+            ref, _ = O.update(method, r_prev=r_cpu)
+            assert np.max(np.abs(G.ranks() - ref)) < TOL, (i, method)
+        # chain DF-P results on both sides
+        G.set_ranks(r_cpu)
+        G.update("dfp")
+        r_cpu, _ = O.update("dfp", r_prev=r_cpu)
+
+
+def test_empty_batch_and_edge_cases(lib):
+    n = 256
+    src, dst = synth.rmat(8, 2000, 3)
+    G, O = make_pair(lib, n, src, dst)
+    r0, _ = O.update("static")
+    G.set_ranks(r0)
+    G.apply_batch()
+    for method in ("df", "dfp", "dt"):
+        G.set_ranks(r0)
+        st = G.update(method)
+        assert st.iterations == 1 and st.delta_R == 0.0 and st.vertices_ever_affected == 0
+        assert np.array_equal(G.ranks(), r0)
+    # max_iter = 0 leaves the ranks as set
+    G.set_ranks(r0)
+    st = G.update("nd", max_iter=0)
+    assert st.iterations == 0 and not st.converged
+    assert np.array_equal(G.ranks(), r0)
+    # a single vertex
+    one = lib.Graph.from_edges(1, [], [])
+    one.update("static")
+    assert one.ranks()[0] == pytest.approx(1.0, abs=1e-15)
+
+
+def test_dynamic_method_without_ranks_is_rejected(lib):
+    G = lib.Graph.from_edges(8, [0, 1], [1, 2])
+    with pytest.raises(lib.PRError) as e:
+        G.update("dfp")
+    assert e.value.status == 4
+
+
+def test_set_ranks_validation(lib):
+    G = lib.Graph.from_edges(4, [0, 1], [1, 2])
+    with pytest.raises(lib.PRError):
+        G.set_ranks([0.5, -0.1, 0.3, 0.3])
+    with pytest.raises(lib.PRError):
+        G.set_ranks([1.0, 1.0, 1.0, 1.0])
+    G.set_ranks([0.25] * 4)
+
+
+def test_device_pointer_entry_points(lib):
+    torch = pytest.importorskip("torch")
+    n = 1 << 10
+    src, dst = synth.rmat(10, 8 * n, 12)
+    O = oracle.Graph(n, src, dst)
+    G = lib.Graph.from_edges(n, torch.from_numpy(src).cuda(), torch.from_numpy(dst).cuda(), device=True)
+    assert_same_graph(G, O)
+    r0, _ = O.update("static")
+    G.set_ranks_device(torch.from_numpy(r0).cuda())
+    b = batches(n, src, dst, 1, 40, 13)[0]
+    O.apply_batch(*b)
+    G.apply_batch_device(*[torch.from_numpy(np.ascontiguousarray(a)).cuda() for a in b])
+    assert_same_graph(G, O)
+    G.update("dfp")
+    ref, _ = O.update("dfp", r_prev=r0)
+    out = torch.empty(n, dtype=torch.float64, device="cuda")
+    G.ranks_device(out)
+    assert np.max(np.abs(out.cpu().numpy() - ref)) < TOL
+
+
+def test_deterministic_across_runs(lib):
+    """Fixed-point sums make repeated runs bitwise identical."""
+    G, O, r0 = rank_case(lib, 13, 16, 200, 31)
+    outs = []
+    for _ in range(3):
+        G.set_ranks(r0)
+        G.update("dfp")
+        outs.append(G.ranks())
+    assert np.array_equal(outs[0], outs[1]) and np.array_equal(outs[1], outs[2])
