@@ -1,0 +1,311 @@
+"""Benchmark: DF-P batch updates on an R-MAT scale-25 graph on GB300.
+
+One step = one batch update of the hot path: pr_apply_batch (in-place edit of
+the CSR and its transpose, effective change) followed by pr_update with DF-P
+(initial marking, frontier sweeps with expansion and pruning, convergence),
+for a random 80/20 batch of 1e-4 |E| edges (Sec. 4.2.2 of the paper) on a
+synthetic R-MAT graph with 2^25 vertices and 2^30 drawn edges (Table 2
+stand-in).  Batches follow one another on the evolving graph.
+
+value  = batch updates per second, inputs resident in HBM (device batches,
+         pr_apply_batch_device + pr_update).
+e2e    = the same through host buffers: pinned host batches in, ranks of all
+         vertices back to host memory (pr_apply_batch, pr_update, pr_ranks).
+roofline: the DF-P rank-sweep kernel, algorithmic bytes (12 B per processed
+         in-edge + 60 B per processed vertex) over its CUDA-event time.
+
+--impl reference times the CPU oracle (the plain C reference of the method)
+on a bounded sample of the same workload on the host cores.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "DF-P batch-update time & HBM GB/s; served updates/s, p50/p99 vs plain launches"
+ALPHA, TAU = 0.85, 1e-10
+SWEEP_BYTES_PER_EDGE = 12
+SWEEP_BYTES_PER_VERTEX = 60
+SAMPLE_SCALE = 18
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    ap.add_argument("--scale", type=int, default=25)
+    ap.add_argument("--edge-factor", type=int, default=32)
+    ap.add_argument("--batch-frac", type=float, default=1e-4)
+    ap.add_argument("--seed", type=int, default=2000)
+    ap.add_argument("--e2e-steps", type=int, default=5)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    return ap.parse_args()
+
+
+def workload_name(a):
+    return ("R-MAT scale %d (2^%d vertices, %d x 2^%d drawn edges, a,b,c,d=.57,.19,.19,.05), self-loops, "
+            "DF-P after each random 80/20 batch of %g |E|" % (a.scale, a.scale, a.edge_factor, a.scale, a.batch_frac))
+
+
+# ------------------------------------------------------------------ clocks
+
+class ClockSampler:
+    """nvidia-smi samples of SM clock and throttle reasons during the timed region."""
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+              "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+              "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.FIELDS,
+                                          "--format=csv,noheader,nounits", "-lms", "100"],
+                                         stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except OSError:
+            self.proc = None
+        time.sleep(0.3)
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        time.sleep(0.2)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        rows = []
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) >= 8:
+                rows.append(parts)
+        os.unlink(self.path)
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        sm = [float(r[0]) for r in rows if r[0].replace(".", "").isdigit()]
+        mx = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if r[4 + i].lower() == "active"})
+        loaded = [s for s in sm if mx and s > 0.5 * max(mx)] or sm
+        return {"sm_mhz": statistics.median(loaded) if loaded else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(rows)}
+
+
+# ------------------------------------------------------------------ CPU oracle sample
+
+def oracle_sample(a, steps=1):
+    """The oracle as it stands, single-threaded, on R-MAT scale SAMPLE_SCALE with
+    the same edge factor and batch fraction; returns (seconds per update, m)."""
+    import oracle
+    import synth
+    sc = min(SAMPLE_SCALE, a.scale)
+    n = 1 << sc
+    src, dst = synth.rmat(sc, a.edge_factor << sc, a.seed)
+    g = oracle.Graph(n, src, dst)
+    r, _ = g.update("static")
+    size = max(1, int(round(a.batch_frac * g.m)))
+    times = []
+    for i in range(steps):
+        b = synth.batch(n, src, dst, size, a.seed + 1 + i)
+        t0 = time.perf_counter()
+        g.apply_batch(*b)
+        r, _ = g.update("dfp", alpha=ALPHA, tau=TAU, r_prev=r)
+        times.append(time.perf_counter() - t0)
+    return times, g.m, sc
+
+
+def cpu_baseline_entry(times, m_sample, sc, full_scale):
+    """Updates/s of the sample, scaled to the full workload by the ratio of drawn
+    edges (2^(sc - full_scale)): the work of an update grows with the edges."""
+    per = statistics.median(times)
+    scale = 2.0 ** (sc - full_scale)
+    return {"value": (1.0 / per) * scale, "unit": "updates/s", "cores": 1, "kind": "oracle",
+            "sample": ("oracle (plain C, 1 thread) apply + DF-P on R-MAT scale %d (%d edges, same edge factor), %d "
+                       "batch(es) of the same fraction; median %.3f s per update, scaled by the drawn-edge ratio "
+                       "2^%d to the full workload" % (sc, m_sample, len(times), per, sc - full_scale))}
+
+
+def run_reference(a, rank, world):
+    if rank != 0:
+        return
+    times, m_sample, sc = oracle_sample(a, steps=a.warmup + a.steps)
+    timed = times[a.warmup:] or times
+    cb = cpu_baseline_entry(timed, m_sample, sc, a.scale)
+    total = sum(timed)
+    line = {"metric": METRIC, "value": cb["value"], "unit": "updates/s", "n_gpus": world, "steps": len(timed),
+            "warmup": a.warmup, "ms_per_step": 1000.0 * total / len(timed), "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": workload_name(a), "inputs": "larger than L2", "sample_scale": sc},
+            "impl": "reference", "cpu_baseline": cb,
+            "e2e": {"value": cb["value"], "unit": "updates/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+# ------------------------------------------------------------------ GPU arm
+
+def run_gpu(a, rank, world, local_rank):
+    import numpy as np
+    import torch
+
+    import paper_2401_15870_gb300 as pr
+    import synth.gpu as sg
+
+    torch.cuda.set_device(local_rank)
+    dev = torch.device("cuda", local_rank)
+    stream = torch.cuda.current_stream()
+    n = 1 << a.scale
+    seed = a.seed + 7919 * rank          # independent replica per rank
+    src, dst = sg.rmat(a.scale, a.edge_factor << a.scale, seed)
+    G = pr.Graph.from_edges(n, src, dst, device=True, stream=stream)
+    m0 = G.m
+    st0 = G.update("static", alpha=ALPHA, tau=TAU, time_sweeps=True)
+    full_sweep_ms = st0.ms_sweep / max(st0.sweeps, 1)
+    size = max(1, int(round(a.batch_frac * m0)))
+    nb = a.warmup + a.steps
+    dev_batches = [sg.batch(n, src, dst, size, seed + 1 + i) for i in range(nb)]
+    host_batches = []
+    for i in range(a.e2e_steps):
+        bt = sg.batch(n, src, dst, size, seed + 100001 + i)
+        host_batches.append([t.cpu().pin_memory() for t in bt])
+    torch.cuda.synchronize()
+    del src, dst
+
+    def step(b):
+        G.apply_batch_device(*b)
+        return G.update("dfp", alpha=ALPHA, tau=TAU, time_sweeps=True)
+
+    for i in range(a.warmup):
+        step(dev_batches[i])
+    torch.cuda.synchronize()
+    if world > 1:
+        torch.distributed.barrier()
+    clocks = ClockSampler(local_rank)
+    clocks.start()
+    l0 = pr.pr_kernel_launches()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    ev0.record(stream)
+    stats = [step(dev_batches[a.warmup + i]) for i in range(a.steps)]
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    launches = pr.pr_kernel_launches() - l0
+    clk = clocks.stop()
+    ms = ev0.elapsed_time(ev1)
+    if world > 1:
+        t = torch.tensor([ms], device=dev)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        ms = float(t.item())
+    value = world * a.steps / (ms / 1000.0)
+
+    sweep_ms = sum(s.ms_sweep for s in stats)
+    sweep_bytes = sum(SWEEP_BYTES_PER_EDGE * s.edges_processed + SWEEP_BYTES_PER_VERTEX * s.vertices_processed
+                      for s in stats)
+    sweeps = sum(s.sweeps for s in stats)
+    achieved = sweep_bytes / (sweep_ms / 1000.0) / 1e9 if sweep_ms > 0 else 0.0
+    peaks = {}
+    try:
+        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except (OSError, ValueError):
+        pass
+    peak = float(peaks.get("hbm_gbs", 6800.0))
+    peak_src = "measured" if "hbm_gbs" in peaks else "fallback"
+
+    # end to end through host buffers: batch in from pinned memory, all ranks out
+    r_host = torch.empty(n, dtype=torch.float64).pin_memory()
+    r_np = r_host.numpy()
+    e2e_ms = None
+    h2d = d2h = 0
+    if a.e2e_steps > 0:
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for b in host_batches:
+            arrs = [t.numpy() for t in b]
+            G.apply_batch(*arrs)
+            G.update("dfp", alpha=ALPHA, tau=TAU)
+            G.ranks(r_np)
+        torch.cuda.synchronize()
+        e2e_ms = (time.perf_counter() - t0) * 1000.0
+        h2d = sum(t.numel() * 4 for t in host_batches[0])
+        d2h = n * 8
+        if world > 1:
+            t = torch.tensor([e2e_ms], device=dev)
+            torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+            e2e_ms = float(t.item())
+    if rank != 0:
+        return
+    line = {
+        "metric": METRIC, "value": value, "unit": "updates/s", "n_gpus": world, "steps": a.steps,
+        "warmup": a.warmup, "ms_per_step": ms / a.steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": workload_name(a), "vertices": n, "edges": m0, "batch_edges": size,
+                   "inputs": "larger than L2 (graph ~%.0f GB resident)" % (m0 * 8 * 1.2 / 1e9),
+                   "parallelism": "replicas" if world > 1 else "single GPU"},
+        "roofline": {"bound": "hbm", "kernel": "k_sweep<DFP>", "achieved": achieved, "peak": peak,
+                     "unit": "GB/s", "frac": achieved / peak, "traffic": None,
+                     "peak_source": peak_src + " (MEASURED_PEAKS.json hbm_gbs)" if peak_src == "measured" else
+                     "fallback 6800 GB/s"},
+        "e2e": {"value": (a.e2e_steps / (e2e_ms / 1000.0) * world) if e2e_ms else None, "unit": "updates/s",
+                "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
+        "gpu_launches": launches,
+        "clocks": clk,
+        "detail": {
+            "iterations_mean": statistics.mean(s.iterations for s in stats),
+            "ms_apply_mean": statistics.mean(s.ms_apply for s in stats),
+            "ms_update_mean": statistics.mean(s.ms_update for s in stats),
+            "sweep_ms_mean_per_launch": sweep_ms / max(sweeps, 1),
+            "sweep_share_of_step": sweep_ms / ms if ms else None,
+            "vertices_ever_affected_mean": statistics.mean(s.vertices_ever_affected for s in stats),
+            "edges_processed_mean": statistics.mean(s.edges_processed for s in stats),
+            "eff_ins_mean": statistics.mean(s.eff_insertions for s in stats),
+            "eff_del_mean": statistics.mean(s.eff_deletions for s in stats),
+            "static_iterations": st0.iterations,
+            "full_sweep_ms": full_sweep_ms,
+            "full_sweep_gbs": (SWEEP_BYTES_PER_EDGE * st0.edges_processed + 40 * st0.vertices_processed)
+            / (st0.ms_sweep / 1000.0) / 1e9 if st0.ms_sweep else None,
+        },
+    }
+    if not a.no_cpu_baseline and world == 1:
+        times, m_sample, sc = oracle_sample(a, steps=1)
+        line["cpu_baseline"] = cpu_baseline_entry(times, m_sample, sc, a.scale)
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    a = parse()
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", str(a.gpus)))
+    local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+    if a.impl == "reference":
+        run_reference(a, rank, world if "WORLD_SIZE" in os.environ else a.gpus)
+        return
+    if world > 1:
+        import torch
+        torch.cuda.set_device(local_rank)
+        torch.distributed.init_process_group("nccl")
+    try:
+        run_gpu(a, rank, world, local_rank)
+    finally:
+        if world > 1:
+            import torch
+            torch.distributed.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -65,8 +65,12 @@ typedef struct {
   double tau_f;       /* frontier tolerance: expand when dr / max(r, R[v]) > tau_f  */
   double tau_p;       /* prune tolerance (DF-P): drop v when dr / max(r, R[v]) <= tau_p */
   int32_t max_iter;   /* MAX_ITERATIONS                                              */
-  int32_t flags;      /* reserved, must be 0                                          */
+  int32_t flags;      /* PR_OPT_* bits; other bits must be 0                          */
 } pr_options;
+
+/* pr_options.flags: time every rank-sweep kernel with CUDA events on the
+ * graph's stream and report the sum in pr_stats.ms_sweep. */
+#define PR_OPT_TIME_SWEEPS 1
 
 /* Outcome of one pr_update (Sec. 4.1.5 measures time and affected vertices). */
 typedef struct {
@@ -80,6 +84,9 @@ typedef struct {
   int64_t eff_insertions;          /* |Delta+| of the last batch                            */
   double ms_apply;                 /* device time of the last pr_apply_batch*               */
   double ms_update;                /* device time of this pr_update                         */
+  double ms_sweep;                 /* rank-sweep kernel time (PR_OPT_TIME_SWEEPS), else 0   */
+  int32_t sweeps;                  /* rank-sweep kernel launches                            */
+  int32_t reserved;
 } pr_stats;
 
 /*
@@ -185,6 +192,10 @@ pr_status pr_last_delta(const pr_graph* g, int64_t* n_del, int64_t* n_ins, int32
  *              u in G_{t-1}, united with those reachable in G_t.
  */
 pr_status pr_affected(pr_graph* g, int32_t which, uint8_t* flags);
+
+/* Number of CUDA kernels this library has launched in this process so far
+ * (all graphs); the difference across a region counts its launches. */
+unsigned long long pr_kernel_launches(void);
 
 /* Text of the last error on this graph ("" if none); valid until the next call. */
 const char* pr_last_error(const pr_graph* g);

@@ -39,7 +39,8 @@ class pr_stats(ctypes.Structure):
     _fields_ = [("iterations", ctypes.c_int32), ("converged", ctypes.c_int32), ("delta_R", ctypes.c_double),
                 ("vertices_ever_affected", ctypes.c_int64), ("edges_processed", ctypes.c_int64),
                 ("vertices_processed", ctypes.c_int64), ("eff_deletions", ctypes.c_int64),
-                ("eff_insertions", ctypes.c_int64), ("ms_apply", ctypes.c_double), ("ms_update", ctypes.c_double)]
+                ("eff_insertions", ctypes.c_int64), ("ms_apply", ctypes.c_double), ("ms_update", ctypes.c_double),
+                ("ms_sweep", ctypes.c_double), ("sweeps", ctypes.c_int32), ("reserved", ctypes.c_int32)]
 
 
 @dataclass
@@ -54,6 +55,8 @@ class Stats:
     eff_insertions: int
     ms_apply: float
     ms_update: float
+    ms_sweep: float
+    sweeps: int
 
 
 _lib = None
@@ -88,6 +91,7 @@ def load():
         "pr_affected": ([_P, i32, _P], ctypes.c_int),
         "pr_last_error": ([_P], ctypes.c_char_p),
         "pr_status_string": ([ctypes.c_int], ctypes.c_char_p),
+        "pr_kernel_launches": ([], ctypes.c_ulonglong),
     }
     for name, (args, res) in sig.items():
         f = getattr(lib, name)
@@ -187,13 +191,17 @@ def pr_apply_batch_device(h, del_src=None, del_dst=None, ins_src=None, ins_dst=N
     _check(load().pr_apply_batch_device(h, dsp, ddp, nd, isp, idp, ni), h)
 
 
-def pr_update(h, method, alpha=0.85, tau=1e-10, tau_f=1e-6, tau_p=1e-6, max_iter=500) -> Stats:
+PR_OPT_TIME_SWEEPS = 1
+
+
+def pr_update(h, method, alpha=0.85, tau=1e-10, tau_f=1e-6, tau_p=1e-6, max_iter=500, time_sweeps=False) -> Stats:
     m = METHODS[method] if isinstance(method, str) else int(method)
-    opts = pr_options(tau_f, tau_p, int(max_iter), 0)
+    opts = pr_options(tau_f, tau_p, int(max_iter), PR_OPT_TIME_SWEEPS if time_sweeps else 0)
     st = pr_stats()
     _check(load().pr_update(h, m, float(alpha), float(tau), ctypes.byref(opts), ctypes.byref(st)), h)
     return Stats(st.iterations, bool(st.converged), st.delta_R, st.vertices_ever_affected, st.edges_processed,
-                 st.vertices_processed, st.eff_deletions, st.eff_insertions, st.ms_apply, st.ms_update)
+                 st.vertices_processed, st.eff_deletions, st.eff_insertions, st.ms_apply, st.ms_update, st.ms_sweep,
+                 st.sweeps)
 
 
 def pr_graph_info(h):
@@ -266,6 +274,10 @@ def pr_affected(h, which):
 
 def pr_last_error(h) -> str:
     return load().pr_last_error(h).decode()
+
+
+def pr_kernel_launches() -> int:
+    return int(load().pr_kernel_launches())
 
 
 # ------------------------------------------------------------------ convenience wrapper

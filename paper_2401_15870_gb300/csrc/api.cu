@@ -20,7 +20,7 @@ using namespace dfpr;
 
 struct pr_graph {
   Graph g;
-  cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};
+  cudaEvent_t ev[6] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
   double ms_apply = 0.0;
   int32_t* lbits_tmp = nullptr;   // bits_to_list scratch
   int64_t* ls_tmp = nullptr;      // list scan scratch
@@ -133,7 +133,7 @@ static pr_status alloc_state(pr_graph* h) {
   TRY(dalloc(g, (void**)&h->vec_tmp, sizeof(double) * (n > 4 ? n : 4)));
   TRY(launch_tables(g->tab_sc, g->tab_cl, 0.85, g->stream));
   g->tab_alpha = 0.85;
-  for (int i = 0; i < 4; i++) TRY(cudaEventCreate(&h->ev[i]));
+  for (int i = 0; i < 6; i++) TRY(cudaEventCreate(&h->ev[i]));
   return PR_OK;
 }
 
@@ -174,7 +174,7 @@ static void destroy_handle(pr_graph* h) {
   if (g->dmin) cudaFree(g->dmin);
   if (g->dplus) cudaFree(g->dplus);
   if (g->ctl_h) cudaFreeHost(g->ctl_h);
-  for (int i = 0; i < 4; i++)
+  for (int i = 0; i < 6; i++)
     if (h->ev[i]) cudaEventDestroy(h->ev[i]);
   delete h;
 }
@@ -301,8 +301,30 @@ static pr_status dt_affected(pr_graph* h) {
   return PR_OK;
 }
 
+// one sweep launch, bracketed by events when timing is on (the host reads the
+// control block right after, so the pair is read back at once)
+struct SweepTimer {
+  pr_graph* h;
+  bool on;
+  double ms = 0.0;
+  int32_t launches = 0;
+  cudaError_t launch(int mode, const SweepParams& p, cudaStream_t s) {
+    if (on) cudaEventRecord(h->ev[4], s);
+    cudaError_t e = launch_sweep(mode, p, s);
+    if (on) cudaEventRecord(h->ev[5], s);
+    launches++;
+    return e;
+  }
+  void collect() {
+    if (!on) return;
+    float t = 0.f;
+    if (cudaEventElapsedTime(&t, h->ev[4], h->ev[5]) == cudaSuccess) ms += t;
+  }
+};
+
 static pr_status run_update(pr_graph* h, int method, double alpha, double tau, double tau_f, double tau_p,
-                            int32_t max_iter, pr_stats* out) {
+                            int32_t max_iter, int32_t flags, pr_stats* out) {
+  SweepTimer timer{h, (flags & PR_OPT_TIME_SWEEPS) != 0};
   Graph* g = &h->g;
   cudaStream_t s = g->stream;
   int32_t n = g->n;
@@ -324,11 +346,12 @@ static pr_status run_update(pr_graph* h, int method, double alpha, double tau, d
     for (int32_t it = 0; it < max_iter; it++) {
       p.Ccur = g->C[g->ccur];
       p.Cnext = g->C[1 - g->ccur];
-      TRY(launch_sweep(SWEEP_FULL, p, s));
+      TRY(timer.launch(SWEEP_FULL, p, s));
       TRY(launch_control(g->ctl, 0, s));
       g->ccur ^= 1;
       pr_status st = read_ctl(g);
       if (st != PR_OK) return st;
+      timer.collect();
       iters = it + 1;
       dR = ctl_dR(g->ctl_h);
       if (dR <= tau) {
@@ -349,12 +372,13 @@ static pr_status run_update(pr_graph* h, int method, double alpha, double tau, d
     p.ntiles_dev = &g->ctl->ntiles;
     p.Ccur = g->C[g->ccur];
     for (int32_t it = 0; it < max_iter; it++) {
-      TRY(launch_sweep(SWEEP_LIST, p, s));
+      TRY(timer.launch(SWEEP_LIST, p, s));
       TRY(launch_commit(g->wl[0], &g->ctl->count[0], g->rnew, g->R, g->C[g->ccur], g->out.deg, g->tab_sc, nullptr, n,
                         s));
       TRY(launch_control(g->ctl, 0, s));
       st = read_ctl(g);
       if (st != PR_OK) return st;
+      timer.collect();
       iters = it + 1;
       dR = ctl_dR(g->ctl_h);
       if (dR <= tau) {
@@ -387,7 +411,7 @@ static pr_status run_update(pr_graph* h, int method, double alpha, double tau, d
       p.cnt_next = &g->ctl->count[1 - cur];
       p.xl = g->xl;
       p.cnt_x = &g->ctl->nexp;
-      TRY(launch_sweep(mode, p, s));
+      TRY(timer.launch(mode, p, s));
       st = run_expand(h, g->xl, &g->ctl->nexp, g->bits[1 - cur], g->ever, g->wl[1 - cur], &g->ctl->count[1 - cur],
                       nullptr);
       if (st != PR_OK) return st;
@@ -397,6 +421,7 @@ static pr_status run_update(pr_graph* h, int method, double alpha, double tau, d
       cur ^= 1;
       st = read_ctl(g);
       if (st != PR_OK) return st;
+      timer.collect();
       iters = it + 1;
       dR = ctl_dR(g->ctl_h);
       if (dR <= tau) {
@@ -431,6 +456,9 @@ static pr_status run_update(pr_graph* h, int method, double alpha, double tau, d
     out->eff_insertions = g->n_dplus;
     out->ms_apply = h->ms_apply;
     out->ms_update = ms;
+    out->ms_sweep = timer.ms;
+    out->sweeps = timer.launches;
+    out->reserved = 0;
   }
   return PR_OK;
 }
@@ -471,8 +499,8 @@ static pr_status create_from_keys_host_edges(int32_t n, int64_t m, const int32_t
       unsigned long long* bad;
       if ((e = cudaMalloc(&bad, sizeof(*bad))) != cudaSuccess) { st = (pr_status)cuda_fail(g, e, "cudaMalloc"); break; }
       cudaMemsetAsync(bad, 0, sizeof(*bad), g->stream);
-      k_validate_ids<<<grid_for(m, 256), 256, 0, g->stream>>>(src, m, n, bad);
-      k_validate_ids<<<grid_for(m, 256), 256, 0, g->stream>>>(dst, m, n, bad);
+      note_launch(); k_validate_ids<<<grid_for(m, 256), 256, 0, g->stream>>>(src, m, n, bad);
+      note_launch(); k_validate_ids<<<grid_for(m, 256), 256, 0, g->stream>>>(dst, m, n, bad);
       unsigned long long hb = 0;
       cudaMemcpyAsync(&hb, bad, sizeof(hb), cudaMemcpyDeviceToHost, g->stream);
       e = cudaStreamSynchronize(g->stream);
@@ -480,7 +508,7 @@ static pr_status create_from_keys_host_edges(int32_t n, int64_t m, const int32_t
       if (e != cudaSuccess) { st = (pr_status)cuda_fail(g, e, "validate"); break; }
       if (hb) { st = PR_ERANGE; break; }
     }
-    k_edge_keys<<<grid_for(m + n, 256), 256, 0, g->stream>>>(s_dev, d_dev, m, n, g->id_bits, keys);
+    note_launch(); k_edge_keys<<<grid_for(m + n, 256), 256, 0, g->stream>>>(s_dev, d_dev, m, n, g->id_bits, keys);
     if ((e = cudaGetLastError()) != cudaSuccess) { st = (pr_status)cuda_fail(g, e, "k_edge_keys"); break; }
     if (ds) { cudaStreamSynchronize(g->stream); cudaFree(ds); ds = nullptr; }
     if (dd) { cudaFree(dd); dd = nullptr; }
@@ -535,7 +563,7 @@ pr_status pr_graph_create(int32_t n, int64_t m, const int64_t* row_off, const in
       (m > 0 && (e = cudaMemcpyAsync(dcol, col, sizeof(int32_t) * m, cudaMemcpyHostToDevice, g->stream)) != cudaSuccess)) {
     st = (pr_status)cuda_fail(g, e, "pr_graph_create copy");
   } else {
-    k_csr_keys<<<grid_for(m + n, 256), 256, 0, g->stream>>>(doff, dcol, m, n, g->id_bits, keys);
+    note_launch(); k_csr_keys<<<grid_for(m + n, 256), 256, 0, g->stream>>>(doff, dcol, m, n, g->id_bits, keys);
     e = cudaStreamSynchronize(g->stream);
     cudaFree(doff);
     cudaFree(dcol);
@@ -621,19 +649,20 @@ pr_status pr_update(pr_graph* h, pr_method method, double alpha, double tau, con
   Graph* g = &h->g;
   g->err.clear();
   double tau_f = 1e-6, tau_p = 1e-6;
-  int32_t max_iter = 500;
+  int32_t max_iter = 500, flags = 0;
   if (opts) {
     tau_f = opts->tau_f;
     tau_p = opts->tau_p;
     max_iter = opts->max_iter;
-    if (opts->flags != 0) return PR_EINVAL;
+    flags = opts->flags;
+    if (flags & ~PR_OPT_TIME_SWEEPS) return PR_EINVAL;
   }
   if ((int)method < PR_STATIC || (int)method > PR_DFP) return PR_EINVAL;
   if (!(alpha >= 0.0 && alpha < 1.0) || !(tau >= 0.0) || !(tau_f >= 0.0) || !(tau_p >= 0.0) || max_iter < 0)
     return PR_EINVAL;
   if (method != PR_STATIC && !g->has_ranks)
     return (pr_status)set_error(g, ENORANKS_, "pr_update: a dynamic method needs ranks (pr_set_ranks or a previous update)");
-  return run_update(h, (int)method, alpha, tau, tau_f, tau_p, max_iter, stats);
+  return run_update(h, (int)method, alpha, tau, tau_f, tau_p, max_iter, flags, stats);
 }
 
 pr_status pr_ranks_device(const pr_graph* hc, double* out) {
@@ -689,7 +718,7 @@ pr_status pr_set_ranks_device(pr_graph* h, const double* r) {
     double sum;
   } hv, *dv = (decltype(dv))h->vec_tmp;
   TRY(cudaMemsetAsync(dv, 0, sizeof(hv), s));
-  k_check_ranks<<<grid_for(g->n, 256), 256, 0, s>>>(r, g->n, &dv->bad, &dv->sum);
+  note_launch(); k_check_ranks<<<grid_for(g->n, 256), 256, 0, s>>>(r, g->n, &dv->bad, &dv->sum);
   TRY(cudaMemcpyAsync(&hv, dv, sizeof(hv), cudaMemcpyDeviceToHost, s));
   TRY(cudaStreamSynchronize(s));
   if (hv.bad || hv.sum > 2.0) return (pr_status)set_error(g, EINVAL_, "pr_set_ranks_device: bad ranks");
@@ -766,12 +795,14 @@ pr_status pr_affected(pr_graph* h, int32_t which, uint8_t* flags) {
   pr_status st = which == 0 ? initial_marking(h) : dt_affected(h);
   if (st != PR_OK) return st;
   uint8_t* tmp = (uint8_t*)h->vec_tmp;
-  if (which == 0) k_bits_to_bytes<<<grid_for(g->n, 256), 256, 0, s>>>(g->bits[0], nullptr, g->perm, g->n, tmp);
-  else k_bits_to_bytes<<<grid_for(g->n, 256), 256, 0, s>>>(g->aux, g->aux2, g->perm, g->n, tmp);
+  if (which == 0) { note_launch(); k_bits_to_bytes<<<grid_for(g->n, 256), 256, 0, s>>>(g->bits[0], nullptr, g->perm, g->n, tmp); }
+  else { note_launch(); k_bits_to_bytes<<<grid_for(g->n, 256), 256, 0, s>>>(g->aux, g->aux2, g->perm, g->n, tmp); }
   TRY(cudaMemcpyAsync(flags, tmp, g->n, cudaMemcpyDeviceToHost, s));
   TRY(cudaStreamSynchronize(s));
   return PR_OK;
 }
+
+unsigned long long pr_kernel_launches(void) { return launches_so_far(); }
 
 const char* pr_last_error(const pr_graph* h) { return h ? h->g.err.c_str() : ""; }
 

@@ -264,7 +264,7 @@ static int edit_direction(Graph* g, Csr* c, const uint64_t* dl, int64_t nd, cons
   uint8_t* flag = cv.take<uint8_t>(nrk);
   void* tmp = cv.take<char>((int64_t)std::max(radix_tmp_bytes(nrk), compact_tmp_bytes(nrk)));
   int64_t* cnt = cv.take<int64_t>(1);
-  k_row_keys<<<grid_for(nrk, 256), 256, 0, s>>>(dl, nd, il, ni, bits, rk);
+  note_launch(); k_row_keys<<<grid_for(nrk, 256), 256, 0, s>>>(dl, nd, il, ni, bits, rk);
   TRY(radix_sort_u64(rk, alt, nrk, bits, tmp, s));
   TRY(flag_unique_sorted(rk, nrk, flag, s));
   TRY(compact_u64(rk, flag, nrk, rows, cnt, tmp, s));
@@ -289,7 +289,7 @@ static int edit_direction(Graph* g, Csr* c, const uint64_t* dl, int64_t nd, cons
   int64_t* sscr = c2.take<int64_t>(scan_tmp_elems(nr));
   unsigned long long* ovf = c2.take<unsigned long long>(1);
   TRY(cudaMemsetAsync(ovf, 0, sizeof(unsigned long long), s));
-  k_row_plan<<<grid_for(nr, 256), 256, 0, s>>>(rows, nr, dl, nd, il, ni, bits, c->off, c->deg, plan, sofs, ovf);
+  note_launch(); k_row_plan<<<grid_for(nr, 256), 256, 0, s>>>(rows, nr, dl, nd, il, ni, bits, c->off, c->deg, plan, sofs, ovf);
   TRY(scan_excl<int64_t>(sofs, sofs, nr, sscr, s));
   unsigned long long ovf_h = 0;
   int64_t stot = 0;
@@ -303,7 +303,7 @@ static int edit_direction(Graph* g, Csr* c, const uint64_t* dl, int64_t nd, cons
     int64_t warps = nr;
     int blocks = (int)std::min<int64_t>(cdiv(warps * 32, 256), (int64_t)num_sms() * 16);
     if (blocks < 1) blocks = 1;
-    k_row_rewrite<<<blocks, 256, 0, s>>>(rows, nr, plan, sofs, dl, il, bits, c->off, c->deg, c->col, (int32_t*)sp,
+    note_launch(); k_row_rewrite<<<blocks, 256, 0, s>>>(rows, nr, plan, sofs, dl, il, bits, c->off, c->deg, c->col, (int32_t*)sp,
                                          g->n);
     TRY(cudaGetLastError());
     return OK;
@@ -316,7 +316,7 @@ static int edit_direction(Graph* g, Csr* c, const uint64_t* dl, int64_t nd, cons
   int64_t* pscr;
   TRY(cudaMalloc(&pos, sizeof(int64_t) * (n + 1)));
   TRY(cudaMalloc(&pscr, sizeof(int64_t) * scan_tmp_elems(n)));
-  k_surv_count<<<grid_for(n, 256), 256, 0, s>>>(c->deg, n, dl, nd, bits, pos);
+  note_launch(); k_surv_count<<<grid_for(n, 256), 256, 0, s>>>(c->deg, n, dl, nd, bits, pos);
   TRY(scan_excl<int64_t>(pos, pos, n, pscr, s));
   int64_t surv = 0;
   TRY(cudaMemcpyAsync(&surv, pos + n, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
@@ -327,7 +327,7 @@ static int edit_direction(Graph* g, Csr* c, const uint64_t* dl, int64_t nd, cons
   TRY(cudaMalloc(&keys, sizeof(uint64_t) * (mtot + 1)));
   TRY(cudaMalloc(&kalt, sizeof(uint64_t) * (mtot + 1)));
   TRY(cudaMalloc(&rtmp, radix_tmp_bytes(mtot)));
-  k_materialize<<<grid_for(n, 128), 128, 0, s>>>(c->off, c->deg, c->col, n, dl, nd, bits, pos, keys);
+  note_launch(); k_materialize<<<grid_for(n, 128), 128, 0, s>>>(c->off, c->deg, c->col, n, dl, nd, bits, pos, keys);
   if (ni) TRY(cudaMemcpyAsync(keys + surv, il, sizeof(uint64_t) * ni, cudaMemcpyDeviceToDevice, s));
   TRY(radix_sort_u64(keys, kalt, mtot, 2 * bits, rtmp, s));
   int rc = build_csr_from_sorted(g, c, keys, mtot, c == &g->in, 2);
@@ -367,8 +367,8 @@ int apply_batch_device(Graph* g, const int32_t* ds, const int32_t* dd, int64_t n
   unsigned long long* small = cv.take<unsigned long long>(4);
   if (!validated && nk) {
     TRY(cudaMemsetAsync(small, 0, sizeof(unsigned long long), s));
-    if (nd) k_validate<<<grid_for(nd, 256), 256, 0, s>>>(ds, dd, nd, n, small);
-    if (ni) k_validate<<<grid_for(ni, 256), 256, 0, s>>>(is, id, ni, n, small);
+    if (nd) { note_launch(); k_validate<<<grid_for(nd, 256), 256, 0, s>>>(ds, dd, nd, n, small); }
+    if (ni) { note_launch(); k_validate<<<grid_for(ni, 256), 256, 0, s>>>(is, id, ni, n, small); }
     unsigned long long bad = 0;
     TRY(cudaMemcpyAsync(&bad, small, sizeof(bad), cudaMemcpyDeviceToHost, s));
     TRY(cudaStreamSynchronize(s));
@@ -390,21 +390,21 @@ int apply_batch_device(Graph* g, const int32_t* ds, const int32_t* dd, int64_t n
     g->cap_dplus = ni;
   }
   if (nd) {
-    k_make_keys<<<grid_for(nd, 256), 256, 0, s>>>(ds, dd, nd, g->perm, bits, dk);
+    note_launch(); k_make_keys<<<grid_for(nd, 256), 256, 0, s>>>(ds, dd, nd, g->perm, bits, dk);
     TRY(radix_sort_u64(dk, alt, nd, 2 * bits, tmp, s));
   }
   if (ni) {
-    k_make_keys<<<grid_for(ni, 256), 256, 0, s>>>(is, id, ni, g->perm, bits, ik);
+    note_launch(); k_make_keys<<<grid_for(ni, 256), 256, 0, s>>>(is, id, ni, g->perm, bits, ik);
     TRY(radix_sort_u64(ik, alt, ni, 2 * bits, tmp, s));
   }
   int64_t* cnts = (int64_t*)(small + 1);
   TRY(cudaMemsetAsync(cnts, 0, 2 * sizeof(int64_t), s));
   if (nd) {
-    k_flag_del<<<grid_for(nd, 256), 256, 0, s>>>(dk, nd, ik, ni, g->out.off, g->out.deg, g->out.col, bits, flag);
+    note_launch(); k_flag_del<<<grid_for(nd, 256), 256, 0, s>>>(dk, nd, ik, ni, g->out.off, g->out.deg, g->out.col, bits, flag);
     TRY(compact_u64(dk, flag, nd, g->dmin, cnts, tmp, s));
   }
   if (ni) {
-    k_flag_ins<<<grid_for(ni, 256), 256, 0, s>>>(ik, ni, g->out.off, g->out.deg, g->out.col, bits, flag + nd);
+    note_launch(); k_flag_ins<<<grid_for(ni, 256), 256, 0, s>>>(ik, ni, g->out.off, g->out.deg, g->out.col, bits, flag + nd);
     TRY(compact_u64(ik, flag + nd, ni, g->dplus, cnts + 1, tmp, s));
   }
   int64_t hc[2] = {0, 0};
@@ -438,11 +438,11 @@ int apply_batch_device(Graph* g, const int32_t* ds, const int32_t* dd, int64_t n
     uint64_t* alt2 = c2.take<uint64_t>(a + b);
     void* tmp2 = c2.take<char>((int64_t)radix_tmp_bytes(a + b));
     if (a) {
-      k_swap_keys<<<grid_for(a, 256), 256, 0, s>>>(g->dmin, a, bits, sd);
+      note_launch(); k_swap_keys<<<grid_for(a, 256), 256, 0, s>>>(g->dmin, a, bits, sd);
       TRY(radix_sort_u64(sd, alt2, a, 2 * bits, tmp2, s));
     }
     if (b) {
-      k_swap_keys<<<grid_for(b, 256), 256, 0, s>>>(g->dplus, b, bits, si);
+      note_launch(); k_swap_keys<<<grid_for(b, 256), 256, 0, s>>>(g->dplus, b, bits, si);
       TRY(radix_sort_u64(si, alt2, b, 2 * bits, tmp2, s));
     }
     rc = edit_direction(g, &g->in, sd, a, si, b, &rep_in);

@@ -18,6 +18,10 @@
 
 namespace dfpr {
 
+// process-wide count of kernel launches made by this library (pr_kernel_launches)
+void note_launch();
+unsigned long long launches_so_far();
+
 // fixed-point scale of the contribution sums: value = integer * 2^-FIX_BITS
 constexpr int FIX_BITS = 61;
 constexpr double FIX_ONE = 2305843009213693952.0;          // 2^61

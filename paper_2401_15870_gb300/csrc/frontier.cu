@@ -34,7 +34,7 @@ __global__ void k_mark_sources(const uint64_t* __restrict__ a, int64_t na, const
 cudaError_t launch_mark_sources(const uint64_t* a, int64_t na, const uint64_t* b, int64_t nb, int id_bits,
                                 uint32_t* seen, int32_t* list, int32_t* count, cudaStream_t s) {
   if (na + nb == 0) return cudaSuccess;
-  k_mark_sources<<<grid_for(na + nb, 256), 256, 0, s>>>(a, na, b, nb, id_bits, seen, list, count);
+  note_launch(); k_mark_sources<<<grid_for(na + nb, 256), 256, 0, s>>>(a, na, b, nb, id_bits, seen, list, count);
   return cudaGetLastError();
 }
 
@@ -59,7 +59,7 @@ __global__ void k_mark_targets(const uint64_t* __restrict__ d, int64_t nd, int b
 cudaError_t launch_mark_targets(const uint64_t* d, int64_t nd, int id_bits, uint32_t* bits, uint32_t* ever,
                                 int32_t* list, int32_t* count, cudaStream_t s) {
   if (nd == 0) return cudaSuccess;
-  k_mark_targets<<<grid_for(nd, 256), 256, 0, s>>>(d, nd, id_bits, bits, ever, list, count);
+  note_launch(); k_mark_targets<<<grid_for(nd, 256), 256, 0, s>>>(d, nd, id_bits, bits, ever, list, count);
   return cudaGetLastError();
 }
 
@@ -82,7 +82,7 @@ __global__ void k_follow_edges(const uint64_t* __restrict__ d, int64_t nd, int b
 cudaError_t launch_follow_edges(const uint64_t* d, int64_t nd, int id_bits, uint32_t* vis, int32_t* list,
                                 int32_t* count, cudaStream_t s) {
   if (nd == 0) return cudaSuccess;
-  k_follow_edges<<<grid_for(nd, 256), 256, 0, s>>>(d, nd, id_bits, vis, list, count);
+  note_launch(); k_follow_edges<<<grid_for(nd, 256), 256, 0, s>>>(d, nd, id_bits, vis, list, count);
   return cudaGetLastError();
 }
 
@@ -95,7 +95,7 @@ __global__ void k_source_bits(const uint64_t* __restrict__ d, int64_t nd, int bi
 
 cudaError_t launch_source_bits(const uint64_t* d, int64_t nd, int id_bits, uint32_t* bits, cudaStream_t s) {
   if (nd == 0) return cudaSuccess;
-  k_source_bits<<<grid_for(nd, 256), 256, 0, s>>>(d, nd, id_bits, bits);
+  note_launch(); k_source_bits<<<grid_for(nd, 256), 256, 0, s>>>(d, nd, id_bits, bits);
   return cudaGetLastError();
 }
 
@@ -137,10 +137,10 @@ cudaError_t launch_bits_to_list(const uint32_t* a, const uint32_t* b, int32_t n,
   int64_t words = cdiv((int64_t)n, 32);
   int32_t* pc = tmp;
   int32_t* scr = tmp + words + 1;
-  k_word_pop<<<grid_for(words, 256), 256, 0, s>>>(a, b, words, n, pc);
+  note_launch(); k_word_pop<<<grid_for(words, 256), 256, 0, s>>>(a, b, words, n, pc);
   cudaError_t e = scan_excl<int32_t>(pc, pc, words, scr, s);
   if (e != cudaSuccess) return e;
-  k_word_emit<<<grid_for(words, 256), 256, 0, s>>>(a, b, words, n, pc, list, count);
+  note_launch(); k_word_emit<<<grid_for(words, 256), 256, 0, s>>>(a, b, words, n, pc, list, count);
   return cudaGetLastError();
 }
 
@@ -155,7 +155,7 @@ cudaError_t launch_popcount(const uint32_t* a, int64_t words, long long* out, cu
   cudaError_t e = cudaMemsetAsync(out, 0, sizeof(long long), s);
   if (e != cudaSuccess) return e;
   if (words == 0) return cudaSuccess;
-  k_popcount<<<grid_for(words, 256), 256, 0, s>>>(a, words, out);
+  note_launch(); k_popcount<<<grid_for(words, 256), 256, 0, s>>>(a, words, out);
   return cudaGetLastError();
 }
 
@@ -174,7 +174,7 @@ __global__ void k_control(Ctl* ctl, int frontier) {
 }
 
 cudaError_t launch_control(Ctl* ctl, int frontier, cudaStream_t s) {
-  k_control<<<1, 1, 0, s>>>(ctl, frontier);
+  note_launch(); k_control<<<1, 1, 0, s>>>(ctl, frontier);
   return cudaGetLastError();
 }
 
@@ -192,7 +192,7 @@ __global__ void k_tables(double* tab_sc, double* tab_cl, double alpha) {
 }
 
 cudaError_t launch_tables(double* tab_sc, double* tab_cl, double alpha, cudaStream_t s) {
-  k_tables<<<cdiv(TAB, 256), 256, 0, s>>>(tab_sc, tab_cl, alpha);
+  note_launch(); k_tables<<<cdiv(TAB, 256), 256, 0, s>>>(tab_sc, tab_cl, alpha);
   return cudaGetLastError();
 }
 
@@ -212,7 +212,7 @@ __global__ void k_init_uniform(double* R, long long* C, const int32_t* odeg, con
 
 cudaError_t launch_init_uniform(double* R, long long* C, const int32_t* odeg, const double* tab_sc, int32_t n,
                                 cudaStream_t s) {
-  k_init_uniform<<<grid_for(n, 256), 256, 0, s>>>(R, C, odeg, tab_sc, n);
+  note_launch(); k_init_uniform<<<grid_for(n, 256), 256, 0, s>>>(R, C, odeg, tab_sc, n);
   return cudaGetLastError();
 }
 
@@ -223,7 +223,7 @@ __global__ void k_contrib_all(const double* R, long long* C, const int32_t* odeg
 
 cudaError_t launch_contrib_all(const double* R, long long* C, const int32_t* odeg, const double* tab_sc, int32_t n,
                                cudaStream_t s) {
-  k_contrib_all<<<grid_for(n, 256), 256, 0, s>>>(R, C, odeg, tab_sc, n);
+  note_launch(); k_contrib_all<<<grid_for(n, 256), 256, 0, s>>>(R, C, odeg, tab_sc, n);
   return cudaGetLastError();
 }
 
@@ -238,7 +238,7 @@ __global__ void k_contrib_list(const int32_t* list, const int32_t* count, const 
 
 cudaError_t launch_contrib_list(const int32_t* list, const int32_t* count, const double* R, long long* C,
                                 const int32_t* odeg, const double* tab_sc, int32_t n, cudaStream_t s) {
-  k_contrib_list<<<grid_for(n, 256), 256, 0, s>>>(list, count, R, C, odeg, tab_sc);
+  note_launch(); k_contrib_list<<<grid_for(n, 256), 256, 0, s>>>(list, count, R, C, odeg, tab_sc);
   return cudaGetLastError();
 }
 
@@ -252,11 +252,11 @@ __global__ void k_scatter_f64(const double* __restrict__ in, const int32_t* __re
 }
 
 cudaError_t launch_gather_f64(const double* in, const int32_t* idx, double* out, int32_t n, cudaStream_t s) {
-  k_gather_f64<<<grid_for(n, 256), 256, 0, s>>>(in, idx, out, n);
+  note_launch(); k_gather_f64<<<grid_for(n, 256), 256, 0, s>>>(in, idx, out, n);
   return cudaGetLastError();
 }
 cudaError_t launch_scatter_f64(const double* in, const int32_t* idx, double* out, int32_t n, cudaStream_t s) {
-  k_scatter_f64<<<grid_for(n, 256), 256, 0, s>>>(in, idx, out, n);
+  note_launch(); k_scatter_f64<<<grid_for(n, 256), 256, 0, s>>>(in, idx, out, n);
   return cudaGetLastError();
 }
 

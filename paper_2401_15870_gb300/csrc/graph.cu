@@ -166,10 +166,10 @@ int build_csr_from_sorted(Graph* g, Csr* c, const uint64_t* keys, int64_t m, boo
   TRY(t.get(&rowstart, n + 1));
   TRY(t.get(&cap, n + 1));
   TRY(t.get(&scr, scan_tmp_elems(n)));
-  k_row_starts<<<grid_for(m, 256), 256, 0, s>>>(keys, m, g->id_bits, rowstart, n);
+  note_launch(); k_row_starts<<<grid_for(m, 256), 256, 0, s>>>(keys, m, g->id_bits, rowstart, n);
   if (!c->deg) TRY(dalloc(g, (void**)&c->deg, sizeof(int32_t) * n));
   if (!c->off) TRY(dalloc(g, (void**)&c->off, sizeof(int64_t) * (n + 1)));
-  k_deg_cap<<<grid_for(n, 256), 256, 0, s>>>(rowstart, n, slack_quads, c->deg, cap);
+  note_launch(); k_deg_cap<<<grid_for(n, 256), 256, 0, s>>>(rowstart, n, slack_quads, c->deg, cap);
   TRY(scan_excl<int64_t>(cap, c->off, n, scr, s));
   int64_t total = 0;
   TRY(cudaMemcpyAsync(&total, c->off + n, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
@@ -185,8 +185,8 @@ int build_csr_from_sorted(Graph* g, Csr* c, const uint64_t* keys, int64_t m, boo
   }
   TRY(dalloc(g, (void**)&c->col, sizeof(int32_t) * total));
   c->cap = total;
-  k_fill_cols<<<grid_for(m, 256), 256, 0, s>>>(keys, m, g->id_bits, rowstart, c->off, c->col);
-  k_pad_rows<<<grid_for(n, 256), 256, 0, s>>>(c->off, c->deg, n, c->col);
+  note_launch(); k_fill_cols<<<grid_for(m, 256), 256, 0, s>>>(keys, m, g->id_bits, rowstart, c->off, c->col);
+  note_launch(); k_pad_rows<<<grid_for(n, 256), 256, 0, s>>>(c->off, c->deg, n, c->col);
   TRY(cudaGetLastError());
   TRY(cudaStreamSynchronize(s));
   return OK;
@@ -205,7 +205,7 @@ int refresh_full_tiles(Graph* g) {
   }
   TRY(dalloc(g, (void**)&g->full_tfirst, sizeof(int32_t) * (nt + 1)));
   g->full_ntiles = nt;
-  k_full_tiles<<<grid_for(g->n, 256), 256, 0, g->stream>>>(g->in.off, g->n, g->full_tfirst, nt);
+  note_launch(); k_full_tiles<<<grid_for(g->n, 256), 256, 0, g->stream>>>(g->in.off, g->n, g->full_tfirst, nt);
   TRY(cudaGetLastError());
   return OK;
 }
@@ -245,16 +245,16 @@ int build_graph_from_user_keys(Graph* g, uint64_t* keys, int64_t nkeys) {
     TRY(t.get(&vk, n));
     TRY(t.get(&vk_alt, n));
     TRY(t.get((char**)&vtmp, radix_tmp_bytes(n)));
-    k_row_starts<<<grid_for(m, 256), 256, 0, s>>>(ukeys, m, bits, rowstart, n);
-    k_relabel_keys<<<grid_for(n, 256), 256, 0, s>>>(rowstart, n, bits, vk);
+    note_launch(); k_row_starts<<<grid_for(m, 256), 256, 0, s>>>(ukeys, m, bits, rowstart, n);
+    note_launch(); k_relabel_keys<<<grid_for(n, 256), 256, 0, s>>>(rowstart, n, bits, vk);
     TRY(radix_sort_u64(vk, vk_alt, n, 32 + bits, vtmp, s));
-    k_perm_from_sorted<<<grid_for(n, 256), 256, 0, s>>>(vk, n, bits, g->perm, g->iperm);
+    note_launch(); k_perm_from_sorted<<<grid_for(n, 256), 256, 0, s>>>(vk, n, bits, g->perm, g->iperm);
   } else {
     TRY(iota_i32(g->perm, n, s));
     TRY(iota_i32(g->iperm, n, s));
   }
   // out-CSR on internal ids
-  k_remap_keys<<<grid_for(m, 256), 256, 0, s>>>(ukeys, m, bits, g->perm, false, keys);
+  note_launch(); k_remap_keys<<<grid_for(m, 256), 256, 0, s>>>(ukeys, m, bits, g->perm, false, keys);
   {
     uint64_t* alt2;
     TRY(t.get(&alt2, m));
@@ -262,7 +262,7 @@ int build_graph_from_user_keys(Graph* g, uint64_t* keys, int64_t nkeys) {
     int rc = build_csr_from_sorted(g, &g->out, keys, m, false, 1);
     if (rc) return rc;
     // in-CSR: swapped keys
-    k_remap_keys<<<grid_for(m, 256), 256, 0, s>>>(ukeys, m, bits, g->perm, true, keys);
+    note_launch(); k_remap_keys<<<grid_for(m, 256), 256, 0, s>>>(ukeys, m, bits, g->perm, true, keys);
     TRY(radix_sort_u64(keys, alt2, m, 2 * bits, rtmp, s));
     rc = build_csr_from_sorted(g, &g->in, keys, m, true, 1);
     if (rc) return rc;

@@ -1,7 +1,12 @@
 // prim.cu -- scan, radix sort, compaction and fills (see prim.cuh).
+#include <atomic>
 #include "prim.cuh"
 
 namespace dfpr {
+
+static std::atomic<unsigned long long> g_launches{0};
+void note_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
+unsigned long long launches_so_far() { return g_launches.load(std::memory_order_relaxed); }
 
 static int g_sms = 0;
 
@@ -113,9 +118,9 @@ template <typename T>
 cudaError_t scan_excl(const T* in, T* out, int64_t n, T* tmp, cudaStream_t s) {
   int64_t nb = cdiv(n > 0 ? n : 1, SC_CHUNK);
   if (n == 0) return cudaMemsetAsync(out, 0, sizeof(T), s);
-  k_scan_reduce<T><<<(unsigned)nb, SC_THREADS, 0, s>>>(in, n, tmp);
-  k_scan_top<T><<<1, SC_THREADS, 0, s>>>(tmp, nb);
-  k_scan_down<T><<<(unsigned)nb, SC_THREADS, 0, s>>>(in, n, tmp, out, nb);
+  note_launch(); k_scan_reduce<T><<<(unsigned)nb, SC_THREADS, 0, s>>>(in, n, tmp);
+  note_launch(); k_scan_top<T><<<1, SC_THREADS, 0, s>>>(tmp, nb);
+  note_launch(); k_scan_down<T><<<(unsigned)nb, SC_THREADS, 0, s>>>(in, n, tmp, out, nb);
   return cudaGetLastError();
 }
 
@@ -208,10 +213,10 @@ cudaError_t radix_sort_u64(uint64_t* keys, uint64_t* alt, int64_t n, int nbits, 
   uint64_t* src = keys;
   uint64_t* dst = alt;
   for (int shift = 0; shift < nbits; shift += 8) {
-    k_rs_hist<<<(unsigned)ntiles, RS_THREADS, 0, s>>>(src, n, shift, counts, ntiles);
+    note_launch(); k_rs_hist<<<(unsigned)ntiles, RS_THREADS, 0, s>>>(src, n, shift, counts, ntiles);
     cudaError_t e = scan_excl<int32_t>(counts, counts, cnt, scratch, s);
     if (e != cudaSuccess) return e;
-    k_rs_scatter<<<(unsigned)ntiles, RS_THREADS, 0, s>>>(src, dst, n, shift, counts, ntiles);
+    note_launch(); k_rs_scatter<<<(unsigned)ntiles, RS_THREADS, 0, s>>>(src, dst, n, shift, counts, ntiles);
     uint64_t* t = src;
     src = dst;
     dst = t;
@@ -242,10 +247,10 @@ cudaError_t compact_u64(const uint64_t* in, const uint8_t* flag, int64_t n, uint
   if (n == 0) return cudaMemsetAsync(count_dev, 0, sizeof(int64_t), s);
   int64_t* pos = (int64_t*)tmp;
   int64_t* scr = pos + n + 1;
-  k_flag_to_i64<<<grid_for(n, 256), 256, 0, s>>>(flag, n, pos);
+  note_launch(); k_flag_to_i64<<<grid_for(n, 256), 256, 0, s>>>(flag, n, pos);
   cudaError_t e = scan_excl<int64_t>(pos, pos, n, scr, s);
   if (e != cudaSuccess) return e;
-  k_compact_scatter<<<grid_for(n, 256), 256, 0, s>>>(in, flag, pos, n, out, count_dev);
+  note_launch(); k_compact_scatter<<<grid_for(n, 256), 256, 0, s>>>(in, flag, pos, n, out, count_dev);
   return cudaGetLastError();
 }
 
@@ -256,7 +261,7 @@ __global__ void k_flag_unique(const uint64_t* __restrict__ k, int64_t n, uint8_t
 
 cudaError_t flag_unique_sorted(const uint64_t* k, int64_t n, uint8_t* flag, cudaStream_t s) {
   if (n == 0) return cudaSuccess;
-  k_flag_unique<<<grid_for(n, 256), 256, 0, s>>>(k, n, flag);
+  note_launch(); k_flag_unique<<<grid_for(n, 256), 256, 0, s>>>(k, n, flag);
   return cudaGetLastError();
 }
 
@@ -273,17 +278,17 @@ __global__ void k_iota(int32_t* p, int64_t n) {
 
 cudaError_t fill_i32(int32_t* p, int32_t v, int64_t n, cudaStream_t s) {
   if (n <= 0) return cudaSuccess;
-  k_fill<int32_t><<<grid_for(n, 256), 256, 0, s>>>(p, v, n);
+  note_launch(); k_fill<int32_t><<<grid_for(n, 256), 256, 0, s>>>(p, v, n);
   return cudaGetLastError();
 }
 cudaError_t fill_i64(int64_t* p, int64_t v, int64_t n, cudaStream_t s) {
   if (n <= 0) return cudaSuccess;
-  k_fill<int64_t><<<grid_for(n, 256), 256, 0, s>>>(p, v, n);
+  note_launch(); k_fill<int64_t><<<grid_for(n, 256), 256, 0, s>>>(p, v, n);
   return cudaGetLastError();
 }
 cudaError_t iota_i32(int32_t* p, int64_t n, cudaStream_t s) {
   if (n <= 0) return cudaSuccess;
-  k_iota<<<grid_for(n, 256), 256, 0, s>>>(p, n);
+  note_launch(); k_iota<<<grid_for(n, 256), 256, 0, s>>>(p, n);
   return cudaGetLastError();
 }
 

@@ -231,10 +231,10 @@ cudaError_t launch_sweep(int mode, const SweepParams& p, cudaStream_t s) {
     if (want < grid) grid = (int)want;
   }
   switch (mode) {
-    case SWEEP_FULL: k_sweep<SWEEP_FULL><<<grid, SW_THREADS, 0, s>>>(p); break;
-    case SWEEP_LIST: k_sweep<SWEEP_LIST><<<grid, SW_THREADS, 0, s>>>(p); break;
-    case SWEEP_DF: k_sweep<SWEEP_DF><<<grid, SW_THREADS, 0, s>>>(p); break;
-    case SWEEP_DFP: k_sweep<SWEEP_DFP><<<grid, SW_THREADS, 0, s>>>(p); break;
+    case SWEEP_FULL: note_launch(); k_sweep<SWEEP_FULL><<<grid, SW_THREADS, 0, s>>>(p); break;
+    case SWEEP_LIST: note_launch(); k_sweep<SWEEP_LIST><<<grid, SW_THREADS, 0, s>>>(p); break;
+    case SWEEP_DF: note_launch(); k_sweep<SWEEP_DF><<<grid, SW_THREADS, 0, s>>>(p); break;
+    case SWEEP_DFP: note_launch(); k_sweep<SWEEP_DFP><<<grid, SW_THREADS, 0, s>>>(p); break;
     default: return cudaErrorInvalidValue;
   }
   return cudaGetLastError();
@@ -326,9 +326,9 @@ cudaError_t launch_list_scan(const int32_t* list, const int32_t* count, const in
   int64_t maxch = cdiv((int64_t)n + 1, LS_CHUNK);
   int grid = (int)(maxch < num_sms() * 4 ? maxch : num_sms() * 4);
   if (grid < 1) grid = 1;
-  k_ls_reduce<<<grid, LS_THREADS, 0, s>>>(list, count, deg, tmp);
-  k_ls_top<<<1, LS_THREADS, 0, s>>>(tmp, count, qtot_dev, ntiles_dev);
-  k_ls_down<<<grid, LS_THREADS, 0, s>>>(list, count, deg, tmp, qs, tfirst, qtot_dev, ntiles_dev);
+  note_launch(); k_ls_reduce<<<grid, LS_THREADS, 0, s>>>(list, count, deg, tmp);
+  note_launch(); k_ls_top<<<1, LS_THREADS, 0, s>>>(tmp, count, qtot_dev, ntiles_dev);
+  note_launch(); k_ls_down<<<grid, LS_THREADS, 0, s>>>(list, count, deg, tmp, qs, tfirst, qtot_dev, ntiles_dev);
   return cudaGetLastError();
 }
 
@@ -403,7 +403,7 @@ __global__ void __launch_bounds__(SW_THREADS) k_expand(ExpandParams p) {
 }
 
 cudaError_t launch_expand(const ExpandParams& p, cudaStream_t s) {
-  k_expand<<<num_sms() * 4, SW_THREADS, 0, s>>>(p);
+  note_launch(); k_expand<<<num_sms() * 4, SW_THREADS, 0, s>>>(p);
   return cudaGetLastError();
 }
 
@@ -426,7 +426,7 @@ __global__ void k_commit(const int32_t* __restrict__ list, const int32_t* count,
 
 cudaError_t launch_commit(const int32_t* list, const int32_t* count, const double* rnew, double* R, long long* C,
                           const int32_t* odeg, const double* tab_sc, uint32_t* bits_clear, int32_t n, cudaStream_t s) {
-  k_commit<<<grid_for(n, 256), 256, 0, s>>>(list, count, rnew, R, C, odeg, tab_sc, bits_clear);
+  note_launch(); k_commit<<<grid_for(n, 256), 256, 0, s>>>(list, count, rnew, R, C, odeg, tab_sc, bits_clear);
   return cudaGetLastError();
 }
 
