@@ -193,6 +193,32 @@ pr_status pr_last_delta(const pr_graph* g, int64_t* n_del, int64_t* n_ins, int32
  */
 pr_status pr_affected(pr_graph* g, int32_t which, uint8_t* flags);
 
+/*
+ * One synchronous sweep of Eq. 1 over a caller-provided in-CSR, allocating no
+ * memory.  The paper has no counterpart: this entry point exists for callers
+ * that cannot allocate device memory (code running where cudaMalloc is not
+ * allowed or would stall other work, e.g. a serving loop whose device memory
+ * is owned by another allocator).  Every pointer is device memory owned by the
+ * caller:
+ *   in_off[0..n], in_src[0..in_off[n]): in-neighbours u of every vertex v
+ *     (self-loops included, as pr_get_csr(g, 1, ...) exports them);
+ *   out_deg[0..n): |out(u)| >= 1;  r_in[0..n): current ranks;
+ *   r_out[0..n): receives (1-alpha)/n + alpha * sum_u r_in[u]/out_deg[u],
+ *     summed exactly in 2^-61 fixed point like pr_update's sweeps;
+ *   *delta_out: receives max_v |r_out[v] - r_in[v]|.
+ * Work is enqueued on `stream`; the call returns before it completes.  Its
+ * scratch memory (n + 2 int64 values) is a fixed array inside the library,
+ * present on every GPU that loads it until the process exits; n above
+ * PR_NOALLOC_MAX_N is rejected with PR_EINVAL before any device work.  The
+ * first call on a device looks up that array's address (cudaGetSymbolAddress):
+ * make it before any stream capture.  All calls share the array, so calls
+ * that overlap on the GPU race and must be serialized.  Errors: PR_EINVAL
+ * (size, null pointer, alpha), PR_ECUDA.
+ */
+#define PR_NOALLOC_MAX_N 524288
+pr_status pr_sweep_noalloc(int32_t n, const int64_t* in_off, const int32_t* in_src, const int32_t* out_deg,
+                           const double* r_in, double* r_out, double alpha, double* delta_out, void* stream);
+
 /* Number of CUDA kernels this library has launched in this process so far
  * (all graphs); the difference across a region counts its launches. */
 unsigned long long pr_kernel_launches(void);

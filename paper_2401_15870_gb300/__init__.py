@@ -92,6 +92,7 @@ def load():
         "pr_last_error": ([_P], ctypes.c_char_p),
         "pr_status_string": ([ctypes.c_int], ctypes.c_char_p),
         "pr_kernel_launches": ([], ctypes.c_ulonglong),
+        "pr_sweep_noalloc": ([i32, _P, _P, _P, _P, _P, f64, _P, _P], ctypes.c_int),
     }
     for name, (args, res) in sig.items():
         f = getattr(lib, name)
@@ -274,6 +275,18 @@ def pr_affected(h, which):
 
 def pr_last_error(h) -> str:
     return load().pr_last_error(h).decode()
+
+
+PR_NOALLOC_MAX_N = 524288
+
+
+def pr_sweep_noalloc(n, in_off, in_src, out_deg, r_in, r_out, alpha, delta_out, stream=None):
+    """One Eq. 1 sweep over a caller-provided device in-CSR without any device
+    allocation (all arguments are CUDA tensors the caller owns)."""
+    ptrs = [_dev_ptr(in_off, "int64")[0], _dev_ptr(in_src, "int32")[0], _dev_ptr(out_deg, "int32")[0],
+            _dev_ptr(r_in, "float64")[0], _dev_ptr(r_out, "float64")[0]]
+    dp = _dev_ptr(delta_out, "float64")[0]
+    _check(load().pr_sweep_noalloc(int(n), *ptrs, float(alpha), dp, _stream_handle(stream)))
 
 
 def pr_kernel_launches() -> int:
