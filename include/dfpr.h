@@ -71,13 +71,19 @@ typedef struct {
 /* pr_options.flags: time every rank-sweep kernel with CUDA events on the
  * graph's stream and report the sum in pr_stats.ms_sweep. */
 #define PR_OPT_TIME_SWEEPS 1
+/* pr_options.flags for DF / DF-P: sweep the frontier only in pull form (every
+ * vertex with a membership test) or only in push form (frontier lists with
+ * explicit expansion).  By default the form is chosen per iteration from the
+ * frontier's size; the result is the same in every form. */
+#define PR_OPT_FORCE_PULL 2
+#define PR_OPT_FORCE_PUSH 4
 
 /* Outcome of one pr_update (Sec. 4.1.5 measures time and affected vertices). */
 typedef struct {
   int32_t iterations;              /* sweeps run                                            */
   int32_t converged;               /* 1 if the last L-inf change was <= tau                 */
   double delta_R;                  /* L-inf change of the last sweep                        */
-  int64_t vertices_ever_affected;  /* vertices ever marked (Sec. 4.2.3); |V| for Static, ND */
+  int64_t vertices_ever_affected;  /* vertices processed by at least one sweep (Sec. 4.2.3) */
   int64_t edges_processed;         /* in-edges summed over all sweeps                       */
   int64_t vertices_processed;      /* vertex updates over all sweeps                        */
   int64_t eff_deletions;           /* |Delta-| of the last batch                            */

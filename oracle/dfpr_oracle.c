@@ -364,7 +364,6 @@ int or_update(const or_graph *g, int method, double alpha, double tau, double ta
   else if (method == OR_DYNAMIC_TRAVERSAL) {
     if (or_dt_affected(g, F) != OR_OK) { free(R); free(Rn); free(F); free(Fn); free(ever); return OR_ENOMEM; }
   } else or_initial_affected(g, F);
-  for (int32_t v = 0; v < n; v++) ever[v] = F[v];
 
   int frontier = (method == OR_DF || method == OR_DFP);
   int prune = (method == OR_DFP);
@@ -376,6 +375,7 @@ int or_update(const or_graph *g, int method, double alpha, double tau, double ta
     if (frontier) memset(Fn, 0, (size_t)n);
     for (int32_t v = 0; v < n; v++) {
       if (!F[v]) continue;
+      ever[v] = 1;                                          /* processed in some sweep */
       double c = in_sum(g, R, v);
       int64_t d = g->out_off[v + 1] - g->out_off[v];
       double r = prune ? or_rank_closed_loop(alpha, n, c, R[v], d) : or_rank_plain(alpha, n, c);
@@ -392,10 +392,7 @@ int or_update(const or_graph *g, int method, double alpha, double tau, double ta
       }
     }
     memcpy(R, Rn, sizeof(double) * (size_t)n);
-    if (frontier) {
-      memcpy(F, Fn, (size_t)n);
-      for (int32_t v = 0; v < n; v++) ever[v] |= F[v];
-    }
+    if (frontier) memcpy(F, Fn, (size_t)n);
     s.iterations = i + 1;
     s.delta_R = dR;
     if (dR <= tau) { s.converged = 1; break; }

@@ -192,12 +192,16 @@ def pr_apply_batch_device(h, del_src=None, del_dst=None, ins_src=None, ins_dst=N
     _check(load().pr_apply_batch_device(h, dsp, ddp, nd, isp, idp, ni), h)
 
 
-PR_OPT_TIME_SWEEPS = 1
+PR_OPT_TIME_SWEEPS, PR_OPT_FORCE_PULL, PR_OPT_FORCE_PUSH = 1, 2, 4
 
 
-def pr_update(h, method, alpha=0.85, tau=1e-10, tau_f=1e-6, tau_p=1e-6, max_iter=500, time_sweeps=False) -> Stats:
+def pr_update(h, method, alpha=0.85, tau=1e-10, tau_f=1e-6, tau_p=1e-6, max_iter=500, time_sweeps=False,
+              direction=None) -> Stats:
+    """direction: None (chosen per iteration), "pull" or "push" (DF / DF-P)."""
     m = METHODS[method] if isinstance(method, str) else int(method)
-    opts = pr_options(tau_f, tau_p, int(max_iter), PR_OPT_TIME_SWEEPS if time_sweeps else 0)
+    flags = (PR_OPT_TIME_SWEEPS if time_sweeps else 0) | {None: 0, "pull": PR_OPT_FORCE_PULL,
+                                                          "push": PR_OPT_FORCE_PUSH}[direction]
+    opts = pr_options(tau_f, tau_p, int(max_iter), flags)
     st = pr_stats()
     _check(load().pr_update(h, m, float(alpha), float(tau), ctypes.byref(opts), ctypes.byref(st)), h)
     return Stats(st.iterations, bool(st.converged), st.delta_R, st.vertices_ever_affected, st.edges_processed,

@@ -18,6 +18,13 @@
 
 using namespace dfpr;
 
+// DF / DF-P direction choice: a frontier whose in-edges exceed this share of
+// all edges is swept in pull form (every vertex, membership test); a pull
+// frontier whose estimated size falls below this share of the vertices goes
+// back to lists
+constexpr double PULL_EDGE_FRACTION = 0.33;
+constexpr double PUSH_VERTEX_FRACTION = 0.10;
+
 struct pr_graph {
   Graph g;
   cudaEvent_t ev[6] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
@@ -123,6 +130,8 @@ static pr_status alloc_state(pr_graph* h) {
   TRY(cudaMemsetAsync(g->gacc, 0, sizeof(long long) * n, g->stream));
   TRY(dalloc(g, (void**)&g->gcnt, sizeof(int32_t) * n));
   TRY(cudaMemsetAsync(g->gcnt, 0, sizeof(int32_t) * n, g->stream));
+  TRY(dalloc(g, (void**)&g->gany, sizeof(int32_t) * n));
+  TRY(cudaMemsetAsync(g->gany, 0, sizeof(int32_t) * n, g->stream));
   TRY(dalloc(g, (void**)&g->tab_sc, sizeof(double) * TAB));
   TRY(dalloc(g, (void**)&g->tab_cl, sizeof(double) * TAB));
   TRY(dalloc(g, (void**)&g->ctl, sizeof(Ctl)));
@@ -256,16 +265,16 @@ static pr_status initial_marking(pr_graph* h) {
   Graph* g = &h->g;
   cudaStream_t s = g->stream;
   int64_t words = cdiv(g->n, 32) + 1;
-  for (uint32_t* b : {g->bits[0], g->bits[1], g->ever, g->aux})
+  for (uint32_t* b : {g->bits[0], g->bits[1], g->ever, g->aux, g->aux2})
     TRY(cudaMemsetAsync(b, 0, sizeof(uint32_t) * words, s));
   TRY(cudaMemsetAsync(g->ctl, 0, sizeof(Ctl), s));
   // sources of the effective change, each once
   TRY(launch_mark_sources(g->dmin, g->n_dmin, g->dplus, g->n_dplus, g->id_bits, g->aux, g->xl, &g->ctl->nexp, s));
   // G_t.out(u) for every source u ...
-  pr_status st = run_expand(h, g->xl, &g->ctl->nexp, g->bits[0], g->ever, g->wl[0], &g->ctl->count[0], nullptr);
+  pr_status st = run_expand(h, g->xl, &g->ctl->nexp, g->bits[0], nullptr, g->wl[0], &g->ctl->count[0], nullptr);
   if (st != PR_OK) return st;
   // ... and the targets of deleted edges, which complete G_{t-1}.out(u)
-  TRY(launch_mark_targets(g->dmin, g->n_dmin, g->id_bits, g->bits[0], g->ever, g->wl[0], &g->ctl->count[0], s));
+  TRY(launch_mark_targets(g->dmin, g->n_dmin, g->id_bits, g->bits[0], nullptr, g->wl[0], &g->ctl->count[0], s));
   TRY(cudaMemsetAsync(&g->ctl->nexp, 0, sizeof(int32_t), s));
   return PR_OK;
 }
@@ -359,7 +368,7 @@ static pr_status run_update(pr_graph* h, int method, double alpha, double tau, d
         break;
       }
     }
-    ever = n;
+    ever = iters > 0 ? n : 0;
   } else if (method == PR_DYNAMIC_TRAVERSAL) {
     pr_status st = dt_affected(h);
     if (st != PR_OK) return st;
@@ -390,15 +399,78 @@ static pr_status run_update(pr_graph* h, int method, double alpha, double tau, d
       st = read_ctl(g);
       if (st != PR_OK) return st;
     }
-    ever = g->ctl_h->count[0];
+    ever = iters > 0 ? g->ctl_h->count[0] : 0;
   } else {
     pr_status st = initial_marking(h);
     if (st != PR_OK) return st;
-    int mode = method == PR_DF ? SWEEP_DF : SWEEP_DFP;
+    const bool prune = method == PR_DFP;
+    const int push_mode = prune ? SWEEP_DFP : SWEEP_DF;
+    const int pull_mode = prune ? SWEEP_PULL_DFP : SWEEP_PULL_DF;
+    uint32_t* xb[2] = {g->aux, g->aux2};
+    const size_t wbytes = sizeof(uint32_t) * (size_t)(cdiv(n, 32) + 1);
+    const double dbar = (double)g->m / (double)n;
     int cur = 0;
+    bool pull = false;
+    // quad prefix of F_0: its edge volume picks push or pull for the first sweep
+    TRY(launch_list_scan(g->wl[0], &g->ctl->count[0], g->in.deg, n, g->qs, g->tfirst, &g->ctl->qtot,
+                         &g->ctl->ntiles, h->ls_tmp, s));
+    st = read_ctl(g);
+    if (st != PR_OK) return st;
     for (int32_t it = 0; it < max_iter; it++) {
-      TRY(launch_list_scan(g->wl[cur], &g->ctl->count[cur], g->in.deg, n, g->qs, g->tfirst, &g->ctl->qtot,
-                           &g->ctl->ntiles, h->ls_tmp, s));
+      const bool want_pull = (flags & PR_OPT_FORCE_PULL) ||
+                             (!(flags & PR_OPT_FORCE_PUSH) && (double)(4 * g->ctl_h->qtot) > PULL_EDGE_FRACTION * (double)g->m);
+      if (!pull && want_pull) {
+        // large frontier: sweep every vertex and test membership (F_i = S u out(X),
+        // S = bits[cur] holds F_i, X empty)
+        pull = true;
+        TRY(cudaMemsetAsync(xb[cur], 0, wbytes, s));
+      }
+      if (pull) {
+        TRY(cudaMemsetAsync(g->bits[1 - cur], 0, wbytes, s));
+        TRY(cudaMemsetAsync(xb[1 - cur], 0, wbytes, s));
+        p.list = nullptr;
+        p.tfirst = g->full_tfirst;
+        p.ntiles_host = g->full_ntiles;
+        p.Ccur = g->C[g->ccur];
+        p.Cnext = g->C[1 - g->ccur];
+        p.S_cur = g->bits[cur];
+        p.X_cur = xb[cur];
+        p.S_next = g->bits[1 - cur];
+        p.X_next = xb[1 - cur];
+        p.gany = g->gany;
+        p.ever = g->ever;
+        p.cnt_next = &g->ctl->count[1 - cur];
+        p.cnt_x = &g->ctl->nexp;
+        TRY(timer.launch(pull_mode, p, s));
+        TRY(launch_control(g->ctl, 1, s));
+        g->ccur ^= 1;
+        cur ^= 1;
+        st = read_ctl(g);
+        if (st != PR_OK) return st;
+        timer.collect();
+        iters = it + 1;
+        dR = ctl_dR(g->ctl_h);
+        if (dR <= tau) {
+          conv = true;
+          break;
+        }
+        double est = (double)g->ctl_h->count[cur] + dbar * (double)g->ctl_h->nexp_last;
+        if (!(flags & PR_OPT_FORCE_PULL) && est < PUSH_VERTEX_FRACTION * (double)n) {
+          // the frontier shrank: materialise F_{i+1} = S u out(X) as a list
+          pull = false;
+          TRY(launch_bits_to_list(g->bits[cur], nullptr, n, g->wl[cur], &g->ctl->count[cur], h->lbits_tmp, s));
+          TRY(launch_bits_to_list(xb[cur], nullptr, n, g->xl, &g->ctl->nexp, h->lbits_tmp, s));
+          st = run_expand(h, g->xl, &g->ctl->nexp, g->bits[cur], nullptr, g->wl[cur], &g->ctl->count[cur], nullptr);
+          if (st != PR_OK) return st;
+          TRY(cudaMemsetAsync(&g->ctl->nexp, 0, sizeof(int32_t), s));
+          TRY(cudaMemsetAsync(g->bits[1 - cur], 0, wbytes, s));
+          TRY(launch_list_scan(g->wl[cur], &g->ctl->count[cur], g->in.deg, n, g->qs, g->tfirst, &g->ctl->qtot,
+                               &g->ctl->ntiles, h->ls_tmp, s));
+          st = read_ctl(g);
+          if (st != PR_OK) return st;
+        }
+        continue;
+      }
       p.list = g->wl[cur];
       p.count = &g->ctl->count[cur];
       p.qs = g->qs;
@@ -411,14 +483,16 @@ static pr_status run_update(pr_graph* h, int method, double alpha, double tau, d
       p.cnt_next = &g->ctl->count[1 - cur];
       p.xl = g->xl;
       p.cnt_x = &g->ctl->nexp;
-      TRY(timer.launch(mode, p, s));
-      st = run_expand(h, g->xl, &g->ctl->nexp, g->bits[1 - cur], g->ever, g->wl[1 - cur], &g->ctl->count[1 - cur],
+      TRY(timer.launch(push_mode, p, s));
+      st = run_expand(h, g->xl, &g->ctl->nexp, g->bits[1 - cur], nullptr, g->wl[1 - cur], &g->ctl->count[1 - cur],
                       nullptr);
       if (st != PR_OK) return st;
       TRY(launch_commit(g->wl[cur], &g->ctl->count[cur], g->rnew, g->R, g->C[g->ccur], g->out.deg, g->tab_sc,
                         g->bits[cur], n, s));
       TRY(launch_control(g->ctl, 1, s));
       cur ^= 1;
+      TRY(launch_list_scan(g->wl[cur], &g->ctl->count[cur], g->in.deg, n, g->qs, g->tfirst, &g->ctl->qtot,
+                           &g->ctl->ntiles, h->ls_tmp, s));
       st = read_ctl(g);
       if (st != PR_OK) return st;
       timer.collect();
@@ -655,7 +729,8 @@ pr_status pr_update(pr_graph* h, pr_method method, double alpha, double tau, con
     tau_p = opts->tau_p;
     max_iter = opts->max_iter;
     flags = opts->flags;
-    if (flags & ~PR_OPT_TIME_SWEEPS) return PR_EINVAL;
+    if (flags & ~(PR_OPT_TIME_SWEEPS | PR_OPT_FORCE_PULL | PR_OPT_FORCE_PUSH)) return PR_EINVAL;
+    if ((flags & PR_OPT_FORCE_PULL) && (flags & PR_OPT_FORCE_PUSH)) return PR_EINVAL;
   }
   if ((int)method < PR_STATIC || (int)method > PR_DFP) return PR_EINVAL;
   if (!(alpha >= 0.0 && alpha < 1.0) || !(tau >= 0.0) || !(tau_f >= 0.0) || !(tau_p >= 0.0) || max_iter < 0)

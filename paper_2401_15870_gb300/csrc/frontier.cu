@@ -169,6 +169,7 @@ __global__ void k_control(Ctl* ctl, int frontier) {
     int c = ctl->cur;
     ctl->count[c] = 0;
     ctl->cur = 1 - c;
+    ctl->nexp_last = ctl->nexp;
     ctl->nexp = 0;
   }
 }

@@ -29,7 +29,7 @@ struct Ctl {
   int64_t edges;                // in-edges processed (all iterations)
   int64_t verts;                // vertices processed (all iterations)
   int32_t status;               // device-detected error (0 = none)
-  int32_t pad;
+  int32_t nexp_last;            // expander count of the last finished iteration
 };
 
 struct Scratch {
@@ -73,6 +73,7 @@ struct Graph {
   int32_t* xtfirst = nullptr;
   long long* gacc = nullptr;                // partial sums of items split across tiles (n)
   int32_t* gcnt = nullptr;                  // tiles that finished each split item (n)
+  int32_t* gany = nullptr;                  // pull sweeps: an in-neighbour of a split item expanded (n)
   int32_t* full_tfirst = nullptr;           // tile starts for the identity list over in-CSR capacity
   int64_t full_ntiles = 0;
 

@@ -76,26 +76,131 @@ __device__ __forceinline__ void block_flush_stats(double dmax, long long edges, 
   }
 }
 
-// owner of local quad q: largest i in [0, nitems) with lstart[i] <= q (lstart[0] == 0)
-__device__ __forceinline__ int tile_owner(const int32_t* lstart, int nitems, int q) {
-  int lo = 0, hi = nitems - 1;
-  while (lo < hi) {
-    int mid = (lo + hi + 1) >> 1;
-    if (lstart[mid] <= q) lo = mid;
-    else hi = mid - 1;
+// ------------------------------------------------------------------ tiles
+
+// L2 policies: the streamed CSR columns are read once per sweep (evict first),
+// the gathered contributions are reused across the whole sweep (evict last)
+__device__ __forceinline__ uint64_t policy_evict_first() {
+  uint64_t p;
+  asm volatile("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(p));
+  return p;
+}
+__device__ __forceinline__ uint64_t policy_evict_last() {
+  uint64_t p;
+  asm volatile("createpolicy.fractional.L2::evict_last.b64 %0, 1.0;" : "=l"(p));
+  return p;
+}
+__device__ __forceinline__ int4 ld_stream4(const int32_t* p, uint64_t pol) {
+  int4 v;
+  asm volatile("ld.global.nc.L1::no_allocate.L2::cache_hint.v4.s32 {%0, %1, %2, %3}, [%4], %5;"
+               : "=r"(v.x), "=r"(v.y), "=r"(v.z), "=r"(v.w)
+               : "l"(p), "l"(pol));
+  return v;
+}
+__device__ __forceinline__ long long ld_keep(const long long* p, uint64_t pol) {
+  long long v;
+  asm volatile("ld.global.nc.L2::cache_hint.b64 %0, [%1], %2;" : "=l"(v) : "l"(p), "l"(pol));
+  return v;
+}
+
+// Shared-memory view of one tile: for every item (list entry) touching the
+// tile its vertex, the slot offset of its quads, how many tiles it spans, and
+// per local quad the item that owns it.
+struct TileSmem {
+  int16_t owner[SW_TILE_Q];
+  long long adj[SW_MAX_ITEMS];
+  long long acc[SW_MAX_ITEMS];
+  int32_t v[SW_MAX_ITEMS];
+  int32_t nt[SW_MAX_ITEMS];
+  int32_t any[SW_MAX_ITEMS];
+  int32_t wmax[SW_THREADS / WARP];
+};
+
+// Load the items of tile [T0, T1) and build owner[] with a block-wide max-scan
+// of the item starts (each item owns at least one quad, so starts are distinct).
+// ident: items are vertices k with quads ioff[k]/4 .. ioff[k+1]/4; otherwise
+// items are list[k] with quads qs[k] .. qs[k+1].  Returns the item count, or -1
+// for a malformed tile table.
+__device__ __forceinline__ int tile_setup(TileSmem& sm, bool ident, const int32_t* list, const int64_t* qs,
+                                          const int64_t* off, int64_t T0, int64_t T1, int32_t k_lo, int32_t k_hi) {
+  const int nq = (int)(T1 - T0);
+  const int nitems = k_hi - k_lo + 1;
+  if (nitems > SW_MAX_ITEMS || nitems < 1) return -1;
+#pragma unroll
+  for (int j = 0; j < SW_QPT; j++) sm.owner[threadIdx.x * SW_QPT + j] = -1;
+  __syncthreads();
+  for (int i = threadIdx.x; i < nitems; i += SW_THREADS) {
+    int32_t k = k_lo + i;
+    int32_t v = ident ? k : list[k];
+    int64_t q0 = ident ? (off[v] >> 2) : qs[k];
+    int64_t q1 = ident ? (off[v + 1] >> 2) : qs[k + 1];
+    sm.v[i] = v;
+    sm.adj[i] = off[v] - 4 * q0 + 4 * T0;
+    int nt;
+    if (q0 >= T1 || q1 <= T0) nt = -1;
+    else if (q0 >= T0 && q1 <= T1) nt = 0;
+    else nt = (int)((q1 - 1) / SW_TILE_Q - q0 / SW_TILE_Q + 1);
+    sm.nt[i] = nt;
+    sm.acc[i] = 0;
+    sm.any[i] = 0;
+    int64_t ls = q0 > T0 ? q0 - T0 : 0;
+    if (ls < nq) sm.owner[ls] = (int16_t)i;
   }
-  return lo;
+  __syncthreads();
+  // inclusive max-scan of owner[] (SW_QPT consecutive entries per thread)
+  int run[SW_QPT];
+  int m = -1;
+#pragma unroll
+  for (int j = 0; j < SW_QPT; j++) {
+    m = max(m, (int)sm.owner[threadIdx.x * SW_QPT + j]);
+    run[j] = m;
+  }
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  int inc = m;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    int y = __shfl_up_sync(0xffffffffu, inc, o);
+    if (lane >= o) inc = max(inc, y);
+  }
+  if (lane == 31) sm.wmax[w] = inc;
+  int excl = __shfl_up_sync(0xffffffffu, inc, 1);
+  if (lane == 0) excl = -1;
+  __syncthreads();
+  for (int ww = 0; ww < w; ww++) excl = max(excl, sm.wmax[ww]);
+#pragma unroll
+  for (int j = 0; j < SW_QPT; j++) sm.owner[threadIdx.x * SW_QPT + j] = (int16_t)max(excl, run[j]);
+  __syncthreads();
+  return nitems;
+}
+
+// set bit v in B for every lane that asks, one atomic per 32-bit word per warp
+__device__ __forceinline__ void agg_set_bit(uint32_t* B, int32_t v, bool set) {
+  unsigned act = __activemask();
+  unsigned word = (unsigned)v >> 5;
+  unsigned grp = __match_any_sync(act, word);
+  unsigned val = __reduce_or_sync(grp, set ? (1u << (v & 31)) : 0u);
+  if ((threadIdx.x & 31) == __ffs(grp) - 1 && val) atomicOr(B + word, val);
+}
+
+__device__ __forceinline__ void agg_count(int32_t* c, bool yes) {
+  unsigned act = __activemask();
+  unsigned k = __popc(__ballot_sync(act, yes));
+  if ((threadIdx.x & 31) == __ffs(act) - 1 && k) atomicAdd(c, (int)k);
 }
 
 // ------------------------------------------------------------------ sweep
 
 template <int MODE>
-__device__ __forceinline__ void finalize(const SweepParams& p, int32_t k, int32_t v, long long sum, double& dmax,
-                                         long long& edges, long long& verts) {
+__device__ __forceinline__ void finalize(const SweepParams& p, int32_t k, int32_t v, long long sum, bool any,
+                                         double& dmax, long long& edges, long long& verts) {
+  constexpr bool pull = MODE == SWEEP_PULL_DF || MODE == SWEEP_PULL_DFP;
+  constexpr bool closed = MODE == SWEEP_DFP || MODE == SWEEP_PULL_DFP;
+  bool member = true;
+  if (pull) member = any || bit_get(p.S_cur, v);
   double Rv = p.R[v];
   int32_t d = p.odeg[v];
   double r;
-  if (MODE == SWEEP_DFP) {
+  if (closed) {
     // Eq. 2: K = sum over in-neighbours minus the vertex's own self-loop term,
     // r = (C0 + alpha K) / (1 - alpha/d); the self term is removed exactly in
     // fixed point
@@ -109,28 +214,44 @@ __device__ __forceinline__ void finalize(const SweepParams& p, int32_t k, int32_
     r = p.C0 + p.alpha * c;
   }
   double dr = fabs(r - Rv);
-  dmax = fmax(dmax, dr);
-  edges += p.ideg[v];
-  verts += 1;
-  if (MODE == SWEEP_FULL) {
-    p.R[v] = r;
-    double sc = d < TAB ? p.tab_sc[d] : FIX_ONE / (double)d;
-    p.Cnext[v] = __double2ll_rn(r * sc);
+  if (member) {
+    dmax = fmax(dmax, dr);
+    edges += p.ideg[v];
+    verts += 1;
+  }
+  if (MODE == SWEEP_FULL || pull) {
+    long long cn;
+    if (member) {
+      p.R[v] = r;
+      double sc = d < TAB ? p.tab_sc[d] : FIX_ONE / (double)d;
+      cn = __double2ll_rn(r * sc);
+    } else {
+      cn = p.Ccur[v];
+    }
+    p.Cnext[v] = cn;
+    if (pull) {
+      // Alg. 1: prune when dr / max(r, R[v]) <= tau_p (DF-P), expand when it
+      // is > tau_f; both compared without the division, in FP64
+      double mr = fmax(r, Rv);
+      bool stay = member && (MODE == SWEEP_PULL_DF || !(dr <= p.tau_p * mr));
+      bool expand = member && dr > p.tau_f * mr;
+      agg_set_bit(p.S_next, v, stay);
+      agg_set_bit(p.X_next, v, expand);
+      agg_set_bit(p.ever, v, member);
+      agg_count(p.cnt_next, stay);
+      agg_count(p.cnt_x, expand);
+    }
     return;
   }
   p.rnew[k] = r;
   if (MODE == SWEEP_DF || MODE == SWEEP_DFP) {
-    // Alg. 1: prune when dr / max(r, R[v]) <= tau_p (DF-P), expand when it is
-    // > tau_f; both compared without the division, in FP64
     double mr = fmax(r, Rv);
     bool stay = (MODE == SWEEP_DF) || !(dr <= p.tau_p * mr);
     bool expand = dr > p.tau_f * mr;
+    agg_set_bit(p.ever, v, true);
     bool add = stay && bit_tas(p.bits_next, v);
     int slot = warp_append(p.cnt_next, add);
-    if (add) {
-      p.wl_next[slot] = v;
-      if (p.ever) atomicOr(p.ever + (v >> 5), 1u << (v & 31));
-    }
+    if (add) p.wl_next[slot] = v;
     int xs = warp_append(p.cnt_x, expand);
     if (expand) p.xl[xs] = v;
   }
@@ -138,19 +259,18 @@ __device__ __forceinline__ void finalize(const SweepParams& p, int32_t k, int32_
 
 template <int MODE>
 __global__ void __launch_bounds__(SW_THREADS) k_sweep(SweepParams p) {
-  __shared__ int32_t s_lstart[SW_MAX_ITEMS + 1];
-  __shared__ long long s_adj[SW_MAX_ITEMS];
-  __shared__ long long s_acc[SW_MAX_ITEMS];
-  __shared__ int32_t s_v[SW_MAX_ITEMS];
-  __shared__ int32_t s_nt[SW_MAX_ITEMS];
-
-  constexpr bool ident = MODE == SWEEP_FULL;
+  __shared__ TileSmem sm;
+  constexpr bool pull = MODE == SWEEP_PULL_DF || MODE == SWEEP_PULL_DFP;
+  constexpr bool ident = MODE == SWEEP_FULL || pull;
   const int64_t ntiles = ident ? p.ntiles_host : *p.ntiles_dev;
   const int32_t K = ident ? p.n : *p.count;
   const int64_t Qtot = ident ? (p.ioff[p.n] >> 2) : p.qs[K];
+  const uint64_t pol_stream = policy_evict_first();
+  const uint64_t pol_keep = policy_evict_last();
+  const int32_t sent = p.n;
   double dmax = 0.0;
   long long edges = 0, verts = 0;
-  const int lane = threadIdx.x & 31;
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
 
   for (int64_t t = blockIdx.x; t < ntiles; t += gridDim.x) {
     const int64_t T0 = t * SW_TILE_Q;
@@ -158,66 +278,79 @@ __global__ void __launch_bounds__(SW_THREADS) k_sweep(SweepParams p) {
     const int32_t k_lo = p.tfirst[t];
     int32_t k_hi = p.tfirst[t + 1];
     if (k_hi > K - 1) k_hi = K - 1;
-    int nitems = k_hi - k_lo + 1;
-    if (nitems > SW_MAX_ITEMS || nitems < 1) {   // cannot happen for a well-formed tile table
+    const int nitems = tile_setup(sm, ident, p.list, p.qs, p.ioff, T0, T1, k_lo, k_hi);
+    if (nitems < 0) {   // cannot happen for a well-formed tile table
       if (threadIdx.x == 0) p.ctl->status = 1;
       break;
     }
-    for (int i = threadIdx.x; i < nitems; i += SW_THREADS) {
-      int32_t k = k_lo + i;
-      int32_t v = ident ? k : p.list[k];
-      int64_t q0 = ident ? (p.ioff[v] >> 2) : p.qs[k];
-      int64_t q1 = ident ? (p.ioff[v + 1] >> 2) : p.qs[k + 1];
-      s_v[i] = v;
-      s_lstart[i] = (int32_t)(max(q0, T0) - T0);
-      s_adj[i] = p.ioff[v] - 4 * q0 + 4 * T0;
-      int nt;
-      if (q0 >= T1 || q1 <= T0) nt = -1;
-      else if (q0 >= T0 && q1 <= T1) nt = 0;
-      else nt = (int)((q1 - 1) / SW_TILE_Q - q0 / SW_TILE_Q + 1);
-      s_nt[i] = nt;
-      s_acc[i] = 0;
-    }
-    if (threadIdx.x == 0) s_lstart[nitems] = INT_MAX;
-    __syncthreads();
     const int nq = (int)(T1 - T0);
+    // all column loads of this thread first, then all gathers, then the reductions
+    int own[SW_QPT];
+    int4 c[SW_QPT];
 #pragma unroll
     for (int j = 0; j < SW_QPT; j++) {
-      const int q = threadIdx.x + j * SW_THREADS;
-      const bool valid = q < nq;
-      int owner = SW_MAX_ITEMS;
-      long long sum = 0;
-      if (valid) {
-        owner = tile_owner(s_lstart, nitems, q);
-        int4 c = __ldg(reinterpret_cast<const int4*>(p.icol + s_adj[owner] + 4 * (int64_t)q));
-        sum = __ldg(p.Ccur + c.x) + __ldg(p.Ccur + c.y) + __ldg(p.Ccur + c.z) + __ldg(p.Ccur + c.w);
+      const int q = lane + WARP * (w + (SW_THREADS / WARP) * j);
+      own[j] = SW_MAX_ITEMS;
+      c[j] = make_int4(sent, sent, sent, sent);
+      if (q < nq) {
+        own[j] = sm.owner[q];
+        const long long base = ident ? 4 * T0 : sm.adj[own[j]];
+        c[j] = ld_stream4(p.icol + base + 4 * (long long)q, pol_stream);
       }
+    }
+    long long sum[SW_QPT];
+    unsigned xb[SW_QPT];
+#pragma unroll
+    for (int j = 0; j < SW_QPT; j++) {
+      sum[j] = ld_keep(p.Ccur + c[j].x, pol_keep) + ld_keep(p.Ccur + c[j].y, pol_keep) +
+               ld_keep(p.Ccur + c[j].z, pol_keep) + ld_keep(p.Ccur + c[j].w, pol_keep);
+      xb[j] = 0;
+      if (pull) {
+        xb[j] = ((__ldg(p.X_cur + (c[j].x >> 5)) >> (c[j].x & 31)) | (__ldg(p.X_cur + (c[j].y >> 5)) >> (c[j].y & 31)) |
+                 (__ldg(p.X_cur + (c[j].z >> 5)) >> (c[j].z & 31)) | (__ldg(p.X_cur + (c[j].w >> 5)) >> (c[j].w & 31))) &
+                1u;
+      }
+    }
+#pragma unroll
+    for (int j = 0; j < SW_QPT; j++) {
+      const int owner = own[j];
+      long long s = sum[j];
+      unsigned x = xb[j];
 #pragma unroll
       for (int o = 1; o < 32; o <<= 1) {
-        long long os = __shfl_down_sync(0xffffffffu, sum, o);
+        long long os = __shfl_down_sync(0xffffffffu, s, o);
+        unsigned ox = __shfl_down_sync(0xffffffffu, x, o);
         int oo = __shfl_down_sync(0xffffffffu, owner, o);
-        if (lane + o < 32 && oo == owner) sum += os;
+        if (lane + o < 32 && oo == owner) {
+          s += os;
+          x |= ox;
+        }
       }
       int prev = __shfl_up_sync(0xffffffffu, owner, 1);
-      if (valid && (lane == 0 || prev != owner))
-        atomicAdd(reinterpret_cast<unsigned long long*>(&s_acc[owner]), (unsigned long long)sum);
+      if (owner != SW_MAX_ITEMS && (lane == 0 || prev != owner)) {
+        atomicAdd(reinterpret_cast<unsigned long long*>(&sm.acc[owner]), (unsigned long long)s);
+        if (pull && x) sm.any[owner] = 1;
+      }
     }
     __syncthreads();
     for (int i = threadIdx.x; i < nitems; i += SW_THREADS) {
-      int nt = s_nt[i];
+      int nt = sm.nt[i];
       if (nt < 0) continue;
       int32_t k = k_lo + i;
-      long long total = s_acc[i];
+      long long total = sm.acc[i];
+      int any = sm.any[i];
       if (nt > 0) {
         atomicAdd(reinterpret_cast<unsigned long long*>(&p.gacc[k]), (unsigned long long)total);
+        if (pull && any) atomicOr(&p.gany[k], 1);
         __threadfence();
         int ticket = atomicAdd(&p.gcnt[k], 1);
         if (ticket != nt - 1) continue;
         __threadfence();
         total = (long long)atomicExch(reinterpret_cast<unsigned long long*>(&p.gacc[k]), 0ull);
+        if (pull) any = atomicExch(&p.gany[k], 0);
         p.gcnt[k] = 0;
       }
-      finalize<MODE>(p, k, s_v[i], total, dmax, edges, verts);
+      finalize<MODE>(p, k, sm.v[i], total, any != 0, dmax, edges, verts);
     }
     __syncthreads();
   }
@@ -226,7 +359,7 @@ __global__ void __launch_bounds__(SW_THREADS) k_sweep(SweepParams p) {
 
 cudaError_t launch_sweep(int mode, const SweepParams& p, cudaStream_t s) {
   int grid = num_sms() * 4;
-  if (mode == SWEEP_FULL) {
+  if (mode == SWEEP_FULL || mode == SWEEP_PULL_DF || mode == SWEEP_PULL_DFP) {
     int64_t want = p.ntiles_host > 0 ? p.ntiles_host : 1;
     if (want < grid) grid = (int)want;
   }
@@ -235,6 +368,8 @@ cudaError_t launch_sweep(int mode, const SweepParams& p, cudaStream_t s) {
     case SWEEP_LIST: note_launch(); k_sweep<SWEEP_LIST><<<grid, SW_THREADS, 0, s>>>(p); break;
     case SWEEP_DF: note_launch(); k_sweep<SWEEP_DF><<<grid, SW_THREADS, 0, s>>>(p); break;
     case SWEEP_DFP: note_launch(); k_sweep<SWEEP_DFP><<<grid, SW_THREADS, 0, s>>>(p); break;
+    case SWEEP_PULL_DF: note_launch(); k_sweep<SWEEP_PULL_DF><<<grid, SW_THREADS, 0, s>>>(p); break;
+    case SWEEP_PULL_DFP: note_launch(); k_sweep<SWEEP_PULL_DFP><<<grid, SW_THREADS, 0, s>>>(p); break;
     default: return cudaErrorInvalidValue;
   }
   return cudaGetLastError();
@@ -346,55 +481,49 @@ __device__ __forceinline__ bool has_key(const uint64_t* k, int64_t len, uint64_t
 
 // mark every out-neighbour of every listed vertex (Alg. 1: "mark v' as affected")
 __global__ void __launch_bounds__(SW_THREADS) k_expand(ExpandParams p) {
-  __shared__ int32_t s_lstart[SW_MAX_ITEMS + 1];
-  __shared__ long long s_adj[SW_MAX_ITEMS];
-  __shared__ int32_t s_v[SW_MAX_ITEMS];
+  __shared__ TileSmem sm;
   const int64_t ntiles = *p.ntiles_dev;
   const int32_t K = *p.count;
   const int64_t Qtot = p.qs[K];
-  const uint64_t sent = (uint64_t)p.n;
+  const uint64_t pol_stream = policy_evict_first();
+  const int32_t sent = p.n;
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
   for (int64_t t = blockIdx.x; t < ntiles; t += gridDim.x) {
     const int64_t T0 = t * SW_TILE_Q;
     const int64_t T1 = min(T0 + (int64_t)SW_TILE_Q, Qtot);
     const int32_t k_lo = p.tfirst[t];
     int32_t k_hi = p.tfirst[t + 1];
     if (k_hi > K - 1) k_hi = K - 1;
-    int nitems = k_hi - k_lo + 1;
-    if (nitems > SW_MAX_ITEMS || nitems < 1) break;
-    for (int i = threadIdx.x; i < nitems; i += SW_THREADS) {
-      int32_t k = k_lo + i;
-      int32_t v = p.list[k];
-      int64_t q0 = p.qs[k];
-      s_v[i] = v;
-      s_lstart[i] = (int32_t)(max(q0, T0) - T0);
-      s_adj[i] = p.ooff[v] - 4 * q0 + 4 * T0;
-    }
-    if (threadIdx.x == 0) s_lstart[nitems] = INT_MAX;
-    __syncthreads();
+    const int nitems = tile_setup(sm, false, p.list, p.qs, p.ooff, T0, T1, k_lo, k_hi);
+    if (nitems < 0) break;
     const int nq = (int)(T1 - T0);
+    int4 c[SW_QPT];
+    int32_t src[SW_QPT];
 #pragma unroll
     for (int j = 0; j < SW_QPT; j++) {
-      const int q = threadIdx.x + j * SW_THREADS;
-      const bool valid = q < nq;
-      int4 c = make_int4(p.n, p.n, p.n, p.n);
-      int32_t v = 0;
-      if (valid) {
-        int owner = tile_owner(s_lstart, nitems, q);
-        v = s_v[owner];
-        c = __ldg(reinterpret_cast<const int4*>(p.ocol + s_adj[owner] + 4 * (int64_t)q));
+      const int q = lane + WARP * (w + (SW_THREADS / WARP) * j);
+      c[j] = make_int4(sent, sent, sent, sent);
+      src[j] = 0;
+      if (q < nq) {
+        const int owner = sm.owner[q];
+        src[j] = sm.v[owner];
+        c[j] = ld_stream4(p.ocol + sm.adj[owner] + 4 * (long long)q, pol_stream);
       }
-      int ws[4] = {c.x, c.y, c.z, c.w};
+    }
+#pragma unroll
+    for (int j = 0; j < SW_QPT; j++) {
+      int ws[4] = {c[j].x, c[j].y, c[j].z, c[j].w};
 #pragma unroll
       for (int e = 0; e < 4; e++) {
-        int32_t w = ws[e];
-        bool cand = (uint64_t)w != sent;
-        if (cand && p.ins_src_bits && bit_get(p.ins_src_bits, v))
-          cand = !has_key(p.dplus, p.n_dplus, ((uint64_t)v << p.id_bits) | (uint64_t)w);
-        bool add = cand && bit_tas(p.bits, w);
+        int32_t wv = ws[e];
+        bool cand = wv != sent;
+        if (cand && p.ins_src_bits && bit_get(p.ins_src_bits, src[j]))
+          cand = !has_key(p.dplus, p.n_dplus, ((uint64_t)src[j] << p.id_bits) | (uint64_t)wv);
+        bool add = cand && bit_tas(p.bits, wv);
         int slot = warp_append(p.cnt, add);
         if (add) {
-          p.wl[slot] = w;
-          if (p.ever) atomicOr(p.ever + (w >> 5), 1u << (w & 31));
+          p.wl[slot] = wv;
+          if (p.ever) atomicOr(p.ever + (wv >> 5), 1u << (wv & 31));
         }
       }
     }

@@ -10,10 +10,12 @@ constexpr int SW_TILE_Q = SW_THREADS * SW_QPT;     // 1024 quads = 4096 edge slo
 constexpr int SW_MAX_ITEMS = SW_TILE_Q + 2;        // items loaded per tile (those touching it, plus one)
 
 enum SweepMode : int {
-  SWEEP_FULL = 0,   // every vertex, Eq. 1, writes R in place and the next contribution buffer (Static, ND)
-  SWEEP_LIST = 1,   // a fixed vertex list, Eq. 1, new ranks to rnew (Dynamic Traversal)
-  SWEEP_DF = 2,     // frontier list, Eq. 1, expand on a large relative change (DF)
-  SWEEP_DFP = 3,    // frontier list, Eq. 2, prune on a small one, expand on a large one (DF-P)
+  SWEEP_FULL = 0,     // every vertex, Eq. 1, writes R in place and the next contribution buffer (Static, ND)
+  SWEEP_LIST = 1,     // a fixed vertex list, Eq. 1, new ranks to rnew (Dynamic Traversal)
+  SWEEP_DF = 2,       // frontier list, Eq. 1, expand on a large relative change (DF, push)
+  SWEEP_DFP = 3,      // frontier list, Eq. 2, prune on a small one, expand on a large one (DF-P, push)
+  SWEEP_PULL_DF = 4,  // every vertex, processed if in the frontier (stay bit or an expanded in-neighbour), DF
+  SWEEP_PULL_DFP = 5, // the same for DF-P
 };
 
 struct SweepParams {
@@ -46,6 +48,14 @@ struct SweepParams {
   int32_t* cnt_next;
   int32_t* xl;
   int32_t* cnt_x;
+  // pull form of the frontier (PULL_*): F_i = S_cur u out(X_cur); the sweep
+  // writes S_next (vertices that stay) and X_next (vertices that expand) and
+  // counts them in *cnt_next / *cnt_x
+  const uint32_t* S_cur;
+  const uint32_t* X_cur;
+  uint32_t* S_next;
+  uint32_t* X_next;
+  int32_t* gany;             // per split item: an in-neighbour expanded (n)
   Ctl* ctl;
 };
 

@@ -195,6 +195,21 @@ def test_ranks_with_hub_rows_spanning_many_tiles(lib):
         assert np.max(np.abs(G.ranks() - ref)) < TOL, method
 
 
+@pytest.mark.parametrize("direction", ["pull", "push", None])
+@pytest.mark.parametrize("method", ["df", "dfp"])
+@pytest.mark.parametrize("scale,bsize", [(12, 40), (14, 262), (13, 3000)])
+def test_frontier_directions_agree_with_oracle(lib, method, direction, scale, bsize):
+    """Pull sweeps (every vertex, membership test), push sweeps (frontier lists)
+    and the automatic choice give the oracle's ranks and processed sets."""
+    G, O, r0 = rank_case(lib, scale, 16, bsize, 50 + scale)
+    G.set_ranks(r0)
+    st = G.update(method, direction=direction)
+    ref, ost = O.update(method, r_prev=r0)
+    assert np.max(np.abs(G.ranks() - ref)) < TOL
+    assert abs(st.iterations - ost.iterations) <= 1
+    assert st.vertices_ever_affected == pytest.approx(ost.vertices_ever_affected, rel=0.01)
+
+
 def test_successive_batches_and_methods_from_same_ranks(lib):
     n = 1 << 12
     src, dst = synth.rmat(12, 16 * n, 77)
