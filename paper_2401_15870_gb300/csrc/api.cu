@@ -9,7 +9,7 @@
 #include <cstring>
 #include <new>
 #include <vector>
-#include "../../include/dfpr.h"
+#include "dfpr.h"
 #include "batch.cuh"
 #include "frontier.cuh"
 #include "graph.cuh"
@@ -24,6 +24,8 @@ using namespace dfpr;
 // back to lists
 constexpr double PULL_EDGE_FRACTION = 0.33;
 constexpr double PUSH_VERTEX_FRACTION = 0.10;
+// share of L2 given to the contributions gathered with an evict-last policy
+constexpr double HOT_L2_FRACTION = 0.5;
 
 struct pr_graph {
   Graph g;
@@ -122,6 +124,7 @@ static pr_status alloc_state(pr_graph* h) {
   TRY(dalloc(g, (void**)&g->ever, sizeof(uint32_t) * words));
   TRY(dalloc(g, (void**)&g->aux, sizeof(uint32_t) * words));
   TRY(dalloc(g, (void**)&g->aux2, sizeof(uint32_t) * words));
+  TRY(dalloc(g, (void**)&g->anyb, sizeof(uint32_t) * words));
   TRY(dalloc(g, (void**)&g->xl, sizeof(int32_t) * n));
   TRY(dalloc(g, (void**)&g->rnew, sizeof(double) * n));
   TRY(dalloc(g, (void**)&g->qs, sizeof(int64_t) * (n + 1)));
@@ -204,6 +207,14 @@ static double ctl_dR(const Ctl* c) {
   return d;
 }
 
+// vertices whose contributions fit in a share of L2 (the most-gathered ones)
+static int32_t hot_vertices(Graph* g) {
+  int l2 = 0;
+  if (cudaDeviceGetAttribute(&l2, cudaDevAttrL2CacheSize, g->dev) != cudaSuccess || l2 <= 0) l2 = 64 << 20;
+  int64_t hot = (int64_t)(HOT_L2_FRACTION * (double)l2) / (int64_t)sizeof(long long);
+  return (int32_t)(hot < g->n ? hot : g->n);
+}
+
 static SweepParams base_params(Graph* g, double alpha, double tau_f, double tau_p) {
   SweepParams p;
   memset(&p, 0, sizeof(p));
@@ -223,6 +234,7 @@ static SweepParams base_params(Graph* g, double alpha, double tau_f, double tau_
   p.gacc = g->gacc;
   p.gcnt = g->gcnt;
   p.ctl = g->ctl;
+  p.hot = hot_vertices(g);
   return p;
 }
 
@@ -319,7 +331,15 @@ struct SweepTimer {
   int32_t launches = 0;
   cudaError_t launch(int mode, const SweepParams& p, cudaStream_t s) {
     if (on) cudaEventRecord(h->ev[4], s);
-    cudaError_t e = launch_sweep(mode, p, s);
+    cudaError_t e;
+    if (mode == SWEEP_FULL || mode == SWEEP_PULL_DF || mode == SWEEP_PULL_DFP) {
+      Graph* g = &h->g;
+      SweepParams q = p;
+      q.ntiles_host = g->in.cap >> 2;
+      e = launch_full_sweep(mode, q, g->rowbits, g->rowbase, g->anyb, s);
+    } else {
+      e = launch_sweep(mode, p, s);
+    }
     if (on) cudaEventRecord(h->ev[5], s);
     launches++;
     return e;

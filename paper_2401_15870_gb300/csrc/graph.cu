@@ -195,6 +195,23 @@ int build_csr_from_sorted(Graph* g, Csr* c, const uint64_t* keys, int64_t m, boo
 int refresh_full_tiles(Graph* g) {
   int64_t quads = g->in.cap >> 2;
   int64_t nt = cdiv(quads, SW_TILE_Q);
+  // row-start index of the in-CSR for the two-phase full sweep
+  for (auto& p : g->allocs)
+    if (p == g->rowbits || p == g->rowbase) {
+      cudaFree(p);
+      p = nullptr;
+    }
+  int64_t words = cdiv(quads, 32) + 1;
+  TRY(dalloc(g, (void**)&g->rowbits, sizeof(uint32_t) * words));
+  TRY(dalloc(g, (void**)&g->rowbase, sizeof(int32_t) * (words + 1)));
+  {
+    int32_t* tmp;
+    TRY(cudaMalloc(&tmp, sizeof(int32_t) * scan_tmp_elems(words)));
+    cudaError_t e = launch_row_start_index(g->in.off, g->n, quads, g->rowbits, g->rowbase, tmp, g->stream);
+    cudaStreamSynchronize(g->stream);
+    cudaFree(tmp);
+    TRY(e);
+  }
   if (g->full_tfirst) {
     for (auto& p : g->allocs)
       if (p == g->full_tfirst) {

@@ -30,6 +30,8 @@ struct Ctl {
   int64_t verts;                // vertices processed (all iterations)
   int32_t status;               // device-detected error (0 = none)
   int32_t nexp_last;            // expander count of the last finished iteration
+  int32_t nbig;                 // rows deferred to the long-row pass of a full sweep
+  int32_t pad;
 };
 
 struct Scratch {
@@ -76,6 +78,9 @@ struct Graph {
   int32_t* gany = nullptr;                  // pull sweeps: an in-neighbour of a split item expanded (n)
   int32_t* full_tfirst = nullptr;           // tile starts for the identity list over in-CSR capacity
   int64_t full_ntiles = 0;
+  uint32_t* rowbits = nullptr;              // full sweeps: in-CSR quads where a row starts
+  int32_t* rowbase = nullptr;               // rows starting before each 32-quad word
+  uint32_t* anyb = nullptr;                 // full pull sweeps: an in-neighbour expanded (n bits)
 
   // effective change of the last batch, packed keys sorted by (src, dst), internal ids
   uint64_t* dmin = nullptr;

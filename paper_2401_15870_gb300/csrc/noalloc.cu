@@ -25,7 +25,7 @@
 //     host threads on one device) race on the array and give wrong results:
 //     serialize them.
 #include <mutex>
-#include "../../include/dfpr.h"
+#include "dfpr.h"
 #include "common.cuh"
 #include "prim.cuh"
 

@@ -15,6 +15,7 @@
 // order of additions gives the same bits: the result does not depend on the
 // tiling, and integer adds run on GB300's integer pipes (FP64 adds are ~36x
 // slower there).
+#include <algorithm>
 #include <climits>
 #include "sweep.cuh"
 #include "prim.cuh"
@@ -97,11 +98,12 @@ __device__ __forceinline__ int4 ld_stream4(const int32_t* p, uint64_t pol) {
                : "l"(p), "l"(pol));
   return v;
 }
-__device__ __forceinline__ long long ld_keep(const long long* p, uint64_t pol) {
+__device__ __forceinline__ long long ld_hint(const long long* p, uint64_t pol) {
   long long v;
   asm volatile("ld.global.nc.L2::cache_hint.b64 %0, [%1], %2;" : "=l"(v) : "l"(p), "l"(pol));
   return v;
 }
+
 
 // Shared-memory view of one tile: for every item (list entry) touching the
 // tile its vertex, the slot offset of its quads, how many tiles it spans, and
@@ -268,6 +270,7 @@ __global__ void __launch_bounds__(SW_THREADS) k_sweep(SweepParams p) {
   const uint64_t pol_stream = policy_evict_first();
   const uint64_t pol_keep = policy_evict_last();
   const int32_t sent = p.n;
+  const int32_t hot = p.hot;
   double dmax = 0.0;
   long long edges = 0, verts = 0;
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
@@ -302,8 +305,10 @@ __global__ void __launch_bounds__(SW_THREADS) k_sweep(SweepParams p) {
     unsigned xb[SW_QPT];
 #pragma unroll
     for (int j = 0; j < SW_QPT; j++) {
-      sum[j] = ld_keep(p.Ccur + c[j].x, pol_keep) + ld_keep(p.Ccur + c[j].y, pol_keep) +
-               ld_keep(p.Ccur + c[j].z, pol_keep) + ld_keep(p.Ccur + c[j].w, pol_keep);
+      sum[j] = ld_hint(p.Ccur + c[j].x, c[j].x < hot ? pol_keep : pol_stream) +
+               ld_hint(p.Ccur + c[j].y, c[j].y < hot ? pol_keep : pol_stream) +
+               ld_hint(p.Ccur + c[j].z, c[j].z < hot ? pol_keep : pol_stream) +
+               ld_hint(p.Ccur + c[j].w, c[j].w < hot ? pol_keep : pol_stream);
       xb[j] = 0;
       if (pull) {
         xb[j] = ((__ldg(p.X_cur + (c[j].x >> 5)) >> (c[j].x & 31)) | (__ldg(p.X_cur + (c[j].y >> 5)) >> (c[j].y & 31)) |
@@ -355,6 +360,146 @@ __global__ void __launch_bounds__(SW_THREADS) k_sweep(SweepParams p) {
     __syncthreads();
   }
   block_flush_stats(dmax, edges, verts, p.ctl);
+}
+
+// ------------------------------------------------------------------ full sweeps in two phases
+//
+// A sweep over every vertex (Static, ND, and the pull form of DF / DF-P) needs
+// no vertex list: the in-CSR rows lie in vertex order, quad-aligned, so the
+// quad space is walked linearly.
+//   k_gather_rows: each warp takes 32 consecutive quads per step (lane = quad),
+//     loads them as 128-bit streams, gathers the four contributions of each,
+//     and finds each quad's row from a bitmap of row starts (one bit per quad)
+//     and the number of rows before every 32-quad word: the owner of quad q is
+//     rowbase[q/32] + popcount(starts up to q) - 1.  A segmented warp
+//     reduction leaves one partial sum per row piece, which is added to the
+//     row's accumulator (exact integer addition, so the order does not
+//     matter).  In pull form it also records whether any source expanded.
+//   k_finish_rows: one thread per vertex reads and clears its accumulator and
+//     runs the epilogue.
+template <bool PULL>
+__global__ void __launch_bounds__(256) k_gather_rows(const int32_t* __restrict__ icol, const long long* __restrict__ C,
+                                                     const uint32_t* __restrict__ X, const uint32_t* __restrict__ rowbits,
+                                                     const int32_t* __restrict__ rowbase, int64_t nquads,
+                                                     long long* __restrict__ acc, uint32_t* __restrict__ anyb) {
+  const int lane = threadIdx.x & 31;
+  const unsigned upto = lane == 31 ? 0xffffffffu : ((2u << lane) - 1u);
+  const int64_t warp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+  const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  const uint64_t pol_stream = policy_evict_first();
+  const uint64_t pol_keep = policy_evict_last();
+  for (int64_t base = warp * 32 * SW_QPT; base < nquads; base += nw * 32 * SW_QPT) {
+    int4 c[SW_QPT];
+    uint32_t bits[SW_QPT];
+    int32_t rb[SW_QPT];
+#pragma unroll
+    for (int j = 0; j < SW_QPT; j++) {
+      const int64_t q = base + 32 * j + lane;
+      c[j] = q < nquads ? ld_stream4(icol + 4 * q, pol_stream) : make_int4(0, 0, 0, 0);
+      const int64_t w = (base >> 5) + j;
+      bits[j] = w * 32 < nquads ? __ldg(rowbits + w) : 0u;
+      rb[j] = w * 32 < nquads ? __ldg(rowbase + w) : 0;
+    }
+    long long s[SW_QPT];
+    unsigned x[SW_QPT];
+#pragma unroll
+    for (int j = 0; j < SW_QPT; j++) {
+      s[j] = ld_hint(C + c[j].x, pol_keep) + ld_hint(C + c[j].y, pol_keep) + ld_hint(C + c[j].z, pol_keep) +
+             ld_hint(C + c[j].w, pol_keep);
+      x[j] = 0;
+      if (PULL)
+        x[j] = ((__ldg(X + (c[j].x >> 5)) >> (c[j].x & 31)) | (__ldg(X + (c[j].y >> 5)) >> (c[j].y & 31)) |
+                (__ldg(X + (c[j].z >> 5)) >> (c[j].z & 31)) | (__ldg(X + (c[j].w >> 5)) >> (c[j].w & 31))) &
+               1u;
+    }
+#pragma unroll
+    for (int j = 0; j < SW_QPT; j++) {
+      const int64_t q = base + 32 * j + lane;
+      const bool valid = q < nquads;
+      const int owner = valid ? rb[j] + __popc(bits[j] & upto) - 1 : -1;
+      long long sum = s[j];
+      unsigned any = x[j];
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        long long os = __shfl_down_sync(0xffffffffu, sum, o);
+        unsigned ox = __shfl_down_sync(0xffffffffu, any, o);
+        int oo = __shfl_down_sync(0xffffffffu, owner, o);
+        if (lane + o < 32 && oo == owner) {
+          sum += os;
+          any |= ox;
+        }
+      }
+      const int prev = __shfl_up_sync(0xffffffffu, owner, 1);
+      if (valid && (lane == 0 || prev != owner)) {
+        if (sum) atomicAdd(reinterpret_cast<unsigned long long*>(acc + owner), (unsigned long long)sum);
+        if (PULL && any) atomicOr(anyb + (owner >> 5), 1u << (owner & 31));
+      }
+    }
+  }
+}
+
+template <int MODE>
+__global__ void __launch_bounds__(256) k_finish_rows(SweepParams p, long long* __restrict__ acc,
+                                                     const uint32_t* __restrict__ anyb) {
+  constexpr bool pull = MODE == SWEEP_PULL_DF || MODE == SWEEP_PULL_DFP;
+  double dmax = 0.0;
+  long long edges = 0, verts = 0;
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; v < p.n; v += stride) {
+    const long long sum = acc[v];
+    acc[v] = 0;
+    const bool any = pull && ((__ldg(anyb + (v >> 5)) >> (v & 31)) & 1u);
+    finalize<MODE>(p, (int32_t)v, (int32_t)v, sum, any, dmax, edges, verts);
+  }
+  block_flush_stats(dmax, edges, verts, p.ctl);
+}
+
+cudaError_t launch_full_sweep(int mode, const SweepParams& p, const uint32_t* rowbits, const int32_t* rowbase,
+                              uint32_t* anyb, cudaStream_t s) {
+  const int64_t nquads = p.ntiles_host;   // quads of the in-CSR capacity
+  const int sms = num_sms();
+  const bool pull = mode == SWEEP_PULL_DF || mode == SWEEP_PULL_DFP;
+  if (pull) {
+    cudaError_t e = cudaMemsetAsync(anyb, 0, sizeof(uint32_t) * (size_t)(cdiv(p.n, 32) + 1), s);
+    if (e != cudaSuccess) return e;
+  }
+  int qgrid = (int)std::min<int64_t>(cdiv(nquads, 32 * SW_QPT * 8) + 1, (int64_t)sms * 16);
+  note_launch();
+  if (pull) k_gather_rows<true><<<qgrid, 256, 0, s>>>(p.icol, p.Ccur, p.X_cur, rowbits, rowbase, nquads, p.gacc, anyb);
+  else k_gather_rows<false><<<qgrid, 256, 0, s>>>(p.icol, p.Ccur, nullptr, rowbits, rowbase, nquads, p.gacc, anyb);
+  int rgrid = grid_for(p.n, 256);
+  switch (mode) {
+    case SWEEP_FULL: note_launch(); k_finish_rows<SWEEP_FULL><<<rgrid, 256, 0, s>>>(p, p.gacc, anyb); break;
+    case SWEEP_PULL_DF: note_launch(); k_finish_rows<SWEEP_PULL_DF><<<rgrid, 256, 0, s>>>(p, p.gacc, anyb); break;
+    case SWEEP_PULL_DFP: note_launch(); k_finish_rows<SWEEP_PULL_DFP><<<rgrid, 256, 0, s>>>(p, p.gacc, anyb); break;
+    default: return cudaErrorInvalidValue;
+  }
+  return cudaGetLastError();
+}
+
+// bitmap of the quads where an in-CSR row starts, and per 32-quad word the
+// number of rows that start before it
+__global__ void k_row_start_bits(const int64_t* __restrict__ off, int32_t n, uint32_t* __restrict__ bits) {
+  for (int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; v < n; v += (int64_t)gridDim.x * blockDim.x) {
+    int64_t q = off[v] >> 2;
+    atomicOr(bits + (q >> 5), 1u << (q & 31));
+  }
+}
+__global__ void k_word_popc(const uint32_t* __restrict__ bits, int64_t words, int32_t* __restrict__ out) {
+  for (int64_t w = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; w < words; w += (int64_t)gridDim.x * blockDim.x)
+    out[w] = __popc(bits[w]);
+}
+
+cudaError_t launch_row_start_index(const int64_t* off, int32_t n, int64_t nquads, uint32_t* rowbits, int32_t* rowbase,
+                                   int32_t* tmp, cudaStream_t s) {
+  const int64_t words = cdiv(nquads, 32);
+  cudaError_t e = cudaMemsetAsync(rowbits, 0, sizeof(uint32_t) * (size_t)(words + 1), s);
+  if (e != cudaSuccess) return e;
+  note_launch(); k_row_start_bits<<<grid_for(n, 256), 256, 0, s>>>(off, n, rowbits);
+  note_launch(); k_word_popc<<<grid_for(words, 256), 256, 0, s>>>(rowbits, words, rowbase);
+  e = scan_excl<int32_t>(rowbase, rowbase, words, tmp, s);
+  if (e != cudaSuccess) return e;
+  return cudaGetLastError();
 }
 
 cudaError_t launch_sweep(int mode, const SweepParams& p, cudaStream_t s) {

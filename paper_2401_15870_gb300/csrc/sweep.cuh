@@ -31,6 +31,10 @@ struct SweepParams {
   const double* tab_sc;      // 2^61 / d
   const double* tab_cl;      // 1 / (1 - alpha/d)
   double alpha, C0, tau_f, tau_p;
+  // contributions of vertices below `hot` are gathered with an L2 evict-last
+  // policy and the rest with evict-first, so the most-read contributions
+  // (internal ids are ordered by decreasing out-degree) stay in L2
+  int32_t hot;
   // the swept list: identity (list == nullptr) over in-CSR capacity quads, or
   // list[0..*count) with quad prefix qs
   const int32_t* list;
@@ -60,6 +64,17 @@ struct SweepParams {
 };
 
 cudaError_t launch_sweep(int mode, const SweepParams& p, cudaStream_t s);
+
+// every-vertex sweep (FULL, PULL_DF, PULL_DFP) in two phases; p.ntiles_host is
+// the number of quads of the in-CSR capacity, p.gacc the all-zero per-vertex
+// accumulators (left zero), rowbits / rowbase the row-start index of the
+// in-CSR (launch_row_start_index), anyb an n-bit scratch bitset
+cudaError_t launch_full_sweep(int mode, const SweepParams& p, const uint32_t* rowbits, const int32_t* rowbase,
+                              uint32_t* anyb, cudaStream_t s);
+// row-start index of the in-CSR: rowbits (nquads/32 + 1 words), rowbase (as
+// many int32 + 1); tmp: scan_tmp_elems(nquads/32 + 1) int32
+cudaError_t launch_row_start_index(const int64_t* off, int32_t n, int64_t nquads, uint32_t* rowbits, int32_t* rowbase,
+                                   int32_t* tmp, cudaStream_t s);
 
 // quad prefix + tile starts of list[0..*count) with quads(v) = ceil(deg[v]/4);
 // writes qs[0..K], tfirst[0..ntiles], *qtot_dev, *ntiles_dev.  tmp: >= list_scan_tmp(n) int64
