@@ -134,11 +134,14 @@ __global__ void k_row_keys(const uint64_t* __restrict__ a, int64_t na, const uin
   GRID_STRIDE(i, na + nb) out[i] = (i < na ? a[i] : b[i - na]) >> bits;
 }
 
-// per touched row: ranges in the deletion / insertion lists, new degree, overflow
+// per touched row: ranges in the deletion / insertion lists, old degree,
+// chunk counts of the copy and write passes, overflow
+constexpr int RW_CH = 1024;   // row elements per chunk (one warp works on a chunk)
+
 __global__ void k_row_plan(const uint64_t* __restrict__ rows, int64_t nr, const uint64_t* __restrict__ dl, int64_t nd,
                            const uint64_t* __restrict__ il, int64_t ni, int bits, const int64_t* __restrict__ off,
                            const int32_t* __restrict__ deg, int64_t* __restrict__ plan, int64_t* __restrict__ olddeg,
-                           unsigned long long* overflow) {
+                           int64_t* __restrict__ cchunks, int64_t* __restrict__ wchunks, unsigned long long* overflow) {
   GRID_STRIDE(j, nr) {
     uint64_t r = rows[j];
     int64_t d0 = lower_key(dl, 0, nd, r << bits), d1 = lower_key(dl, d0, nd, (r + 1) << bits);
@@ -150,58 +153,116 @@ __global__ void k_row_plan(const uint64_t* __restrict__ rows, int64_t nr, const 
     plan[4 * j + 2] = i0;
     plan[4 * j + 3] = i1;
     olddeg[j] = dg;
+    cchunks[j] = cdiv(dg, RW_CH);
+    wchunks[j] = cdiv(round4(dg > nd2 ? dg : nd2), RW_CH);
     if (round4(nd2) > off[r + 1] - off[r]) atomicAdd(overflow, 1ull);
   }
 }
 
-// one warp per touched row: copy old row to scratch, then write the merged row
-__global__ void k_row_rewrite(const uint64_t* __restrict__ rows, int64_t nr, const int64_t* __restrict__ plan,
-                              const int64_t* __restrict__ sofs, const uint64_t* __restrict__ dl,
-                              const uint64_t* __restrict__ il, int bits, const int64_t* __restrict__ off,
-                              int32_t* __restrict__ deg, int32_t* __restrict__ col, int32_t* __restrict__ scratch,
-                              int32_t sent) {
-  uint64_t mask = (1ull << bits) - 1;
-  int lane = threadIdx.x & 31;
-  int64_t warp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
-  int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
-  for (int64_t j = warp; j < nr; j += nwarps) {
-    int64_t r = (int64_t)rows[j];
-    int64_t base = off[r];
-    int32_t d_old = deg[r];
-    int64_t d0 = plan[4 * j], d1 = plan[4 * j + 1], i0 = plan[4 * j + 2], i1 = plan[4 * j + 3];
+// row j of chunk c: largest j with pre[j] <= c
+__device__ __forceinline__ int64_t chunk_row(const int64_t* pre, int64_t nr, int64_t c) {
+  int64_t lo = 0, hi = nr - 1;
+  while (lo < hi) {
+    int64_t mid = (lo + hi + 1) >> 1;
+    if (pre[mid] <= c) lo = mid;
+    else hi = mid - 1;
+  }
+  return lo;
+}
+
+// copy pass: the old elements of every touched row into scratch, one warp per chunk
+__global__ void k_row_copy(const uint64_t* __restrict__ rows, int64_t nr, const int64_t* __restrict__ sofs,
+                           const int64_t* __restrict__ cpre, const int64_t* __restrict__ off,
+                           const int32_t* __restrict__ deg, const int32_t* __restrict__ col, int32_t* __restrict__ scratch) {
+  const int lane = threadIdx.x & 31;
+  const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  const int64_t total = cpre[nr];
+  for (int64_t c = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5; c < total; c += nw) {
+    const int64_t j = chunk_row(cpre, nr, c);
+    const int64_t r = (int64_t)rows[j];
+    const int64_t x0 = (c - cpre[j]) * RW_CH;
+    const int64_t x1 = min(x0 + (int64_t)RW_CH, (int64_t)deg[r]);
+    const int64_t base = off[r];
     int32_t* S = scratch + sofs[j];
-    const int64_t cap = off[r + 1] - base;   // every write below is kept inside the row
-    for (int32_t x = lane; x < d_old; x += 32) S[x] = col[base + x];
-    __syncwarp();
-    // survivors
-    for (int32_t x = lane; x < d_old; x += 32) {
-      int32_t v = S[x];
-      uint64_t key = ((uint64_t)r << bits) | (uint64_t)v;
-      int64_t dl_lt = lower_key(dl, d0, d1, key);
-      if (dl_lt < d1 && dl[dl_lt] == key) continue;   // deleted
-      int64_t il_lt = lower_key(il, i0, i1, key);
-      int64_t pos = x - (dl_lt - d0) + (il_lt - i0);
-      if (pos >= 0 && pos < cap) col[base + pos] = v;
-    }
-    // insertions
-    for (int64_t k = i0 + lane; k < i1; k += 32) {
-      int32_t y = (int32_t)(il[k] & mask);
-      int32_t lo = 0, hi = d_old;
-      while (lo < hi) {
-        int32_t mid = (lo + hi) >> 1;
-        if (S[mid] < y) lo = mid + 1;
-        else hi = mid;
+    for (int64_t x = x0 + lane; x < x1; x += 32) S[x] = col[base + x];
+  }
+}
+
+// write pass over old positions: every surviving element moves to
+// x - (#deletions below it) + (#insertions below it); slots from the new degree
+// up to the old end get the sentinel
+__global__ void k_row_survivors(const uint64_t* __restrict__ rows, int64_t nr, const int64_t* __restrict__ plan,
+                                const int64_t* __restrict__ sofs, const int64_t* __restrict__ wpre,
+                                const uint64_t* __restrict__ dl, const uint64_t* __restrict__ il, int bits,
+                                const int64_t* __restrict__ off, const int32_t* __restrict__ deg, int32_t* __restrict__ col,
+                                const int32_t* __restrict__ scratch, int32_t sent) {
+  const int lane = threadIdx.x & 31;
+  const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  const int64_t total = wpre[nr];
+  for (int64_t c = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5; c < total; c += nw) {
+    const int64_t j = chunk_row(wpre, nr, c);
+    const int64_t r = (int64_t)rows[j];
+    const int64_t d0 = plan[4 * j], d1 = plan[4 * j + 1], i0 = plan[4 * j + 2], i1 = plan[4 * j + 3];
+    const int64_t d_old = deg[r];
+    const int64_t d_new = d_old - (d1 - d0) + (i1 - i0);
+    const int64_t pad_end = round4(d_old > d_new ? d_old : d_new);
+    const int64_t base = off[r], cap = off[r + 1] - base;
+    const int32_t* S = scratch + sofs[j];
+    const int64_t x0 = (c - wpre[j]) * RW_CH;
+    const int64_t x1 = min(x0 + (int64_t)RW_CH, pad_end);
+    for (int64_t x = x0 + lane; x < x1; x += 32) {
+      if (x < d_old) {
+        const int32_t v = S[x];
+        const uint64_t key = ((uint64_t)r << bits) | (uint64_t)v;
+        const int64_t dl_lt = lower_key(dl, d0, d1, key);
+        if (!(dl_lt < d1 && dl[dl_lt] == key)) {
+          const int64_t pos = x - (dl_lt - d0) + (lower_key(il, i0, i1, key) - i0);
+          if (pos >= 0 && pos < cap) col[base + pos] = v;
+        }
       }
-      uint64_t key = ((uint64_t)r << bits) | (uint64_t)y;
-      int64_t dl_lt = lower_key(dl, d0, d1, key);
-      int64_t pos = (k - i0) + lo - (dl_lt - d0);
-      if (pos >= 0 && pos < cap) col[base + pos] = y;
+      if (x >= d_new && x < cap) col[base + x] = sent;
     }
-    int32_t d_new = d_old - (int32_t)(d1 - d0) + (int32_t)(i1 - i0);
-    int64_t pad_end = round4(d_old > d_new ? d_old : d_new);
-    for (int64_t x = d_new + lane; x < pad_end && x < cap; x += 32) col[base + x] = sent;
-    if (lane == 0) deg[r] = d_new;
-    __syncwarp();
+  }
+}
+
+// write pass over insertions: insertion k of row r goes to
+// (#insertions below it) + (#old elements below it) - (#deletions below it)
+__global__ void k_row_insertions(const uint64_t* __restrict__ rows, int64_t nr, const int64_t* __restrict__ plan,
+                                 const int64_t* __restrict__ sofs, const uint64_t* __restrict__ dl,
+                                 const uint64_t* __restrict__ il, int64_t ni, int bits, const int64_t* __restrict__ off,
+                                 const int32_t* __restrict__ deg, int32_t* __restrict__ col,
+                                 const int32_t* __restrict__ scratch) {
+  const uint64_t mask = (1ull << bits) - 1;
+  GRID_STRIDE(k, ni) {
+    const uint64_t r = il[k] >> bits;
+    int64_t lo = 0, hi = nr - 1;   // touched-row index of r
+    while (lo < hi) {
+      int64_t mid = (lo + hi) >> 1;
+      if (rows[mid] < r) lo = mid + 1;
+      else hi = mid;
+    }
+    const int64_t j = lo;
+    const int64_t d0 = plan[4 * j], d1 = plan[4 * j + 1], i0 = plan[4 * j + 2];
+    const int32_t y = (int32_t)(il[k] & mask);
+    const int32_t* S = scratch + sofs[j];
+    int32_t a = 0, b = deg[r];
+    while (a < b) {
+      int32_t mid = (a + b) >> 1;
+      if (S[mid] < y) a = mid + 1;
+      else b = mid;
+    }
+    const int64_t dl_lt = lower_key(dl, d0, d1, (r << bits) | (uint64_t)y);
+    const int64_t pos = (k - i0) + a - (dl_lt - d0);
+    const int64_t base = off[r], cap = off[r + 1] - base;
+    if (pos >= 0 && pos < cap) col[base + pos] = y;
+  }
+}
+
+__global__ void k_row_degrees(const uint64_t* __restrict__ rows, int64_t nr, const int64_t* __restrict__ plan,
+                              int32_t* __restrict__ deg) {
+  GRID_STRIDE(j, nr) {
+    const uint64_t r = rows[j];
+    deg[r] = deg[r] - (int32_t)(plan[4 * j + 1] - plan[4 * j]) + (int32_t)(plan[4 * j + 3] - plan[4 * j + 2]);
   }
 }
 
@@ -277,7 +338,7 @@ static int edit_direction(Graph* g, Csr* c, const uint64_t* dl, int64_t nd, cons
   {
     Carve probe(nullptr);
     probe.take<int64_t>(4 * nr);
-    probe.take<int64_t>(nr + 1);
+    for (int i = 0; i < 3; i++) probe.take<int64_t>(nr + 1);
     probe.take<int64_t>(scan_tmp_elems(nr));
     probe.take<unsigned long long>(1);
     need2 = probe.used + 4096;
@@ -286,11 +347,16 @@ static int edit_direction(Graph* g, Csr* c, const uint64_t* dl, int64_t nd, cons
   Carve c2(base2);
   int64_t* plan = c2.take<int64_t>(4 * nr);
   int64_t* sofs = c2.take<int64_t>(nr + 1);
+  int64_t* cpre = c2.take<int64_t>(nr + 1);
+  int64_t* wpre = c2.take<int64_t>(nr + 1);
   int64_t* sscr = c2.take<int64_t>(scan_tmp_elems(nr));
   unsigned long long* ovf = c2.take<unsigned long long>(1);
   TRY(cudaMemsetAsync(ovf, 0, sizeof(unsigned long long), s));
-  note_launch(); k_row_plan<<<grid_for(nr, 256), 256, 0, s>>>(rows, nr, dl, nd, il, ni, bits, c->off, c->deg, plan, sofs, ovf);
+  note_launch(); k_row_plan<<<grid_for(nr, 256), 256, 0, s>>>(rows, nr, dl, nd, il, ni, bits, c->off, c->deg, plan, sofs,
+                                                              cpre, wpre, ovf);
   TRY(scan_excl<int64_t>(sofs, sofs, nr, sscr, s));
+  TRY(scan_excl<int64_t>(cpre, cpre, nr, sscr, s));
+  TRY(scan_excl<int64_t>(wpre, wpre, nr, sscr, s));
   unsigned long long ovf_h = 0;
   int64_t stot = 0;
   TRY(cudaMemcpyAsync(&ovf_h, ovf, sizeof(ovf_h), cudaMemcpyDeviceToHost, s));
@@ -300,11 +366,16 @@ static int edit_direction(Graph* g, Csr* c, const uint64_t* dl, int64_t nd, cons
   if (ovf_h == 0) {
     void* sp;
     TRY(scratch_get(g, 5, sizeof(int32_t) * (size_t)(stot + 1), &sp));
-    int64_t warps = nr;
-    int blocks = (int)std::min<int64_t>(cdiv(warps * 32, 256), (int64_t)num_sms() * 16);
-    if (blocks < 1) blocks = 1;
-    note_launch(); k_row_rewrite<<<blocks, 256, 0, s>>>(rows, nr, plan, sofs, dl, il, bits, c->off, c->deg, c->col, (int32_t*)sp,
-                                         g->n);
+    int32_t* S = (int32_t*)sp;
+    const int wgrid = num_sms() * 16;
+    note_launch(); k_row_copy<<<wgrid, 256, 0, s>>>(rows, nr, sofs, cpre, c->off, c->deg, c->col, S);
+    note_launch(); k_row_survivors<<<wgrid, 256, 0, s>>>(rows, nr, plan, sofs, wpre, dl, il, bits, c->off, c->deg, c->col, S,
+                                                         g->n);
+    if (ni) {
+      note_launch(); k_row_insertions<<<grid_for(ni, 256), 256, 0, s>>>(rows, nr, plan, sofs, dl, il, ni, bits, c->off,
+                                                                        c->deg, c->col, S);
+    }
+    note_launch(); k_row_degrees<<<grid_for(nr, 256), 256, 0, s>>>(rows, nr, plan, c->deg);
     TRY(cudaGetLastError());
     return OK;
   }
