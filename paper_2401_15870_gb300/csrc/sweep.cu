@@ -379,8 +379,9 @@ __global__ void __launch_bounds__(SW_THREADS) k_sweep(SweepParams p) {
 //     runs the epilogue.
 template <bool PULL>
 __global__ void __launch_bounds__(256) k_gather_rows(const int32_t* __restrict__ icol, const long long* __restrict__ C,
-                                                     const uint32_t* __restrict__ X, const uint32_t* __restrict__ rowbits,
-                                                     const int32_t* __restrict__ rowbase, int64_t nquads,
+                                                     const uint32_t* __restrict__ X, const uint32_t* __restrict__ S,
+                                                     const uint32_t* __restrict__ rowbits,
+                                                     const int32_t* __restrict__ rowbase, int64_t nquads, int32_t sent,
                                                      long long* __restrict__ acc, uint32_t* __restrict__ anyb) {
   const int lane = threadIdx.x & 31;
   const unsigned upto = lane == 31 ? 0xffffffffu : ((2u << lane) - 1u);
@@ -388,51 +389,52 @@ __global__ void __launch_bounds__(256) k_gather_rows(const int32_t* __restrict__
   const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
   const uint64_t pol_stream = policy_evict_first();
   const uint64_t pol_keep = policy_evict_last();
+  // sentinel slots (row slack) contribute 0 and issue no load
+  auto contrib = [&](int32_t c) -> long long { return c != sent ? ld_hint(C + c, pol_keep) : 0ll; };
+  auto expanded = [&](int32_t c) -> unsigned { return c != sent ? (__ldg(X + (c >> 5)) >> (c & 31)) : 0u; };
   for (int64_t base = warp * 32 * SW_QPT; base < nquads; base += nw * 32 * SW_QPT) {
     int4 c[SW_QPT];
-    uint32_t bits[SW_QPT];
-    int32_t rb[SW_QPT];
+    int owner[SW_QPT];
 #pragma unroll
     for (int j = 0; j < SW_QPT; j++) {
       const int64_t q = base + 32 * j + lane;
-      c[j] = q < nquads ? ld_stream4(icol + 4 * q, pol_stream) : make_int4(0, 0, 0, 0);
+      const bool valid = q < nquads;
+      c[j] = valid ? ld_stream4(icol + 4 * q, pol_stream) : make_int4(sent, sent, sent, sent);
       const int64_t w = (base >> 5) + j;
-      bits[j] = w * 32 < nquads ? __ldg(rowbits + w) : 0u;
-      rb[j] = w * 32 < nquads ? __ldg(rowbase + w) : 0;
+      const uint32_t bits = w * 32 < nquads ? __ldg(rowbits + w) : 0u;
+      const int32_t rb = w * 32 < nquads ? __ldg(rowbase + w) : 0;
+      owner[j] = valid ? rb + __popc(bits & upto) - 1 : -1;
     }
     long long s[SW_QPT];
     unsigned x[SW_QPT];
 #pragma unroll
     for (int j = 0; j < SW_QPT; j++) {
-      s[j] = ld_hint(C + c[j].x, pol_keep) + ld_hint(C + c[j].y, pol_keep) + ld_hint(C + c[j].z, pol_keep) +
-             ld_hint(C + c[j].w, pol_keep);
+      s[j] = contrib(c[j].x) + contrib(c[j].y) + contrib(c[j].z) + contrib(c[j].w);
       x[j] = 0;
-      if (PULL)
-        x[j] = ((__ldg(X + (c[j].x >> 5)) >> (c[j].x & 31)) | (__ldg(X + (c[j].y >> 5)) >> (c[j].y & 31)) |
-                (__ldg(X + (c[j].z >> 5)) >> (c[j].z & 31)) | (__ldg(X + (c[j].w >> 5)) >> (c[j].w & 31))) &
-               1u;
+      // a row whose vertex stays in the frontier is processed anyway: its
+      // sources' expanded bits are not needed
+      if (PULL && owner[j] >= 0 && !((__ldg(S + (owner[j] >> 5)) >> (owner[j] & 31)) & 1u))
+        x[j] = (expanded(c[j].x) | expanded(c[j].y) | expanded(c[j].z) | expanded(c[j].w)) & 1u;
     }
 #pragma unroll
     for (int j = 0; j < SW_QPT; j++) {
-      const int64_t q = base + 32 * j + lane;
-      const bool valid = q < nquads;
-      const int owner = valid ? rb[j] + __popc(bits[j] & upto) - 1 : -1;
+      const int own = owner[j];
       long long sum = s[j];
       unsigned any = x[j];
 #pragma unroll
       for (int o = 1; o < 32; o <<= 1) {
         long long os = __shfl_down_sync(0xffffffffu, sum, o);
         unsigned ox = __shfl_down_sync(0xffffffffu, any, o);
-        int oo = __shfl_down_sync(0xffffffffu, owner, o);
-        if (lane + o < 32 && oo == owner) {
+        int oo = __shfl_down_sync(0xffffffffu, own, o);
+        if (lane + o < 32 && oo == own) {
           sum += os;
           any |= ox;
         }
       }
-      const int prev = __shfl_up_sync(0xffffffffu, owner, 1);
-      if (valid && (lane == 0 || prev != owner)) {
-        if (sum) atomicAdd(reinterpret_cast<unsigned long long*>(acc + owner), (unsigned long long)sum);
-        if (PULL && any) atomicOr(anyb + (owner >> 5), 1u << (owner & 31));
+      const int prev = __shfl_up_sync(0xffffffffu, own, 1);
+      if (own >= 0 && (lane == 0 || prev != own)) {
+        if (sum) atomicAdd(reinterpret_cast<unsigned long long*>(acc + own), (unsigned long long)sum);
+        if (PULL && any) atomicOr(anyb + (own >> 5), 1u << (own & 31));
       }
     }
   }
@@ -465,8 +467,12 @@ cudaError_t launch_full_sweep(int mode, const SweepParams& p, const uint32_t* ro
   }
   int qgrid = (int)std::min<int64_t>(cdiv(nquads, 32 * SW_QPT * 8) + 1, (int64_t)sms * 16);
   note_launch();
-  if (pull) k_gather_rows<true><<<qgrid, 256, 0, s>>>(p.icol, p.Ccur, p.X_cur, rowbits, rowbase, nquads, p.gacc, anyb);
-  else k_gather_rows<false><<<qgrid, 256, 0, s>>>(p.icol, p.Ccur, nullptr, rowbits, rowbase, nquads, p.gacc, anyb);
+  if (pull)
+    k_gather_rows<true><<<qgrid, 256, 0, s>>>(p.icol, p.Ccur, p.X_cur, p.S_cur, rowbits, rowbase, nquads, p.n, p.gacc,
+                                               anyb);
+  else
+    k_gather_rows<false><<<qgrid, 256, 0, s>>>(p.icol, p.Ccur, nullptr, nullptr, rowbits, rowbase, nquads, p.n, p.gacc,
+                                                anyb);
   int rgrid = grid_for(p.n, 256);
   switch (mode) {
     case SWEEP_FULL: note_launch(); k_finish_rows<SWEEP_FULL><<<rgrid, 256, 0, s>>>(p, p.gacc, anyb); break;
