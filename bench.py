@@ -3,7 +3,7 @@
 One step = one batch update of the hot path: pr_apply_batch (in-place edit of
 the CSR and its transpose, effective change) followed by pr_update with DF-P
 (initial marking, frontier sweeps with expansion and pruning, convergence),
-for a random 80/20 batch of 1e-4 |E| edges (Sec. 4.2.2 of the paper) on a
+for a random 80/20 batch of 1e-4 |E| edges (Sec. 5.2.2 of the paper) on a
 synthetic R-MAT graph with 2^25 vertices and 2^30 drawn edges (Table 2
 stand-in).  Batches follow one another on the evolving graph.
 

@@ -7,7 +7,7 @@
  *
  * Conventions for every call:
  *   - Vertex ids are int32 in [0, n); n is fixed when the graph is created
- *     (Sec. 4.2.2: batches add or remove no vertices).
+ *     (Sec. 5.2.2: batches add or remove no vertices).
  *   - "host" pointers are ordinary CPU memory; "device" pointers are CUDA
  *     global memory on the graph's device (for example torch CUDA tensors).
  *     Input arrays stay owned by the caller and are only read during the call.
@@ -26,7 +26,7 @@
  *     nearest multiple of 2^-61), so results do not depend on the order of
  *     additions; the caller's ranks must be finite, non-negative and sum to at
  *     most 2.
- *   - One caller at a time per graph (Sec. 2.2: one writer on the graph at
+ *   - One caller at a time per graph (Sec. 3.2: one writer on the graph at
  *     any given time).  Different graphs may be used from different threads.
  */
 #ifndef DFPR_H
@@ -40,13 +40,13 @@ extern "C" {
 
 typedef struct pr_graph pr_graph;
 
-/* Update methods (Sec. 2.1, Sec. 2.3, Sec. 3.1). */
+/* Update methods (Sec. 3.1, Sec. 3.3, Sec. 4.1). */
 typedef enum {
-  PR_STATIC = 0,            /* power iteration from 1/|V| over all vertices (Sec. 2.1)          */
-  PR_NAIVE_DYNAMIC = 1,     /* all vertices, starting from the current ranks (Sec. 2.3.1)        */
+  PR_STATIC = 0,            /* power iteration from 1/|V| over all vertices (Sec. 3.1)          */
+  PR_NAIVE_DYNAMIC = 1,     /* all vertices, starting from the current ranks (Sec. 3.3.1)        */
   PR_DYNAMIC_TRAVERSAL = 2, /* vertices reachable from updated sources in G_{t-1} or G_t (2.3.2) */
-  PR_DF = 3,                /* Dynamic Frontier (Sec. 3.1.1, Alg. 1)                            */
-  PR_DFP = 4                /* Dynamic Frontier with Pruning (Sec. 3.1.2, Alg. 1, Eq. 2)         */
+  PR_DF = 3,                /* Dynamic Frontier (Sec. 4.1.1, Alg. 1)                            */
+  PR_DFP = 4                /* Dynamic Frontier with Pruning (Sec. 4.1.2, Alg. 1, Eq. 2)         */
 } pr_method;
 
 typedef enum {
@@ -60,7 +60,7 @@ typedef enum {
 } pr_status;
 
 /* Tolerances of Alg. 1; NULL options mean tau_f = tau_p = 1e-6 and 500
- * iterations (Sec. 4.1.2, Sec. 3.2, Sec. 3.3). */
+ * iterations (Sec. 5.1.2, Sec. 4.2, Sec. 4.3). */
 typedef struct {
   double tau_f;       /* frontier tolerance: expand when dr / max(r, R[v]) > tau_f  */
   double tau_p;       /* prune tolerance (DF-P): drop v when dr / max(r, R[v]) <= tau_p */
@@ -78,12 +78,12 @@ typedef struct {
 #define PR_OPT_FORCE_PULL 2
 #define PR_OPT_FORCE_PUSH 4
 
-/* Outcome of one pr_update (Sec. 4.1.5 measures time and affected vertices). */
+/* Outcome of one pr_update (Sec. 5.1.5 measures time and affected vertices). */
 typedef struct {
   int32_t iterations;              /* sweeps run                                            */
   int32_t converged;               /* 1 if the last L-inf change was <= tau                 */
   double delta_R;                  /* L-inf change of the last sweep                        */
-  int64_t vertices_ever_affected;  /* vertices processed by at least one sweep (Sec. 4.2.3) */
+  int64_t vertices_ever_affected;  /* vertices processed by at least one sweep (Sec. 5.2.3) */
   int64_t edges_processed;         /* in-edges summed over all sweeps                       */
   int64_t vertices_processed;      /* vertex updates over all sweeps                        */
   int64_t eff_deletions;           /* |Delta-| of the last batch                            */
@@ -96,10 +96,10 @@ typedef struct {
 } pr_stats;
 
 /*
- * Create a graph from an out-edge CSR in host memory (Sec. 2.1 notation:
+ * Create a graph from an out-edge CSR in host memory (Sec. 3.1 notation:
  * G.out(u) = col[row_off[u] .. row_off[u+1])).  row_off has n+1 entries with
  * row_off[0] = 0 and row_off[n] = m; col has m entries in [0, n).  Repeated
- * edges are collapsed and every vertex gets exactly one self-loop (Sec. 4.1.3:
+ * edges are collapsed and every vertex gets exactly one self-loop (Sec. 5.1.3:
  * self-loops on all vertices remove dead ends).  stream is a cudaStream_t
  * (NULL = the default stream) on the current device.  On success *out owns a
  * new graph without ranks.  Errors: PR_EINVAL (n < 1, m < 0, null pointers,
@@ -127,11 +127,11 @@ void pr_graph_destroy(pr_graph* g);
 pr_status pr_set_stream(pr_graph* g, void* stream);
 
 /*
- * Apply one batch update (Sec. 2.2): E_t = (E_{t-1} \ D) u I, deletions
+ * Apply one batch update (Sec. 3.2): E_t = (E_{t-1} \ D) u I, deletions
  * first.  D = {(del_src[i], del_dst[i])}, I = {(ins_src[i], ins_dst[i])}, all
  * in host memory.  Repeats, deletions of absent edges, insertions of present
  * edges and self-loop deletions have no effect (self-loops are re-added with
- * every batch, Sec. 4.2.2).  The CSR and its transpose are edited in place on
+ * every batch, Sec. 5.2.2).  The CSR and its transpose are edited in place on
  * the device, and the effective change Delta- = E_{t-1} \ E_t, Delta+ =
  * E_t \ E_{t-1} is kept for the next pr_update.  Contributions of sources
  * whose out-degree changed are refreshed.  Errors: PR_EINVAL (null pointer
@@ -146,7 +146,7 @@ pr_status pr_apply_batch_device(pr_graph* g, const int32_t* del_src, const int32
                                 const int32_t* ins_src, const int32_t* ins_dst, int64_t n_ins);
 
 /*
- * Update the ranks with one method (Sec. 2.1, 2.3, Alg. 1) after the last
+ * Update the ranks with one method (Sec. 3.1, 2.3, Alg. 1) after the last
  * batch, iterating until the L-inf change of a sweep is <= tau or
  * opts->max_iter sweeps have run.  alpha in [0, 1) is the damping factor
  * (0.85 in the paper), tau >= 0 the iteration tolerance (1e-10, L-inf).
@@ -194,7 +194,7 @@ pr_status pr_last_delta(const pr_graph* g, int64_t* n_del, int64_t* n_ins, int32
  * to host memory flags[0..n):
  *   which = 0: initial marking of DF / DF-P (Alg. 1): every v' in
  *              (G_{t-1} u G_t).out(u) for (u, v) in Delta- u Delta+;
- *   which = 1: Dynamic Traversal (Sec. 2.3.2): vertices reachable from those
+ *   which = 1: Dynamic Traversal (Sec. 3.3.2): vertices reachable from those
  *              u in G_{t-1}, united with those reachable in G_t.
  */
 pr_status pr_affected(pr_graph* g, int32_t which, uint8_t* flags);

@@ -3,21 +3,21 @@
 TEST INFRASTRUCTURE ONLY: a plain, slow, single-threaded FP64 C
 implementation (``dfpr_oracle.c``) of Static, Naive-dynamic, Dynamic
 Traversal, DF and DF-P PageRank, in the synchronous order, with the batch
-update of Sec. 2.2.  Only the tests, the package smoke check and the
+update of Sec. 3.2.  Only the tests, the package smoke check and the
 benchmark's CPU-baseline leg may import this module.  It shares no code with
 the CUDA library and never imports it.
 
 Every function follows a passage of the paper:
-  * ``Graph``            -- edge set with one self-loop per vertex (Sec. 4.1.3)
-  * ``Graph.apply_batch`` -- E_t = (E_{t-1} \\ D) u I, effective deltas (Sec. 2.2)
-  * ``Graph.update``      -- Static / ND / DT / DF / DF-P (Sec. 2.1, 2.3, Alg. 1)
+  * ``Graph``            -- edge set with one self-loop per vertex (Sec. 5.1.3)
+  * ``Graph.apply_batch`` -- E_t = (E_{t-1} \\ D) u I, effective deltas (Sec. 3.2)
+  * ``Graph.update``      -- Static / ND / DT / DF / DF-P (Sec. 3.1, 2.3, Alg. 1)
   * ``Graph.initial_affected`` -- initial marking of Alg. 1
-  * ``Graph.dt_affected`` -- reachability of Dynamic Traversal (Sec. 2.3.2)
+  * ``Graph.dt_affected`` -- reachability of Dynamic Traversal (Sec. 3.3.2)
   * ``rank_plain`` / ``rank_closed_loop`` -- Eq. 1 and Eq. 2
 
 Parity status: Static / ND / DT ranks are pinned to the linear-system
 solution, to closed forms and to mass conservation; the marking and
-reachability sets to brute force and to the worked example of Sec. 3.1.3.
+reachability sets to brute force and to the worked example of Sec. 4.1.3.
 DF / DF-P ranks on general inputs are pinned only by their invariants and
 by their limits (tau_f = tau_p = 0 gives the linear-system solution):
 parity unpinned beyond those.
@@ -123,7 +123,7 @@ def rank_closed_loop(alpha: float, n: int, c: float, Rv: float, d: int) -> float
 
 
 class Graph:
-    """Edge set over [0, n) with one self-loop per vertex (Sec. 4.1.3)."""
+    """Edge set over [0, n) with one self-loop per vertex (Sec. 5.1.3)."""
 
     def __init__(self, n: int, src, dst):
         lib = _load()
@@ -151,7 +151,7 @@ class Graph:
         return _load().or_num_edges(self._h)
 
     def apply_batch(self, del_src=(), del_dst=(), ins_src=(), ins_dst=()):
-        """Deletions, then insertions, set semantics (Sec. 2.2)."""
+        """Deletions, then insertions, set semantics (Sec. 3.2)."""
         ds, dd, is_, id_ = _i32(del_src), _i32(del_dst), _i32(ins_src), _i32(ins_dst)
         if ds.shape != dd.shape or is_.shape != id_.shape:
             raise ValueError("endpoint arrays differ in length")

@@ -11,32 +11,32 @@
  *
  * Everything is written for readability against the paper, not for speed:
  *   - a graph is the sorted set of its edge keys (src << 32 | dst), with
- *     exactly one self-loop on every vertex (Sec. 4.1.3, Sec. 4.1.4: self-loops
+ *     exactly one self-loop on every vertex (Sec. 5.1.3, Sec. 5.1.4: self-loops
  *     are added to all vertices, so there are no dead ends);
  *   - out- and in-adjacency lists are rebuilt from that set after every batch;
  *   - every method runs in the synchronous (Jacobi) order: all vertices
  *     processed in iteration i read the ranks R_i of the start of the iteration
- *     (Sec. 3.4 runs Alg. 1 asynchronously with one rank vector, which leaves
+ *     (Sec. 4.4 runs Alg. 1 asynchronously with one rank vector, which leaves
  *     the schedule undefined; the synchronous order is one legal interleaving
  *     of its parallel loop and is reproducible).
  *
  * Readings of points where the paper is silent (each is also listed in the
  * design notes):
  *   - set semantics for batches: E_t = (E_{t-1} \ D) u I, deletions first,
- *     duplicate and ineffective entries have no effect (Sec. 2.2 defines the
+ *     duplicate and ineffective entries have no effect (Sec. 3.2 defines the
  *     deletions and insertions as set differences);
  *   - a deletion of a self-loop is ignored: self-loops are re-added with every
- *     batch (Sec. 4.1.4, Sec. 4.2.2);
+ *     batch (Sec. 5.1.4, Sec. 5.2.2);
  *   - the initial marking of Alg. 1 marks (G_{t-1} u G_t).out(u) for every
  *     updated edge (u, v); that set contains u itself through its self-loop;
  *   - Delta r / max(r, R[v]) uses the larger of the new and the old rank
- *     (Sec. 3.2);
+ *     (Sec. 4.2);
  *   - prune when the relative change is <= tau_p, expand when it is > tau_f,
  *     stop when the L-infinity change is <= tau (Alg. 1);
  *   - when a vertex is pruned and also re-marked by an expansion in the same
  *     iteration, the mark wins: F_{i+1} = M_i u (F_i \ P_i);
  *   - Dynamic Traversal marks the union of the vertices reachable from the
- *     updated sources in G_{t-1} and those reachable in G_t (Sec. 2.3.2).
+ *     updated sources in G_{t-1} and those reachable in G_t (Sec. 3.3.2).
  *
  * Build: gcc -O2 -std=c11 -shared -fPIC dfpr_oracle.c -o liboracle.so
  * (no -ffast-math: IEEE round-to-nearest FP64 throughout).
@@ -170,7 +170,7 @@ void or_graph_destroy(or_graph *g) {
 }
 
 /* Graph from a raw edge list (repeats and self-loops allowed): the edge set
- * with exactly one self-loop per vertex (Sec. 4.1.3). */
+ * with exactly one self-loop per vertex (Sec. 5.1.3). */
 int or_graph_create(int32_t n, int64_t m, const int32_t *src, const int32_t *dst, or_graph **out) {
   *out = NULL;
   if (n <= 0 || m < 0) return OR_EINVAL;
@@ -191,7 +191,7 @@ int or_graph_create(int32_t n, int64_t m, const int32_t *src, const int32_t *dst
   return OR_OK;
 }
 
-/* Batch update (Sec. 2.2): E_t = (E_{t-1} \ D) u I with self-loop deletions
+/* Batch update (Sec. 3.2): E_t = (E_{t-1} \ D) u I with self-loop deletions
  * ignored; records the effective Delta- = E_{t-1} \ E_t and Delta+ = E_t \ E_{t-1}.
  * Ids are validated before anything changes. */
 int or_apply_batch(or_graph *g, const int32_t *del_src, const int32_t *del_dst, int64_t n_del,
@@ -273,7 +273,7 @@ void or_initial_affected(const or_graph *g, uint8_t *flag) {
 }
 
 /* Vertices reachable from the sources of the updated edges, in G_{t-1} and
- * in G_t separately, united (Dynamic Traversal, Sec. 2.3.2).  A source reaches
+ * in G_t separately, united (Dynamic Traversal, Sec. 3.3.2).  A source reaches
  * itself. */
 int or_dt_affected(const or_graph *g, uint8_t *flag) {
   int32_t n = g->n;
@@ -340,7 +340,7 @@ double or_rank_closed_loop(double alpha, int32_t n, double c, double Rv, int64_t
 }
 
 /*
- * One method run (Sec. 2.1, Sec. 2.3, Alg. 1), synchronous order.
+ * One method run (Sec. 3.1, Sec. 3.3, Alg. 1), synchronous order.
  * r_prev: ranks of the previous snapshot (ignored by Static, required by the
  * others).  r_out: the updated ranks.  Returns OR_ENORANKS when a dynamic
  * method has no r_prev.

@@ -1,9 +1,9 @@
 // batch.cu -- a batch of edge deletions and insertions applied to the device
-// CSR and transpose-CSR in place (Sec. 2.2).
+// CSR and transpose-CSR in place (Sec. 3.2).
 //
 //   E_t = (E_{t-1} \ D) u I      (deletions first; self-loop deletions are
 //                                 ignored because self-loops are re-added with
-//                                 every batch, Sec. 4.1.4 / 4.2.2)
+//                                 every batch, Sec. 5.1.4 / 4.2.2)
 //   Delta- = E_{t-1} \ E_t,  Delta+ = E_t \ E_{t-1}   (the effective change)
 //
 // Steps: packed keys -> radix sort -> first occurrences -> effective flags by

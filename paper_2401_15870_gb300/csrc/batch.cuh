@@ -1,4 +1,4 @@
-// batch.cuh -- in-place batch edit of the device graph (Sec. 2.2).
+// batch.cuh -- in-place batch edit of the device graph (Sec. 3.2).
 #pragma once
 #include "graph.cuh"
 

@@ -1,4 +1,4 @@
-// frontier.cu -- initial marking (Alg. 1), reachability helpers (Sec. 2.3.2),
+// frontier.cu -- initial marking (Alg. 1), reachability helpers (Sec. 3.3.2),
 // per-iteration bookkeeping, contribution refresh.
 #include "frontier.cuh"
 #include "prim.cuh"

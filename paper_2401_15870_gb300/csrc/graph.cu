@@ -1,6 +1,6 @@
 // graph.cu -- building the device CSR + transpose-CSR from an edge list.
 //
-// Graph construction (Sec. 4.1.3: a self-loop on every vertex, the edge set
+// Graph construction (Sec. 5.1.3: a self-loop on every vertex, the edge set
 // with repeats collapsed) runs on the device: radix sort of packed edge keys,
 // first-occurrence compaction, then one CSR per direction with rows rounded to
 // whole 16-byte quads plus slack quads for later in-place batch edits.

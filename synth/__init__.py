@@ -9,12 +9,12 @@ in ``synth.c``, so for equal arguments they produce equal arrays.
 
 Stand-ins (the paper's datasets are not available):
   * ``rmat``      -- R-MAT power-law graphs for the SuiteSparse graphs of Table 2
-                     (random batches, Sec. 4.2.2);
+                     (random batches, Sec. 5.2.2);
   * ``batch``     -- 80 % uniform-pair insertions, 20 % deletions of existing
-                     edges (Sec. 4.2.2);
+                     edges (Sec. 5.2.2);
   * ``temporal``  -- timestamped edge stream with repeats and heavy-tailed
                      degrees for the SNAP temporal graphs of Table 1
-                     (Sec. 4.1.4).
+                     (Sec. 5.1.4).
 """
 from __future__ import annotations
 

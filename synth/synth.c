@@ -16,7 +16,7 @@
  *                bijection of [0, 2^scale) so hubs do not cluster at id 0.
  *                Repeats and self-loops are left in; graph builders collapse
  *                them (set semantics) and add one self-loop per vertex.
- *   sy_batch     80/20-style random batch (Sec. 4.2.2 of the paper): uniform
+ *   sy_batch     80/20-style random batch (Sec. 5.2.2 of the paper): uniform
  *                vertex-pair insertions (u != v), deletions drawn uniformly
  *                from a caller-given candidate edge list.
  *   sy_temporal  a temporal edge stream with repeats and a heavy-tailed

@@ -3,7 +3,7 @@
 Each test checks the oracle against something other than itself: the linear
 system whose solution is the PageRank fixed point (numpy's LAPACK solver),
 closed forms, conservation laws, the appendix's geometric series, brute-force
-reachability and set arithmetic, and the worked example of Sec. 3.1.3.
+reachability and set arithmetic, and the worked example of Sec. 4.1.3.
 """
 import os
 
@@ -266,8 +266,8 @@ def load_worked_example():
     return edges, meta
 
 
-def test_worked_example_sec_3_1_3():
-    """The 16-vertex example of Sec. 3.1.3.  The oracle adds self-loops, so the
+def test_worked_example_sec_4_1_3():
+    """The 16-vertex example of Sec. 4.1.3.  The oracle adds self-loops, so the
     initial marking also contains the two sources 2 and 4 (their self-loops are
     out-edges); the narrated set is the marking without them."""
     edges, meta = load_worked_example()
@@ -323,13 +323,13 @@ def test_dynamic_methods_require_previous_ranks():
 
 
 def test_error_ordering_soft_claim():
-    """Sec. 4.2.1: DF error lies below Static's at the same tau and ND's below
-    DF's (errors are L1 against a tightly converged static solve, Sec. 4.1.5).
+    """Sec. 5.2.1: DF error lies below Static's at the same tau and ND's below
+    DF's (errors are L1 against a tightly converged static solve, Sec. 5.1.5).
     DF-P's error is governed by its relative prune tolerance: it stays within a
     small multiple of tau_p / (1 - alpha).  The paper's DF-P-below-Static
     ordering needs graphs large enough that tau = 1e-10 (absolute) is loose
     relative to the ranks; at this size it is not asserted (the paper itself
-    reports DF-P above Static on web graphs, Sec. 4.2.2)."""
+    reports DF-P above Static on web graphs, Sec. 5.2.2)."""
     n = 1 << 11
     src, dst = synth.rmat(11, 1 << 15, 41)
     g = oracle.Graph(n, src, dst)
