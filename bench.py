@@ -257,7 +257,8 @@ def run_gpu(a, rank, world, local_rank):
         "config": {"workload": workload_name(a), "vertices": n, "edges": m0, "batch_edges": size,
                    "inputs": "larger than L2 (graph ~%.0f GB resident)" % (m0 * 8 * 1.2 / 1e9),
                    "parallelism": "replicas" if world > 1 else "single GPU"},
-        "roofline": {"bound": "hbm", "kernel": "k_sweep<DFP>", "achieved": achieved, "peak": peak,
+        "roofline": {"bound": "hbm", "kernel": "DF-P rank sweep (k_gather_rows + k_finish_rows in pull form, "
+                               "k_sweep<DFP> in push form)", "achieved": achieved, "peak": peak,
                      "unit": "GB/s", "frac": achieved / peak, "traffic": None,
                      "peak_source": peak_src + " (MEASURED_PEAKS.json hbm_gbs)" if peak_src == "measured" else
                      "fallback 6800 GB/s"},

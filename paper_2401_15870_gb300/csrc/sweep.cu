@@ -441,12 +441,13 @@ __global__ void __launch_bounds__(256) k_gather_rows(const int32_t* __restrict__
 }
 
 template <int MODE>
-__global__ void __launch_bounds__(256) k_finish_rows(SweepParams p, long long* __restrict__ acc,
-                                                     const uint32_t* __restrict__ anyb) {
+__global__ void __launch_bounds__(256, 6) k_finish_rows(SweepParams p, long long* __restrict__ acc,
+                                                        const uint32_t* __restrict__ anyb) {
   constexpr bool pull = MODE == SWEEP_PULL_DF || MODE == SWEEP_PULL_DFP;
   double dmax = 0.0;
   long long edges = 0, verts = 0;
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+#pragma unroll 2
   for (int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; v < p.n; v += stride) {
     const long long sum = acc[v];
     acc[v] = 0;
