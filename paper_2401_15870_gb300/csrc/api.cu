@@ -446,8 +446,7 @@ static pr_status run_update(pr_graph* h, int method, double alpha, double tau, d
         TRY(cudaMemsetAsync(xb[cur], 0, wbytes, s));
       }
       if (pull) {
-        TRY(cudaMemsetAsync(g->bits[1 - cur], 0, wbytes, s));
-        TRY(cudaMemsetAsync(xb[1 - cur], 0, wbytes, s));
+        // the pull epilogue writes every word of S_next and X_next
         p.list = nullptr;
         p.tfirst = g->full_tfirst;
         p.ntiles_host = g->full_ntiles;
