@@ -440,88 +440,119 @@ __global__ void __launch_bounds__(256) k_gather_rows(const int32_t* __restrict__
   }
 }
 
-template <int MODE>
-__global__ void __launch_bounds__(256, 6) k_finish_rows(SweepParams p, long long* __restrict__ acc,
-                                                        const uint32_t* __restrict__ anyb) {
-  constexpr bool pull = MODE == SWEEP_PULL_DF || MODE == SWEEP_PULL_DFP;
-  double dmax = 0.0;
-  long long edges = 0, verts = 0;
-  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-#pragma unroll 2
-  for (int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; v < p.n; v += stride) {
-    const long long sum = acc[v];
-    acc[v] = 0;
-    const bool any = pull && ((__ldg(anyb + (v >> 5)) >> (v & 31)) & 1u);
-    finalize<MODE>(p, (int32_t)v, (int32_t)v, sum, any, dmax, edges, verts);
-  }
-  block_flush_stats(dmax, edges, verts, p.ctl);
-}
-
 // Pull-form epilogue: one warp per 32 consecutive vertices (one 32-bit word of
 // every bitset), so the next frontier's stay / expanded words are built with
 // ballots and written whole, with no atomics and no clearing beforehand.
 // Vertices outside F_i keep their rank and copy their contribution.
 template <bool CLOSED>
-__global__ void __launch_bounds__(256, 6) k_finish_pull(SweepParams p, long long* __restrict__ acc,
+__global__ void __launch_bounds__(256, 4) k_finish_pull(SweepParams p, long long* __restrict__ acc,
                                                         const uint32_t* __restrict__ anyb) {
+  constexpr int U = 4;   // chunks per warp step: their loads are issued together
   const int lane = threadIdx.x & 31;
   const int64_t nchunks = cdiv(p.n, 32);
   const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
   double dmax = 0.0;
   long long edges = 0, verts = 0;
   int stays = 0, exps = 0;
-  for (int64_t ch = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5; ch < nchunks; ch += nw) {
-    const int64_t v = ch * 32 + lane;
-    const bool valid = v < p.n;
-    long long sum = 0;
-    if (valid) {
-      sum = acc[v];
-      acc[v] = 0;
+  for (int64_t ch0 = ((blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5) * U; ch0 < nchunks; ch0 += nw * U) {
+    long long sum[U], cself[U];
+    double Rv[U];
+    int32_t d[U];
+    bool member[U], valid[U];
+#pragma unroll
+    for (int u = 0; u < U; u++) {
+      const int64_t ch = ch0 + u;
+      const int64_t v = ch * 32 + lane;
+      valid[u] = ch < nchunks && v < p.n;
+      const uint32_t in_f = ch < nchunks ? (__ldg(anyb + ch) | __ldg(p.S_cur + ch)) : 0u;
+      member[u] = valid[u] && ((in_f >> lane) & 1u);
+      sum[u] = valid[u] ? acc[v] : 0;
+      cself[u] = valid[u] ? p.Ccur[v] : 0;
+      Rv[u] = member[u] ? p.R[v] : 0.0;
+      d[u] = member[u] ? p.odeg[v] : 1;
     }
-    const uint32_t in_f = __ldg(anyb + ch) | __ldg(p.S_cur + ch);
-    const bool member = valid && ((in_f >> lane) & 1u);
-    bool stay = false, expand = false;
-    if (member) {
-      const double Rv = p.R[v];
-      const int32_t d = p.odeg[v];
-      double r;
-      if (CLOSED) {
-        // Eq. 2, the self term removed exactly in fixed point
-        const long long K = sum - p.Ccur[v];
-        const double f = d < TAB ? p.tab_cl[d] : 1.0 / (1.0 - p.alpha / (double)d);
-        r = f * (p.C0 + p.alpha * ((double)K * FIX_INV));
-      } else {
-        r = p.C0 + p.alpha * ((double)sum * FIX_INV);   // Eq. 1
+#pragma unroll
+    for (int u = 0; u < U; u++) {
+      const int64_t ch = ch0 + u;
+      const int64_t v = ch * 32 + lane;
+      bool stay = false, expand = false;
+      if (valid[u]) acc[v] = 0;
+      if (member[u]) {
+        double r;
+        if (CLOSED) {
+          // Eq. 2, the self term removed exactly in fixed point
+          const long long K = sum[u] - cself[u];
+          const double f = d[u] < TAB ? p.tab_cl[d[u]] : 1.0 / (1.0 - p.alpha / (double)d[u]);
+          r = f * (p.C0 + p.alpha * ((double)K * FIX_INV));
+        } else {
+          r = p.C0 + p.alpha * ((double)sum[u] * FIX_INV);   // Eq. 1
+        }
+        const double dr = fabs(r - Rv[u]);
+        dmax = fmax(dmax, dr);
+        edges += p.ideg[v];
+        verts += 1;
+        p.R[v] = r;
+        const double sc = d[u] < TAB ? p.tab_sc[d[u]] : FIX_ONE / (double)d[u];
+        p.Cnext[v] = __double2ll_rn(r * sc);
+        // Alg. 1: prune when dr / max(r, R[v]) <= tau_p (DF-P), expand when it
+        // is > tau_f; compared without the division, in FP64
+        const double mr = fmax(r, Rv[u]);
+        stay = !CLOSED || !(dr <= p.tau_p * mr);
+        expand = dr > p.tau_f * mr;
+      } else if (valid[u]) {
+        p.Cnext[v] = cself[u];
       }
-      const double dr = fabs(r - Rv);
-      dmax = fmax(dmax, dr);
-      edges += p.ideg[v];
-      verts += 1;
-      p.R[v] = r;
-      const double sc = d < TAB ? p.tab_sc[d] : FIX_ONE / (double)d;
-      p.Cnext[v] = __double2ll_rn(r * sc);
-      // Alg. 1: prune when dr / max(r, R[v]) <= tau_p (DF-P), expand when it is
-      // > tau_f; compared without the division, in FP64
-      const double mr = fmax(r, Rv);
-      stay = !CLOSED || !(dr <= p.tau_p * mr);
-      expand = dr > p.tau_f * mr;
-    } else if (valid) {
-      p.Cnext[v] = p.Ccur[v];
-    }
-    const unsigned ms = __ballot_sync(0xffffffffu, stay);
-    const unsigned mx = __ballot_sync(0xffffffffu, expand);
-    const unsigned mm = __ballot_sync(0xffffffffu, member);
-    if (lane == 0) {
-      p.S_next[ch] = ms;
-      p.X_next[ch] = mx;
-      if (mm) p.ever[ch] |= mm;
-      stays += __popc(ms);
-      exps += __popc(mx);
+      const unsigned ms = __ballot_sync(0xffffffffu, stay);
+      const unsigned mx = __ballot_sync(0xffffffffu, expand);
+      const unsigned mm = __ballot_sync(0xffffffffu, member[u]);
+      if (lane == 0 && ch < nchunks) {
+        p.S_next[ch] = ms;
+        p.X_next[ch] = mx;
+        if (mm) p.ever[ch] |= mm;
+        stays += __popc(ms);
+        exps += __popc(mx);
+      }
     }
   }
   if (lane == 0) {
     if (stays) atomicAdd(p.cnt_next, stays);
     if (exps) atomicAdd(p.cnt_x, exps);
+  }
+  block_flush_stats(dmax, edges, verts, p.ctl);
+}
+
+// Epilogue of a sweep over every vertex with Eq. 1 (Static, ND): all vertices
+// are processed; loads of U vertices per lane are issued together.
+__global__ void __launch_bounds__(256, 4) k_finish_full(SweepParams p, long long* __restrict__ acc) {
+  constexpr int U = 4;
+  double dmax = 0.0;
+  long long edges = 0, verts = 0;
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t v0 = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; v0 < p.n; v0 += stride * U) {
+    long long sum[U];
+    double Rv[U];
+    int32_t d[U];
+#pragma unroll
+    for (int u = 0; u < U; u++) {
+      const int64_t v = v0 + u * stride;
+      const bool ok = v < p.n;
+      sum[u] = ok ? acc[v] : 0;
+      Rv[u] = ok ? p.R[v] : 0.0;
+      d[u] = ok ? p.odeg[v] : 1;
+    }
+#pragma unroll
+    for (int u = 0; u < U; u++) {
+      const int64_t v = v0 + u * stride;
+      if (v >= p.n) continue;
+      acc[v] = 0;
+      const double r = p.C0 + p.alpha * ((double)sum[u] * FIX_INV);   // Eq. 1
+      dmax = fmax(dmax, fabs(r - Rv[u]));
+      edges += p.ideg[v];
+      verts += 1;
+      p.R[v] = r;
+      const double sc = d[u] < TAB ? p.tab_sc[d[u]] : FIX_ONE / (double)d[u];
+      p.Cnext[v] = __double2ll_rn(r * sc);
+    }
   }
   block_flush_stats(dmax, edges, verts, p.ctl);
 }
@@ -545,7 +576,7 @@ cudaError_t launch_full_sweep(int mode, const SweepParams& p, const uint32_t* ro
                                                 anyb);
   int rgrid = grid_for(p.n, 256);
   switch (mode) {
-    case SWEEP_FULL: note_launch(); k_finish_rows<SWEEP_FULL><<<rgrid, 256, 0, s>>>(p, p.gacc, anyb); break;
+    case SWEEP_FULL: note_launch(); k_finish_full<<<rgrid, 256, 0, s>>>(p, p.gacc); break;
     case SWEEP_PULL_DF: note_launch(); k_finish_pull<false><<<rgrid, 256, 0, s>>>(p, p.gacc, anyb); break;
     case SWEEP_PULL_DFP: note_launch(); k_finish_pull<true><<<rgrid, 256, 0, s>>>(p, p.gacc, anyb); break;
     default: return cudaErrorInvalidValue;
