@@ -444,6 +444,13 @@ __global__ void __launch_bounds__(256) k_gather_rows(const int32_t* __restrict__
 // every bitset), so the next frontier's stay / expanded words are built with
 // ballots and written whole, with no atomics and no clearing beforehand.
 // Vertices outside F_i keep their rank and copy their contribution.
+// FP64 is the binding pipe of the epilogues on GB300 (about 0.6 Tops/s), so
+// they spend it only where the formulas need it: the 2^-61 scale is folded
+// into alpha (a power of two, so the product is exact), and maxima and the
+// threshold tests of non-negative doubles compare their bit patterns as
+// integers, which orders them the same way.
+__device__ __forceinline__ unsigned long long dbits(double x) { return (unsigned long long)__double_as_longlong(x); }
+
 template <bool CLOSED>
 __global__ void __launch_bounds__(256, 4) k_finish_pull(SweepParams p, long long* __restrict__ acc,
                                                         const uint32_t* __restrict__ anyb) {
@@ -451,7 +458,9 @@ __global__ void __launch_bounds__(256, 4) k_finish_pull(SweepParams p, long long
   const int lane = threadIdx.x & 31;
   const int64_t nchunks = cdiv(p.n, 32);
   const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
-  double dmax = 0.0;
+  const double alpha_fix = p.alpha * FIX_INV;
+  const bool same_tau = p.tau_f == p.tau_p;
+  unsigned long long dmax = 0ull;
   long long edges = 0, verts = 0;
   int stays = 0, exps = 0;
   for (int64_t ch0 = ((blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5) * U; ch0 < nchunks; ch0 += nw * U) {
@@ -483,22 +492,24 @@ __global__ void __launch_bounds__(256, 4) k_finish_pull(SweepParams p, long long
           // Eq. 2, the self term removed exactly in fixed point
           const long long K = sum[u] - cself[u];
           const double f = d[u] < TAB ? p.tab_cl[d[u]] : 1.0 / (1.0 - p.alpha / (double)d[u]);
-          r = f * (p.C0 + p.alpha * ((double)K * FIX_INV));
+          r = f * fma(alpha_fix, (double)K, p.C0);
         } else {
-          r = p.C0 + p.alpha * ((double)sum[u] * FIX_INV);   // Eq. 1
+          r = fma(alpha_fix, (double)sum[u], p.C0);   // Eq. 1
         }
-        const double dr = fabs(r - Rv[u]);
-        dmax = fmax(dmax, dr);
+        const unsigned long long drb = dbits(fabs(r - Rv[u]));
+        dmax = drb > dmax ? drb : dmax;
         edges += p.ideg[v];
         verts += 1;
         p.R[v] = r;
         const double sc = d[u] < TAB ? p.tab_sc[d[u]] : FIX_ONE / (double)d[u];
         p.Cnext[v] = __double2ll_rn(r * sc);
         // Alg. 1: prune when dr / max(r, R[v]) <= tau_p (DF-P), expand when it
-        // is > tau_f; compared without the division, in FP64
-        const double mr = fmax(r, Rv[u]);
-        stay = !CLOSED || !(dr <= p.tau_p * mr);
-        expand = dr > p.tau_f * mr;
+        // is > tau_f; compared without the division
+        const double mr = dbits(r) > dbits(Rv[u]) ? r : Rv[u];
+        const unsigned long long tf = dbits(p.tau_f * mr);
+        const unsigned long long tp = same_tau ? tf : dbits(p.tau_p * mr);
+        stay = !CLOSED || drb > tp;
+        expand = drb > tf;
       } else if (valid[u]) {
         p.Cnext[v] = cself[u];
       }
@@ -518,14 +529,15 @@ __global__ void __launch_bounds__(256, 4) k_finish_pull(SweepParams p, long long
     if (stays) atomicAdd(p.cnt_next, stays);
     if (exps) atomicAdd(p.cnt_x, exps);
   }
-  block_flush_stats(dmax, edges, verts, p.ctl);
+  block_flush_stats(__longlong_as_double((long long)dmax), edges, verts, p.ctl);
 }
 
 // Epilogue of a sweep over every vertex with Eq. 1 (Static, ND): all vertices
 // are processed; loads of U vertices per lane are issued together.
 __global__ void __launch_bounds__(256, 4) k_finish_full(SweepParams p, long long* __restrict__ acc) {
   constexpr int U = 4;
-  double dmax = 0.0;
+  const double alpha_fix = p.alpha * FIX_INV;
+  unsigned long long dmax = 0ull;
   long long edges = 0, verts = 0;
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
   for (int64_t v0 = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; v0 < p.n; v0 += stride * U) {
@@ -545,8 +557,9 @@ __global__ void __launch_bounds__(256, 4) k_finish_full(SweepParams p, long long
       const int64_t v = v0 + u * stride;
       if (v >= p.n) continue;
       acc[v] = 0;
-      const double r = p.C0 + p.alpha * ((double)sum[u] * FIX_INV);   // Eq. 1
-      dmax = fmax(dmax, fabs(r - Rv[u]));
+      const double r = fma(alpha_fix, (double)sum[u], p.C0);   // Eq. 1
+      const unsigned long long drb = dbits(fabs(r - Rv[u]));
+      dmax = drb > dmax ? drb : dmax;
       edges += p.ideg[v];
       verts += 1;
       p.R[v] = r;
@@ -554,7 +567,7 @@ __global__ void __launch_bounds__(256, 4) k_finish_full(SweepParams p, long long
       p.Cnext[v] = __double2ll_rn(r * sc);
     }
   }
-  block_flush_stats(dmax, edges, verts, p.ctl);
+  block_flush_stats(__longlong_as_double((long long)dmax), edges, verts, p.ctl);
 }
 
 cudaError_t launch_full_sweep(int mode, const SweepParams& p, const uint32_t* rowbits, const int32_t* rowbase,
