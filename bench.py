@@ -36,6 +36,9 @@ ALPHA, TAU = 0.85, 1e-10
 SWEEP_BYTES_PER_EDGE = 12
 SWEEP_BYTES_PER_VERTEX = 60
 SAMPLE_SCALE = 18
+# DRAM bytes (read + write) of one pull-form DF-P sweep (k_gather_rows + k_finish_pull) on the
+# default workload, from the one-pass ncu capture in profiles/k_gather_rows_k_finish_pull_rmat24_rmat25.md
+SWEEP_DRAM_BYTES_RMAT25 = 11.42e9
 
 
 def parse():
@@ -259,7 +262,8 @@ def run_gpu(a, rank, world, local_rank):
                    "parallelism": "replicas" if world > 1 else "single GPU"},
         "roofline": {"bound": "hbm", "kernel": "DF-P rank sweep (k_gather_rows + k_finish_rows in pull form, "
                                "k_sweep<DFP> in push form)", "achieved": achieved, "peak": peak,
-                     "unit": "GB/s", "frac": achieved / peak, "traffic": None,
+                     "unit": "GB/s", "frac": achieved / peak,
+                     "traffic": SWEEP_DRAM_BYTES_RMAT25 if (a.scale, a.edge_factor, a.batch_frac) == (25, 32, 1e-4) else None,
                      "peak_source": peak_src + " (MEASURED_PEAKS.json hbm_gbs)" if peak_src == "measured" else
                      "fallback 6800 GB/s"},
         "e2e": {"value": (a.e2e_steps / (e2e_ms / 1000.0) * world) if e2e_ms else None, "unit": "updates/s",
