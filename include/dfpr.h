@@ -184,6 +184,16 @@ pr_status pr_graph_info(const pr_graph* g, int32_t* n, int64_t* m);
  */
 pr_status pr_get_csr(const pr_graph* g, int32_t which, int64_t* off, int32_t* adj);
 
+/*
+ * Rows of selected vertices (host memory, caller's ids): which = 0 for
+ * out-neighbours, 1 for in-neighbours.  off[0..count] receives the row offsets
+ * (off[k+1] - off[k] is the degree of vertices[k]); if adj is not NULL it
+ * receives the rows, each sorted ascending (size it from a first call with
+ * adj = NULL).  Errors: PR_EINVAL, PR_ERANGE (a vertex outside [0, n)).
+ */
+pr_status pr_get_rows(const pr_graph* g, int32_t which, int64_t count, const int32_t* vertices, int64_t* off,
+                      int32_t* adj);
+
 /* Effective change of the last batch: sizes, then the edges (caller's ids,
  * each array sorted by (src, dst)).  Any output pointer may be NULL. */
 pr_status pr_last_delta(const pr_graph* g, int64_t* n_del, int64_t* n_ins, int32_t* del_src, int32_t* del_dst,

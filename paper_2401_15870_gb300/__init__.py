@@ -87,6 +87,7 @@ def load():
         "pr_set_ranks_device": ([_P, _P], ctypes.c_int),
         "pr_graph_info": ([_P, ctypes.POINTER(i32), ctypes.POINTER(i64)], ctypes.c_int),
         "pr_get_csr": ([_P, i32, _P, _P], ctypes.c_int),
+        "pr_get_rows": ([_P, i32, i64, _P, _P, _P], ctypes.c_int),
         "pr_last_delta": ([_P, ctypes.POINTER(i64), ctypes.POINTER(i64), _P, _P, _P, _P], ctypes.c_int),
         "pr_affected": ([_P, i32, _P], ctypes.c_int),
         "pr_last_error": ([_P], ctypes.c_char_p),
@@ -259,6 +260,21 @@ def pr_get_csr(h, which=0):
     return off, adj[: off[-1]]
 
 
+def pr_get_rows(h, which, vertices, degrees_only=False):
+    """Rows of the given vertices (which 0: out, 1: in): (off, adj) with
+    adj[off[k]:off[k+1]] the sorted neighbours of vertices[k]; with
+    degrees_only, just off."""
+    v, vp = _host_i32(vertices)
+    off = np.empty(v.size + 1, np.int64)
+    lib = load()
+    _check(lib.pr_get_rows(h, int(which), v.size, vp, off.ctypes.data, None), h)
+    if degrees_only:
+        return off
+    adj = np.empty(max(int(off[-1]), 1), np.int32)
+    _check(lib.pr_get_rows(h, int(which), v.size, vp, off.ctypes.data, adj.ctypes.data), h)
+    return off, adj[: off[-1]]
+
+
 def pr_last_delta(h):
     nd, ni = ctypes.c_int64(), ctypes.c_int64()
     lib = load()
@@ -356,6 +372,9 @@ class Graph:
 
     def set_ranks_device(self, r):
         pr_set_ranks_device(self._h, r)
+
+    def rows(self, which, vertices, degrees_only=False):
+        return pr_get_rows(self._h, which, vertices, degrees_only)
 
     def out_csr(self):
         return pr_get_csr(self._h, 0)

@@ -49,6 +49,16 @@ struct pr_graph {
     if (_r != OK) return (pr_status)_r; \
   } while (0)
 
+// temporary device buffer of an export call, freed on every return path
+template <typename T>
+struct DevBuf {
+  T* p = nullptr;
+  cudaError_t alloc(int64_t count) { return cudaMalloc((void**)&p, sizeof(T) * (size_t)(count > 0 ? count : 1)); }
+  ~DevBuf() {
+    if (p) cudaFree(p);
+  }
+};
+
 static int bits_for(int32_t n) {
   int b = 1;
   while ((1ll << b) < (int64_t)n) b++;
@@ -87,6 +97,29 @@ __global__ void k_validate_ids(const int32_t* __restrict__ a, int64_t m, int32_t
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < m; i += (int64_t)gridDim.x * blockDim.x)
     c += (a[i] < 0 || a[i] >= n) ? 1 : 0;
   if (c) atomicAdd(bad, c);
+}
+
+// pr_get_rows: degree and row start of each requested vertex (caller's ids)
+__global__ void k_row_meta(const int32_t* __restrict__ v, int64_t count, const int32_t* __restrict__ perm,
+                           const int64_t* __restrict__ off, const int32_t* __restrict__ deg, int32_t* __restrict__ d_out,
+                           int64_t* __restrict__ base_out) {
+  for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < count; k += (int64_t)gridDim.x * blockDim.x) {
+    int32_t r = perm[v[k]];
+    d_out[k] = deg[r];
+    base_out[k] = off[r];
+  }
+}
+
+// pr_get_rows: one warp per requested row, neighbours mapped back to caller's ids
+__global__ void k_row_copy_out(int64_t count, const int64_t* __restrict__ base, const int64_t* __restrict__ off,
+                               const int32_t* __restrict__ col, const int32_t* __restrict__ iperm,
+                               int32_t* __restrict__ adj) {
+  int lane = threadIdx.x & 31;
+  int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  for (int64_t k = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5; k < count; k += nw) {
+    int64_t d = off[k + 1] - off[k];
+    for (int64_t x = lane; x < d; x += 32) adj[off[k] + x] = iperm[col[base[k] + x]];
+  }
 }
 
 __global__ void k_check_ranks(const double* __restrict__ r, int32_t n, unsigned long long* bad, double* sum) {
@@ -850,6 +883,48 @@ pr_status pr_get_csr(const pr_graph* hc, int32_t which, int64_t* off, int32_t* a
     std::sort(adj + start, adj + w);
   }
   off[n] = w;
+  return PR_OK;
+}
+
+pr_status pr_get_rows(const pr_graph* hc, int32_t which, int64_t count, const int32_t* vertices, int64_t* off,
+                      int32_t* adj) {
+  pr_graph* h = const_cast<pr_graph*>(hc);
+  if (!h || count < 0 || (count > 0 && !vertices) || !off || (which != 0 && which != 1)) return PR_EINVAL;
+  Graph* g = &h->g;
+  const Csr& c = which == 0 ? g->out : g->in;
+  int32_t n = g->n;
+  for (int64_t k = 0; k < count; k++)
+    if (vertices[k] < 0 || vertices[k] >= n) return (pr_status)set_error(g, ERANGE_, "pr_get_rows: vertex id out of range");
+  off[0] = 0;
+  if (count == 0) return PR_OK;
+  cudaStream_t s = g->stream;
+  // device side: map the ids, gather degree and row start of every vertex
+  DevBuf<int32_t> dv, ddeg;
+  DevBuf<int64_t> dbase;
+  TRY(dv.alloc(count));
+  TRY(ddeg.alloc(count));
+  TRY(dbase.alloc(count));
+  TRY(cudaMemcpyAsync(dv.p, vertices, sizeof(int32_t) * count, cudaMemcpyHostToDevice, s));
+  int grid = grid_for(count, 256);
+  note_launch();
+  k_row_meta<<<grid, 256, 0, s>>>(dv.p, count, g->perm, c.off, c.deg, ddeg.p, dbase.p);
+  TRY(cudaGetLastError());
+  std::vector<int32_t> deg(count);
+  TRY(cudaMemcpyAsync(deg.data(), ddeg.p, sizeof(int32_t) * count, cudaMemcpyDeviceToHost, s));
+  TRY(cudaStreamSynchronize(s));
+  for (int64_t k = 0; k < count; k++) off[k + 1] = off[k] + deg[k];
+  if (!adj || off[count] == 0) return PR_OK;
+  DevBuf<int64_t> doff;
+  DevBuf<int32_t> dadj;
+  TRY(doff.alloc(count + 1));
+  TRY(dadj.alloc(off[count]));
+  TRY(cudaMemcpyAsync(doff.p, off, sizeof(int64_t) * (count + 1), cudaMemcpyHostToDevice, s));
+  note_launch();
+  k_row_copy_out<<<grid_for(count * 32, 256), 256, 0, s>>>(count, dbase.p, doff.p, c.col, g->iperm, dadj.p);
+  TRY(cudaGetLastError());
+  TRY(cudaMemcpyAsync(adj, dadj.p, sizeof(int32_t) * off[count], cudaMemcpyDeviceToHost, s));
+  TRY(cudaStreamSynchronize(s));
+  for (int64_t k = 0; k < count; k++) std::sort(adj + off[k], adj + off[k + 1]);
   return PR_OK;
 }
 

@@ -206,14 +206,14 @@ __device__ __forceinline__ void finalize(const SweepParams& p, int32_t k, int32_
     // Eq. 2: K = sum over in-neighbours minus the vertex's own self-loop term,
     // r = (C0 + alpha K) / (1 - alpha/d); the self term is removed exactly in
     // fixed point
+    // (one rounding for C0 + alpha K, as in the every-vertex epilogues, so
+    // that push and pull forms give bit-identical ranks)
     long long K = sum - p.Ccur[v];
-    double Kd = (double)K * FIX_INV;
     double f = d < TAB ? p.tab_cl[d] : 1.0 / (1.0 - p.alpha / (double)d);
-    r = f * (p.C0 + p.alpha * Kd);
+    r = f * fma(p.alpha * FIX_INV, (double)K, p.C0);
   } else {
     // Eq. 1: r = C0 + alpha c
-    double c = (double)sum * FIX_INV;
-    r = p.C0 + p.alpha * c;
+    r = fma(p.alpha * FIX_INV, (double)sum, p.C0);
   }
   double dr = fabs(r - Rv);
   if (member) {

@@ -210,6 +210,24 @@ def test_frontier_directions_agree_with_oracle(lib, method, direction, scale, bs
     assert st.vertices_ever_affected == pytest.approx(ost.vertices_ever_affected, rel=0.01)
 
 
+@pytest.mark.parametrize("method", ["df", "dfp"])
+@pytest.mark.parametrize("scale,bsize", [(12, 40), (14, 262), (13, 3000)])
+def test_frontier_directions_agree_bitwise(lib, method, scale, bsize):
+    """Both sweep forms sum the same fixed-point contributions exactly and
+    evaluate Eq. 1 / Eq. 2 with the same roundings, so the direction taken in
+    each iteration changes neither the ranks nor the frontier: pull, push and
+    the automatic choice give bit-identical ranks and statistics."""
+    G, O, r0 = rank_case(lib, scale, 16, bsize, 50 + scale)
+    out = []
+    for direction in ("pull", "push", None):
+        G.set_ranks(r0)
+        st = G.update(method, direction=direction)
+        out.append((G.ranks(), st.iterations, st.vertices_ever_affected, st.vertices_processed))
+    for r, it, ev, vp in out[1:]:
+        assert np.array_equal(r, out[0][0])
+        assert (it, ev, vp) == out[0][1:]
+
+
 def test_successive_batches_and_methods_from_same_ranks(lib):
     n = 1 << 12
     src, dst = synth.rmat(12, 16 * n, 77)
