@@ -235,6 +235,37 @@ pr_status pr_affected(pr_graph* g, int32_t which, uint8_t* flags);
 pr_status pr_sweep_noalloc(int32_t n, const int64_t* in_off, const int32_t* in_src, const int32_t* out_deg,
                            const double* r_in, double* r_out, double alpha, double* delta_out, void* stream);
 
+/*
+ * Groups: one update of many graphs at once.  The paper updates one graph at
+ * a time; a group serves callers that hold many independent graphs (for
+ * example one per tenant or per time window) and would otherwise run one
+ * launch sequence per graph.  Every iteration sweeps all graphs of the group
+ * that have not converged in one launch pair (gather, then the epilogue of
+ * Alg. 1 / Eq. 1-2), and the loop over iterations runs on the device (a CUDA
+ * graph with a WHILE node), so each graph stops on its own criterion with no
+ * host round trip.  A graph's ranks and statistics are bit-identical to those
+ * of pr_update on the graph alone.
+ *
+ * pr_group_create: count in [1, PR_GROUP_MAX] distinct graphs (host array of
+ *   handles, read during the call), all on the current device.  The group
+ *   refers to the graphs and owns none of them: destroy the group before any
+ *   of its graphs.  stream: the CUDA stream of the group's work (NULL: the
+ *   legacy default stream).  Errors: PR_EINVAL, PR_ENOMEM, PR_ECUDA.
+ * pr_group_update: method PR_STATIC, PR_NAIVE_DYNAMIC, PR_DF or PR_DFP (Dynamic
+ *   Traversal is not offered), alpha / tau / opts as in pr_update (the flags
+ *   of opts are ignored).  The update runs after the work already queued on
+ *   every graph's stream and is complete on return.  stats: NULL or count
+ *   entries, one per graph in creation order; ms_update is the time of the
+ *   whole group, ms_sweep is 0.  Errors: PR_EINVAL, PR_ENORANKS (a dynamic
+ *   method on a graph without ranks; nothing is changed), PR_ECUDA.
+ */
+#define PR_GROUP_MAX 1024
+typedef struct pr_group pr_group;
+pr_status pr_group_create(int32_t count, pr_graph* const* graphs, void* stream, pr_group** out);
+pr_status pr_group_update(pr_group* grp, pr_method method, double alpha, double tau, const pr_options* opts,
+                          pr_stats* stats);
+void pr_group_destroy(pr_group* grp);
+
 /* Number of CUDA kernels this library has launched in this process so far
  * (all graphs); the difference across a region counts its launches. */
 unsigned long long pr_kernel_launches(void);

@@ -94,6 +94,9 @@ def load():
         "pr_status_string": ([ctypes.c_int], ctypes.c_char_p),
         "pr_kernel_launches": ([], ctypes.c_ulonglong),
         "pr_sweep_noalloc": ([i32, _P, _P, _P, _P, _P, f64, _P, _P], ctypes.c_int),
+        "pr_group_create": ([i32, _P, _P, ctypes.POINTER(_P)], ctypes.c_int),
+        "pr_group_update": ([_P, ctypes.c_int, f64, f64, _P, _P], ctypes.c_int),
+        "pr_group_destroy": ([_P], None),
     }
     for name, (args, res) in sig.items():
         f = getattr(lib, name)
@@ -205,6 +208,10 @@ def pr_update(h, method, alpha=0.85, tau=1e-10, tau_f=1e-6, tau_p=1e-6, max_iter
     opts = pr_options(tau_f, tau_p, int(max_iter), flags)
     st = pr_stats()
     _check(load().pr_update(h, m, float(alpha), float(tau), ctypes.byref(opts), ctypes.byref(st)), h)
+    return _stats(st)
+
+
+def _stats(st):
     return Stats(st.iterations, bool(st.converged), st.delta_R, st.vertices_ever_affected, st.edges_processed,
                  st.vertices_processed, st.eff_deletions, st.eff_insertions, st.ms_apply, st.ms_update, st.ms_sweep,
                  st.sweeps)
@@ -309,6 +316,35 @@ def pr_sweep_noalloc(n, in_off, in_src, out_deg, r_in, r_out, alpha, delta_out, 
     _check(load().pr_sweep_noalloc(int(n), *ptrs, float(alpha), dp, _stream_handle(stream)))
 
 
+PR_GROUP_MAX = 1024
+
+
+def pr_group_create(handles, stream=None):
+    arr = (_P * len(handles))(*[h.value if isinstance(h, _P) else h for h in handles])
+    out = _P()
+    _check(load().pr_group_create(len(handles), arr, _stream_handle(stream), ctypes.byref(out)))
+    _group_sizes[out.value] = len(handles)
+    return out
+
+
+def pr_group_update(q, method, alpha=0.85, tau=1e-10, tau_f=1e-6, tau_p=1e-6, max_iter=500):
+    """One update of every graph of the group; returns one Stats per graph."""
+    m = METHODS[method] if isinstance(method, str) else int(method)
+    opts = pr_options(tau_f, tau_p, int(max_iter), 0)
+    n = _group_sizes[q.value]
+    st = (pr_stats * n)()
+    _check(load().pr_group_update(q, m, float(alpha), float(tau), ctypes.byref(opts), st))
+    return [_stats(x) for x in st]
+
+
+def pr_group_destroy(q):
+    _group_sizes.pop(q.value, None)
+    load().pr_group_destroy(q)
+
+
+_group_sizes = {}
+
+
 def pr_kernel_launches() -> int:
     return int(load().pr_kernel_launches())
 
@@ -390,3 +426,25 @@ class Graph:
 
     def dt_affected(self):
         return pr_affected(self._h, 1)
+
+
+class Group:
+    """Owning wrapper around a pr_group handle; keeps its graphs alive."""
+
+    def __init__(self, graphs, stream=None):
+        self.graphs = list(graphs)
+        self._q = pr_group_create([g.handle for g in self.graphs], stream)
+
+    def update(self, method, **kw):
+        return pr_group_update(self._q, method, **kw)
+
+    def close(self):
+        if self._q:
+            pr_group_destroy(self._q)
+            self._q = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -13,6 +13,7 @@
 #include "batch.cuh"
 #include "frontier.cuh"
 #include "graph.cuh"
+#include "handle.cuh"
 #include "prim.cuh"
 #include "sweep.cuh"
 
@@ -27,15 +28,6 @@ constexpr double PUSH_VERTEX_FRACTION = 0.10;
 // share of L2 given to the contributions gathered with an evict-last policy
 constexpr double HOT_L2_FRACTION = 0.5;
 
-struct pr_graph {
-  Graph g;
-  cudaEvent_t ev[6] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
-  double ms_apply = 0.0;
-  int32_t* lbits_tmp = nullptr;   // bits_to_list scratch
-  int64_t* ls_tmp = nullptr;      // list scan scratch
-  int64_t tiles_cap = 0;          // capacity of the tile tables
-  double* vec_tmp = nullptr;      // n doubles (rank import / export)
-};
 
 #define TRY(x)                                          \
   do {                                                  \

@@ -20,6 +20,7 @@ namespace dfpr {
 
 // process-wide count of kernel launches made by this library (pr_kernel_launches)
 void note_launch();
+void note_launches(unsigned long long k);   // kernels run by a CUDA graph launch
 unsigned long long launches_so_far();
 
 // fixed-point scale of the contribution sums: value = integer * 2^-FIX_BITS

@@ -1,0 +1,574 @@
+// group.cu -- one update (Static, ND, DF or DF-P) of many graphs at once.
+//
+// Every iteration sweeps all graphs of the group that have not converged in
+// one launch pair: a gather kernel whose warps walk a work space made of every
+// graph's in-CSR quads laid end to end, and an epilogue kernel over every
+// graph's 32-vertex chunks laid end to end.  A warp finds the graph of a work
+// unit by binary search over a prefix of the per-graph unit counts held in
+// shared memory, then runs the same warp step as the single-graph pull sweep
+// (pull_step.cuh), so a graph's ranks do not depend on the group it runs in.
+// Each graph converges on its own: a one-block control kernel closes the
+// iteration of every live graph (L-inf change against tau, iteration count
+// against max_iter) and sets the condition of the CUDA graph's WHILE node that
+// repeats the iteration, so the whole update runs without a host round trip.
+//
+// The initial frontier of DF / DF-P (Alg. 1) is expressed in the pull form of
+// the frontier, F = S u out(X): X holds the sources of the effective change,
+// whose G_t out-neighbours are found by the gather step from the in-rows
+// (every source reaches itself through its self-loop), and S holds the
+// targets of deleted edges, which completes G_{t-1}.out(u).  Static and ND
+// start with every vertex in S and never prune, which makes every iteration a
+// full sweep of Eq. 1.
+#include <algorithm>
+#include <cstring>
+#include <new>
+#include <vector>
+#include "dfpr.h"
+#include "frontier.cuh"
+#include "handle.cuh"
+#include "prim.cuh"
+#include "pull_step.cuh"
+
+using namespace dfpr;
+
+namespace {
+
+constexpr int GR_THREADS = 256;
+constexpr int64_t GR_GATHER_QUADS = 32 * SW_QPT;   // quads per gather work unit (one warp step)
+
+// per graph, fixed during one update
+struct GDesc {
+  const int32_t* icol;
+  const uint32_t* rowbits;
+  const int32_t* rowbase;
+  int64_t nquads;
+  const int32_t* odeg;
+  const int32_t* ideg;
+  long long* C[2];       // C[0] holds the contributions of the ranks on entry
+  double* R;
+  long long* acc;
+  uint32_t* anyb;
+  uint32_t* S[2];
+  uint32_t* X[2];
+  uint32_t* ever;
+  const uint64_t* dmin;
+  const uint64_t* dplus;
+  int64_t n_dmin, n_dplus;
+  int32_t n, id_bits;
+  double C0;
+};
+
+// per graph, written by the loop
+struct GState {
+  unsigned long long dR;        // this iteration's L-inf change (bits of a non-negative double)
+  unsigned long long dR_last;   // of the last finished iteration
+  long long edges, verts, ever;
+  int32_t cur, iter, done, converged;
+};
+
+// the update: method, tolerances and the work-space prefixes (G + 1 each)
+struct GRun {
+  double alpha, tau, tau_f, tau_p;
+  int32_t max_iter, method, G, loops;
+  const int64_t* wpre;   // gather units
+  const int64_t* fpre;   // epilogue units (FIN_U chunks)
+  const int64_t* bpre;   // bitset words
+  const int64_t* dpre;   // changed edges (deletions then insertions)
+  const double* tab_sc;
+  const double* tab_cl;
+};
+
+// the largest g in [0, G) with pre[g] <= u (pre[0] = 0 <= u < pre[G]); graphs
+// with no units of this kind are passed over
+__device__ __forceinline__ int find_graph(const int64_t* pre, int G, int64_t u) {
+  int lo = 0, hi = G;
+  while (hi - lo > 1) {
+    int mid = (lo + hi) >> 1;
+    if (pre[mid] <= u) lo = mid;
+    else hi = mid;
+  }
+  return lo;
+}
+
+__device__ __forceinline__ void load_prefix(int64_t* sm, const int64_t* pre, int G) {
+  for (int i = threadIdx.x; i <= G; i += blockDim.x) sm[i] = pre[i];
+  __syncthreads();
+}
+
+// bitsets of every graph cleared, Static / ND frontiers set to every vertex,
+// Static ranks set to 1/n; the loop condition set from max_iter
+__global__ void __launch_bounds__(GR_THREADS) k_g_init(const GRun* __restrict__ run, const GDesc* __restrict__ desc,
+                                                       GState* __restrict__ st, cudaGraphConditionalHandle cond) {
+  __shared__ int64_t pre[PR_GROUP_MAX + 1];
+  const int G = run->G;
+  const int method = run->method;
+  load_prefix(pre, run->bpre, G);
+  if (blockIdx.x == 0) {
+    for (int g = threadIdx.x; g < G; g += blockDim.x) {
+      GState z;
+      memset(&z, 0, sizeof(z));
+      st[g] = z;
+    }
+    // the sentinel slot n of both contribution buffers reads as zero
+    for (int g = threadIdx.x; g < G; g += blockDim.x) {
+      desc[g].C[0][desc[g].n] = 0;
+      desc[g].C[1][desc[g].n] = 0;
+    }
+    if (threadIdx.x == 0) cudaGraphSetConditional(cond, run->max_iter > 0 ? 1u : 0u);
+  }
+  const int lane = threadIdx.x & 31;
+  const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  const int64_t total = pre[G];
+  for (int64_t u = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5; u < total; u += nw) {
+    const int g = find_graph(pre, G, u);
+    const GDesc& d = desc[g];
+    const int64_t w = u - pre[g];
+    const int64_t v = w * 32 + lane;
+    const bool valid = v < d.n;
+    const unsigned all = __ballot_sync(0xffffffffu, valid);
+    if (method == PR_STATIC && valid) {
+      const double r = 1.0 / (double)d.n;
+      const int32_t dv = d.odeg[v];
+      const double sc = dv < TAB ? run->tab_sc[dv] : FIX_ONE / (double)dv;
+      d.R[v] = r;
+      d.C[0][v] = __double2ll_rn(r * sc);
+    }
+    if (lane == 0) {
+      d.S[0][w] = (method == PR_STATIC || method == PR_NAIVE_DYNAMIC) ? all : 0u;
+      d.X[0][w] = 0u;
+      d.ever[w] = 0u;
+      d.anyb[w] = 0u;
+    }
+  }
+}
+
+// DF / DF-P initial frontier: X <- sources of the effective change, S <-
+// targets of deleted edges
+__global__ void __launch_bounds__(GR_THREADS) k_g_mark(const GRun* __restrict__ run, const GDesc* __restrict__ desc) {
+  __shared__ int64_t pre[PR_GROUP_MAX + 1];
+  const int G = run->G;
+  if (run->method != PR_DF && run->method != PR_DFP) return;
+  load_prefix(pre, run->dpre, G);
+  const int64_t total = pre[G];
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < total; i += (int64_t)gridDim.x * blockDim.x) {
+    const int g = find_graph(pre, G, i);
+    const GDesc& d = desc[g];
+    const int64_t k = i - pre[g];
+    const bool del = k < d.n_dmin;
+    const uint64_t key = del ? d.dmin[k] : d.dplus[k - d.n_dmin];
+    const int32_t src = (int32_t)(key >> d.id_bits);
+    atomicOr(d.X[0] + (src >> 5), 1u << (src & 31));
+    if (del) {
+      const int32_t dst = (int32_t)(key & ((1ull << d.id_bits) - 1));
+      atomicOr(d.S[0] + (dst >> 5), 1u << (dst & 31));
+    }
+  }
+}
+
+// gather phase of one iteration, every live graph
+__global__ void __launch_bounds__(GR_THREADS) k_g_gather(const GRun* __restrict__ run, const GDesc* __restrict__ desc,
+                                                         const GState* __restrict__ st) {
+  __shared__ int64_t pre[PR_GROUP_MAX + 1];
+  const int G = run->G;
+  load_prefix(pre, run->wpre, G);
+  const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  const int64_t total = pre[G];
+  const uint64_t pol_stream = policy_evict_first();
+  const uint64_t pol_keep = policy_evict_last();
+  for (int64_t u = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5; u < total; u += nw) {
+    const int g = find_graph(pre, G, u);
+    if (st[g].done) continue;
+    const GDesc& d = desc[g];
+    const int c = st[g].cur;
+    gather_step<true>(d.icol, d.C[c], d.X[c], d.S[c], d.rowbits, d.rowbase, d.nquads, d.n, d.acc, d.anyb,
+                      (u - pre[g]) * GR_GATHER_QUADS, pol_stream, pol_keep);
+  }
+}
+
+// the fields finish_pull_step reads, for one graph and one parity
+struct GView {
+  int32_t n;
+  const int32_t* odeg;
+  const int32_t* ideg;
+  double* R;
+  const long long* Ccur;
+  long long* Cnext;
+  const uint32_t* S_cur;
+  uint32_t* S_next;
+  uint32_t* X_next;
+  uint32_t* ever;
+  const double* tab_sc;
+  const double* tab_cl;
+  double alpha, C0, tau_f, tau_p;
+};
+
+__device__ __forceinline__ void flush_totals(PullTotals& t, GState* s) {
+  const int lane = threadIdx.x & 31;
+  unsigned long long dm = t.dmax;
+  long long e = t.edges, v = t.verts;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    unsigned long long odm = __shfl_xor_sync(0xffffffffu, dm, o);
+    dm = odm > dm ? odm : dm;
+    e += __shfl_xor_sync(0xffffffffu, e, o);
+    v += __shfl_xor_sync(0xffffffffu, v, o);
+  }
+  if (lane == 0) {
+    if (dm) atomicMax(&s->dR, dm);
+    if (e) atomicAdd(reinterpret_cast<unsigned long long*>(&s->edges), (unsigned long long)e);
+    if (v) atomicAdd(reinterpret_cast<unsigned long long*>(&s->verts), (unsigned long long)v);
+    if (t.ever_new) atomicAdd(reinterpret_cast<unsigned long long*>(&s->ever), (unsigned long long)t.ever_new);
+  }
+  t = PullTotals();
+}
+
+// epilogue phase of one iteration, every live graph
+// (Eq. 2 for DF-P when CLOSED, else Eq. 1)
+template <bool CLOSED>
+__global__ void __launch_bounds__(GR_THREADS, 2) k_g_finish(const GRun* __restrict__ run,
+                                                            const GDesc* __restrict__ desc, GState* __restrict__ st) {
+  __shared__ int64_t pre[PR_GROUP_MAX + 1];
+  const int G = run->G;
+  load_prefix(pre, run->fpre, G);
+  const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  const int64_t total = pre[G];
+  PullTotals t;
+  int tg = -1;   // graph the totals belong to
+  for (int64_t u = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5; u < total; u += nw) {
+    const int g = find_graph(pre, G, u);
+    if (st[g].done) continue;
+    if (g != tg) {
+      if (tg >= 0) flush_totals(t, st + tg);
+      tg = g;
+    }
+    const GDesc& d = desc[g];
+    const int c = st[g].cur;
+    GView p;
+    p.n = d.n;
+    p.odeg = d.odeg;
+    p.ideg = d.ideg;
+    p.R = d.R;
+    p.Ccur = d.C[c];
+    p.Cnext = d.C[c ^ 1];
+    p.S_cur = d.S[c];
+    p.S_next = d.S[c ^ 1];
+    p.X_next = d.X[c ^ 1];
+    p.ever = d.ever;
+    p.tab_sc = run->tab_sc;
+    p.tab_cl = run->tab_cl;
+    p.alpha = run->alpha;
+    p.C0 = d.C0;
+    p.tau_f = run->tau_f;
+    p.tau_p = run->tau_p;
+    const int64_t nchunks = cdiv(d.n, 32);
+    const int64_t ch0 = (u - pre[g]) * FIN_U;
+    finish_pull_step<CLOSED>(p, d.acc, d.anyb, ch0, nchunks, t);
+  }
+  if (tg >= 0) flush_totals(t, st + tg);
+}
+
+// close the iteration of every live graph; loop while any is live
+__global__ void k_g_control(GRun* run, GState* st, cudaGraphConditionalHandle cond) {
+  __shared__ int live;
+  if (threadIdx.x == 0) live = 0;
+  __syncthreads();
+  const double tau = run->tau;
+  for (int g = threadIdx.x; g < run->G; g += blockDim.x) {
+    GState& s = st[g];
+    if (s.done) continue;
+    s.iter += 1;
+    s.cur ^= 1;
+    s.dR_last = s.dR;
+    s.dR = 0ull;
+    const double dR = __longlong_as_double((long long)s.dR_last);
+    if (dR <= tau) {
+      s.converged = 1;
+      s.done = 1;
+    } else if (s.iter >= run->max_iter) {
+      s.done = 1;
+    } else {
+      live = 1;
+    }
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    run->loops += 1;
+    // every graph is done after max_iter iterations; the guard bounds the loop
+    // even if a state were corrupted
+    cudaGraphSetConditional(cond, (live && run->loops < run->max_iter) ? 1u : 0u);
+  }
+}
+
+}  // namespace
+
+struct pr_group {
+  int32_t G = 0;
+  std::vector<pr_graph*> graphs;
+  int dev = 0;
+  cudaStream_t stream = nullptr;
+  // device: run, descriptors, states, prefixes (4 x (G + 1)), tables
+  GRun* d_run = nullptr;
+  GDesc* d_desc = nullptr;
+  GState* d_state = nullptr;
+  int64_t* d_pre = nullptr;
+  double* tab_sc = nullptr;
+  double* tab_cl = nullptr;
+  double tab_alpha = -1.0;
+  // pinned host staging
+  GRun* h_run = nullptr;
+  GDesc* h_desc = nullptr;
+  GState* h_state = nullptr;
+  int64_t* h_pre = nullptr;
+  // one CUDA graph per epilogue form (index 1: DF-P), built on first use
+  cudaGraph_t graph[2] = {nullptr, nullptr};
+  cudaGraphExec_t exec[2] = {nullptr, nullptr};
+  cudaGraphConditionalHandle cond[2] = {0, 0};
+  cudaEvent_t ev[3] = {nullptr, nullptr, nullptr};
+};
+
+static void group_free(pr_group* q) {
+  if (!q) return;
+  if (q->stream) cudaStreamSynchronize(q->stream);
+  for (int k = 0; k < 2; k++) {
+    if (q->exec[k]) cudaGraphExecDestroy(q->exec[k]);
+    if (q->graph[k]) cudaGraphDestroy(q->graph[k]);
+  }
+  for (void* p : {(void*)q->d_run, (void*)q->d_desc, (void*)q->d_state, (void*)q->d_pre, (void*)q->tab_sc,
+                  (void*)q->tab_cl})
+    if (p) cudaFree(p);
+  for (void* p : {(void*)q->h_run, (void*)q->h_desc, (void*)q->h_state, (void*)q->h_pre})
+    if (p) cudaFreeHost(p);
+  for (cudaEvent_t e : q->ev)
+    if (e) cudaEventDestroy(e);
+  delete q;
+}
+
+static int blocks_per_sm(const void* fn, int threads) {
+  int b = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, fn, threads, 0) != cudaSuccess || b < 1) b = 1;
+  return b;
+}
+
+static cudaError_t add_kernel(cudaGraph_t graph, cudaGraphNode_t* node, const cudaGraphNode_t* dep, size_t ndep,
+                              const void* fn, int grid, void** args) {
+  cudaKernelNodeParams kp;
+  memset(&kp, 0, sizeof(kp));
+  kp.func = const_cast<void*>(fn);
+  kp.gridDim = dim3(grid);
+  kp.blockDim = dim3(GR_THREADS);
+  kp.kernelParams = args;
+  return cudaGraphAddKernelNode(node, graph, dep, ndep, &kp);
+}
+
+// init -> mark -> WHILE (gather -> finish -> control); k = 1 for the DF-P epilogue
+static cudaError_t build_exec(pr_group* q, int k) {
+  cudaError_t e;
+  cudaGraph_t& graph = q->graph[k];
+  if ((e = cudaGraphCreate(&graph, 0)) != cudaSuccess) return e;
+  if ((e = cudaGraphConditionalHandleCreate(&q->cond[k], graph, 0, 0)) != cudaSuccess) return e;
+  const void* fin = k ? (const void*)k_g_finish<true> : (const void*)k_g_finish<false>;
+  const int sms = num_sms();
+  const int g_init = sms * blocks_per_sm((const void*)k_g_init, GR_THREADS);
+  const int g_gather = sms * blocks_per_sm((const void*)k_g_gather, GR_THREADS);
+  const int g_finish = sms * blocks_per_sm(fin, GR_THREADS);
+  cudaGraphNode_t n_init, n_mark, n_loop, n_gather, n_finish, n_ctl;
+  void* a_init[] = {&q->d_run, &q->d_desc, &q->d_state, &q->cond[k]};
+  void* a_mark[] = {&q->d_run, &q->d_desc};
+  void* a_gather[] = {&q->d_run, &q->d_desc, &q->d_state};
+  void* a_finish[] = {&q->d_run, &q->d_desc, &q->d_state};
+  void* a_ctl[] = {&q->d_run, &q->d_state, &q->cond[k]};
+  if ((e = add_kernel(graph, &n_init, nullptr, 0, (const void*)k_g_init, g_init, a_init)) != cudaSuccess) return e;
+  if ((e = add_kernel(graph, &n_mark, &n_init, 1, (const void*)k_g_mark, g_init, a_mark)) != cudaSuccess) return e;
+  cudaGraphNodeParams cp = {};
+  cp.type = cudaGraphNodeTypeConditional;
+  cp.conditional.handle = q->cond[k];
+  cp.conditional.type = cudaGraphCondTypeWhile;
+  cp.conditional.size = 1;
+  if ((e = cudaGraphAddNode(&n_loop, graph, &n_mark, nullptr, 1, &cp)) != cudaSuccess) return e;
+  cudaGraph_t body = cp.conditional.phGraph_out[0];
+  if ((e = add_kernel(body, &n_gather, nullptr, 0, (const void*)k_g_gather, g_gather, a_gather)) != cudaSuccess)
+    return e;
+  if ((e = add_kernel(body, &n_finish, &n_gather, 1, fin, g_finish, a_finish)) != cudaSuccess) return e;
+  cudaKernelNodeParams kp;
+  memset(&kp, 0, sizeof(kp));
+  kp.func = (void*)k_g_control;
+  kp.gridDim = dim3(1);
+  kp.blockDim = dim3(GR_THREADS);
+  kp.kernelParams = a_ctl;
+  if ((e = cudaGraphAddKernelNode(&n_ctl, body, &n_finish, 1, &kp)) != cudaSuccess) return e;
+  return cudaGraphInstantiate(&q->exec[k], graph, 0);
+}
+
+extern "C" {
+
+pr_status pr_group_create(int32_t count, pr_graph* const* graphs, void* stream, pr_group** out) {
+  if (!out) return PR_EINVAL;
+  *out = nullptr;
+  if (count < 1 || count > PR_GROUP_MAX || !graphs) return PR_EINVAL;
+  int dev = -1;
+  for (int32_t i = 0; i < count; i++) {
+    if (!graphs[i]) return PR_EINVAL;
+    for (int32_t j = 0; j < i; j++)
+      if (graphs[j] == graphs[i]) return PR_EINVAL;   // each graph once
+    if (i == 0) dev = graphs[i]->g.dev;
+    else if (graphs[i]->g.dev != dev) return PR_EINVAL;
+  }
+  int cur = 0;
+  if (cudaGetDevice(&cur) != cudaSuccess || cur != dev) return PR_EINVAL;
+  pr_group* q = new (std::nothrow) pr_group();
+  if (!q) return PR_ENOMEM;
+  q->G = count;
+  q->graphs.assign(graphs, graphs + count);
+  q->dev = dev;
+  q->stream = (cudaStream_t)stream;
+  const size_t pre_elems = 4 * (size_t)(count + 1);
+  bool ok = cudaMalloc((void**)&q->d_run, sizeof(GRun)) == cudaSuccess &&
+            cudaMalloc((void**)&q->d_desc, sizeof(GDesc) * count) == cudaSuccess &&
+            cudaMalloc((void**)&q->d_state, sizeof(GState) * count) == cudaSuccess &&
+            cudaMalloc((void**)&q->d_pre, sizeof(int64_t) * pre_elems) == cudaSuccess &&
+            cudaMalloc((void**)&q->tab_sc, sizeof(double) * TAB) == cudaSuccess &&
+            cudaMalloc((void**)&q->tab_cl, sizeof(double) * TAB) == cudaSuccess &&
+            cudaMallocHost((void**)&q->h_run, sizeof(GRun)) == cudaSuccess &&
+            cudaMallocHost((void**)&q->h_desc, sizeof(GDesc) * count) == cudaSuccess &&
+            cudaMallocHost((void**)&q->h_state, sizeof(GState) * count) == cudaSuccess &&
+            cudaMallocHost((void**)&q->h_pre, sizeof(int64_t) * pre_elems) == cudaSuccess;
+  for (int i = 0; ok && i < 3; i++) ok = cudaEventCreate(&q->ev[i]) == cudaSuccess;
+  if (!ok) {
+    cudaGetLastError();
+    group_free(q);
+    return PR_ENOMEM;
+  }
+  *out = q;
+  return PR_OK;
+}
+
+void pr_group_destroy(pr_group* q) { group_free(q); }
+
+pr_status pr_group_update(pr_group* q, pr_method method, double alpha, double tau, const pr_options* opts,
+                          pr_stats* stats) {
+  if (!q) return PR_EINVAL;
+  if (method != PR_STATIC && method != PR_NAIVE_DYNAMIC && method != PR_DF && method != PR_DFP) return PR_EINVAL;
+  if (!(alpha >= 0.0 && alpha < 1.0) || !(tau >= 0.0)) return PR_EINVAL;
+  pr_options o = {1e-6, 1e-6, 500, 0};
+  if (opts) o = *opts;
+  if (!(o.tau_f >= 0.0) || !(o.tau_p >= 0.0) || o.max_iter < 0) return PR_EINVAL;
+  const int G = q->G;
+  if (method != PR_STATIC)
+    for (int i = 0; i < G; i++)
+      if (!q->graphs[i]->g.has_ranks) return PR_ENORANKS;
+  cudaStream_t s = q->stream;
+  int64_t* wpre = q->h_pre;
+  int64_t* fpre = wpre + (G + 1);
+  int64_t* bpre = fpre + (G + 1);
+  int64_t* dpre = bpre + (G + 1);
+  wpre[0] = fpre[0] = bpre[0] = dpre[0] = 0;
+  for (int i = 0; i < G; i++) {
+    Graph* g = &q->graphs[i]->g;
+    GDesc& d = q->h_desc[i];
+    memset(&d, 0, sizeof(d));
+    d.icol = g->in.col;
+    d.rowbits = g->rowbits;
+    d.rowbase = g->rowbase;
+    d.nquads = g->in.cap >> 2;
+    d.odeg = g->out.deg;
+    d.ideg = g->in.deg;
+    d.C[0] = g->C[g->ccur];
+    d.C[1] = g->C[g->ccur ^ 1];
+    d.R = g->R;
+    d.acc = g->gacc;
+    d.anyb = g->anyb;
+    d.S[0] = g->bits[0];
+    d.S[1] = g->bits[1];
+    d.X[0] = g->aux;
+    d.X[1] = g->aux2;
+    d.ever = g->ever;
+    d.dmin = g->dmin;
+    d.dplus = g->dplus;
+    d.n_dmin = g->n_dmin;
+    d.n_dplus = g->n_dplus;
+    d.n = g->n;
+    d.id_bits = g->id_bits;
+    d.C0 = (1.0 - alpha) / (double)g->n;
+    wpre[i + 1] = wpre[i] + cdiv(d.nquads, GR_GATHER_QUADS);
+    fpre[i + 1] = fpre[i] + cdiv(cdiv((int64_t)g->n, 32), FIN_U);
+    bpre[i + 1] = bpre[i] + cdiv((int64_t)g->n, 32);
+    dpre[i + 1] = dpre[i] + ((method == PR_DF || method == PR_DFP) ? g->n_dmin + g->n_dplus : 0);
+  }
+  GRun& r = *q->h_run;
+  memset(&r, 0, sizeof(r));
+  r.alpha = alpha;
+  r.tau = tau;
+  r.tau_f = o.tau_f;
+  r.tau_p = o.tau_p;
+  r.max_iter = o.max_iter;
+  r.method = (int32_t)method;
+  r.G = G;
+  r.loops = 0;
+  r.wpre = q->d_pre;
+  r.fpre = q->d_pre + (G + 1);
+  r.bpre = q->d_pre + 2 * (G + 1);
+  r.dpre = q->d_pre + 3 * (G + 1);
+  r.tab_sc = q->tab_sc;
+  r.tab_cl = q->tab_cl;
+
+  // order after the work already queued on the graphs' streams
+  for (int i = 0; i < G; i++) {
+    cudaStream_t gs = q->graphs[i]->g.stream;
+    if (gs == s) continue;
+    if (cudaEventRecord(q->ev[2], gs) != cudaSuccess || cudaStreamWaitEvent(s, q->ev[2], 0) != cudaSuccess)
+      return PR_ECUDA;
+  }
+  if (cudaEventRecord(q->ev[0], s) != cudaSuccess) return PR_ECUDA;
+  if (q->tab_alpha != alpha) {
+    if (launch_tables(q->tab_sc, q->tab_cl, alpha, s) != cudaSuccess) return PR_ECUDA;
+    q->tab_alpha = alpha;
+  }
+  if (cudaMemcpyAsync(q->d_pre, q->h_pre, sizeof(int64_t) * 4 * (size_t)(G + 1), cudaMemcpyHostToDevice, s) !=
+          cudaSuccess ||
+      cudaMemcpyAsync(q->d_desc, q->h_desc, sizeof(GDesc) * G, cudaMemcpyHostToDevice, s) != cudaSuccess ||
+      cudaMemcpyAsync(q->d_run, q->h_run, sizeof(GRun), cudaMemcpyHostToDevice, s) != cudaSuccess)
+    return PR_ECUDA;
+  const int k = method == PR_DFP ? 1 : 0;
+  if (!q->exec[k] && build_exec(q, k) != cudaSuccess) {
+    cudaGetLastError();
+    return PR_ECUDA;
+  }
+  if (cudaGraphLaunch(q->exec[k], s) != cudaSuccess) return PR_ECUDA;
+  if (cudaMemcpyAsync(q->h_state, q->d_state, sizeof(GState) * G, cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+      cudaMemcpyAsync(q->h_run, q->d_run, sizeof(GRun), cudaMemcpyDeviceToHost, s) != cudaSuccess)
+    return PR_ECUDA;
+  if (cudaEventRecord(q->ev[1], s) != cudaSuccess || cudaEventSynchronize(q->ev[1]) != cudaSuccess) return PR_ECUDA;
+  float ms = 0.f;
+  cudaEventElapsedTime(&ms, q->ev[0], q->ev[1]);
+  // kernels the CUDA graph ran: init, mark, and three per loop pass
+  note_launches(2ull + 3ull * (unsigned long long)q->h_run->loops);
+  for (int i = 0; i < G; i++) {
+    pr_graph* h = q->graphs[i];
+    Graph* g = &h->g;
+    const GState& st = q->h_state[i];
+    if (st.cur) g->ccur ^= 1;
+    g->has_ranks = true;
+    if (stats) {
+      pr_stats& o2 = stats[i];
+      memset(&o2, 0, sizeof(o2));
+      double dR;
+      memcpy(&dR, &st.dR_last, sizeof(dR));
+      o2.iterations = st.iter;
+      o2.converged = st.converged;
+      o2.delta_R = st.iter ? dR : 0.0;
+      o2.vertices_ever_affected =
+          (method == PR_DF || method == PR_DFP) ? st.ever : (st.iter > 0 ? (int64_t)g->n : 0);
+      o2.edges_processed = st.edges;
+      o2.vertices_processed = st.verts;
+      o2.eff_deletions = g->n_dmin;
+      o2.eff_insertions = g->n_dplus;
+      o2.ms_apply = h->ms_apply;
+      o2.ms_update = ms;
+      o2.ms_sweep = 0.0;
+      o2.sweeps = st.iter;
+    }
+  }
+  return PR_OK;
+}
+
+}  // extern "C"

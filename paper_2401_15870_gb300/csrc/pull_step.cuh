@@ -1,0 +1,204 @@
+// pull_step.cuh -- one warp step of the every-vertex sweep (gather and
+// epilogue), shared by the single-graph kernels (sweep.cu) and the kernels
+// that sweep a group of graphs in one launch (group.cu).
+//
+// Gather step: a warp takes 32 x SW_QPT consecutive quads of the in-CSR
+// capacity (lane = quad), loads them as 128-bit streams, gathers the four
+// contributions of each and finds each quad's row from a bitmap of row
+// starts (one bit per quad) and the number of rows before every 32-quad word:
+// the owner of quad q is rowbase[q/32] + popcount(starts up to q) - 1.  A
+// segmented warp reduction leaves one partial sum per row piece, which is
+// added to the row's accumulator (exact integer addition, so the order does
+// not matter).  In pull form it also records whether any source expanded.
+//
+// Epilogue step (pull form): a warp owns U consecutive 32-vertex chunks, one
+// 32-bit word of every bitset each, so the next frontier's stay / expanded
+// words are built with ballots and written whole, with no atomics and no
+// clearing beforehand.  Vertices outside F_i keep their rank and copy their
+// contribution.  FP64 is the binding pipe of the epilogue on GB300 (about 0.6
+// Tops/s), so it is spent only where the formulas need it: the 2^-61 scale is
+// folded into alpha (a power of two, so the product is exact), and maxima and
+// the threshold tests of non-negative doubles compare their bit patterns as
+// integers, which orders them the same way.
+#pragma once
+#include "sweep.cuh"
+
+namespace dfpr {
+
+// L2 policies: the streamed CSR columns are read once per sweep (evict first),
+// the gathered contributions are reused across the whole sweep (evict last)
+__device__ __forceinline__ uint64_t policy_evict_first() {
+  uint64_t p;
+  asm volatile("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(p));
+  return p;
+}
+__device__ __forceinline__ uint64_t policy_evict_last() {
+  uint64_t p;
+  asm volatile("createpolicy.fractional.L2::evict_last.b64 %0, 1.0;" : "=l"(p));
+  return p;
+}
+__device__ __forceinline__ int4 ld_stream4(const int32_t* p, uint64_t pol) {
+  int4 v;
+  asm volatile("ld.global.nc.L1::no_allocate.L2::cache_hint.v4.s32 {%0, %1, %2, %3}, [%4], %5;"
+               : "=r"(v.x), "=r"(v.y), "=r"(v.z), "=r"(v.w)
+               : "l"(p), "l"(pol));
+  return v;
+}
+__device__ __forceinline__ long long ld_hint(const long long* p, uint64_t pol) {
+  long long v;
+  asm volatile("ld.global.nc.L2::cache_hint.b64 %0, [%1], %2;" : "=l"(v) : "l"(p), "l"(pol));
+  return v;
+}
+
+__device__ __forceinline__ unsigned long long dbits(double x) { return (unsigned long long)__double_as_longlong(x); }
+
+// quads [base, base + 32 * SW_QPT) of one in-CSR; S / X / anyb only in pull form
+template <bool PULL>
+__device__ __forceinline__ void gather_step(const int32_t* __restrict__ icol, const long long* __restrict__ C,
+                                            const uint32_t* __restrict__ X, const uint32_t* __restrict__ S,
+                                            const uint32_t* __restrict__ rowbits, const int32_t* __restrict__ rowbase,
+                                            int64_t nquads, int32_t sent, long long* __restrict__ acc,
+                                            uint32_t* __restrict__ anyb, int64_t base, uint64_t pol_stream,
+                                            uint64_t pol_keep) {
+  const int lane = threadIdx.x & 31;
+  const unsigned upto = lane == 31 ? 0xffffffffu : ((2u << lane) - 1u);
+  // sentinel slots (row slack) contribute 0 and issue no load
+  auto contrib = [&](int32_t c) -> long long { return c != sent ? ld_hint(C + c, pol_keep) : 0ll; };
+  auto expanded = [&](int32_t c) -> unsigned { return c != sent ? (__ldg(X + (c >> 5)) >> (c & 31)) : 0u; };
+  int4 c[SW_QPT];
+  int owner[SW_QPT];
+#pragma unroll
+  for (int j = 0; j < SW_QPT; j++) {
+    const int64_t q = base + 32 * j + lane;
+    const bool valid = q < nquads;
+    c[j] = valid ? ld_stream4(icol + 4 * q, pol_stream) : make_int4(sent, sent, sent, sent);
+    const int64_t w = (base >> 5) + j;
+    const uint32_t bits = w * 32 < nquads ? __ldg(rowbits + w) : 0u;
+    const int32_t rb = w * 32 < nquads ? __ldg(rowbase + w) : 0;
+    owner[j] = valid ? rb + __popc(bits & upto) - 1 : -1;
+  }
+  long long s[SW_QPT];
+  unsigned x[SW_QPT];
+#pragma unroll
+  for (int j = 0; j < SW_QPT; j++) {
+    s[j] = contrib(c[j].x) + contrib(c[j].y) + contrib(c[j].z) + contrib(c[j].w);
+    x[j] = 0;
+    // a row whose vertex stays in the frontier is processed anyway: its
+    // sources' expanded bits are not needed
+    if (PULL && owner[j] >= 0 && !((__ldg(S + (owner[j] >> 5)) >> (owner[j] & 31)) & 1u))
+      x[j] = (expanded(c[j].x) | expanded(c[j].y) | expanded(c[j].z) | expanded(c[j].w)) & 1u;
+  }
+#pragma unroll
+  for (int j = 0; j < SW_QPT; j++) {
+    const int own = owner[j];
+    long long sum = s[j];
+    unsigned any = x[j];
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      long long os = __shfl_down_sync(0xffffffffu, sum, o);
+      unsigned ox = __shfl_down_sync(0xffffffffu, any, o);
+      int oo = __shfl_down_sync(0xffffffffu, own, o);
+      if (lane + o < 32 && oo == own) {
+        sum += os;
+        any |= ox;
+      }
+    }
+    const int prev = __shfl_up_sync(0xffffffffu, own, 1);
+    if (own >= 0 && (lane == 0 || prev != own)) {
+      if (sum) atomicAdd(reinterpret_cast<unsigned long long*>(acc + own), (unsigned long long)sum);
+      if (PULL && any) atomicOr(anyb + (own >> 5), 1u << (own & 31));
+    }
+  }
+}
+
+constexpr int FIN_U = 4;   // chunks per warp step of the epilogue: their loads are issued together
+
+// per-thread totals of the epilogue (lane 0 holds the frontier counts)
+struct PullTotals {
+  unsigned long long dmax = 0ull;   // max |r - R[v]| as the bits of a non-negative double
+  long long edges = 0, verts = 0;
+  long long ever_new = 0;           // vertices processed for the first time in this update
+  int stays = 0, exps = 0;
+};
+
+// chunks [ch0, ch0 + FIN_U) of one graph.  P provides n, odeg, ideg, R, Ccur,
+// Cnext, S_cur, S_next, X_next, ever, tab_sc, tab_cl, alpha, C0, tau_f, tau_p.
+// The accumulators and the expanded-source words it reads are left zero for
+// the next sweep.
+template <bool CLOSED, class P>
+__device__ __forceinline__ void finish_pull_step(const P& p, long long* __restrict__ acc, uint32_t* __restrict__ anyb,
+                                                 int64_t ch0, int64_t nchunks, PullTotals& t) {
+  constexpr int U = FIN_U;
+  const int lane = threadIdx.x & 31;
+  const double alpha_fix = p.alpha * FIX_INV;
+  const bool same_tau = p.tau_f == p.tau_p;
+  long long sum[U], cself[U];
+  double Rv[U];
+  int32_t d[U];
+  bool member[U], valid[U];
+#pragma unroll
+  for (int u = 0; u < U; u++) {
+    const int64_t ch = ch0 + u;
+    const int64_t v = ch * 32 + lane;
+    valid[u] = ch < nchunks && v < p.n;
+    const uint32_t in_f = ch < nchunks ? (anyb[ch] | __ldg(p.S_cur + ch)) : 0u;
+    member[u] = valid[u] && ((in_f >> lane) & 1u);
+    sum[u] = valid[u] ? acc[v] : 0;
+    cself[u] = valid[u] ? p.Ccur[v] : 0;
+    Rv[u] = member[u] ? p.R[v] : 0.0;
+    d[u] = member[u] ? p.odeg[v] : 1;
+  }
+#pragma unroll
+  for (int u = 0; u < U; u++) {
+    const int64_t ch = ch0 + u;
+    const int64_t v = ch * 32 + lane;
+    bool stay = false, expand = false;
+    if (valid[u]) acc[v] = 0;
+    if (member[u]) {
+      double r;
+      if (CLOSED) {
+        // Eq. 2, the self term removed exactly in fixed point
+        const long long K = sum[u] - cself[u];
+        const double f = d[u] < TAB ? p.tab_cl[d[u]] : 1.0 / (1.0 - p.alpha / (double)d[u]);
+        r = f * fma(alpha_fix, (double)K, p.C0);
+      } else {
+        r = fma(alpha_fix, (double)sum[u], p.C0);   // Eq. 1
+      }
+      const unsigned long long drb = dbits(fabs(r - Rv[u]));
+      t.dmax = drb > t.dmax ? drb : t.dmax;
+      t.edges += p.ideg[v];
+      t.verts += 1;
+      p.R[v] = r;
+      const double sc = d[u] < TAB ? p.tab_sc[d[u]] : FIX_ONE / (double)d[u];
+      p.Cnext[v] = __double2ll_rn(r * sc);
+      // Alg. 1: prune when dr / max(r, R[v]) <= tau_p (DF-P), expand when it
+      // is > tau_f; compared without the division
+      const double mr = dbits(r) > dbits(Rv[u]) ? r : Rv[u];
+      const unsigned long long tf = dbits(p.tau_f * mr);
+      const unsigned long long tp = same_tau ? tf : dbits(p.tau_p * mr);
+      stay = !CLOSED || drb > tp;
+      expand = drb > tf;
+    } else if (valid[u]) {
+      p.Cnext[v] = cself[u];
+    }
+    const unsigned ms = __ballot_sync(0xffffffffu, stay);
+    const unsigned mx = __ballot_sync(0xffffffffu, expand);
+    const unsigned mm = __ballot_sync(0xffffffffu, member[u]);
+    if (lane == 0 && ch < nchunks) {
+      anyb[ch] = 0u;
+      p.S_next[ch] = ms;
+      p.X_next[ch] = mx;
+      if (mm) {
+        const uint32_t old = p.ever[ch];
+        if (mm & ~old) {
+          p.ever[ch] = old | mm;
+          t.ever_new += __popc(mm & ~old);
+        }
+      }
+      t.stays += __popc(ms);
+      t.exps += __popc(mx);
+    }
+  }
+}
+
+}  // namespace dfpr

@@ -18,6 +18,7 @@
 #include <algorithm>
 #include <climits>
 #include "sweep.cuh"
+#include "pull_step.cuh"
 #include "prim.cuh"
 
 namespace dfpr {
@@ -78,32 +79,6 @@ __device__ __forceinline__ void block_flush_stats(double dmax, long long edges, 
 }
 
 // ------------------------------------------------------------------ tiles
-
-// L2 policies: the streamed CSR columns are read once per sweep (evict first),
-// the gathered contributions are reused across the whole sweep (evict last)
-__device__ __forceinline__ uint64_t policy_evict_first() {
-  uint64_t p;
-  asm volatile("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(p));
-  return p;
-}
-__device__ __forceinline__ uint64_t policy_evict_last() {
-  uint64_t p;
-  asm volatile("createpolicy.fractional.L2::evict_last.b64 %0, 1.0;" : "=l"(p));
-  return p;
-}
-__device__ __forceinline__ int4 ld_stream4(const int32_t* p, uint64_t pol) {
-  int4 v;
-  asm volatile("ld.global.nc.L1::no_allocate.L2::cache_hint.v4.s32 {%0, %1, %2, %3}, [%4], %5;"
-               : "=r"(v.x), "=r"(v.y), "=r"(v.z), "=r"(v.w)
-               : "l"(p), "l"(pol));
-  return v;
-}
-__device__ __forceinline__ long long ld_hint(const long long* p, uint64_t pol) {
-  long long v;
-  asm volatile("ld.global.nc.L2::cache_hint.b64 %0, [%1], %2;" : "=l"(v) : "l"(p), "l"(pol));
-  return v;
-}
-
 
 // Shared-memory view of one tile: for every item (list entry) touching the
 // tile its vertex, the slot offset of its quads, how many tiles it spans, and
@@ -366,170 +341,39 @@ __global__ void __launch_bounds__(SW_THREADS) k_sweep(SweepParams p) {
 //
 // A sweep over every vertex (Static, ND, and the pull form of DF / DF-P) needs
 // no vertex list: the in-CSR rows lie in vertex order, quad-aligned, so the
-// quad space is walked linearly.
-//   k_gather_rows: each warp takes 32 consecutive quads per step (lane = quad),
-//     loads them as 128-bit streams, gathers the four contributions of each,
-//     and finds each quad's row from a bitmap of row starts (one bit per quad)
-//     and the number of rows before every 32-quad word: the owner of quad q is
-//     rowbase[q/32] + popcount(starts up to q) - 1.  A segmented warp
-//     reduction leaves one partial sum per row piece, which is added to the
-//     row's accumulator (exact integer addition, so the order does not
-//     matter).  In pull form it also records whether any source expanded.
-//   k_finish_rows: one thread per vertex reads and clears its accumulator and
-//     runs the epilogue.
+// quad space is walked linearly (pull_step.cuh).
+//   k_gather_rows: warps take 32 x SW_QPT quads per step and add each row
+//     piece's partial sum to the row's accumulator;
+//   k_finish_pull / k_finish_full: read and clear each vertex's accumulator
+//     and run the epilogue.
 template <bool PULL>
 __global__ void __launch_bounds__(256) k_gather_rows(const int32_t* __restrict__ icol, const long long* __restrict__ C,
                                                      const uint32_t* __restrict__ X, const uint32_t* __restrict__ S,
                                                      const uint32_t* __restrict__ rowbits,
                                                      const int32_t* __restrict__ rowbase, int64_t nquads, int32_t sent,
                                                      long long* __restrict__ acc, uint32_t* __restrict__ anyb) {
-  const int lane = threadIdx.x & 31;
-  const unsigned upto = lane == 31 ? 0xffffffffu : ((2u << lane) - 1u);
   const int64_t warp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
   const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
   const uint64_t pol_stream = policy_evict_first();
   const uint64_t pol_keep = policy_evict_last();
-  // sentinel slots (row slack) contribute 0 and issue no load
-  auto contrib = [&](int32_t c) -> long long { return c != sent ? ld_hint(C + c, pol_keep) : 0ll; };
-  auto expanded = [&](int32_t c) -> unsigned { return c != sent ? (__ldg(X + (c >> 5)) >> (c & 31)) : 0u; };
-  for (int64_t base = warp * 32 * SW_QPT; base < nquads; base += nw * 32 * SW_QPT) {
-    int4 c[SW_QPT];
-    int owner[SW_QPT];
-#pragma unroll
-    for (int j = 0; j < SW_QPT; j++) {
-      const int64_t q = base + 32 * j + lane;
-      const bool valid = q < nquads;
-      c[j] = valid ? ld_stream4(icol + 4 * q, pol_stream) : make_int4(sent, sent, sent, sent);
-      const int64_t w = (base >> 5) + j;
-      const uint32_t bits = w * 32 < nquads ? __ldg(rowbits + w) : 0u;
-      const int32_t rb = w * 32 < nquads ? __ldg(rowbase + w) : 0;
-      owner[j] = valid ? rb + __popc(bits & upto) - 1 : -1;
-    }
-    long long s[SW_QPT];
-    unsigned x[SW_QPT];
-#pragma unroll
-    for (int j = 0; j < SW_QPT; j++) {
-      s[j] = contrib(c[j].x) + contrib(c[j].y) + contrib(c[j].z) + contrib(c[j].w);
-      x[j] = 0;
-      // a row whose vertex stays in the frontier is processed anyway: its
-      // sources' expanded bits are not needed
-      if (PULL && owner[j] >= 0 && !((__ldg(S + (owner[j] >> 5)) >> (owner[j] & 31)) & 1u))
-        x[j] = (expanded(c[j].x) | expanded(c[j].y) | expanded(c[j].z) | expanded(c[j].w)) & 1u;
-    }
-#pragma unroll
-    for (int j = 0; j < SW_QPT; j++) {
-      const int own = owner[j];
-      long long sum = s[j];
-      unsigned any = x[j];
-#pragma unroll
-      for (int o = 1; o < 32; o <<= 1) {
-        long long os = __shfl_down_sync(0xffffffffu, sum, o);
-        unsigned ox = __shfl_down_sync(0xffffffffu, any, o);
-        int oo = __shfl_down_sync(0xffffffffu, own, o);
-        if (lane + o < 32 && oo == own) {
-          sum += os;
-          any |= ox;
-        }
-      }
-      const int prev = __shfl_up_sync(0xffffffffu, own, 1);
-      if (own >= 0 && (lane == 0 || prev != own)) {
-        if (sum) atomicAdd(reinterpret_cast<unsigned long long*>(acc + own), (unsigned long long)sum);
-        if (PULL && any) atomicOr(anyb + (own >> 5), 1u << (own & 31));
-      }
-    }
-  }
+  for (int64_t base = warp * 32 * SW_QPT; base < nquads; base += nw * 32 * SW_QPT)
+    gather_step<PULL>(icol, C, X, S, rowbits, rowbase, nquads, sent, acc, anyb, base, pol_stream, pol_keep);
 }
-
-// Pull-form epilogue: one warp per 32 consecutive vertices (one 32-bit word of
-// every bitset), so the next frontier's stay / expanded words are built with
-// ballots and written whole, with no atomics and no clearing beforehand.
-// Vertices outside F_i keep their rank and copy their contribution.
-// FP64 is the binding pipe of the epilogues on GB300 (about 0.6 Tops/s), so
-// they spend it only where the formulas need it: the 2^-61 scale is folded
-// into alpha (a power of two, so the product is exact), and maxima and the
-// threshold tests of non-negative doubles compare their bit patterns as
-// integers, which orders them the same way.
-__device__ __forceinline__ unsigned long long dbits(double x) { return (unsigned long long)__double_as_longlong(x); }
 
 template <bool CLOSED>
 __global__ void __launch_bounds__(256, 4) k_finish_pull(SweepParams p, long long* __restrict__ acc,
-                                                        const uint32_t* __restrict__ anyb) {
-  constexpr int U = 4;   // chunks per warp step: their loads are issued together
+                                                        uint32_t* __restrict__ anyb) {
   const int lane = threadIdx.x & 31;
   const int64_t nchunks = cdiv(p.n, 32);
   const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
-  const double alpha_fix = p.alpha * FIX_INV;
-  const bool same_tau = p.tau_f == p.tau_p;
-  unsigned long long dmax = 0ull;
-  long long edges = 0, verts = 0;
-  int stays = 0, exps = 0;
-  for (int64_t ch0 = ((blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5) * U; ch0 < nchunks; ch0 += nw * U) {
-    long long sum[U], cself[U];
-    double Rv[U];
-    int32_t d[U];
-    bool member[U], valid[U];
-#pragma unroll
-    for (int u = 0; u < U; u++) {
-      const int64_t ch = ch0 + u;
-      const int64_t v = ch * 32 + lane;
-      valid[u] = ch < nchunks && v < p.n;
-      const uint32_t in_f = ch < nchunks ? (__ldg(anyb + ch) | __ldg(p.S_cur + ch)) : 0u;
-      member[u] = valid[u] && ((in_f >> lane) & 1u);
-      sum[u] = valid[u] ? acc[v] : 0;
-      cself[u] = valid[u] ? p.Ccur[v] : 0;
-      Rv[u] = member[u] ? p.R[v] : 0.0;
-      d[u] = member[u] ? p.odeg[v] : 1;
-    }
-#pragma unroll
-    for (int u = 0; u < U; u++) {
-      const int64_t ch = ch0 + u;
-      const int64_t v = ch * 32 + lane;
-      bool stay = false, expand = false;
-      if (valid[u]) acc[v] = 0;
-      if (member[u]) {
-        double r;
-        if (CLOSED) {
-          // Eq. 2, the self term removed exactly in fixed point
-          const long long K = sum[u] - cself[u];
-          const double f = d[u] < TAB ? p.tab_cl[d[u]] : 1.0 / (1.0 - p.alpha / (double)d[u]);
-          r = f * fma(alpha_fix, (double)K, p.C0);
-        } else {
-          r = fma(alpha_fix, (double)sum[u], p.C0);   // Eq. 1
-        }
-        const unsigned long long drb = dbits(fabs(r - Rv[u]));
-        dmax = drb > dmax ? drb : dmax;
-        edges += p.ideg[v];
-        verts += 1;
-        p.R[v] = r;
-        const double sc = d[u] < TAB ? p.tab_sc[d[u]] : FIX_ONE / (double)d[u];
-        p.Cnext[v] = __double2ll_rn(r * sc);
-        // Alg. 1: prune when dr / max(r, R[v]) <= tau_p (DF-P), expand when it
-        // is > tau_f; compared without the division
-        const double mr = dbits(r) > dbits(Rv[u]) ? r : Rv[u];
-        const unsigned long long tf = dbits(p.tau_f * mr);
-        const unsigned long long tp = same_tau ? tf : dbits(p.tau_p * mr);
-        stay = !CLOSED || drb > tp;
-        expand = drb > tf;
-      } else if (valid[u]) {
-        p.Cnext[v] = cself[u];
-      }
-      const unsigned ms = __ballot_sync(0xffffffffu, stay);
-      const unsigned mx = __ballot_sync(0xffffffffu, expand);
-      const unsigned mm = __ballot_sync(0xffffffffu, member[u]);
-      if (lane == 0 && ch < nchunks) {
-        p.S_next[ch] = ms;
-        p.X_next[ch] = mx;
-        if (mm) p.ever[ch] |= mm;
-        stays += __popc(ms);
-        exps += __popc(mx);
-      }
-    }
-  }
+  PullTotals t;
+  for (int64_t ch0 = ((blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5) * FIN_U; ch0 < nchunks; ch0 += nw * FIN_U)
+    finish_pull_step<CLOSED>(p, acc, anyb, ch0, nchunks, t);
   if (lane == 0) {
-    if (stays) atomicAdd(p.cnt_next, stays);
-    if (exps) atomicAdd(p.cnt_x, exps);
+    if (t.stays) atomicAdd(p.cnt_next, t.stays);
+    if (t.exps) atomicAdd(p.cnt_x, t.exps);
   }
-  block_flush_stats(__longlong_as_double((long long)dmax), edges, verts, p.ctl);
+  block_flush_stats(__longlong_as_double((long long)t.dmax), t.edges, t.verts, p.ctl);
 }
 
 // Epilogue of a sweep over every vertex with Eq. 1 (Static, ND): all vertices

@@ -1,0 +1,163 @@
+"""Groups: one update of many graphs in one launch sequence with the iteration
+loop on the device.  Every graph's ranks must match the oracle within 1e-9
+and be bit-identical, with identical statistics, to pr_update on the graph
+alone from the same previous ranks (same arithmetic; the group only changes
+how the work is scheduled)."""
+import numpy as np
+import pytest
+
+import oracle
+import synth
+
+pytestmark = pytest.mark.gpu
+
+TOL = 1e-9
+
+
+@pytest.fixture(scope="module")
+def lib():
+    import paper_2401_15870_gb300 as pr
+    pr.load()
+    return pr
+
+
+def make_case(pr, scale, ef, bsize, seed, n=None):
+    """GPU graph + oracle graph, static ranks of the base graph, one batch applied."""
+    n = n or (1 << scale)
+    src, dst = synth.rmat(max(scale, 1), ef * n, seed)
+    src, dst = src % n, dst % n
+    G = pr.Graph.from_edges(n, src, dst)
+    O = oracle.Graph(n, src, dst)
+    r0, _ = O.update("static")
+    if bsize:
+        cs, cd = synth.unique_edges(src, dst)
+        b = synth.batch(n, cs, cd, bsize, seed + 1)
+        G.apply_batch(*b)
+        O.apply_batch(*b)
+    return G, O, r0
+
+
+# sizes: tiny, odd, not a multiple of 32, several quad tiles, an empty batch
+CASES = [(1, 2, 2, 3, None), (6, 3, 5, 4, 37), (9, 8, 40, 5, None), (12, 16, 300, 6, None), (14, 16, 262, 7, None),
+         (11, 24, 0, 8, None), (13, 4, 2000, 9, 5000)]
+
+
+@pytest.fixture(scope="module")
+def cases(lib):
+    return [make_case(lib, *c) for c in CASES]
+
+
+def solo(G, r0, method, **kw):
+    G.set_ranks(r0)
+    st = G.update(method, **kw)
+    return G.ranks(), st
+
+
+def same_stats(a, b):
+    return (a.iterations, a.converged, a.vertices_ever_affected, a.edges_processed, a.vertices_processed) == \
+        (b.iterations, b.converged, b.vertices_ever_affected, b.edges_processed, b.vertices_processed)
+
+
+@pytest.mark.parametrize("method", ["dfp", "df", "nd", "static"])
+def test_group_matches_oracle_and_solo_runs(lib, cases, method):
+    graphs = [c[0] for c in cases]
+    grp = lib.Group(graphs)
+    try:
+        for G, O, r0 in cases:
+            G.set_ranks(r0)
+        stats = grp.update(method)
+        got = [G.ranks() for G in graphs]
+        for (G, O, r0), r, st in zip(cases, got, stats):
+            ref, ost = O.update(method, r_prev=r0)
+            assert np.max(np.abs(r - ref)) < TOL
+            assert st.iterations == ost.iterations
+            assert st.converged == ost.converged
+            r_solo, st_solo = solo(G, r0, method)
+            assert np.array_equal(r, r_solo), (G.n, method)
+            assert same_stats(st, st_solo), (st, st_solo)
+            if method in ("df", "dfp"):
+                assert st.vertices_ever_affected == ost.vertices_ever_affected
+    finally:
+        grp.close()
+
+
+def test_group_max_iter_and_empty_batch(lib, cases):
+    graphs = [c[0] for c in cases]
+    grp = lib.Group(graphs)
+    try:
+        for G, O, r0 in cases:
+            G.set_ranks(r0)
+        stats = grp.update("dfp", max_iter=0)
+        for (G, O, r0), st in zip(cases, stats):
+            assert st.iterations == 0 and not st.converged
+            assert np.array_equal(G.ranks(), r0)
+        stats = grp.update("dfp", max_iter=3)
+        for (G, O, r0), st in zip(cases, stats):
+            assert st.iterations <= 3
+            ref, _ = O.update("dfp", r_prev=r0, max_iter=3)
+            assert np.max(np.abs(G.ranks() - ref)) < TOL
+        # the graph whose batch was empty: F_0 is empty, one iteration, ranks kept
+        G, O, r0 = cases[5]
+        G.set_ranks(r0)
+        st = grp.update("dfp")[5]
+        assert st.iterations == 1 and st.converged and st.vertices_ever_affected == 0
+        assert np.array_equal(G.ranks(), r0)
+    finally:
+        grp.close()
+
+
+def test_group_successive_batches(lib):
+    """Chained updates: batch, group DF-P, batch, group DF-P, ... equal the
+    oracle's chain and the solo chain."""
+    specs = [(10, 8, 50, 21), (12, 16, 200, 22), (8, 4, 10, 23)]
+    pairs = []
+    for scale, ef, _, seed in specs:
+        n = 1 << scale
+        src, dst = synth.rmat(scale, ef * n, seed)
+        pairs.append((n, src, dst, lib.Graph.from_edges(n, src, dst), lib.Graph.from_edges(n, src, dst),
+                      oracle.Graph(n, src, dst)))
+    grp = lib.Group([p[3] for p in pairs])
+    try:
+        grp.update("static")
+        r_cpu = []
+        for n, src, dst, G, S, O in pairs:
+            r, _ = O.update("static")
+            r_cpu.append(r)
+            S.update("static")
+            assert np.array_equal(G.ranks(), S.ranks())
+        for step in range(3):
+            for k, ((n, src, dst, G, S, O), (_, _, bsize, seed)) in enumerate(zip(pairs, specs)):
+                cs, cd = synth.unique_edges(src, dst)
+                b = synth.batch(n, cs, cd, bsize, seed * 100 + step)
+                for x in (G, S, O):
+                    x.apply_batch(*b)
+            grp.update("dfp")
+            for k, (n, src, dst, G, S, O) in enumerate(pairs):
+                S.update("dfp")
+                r_cpu[k], _ = O.update("dfp", r_prev=r_cpu[k])
+                assert np.array_equal(G.ranks(), S.ranks()), (step, k)
+                assert np.max(np.abs(G.ranks() - r_cpu[k])) < 1e-8
+    finally:
+        grp.close()
+
+
+def test_group_errors(lib):
+    n = 64
+    src, dst = synth.rmat(6, 256, 5)
+    A = lib.Graph.from_edges(n, src, dst)
+    B = lib.Graph.from_edges(n, src, dst)
+    with pytest.raises(lib.PRError):
+        lib.Group([A, A])
+    with pytest.raises(lib.PRError):
+        lib.Group([])
+    grp = lib.Group([A, B])
+    try:
+        with pytest.raises(lib.PRError) as e:
+            grp.update("dfp")               # no ranks yet
+        assert e.value.status == 4
+        with pytest.raises(lib.PRError):
+            grp.update("dt")                # not offered for groups
+        grp.update("static")
+        grp.update("dfp")
+    finally:
+        grp.close()
