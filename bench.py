@@ -53,6 +53,9 @@ def parse():
     ap.add_argument("--seed", type=int, default=2000)
     ap.add_argument("--e2e-steps", type=int, default=5)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--workload", default="large", choices=["large", "batched"],
+                    help="large: one R-MAT scale-25 graph (default); batched: a group of R-MAT graphs updated together")
+    ap.add_argument("--graphs", type=int, default=64, help="batched: graphs in the group")
     return ap.parse_args()
 
 
@@ -260,7 +263,7 @@ def run_gpu(a, rank, world, local_rank):
         "config": {"workload": workload_name(a), "vertices": n, "edges": m0, "batch_edges": size,
                    "inputs": "larger than L2 (graph ~%.0f GB resident)" % (m0 * 8 * 1.2 / 1e9),
                    "parallelism": "replicas" if world > 1 else "single GPU"},
-        "roofline": {"bound": "hbm", "kernel": "DF-P rank sweep (k_gather_rows + k_finish_rows in pull form, "
+        "roofline": {"bound": "hbm", "kernel": "DF-P rank sweep (k_gather_rows + k_finish_pull in pull form, "
                                "k_sweep<DFP> in push form)", "achieved": achieved, "peak": peak,
                      "unit": "GB/s", "frac": achieved / peak,
                      "traffic": SWEEP_DRAM_BYTES_RMAT25 if (a.scale, a.edge_factor, a.batch_frac) == (25, 32, 1e-4) else None,
@@ -292,6 +295,144 @@ def run_gpu(a, rank, world, local_rank):
     print(json.dumps(line), flush=True)
 
 
+# ------------------------------------------------------------------ batched workload
+
+def batched_specs(a):
+    """Graph sizes of the batched workload: scale uniform over the integers
+    12..21 (vertex counts log-uniform in 2^12 .. 2^21), edge factor uniform in
+    8..32, one seed per graph."""
+    import numpy as np
+    rng = np.random.default_rng(a.seed)
+    return [(int(rng.integers(12, 22)), int(rng.integers(8, 33)), a.seed + 1000 * (i + 1)) for i in range(a.graphs)]
+
+
+def batched_name(a):
+    return ("%d R-MAT graphs (scales 12..21 uniform, edge factor 8..32 uniform, a,b,c,d=.57,.19,.19,.05), "
+            "self-loops, each DF-P-updated after its own random 80/20 batch of %g |E|; one group update "
+            "(pr_group_update) per step" % (a.graphs, a.batch_frac))
+
+
+def run_batched(a, rank, world, local_rank):
+    import torch
+
+    import paper_2401_15870_gb300 as pr
+    import synth.gpu as sg
+
+    torch.cuda.set_device(local_rank)
+    stream = torch.cuda.current_stream()
+    specs = batched_specs(a)
+    graphs, batches, host_batches, sizes = [], [], [], []
+    nb = a.warmup + a.steps
+    for scale, ef, seed in specs:
+        n = 1 << scale
+        src, dst = sg.rmat(scale, ef << scale, seed + 7919 * rank)
+        G = pr.Graph.from_edges(n, src, dst, device=True, stream=stream)
+        size = max(1, int(round(a.batch_frac * G.m)))
+        # batches for the group steps, then as many for the plain steps
+        batches.append([sg.batch(n, src, dst, size, seed + 1 + i) for i in range(2 * nb)])
+        host_batches.append([[t.cpu().pin_memory() for t in sg.batch(n, src, dst, size, seed + 50001 + i)]
+                             for i in range(a.e2e_steps)])
+        graphs.append(G)
+        sizes.append((n, G.m, size))
+        del src, dst
+    torch.cuda.synchronize()
+    grp = pr.Group(graphs, stream=stream)
+    grp.update("static", alpha=ALPHA, tau=TAU)
+
+    def group_step(i):
+        for G, b in zip(graphs, batches):
+            G.apply_batch_device(*b[i])
+        return grp.update("dfp", alpha=ALPHA, tau=TAU)
+
+    def plain_step(i):
+        out = []
+        for G, b in zip(graphs, batches):
+            G.apply_batch_device(*b[i])
+            out.append(G.update("dfp", alpha=ALPHA, tau=TAU))
+        return out
+
+    def timed(fn, first):
+        for i in range(a.warmup):
+            fn(first + i)
+        torch.cuda.synchronize()
+        l0 = pr.pr_kernel_launches()
+        ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        ev0.record(stream)
+        st = [fn(first + a.warmup + i) for i in range(a.steps)]
+        ev1.record(stream)
+        torch.cuda.synchronize()
+        return ev0.elapsed_time(ev1), st, pr.pr_kernel_launches() - l0
+
+    clocks = ClockSampler(local_rank)
+    clocks.start()
+    ms_g, st_g, launches_g = timed(group_step, 0)
+    clk = clocks.stop()
+    ms_p, st_p, launches_p = timed(plain_step, nb)
+    value = len(graphs) * a.steps / (ms_g / 1000.0)
+    plain = len(graphs) * a.steps / (ms_p / 1000.0)
+
+    # end to end through host buffers: every graph's batch from pinned memory,
+    # every graph's ranks back to host memory
+    r_host = [torch.empty(n, dtype=torch.float64).pin_memory() for n, _, _ in sizes]
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for i in range(a.e2e_steps):
+        for G, hb in zip(graphs, host_batches):
+            G.apply_batch(*[t.numpy() for t in hb[i]])
+        grp.update("dfp", alpha=ALPHA, tau=TAU)
+        for G, r in zip(graphs, r_host):
+            G.ranks(r.numpy())
+    torch.cuda.synchronize()
+    e2e_ms = (time.perf_counter() - t0) * 1000.0
+    h2d = sum(sum(t.numel() * 4 for t in hb[0]) for hb in host_batches)
+    d2h = sum(n * 8 for n, _, _ in sizes)
+
+    # group sweep loop against HBM: algorithmic bytes of the sweeps over the
+    # group update's time (which also holds its init, marking and control)
+    flat = [s for step in st_g for s in step]
+    upd_ms = sum(step[0].ms_update for step in st_g)
+    sweep_bytes = sum(SWEEP_BYTES_PER_EDGE * s.edges_processed + SWEEP_BYTES_PER_VERTEX * s.vertices_processed
+                      for s in flat)
+    achieved = sweep_bytes / (upd_ms / 1000.0) / 1e9 if upd_ms else 0.0
+    peaks = {}
+    try:
+        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except (OSError, ValueError):
+        pass
+    peak = float(peaks.get("hbm_gbs", 6800.0))
+    if rank != 0:
+        return
+    m_tot = sum(m for _, m, _ in sizes)
+    line = {
+        "metric": METRIC, "value": value, "unit": "graph updates/s", "n_gpus": world, "steps": a.steps,
+        "warmup": a.warmup, "ms_per_step": ms_g / a.steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": batched_name(a), "graphs": len(graphs), "vertices": sum(n for n, _, _ in sizes),
+                   "edges": m_tot, "batch_edges": sum(b for _, _, b in sizes),
+                   "inputs": "larger than L2 (graphs ~%.1f GB resident)" % (m_tot * 8 * 1.2 / 1e9),
+                   "parallelism": "single GPU"},
+        "plain": {"value": plain, "unit": "graph updates/s", "ms_per_step": ms_p / a.steps,
+                  "gpu_launches": launches_p,
+                  "what": "the same steps with one pr_apply_batch_device + pr_update per graph"},
+        "speedup_vs_plain": value / plain,
+        "roofline": {"bound": "hbm", "kernel": "group DF-P loop (k_g_gather + k_g_finish, with init / mark / control)",
+                     "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak, "traffic": None},
+        "e2e": {"value": len(graphs) * a.e2e_steps / (e2e_ms / 1000.0), "unit": "graph updates/s",
+                "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
+        "gpu_launches": launches_g,
+        "clocks": clk,
+        "detail": {
+            "group_update_ms_mean": upd_ms / a.steps,
+            "iterations_max_mean": statistics.mean(max(s.iterations for s in step) for step in st_g),
+            "iterations_mean": statistics.mean(s.iterations for s in flat),
+            "ms_apply_sum_mean": statistics.mean(sum(s.ms_apply for s in step) for step in st_g),
+            "plain_update_ms_sum_mean": statistics.mean(sum(s.ms_update for s in step) for step in st_p),
+        },
+    }
+    print(json.dumps(line), flush=True)
+    grp.close()
+
+
 def main():
     a = parse()
     rank = int(os.environ.get("RANK", "0"))
@@ -305,7 +446,10 @@ def main():
         torch.cuda.set_device(local_rank)
         torch.distributed.init_process_group("nccl")
     try:
-        run_gpu(a, rank, world, local_rank)
+        if a.workload == "batched":
+            run_batched(a, rank, world, local_rank)
+        else:
+            run_gpu(a, rank, world, local_rank)
     finally:
         if world > 1:
             import torch
