@@ -211,6 +211,7 @@ static void destroy_handle(pr_graph* h) {
   if (g->dmin) cudaFree(g->dmin);
   if (g->dplus) cudaFree(g->dplus);
   if (g->ctl_h) cudaFreeHost(g->ctl_h);
+  if (g->small_h) cudaFreeHost(g->small_h);
   for (int i = 0; i < 6; i++)
     if (h->ev[i]) cudaEventDestroy(h->ev[i]);
   delete h;

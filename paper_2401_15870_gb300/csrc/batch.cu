@@ -171,9 +171,12 @@ __device__ __forceinline__ int64_t chunk_row(const int64_t* pre, int64_t nr, int
 }
 
 // copy pass: the old elements of every touched row into scratch, one warp per chunk
-__global__ void k_row_copy(const uint64_t* __restrict__ rows, int64_t nr, const int64_t* __restrict__ sofs,
-                           const int64_t* __restrict__ cpre, const int64_t* __restrict__ off,
-                           const int32_t* __restrict__ deg, const int32_t* __restrict__ col, int32_t* __restrict__ scratch) {
+__global__ void k_row_copy(const uint64_t* __restrict__ rows, const int64_t* __restrict__ nrp,
+                           const int64_t* __restrict__ sofs, const int64_t* __restrict__ cpre,
+                           const int64_t* __restrict__ off, const int32_t* __restrict__ deg,
+                           const int32_t* __restrict__ col, int32_t* __restrict__ scratch, const int32_t* skip) {
+  if (skip && *skip) return;
+  const int64_t nr = *nrp;
   const int lane = threadIdx.x & 31;
   const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
   const int64_t total = cpre[nr];
@@ -191,11 +194,14 @@ __global__ void k_row_copy(const uint64_t* __restrict__ rows, int64_t nr, const 
 // write pass over old positions: every surviving element moves to
 // x - (#deletions below it) + (#insertions below it); slots from the new degree
 // up to the old end get the sentinel
-__global__ void k_row_survivors(const uint64_t* __restrict__ rows, int64_t nr, const int64_t* __restrict__ plan,
-                                const int64_t* __restrict__ sofs, const int64_t* __restrict__ wpre,
-                                const uint64_t* __restrict__ dl, const uint64_t* __restrict__ il, int bits,
-                                const int64_t* __restrict__ off, const int32_t* __restrict__ deg, int32_t* __restrict__ col,
-                                const int32_t* __restrict__ scratch, int32_t sent) {
+__global__ void k_row_survivors(const uint64_t* __restrict__ rows, const int64_t* __restrict__ nrp,
+                                const int64_t* __restrict__ plan, const int64_t* __restrict__ sofs,
+                                const int64_t* __restrict__ wpre, const uint64_t* __restrict__ dl,
+                                const uint64_t* __restrict__ il, int bits, const int64_t* __restrict__ off,
+                                const int32_t* __restrict__ deg, int32_t* __restrict__ col,
+                                const int32_t* __restrict__ scratch, int32_t sent, const int32_t* skip) {
+  if (skip && *skip) return;
+  const int64_t nr = *nrp;
   const int lane = threadIdx.x & 31;
   const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
   const int64_t total = wpre[nr];
@@ -227,11 +233,14 @@ __global__ void k_row_survivors(const uint64_t* __restrict__ rows, int64_t nr, c
 
 // write pass over insertions: insertion k of row r goes to
 // (#insertions below it) + (#old elements below it) - (#deletions below it)
-__global__ void k_row_insertions(const uint64_t* __restrict__ rows, int64_t nr, const int64_t* __restrict__ plan,
-                                 const int64_t* __restrict__ sofs, const uint64_t* __restrict__ dl,
-                                 const uint64_t* __restrict__ il, int64_t ni, int bits, const int64_t* __restrict__ off,
+__global__ void k_row_insertions(const uint64_t* __restrict__ rows, const int64_t* __restrict__ nrp,
+                                 const int64_t* __restrict__ plan, const int64_t* __restrict__ sofs,
+                                 const uint64_t* __restrict__ dl, const uint64_t* __restrict__ il,
+                                 const int64_t* __restrict__ nip, int bits, const int64_t* __restrict__ off,
                                  const int32_t* __restrict__ deg, int32_t* __restrict__ col,
-                                 const int32_t* __restrict__ scratch) {
+                                 const int32_t* __restrict__ scratch, const int32_t* skip) {
+  if (skip && *skip) return;
+  const int64_t nr = *nrp, ni = *nip;
   const uint64_t mask = (1ull << bits) - 1;
   GRID_STRIDE(k, ni) {
     const uint64_t r = il[k] >> bits;
@@ -258,8 +267,10 @@ __global__ void k_row_insertions(const uint64_t* __restrict__ rows, int64_t nr, 
   }
 }
 
-__global__ void k_row_degrees(const uint64_t* __restrict__ rows, int64_t nr, const int64_t* __restrict__ plan,
-                              int32_t* __restrict__ deg) {
+__global__ void k_row_degrees(const uint64_t* __restrict__ rows, const int64_t* __restrict__ nrp,
+                              const int64_t* __restrict__ plan, int32_t* __restrict__ deg, const int32_t* skip) {
+  if (skip && *skip) return;
+  const int64_t nr = *nrp;
   GRID_STRIDE(j, nr) {
     const uint64_t r = rows[j];
     deg[r] = deg[r] - (int32_t)(plan[4 * j + 1] - plan[4 * j]) + (int32_t)(plan[4 * j + 3] - plan[4 * j + 2]);
@@ -297,8 +308,41 @@ __global__ void k_u64_to_i32_low(const uint64_t* __restrict__ in, int64_t k, int
 
 // ------------------------------------------------------------------ host
 
+// a direction whose new rows do not fit their capacity is rebuilt: every
+// surviving edge plus the insertions, sorted, laid out with fresh slack
+static int repack_direction(Graph* g, Csr* c, const uint64_t* dl, int64_t nd, const uint64_t* il, int64_t ni) {
+  cudaStream_t s = g->stream;
+  int bits = g->id_bits;
+  int32_t n = g->n;
+  int64_t* pos;
+  int64_t* pscr;
+  TRY(cudaMalloc(&pos, sizeof(int64_t) * (n + 1)));
+  TRY(cudaMalloc(&pscr, sizeof(int64_t) * scan_tmp_elems(n)));
+  note_launch(); k_surv_count<<<grid_for(n, 256), 256, 0, s>>>(c->deg, n, dl, nd, bits, pos);
+  TRY(scan_excl<int64_t>(pos, pos, n, pscr, s));
+  int64_t surv = 0;
+  TRY(cudaMemcpyAsync(&surv, pos + n, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+  TRY(cudaStreamSynchronize(s));
+  int64_t mtot = surv + ni;
+  uint64_t *keys, *kalt;
+  void* rtmp;
+  TRY(cudaMalloc(&keys, sizeof(uint64_t) * (mtot + 1)));
+  TRY(cudaMalloc(&kalt, sizeof(uint64_t) * (mtot + 1)));
+  TRY(cudaMalloc(&rtmp, radix_tmp_bytes(mtot)));
+  note_launch(); k_materialize<<<grid_for(n, 128), 128, 0, s>>>(c->off, c->deg, c->col, n, dl, nd, bits, pos, keys);
+  if (ni) TRY(cudaMemcpyAsync(keys + surv, il, sizeof(uint64_t) * ni, cudaMemcpyDeviceToDevice, s));
+  TRY(radix_sort_u64(keys, kalt, mtot, 2 * bits, rtmp, s));
+  int rc = build_csr_from_sorted(g, c, keys, mtot, c == &g->in, 2);
+  cudaFree(pos);
+  cudaFree(pscr);
+  cudaFree(keys);
+  cudaFree(kalt);
+  cudaFree(rtmp);
+  return rc;
+}
+
 static int edit_direction(Graph* g, Csr* c, const uint64_t* dl, int64_t nd, const uint64_t* il, int64_t ni,
-                          bool* repacked) {
+                          const int64_t* ni_dev, bool* repacked) {
   cudaStream_t s = g->stream;
   int bits = g->id_bits;
   *repacked = false;
@@ -368,46 +412,412 @@ static int edit_direction(Graph* g, Csr* c, const uint64_t* dl, int64_t nd, cons
     TRY(scratch_get(g, 5, sizeof(int32_t) * (size_t)(stot + 1), &sp));
     int32_t* S = (int32_t*)sp;
     const int wgrid = num_sms() * 16;
-    note_launch(); k_row_copy<<<wgrid, 256, 0, s>>>(rows, nr, sofs, cpre, c->off, c->deg, c->col, S);
-    note_launch(); k_row_survivors<<<wgrid, 256, 0, s>>>(rows, nr, plan, sofs, wpre, dl, il, bits, c->off, c->deg, c->col, S,
-                                                         g->n);
+    note_launch(); k_row_copy<<<wgrid, 256, 0, s>>>(rows, cnt, sofs, cpre, c->off, c->deg, c->col, S, nullptr);
+    note_launch(); k_row_survivors<<<wgrid, 256, 0, s>>>(rows, cnt, plan, sofs, wpre, dl, il, bits, c->off, c->deg, c->col,
+                                                         S, g->n, nullptr);
     if (ni) {
-      note_launch(); k_row_insertions<<<grid_for(ni, 256), 256, 0, s>>>(rows, nr, plan, sofs, dl, il, ni, bits, c->off,
-                                                                        c->deg, c->col, S);
+      note_launch(); k_row_insertions<<<grid_for(ni, 256), 256, 0, s>>>(rows, cnt, plan, sofs, dl, il, ni_dev, bits,
+                                                                        c->off, c->deg, c->col, S, nullptr);
     }
-    note_launch(); k_row_degrees<<<grid_for(nr, 256), 256, 0, s>>>(rows, nr, plan, c->deg);
+    note_launch(); k_row_degrees<<<grid_for(nr, 256), 256, 0, s>>>(rows, cnt, plan, c->deg, nullptr);
     TRY(cudaGetLastError());
     return OK;
   }
 
   // repack this direction: survivors + insertions, sorted, rebuilt with more slack
   *repacked = true;
-  int32_t n = g->n;
-  int64_t* pos;
-  int64_t* pscr;
-  TRY(cudaMalloc(&pos, sizeof(int64_t) * (n + 1)));
-  TRY(cudaMalloc(&pscr, sizeof(int64_t) * scan_tmp_elems(n)));
-  note_launch(); k_surv_count<<<grid_for(n, 256), 256, 0, s>>>(c->deg, n, dl, nd, bits, pos);
-  TRY(scan_excl<int64_t>(pos, pos, n, pscr, s));
-  int64_t surv = 0;
-  TRY(cudaMemcpyAsync(&surv, pos + n, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+  return repack_direction(g, c, dl, nd, il, ni);
+}
+
+// ------------------------------------------------------------------ small batches
+//
+// A batch of at most SMALL_MAX edges is ingested by one thread block with the
+// keys in shared memory: validation, packed keys, sort (bitonic), effective
+// flags, compaction, the same lists keyed (dst, src), and for each direction
+// the touched rows with their edit plans and prefix sums.  The row rewrite
+// kernels above then read every count from the device, so the whole batch
+// costs about ten launches and one host synchronisation (the status read at
+// the end) instead of ~170 launches and six synchronisations.  A direction
+// whose rows overflow their capacity, or whose staging buffer is too small,
+// is skipped by the device and finished by the host after the status read.
+constexpr int SMALL_MAX = 4096;                 // edges of a batch (deletions + insertions)
+constexpr int SMALL_THREADS = 1024;
+constexpr int SMALL_SORT = 2 * SMALL_MAX;       // sort slots (each side padded to a power of two)
+
+struct SmallStatus {
+  int64_t n_del, n_ins;   // effective deletions / insertions
+  int64_t nr[2];          // touched rows, out (0) and in (1)
+  int64_t stot[2];        // staging elements (old degrees of the touched rows)
+  int32_t skip[2];        // the device left this direction's rows unchanged
+  int32_t bad, ovf[2], need[2], pad;
+};
+
+struct SmallBufs {
+  uint64_t edl[SMALL_MAX], eil[SMALL_MAX];   // Delta-, Delta+ sorted by (src, dst)
+  uint64_t sdl[SMALL_MAX], sil[SMALL_MAX];   // the same sorted by (dst, src)
+  uint64_t rows[2][SMALL_MAX];
+  int64_t plan[2][4 * SMALL_MAX];
+  int64_t sofs[2][SMALL_MAX + 1], cpre[2][SMALL_MAX + 1], wpre[2][SMALL_MAX + 1];
+  SmallStatus st;
+};
+
+constexpr size_t SMALL_SMEM = sizeof(uint64_t) * (2 * SMALL_SORT + SMALL_MAX) + sizeof(int64_t) * SMALL_MAX;
+
+__host__ __device__ __forceinline__ int pow2_at_least(int x) {
+  int p = x > 0 ? 1 : 0;
+  while (p < x) p <<= 1;
+  return p;
+}
+
+// ascending bitonic sort of a[0..N), N a power of two (or 0), whole block
+__device__ void block_bitonic(uint64_t* a, int N) {
+  for (int k = 2; k <= N; k <<= 1)
+    for (int j = k >> 1; j > 0; j >>= 1) {
+      for (int i = threadIdx.x; i < N; i += blockDim.x) {
+        const int x = i ^ j;
+        if (x > i) {
+          const uint64_t p = a[i], q = a[x];
+          if ((p > q) == ((i & k) == 0)) {
+            a[i] = q;
+            a[x] = p;
+          }
+        }
+      }
+      __syncthreads();
+    }
+}
+
+// exclusive prefix sum of w[0..len) in place, whole block; returns the total
+__device__ int64_t block_excl_scan(int64_t* w, int len, int64_t* wsum /* 32 */) {
+  const int T = blockDim.x, tid = threadIdx.x, lane = tid & 31, wp = tid >> 5;
+  const int per = (len + T - 1) / T;
+  const int b = min(tid * per, len), e = min(b + per, len);
+  int64_t loc = 0;
+  for (int i = b; i < e; i++) loc += w[i];
+  int64_t x = loc;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    int64_t y = __shfl_up_sync(0xffffffffu, x, o);
+    if (lane >= o) x += y;
+  }
+  if (lane == 31) wsum[wp] = x;
+  __syncthreads();
+  if (wp == 0) {
+    int64_t z = lane < (T >> 5) ? wsum[lane] : 0;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      int64_t y = __shfl_up_sync(0xffffffffu, z, o);
+      if (lane >= o) z += y;
+    }
+    wsum[lane] = z;
+  }
+  __syncthreads();
+  int64_t before = (wp ? wsum[wp - 1] : 0) + x - loc;
+  const int64_t total = wsum[(T >> 5) - 1];
+  for (int i = b; i < e; i++) {
+    const int64_t v = w[i];
+    w[i] = before;
+    before += v;
+  }
+  __syncthreads();
+  return total;
+}
+
+// touched rows of one direction and their edit plans; L holds the deletions
+// [0, nde) and insertions [nde, nde + nie), each sorted by (row, col)
+__device__ void small_plan(int dir, const uint64_t* L, int nde, int nie, int bits, const int64_t* __restrict__ off,
+                           const int32_t* __restrict__ deg, int64_t scap, uint64_t* R, int64_t* W, int64_t* wsum,
+                           SmallBufs* B) {
+  __shared__ int ovf;
+  const int tid = threadIdx.x, T = blockDim.x;
+  const int tot = nde + nie, P = pow2_at_least(tot);
+  if (tid == 0) ovf = 0;
+  for (int i = tid; i < P; i += T) R[i] = i < tot ? (L[i] >> bits) : DROP;
+  __syncthreads();
+  block_bitonic(R, P);
+  for (int i = tid; i < tot; i += T) W[i] = (i == 0 || R[i - 1] != R[i]) ? 1 : 0;
+  __syncthreads();
+  const int nr = (int)block_excl_scan(W, tot, wsum);
+  uint64_t* rows = B->rows[dir];
+  for (int i = tid; i < tot; i += T)
+    if (i == 0 || R[i - 1] != R[i]) rows[W[i]] = R[i];
+  __syncthreads();
+  int64_t* plan = B->plan[dir];
+  for (int j = tid; j < nr; j += T) {
+    const uint64_t r = rows[j];
+    const int64_t d0 = lower_key(L, 0, nde, r << bits), d1 = lower_key(L, d0, nde, (r + 1) << bits);
+    const int64_t i0 = lower_key(L + nde, 0, nie, r << bits), i1 = lower_key(L + nde, i0, nie, (r + 1) << bits);
+    const int64_t dg = deg[r];
+    const int64_t nd2 = dg - (d1 - d0) + (i1 - i0);
+    plan[4 * j + 0] = d0;
+    plan[4 * j + 1] = d1;
+    plan[4 * j + 2] = i0;
+    plan[4 * j + 3] = i1;
+    if (round4(nd2) > off[r + 1] - off[r]) ovf = 1;
+    W[j] = dg;
+  }
+  __syncthreads();
+  const int64_t stot = block_excl_scan(W, nr, wsum);
+  for (int j = tid; j < nr; j += T) B->sofs[dir][j] = W[j];
+  for (int j = tid; j < nr; j += T) W[j] = cdiv((int64_t)deg[rows[j]], RW_CH);
+  __syncthreads();
+  const int64_t ctot = block_excl_scan(W, nr, wsum);
+  for (int j = tid; j < nr; j += T) B->cpre[dir][j] = W[j];
+  for (int j = tid; j < nr; j += T) {
+    const int64_t dg = deg[rows[j]];
+    const int64_t nd2 = dg - (plan[4 * j + 1] - plan[4 * j]) + (plan[4 * j + 3] - plan[4 * j + 2]);
+    W[j] = cdiv(round4(dg > nd2 ? dg : nd2), RW_CH);
+  }
+  __syncthreads();
+  const int64_t wtot = block_excl_scan(W, nr, wsum);
+  for (int j = tid; j < nr; j += T) B->wpre[dir][j] = W[j];
+  if (tid == 0) {
+    B->sofs[dir][nr] = stot;
+    B->cpre[dir][nr] = ctot;
+    B->wpre[dir][nr] = wtot;
+    SmallStatus& st = B->st;
+    st.nr[dir] = nr;
+    st.stot[dir] = stot;
+    st.ovf[dir] = ovf;
+    st.need[dir] = stot > scap ? 1 : 0;
+    st.skip[dir] = (ovf || stot > scap) ? 1 : 0;
+  }
+  __syncthreads();
+}
+
+__global__ void __launch_bounds__(SMALL_THREADS) k_small_ingest(
+    const int32_t* __restrict__ ds, const int32_t* __restrict__ dd, int nd, const int32_t* __restrict__ is,
+    const int32_t* __restrict__ id, int ni, int32_t n, int bits, const int32_t* __restrict__ perm,
+    const int64_t* __restrict__ ooff, const int32_t* __restrict__ odeg, const int32_t* __restrict__ ocol,
+    const int64_t* __restrict__ ioff, const int32_t* __restrict__ ideg, int64_t scap_out, int64_t scap_in,
+    SmallBufs* B) {
+  extern __shared__ uint64_t smem[];
+  uint64_t* A = smem;                           // SMALL_SORT: sorts
+  uint64_t* L = A + SMALL_SORT;                 // SMALL_MAX: effective lists of the current direction
+  uint64_t* R = L + SMALL_MAX;                  // SMALL_SORT: row ids, flags
+  int64_t* W = reinterpret_cast<int64_t*>(R + SMALL_SORT);   // SMALL_MAX: scans
+  __shared__ int64_t wsum[32];
+  __shared__ int bad;
+  const int tid = threadIdx.x, T = blockDim.x;
+  const uint64_t mask = (1ull << bits) - 1;
+  if (tid == 0) bad = 0;
+  __syncthreads();
+  const int Pd = pow2_at_least(nd), Pi = pow2_at_least(ni);
+  uint64_t* dk = A;
+  uint64_t* ik = A + Pd;
+  // keys in internal ids; self-loops and padding sort last as DROP
+  for (int i = tid; i < Pd + Pi; i += T) {
+    const bool del = i < Pd;
+    const int k = del ? i : i - Pd;
+    uint64_t key = DROP;
+    if (k < (del ? nd : ni)) {
+      const int32_t u = del ? ds[k] : is[k], v = del ? dd[k] : id[k];
+      if (u < 0 || u >= n || v < 0 || v >= n) bad = 1;
+      else if (u != v) key = ((uint64_t)perm[u] << bits) | (uint64_t)perm[v];
+    }
+    A[i] = key;
+  }
+  __syncthreads();
+  if (bad) {
+    if (tid == 0) {
+      SmallStatus& st = B->st;
+      memset(&st, 0, sizeof(st));
+      st.bad = 1;
+      st.skip[0] = st.skip[1] = 1;
+    }
+    return;
+  }
+  block_bitonic(dk, Pd);
+  block_bitonic(ik, Pi);
+  // effective flags (Sec. 3.2): a deletion is a first occurrence, present in
+  // E_{t-1} and not re-inserted; an insertion is a first occurrence absent from E_{t-1}
+  for (int i = tid; i < nd + ni; i += T) {
+    const bool del = i < nd;
+    const uint64_t key = del ? dk[i] : ik[i - nd];
+    const uint64_t prev = del ? (i > 0 ? dk[i - 1] : DROP) : (i > nd ? ik[i - nd - 1] : DROP);
+    bool e = key != DROP && key != prev;
+    if (e) {
+      const int32_t u = (int32_t)(key >> bits), v = (int32_t)(key & mask);
+      const bool present = in_row(ocol, ooff[u], odeg[u], v);
+      e = del ? (present && !key_in(ik, ni, key)) : !present;
+    }
+    R[i] = e;
+    W[i] = e;
+  }
+  __syncthreads();
+  const int nde = (int)block_excl_scan(W, nd, wsum);
+  const int nie = (int)block_excl_scan(W + nd, ni, wsum);
+  for (int i = tid; i < nd + ni; i += T) {
+    if (!R[i]) continue;
+    if (i < nd) {
+      L[W[i]] = dk[i];
+      B->edl[W[i]] = dk[i];
+    } else {
+      L[nde + W[i]] = ik[i - nd];
+      B->eil[W[i]] = ik[i - nd];
+    }
+  }
+  __syncthreads();
+  small_plan(0, L, nde, nie, bits, ooff, odeg, scap_out, R, W, wsum, B);
+  // the same lists keyed (dst, src) for the in-CSR
+  const int Pde = pow2_at_least(nde), Pie = pow2_at_least(nie);
+  for (int i = tid; i < Pde + Pie; i += T) {
+    const bool del = i < Pde;
+    const int k = del ? i : i - Pde;
+    uint64_t key = DROP;
+    if (k < (del ? nde : nie)) {
+      const uint64_t x = L[del ? k : nde + k];
+      key = ((x & mask) << bits) | (x >> bits);
+    }
+    A[i] = key;
+  }
+  __syncthreads();
+  block_bitonic(A, Pde);
+  block_bitonic(A + Pde, Pie);
+  for (int i = tid; i < nde + nie; i += T) {
+    const bool del = i < nde;
+    const uint64_t key = del ? A[i] : A[Pde + i - nde];
+    L[i] = key;
+    if (del) B->sdl[i] = key;
+    else B->sil[i - nde] = key;
+  }
+  __syncthreads();
+  small_plan(1, L, nde, nie, bits, ioff, ideg, scap_in, R, W, wsum, B);
+  if (tid == 0) {
+    B->st.n_del = nde;
+    B->st.n_ins = nie;
+    B->st.bad = 0;
+  }
+}
+
+// contributions of the touched out-rows' vertices (the sources of the change)
+__global__ void k_small_contrib(const uint64_t* __restrict__ rows, const int64_t* __restrict__ nrp,
+                                const int32_t* skip, const double* __restrict__ R, long long* __restrict__ C,
+                                const int32_t* __restrict__ odeg, const double* __restrict__ tab_sc) {
+  if (*skip) return;
+  const int64_t nr = *nrp;
+  GRID_STRIDE(j, nr) {
+    const int32_t u = (int32_t)rows[j];
+    const int32_t d = odeg[u];
+    const double sc = d < TAB ? tab_sc[d] : FIX_ONE / (double)d;
+    C[u] = __double2ll_rn(R[u] * sc);
+  }
+}
+
+static void launch_small_edit(Graph* g, Csr* c, SmallBufs* B, int dir, int32_t* S, int64_t nk) {
+  cudaStream_t s = g->stream;
+  const int bits = g->id_bits;
+  const uint64_t* dl = dir == 0 ? B->edl : B->sdl;
+  const uint64_t* il = dir == 0 ? B->eil : B->sil;
+  const int32_t* skip = &B->st.skip[dir];
+  const int64_t* nrp = &B->st.nr[dir];
+  const int wgrid = num_sms() * 4;
+  note_launch(); k_row_copy<<<wgrid, 256, 0, s>>>(B->rows[dir], nrp, B->sofs[dir], B->cpre[dir], c->off, c->deg, c->col,
+                                                 S, skip);
+  note_launch(); k_row_survivors<<<wgrid, 256, 0, s>>>(B->rows[dir], nrp, B->plan[dir], B->sofs[dir], B->wpre[dir], dl,
+                                                      il, bits, c->off, c->deg, c->col, S, g->n, skip);
+  note_launch(); k_row_insertions<<<grid_for(nk, 256), 256, 0, s>>>(B->rows[dir], nrp, B->plan[dir], B->sofs[dir], dl, il,
+                                                                   &B->st.n_ins, bits, c->off, c->deg, c->col, S, skip);
+  note_launch(); k_row_degrees<<<grid_for(nk, 256), 256, 0, s>>>(B->rows[dir], nrp, B->plan[dir], c->deg, skip);
+}
+
+// grow-only staging buffer of one direction (scratch slot 5: out, 7: in)
+static cudaError_t small_staging(Graph* g, int dir, int64_t elems, int32_t** out, int64_t* cap) {
+  const int slot = dir == 0 ? 5 : 7;
+  void* p;
+  cudaError_t e = scratch_get(g, slot, sizeof(int32_t) * (size_t)(elems + 1), &p);
+  if (e != cudaSuccess) return e;
+  *out = (int32_t*)p;
+  *cap = (int64_t)(g->scr[slot].bytes / sizeof(int32_t)) - 1;
+  return cudaSuccess;
+}
+
+static int apply_small(Graph* g, const int32_t* ds, const int32_t* dd, int64_t nd, const int32_t* is,
+                       const int32_t* id, int64_t ni) {
+  cudaStream_t s = g->stream;
+  const int32_t n = g->n;
+  const int64_t nk = nd + ni;
+  void* bp;
+  TRY(scratch_get(g, 6, sizeof(SmallBufs), &bp));
+  SmallBufs* B = (SmallBufs*)bp;
+  if (!g->small_h) TRY(cudaMallocHost(&g->small_h, sizeof(SmallStatus)));
+  SmallStatus* h = (SmallStatus*)g->small_h;
+  int32_t* S[2];
+  int64_t cap[2];
+  // staging of at least 64K elements per direction; larger rows are handled by growing it
+  TRY(small_staging(g, 0, 65536, &S[0], &cap[0]));
+  TRY(small_staging(g, 1, 65536, &S[1], &cap[1]));
+  static bool attr_set[64] = {false};
+  const bool known = g->dev >= 0 && g->dev < 64;
+  if (!known || !attr_set[g->dev]) {
+    TRY(cudaFuncSetAttribute(k_small_ingest, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SMALL_SMEM));
+    if (known) attr_set[g->dev] = true;
+  }
+  note_launch();
+  k_small_ingest<<<1, SMALL_THREADS, SMALL_SMEM, s>>>(ds, dd, (int)nd, is, id, (int)ni, n, g->id_bits, g->perm,
+                                                      g->out.off, g->out.deg, g->out.col, g->in.off, g->in.deg, cap[0],
+                                                      cap[1], B);
+  TRY(cudaGetLastError());
+  launch_small_edit(g, &g->out, B, 0, S[0], nk);
+  launch_small_edit(g, &g->in, B, 1, S[1], nk);
+  if (g->has_ranks) {
+    note_launch();
+    k_small_contrib<<<grid_for(nk, 256), 256, 0, s>>>(B->rows[0], &B->st.nr[0], &B->st.skip[0], g->R, g->C[g->ccur],
+                                                      g->out.deg, g->tab_sc);
+  }
+  TRY(cudaMemcpyAsync(h, &B->st, sizeof(SmallStatus), cudaMemcpyDeviceToHost, s));
   TRY(cudaStreamSynchronize(s));
-  int64_t mtot = surv + ni;
-  uint64_t *keys, *kalt;
-  void* rtmp;
-  TRY(cudaMalloc(&keys, sizeof(uint64_t) * (mtot + 1)));
-  TRY(cudaMalloc(&kalt, sizeof(uint64_t) * (mtot + 1)));
-  TRY(cudaMalloc(&rtmp, radix_tmp_bytes(mtot)));
-  note_launch(); k_materialize<<<grid_for(n, 128), 128, 0, s>>>(c->off, c->deg, c->col, n, dl, nd, bits, pos, keys);
-  if (ni) TRY(cudaMemcpyAsync(keys + surv, il, sizeof(uint64_t) * ni, cudaMemcpyDeviceToDevice, s));
-  TRY(radix_sort_u64(keys, kalt, mtot, 2 * bits, rtmp, s));
-  int rc = build_csr_from_sorted(g, c, keys, mtot, c == &g->in, 2);
-  cudaFree(pos);
-  cudaFree(pscr);
-  cudaFree(keys);
-  cudaFree(kalt);
-  cudaFree(rtmp);
-  return rc;
+  if (h->bad) return set_error(g, ERANGE_, "pr_apply_batch: vertex id out of range");
+  const int64_t a = h->n_del, b = h->n_ins;
+  // the effective change, kept for the update (grow-only buffers owned by the graph)
+  if (g->cap_dmin < a) {
+    if (g->dmin) cudaFree(g->dmin);
+    g->dmin = nullptr;
+    g->cap_dmin = 0;
+    TRY(cudaMalloc(&g->dmin, sizeof(uint64_t) * (a + 1)));
+    g->cap_dmin = a;
+  }
+  if (g->cap_dplus < b) {
+    if (g->dplus) cudaFree(g->dplus);
+    g->dplus = nullptr;
+    g->cap_dplus = 0;
+    TRY(cudaMalloc(&g->dplus, sizeof(uint64_t) * (b + 1)));
+    g->cap_dplus = b;
+  }
+  if (a) TRY(cudaMemcpyAsync(g->dmin, B->edl, sizeof(uint64_t) * a, cudaMemcpyDeviceToDevice, s));
+  if (b) TRY(cudaMemcpyAsync(g->dplus, B->eil, sizeof(uint64_t) * b, cudaMemcpyDeviceToDevice, s));
+  g->n_dmin = a;
+  g->n_dplus = b;
+  if (a + b == 0) return OK;
+  // directions the device skipped: a larger staging buffer, or a repack
+  bool redo_out = false, rep_in = false;
+  for (int dir = 0; dir < 2; dir++) {
+    if (!h->skip[dir]) continue;
+    Csr* c = dir == 0 ? &g->out : &g->in;
+    if (h->ovf[dir]) {
+      int rc = repack_direction(g, c, dir == 0 ? B->edl : B->sdl, a, dir == 0 ? B->eil : B->sil, b);
+      if (rc) return rc;
+      if (dir == 1) rep_in = true;
+    } else {
+      TRY(small_staging(g, dir, h->stot[dir], &S[dir], &cap[dir]));
+      TRY(cudaMemsetAsync(&B->st.skip[dir], 0, sizeof(int32_t), s));
+      launch_small_edit(g, c, B, dir, S[dir], nk);
+    }
+    if (dir == 0) redo_out = true;
+  }
+  if (rep_in) {
+    int rc = refresh_full_tiles(g);
+    if (rc) return rc;
+  }
+  if (redo_out && g->has_ranks) {
+    TRY(cudaMemsetAsync(g->aux, 0, sizeof(uint32_t) * (size_t)(cdiv(n, 32) + 1), s));
+    TRY(cudaMemsetAsync(&g->ctl->count[0], 0, sizeof(int32_t), s));
+    TRY(launch_mark_sources(g->dmin, a, g->dplus, b, g->id_bits, g->aux, g->wl[0], &g->ctl->count[0], s));
+    TRY(launch_contrib_list(g->wl[0], &g->ctl->count[0], g->R, g->C[g->ccur], g->out.deg, g->tab_sc, n, s));
+    TRY(cudaMemsetAsync(&g->ctl->count[0], 0, sizeof(int32_t), s));
+  }
+  TRY(cudaGetLastError());
+  return OK;
 }
 
 int apply_batch_device(Graph* g, const int32_t* ds, const int32_t* dd, int64_t nd, const int32_t* is,
@@ -416,6 +826,7 @@ int apply_batch_device(Graph* g, const int32_t* ds, const int32_t* dd, int64_t n
   int bits = g->id_bits;
   int32_t n = g->n;
   int64_t nk = nd + ni;
+  if (nk > 0 && nk <= SMALL_MAX) return apply_small(g, ds, dd, nd, is, id, ni);
   size_t need;
   {
     Carve probe(nullptr);
@@ -487,7 +898,7 @@ int apply_batch_device(Graph* g, const int32_t* ds, const int32_t* dd, int64_t n
 
   // out-CSR: lists are sorted by (src, dst)
   bool rep_out = false, rep_in = false;
-  int rc = edit_direction(g, &g->out, g->dmin, hc[0], g->dplus, hc[1], &rep_out);
+  int rc = edit_direction(g, &g->out, g->dmin, hc[0], g->dplus, hc[1], cnts + 1, &rep_out);
   if (rc) return rc;
   // in-CSR: the same lists keyed (dst, src)
   {
@@ -516,7 +927,7 @@ int apply_batch_device(Graph* g, const int32_t* ds, const int32_t* dd, int64_t n
       note_launch(); k_swap_keys<<<grid_for(b, 256), 256, 0, s>>>(g->dplus, b, bits, si);
       TRY(radix_sort_u64(si, alt2, b, 2 * bits, tmp2, s));
     }
-    rc = edit_direction(g, &g->in, sd, a, si, b, &rep_in);
+    rc = edit_direction(g, &g->in, sd, a, si, b, cnts + 1, &rep_in);
     if (rc) return rc;
   }
   if (rep_in) {

@@ -91,7 +91,8 @@ struct Graph {
   Ctl* ctl = nullptr;       // device
   Ctl* ctl_h = nullptr;     // pinned host mirror
 
-  Scratch scr[6];
+  Scratch scr[8];
+  void* small_h = nullptr;  // pinned host copy of the small-batch status (batch.cu)
   std::vector<void*> allocs;
   std::string err;
 };

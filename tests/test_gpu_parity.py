@@ -73,8 +73,10 @@ def batches(n, src, dst, count, size, seed):
     return out
 
 
-@pytest.mark.parametrize("scale,size", [(6, 20), (10, 300), (14, 262)])
+@pytest.mark.parametrize("scale,size", [(6, 20), (10, 300), (14, 262), (12, 4000), (14, 20000)])
 def test_batch_edit_matches_oracle(lib, scale, size):
+    """Batches up to 4096 edges take the one-block ingest path, larger ones the
+    multi-kernel path; both must be bit-exact."""
     n = 1 << scale
     src, dst = synth.rmat(scale, 16 * n, 200 + scale)
     G, O = make_pair(lib, n, src, dst)
@@ -86,6 +88,32 @@ def test_batch_edit_matches_oracle(lib, scale, size):
         assert np.array_equal(gd, od) and np.array_equal(gp, op)
         assert G.m == O.m
         assert_same_graph(G, O)
+
+
+def test_small_batch_on_hub_rows(lib):
+    """A small batch touching rows longer than the small path's first staging
+    buffer (64K elements): the device skips the direction, the host grows the
+    buffer and finishes it."""
+    n = 1 << 18
+    rng = np.random.default_rng(3)
+    hub_out = np.arange(1, 150001, dtype=np.int32)
+    src = np.concatenate([np.zeros(hub_out.size, np.int32), hub_out, rng.integers(0, n, 50000).astype(np.int32)])
+    dst = np.concatenate([hub_out, np.zeros(hub_out.size, np.int32), rng.integers(0, n, 50000).astype(np.int32)])
+    G, O = make_pair(lib, n, src, dst)
+    G.update("static")
+    r0 = G.ranks()
+    b = (np.array([0, 5, 7], np.int32), np.array([10, 0, 0], np.int32),
+         np.array([0, 200000, 0], np.int32), np.array([200001, 0, 5], np.int32))
+    G.apply_batch(*b)
+    O.apply_batch(*b)
+    assert_same_graph(G, O)
+    dm, dp = G.effective_delta()
+    odm, odp = O.effective_delta()
+    assert np.array_equal(dm, odm) and np.array_equal(dp, odp)
+    G.set_ranks(r0)
+    G.update("dfp")
+    ref, _ = O.update("dfp", r_prev=r0)
+    assert np.max(np.abs(G.ranks() - ref)) < TOL
 
 
 def test_batch_overflow_repacks(lib):
