@@ -77,6 +77,16 @@ typedef struct {
  * frontier's size; the result is the same in every form. */
 #define PR_OPT_FORCE_PULL 2
 #define PR_OPT_FORCE_PUSH 4
+/* pr_options.flags for Static, ND, DF and DF-P: where the iteration loop runs.
+ * The host loop reads the iteration's change back after every sweep and picks
+ * the sweep form; the device loop runs the iterations as a CUDA graph whose
+ * WHILE node is driven by a control kernel (the pull form only, no host round
+ * trip).  By default graphs below PR_DEVICE_LOOP_SLOTS in-CSR slots use the
+ * device loop unless another flag asks for the host loop (any of the flags
+ * above).  The result is the same either way. */
+#define PR_OPT_DEVICE_LOOP 8
+#define PR_OPT_HOST_LOOP 16
+#define PR_DEVICE_LOOP_SLOTS (1ll << 24)
 
 /* Outcome of one pr_update (Sec. 5.1.5 measures time and affected vertices). */
 typedef struct {

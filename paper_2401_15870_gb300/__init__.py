@@ -197,14 +197,18 @@ def pr_apply_batch_device(h, del_src=None, del_dst=None, ins_src=None, ins_dst=N
 
 
 PR_OPT_TIME_SWEEPS, PR_OPT_FORCE_PULL, PR_OPT_FORCE_PUSH = 1, 2, 4
+PR_OPT_DEVICE_LOOP, PR_OPT_HOST_LOOP = 8, 16
+PR_DEVICE_LOOP_SLOTS = 1 << 24
 
 
 def pr_update(h, method, alpha=0.85, tau=1e-10, tau_f=1e-6, tau_p=1e-6, max_iter=500, time_sweeps=False,
-              direction=None) -> Stats:
-    """direction: None (chosen per iteration), "pull" or "push" (DF / DF-P)."""
+              direction=None, loop=None) -> Stats:
+    """direction: None (chosen per iteration), "pull" or "push" (DF / DF-P, host loop).
+    loop: None (by graph size), "device" or "host"."""
     m = METHODS[method] if isinstance(method, str) else int(method)
     flags = (PR_OPT_TIME_SWEEPS if time_sweeps else 0) | {None: 0, "pull": PR_OPT_FORCE_PULL,
                                                           "push": PR_OPT_FORCE_PUSH}[direction]
+    flags |= {None: 0, "device": PR_OPT_DEVICE_LOOP, "host": PR_OPT_HOST_LOOP}[loop]
     opts = pr_options(tau_f, tau_p, int(max_iter), flags)
     st = pr_stats()
     _check(load().pr_update(h, m, float(alpha), float(tau), ctypes.byref(opts), ctypes.byref(st)), h)

@@ -205,6 +205,7 @@ static pr_status finish_create(pr_graph* h, uint64_t* keys, int64_t nkeys, pr_gr
 
 static void destroy_handle(pr_graph* h) {
   if (!h) return;
+  if (h->solo) pr_group_destroy(h->solo);
   Graph* g = &h->g;
   if (g->stream) cudaStreamSynchronize(g->stream);
   dfree_all(g);
@@ -705,6 +706,10 @@ pr_status pr_set_stream(pr_graph* h, void* stream) {
   Graph* g = &h->g;
   TRY(cudaStreamSynchronize(g->stream));
   g->stream = (cudaStream_t)stream;
+  if (h->solo) {   // rebuilt on the new stream when next used
+    pr_group_destroy(h->solo);
+    h->solo = nullptr;
+  }
   return PR_OK;
 }
 
@@ -774,14 +779,30 @@ pr_status pr_update(pr_graph* h, pr_method method, double alpha, double tau, con
     tau_p = opts->tau_p;
     max_iter = opts->max_iter;
     flags = opts->flags;
-    if (flags & ~(PR_OPT_TIME_SWEEPS | PR_OPT_FORCE_PULL | PR_OPT_FORCE_PUSH)) return PR_EINVAL;
+    if (flags & ~(PR_OPT_TIME_SWEEPS | PR_OPT_FORCE_PULL | PR_OPT_FORCE_PUSH | PR_OPT_DEVICE_LOOP | PR_OPT_HOST_LOOP))
+      return PR_EINVAL;
     if ((flags & PR_OPT_FORCE_PULL) && (flags & PR_OPT_FORCE_PUSH)) return PR_EINVAL;
+    if ((flags & PR_OPT_DEVICE_LOOP) &&
+        (flags & (PR_OPT_HOST_LOOP | PR_OPT_TIME_SWEEPS | PR_OPT_FORCE_PULL | PR_OPT_FORCE_PUSH)))
+      return PR_EINVAL;
   }
   if ((int)method < PR_STATIC || (int)method > PR_DFP) return PR_EINVAL;
   if (!(alpha >= 0.0 && alpha < 1.0) || !(tau >= 0.0) || !(tau_f >= 0.0) || !(tau_p >= 0.0) || max_iter < 0)
     return PR_EINVAL;
   if (method != PR_STATIC && !g->has_ranks)
     return (pr_status)set_error(g, ENORANKS_, "pr_update: a dynamic method needs ranks (pr_set_ranks or a previous update)");
+  const bool host_flags = flags & (PR_OPT_HOST_LOOP | PR_OPT_TIME_SWEEPS | PR_OPT_FORCE_PULL | PR_OPT_FORCE_PUSH);
+  const bool loopable = method != PR_DYNAMIC_TRAVERSAL;
+  if (loopable && ((flags & PR_OPT_DEVICE_LOOP) || (!host_flags && g->in.cap < PR_DEVICE_LOOP_SLOTS))) {
+    // the iteration loop on the device: a group of this one graph, on its stream
+    if (!h->solo) {
+      pr_graph* one[1] = {h};
+      pr_status st = pr_group_create(1, one, g->stream, &h->solo);
+      if (st != PR_OK) return st;
+    }
+    pr_options o = {tau_f, tau_p, max_iter, 0};
+    return pr_group_update(h->solo, method, alpha, tau, &o, stats);
+  }
   return run_update(h, (int)method, alpha, tau, tau_f, tau_p, max_iter, flags, stats);
 }
 

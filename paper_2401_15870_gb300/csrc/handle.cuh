@@ -11,4 +11,5 @@ struct pr_graph {
   int64_t* ls_tmp = nullptr;      // list scan scratch
   int64_t tiles_cap = 0;          // capacity of the tile tables
   double* vec_tmp = nullptr;      // n doubles (rank import / export)
+  struct pr_group* solo = nullptr;  // one-graph group behind the device loop of pr_update
 };

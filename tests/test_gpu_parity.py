@@ -238,6 +238,24 @@ def test_frontier_directions_agree_with_oracle(lib, method, direction, scale, bs
     assert st.vertices_ever_affected == pytest.approx(ost.vertices_ever_affected, rel=0.01)
 
 
+@pytest.mark.parametrize("method", ["static", "nd", "df", "dfp"])
+@pytest.mark.parametrize("scale,bsize", [(12, 40), (14, 262), (13, 3000)])
+def test_device_and_host_loops_agree_bitwise(lib, method, scale, bsize):
+    """The iteration loop on the device (CUDA graph, pull form) and on the host
+    give bit-identical ranks and statistics."""
+    G, O, r0 = rank_case(lib, scale, 16, bsize, 70 + scale)
+    out = []
+    for loop in ("device", "host"):
+        G.set_ranks(r0)
+        st = G.update(method, loop=loop)
+        out.append((G.ranks(), st.iterations, st.converged, st.vertices_ever_affected, st.vertices_processed,
+                    st.edges_processed))
+    assert np.array_equal(out[0][0], out[1][0])
+    assert out[0][1:] == out[1][1:]
+    ref, _ = O.update(method, r_prev=r0)
+    assert np.max(np.abs(out[0][0] - ref)) < TOL
+
+
 @pytest.mark.parametrize("method", ["df", "dfp"])
 @pytest.mark.parametrize("scale,bsize", [(12, 40), (14, 262), (13, 3000)])
 def test_frontier_directions_agree_bitwise(lib, method, scale, bsize):
