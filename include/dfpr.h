@@ -274,7 +274,78 @@ typedef struct pr_group pr_group;
 pr_status pr_group_create(int32_t count, pr_graph* const* graphs, void* stream, pr_group** out);
 pr_status pr_group_update(pr_group* grp, pr_method method, double alpha, double tau, const pr_options* opts,
                           pr_stats* stats);
+/* The same for the graphs at the given group positions only (count distinct
+ * indices in [0, group size)); the others are left as they are.  stats: NULL
+ * or one entry per graph of the group, by position; only the members' entries
+ * are written. */
+pr_status pr_group_update_members(pr_group* grp, pr_method method, double alpha, double tau,
+                                  const pr_options* opts, const int32_t* members, int32_t count, pr_stats* stats);
 void pr_group_destroy(pr_group* grp);
+
+/*
+ * Serving: a request loop over resident graphs.  The paper updates one graph
+ * per batch; a server accepts update batches for many graphs as they arrive
+ * (from any thread) and turns them into DF / DF-P updates on one worker
+ * thread.
+ *   PR_SERVE_GROUPED: continuous batching.  Requests of a graph that queue up
+ *     are merged in arrival order into one batch (per edge the last operation
+ *     wins, deletions of a request before its insertions; the resulting edge
+ *     set is the one the requests give one after another, Sec. 3.2).  Batches
+ *     are applied while the previous group update runs, and every graph with
+ *     an applied batch joins the next group update (one launch pair per
+ *     iteration for all of them, the loop on the device).  A round admits
+ *     graphs while their estimated batch scratch leaves hbm_reserve bytes of
+ *     device memory free and the round's edges stay within max_round_edges
+ *     (0: no cap); the first graph of a round is always admitted.
+ *   PR_SERVE_PLAIN: one pr_apply_batch + pr_update per request, in arrival
+ *     order (the baseline).
+ * While the server runs, the graphs' work is on a stream of the server's
+ * (pr_set_stream; the previous streams are restored by pr_server_destroy) and
+ * the caller must not use the graphs.  Every graph needs ranks.
+ */
+#define PR_SERVE_GROUPED 0
+#define PR_SERVE_PLAIN 1
+typedef struct {
+  int32_t mode;              /* PR_SERVE_GROUPED or PR_SERVE_PLAIN            */
+  int32_t method;            /* PR_DF or PR_DFP                               */
+  double alpha, tau;         /* as in pr_update                               */
+  pr_options opts;           /* tolerances and max_iter; flags must be 0      */
+  int64_t hbm_reserve;       /* device bytes a round leaves free (grouped)    */
+  int64_t max_round_edges;   /* batch edges admitted per round, 0: no cap     */
+} pr_server_options;
+
+/* Outcome of one request. */
+typedef struct {
+  int64_t ticket;
+  int32_t graph;
+  int32_t status;            /* pr_status of the apply / update that served it */
+  int64_t round;             /* update round; requests of one graph in one round were merged */
+  int32_t merged;            /* requests merged into that round's batch of this graph */
+  int32_t pad;
+  double t_submit;           /* pr_server_clock() seconds: submitted          */
+  double t_start;            /* its batch started to be applied               */
+  double t_done;             /* its graph's update finished (ranks ready)     */
+  pr_stats stats;            /* that update of its graph                      */
+} pr_request_info;
+
+typedef struct pr_server pr_server;
+/* count graphs (host array of handles; the server refers to them, destroy it
+ * first).  Errors: PR_EINVAL, PR_ENORANKS, PR_ENOMEM, PR_ECUDA. */
+pr_status pr_server_create(int32_t count, pr_graph* const* graphs, const pr_server_options* opts, pr_server** out);
+/* Queue a batch (host arrays in the caller's ids, copied before the call
+ * returns) for graph index `graph`; *ticket identifies the request.  Ids are
+ * checked here: PR_ERANGE rejects the request.  Thread-safe. */
+pr_status pr_server_submit(pr_server* srv, int32_t graph, const int32_t* del_src, const int32_t* del_dst,
+                           int64_t n_del, const int32_t* ins_src, const int32_t* ins_dst, int64_t n_ins,
+                           int64_t* ticket);
+/* Wait up to timeout_s seconds for a request; PR_ETIMEOUT if it is not done. */
+pr_status pr_server_wait(pr_server* srv, int64_t ticket, double timeout_s, pr_request_info* info);
+/* Wait up to timeout_s seconds until every submitted request is done. */
+pr_status pr_server_drain(pr_server* srv, double timeout_s);
+/* Seconds on the steady clock the request times use. */
+double pr_server_clock(void);
+/* Finish the submitted requests, stop the worker, restore the graphs' streams. */
+void pr_server_destroy(pr_server* srv);
 
 /* Number of CUDA kernels this library has launched in this process so far
  * (all graphs); the difference across a region counts its launches. */

@@ -97,6 +97,13 @@ def load():
         "pr_group_create": ([i32, _P, _P, ctypes.POINTER(_P)], ctypes.c_int),
         "pr_group_update": ([_P, ctypes.c_int, f64, f64, _P, _P], ctypes.c_int),
         "pr_group_destroy": ([_P], None),
+        "pr_group_update_members": ([_P, ctypes.c_int, f64, f64, _P, _P, i32, _P], ctypes.c_int),
+        "pr_server_create": ([i32, _P, _P, ctypes.POINTER(_P)], ctypes.c_int),
+        "pr_server_submit": ([_P, i32, _P, _P, i64, _P, _P, i64, ctypes.POINTER(i64)], ctypes.c_int),
+        "pr_server_wait": ([_P, i64, f64, _P], ctypes.c_int),
+        "pr_server_drain": ([_P, f64], ctypes.c_int),
+        "pr_server_clock": ([], f64),
+        "pr_server_destroy": ([_P], None),
     }
     for name, (args, res) in sig.items():
         f = getattr(lib, name)
@@ -341,6 +348,17 @@ def pr_group_update(q, method, alpha=0.85, tau=1e-10, tau_f=1e-6, tau_p=1e-6, ma
     return [_stats(x) for x in st]
 
 
+def pr_group_update_members(q, members, method, alpha=0.85, tau=1e-10, tau_f=1e-6, tau_p=1e-6, max_iter=500):
+    """Update only the graphs at the given group positions; returns {position: Stats}."""
+    m = METHODS[method] if isinstance(method, str) else int(method)
+    opts = pr_options(tau_f, tau_p, int(max_iter), 0)
+    mem = np.ascontiguousarray(np.asarray(members, np.int32))
+    st = (pr_stats * _group_sizes[q.value])()
+    _check(load().pr_group_update_members(q, m, float(alpha), float(tau), ctypes.byref(opts), mem.ctypes.data,
+                                          mem.size, st))
+    return {int(i): _stats(st[int(i)]) for i in mem}
+
+
 def pr_group_destroy(q):
     _group_sizes.pop(q.value, None)
     load().pr_group_destroy(q)
@@ -442,10 +460,96 @@ class Group:
     def update(self, method, **kw):
         return pr_group_update(self._q, method, **kw)
 
+    def update_members(self, members, method, **kw):
+        return pr_group_update_members(self._q, members, method, **kw)
+
     def close(self):
         if self._q:
             pr_group_destroy(self._q)
             self._q = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+# ------------------------------------------------------------------ serving
+
+PR_SERVE_GROUPED, PR_SERVE_PLAIN = 0, 1
+
+
+class pr_server_options(ctypes.Structure):
+    _fields_ = [("mode", ctypes.c_int32), ("method", ctypes.c_int32), ("alpha", ctypes.c_double),
+                ("tau", ctypes.c_double), ("opts", pr_options), ("hbm_reserve", ctypes.c_int64),
+                ("max_round_edges", ctypes.c_int64)]
+
+
+class pr_request_info(ctypes.Structure):
+    _fields_ = [("ticket", ctypes.c_int64), ("graph", ctypes.c_int32), ("status", ctypes.c_int32),
+                ("round", ctypes.c_int64), ("merged", ctypes.c_int32), ("pad", ctypes.c_int32),
+                ("t_submit", ctypes.c_double), ("t_start", ctypes.c_double), ("t_done", ctypes.c_double),
+                ("stats", pr_stats)]
+
+
+@dataclass
+class RequestInfo:
+    ticket: int
+    graph: int
+    status: int
+    round: int
+    merged: int
+    t_submit: float
+    t_start: float
+    t_done: float
+    stats: Stats
+
+
+def pr_server_clock() -> float:
+    return float(load().pr_server_clock())
+
+
+class Server:
+    """Request loop over resident graphs (pr_server_*); keeps its graphs alive."""
+
+    def __init__(self, graphs, mode="grouped", method="dfp", alpha=0.85, tau=1e-10, tau_f=1e-6, tau_p=1e-6,
+                 max_iter=500, hbm_reserve=0, max_round_edges=0):
+        self.graphs = list(graphs)
+        o = pr_server_options(PR_SERVE_GROUPED if mode == "grouped" else PR_SERVE_PLAIN,
+                              METHODS[method] if isinstance(method, str) else int(method), float(alpha),
+                              float(tau), pr_options(tau_f, tau_p, int(max_iter), 0), int(hbm_reserve),
+                              int(max_round_edges))
+        arr = (_P * len(self.graphs))(*[g.handle.value if isinstance(g.handle, _P) else g.handle
+                                        for g in self.graphs])
+        out = _P()
+        _check(load().pr_server_create(len(self.graphs), arr, ctypes.byref(o), ctypes.byref(out)))
+        self._s = out
+
+    def submit(self, graph, del_src=(), del_dst=(), ins_src=(), ins_dst=()):
+        ds, dsp = _host_i32(del_src)
+        dd, ddp = _host_i32(del_dst)
+        is_, isp = _host_i32(ins_src)
+        id_, idp = _host_i32(ins_dst)
+        if ds.size != dd.size or is_.size != id_.size:
+            raise ValueError("endpoint arrays differ in length")
+        t = ctypes.c_int64()
+        _check(load().pr_server_submit(self._s, int(graph), dsp, ddp, ds.size, isp, idp, is_.size, ctypes.byref(t)))
+        return t.value
+
+    def wait(self, ticket, timeout=600.0) -> RequestInfo:
+        info = pr_request_info()
+        _check(load().pr_server_wait(self._s, int(ticket), float(timeout), ctypes.byref(info)))
+        return RequestInfo(info.ticket, info.graph, info.status, info.round, info.merged, info.t_submit,
+                           info.t_start, info.t_done, _stats(info.stats))
+
+    def drain(self, timeout=600.0):
+        _check(load().pr_server_drain(self._s, float(timeout)))
+
+    def close(self):
+        if self._s:
+            load().pr_server_destroy(self._s)
+            self._s = None
 
     def __del__(self):
         try:

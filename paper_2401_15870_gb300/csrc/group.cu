@@ -28,6 +28,7 @@
 #include "handle.cuh"
 #include "prim.cuh"
 #include "pull_step.cuh"
+#include "group.cuh"
 
 using namespace dfpr;
 
@@ -324,6 +325,10 @@ struct pr_group {
   cudaGraphExec_t exec[2] = {nullptr, nullptr};
   cudaGraphConditionalHandle cond[2] = {0, 0};
   cudaEvent_t ev[3] = {nullptr, nullptr, nullptr};
+  // the update in flight: its members (group indices) and method
+  std::vector<int32_t> members;
+  bool in_flight = false;
+  pr_method cur_method = PR_DFP;
 };
 
 static void group_free(pr_group* q) {
@@ -444,18 +449,35 @@ pr_status pr_group_create(int32_t count, pr_graph* const* graphs, void* stream, 
 
 void pr_group_destroy(pr_group* q) { group_free(q); }
 
-pr_status pr_group_update(pr_group* q, pr_method method, double alpha, double tau, const pr_options* opts,
-                          pr_stats* stats) {
-  if (!q) return PR_EINVAL;
+}  // extern "C"
+
+// launch an update of the members (indices into the group; NULL: every graph)
+// on the group's stream without waiting for it
+pr_status group_launch(pr_group* q, pr_method method, double alpha, double tau, const pr_options* opts,
+                       const int32_t* members, int32_t nm) {
+  if (!q || q->in_flight) return PR_EINVAL;
   if (method != PR_STATIC && method != PR_NAIVE_DYNAMIC && method != PR_DF && method != PR_DFP) return PR_EINVAL;
   if (!(alpha >= 0.0 && alpha < 1.0) || !(tau >= 0.0)) return PR_EINVAL;
   pr_options o = {1e-6, 1e-6, 500, 0};
   if (opts) o = *opts;
   if (!(o.tau_f >= 0.0) || !(o.tau_p >= 0.0) || o.max_iter < 0) return PR_EINVAL;
-  const int G = q->G;
+  std::vector<int32_t>& mem = q->members;
+  mem.clear();
+  if (members) {
+    if (nm < 1 || nm > q->G) return PR_EINVAL;
+    std::vector<char> seen(q->G, 0);
+    for (int32_t i = 0; i < nm; i++) {
+      if (members[i] < 0 || members[i] >= q->G || seen[members[i]]) return PR_EINVAL;
+      seen[members[i]] = 1;
+      mem.push_back(members[i]);
+    }
+  } else {
+    for (int32_t i = 0; i < q->G; i++) mem.push_back(i);
+  }
+  const int G = (int)mem.size();
   if (method != PR_STATIC)
     for (int i = 0; i < G; i++)
-      if (!q->graphs[i]->g.has_ranks) return PR_ENORANKS;
+      if (!q->graphs[mem[i]]->g.has_ranks) return PR_ENORANKS;
   cudaStream_t s = q->stream;
   int64_t* wpre = q->h_pre;
   int64_t* fpre = wpre + (G + 1);
@@ -463,7 +485,7 @@ pr_status pr_group_update(pr_group* q, pr_method method, double alpha, double ta
   int64_t* dpre = bpre + (G + 1);
   wpre[0] = fpre[0] = bpre[0] = dpre[0] = 0;
   for (int i = 0; i < G; i++) {
-    Graph* g = &q->graphs[i]->g;
+    Graph* g = &q->graphs[mem[i]]->g;
     GDesc& d = q->h_desc[i];
     memset(&d, 0, sizeof(d));
     d.icol = g->in.col;
@@ -511,9 +533,9 @@ pr_status pr_group_update(pr_group* q, pr_method method, double alpha, double ta
   r.tab_sc = q->tab_sc;
   r.tab_cl = q->tab_cl;
 
-  // order after the work already queued on the graphs' streams
+  // order after the work already queued on the members' streams
   for (int i = 0; i < G; i++) {
-    cudaStream_t gs = q->graphs[i]->g.stream;
+    cudaStream_t gs = q->graphs[mem[i]]->g.stream;
     if (gs == s) continue;
     if (cudaEventRecord(q->ev[2], gs) != cudaSuccess || cudaStreamWaitEvent(s, q->ev[2], 0) != cudaSuccess)
       return PR_ECUDA;
@@ -537,19 +559,35 @@ pr_status pr_group_update(pr_group* q, pr_method method, double alpha, double ta
   if (cudaMemcpyAsync(q->h_state, q->d_state, sizeof(GState) * G, cudaMemcpyDeviceToHost, s) != cudaSuccess ||
       cudaMemcpyAsync(q->h_run, q->d_run, sizeof(GRun), cudaMemcpyDeviceToHost, s) != cudaSuccess)
     return PR_ECUDA;
-  if (cudaEventRecord(q->ev[1], s) != cudaSuccess || cudaEventSynchronize(q->ev[1]) != cudaSuccess) return PR_ECUDA;
+  if (cudaEventRecord(q->ev[1], s) != cudaSuccess) return PR_ECUDA;
+  q->in_flight = true;
+  q->cur_method = method;
+  return PR_OK;
+}
+
+// true when the launched update has finished (does not block)
+bool group_done(pr_group* q) { return !q->in_flight || cudaEventQuery(q->ev[1]) != cudaErrorNotReady; }
+
+// wait for the launched update; stats (NULL or one entry per graph of the
+// group, by group index) are written for the members
+pr_status group_complete(pr_group* q, pr_stats* stats) {
+  if (!q || !q->in_flight) return PR_EINVAL;
+  q->in_flight = false;
+  if (cudaEventSynchronize(q->ev[1]) != cudaSuccess) return PR_ECUDA;
+  const pr_method method = q->cur_method;
   float ms = 0.f;
   cudaEventElapsedTime(&ms, q->ev[0], q->ev[1]);
   // kernels the CUDA graph ran: init, mark, and three per loop pass
   note_launches(2ull + 3ull * (unsigned long long)q->h_run->loops);
-  for (int i = 0; i < G; i++) {
-    pr_graph* h = q->graphs[i];
+  for (size_t i = 0; i < q->members.size(); i++) {
+    const int32_t gi = q->members[i];
+    pr_graph* h = q->graphs[gi];
     Graph* g = &h->g;
     const GState& st = q->h_state[i];
     if (st.cur) g->ccur ^= 1;
     g->has_ranks = true;
     if (stats) {
-      pr_stats& o2 = stats[i];
+      pr_stats& o2 = stats[gi];
       memset(&o2, 0, sizeof(o2));
       double dR;
       memcpy(&dR, &st.dR_last, sizeof(dR));
@@ -571,4 +609,19 @@ pr_status pr_group_update(pr_group* q, pr_method method, double alpha, double ta
   return PR_OK;
 }
 
+extern "C" {
+
+pr_status pr_group_update(pr_group* q, pr_method method, double alpha, double tau, const pr_options* opts,
+                          pr_stats* stats) {
+  return pr_group_update_members(q, method, alpha, tau, opts, nullptr, 0, stats);
+}
+
+pr_status pr_group_update_members(pr_group* q, pr_method method, double alpha, double tau, const pr_options* opts,
+                                  const int32_t* members, int32_t count, pr_stats* stats) {
+  pr_status st = group_launch(q, method, alpha, tau, opts, members, count);
+  if (st != PR_OK) return st;
+  return group_complete(q, stats);
+}
+
 }  // extern "C"
+

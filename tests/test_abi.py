@@ -69,3 +69,30 @@ def test_product_path_has_no_oracle_or_cpu_fallback():
                 text = open(os.path.join(dirpath, f)).read()
                 assert "import oracle" not in text and "from oracle" not in text
                 assert "dfpr_oracle" not in text and "liboracle" not in text
+
+
+def test_binding_structs_match_the_header(tmp_path):
+    """Sizes and field offsets of the ctypes mirrors equal those gcc computes
+    from include/dfpr.h."""
+    import shutil
+    import subprocess
+    if not shutil.which("gcc"):
+        pytest.skip("gcc not found")
+    import paper_2401_15870_gb300 as pr
+    structs = {"pr_options": pr.pr_options, "pr_stats": pr.pr_stats, "pr_server_options": pr.pr_server_options,
+               "pr_request_info": pr.pr_request_info}
+    lines = ['#include <stdio.h>', '#include <stddef.h>', '#include "dfpr.h"', "int main(void) {"]
+    for name, cls in structs.items():
+        lines.append('printf("%s %%zu\\n", sizeof(%s));' % (name, name))
+        for field, _ in cls._fields_:
+            lines.append('printf("%s.%s %%zu\\n", offsetof(%s, %s));' % (name, field, name, field))
+    lines.append("return 0; }")
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines))
+    exe = tmp_path / "layout"
+    subprocess.check_call(["gcc", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)])
+    got = dict(line.split() for line in subprocess.check_output([str(exe)]).decode().splitlines())
+    for name, cls in structs.items():
+        assert int(got[name]) == ctypes.sizeof(cls), name
+        for field, _ in cls._fields_:
+            assert int(got[name + "." + field]) == getattr(cls, field).offset, (name, field)
