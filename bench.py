@@ -53,8 +53,11 @@ def parse():
     ap.add_argument("--seed", type=int, default=2000)
     ap.add_argument("--e2e-steps", type=int, default=5)
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--workload", default="large", choices=["large", "batched"],
-                    help="large: one R-MAT scale-25 graph (default); batched: a group of R-MAT graphs updated together")
+    ap.add_argument("--workload", default="large", choices=["large", "batched", "serving"],
+                    help="large: one R-MAT scale-25 graph (default); batched: a group of R-MAT graphs updated "
+                         "together; serving: Poisson request arrivals for resident graphs")
+    ap.add_argument("--rates", default="50,200,500,1000,2000", help="serving: arrival rates (requests/s)")
+    ap.add_argument("--max-requests", type=int, default=400, help="serving: requests per rate at most")
     ap.add_argument("--graphs", type=int, default=64, help="batched: graphs in the group")
     return ap.parse_args()
 
@@ -433,6 +436,109 @@ def run_batched(a, rank, world, local_rank):
     grp.close()
 
 
+# ------------------------------------------------------------------ serving workload
+
+def serving_name(a):
+    return ("16 resident R-MAT graphs (scales 18..24 uniform, edge factor 16), requests with Poisson arrivals, "
+            "batch sizes log-uniform in 10..1e5 edges (80/20), DF-P; server (pr_server, grouped: coalescing + "
+            "group updates overlapping batch edits) vs one pr_apply_batch + pr_update per request")
+
+
+def run_serving(a, rank, world, local_rank):
+    import threading
+
+    import numpy as np
+    import torch
+
+    import paper_2401_15870_gb300 as pr
+    import synth.gpu as sg
+
+    torch.cuda.set_device(local_rank)
+    rng = np.random.default_rng(a.seed + 5)
+    specs = [(int(rng.integers(18, 25)), 16, a.seed + 3000 + 17 * i) for i in range(16)]
+    graphs, cands = [], []
+    for scale, ef, seed in specs:
+        n = 1 << scale
+        src, dst = sg.rmat(scale, ef << scale, seed)
+        graphs.append(pr.Graph.from_edges(n, src, dst, device=True))
+        cands.append((n, src, dst))
+    torch.cuda.synchronize()
+    grp = pr.Group(graphs)
+    grp.update("static", alpha=ALPHA, tau=TAU)
+    grp.close()
+    rates = [float(x) for x in a.rates.split(",")]
+
+    def requests(rate, k0):
+        """Poisson arrivals: (arrival offset s, graph, host batch).  The arrival
+        times, graphs and sizes depend on the rate only; the edges on k0, so each
+        arm gets batches of its own (a batch applied twice changes nothing)."""
+        r2 = np.random.default_rng(a.seed + int(rate))
+        count = max(20, min(a.max_requests, int(rate * 1.0)))
+        t = np.cumsum(r2.exponential(1.0 / rate, count))
+        out = []
+        for i in range(count):
+            g = int(r2.integers(0, len(graphs)))
+            size = int(round(10 ** r2.uniform(1, 5)))
+            n, src, dst = cands[g]
+            b = sg.batch(n, src, dst, size, k0 + i)
+            out.append((float(t[i]), g, [x.cpu().numpy() for x in b]))
+        return out
+
+    def serve(mode, reqs):
+        srv = pr.Server(graphs, mode=mode, method="dfp", alpha=ALPHA, tau=TAU)
+        tickets = []
+        t0 = pr.pr_server_clock()
+
+        def submitter():
+            for at, g, b in reqs:
+                dt = t0 + at - pr.pr_server_clock()
+                if dt > 0:
+                    time.sleep(dt)
+                tickets.append(srv.submit(g, *b))
+        th = threading.Thread(target=submitter)
+        th.start()
+        th.join()
+        srv.drain(3600)
+        infos = [srv.wait(t, 60) for t in tickets]
+        srv.close()
+        lat = np.array([i.t_done - i.t_submit for i in infos]) * 1000.0
+        span = max(i.t_done for i in infos) - t0
+        rounds = len({i.round for i in infos})
+        return {"updates_per_s": len(infos) / span, "p50_ms": float(np.percentile(lat, 50)),
+                "p99_ms": float(np.percentile(lat, 99)), "requests": len(infos), "rounds": rounds,
+                "mean_merged": float(np.mean([i.merged for i in infos])),
+                "iterations_mean": float(np.mean([i.stats.iterations for i in infos])),
+                "eff_edges_mean": float(np.mean([i.stats.eff_insertions + i.stats.eff_deletions for i in infos])),
+                "failed": int(sum(1 for i in infos if i.status != 0))}
+
+    rows = []
+    l0 = pr.pr_kernel_launches()
+    for k, rate in enumerate(rates):
+        row = {"rate_per_s": rate}
+        for j, mode in enumerate(("grouped", "plain")):
+            reqs = requests(rate, a.seed + 100000 * (k + 1) + 50000 * j)
+            row["batch_edges_mean"] = float(np.mean([len(b[0]) + len(b[2]) for _, _, b in reqs]))
+            row[mode] = serve(mode, reqs)
+        rows.append(row)
+    launches = pr.pr_kernel_launches() - l0
+    if rank != 0:
+        return
+    top = rows[-1]
+    line = {
+        "metric": METRIC, "value": top["grouped"]["updates_per_s"], "unit": "served updates/s", "n_gpus": world,
+        "steps": sum(r["grouped"]["requests"] for r in rows), "warmup": 0, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": serving_name(a), "graphs": len(graphs), "scales": [s for s, _, _ in specs],
+                   "edges": sum(g.m for g in graphs), "inputs": "host batches through pr_server_submit; ranks "
+                   "ready on the device at completion", "parallelism": "single GPU"},
+        "p50_ms": top["grouped"]["p50_ms"], "p99_ms": top["grouped"]["p99_ms"],
+        "plain": {"value": top["plain"]["updates_per_s"], "p50_ms": top["plain"]["p50_ms"],
+                  "p99_ms": top["plain"]["p99_ms"]},
+        "rates": rows, "gpu_launches": launches,
+    }
+    print(json.dumps(line), flush=True)
+
+
 def main():
     a = parse()
     rank = int(os.environ.get("RANK", "0"))
@@ -448,6 +554,8 @@ def main():
     try:
         if a.workload == "batched":
             run_batched(a, rank, world, local_rank)
+        elif a.workload == "serving":
+            run_serving(a, rank, world, local_rank)
         else:
             run_gpu(a, rank, world, local_rank)
     finally:

@@ -15,7 +15,8 @@
 //      on the graphs' stream -- this overlaps with the group update already
 //      running on the group stream;
 //   3. when no update is running, launch one group update (pr_group machinery)
-//      over every READY graph;
+//      over every READY graph (a lone READY graph with nothing else queued
+//      runs pr_update instead, whose host loop may pick the push form);
 //   4. when the running update has finished, complete its requests.
 // A request that arrives for a READY or IN_FLIGHT graph waits for the next
 // round of that graph, so the batches of a graph are applied in arrival order.
@@ -273,7 +274,26 @@ void run_grouped(pr_server* S) {
       S->members.clear();
       for (int i = 0; i < G; i++)
         if (S->state[i] == READY) S->members.push_back(i);
-      if (!S->members.empty()) {
+      bool alone = false;
+      if (S->members.size() == 1) {
+        std::lock_guard<std::mutex> lk(S->mu);
+        alone = S->pending.empty();
+      }
+      if (alone) {
+        // one graph and no other work: its own update, with the direction
+        // choice of pr_update (cheaper than the pull-only group form on a
+        // large graph whose frontier starts small)
+        const int32_t gi = S->members[0];
+        pr_stats st;
+        memset(&st, 0, sizeof(st));
+        pr_status rc = pr_update(S->graphs[gi], (pr_method)S->opt.method, S->opt.alpha, S->opt.tau, &S->opt.opts,
+                                 &st);
+        finish_requests(S, S->ready_reqs[gi], rc, S->round++, S->t_start[gi], &st);
+        S->ready_bytes = 0;
+        S->ready_edges = 0;
+        std::lock_guard<std::mutex> lk(S->mu);
+        S->state[gi] = IDLE;
+      } else if (!S->members.empty()) {
         pr_status rc = group_launch(S->group, (pr_method)S->opt.method, S->opt.alpha, S->opt.tau, &S->opt.opts,
                                     S->members.data(), (int32_t)S->members.size());
         if (rc != PR_OK) {
