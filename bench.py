@@ -53,11 +53,14 @@ def parse():
     ap.add_argument("--seed", type=int, default=2000)
     ap.add_argument("--e2e-steps", type=int, default=5)
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--workload", default="large", choices=["large", "batched", "serving"],
+    ap.add_argument("--workload", default="large", choices=["large", "batched", "serving", "methods"],
                     help="large: one R-MAT scale-25 graph (default); batched: a group of R-MAT graphs updated "
                          "together; serving: Poisson request arrivals for resident graphs")
     ap.add_argument("--rates", default="50,200,500,1000,2000", help="serving: arrival rates (requests/s)")
     ap.add_argument("--max-requests", type=int, default=400, help="serving: requests per rate at most")
+    ap.add_argument("--batch-fracs", default="1e-7,1e-6,1e-5,1e-4,1e-3,1e-2,1e-1",
+                    help="methods: batch sizes as fractions of |E|")
+    ap.add_argument("--reps", type=int, default=1, help="methods: batches per size")
     ap.add_argument("--graphs", type=int, default=64, help="batched: graphs in the group")
     return ap.parse_args()
 
@@ -539,6 +542,96 @@ def run_serving(a, rank, world, local_rank):
     print(json.dumps(line), flush=True)
 
 
+# ------------------------------------------------------------------ every method over batch sizes
+
+def run_methods(a, rank, world, local_rank):
+    """Static, ND, DT, DF and DF-P from the same previous ranks after one batch
+    of each size: apply and update times, updated edges/s, iterations, share
+    of vertices processed, bytes moved per second, and the L1 error against a
+    Static solve of 500 iterations at tau = 0 (the paper's reference solve).
+    The graph is put back after every batch by applying its inverse (the
+    effective insertions deleted, the effective deletions re-inserted).  On
+    graphs of at most 2^16 vertices the CPU oracle runs the same methods on the
+    same batch beside it."""
+    import numpy as np
+    import torch
+
+    import paper_2401_15870_gb300 as pr
+    import synth.gpu as sg
+
+    torch.cuda.set_device(local_rank)
+    n = 1 << a.scale
+    src, dst = sg.rmat(a.scale, a.edge_factor << a.scale, a.seed)
+    G = pr.Graph.from_edges(n, src, dst, device=True)
+    m0 = G.m
+    st0 = G.update("static", alpha=ALPHA, tau=TAU)
+    r_prev = G.ranks()
+    O = None
+    if a.scale <= 16:
+        import oracle
+        O = oracle.Graph(n, src.cpu().numpy(), dst.cpu().numpy())
+    peaks = {}
+    try:
+        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except (OSError, ValueError):
+        pass
+    peak = float(peaks.get("hbm_gbs", 6800.0))
+    rows = []
+    for frac in [float(x) for x in a.batch_fracs.split(",")]:
+        size = max(1, int(round(frac * m0)))
+        for rep in range(a.reps):
+            b = sg.batch(n, src, dst, size, a.seed + 1 + rep + int(round(1e9 * frac)) % 100003)
+            torch.cuda.synchronize()
+            G.set_ranks(r_prev)
+            G.apply_batch_device(*b)
+            if O is not None:
+                O.apply_batch(*[x.cpu().numpy() for x in b])
+            ref = G.update("static", alpha=ALPHA, tau=0.0, max_iter=500)
+            r_ref = G.ranks()
+            for method in ("static", "nd", "dt", "df", "dfp"):
+                G.set_ranks(r_prev)
+                st = G.update(method, alpha=ALPHA, tau=TAU)
+                r = G.ranks()
+                eff = st.eff_insertions + st.eff_deletions
+                row = {"batch_frac": frac, "batch_edges": size, "effective_edges": eff, "method": method,
+                       "ms_apply": st.ms_apply, "ms_update": st.ms_update,
+                       "updated_edges_per_s": eff / ((st.ms_apply + st.ms_update) / 1000.0),
+                       "iterations": st.iterations, "converged": st.converged,
+                       "affected_share": st.vertices_ever_affected / n,
+                       "gbs": (SWEEP_BYTES_PER_EDGE * st.edges_processed +
+                               (40 if method in ("static", "nd") else SWEEP_BYTES_PER_VERTEX) *
+                               st.vertices_processed) / (st.ms_update / 1000.0) / 1e9,
+                       "l1_error": float(np.abs(r - r_ref).sum()), "linf_error": float(np.abs(r - r_ref).max())}
+                row["hbm_frac"] = row["gbs"] / peak
+                if O is not None:
+                    t0 = time.perf_counter()
+                    ro, ost = O.update(method, alpha=ALPHA, tau=TAU, r_prev=None if method == "static" else r_prev)
+                    row["oracle_ms"] = (time.perf_counter() - t0) * 1000.0
+                    row["oracle_linf_diff"] = float(np.abs(r - ro).max())
+                    row["oracle_iterations"] = ost.iterations
+                rows.append(row)
+            row_ref = {"batch_frac": frac, "method": "reference static (500 iterations, tau = 0)",
+                       "iterations": ref.iterations, "ms_update": ref.ms_update}
+            rows.append(row_ref)
+            # put the graph back
+            dm, dp = G.effective_delta()
+            G.apply_batch(dp[:, 0], dp[:, 1], dm[:, 0], dm[:, 1])
+            if O is not None:
+                O.apply_batch(dp[:, 0], dp[:, 1], dm[:, 0], dm[:, 1])
+    if rank != 0:
+        return
+    dfp = [r for r in rows if r.get("method") == "dfp"]
+    line = {
+        "metric": METRIC, "value": statistics.mean(r["ms_apply"] + r["ms_update"] for r in dfp),
+        "unit": "ms per DF-P batch update (mean over batch sizes)", "n_gpus": world, "higher_is_better": False,
+        "dtype": "f64", "data": "synthetic",
+        "config": {"workload": "R-MAT scale %d, edge factor %d; every method after one random 80/20 batch per size"
+                   % (a.scale, a.edge_factor), "vertices": n, "edges": m0, "static_iterations": st0.iterations},
+        "peak_gbs": peak, "rows": rows,
+    }
+    print(json.dumps(line), flush=True)
+
+
 def main():
     a = parse()
     rank = int(os.environ.get("RANK", "0"))
@@ -556,6 +649,8 @@ def main():
             run_batched(a, rank, world, local_rank)
         elif a.workload == "serving":
             run_serving(a, rank, world, local_rank)
+        elif a.workload == "methods":
+            run_methods(a, rank, world, local_rank)
         else:
             run_gpu(a, rank, world, local_rank)
     finally:

@@ -277,28 +277,57 @@ __global__ void k_row_degrees(const uint64_t* __restrict__ rows, const int64_t* 
   }
 }
 
-// repack: every surviving edge of a direction as a packed key (row << bits | col)
-__global__ void k_materialize(const int64_t* __restrict__ off, const int32_t* __restrict__ deg,
-                              const int32_t* __restrict__ col, int32_t n, const uint64_t* __restrict__ dl, int64_t nd,
-                              int bits, const int64_t* __restrict__ pos, uint64_t* __restrict__ out) {
+// repack of a direction, pass 1: per row the new degree and the new capacity
+// (round4(degree) + 8 slots of slack)
+__global__ void k_repack_plan(const int32_t* __restrict__ deg, int32_t n, const uint64_t* __restrict__ dl, int64_t nd,
+                              const uint64_t* __restrict__ il, int64_t ni, int bits, int32_t* __restrict__ newdeg,
+                              int64_t* __restrict__ cap) {
   GRID_STRIDE(r, n) {
-    int64_t w = pos[r];
-    uint64_t rk = (uint64_t)r << bits;
-    int64_t d0 = lower_key(dl, 0, nd, rk), d1 = lower_key(dl, d0, nd, rk + (1ull << bits));
-    for (int32_t x = 0; x < deg[r]; x++) {
-      uint64_t key = rk | (uint64_t)col[off[r] + x];
-      if (d1 > d0 && key_in(dl + d0, d1 - d0, key)) continue;
-      out[w++] = key;
-    }
+    const uint64_t rk = (uint64_t)r << bits, rk1 = (uint64_t)(r + 1) << bits;
+    const int64_t d0 = lower_key(dl, 0, nd, rk), d1 = lower_key(dl, d0, nd, rk1);
+    const int64_t i0 = lower_key(il, 0, ni, rk), i1 = lower_key(il, i0, ni, rk1);
+    const int64_t d = deg[r] - (d1 - d0) + (i1 - i0);
+    newdeg[r] = (int32_t)d;
+    cap[r] = round4(d) + 8;
   }
 }
 
-__global__ void k_surv_count(const int32_t* __restrict__ deg, int32_t n, const uint64_t* __restrict__ dl, int64_t nd,
-                             int bits, int64_t* __restrict__ cnt) {
-  GRID_STRIDE(r, n) {
-    uint64_t rk = (uint64_t)r << bits;
-    int64_t d0 = lower_key(dl, 0, nd, rk), d1 = lower_key(dl, d0, nd, rk + (1ull << bits));
-    cnt[r] = deg[r] - (d1 - d0);
+// pass 2, one warp per row: the surviving old elements and the insertions
+// merged into the new column array (both are sorted, so each element's output
+// position is its rank: survivors x -> i - #deletions below x + #insertions
+// below x, insertion y -> k + #old below y - #deletions below y), then the
+// padding slots get the sentinel
+__global__ void k_repack_rows(const int64_t* __restrict__ off, const int32_t* __restrict__ deg,
+                              const int32_t* __restrict__ col, int32_t n, const uint64_t* __restrict__ dl, int64_t nd,
+                              const uint64_t* __restrict__ il, int64_t ni, int bits, const int64_t* __restrict__ noff,
+                              const int32_t* __restrict__ ndeg, int32_t* __restrict__ ncol) {
+  const int lane = threadIdx.x & 31;
+  const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  const uint64_t mask = (1ull << bits) - 1;
+  for (int64_t r = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5; r < n; r += nw) {
+    const uint64_t rk = (uint64_t)r << bits, rk1 = (uint64_t)(r + 1) << bits;
+    const int64_t d0 = lower_key(dl, 0, nd, rk), d1 = lower_key(dl, d0, nd, rk1);
+    const int64_t i0 = lower_key(il, 0, ni, rk), i1 = lower_key(il, i0, ni, rk1);
+    const int64_t base = off[r], nbase = noff[r], dg = deg[r];
+    const int32_t* row = col + base;
+    for (int64_t x = lane; x < dg; x += 32) {
+      const int32_t v = row[x];
+      const uint64_t key = rk | (uint64_t)v;
+      const int64_t dlt = lower_key(dl, d0, d1, key);
+      if (dlt < d1 && dl[dlt] == key) continue;   // deleted
+      ncol[nbase + x - (dlt - d0) + (lower_key(il, i0, i1, key) - i0)] = v;
+    }
+    for (int64_t k = i0 + lane; k < i1; k += 32) {
+      const int32_t y = (int32_t)(il[k] & mask);
+      int64_t a = 0, b = dg;   // old elements below y
+      while (a < b) {
+        const int64_t mid = (a + b) >> 1;
+        if (row[mid] < y) a = mid + 1;
+        else b = mid;
+      }
+      ncol[nbase + (k - i0) + a - (lower_key(dl, d0, d1, rk | (uint64_t)y) - d0)] = y;
+    }
+    for (int64_t x = ndeg[r] + lane; x < noff[r + 1] - nbase; x += 32) ncol[nbase + x] = n;
   }
 }
 
@@ -308,37 +337,63 @@ __global__ void k_u64_to_i32_low(const uint64_t* __restrict__ in, int64_t k, int
 
 // ------------------------------------------------------------------ host
 
-// a direction whose new rows do not fit their capacity is rebuilt: every
-// surviving edge plus the insertions, sorted, laid out with fresh slack
+// a direction whose new rows do not fit their capacity is rebuilt with fresh
+// slack: new degrees and capacities, their prefix as the new offsets, and the
+// rows merged straight into a new column array (no sort: the old rows and the
+// insertions are both sorted)
 static int repack_direction(Graph* g, Csr* c, const uint64_t* dl, int64_t nd, const uint64_t* il, int64_t ni) {
   cudaStream_t s = g->stream;
-  int bits = g->id_bits;
-  int32_t n = g->n;
-  int64_t* pos;
-  int64_t* pscr;
-  TRY(cudaMalloc(&pos, sizeof(int64_t) * (n + 1)));
-  TRY(cudaMalloc(&pscr, sizeof(int64_t) * scan_tmp_elems(n)));
-  note_launch(); k_surv_count<<<grid_for(n, 256), 256, 0, s>>>(c->deg, n, dl, nd, bits, pos);
-  TRY(scan_excl<int64_t>(pos, pos, n, pscr, s));
-  int64_t surv = 0;
-  TRY(cudaMemcpyAsync(&surv, pos + n, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
-  TRY(cudaStreamSynchronize(s));
-  int64_t mtot = surv + ni;
-  uint64_t *keys, *kalt;
-  void* rtmp;
-  TRY(cudaMalloc(&keys, sizeof(uint64_t) * (mtot + 1)));
-  TRY(cudaMalloc(&kalt, sizeof(uint64_t) * (mtot + 1)));
-  TRY(cudaMalloc(&rtmp, radix_tmp_bytes(mtot)));
-  note_launch(); k_materialize<<<grid_for(n, 128), 128, 0, s>>>(c->off, c->deg, c->col, n, dl, nd, bits, pos, keys);
-  if (ni) TRY(cudaMemcpyAsync(keys + surv, il, sizeof(uint64_t) * ni, cudaMemcpyDeviceToDevice, s));
-  TRY(radix_sort_u64(keys, kalt, mtot, 2 * bits, rtmp, s));
-  int rc = build_csr_from_sorted(g, c, keys, mtot, c == &g->in, 2);
-  cudaFree(pos);
-  cudaFree(pscr);
-  cudaFree(keys);
-  cudaFree(kalt);
-  cudaFree(rtmp);
-  return rc;
+  const int bits = g->id_bits;
+  const int32_t n = g->n;
+  int32_t* ndeg = nullptr;
+  int64_t *cap = nullptr, *noff = nullptr, *scr = nullptr;
+  int32_t* ncol = nullptr;
+  auto release = [&] {
+    cudaFree(ndeg);
+    cudaFree(cap);
+    cudaFree(noff);
+    cudaFree(scr);
+  };
+  cudaError_t e;
+  if ((e = cudaMalloc(&ndeg, sizeof(int32_t) * n)) != cudaSuccess ||
+      (e = cudaMalloc(&cap, sizeof(int64_t) * (n + 1))) != cudaSuccess ||
+      (e = cudaMalloc(&noff, sizeof(int64_t) * (n + 1))) != cudaSuccess ||
+      (e = cudaMalloc(&scr, sizeof(int64_t) * scan_tmp_elems(n))) != cudaSuccess) {
+    release();
+    return cuda_fail(g, e, "cudaMalloc(repack)");
+  }
+  note_launch(); k_repack_plan<<<grid_for(n, 256), 256, 0, s>>>(c->deg, n, dl, nd, il, ni, bits, ndeg, cap);
+  e = scan_excl<int64_t>(cap, noff, n, scr, s);
+  int64_t total = 0;
+  if (e == cudaSuccess) e = cudaMemcpyAsync(&total, noff + n, sizeof(int64_t), cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  if (e == cudaSuccess) e = cudaMalloc(&ncol, sizeof(int32_t) * (size_t)total);
+  if (e != cudaSuccess) {
+    release();
+    return cuda_fail(g, e, "repack");
+  }
+  note_launch(); k_repack_rows<<<num_sms() * 16, 256, 0, s>>>(c->off, c->deg, c->col, n, dl, nd, il, ni, bits, noff,
+                                                              ndeg, ncol);
+  e = cudaMemcpyAsync(c->off, noff, sizeof(int64_t) * (n + 1), cudaMemcpyDeviceToDevice, s);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(c->deg, ndeg, sizeof(int32_t) * n, cudaMemcpyDeviceToDevice, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  release();
+  if (e != cudaSuccess) {
+    cudaFree(ncol);
+    return cuda_fail(g, e, "repack");
+  }
+  // the new column array replaces the old one in the graph's allocations
+  bool owned = false;
+  for (auto& p : g->allocs)
+    if (p == c->col) {
+      cudaFree(p);
+      p = ncol;
+      owned = true;
+    }
+  if (!owned) g->allocs.push_back(ncol);
+  c->col = ncol;
+  c->cap = total;
+  return OK;
 }
 
 static int edit_direction(Graph* g, Csr* c, const uint64_t* dl, int64_t nd, const uint64_t* il, int64_t ni,
