@@ -53,7 +53,7 @@ def parse():
     ap.add_argument("--seed", type=int, default=2000)
     ap.add_argument("--e2e-steps", type=int, default=5)
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--workload", default="large", choices=["large", "batched", "serving", "methods"],
+    ap.add_argument("--workload", default="large", choices=["large", "batched", "serving", "methods", "temporal"],
                     help="large: one R-MAT scale-25 graph (default); batched: a group of R-MAT graphs updated "
                          "together; serving: Poisson request arrivals for resident graphs")
     ap.add_argument("--rates", default="50,200,500,1000,2000", help="serving: arrival rates (requests/s)")
@@ -61,6 +61,7 @@ def parse():
     ap.add_argument("--batch-fracs", default="1e-7,1e-6,1e-5,1e-4,1e-3,1e-2,1e-1",
                     help="methods: batch sizes as fractions of |E|")
     ap.add_argument("--reps", type=int, default=1, help="methods: batches per size")
+    ap.add_argument("--temporal-batches", type=int, default=100, help="temporal: consecutive batches per size")
     ap.add_argument("--graphs", type=int, default=64, help="batched: graphs in the group")
     return ap.parse_args()
 
@@ -632,6 +633,88 @@ def run_methods(a, rank, world, local_rank):
     print(json.dumps(line), flush=True)
 
 
+# ------------------------------------------------------------------ temporal stream
+
+def run_temporal(a, rank, world, local_rank):
+    """A temporal edge stream of 2.6M vertices and 63M timestamped edges with
+    repeats (copying / preferential attachment): the first 90% is the base
+    graph; then consecutive insertion-only batches of 1e-5, 1e-4 and 1e-3 |E_T|
+    in timestamp order, each followed by DF-P from the previous ranks.  Every
+    tenth batch also runs DF and Static from the same previous ranks and a
+    Static solve of 500 iterations at tau = 0 as the reference for the L1 error."""
+    import numpy as np
+    import torch
+
+    import paper_2401_15870_gb300 as pr
+    import synth
+
+    torch.cuda.set_device(local_rank)
+    n, m_t = 2_600_000, 63_000_000
+    t0 = time.perf_counter()
+    src, dst = synth.temporal(n, m_t, a.seed + 77)
+    gen_s = time.perf_counter() - t0
+    base = int(0.9 * m_t)
+    out = []
+    for frac in (1e-5, 1e-4, 1e-3):
+        size = int(round(frac * m_t))
+        G = pr.Graph.from_edges(n, src[:base], dst[:base])
+        base_m = G.m
+        G.update("static", alpha=ALPHA, tau=TAU)
+        rec = {"batch_frac": frac, "batch_edges": size, "apply_ms": [], "dfp_ms": [], "dfp_iterations": [],
+               "eff_edges": [], "affected_share": [], "checks": []}
+        pos = base
+        for k in range(a.temporal_batches):
+            if pos + size > m_t:
+                break
+            bs, bd = src[pos:pos + size], dst[pos:pos + size]
+            pos += size
+            r_prev = G.ranks()
+            G.apply_batch(ins_src=bs, ins_dst=bd)
+            st = G.update("dfp", alpha=ALPHA, tau=TAU)
+            rec["apply_ms"].append(st.ms_apply)
+            rec["dfp_ms"].append(st.ms_update)
+            rec["dfp_iterations"].append(st.iterations)
+            rec["eff_edges"].append(st.eff_insertions)
+            rec["affected_share"].append(st.vertices_ever_affected / n)
+            if k % 10 == 9:
+                r_dfp = G.ranks()
+                chk = {"batch": k}
+                G.update("static", alpha=ALPHA, tau=0.0, max_iter=500)
+                r_ref = G.ranks()
+                chk["dfp_l1"] = float(np.abs(r_dfp - r_ref).sum())
+                for method in ("df", "static"):
+                    G.set_ranks(r_prev)
+                    s2 = G.update(method, alpha=ALPHA, tau=TAU)
+                    chk[method + "_ms"] = s2.ms_update
+                    chk[method + "_iterations"] = s2.iterations
+                    chk[method + "_l1"] = float(np.abs(G.ranks() - r_ref).sum())
+                rec["checks"].append(chk)
+                G.set_ranks(r_dfp)   # the stream goes on from the DF-P ranks
+        G.close()
+        summ = {"batch_frac": frac, "batch_edges": size, "batches": len(rec["dfp_ms"]),
+                "apply_ms_mean": statistics.mean(rec["apply_ms"]), "dfp_ms_mean": statistics.mean(rec["dfp_ms"]),
+                "dfp_iterations_mean": statistics.mean(rec["dfp_iterations"]),
+                "effective_edges_mean": statistics.mean(rec["eff_edges"]),
+                "affected_share_mean": statistics.mean(rec["affected_share"]),
+                "updated_edges_per_s": sum(rec["eff_edges"]) / ((sum(rec["apply_ms"]) + sum(rec["dfp_ms"])) / 1e3),
+                "static_ms_mean": statistics.mean(c["static_ms"] for c in rec["checks"]),
+                "df_ms_mean": statistics.mean(c["df_ms"] for c in rec["checks"]),
+                "dfp_l1_mean": statistics.mean(c["dfp_l1"] for c in rec["checks"]),
+                "df_l1_mean": statistics.mean(c["df_l1"] for c in rec["checks"]),
+                "static_l1_mean": statistics.mean(c["static_l1"] for c in rec["checks"])}
+        summ["dfp_speedup_vs_static"] = summ["static_ms_mean"] / summ["dfp_ms_mean"]
+        out.append(summ)
+    if rank != 0:
+        return
+    line = {"metric": METRIC, "value": out[1]["dfp_ms_mean"], "unit": "ms per DF-P update (1e-4 |E_T| batches)",
+            "n_gpus": world, "higher_is_better": False, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": "temporal stream (copying / preferential attachment with repeats), %d vertices, "
+                       "%d timestamped edges, base = first 90%%, consecutive insertion-only batches" % (n, m_t),
+                       "generation_s": gen_s, "base_edges_with_self_loops": base_m},
+            "sizes": out}
+    print(json.dumps(line), flush=True)
+
+
 def main():
     a = parse()
     rank = int(os.environ.get("RANK", "0"))
@@ -651,6 +734,8 @@ def main():
             run_serving(a, rank, world, local_rank)
         elif a.workload == "methods":
             run_methods(a, rank, world, local_rank)
+        elif a.workload == "temporal":
+            run_temporal(a, rank, world, local_rank)
         else:
             run_gpu(a, rank, world, local_rank)
     finally:

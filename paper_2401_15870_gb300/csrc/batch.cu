@@ -277,18 +277,24 @@ __global__ void k_row_degrees(const uint64_t* __restrict__ rows, const int64_t* 
   }
 }
 
-// repack of a direction, pass 1: per row the new degree and the new capacity
-// (round4(degree) + 8 slots of slack)
-__global__ void k_repack_plan(const int32_t* __restrict__ deg, int32_t n, const uint64_t* __restrict__ dl, int64_t nd,
-                              const uint64_t* __restrict__ il, int64_t ni, int bits, int32_t* __restrict__ newdeg,
-                              int64_t* __restrict__ cap) {
+// repack of a direction, pass 1: per row the new degree and the new capacity:
+// round4(degree) + 8 slots of slack, a quarter of the degree more for a row
+// that received insertions (rows that grew tend to grow again -- a hub of a
+// temporal stream -- and geometric slack makes their repacks rare), an eighth
+// more for every row of degree >= 64 once the direction has been repacked
+// before (the graph keeps growing), and never less than the row had
+__global__ void k_repack_plan(const int64_t* __restrict__ off, const int32_t* __restrict__ deg, int32_t n,
+                              const uint64_t* __restrict__ dl, int64_t nd, const uint64_t* __restrict__ il, int64_t ni,
+                              int bits, bool growing, int32_t* __restrict__ newdeg, int64_t* __restrict__ cap) {
   GRID_STRIDE(r, n) {
     const uint64_t rk = (uint64_t)r << bits, rk1 = (uint64_t)(r + 1) << bits;
     const int64_t d0 = lower_key(dl, 0, nd, rk), d1 = lower_key(dl, d0, nd, rk1);
     const int64_t i0 = lower_key(il, 0, ni, rk), i1 = lower_key(il, i0, ni, rk1);
     const int64_t d = deg[r] - (d1 - d0) + (i1 - i0);
     newdeg[r] = (int32_t)d;
-    cap[r] = round4(d) + 8;
+    const int64_t extra = i1 > i0 ? round4(d >> 2) : (growing && d >= 64 ? round4(d >> 3) : 0);
+    const int64_t want = round4(d) + 8 + extra, had = off[r + 1] - off[r];
+    cap[r] = want > had ? want : had;
   }
 }
 
@@ -362,7 +368,8 @@ static int repack_direction(Graph* g, Csr* c, const uint64_t* dl, int64_t nd, co
     release();
     return cuda_fail(g, e, "cudaMalloc(repack)");
   }
-  note_launch(); k_repack_plan<<<grid_for(n, 256), 256, 0, s>>>(c->deg, n, dl, nd, il, ni, bits, ndeg, cap);
+  note_launch(); k_repack_plan<<<grid_for(n, 256), 256, 0, s>>>(c->off, c->deg, n, dl, nd, il, ni, bits, c->repacks > 0,
+                                                                 ndeg, cap);
   e = scan_excl<int64_t>(cap, noff, n, scr, s);
   int64_t total = 0;
   if (e == cudaSuccess) e = cudaMemcpyAsync(&total, noff + n, sizeof(int64_t), cudaMemcpyDeviceToHost, s);
@@ -393,6 +400,7 @@ static int repack_direction(Graph* g, Csr* c, const uint64_t* dl, int64_t nd, co
   if (!owned) g->allocs.push_back(ncol);
   c->col = ncol;
   c->cap = total;
+  c->repacks++;
   return OK;
 }
 

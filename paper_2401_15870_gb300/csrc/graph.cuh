@@ -12,6 +12,7 @@ struct Csr {
   int32_t* deg = nullptr;   // n
   int32_t* col = nullptr;   // off[n] slots, SENT beyond deg
   int64_t cap = 0;          // off[n] (host copy)
+  int32_t repacks = 0;      // times this direction was rebuilt after an overflow
 };
 
 // Per-iteration control block, device resident; the host reads a copy.
