@@ -63,6 +63,8 @@ def parse():
     ap.add_argument("--reps", type=int, default=1, help="methods: batches per size")
     ap.add_argument("--temporal-batches", type=int, default=100, help="temporal: consecutive batches per size")
     ap.add_argument("--graphs", type=int, default=64, help="batched: graphs in the group")
+    ap.add_argument("--group-loop", default="device", choices=["device", "host"],
+                    help="batched: iteration loop of the group update (host: kernels launched one by one)")
     return ap.parse_args()
 
 
@@ -349,7 +351,7 @@ def run_batched(a, rank, world, local_rank):
     def group_step(i):
         for G, b in zip(graphs, batches):
             G.apply_batch_device(*b[i])
-        return grp.update("dfp", alpha=ALPHA, tau=TAU)
+        return grp.update("dfp", alpha=ALPHA, tau=TAU, loop=a.group_loop)
 
     def plain_step(i):
         out = []
@@ -380,19 +382,21 @@ def run_batched(a, rank, world, local_rank):
 
     # end to end through host buffers: every graph's batch from pinned memory,
     # every graph's ranks back to host memory
-    r_host = [torch.empty(n, dtype=torch.float64).pin_memory() for n, _, _ in sizes]
-    torch.cuda.synchronize()
-    t0 = time.perf_counter()
-    for i in range(a.e2e_steps):
-        for G, hb in zip(graphs, host_batches):
-            G.apply_batch(*[t.numpy() for t in hb[i]])
-        grp.update("dfp", alpha=ALPHA, tau=TAU)
-        for G, r in zip(graphs, r_host):
-            G.ranks(r.numpy())
-    torch.cuda.synchronize()
-    e2e_ms = (time.perf_counter() - t0) * 1000.0
-    h2d = sum(sum(t.numel() * 4 for t in hb[0]) for hb in host_batches)
-    d2h = sum(n * 8 for n, _, _ in sizes)
+    e2e_ms, h2d, d2h = None, 0, 0
+    if a.e2e_steps > 0:
+        r_host = [torch.empty(n, dtype=torch.float64).pin_memory() for n, _, _ in sizes]
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for i in range(a.e2e_steps):
+            for G, hb in zip(graphs, host_batches):
+                G.apply_batch(*[t.numpy() for t in hb[i]])
+            grp.update("dfp", alpha=ALPHA, tau=TAU)
+            for G, r in zip(graphs, r_host):
+                G.ranks(r.numpy())
+        torch.cuda.synchronize()
+        e2e_ms = (time.perf_counter() - t0) * 1000.0
+        h2d = sum(sum(t.numel() * 4 for t in hb[0]) for hb in host_batches)
+        d2h = sum(n * 8 for n, _, _ in sizes)
 
     # group sweep loop against HBM: algorithmic bytes of the sweeps over the
     # group update's time (which also holds its init, marking and control)
@@ -424,8 +428,8 @@ def run_batched(a, rank, world, local_rank):
         "speedup_vs_plain": value / plain,
         "roofline": {"bound": "hbm", "kernel": "group DF-P loop (k_g_gather + k_g_finish, with init / mark / control)",
                      "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak, "traffic": None},
-        "e2e": {"value": len(graphs) * a.e2e_steps / (e2e_ms / 1000.0), "unit": "graph updates/s",
-                "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
+        "e2e": {"value": len(graphs) * a.e2e_steps / (e2e_ms / 1000.0) if e2e_ms else None,
+                "unit": "graph updates/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
         "gpu_launches": launches_g,
         "clocks": clk,
         "detail": {

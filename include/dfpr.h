@@ -262,8 +262,11 @@ pr_status pr_sweep_noalloc(int32_t n, const int64_t* in_off, const int32_t* in_s
  *   of its graphs.  stream: the CUDA stream of the group's work (NULL: the
  *   legacy default stream).  Errors: PR_EINVAL, PR_ENOMEM, PR_ECUDA.
  * pr_group_update: method PR_STATIC, PR_NAIVE_DYNAMIC, PR_DF or PR_DFP (Dynamic
- *   Traversal is not offered), alpha / tau / opts as in pr_update (the flags
- *   of opts are ignored).  The update runs after the work already queued on
+ *   Traversal is not offered), alpha / tau / opts as in pr_update; the only
+ *   flag accepted is PR_OPT_HOST_LOOP (or PR_OPT_DEVICE_LOOP, the default):
+ *   the same kernels launched one by one with the loop condition read back
+ *   after every iteration, for profilers that cannot look into a CUDA graph
+ *   with conditional nodes and for drivers without them.  The update runs after the work already queued on
  *   every graph's stream and is complete on return.  stats: NULL or count
  *   entries, one per graph in creation order; ms_update is the time of the
  *   whole group, ms_sweep is 0.  Errors: PR_EINVAL, PR_ENORANKS (a dynamic

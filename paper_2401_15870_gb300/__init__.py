@@ -338,10 +338,11 @@ def pr_group_create(handles, stream=None):
     return out
 
 
-def pr_group_update(q, method, alpha=0.85, tau=1e-10, tau_f=1e-6, tau_p=1e-6, max_iter=500):
-    """One update of every graph of the group; returns one Stats per graph."""
+def pr_group_update(q, method, alpha=0.85, tau=1e-10, tau_f=1e-6, tau_p=1e-6, max_iter=500, loop=None):
+    """One update of every graph of the group; returns one Stats per graph.
+    loop: None / "device" (CUDA graph) or "host" (kernels launched one by one)."""
     m = METHODS[method] if isinstance(method, str) else int(method)
-    opts = pr_options(tau_f, tau_p, int(max_iter), 0)
+    opts = pr_options(tau_f, tau_p, int(max_iter), {None: 0, "device": 0, "host": PR_OPT_HOST_LOOP}[loop])
     n = _group_sizes[q.value]
     st = (pr_stats * n)()
     _check(load().pr_group_update(q, m, float(alpha), float(tau), ctypes.byref(opts), st))

@@ -71,6 +71,7 @@ struct GState {
 struct GRun {
   double alpha, tau, tau_f, tau_p;
   int32_t max_iter, method, G, loops;
+  int32_t live, use_graph;   // loop condition, written to `live` instead of the WHILE node when use_graph is 0
   const int64_t* wpre;   // gather units
   const int64_t* fpre;   // epilogue units (FIN_U chunks)
   const int64_t* bpre;   // bitset words
@@ -115,7 +116,7 @@ __global__ void __launch_bounds__(GR_THREADS) k_g_init(const GRun* __restrict__ 
       desc[g].C[0][desc[g].n] = 0;
       desc[g].C[1][desc[g].n] = 0;
     }
-    if (threadIdx.x == 0) cudaGraphSetConditional(cond, run->max_iter > 0 ? 1u : 0u);
+    if (threadIdx.x == 0 && run->use_graph) cudaGraphSetConditional(cond, run->max_iter > 0 ? 1u : 0u);
   }
   const int lane = threadIdx.x & 31;
   const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
@@ -296,7 +297,9 @@ __global__ void k_g_control(GRun* run, GState* st, cudaGraphConditionalHandle co
     run->loops += 1;
     // every graph is done after max_iter iterations; the guard bounds the loop
     // even if a state were corrupted
-    cudaGraphSetConditional(cond, (live && run->loops < run->max_iter) ? 1u : 0u);
+    const unsigned go = (live && run->loops < run->max_iter) ? 1u : 0u;
+    run->live = (int32_t)go;
+    if (run->use_graph) cudaGraphSetConditional(cond, go);
   }
 }
 
@@ -451,6 +454,37 @@ void pr_group_destroy(pr_group* q) { group_free(q); }
 
 }  // extern "C"
 
+// the same kernels launched one by one, the loop condition read back after
+// every iteration (PR_OPT_HOST_LOOP): for profilers that cannot see into a
+// CUDA graph with conditional nodes, and for drivers without them
+static cudaError_t host_loop(pr_group* q, int k, int32_t max_iter) {
+  cudaStream_t s = q->stream;
+  const int sms = num_sms();
+  const void* fin = k ? (const void*)k_g_finish<true> : (const void*)k_g_finish<false>;
+  const int g_init = sms * blocks_per_sm((const void*)k_g_init, GR_THREADS);
+  const int g_gather = sms * blocks_per_sm((const void*)k_g_gather, GR_THREADS);
+  const int g_finish = sms * blocks_per_sm(fin, GR_THREADS);
+  const cudaGraphConditionalHandle none = 0;
+  note_launch();
+  k_g_init<<<g_init, GR_THREADS, 0, s>>>(q->d_run, q->d_desc, q->d_state, none);
+  note_launch();
+  k_g_mark<<<g_init, GR_THREADS, 0, s>>>(q->d_run, q->d_desc);
+  for (int32_t it = 0; it < max_iter; it++) {
+    note_launch();
+    k_g_gather<<<g_gather, GR_THREADS, 0, s>>>(q->d_run, q->d_desc, q->d_state);
+    note_launch();
+    if (k) k_g_finish<true><<<g_finish, GR_THREADS, 0, s>>>(q->d_run, q->d_desc, q->d_state);
+    else k_g_finish<false><<<g_finish, GR_THREADS, 0, s>>>(q->d_run, q->d_desc, q->d_state);
+    note_launch();
+    k_g_control<<<1, GR_THREADS, 0, s>>>(q->d_run, q->d_state, none);
+    cudaError_t e = cudaMemcpyAsync(&q->h_run->live, &q->d_run->live, sizeof(int32_t), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) return e;
+    if (!q->h_run->live) break;
+  }
+  return cudaGetLastError();
+}
+
 // launch an update of the members (indices into the group; NULL: every graph)
 // on the group's stream without waiting for it
 pr_status group_launch(pr_group* q, pr_method method, double alpha, double tau, const pr_options* opts,
@@ -461,6 +495,8 @@ pr_status group_launch(pr_group* q, pr_method method, double alpha, double tau, 
   pr_options o = {1e-6, 1e-6, 500, 0};
   if (opts) o = *opts;
   if (!(o.tau_f >= 0.0) || !(o.tau_p >= 0.0) || o.max_iter < 0) return PR_EINVAL;
+  if (o.flags & ~(PR_OPT_HOST_LOOP | PR_OPT_DEVICE_LOOP)) return PR_EINVAL;
+  if ((o.flags & PR_OPT_HOST_LOOP) && (o.flags & PR_OPT_DEVICE_LOOP)) return PR_EINVAL;
   std::vector<int32_t>& mem = q->members;
   mem.clear();
   if (members) {
@@ -532,6 +568,7 @@ pr_status group_launch(pr_group* q, pr_method method, double alpha, double tau, 
   r.dpre = q->d_pre + 3 * (G + 1);
   r.tab_sc = q->tab_sc;
   r.tab_cl = q->tab_cl;
+  r.use_graph = (o.flags & PR_OPT_HOST_LOOP) ? 0 : 1;
 
   // order after the work already queued on the members' streams
   for (int i = 0; i < G; i++) {
@@ -551,11 +588,15 @@ pr_status group_launch(pr_group* q, pr_method method, double alpha, double tau, 
       cudaMemcpyAsync(q->d_run, q->h_run, sizeof(GRun), cudaMemcpyHostToDevice, s) != cudaSuccess)
     return PR_ECUDA;
   const int k = method == PR_DFP ? 1 : 0;
-  if (!q->exec[k] && build_exec(q, k) != cudaSuccess) {
-    cudaGetLastError();
+  if (r.use_graph) {
+    if (!q->exec[k] && build_exec(q, k) != cudaSuccess) {
+      cudaGetLastError();
+      return PR_ECUDA;
+    }
+    if (cudaGraphLaunch(q->exec[k], s) != cudaSuccess) return PR_ECUDA;
+  } else if (host_loop(q, k, o.max_iter) != cudaSuccess) {
     return PR_ECUDA;
   }
-  if (cudaGraphLaunch(q->exec[k], s) != cudaSuccess) return PR_ECUDA;
   if (cudaMemcpyAsync(q->h_state, q->d_state, sizeof(GState) * G, cudaMemcpyDeviceToHost, s) != cudaSuccess ||
       cudaMemcpyAsync(q->h_run, q->d_run, sizeof(GRun), cudaMemcpyDeviceToHost, s) != cudaSuccess)
     return PR_ECUDA;
@@ -577,8 +618,9 @@ pr_status group_complete(pr_group* q, pr_stats* stats) {
   const pr_method method = q->cur_method;
   float ms = 0.f;
   cudaEventElapsedTime(&ms, q->ev[0], q->ev[1]);
-  // kernels the CUDA graph ran: init, mark, and three per loop pass
-  note_launches(2ull + 3ull * (unsigned long long)q->h_run->loops);
+  // kernels the CUDA graph ran: init, mark, and three per loop pass (the host
+  // loop counted its launches itself)
+  if (q->h_run->use_graph) note_launches(2ull + 3ull * (unsigned long long)q->h_run->loops);
   for (size_t i = 0; i < q->members.size(); i++) {
     const int32_t gi = q->members[i];
     pr_graph* h = q->graphs[gi];
