@@ -350,6 +350,59 @@ double pr_server_clock(void);
 /* Finish the submitted requests, stop the worker, restore the graphs' streams. */
 void pr_server_destroy(pr_server* srv);
 
+/*
+ * Autotuning of the every-vertex rank sweep (Static, ND and the pull form of
+ * DF / DF-P; Alg. 1's sweep, Eq. 1 / Eq. 2).  The paper schedules its sweep
+ * with OpenMP dynamic chunks of 2048 vertices (Sec. 5.1.2); on the GPU the
+ * sweep's gather is edge-balanced and its speed depends on three settings
+ * that pr_autotune picks by timing them on the graph itself:
+ *   threads          threads per block: 256, 512 or 1024;
+ *   quads_per_lane   in-CSR quads (4 edge slots each) a lane loads per warp
+ *                    step: 2, 4 or 8;
+ *   hub_vertices     the contributions R[u]/|out(u)| of this many vertices of
+ *                    highest out-degree are staged in shared memory by every
+ *                    block (0: none).  This is a degree threshold: every vertex
+ *                    of out-degree >= hub_min_degree is staged;
+ *   fused_epilogue   1: Eq. 1 / Eq. 2 and the frontier tests run inside the
+ *                    gather kernel, for each 128-vertex chunk as soon as its
+ *                    rows are summed; 0: in a second kernel after the gather.
+ * The setting changes no result: contribution sums are exact (see the
+ * conventions above), so every setting gives the same bits.  It belongs to
+ * the graph and survives batches.
+ * pr_autotune: times every candidate setting on the graph's stream (CUDA
+ *   events) and keeps the fastest, writing it to *out (NULL: not written).
+ *   method PR_STATIC or PR_NAIVE_DYNAMIC: reps (0: 3; at most 100) sweeps of
+ *   Eq. 1 over every vertex per candidate, from the current contributions;
+ *   the graph's ranks and edges are left as they were.  method PR_DF or
+ *   PR_DFP: reps (0: 1) whole updates per candidate (the iteration loop on the
+ *   host, options at their defaults), each from the ranks the graph has on
+ *   entry and with its last batch; the rank-sweep kernel time decides.  Every
+ *   setting gives the same bits, so the graph is left as after one
+ *   pr_update(method, alpha, tau).  Needs ranks (PR_ENORANKS).  The trials
+ *   allocate one n-vector of device memory for the duration of the call.
+ *   Errors: PR_EINVAL (method PR_DYNAMIC_TRAVERSAL, whose sweeps are list
+ *   sweeps, or bad alpha / tau / reps), PR_ENORANKS, PR_ENOMEM, PR_ECUDA.
+ * pr_get_tuning: the graph's current setting (the defaults 256 / 4 / 0 / 0
+ *   until tuned or set).  ms_gather and candidates are 0 unless pr_autotune chose it.
+ * pr_set_tuning: sets threads, quads_per_lane, hub_vertices and
+ *   fused_epilogue (the other fields are ignored).  hub_vertices above n is clamped; a setting outside
+ *   the values above, or a hub too large for one block's shared memory
+ *   (about 27.9K vertices), gives PR_EINVAL and no change.
+ */
+typedef struct {
+  int32_t threads;
+  int32_t quads_per_lane;
+  int32_t hub_vertices;
+  int32_t fused_epilogue;
+  int32_t hub_min_degree;   /* out-degree of the last staged vertex (0: none)   */
+  float ms_gather;          /* pr_autotune: the chosen setting's time per trial (ms): one sweep, or
+                               the rank sweeps of one update                        */
+  int32_t candidates;       /* pr_autotune: settings timed                      */
+} pr_tuning;
+pr_status pr_autotune(pr_graph* g, pr_method method, double alpha, double tau, int32_t reps, pr_tuning* out);
+pr_status pr_get_tuning(const pr_graph* g, pr_tuning* out);
+pr_status pr_set_tuning(pr_graph* g, const pr_tuning* in);
+
 /* Number of CUDA kernels this library has launched in this process so far
  * (all graphs); the difference across a region counts its launches. */
 unsigned long long pr_kernel_launches(void);

@@ -43,6 +43,23 @@ class pr_stats(ctypes.Structure):
                 ("ms_sweep", ctypes.c_double), ("sweeps", ctypes.c_int32), ("reserved", ctypes.c_int32)]
 
 
+class pr_tuning(ctypes.Structure):
+    _fields_ = [("threads", ctypes.c_int32), ("quads_per_lane", ctypes.c_int32), ("hub_vertices", ctypes.c_int32),
+                ("fused_epilogue", ctypes.c_int32), ("hub_min_degree", ctypes.c_int32), ("ms_gather", ctypes.c_float),
+                ("candidates", ctypes.c_int32)]
+
+
+@dataclass
+class Tuning:
+    threads: int
+    quads_per_lane: int
+    hub_vertices: int
+    fused_epilogue: int
+    hub_min_degree: int
+    ms_gather: float
+    candidates: int
+
+
 @dataclass
 class Stats:
     iterations: int
@@ -104,6 +121,9 @@ def load():
         "pr_server_drain": ([_P, f64], ctypes.c_int),
         "pr_server_clock": ([], f64),
         "pr_server_destroy": ([_P], None),
+        "pr_autotune": ([_P, ctypes.c_int, f64, f64, i32, _P], ctypes.c_int),
+        "pr_get_tuning": ([_P, _P], ctypes.c_int),
+        "pr_set_tuning": ([_P, _P], ctypes.c_int),
     }
     for name, (args, res) in sig.items():
         f = getattr(lib, name)
@@ -368,6 +388,31 @@ def pr_group_destroy(q):
 _group_sizes = {}
 
 
+def _tuning(t):
+    return Tuning(*(getattr(t, f) for f, _ in pr_tuning._fields_))
+
+
+def pr_autotune(h, method="nd", alpha=0.85, tau=1e-10, reps=0):
+    """Time the candidate sweep settings on the graph and keep the fastest:
+    every-vertex sweeps (static / nd) or whole updates from the current ranks
+    (df / dfp, which leaves the graph as after one update)."""
+    m = METHODS[method] if isinstance(method, str) else int(method)
+    t = pr_tuning()
+    _check(load().pr_autotune(h, m, float(alpha), float(tau), int(reps), ctypes.byref(t)), h)
+    return _tuning(t)
+
+
+def pr_get_tuning(h):
+    t = pr_tuning()
+    _check(load().pr_get_tuning(h, ctypes.byref(t)), h)
+    return _tuning(t)
+
+
+def pr_set_tuning(h, threads=256, quads_per_lane=4, hub_vertices=0, fused_epilogue=1):
+    t = pr_tuning(int(threads), int(quads_per_lane), int(hub_vertices), int(fused_epilogue), 0, 0.0, 0)
+    _check(load().pr_set_tuning(h, ctypes.byref(t)), h)
+
+
 def pr_kernel_launches() -> int:
     return int(load().pr_kernel_launches())
 
@@ -449,6 +494,15 @@ class Graph:
 
     def dt_affected(self):
         return pr_affected(self._h, 1)
+
+    def autotune(self, method="nd", alpha=0.85, tau=1e-10, reps=0) -> Tuning:
+        return pr_autotune(self._h, method, alpha, tau, reps)
+
+    def tuning(self) -> Tuning:
+        return pr_get_tuning(self._h)
+
+    def set_tuning(self, threads=256, quads_per_lane=4, hub_vertices=0, fused_epilogue=1):
+        pr_set_tuning(self._h, threads, quads_per_lane, hub_vertices, fused_epilogue)
 
 
 class Group:

@@ -160,6 +160,8 @@ static pr_status alloc_state(pr_graph* h) {
   TRY(cudaMemsetAsync(g->gcnt, 0, sizeof(int32_t) * n, g->stream));
   TRY(dalloc(g, (void**)&g->gany, sizeof(int32_t) * n));
   TRY(cudaMemsetAsync(g->gany, 0, sizeof(int32_t) * n, g->stream));
+  TRY(dalloc(g, (void**)&g->done, sizeof(int32_t) * (cdiv(n, 128) + 1)));
+  TRY(cudaMemsetAsync(g->done, 0, sizeof(int32_t) * (cdiv(n, 128) + 1), g->stream));
   TRY(dalloc(g, (void**)&g->tab_sc, sizeof(double) * TAB));
   TRY(dalloc(g, (void**)&g->tab_cl, sizeof(double) * TAB));
   TRY(dalloc(g, (void**)&g->ctl, sizeof(Ctl)));
@@ -242,7 +244,7 @@ static int32_t hot_vertices(Graph* g) {
   return (int32_t)(hot < g->n ? hot : g->n);
 }
 
-static SweepParams base_params(Graph* g, double alpha, double tau_f, double tau_p) {
+SweepParams dfpr::base_params(Graph* g, double alpha, double tau_f, double tau_p) {
   SweepParams p;
   memset(&p, 0, sizeof(p));
   p.n = g->n;
@@ -363,7 +365,7 @@ struct SweepTimer {
       Graph* g = &h->g;
       SweepParams q = p;
       q.ntiles_host = g->in.cap >> 2;
-      e = launch_full_sweep(mode, q, g->rowbits, g->rowbase, g->anyb, s);
+      e = launch_full_sweep(mode, q, h->gcfg, g->rowbits, g->rowbase, g->anyb, g->done, s);
     } else {
       e = launch_sweep(mode, p, s);
     }
@@ -378,8 +380,8 @@ struct SweepTimer {
   }
 };
 
-static pr_status run_update(pr_graph* h, int method, double alpha, double tau, double tau_f, double tau_p,
-                            int32_t max_iter, int32_t flags, pr_stats* out) {
+pr_status dfpr::run_update(pr_graph* h, int method, double alpha, double tau, double tau_f, double tau_p,
+                           int32_t max_iter, int32_t flags, pr_stats* out) {
   SweepTimer timer{h, (flags & PR_OPT_TIME_SWEEPS) != 0};
   Graph* g = &h->g;
   cudaStream_t s = g->stream;

@@ -82,6 +82,7 @@ struct Graph {
   uint32_t* rowbits = nullptr;              // full sweeps: in-CSR quads where a row starts
   int32_t* rowbase = nullptr;               // rows starting before each 32-quad word
   uint32_t* anyb = nullptr;                 // full pull sweeps: an in-neighbour expanded (n bits)
+  int32_t* done = nullptr;                  // one-launch full sweeps: gather units counted per 128-vertex chunk
 
   // effective change of the last batch, packed keys sorted by (src, dst), internal ids
   uint64_t* dmin = nullptr;

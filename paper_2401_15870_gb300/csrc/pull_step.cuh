@@ -52,23 +52,51 @@ __device__ __forceinline__ long long ld_hint(const long long* p, uint64_t pol) {
 
 __device__ __forceinline__ unsigned long long dbits(double x) { return (unsigned long long)__double_as_longlong(x); }
 
-// quads [base, base + 32 * SW_QPT) of one in-CSR; S / X / anyb only in pull form
-template <bool PULL>
-__device__ __forceinline__ void gather_step(const int32_t* __restrict__ icol, const long long* __restrict__ C,
-                                            const uint32_t* __restrict__ X, const uint32_t* __restrict__ S,
-                                            const uint32_t* __restrict__ rowbits, const int32_t* __restrict__ rowbase,
-                                            int64_t nquads, int32_t sent, long long* __restrict__ acc,
-                                            uint32_t* __restrict__ anyb, int64_t base, uint64_t pol_stream,
-                                            uint64_t pol_keep) {
+// Contributions (and, in pull form, expanded-source bits) of the hub vertices
+// [0, k) staged in shared memory by the kernel.  Internal ids are ordered by
+// decreasing out-degree, so [0, k) are the vertices of out-degree at least
+// odeg[k-1]: the sources that the most in-rows gather from.  A shared-memory
+// load of random addresses costs a few bank wavefronts per warp, where the
+// same loads from global memory cost about one L1TEX wavefront per lane.
+struct HubView {
+  const long long* c = nullptr;   // c[0..k): C[0..k)
+  const uint32_t* x = nullptr;    // x[0..kx): X[0..kx) (pull form)
+  int32_t k = 0, kx = 0;
+};
+
+// What one gather step touched: the rows of its first and last quads (the
+// same in every lane) and whether this lane wrote an accumulator.
+struct GatherSpan {
+  int first, last;
+  bool wrote;
+};
+
+// quads [base, base + 32 * QPT) of one in-CSR; S / X / anyb only in pull form
+template <bool PULL, int QPT = SW_QPT, bool HUB = false>
+__device__ __forceinline__ GatherSpan gather_step(const int32_t* __restrict__ icol, const long long* __restrict__ C,
+                                                  const uint32_t* __restrict__ X, const uint32_t* __restrict__ S,
+                                                  const uint32_t* __restrict__ rowbits,
+                                                  const int32_t* __restrict__ rowbase, int64_t nquads, int32_t sent,
+                                                  long long* __restrict__ acc, uint32_t* __restrict__ anyb,
+                                                  int64_t base, uint64_t pol_stream, uint64_t pol_keep,
+                                                  const HubView& hub = HubView()) {
   const int lane = threadIdx.x & 31;
   const unsigned upto = lane == 31 ? 0xffffffffu : ((2u << lane) - 1u);
-  // sentinel slots (row slack) contribute 0 and issue no load
-  auto contrib = [&](int32_t c) -> long long { return c != sent ? ld_hint(C + c, pol_keep) : 0ll; };
-  auto expanded = [&](int32_t c) -> unsigned { return c != sent ? (__ldg(X + (c >> 5)) >> (c & 31)) : 0u; };
-  int4 c[SW_QPT];
-  int owner[SW_QPT];
+  // sentinel slots (row slack) contribute 0 and issue no load; a hub cache
+  // that covers the sentinel id holds C[sent] = 0
+  auto contrib = [&](int32_t c) -> long long {
+    if (HUB && c < hub.k) return hub.c[c];
+    return c != sent ? ld_hint(C + c, pol_keep) : 0ll;
+  };
+  auto expanded = [&](int32_t c) -> unsigned {
+    if (c == sent) return 0u;
+    const uint32_t w = HUB && (c >> 5) < hub.kx ? hub.x[c >> 5] : __ldg(X + (c >> 5));
+    return w >> (c & 31);
+  };
+  int4 c[QPT];
+  int owner[QPT];
 #pragma unroll
-  for (int j = 0; j < SW_QPT; j++) {
+  for (int j = 0; j < QPT; j++) {
     const int64_t q = base + 32 * j + lane;
     const bool valid = q < nquads;
     c[j] = valid ? ld_stream4(icol + 4 * q, pol_stream) : make_int4(sent, sent, sent, sent);
@@ -77,10 +105,10 @@ __device__ __forceinline__ void gather_step(const int32_t* __restrict__ icol, co
     const int32_t rb = w * 32 < nquads ? __ldg(rowbase + w) : 0;
     owner[j] = valid ? rb + __popc(bits & upto) - 1 : -1;
   }
-  long long s[SW_QPT];
-  unsigned x[SW_QPT];
+  long long s[QPT];
+  unsigned x[QPT];
 #pragma unroll
-  for (int j = 0; j < SW_QPT; j++) {
+  for (int j = 0; j < QPT; j++) {
     s[j] = contrib(c[j].x) + contrib(c[j].y) + contrib(c[j].z) + contrib(c[j].w);
     x[j] = 0;
     // a row whose vertex stays in the frontier is processed anyway: its
@@ -88,8 +116,15 @@ __device__ __forceinline__ void gather_step(const int32_t* __restrict__ icol, co
     if (PULL && owner[j] >= 0 && !((__ldg(S + (owner[j] >> 5)) >> (owner[j] & 31)) & 1u))
       x[j] = (expanded(c[j].x) | expanded(c[j].y) | expanded(c[j].z) | expanded(c[j].w)) & 1u;
   }
+  GatherSpan span;
+  span.first = __shfl_sync(0xffffffffu, owner[0], 0);
+  int hi = owner[0];
 #pragma unroll
-  for (int j = 0; j < SW_QPT; j++) {
+  for (int j = 1; j < QPT; j++) hi = max(hi, owner[j]);
+  span.last = __reduce_max_sync(0xffffffffu, hi);
+  span.wrote = false;
+#pragma unroll
+  for (int j = 0; j < QPT; j++) {
     const int own = owner[j];
     long long sum = s[j];
     unsigned any = x[j];
@@ -107,8 +142,10 @@ __device__ __forceinline__ void gather_step(const int32_t* __restrict__ icol, co
     if (own >= 0 && (lane == 0 || prev != own)) {
       if (sum) atomicAdd(reinterpret_cast<unsigned long long*>(acc + own), (unsigned long long)sum);
       if (PULL && any) atomicOr(anyb + (own >> 5), 1u << (own & 31));
+      span.wrote = span.wrote || sum != 0 || (PULL && any);
     }
   }
+  return span;
 }
 
 constexpr int FIN_U = 4;   // chunks per warp step of the epilogue: their loads are issued together
@@ -121,14 +158,14 @@ struct PullTotals {
   int stays = 0, exps = 0;
 };
 
-// chunks [ch0, ch0 + FIN_U) of one graph.  P provides n, odeg, ideg, R, Ccur,
+// chunks [ch0, ch0 + U) of one graph.  P provides n, odeg, ideg, R, Ccur,
 // Cnext, S_cur, S_next, X_next, ever, tab_sc, tab_cl, alpha, C0, tau_f, tau_p.
 // The accumulators and the expanded-source words it reads are left zero for
-// the next sweep.
-template <bool CLOSED, class P>
+// the next sweep.  L2: read them from L2 (they were written by other SMs in
+// the same launch).
+template <bool CLOSED, class P, bool L2 = false, int U = FIN_U>
 __device__ __forceinline__ void finish_pull_step(const P& p, long long* __restrict__ acc, uint32_t* __restrict__ anyb,
                                                  int64_t ch0, int64_t nchunks, PullTotals& t) {
-  constexpr int U = FIN_U;
   const int lane = threadIdx.x & 31;
   const double alpha_fix = p.alpha * FIX_INV;
   const bool same_tau = p.tau_f == p.tau_p;
@@ -141,9 +178,10 @@ __device__ __forceinline__ void finish_pull_step(const P& p, long long* __restri
     const int64_t ch = ch0 + u;
     const int64_t v = ch * 32 + lane;
     valid[u] = ch < nchunks && v < p.n;
-    const uint32_t in_f = ch < nchunks ? (anyb[ch] | __ldg(p.S_cur + ch)) : 0u;
+    const uint32_t ab = ch < nchunks ? (L2 ? __ldcg(anyb + ch) : anyb[ch]) : 0u;
+    const uint32_t in_f = ch < nchunks ? (ab | __ldg(p.S_cur + ch)) : 0u;
     member[u] = valid[u] && ((in_f >> lane) & 1u);
-    sum[u] = valid[u] ? acc[v] : 0;
+    sum[u] = valid[u] ? (L2 ? __ldcg(acc + v) : acc[v]) : 0;
     cself[u] = valid[u] ? p.Ccur[v] : 0;
     Rv[u] = member[u] ? p.R[v] : 0.0;
     d[u] = member[u] ? p.odeg[v] : 1;

@@ -17,6 +17,9 @@
 // slower there).
 #include <algorithm>
 #include <climits>
+#include <map>
+#include <mutex>
+#include <tuple>
 #include "sweep.cuh"
 #include "pull_step.cuh"
 #include "prim.cuh"
@@ -346,18 +349,38 @@ __global__ void __launch_bounds__(SW_THREADS) k_sweep(SweepParams p) {
 //     piece's partial sum to the row's accumulator;
 //   k_finish_pull / k_finish_full: read and clear each vertex's accumulator
 //     and run the epilogue.
-template <bool PULL>
-__global__ void __launch_bounds__(256) k_gather_rows(const int32_t* __restrict__ icol, const long long* __restrict__ C,
-                                                     const uint32_t* __restrict__ X, const uint32_t* __restrict__ S,
-                                                     const uint32_t* __restrict__ rowbits,
-                                                     const int32_t* __restrict__ rowbase, int64_t nquads, int32_t sent,
-                                                     long long* __restrict__ acc, uint32_t* __restrict__ anyb) {
+//   With HUB, every block first stages the contributions of the hub vertices
+//   [0, hub_k) (and, in pull form, the expanded bits of their words) in
+//   shared memory; the grid is then one wave of resident blocks, so the
+//   staging is paid once per block and sweep.
+template <bool PULL, int QPT, bool HUB>
+__global__ void __launch_bounds__(1024) k_gather_rows(const int32_t* __restrict__ icol, const long long* __restrict__ C,
+                                                      const uint32_t* __restrict__ X, const uint32_t* __restrict__ S,
+                                                      const uint32_t* __restrict__ rowbits,
+                                                      const int32_t* __restrict__ rowbase, int64_t nquads, int32_t sent,
+                                                      long long* __restrict__ acc, uint32_t* __restrict__ anyb,
+                                                      int32_t hub_k, int32_t hub_kx) {
+  extern __shared__ __align__(16) unsigned char hub_smem[];
   const int64_t warp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
   const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
   const uint64_t pol_stream = policy_evict_first();
   const uint64_t pol_keep = policy_evict_last();
-  for (int64_t base = warp * 32 * SW_QPT; base < nquads; base += nw * 32 * SW_QPT)
-    gather_step<PULL>(icol, C, X, S, rowbits, rowbase, nquads, sent, acc, anyb, base, pol_stream, pol_keep);
+  HubView hub;
+  if (HUB) {
+    long long* hc = reinterpret_cast<long long*>(hub_smem);
+    uint32_t* hx = reinterpret_cast<uint32_t*>(hc + hub_k);
+    for (int i = threadIdx.x; i < hub_k; i += blockDim.x) hc[i] = ld_hint(C + i, pol_keep);
+    if (PULL)
+      for (int i = threadIdx.x; i < hub_kx; i += blockDim.x) hx[i] = __ldg(X + i);
+    __syncthreads();
+    hub.c = hc;
+    hub.x = hx;
+    hub.k = hub_k;
+    hub.kx = PULL ? hub_kx : 0;
+  }
+  for (int64_t base = warp * 32 * QPT; base < nquads; base += nw * 32 * QPT)
+    gather_step<PULL, QPT, HUB>(icol, C, X, S, rowbits, rowbase, nquads, sent, acc, anyb, base, pol_stream, pol_keep,
+                                hub);
 }
 
 template <bool CLOSED>
@@ -414,23 +437,308 @@ __global__ void __launch_bounds__(256, 4) k_finish_full(SweepParams p, long long
   block_flush_stats(__longlong_as_double((long long)dmax), edges, verts, p.ctl);
 }
 
-cudaError_t launch_full_sweep(int mode, const SweepParams& p, const uint32_t* rowbits, const int32_t* rowbase,
-                              uint32_t* anyb, cudaStream_t s) {
+// ------------------------------------------------------------------ every-vertex sweep in one launch
+//
+// The gather of the rows and the epilogue of Eq. 1 / Eq. 2 in one kernel.  The
+// vertices are cut into chunks of FIN_U x 32; every task (TASK_Q consecutive
+// quads, gathered by one warp) that adds to the rows of a chunk counts itself
+// in done[chunk] after its writes are visible (fence, then the count).  The
+// task that brings the count to the number of tasks over the chunk's rows runs
+// the chunk's epilogue itself and resets the count.  Nothing waits on anything: a chunk
+// is finished by whichever warp completes it.  The epilogue is bound by the
+// FP64 pipe and the gather by the L1TEX data pipe, so in one launch the two
+// overlap across the warps of an SM.
+
+// Eq. 1 for every vertex of chunks [ch0, ch0 + U) (Static, ND): the
+// arithmetic of k_finish_full, one lane per vertex
+template <int U>
+__device__ __forceinline__ void finish_full_step(const SweepParams& p, long long* __restrict__ acc, int64_t ch0,
+                                                 PullTotals& t) {
+  const int lane = threadIdx.x & 31;
+  const double alpha_fix = p.alpha * FIX_INV;
+  long long sum[U];
+  double Rv[U];
+  int32_t d[U];
+#pragma unroll
+  for (int u = 0; u < U; u++) {
+    const int64_t v = (ch0 + u) * 32 + lane;
+    const bool ok = v < p.n;
+    sum[u] = ok ? __ldcg(acc + v) : 0;
+    Rv[u] = ok ? p.R[v] : 0.0;
+    d[u] = ok ? p.odeg[v] : 1;
+  }
+#pragma unroll
+  for (int u = 0; u < U; u++) {
+    const int64_t v = (ch0 + u) * 32 + lane;
+    if (v >= p.n) continue;
+    acc[v] = 0;
+    const double r = fma(alpha_fix, (double)sum[u], p.C0);   // Eq. 1
+    const unsigned long long drb = dbits(fabs(r - Rv[u]));
+    t.dmax = drb > t.dmax ? drb : t.dmax;
+    t.edges += p.ideg[v];
+    t.verts += 1;
+    p.R[v] = r;
+    const double sc = d[u] < TAB ? p.tab_sc[d[u]] : FIX_ONE / (double)d[u];
+    p.Cnext[v] = __double2ll_rn(r * sc);
+  }
+}
+
+// block totals of the epilogue (any block size up to 1024)
+__device__ __forceinline__ void block_flush_totals(const PullTotals& t, Ctl* ctl, int32_t* cnt_next, int32_t* cnt_x) {
+  __shared__ unsigned long long s_d[32];
+  __shared__ long long s_e[32], s_v[32];
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  if (lane == 0) {
+    if (t.stays) atomicAdd(cnt_next, t.stays);
+    if (t.exps) atomicAdd(cnt_x, t.exps);
+  }
+  unsigned long long dm = t.dmax;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    const unsigned long long y = __shfl_xor_sync(0xffffffffu, dm, o);
+    dm = y > dm ? y : dm;
+  }
+  const long long e = warp_sum_ll(t.edges), v = warp_sum_ll(t.verts);
+  if (lane == 0) {
+    s_d[w] = dm;
+    s_e[w] = e;
+    s_v[w] = v;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    unsigned long long d = 0;
+    long long es = 0, vs = 0;
+    for (int i = 0; i < (int)(blockDim.x >> 5); i++) {
+      d = s_d[i] > d ? s_d[i] : d;
+      es += s_e[i];
+      vs += s_v[i];
+    }
+    if (d) atomicMax(&ctl->dR, d);
+    if (es) atomicAdd((unsigned long long*)&ctl->edges, (unsigned long long)es);
+    if (vs) atomicAdd((unsigned long long*)&ctl->verts, (unsigned long long)vs);
+  }
+}
+
+constexpr int64_t TASK_Q = 1024;   // quads per task of k_sweep_rows (a multiple of 32 x QPT)
+
+template <int MODE, int QPT, bool HUB>
+__global__ void __launch_bounds__(1024) k_sweep_rows(SweepParams p, const uint32_t* __restrict__ rowbits,
+                                                     const int32_t* __restrict__ rowbase, uint32_t* __restrict__ anyb,
+                                                     int32_t* __restrict__ done, int32_t hub_k, int32_t hub_kx) {
+  constexpr bool PULL = MODE != SWEEP_FULL;
+  constexpr int64_t UQ = 32 * QPT;          // quads per gather step
+  constexpr int CV = FIN_U * 32;            // vertices per epilogue chunk
+  extern __shared__ __align__(16) unsigned char hub_smem[];
+  const int lane = threadIdx.x & 31;
+  const int64_t warp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+  const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  const int64_t nquads = p.ntiles_host;
+  const int64_t nunits = cdiv(nquads, UQ);
+  const int64_t nch32 = cdiv(p.n, 32);
+  const uint64_t pol_stream = policy_evict_first();
+  const uint64_t pol_keep = policy_evict_last();
+  HubView hub;
+  if (HUB) {
+    long long* hc = reinterpret_cast<long long*>(hub_smem);
+    uint32_t* hx = reinterpret_cast<uint32_t*>(hc + hub_k);
+    for (int i = threadIdx.x; i < hub_k; i += blockDim.x) hc[i] = ld_hint(p.Ccur + i, pol_keep);
+    if (PULL)
+      for (int i = threadIdx.x; i < hub_kx; i += blockDim.x) hx[i] = __ldg(p.X_cur + i);
+    __syncthreads();
+    hub.c = hc;
+    hub.x = hx;
+    hub.k = hub_k;
+    hub.kx = PULL ? hub_kx : 0;
+  }
+  PullTotals t;
+  // a warp takes TASK_Q consecutive quads (RU gather steps) at a time, so the
+  // fence that publishes its sums is paid once per task
+  constexpr int RU = (int)(TASK_Q / UQ);
+  const int64_t ntasks = cdiv(nunits, RU);
+  for (int64_t tk = warp; tk < ntasks; tk += nw) {
+    int first = INT_MAX, last = -1;
+    bool wrote = false;
+    for (int r = 0; r < RU; r++) {
+      const int64_t u = tk * RU + r;
+      if (u >= nunits) break;
+      const GatherSpan sp = gather_step<PULL, QPT, HUB>(p.icol, p.Ccur, p.X_cur, p.S_cur, rowbits, rowbase, nquads,
+                                                        p.n, p.gacc, anyb, u * UQ, pol_stream, pol_keep, hub);
+      first = min(first, sp.first);
+      last = max(last, sp.last);
+      wrote = wrote || sp.wrote;
+    }
+    // publish this task's sums, then count it in every chunk it touched; a
+    // task spans at most TASK_Q rows, so at most TASK_Q / CV + 2 chunks
+    if (wrote) __threadfence();
+    __syncwarp();
+    const int c0 = first / CV, c1 = last / CV;
+    unsigned mine = 0u;
+    if (lane <= c1 - c0) {
+      const int c = c0 + lane;
+      const int64_t v0 = (int64_t)c * CV, v1 = min((int64_t)p.n, v0 + CV);
+      const int64_t need = (__ldg(p.ioff + v1) / 4 - 1) / TASK_Q - (__ldg(p.ioff + v0) / 4) / TASK_Q + 1;
+      if (atomicAdd(done + c, 1) == (int)need - 1) {
+        done[c] = 0;
+        mine = 1u;
+      }
+    }
+    unsigned fin = __ballot_sync(0xffffffffu, mine);
+    if (fin) __threadfence();   // the chunk's sums, now complete, are read after the count
+    while (fin) {
+      const int k = __ffs(fin) - 1;
+      fin &= fin - 1;
+      // one 32-vertex word at a time: other warps hide the latency, and the
+      // gather keeps its registers
+      for (int w = 0; w < FIN_U; w++) {
+        const int64_t ch = (int64_t)(c0 + k) * FIN_U + w;
+        if (MODE == SWEEP_FULL)
+          finish_full_step<1>(p, p.gacc, ch, t);
+        else
+          finish_pull_step<MODE == SWEEP_PULL_DFP, SweepParams, true, 1>(p, p.gacc, anyb, ch, nch32, t);
+      }
+    }
+  }
+  block_flush_totals(t, p.ctl, p.cnt_next, p.cnt_x);
+}
+
+template <int MODE, int QPT, bool HUB>
+static cudaError_t sweep_rows_launch(const SweepParams& p, const uint32_t* rowbits, const int32_t* rowbase,
+                                     uint32_t* anyb, int32_t* done, int threads, int32_t hub_k, int32_t hub_kx,
+                                     cudaStream_t s) {
+  const void* fn = (const void*)k_sweep_rows<MODE, QPT, HUB>;
+  const size_t smem = HUB ? gather_hub_bytes(hub_k, hub_kx) : 0;
+  int bps = 1;
+  cudaError_t e = gather_occupancy(fn, threads, smem, &bps);
+  if (e != cudaSuccess) return e;
+  const int64_t tasks = cdiv(p.ntiles_host, TASK_Q);
+  const int64_t cap = (int64_t)num_sms() * bps;
+  const int grid = (int)std::max<int64_t>(1, std::min<int64_t>(cdiv(tasks, threads / 32), cap));
+  note_launch();
+  k_sweep_rows<MODE, QPT, HUB><<<grid, threads, smem, s>>>(p, rowbits, rowbase, anyb, done, hub_k, hub_kx);
+  return cudaGetLastError();
+}
+
+template <int MODE>
+static cudaError_t sweep_rows_dispatch(const SweepParams& p, const GatherCfg& cfg, const uint32_t* rowbits,
+                                       const int32_t* rowbase, uint32_t* anyb, int32_t* done, cudaStream_t s) {
+  constexpr bool PULL = MODE != SWEEP_FULL;
+  const int32_t hub_k = std::min<int32_t>(cfg.hub, p.n + 1);
+  const int32_t hub_kx = PULL ? (int32_t)cdiv(std::min<int32_t>(hub_k, p.n), 32) : 0;
+  const int t = cfg.threads;
+  switch (cfg.qpt * 2 + (hub_k > 0 ? 1 : 0)) {
+    case 4: return sweep_rows_launch<MODE, 2, false>(p, rowbits, rowbase, anyb, done, t, 0, 0, s);
+    case 5: return sweep_rows_launch<MODE, 2, true>(p, rowbits, rowbase, anyb, done, t, hub_k, hub_kx, s);
+    case 8: return sweep_rows_launch<MODE, 4, false>(p, rowbits, rowbase, anyb, done, t, 0, 0, s);
+    case 9: return sweep_rows_launch<MODE, 4, true>(p, rowbits, rowbase, anyb, done, t, hub_k, hub_kx, s);
+    case 16: return sweep_rows_launch<MODE, 8, false>(p, rowbits, rowbase, anyb, done, t, 0, 0, s);
+    case 17: return sweep_rows_launch<MODE, 8, true>(p, rowbits, rowbase, anyb, done, t, hub_k, hub_kx, s);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+template <bool PULL, int QPT, bool HUB>
+static cudaError_t gather_launch(const SweepParams& p, const uint32_t* rowbits, const int32_t* rowbase, uint32_t* anyb,
+                                 int64_t nquads, int threads, int32_t hub_k, int32_t hub_kx, cudaStream_t s) {
+  const void* fn = (const void*)k_gather_rows<PULL, QPT, HUB>;
+  const size_t smem = HUB ? gather_hub_bytes(hub_k, hub_kx) : 0;
+  int bps = 1;
+  cudaError_t e = gather_occupancy(fn, threads, smem, &bps);
+  if (e != cudaSuccess) return e;
+  // one wave of resident blocks when each block stages a hub cache, else up
+  // to 16 blocks of 256 threads per SM; never more warps than work units
+  const int64_t units = cdiv(nquads, 32 * QPT);
+  const int64_t cap = HUB ? (int64_t)num_sms() * bps : (int64_t)num_sms() * 16 * 256 / threads;
+  const int grid = (int)std::max<int64_t>(1, std::min<int64_t>(cdiv(units, threads / 32), cap));
+  note_launch();
+  k_gather_rows<PULL, QPT, HUB><<<grid, threads, smem, s>>>(p.icol, p.Ccur, PULL ? p.X_cur : nullptr,
+                                                          PULL ? p.S_cur : nullptr, rowbits, rowbase, nquads, p.n,
+                                                          p.gacc, anyb, hub_k, hub_kx);
+  return cudaGetLastError();
+}
+
+template <bool PULL>
+static cudaError_t gather_dispatch(const SweepParams& p, const GatherCfg& cfg, const uint32_t* rowbits,
+                                   const int32_t* rowbase, uint32_t* anyb, int64_t nquads, cudaStream_t s) {
+  const int32_t hub_k = std::min<int32_t>(cfg.hub, p.n + 1);
+  const int32_t hub_kx = PULL ? (int32_t)cdiv(std::min<int32_t>(hub_k, p.n), 32) : 0;
+  const bool hub = hub_k > 0;
+  const int t = cfg.threads;
+  switch (cfg.qpt * 2 + (hub ? 1 : 0)) {
+    case 4: return gather_launch<PULL, 2, false>(p, rowbits, rowbase, anyb, nquads, t, 0, 0, s);
+    case 5: return gather_launch<PULL, 2, true>(p, rowbits, rowbase, anyb, nquads, t, hub_k, hub_kx, s);
+    case 8: return gather_launch<PULL, 4, false>(p, rowbits, rowbase, anyb, nquads, t, 0, 0, s);
+    case 9: return gather_launch<PULL, 4, true>(p, rowbits, rowbase, anyb, nquads, t, hub_k, hub_kx, s);
+    case 16: return gather_launch<PULL, 8, false>(p, rowbits, rowbase, anyb, nquads, t, 0, 0, s);
+    case 17: return gather_launch<PULL, 8, true>(p, rowbits, rowbase, anyb, nquads, t, hub_k, hub_kx, s);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+size_t gather_hub_bytes(int32_t hub_k, int32_t hub_kx) {
+  return sizeof(long long) * (size_t)hub_k + sizeof(uint32_t) * (size_t)hub_kx;
+}
+
+// resident blocks per SM of a gather kernel with `smem` bytes of dynamic
+// shared memory (raising the kernel's dynamic shared memory limit once)
+cudaError_t gather_occupancy(const void* fn, int threads, size_t smem, int* bps) {
+  static std::mutex mu;
+  static std::map<const void*, size_t> limit;
+  static std::map<std::tuple<const void*, int, size_t>, int> cache;
+  std::lock_guard<std::mutex> lock(mu);
+  auto key = std::make_tuple(fn, threads, smem);
+  auto it = cache.find(key);
+  if (it != cache.end()) {
+    *bps = it->second;
+    return cudaSuccess;
+  }
+  size_t& lim = limit[fn];
+  if (smem > lim) {
+    cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    lim = smem;
+  }
+  int b = 0;
+  cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, fn, threads, smem);
+  if (e != cudaSuccess) return e;
+  if (b < 1) return cudaErrorInvalidConfiguration;
+  cache[key] = b;
+  *bps = b;
+  return cudaSuccess;
+}
+
+bool gather_cfg_valid(const GatherCfg& c) {
+  if (c.threads != 256 && c.threads != 512 && c.threads != 1024) return false;
+  if (c.qpt != 2 && c.qpt != 4 && c.qpt != 8) return false;
+  if (c.fused != 0 && c.fused != 1) return false;
+  return c.hub >= 0 && gather_hub_bytes(c.hub, (int32_t)cdiv(c.hub, 32)) <= (size_t)GATHER_SMEM_MAX;
+}
+
+cudaError_t launch_gather(bool pull, const SweepParams& p, const GatherCfg& cfg, const uint32_t* rowbits,
+                          const int32_t* rowbase, uint32_t* anyb, int64_t nquads, cudaStream_t s) {
+  if (!gather_cfg_valid(cfg)) return cudaErrorInvalidValue;
+  return pull ? gather_dispatch<true>(p, cfg, rowbits, rowbase, anyb, nquads, s)
+              : gather_dispatch<false>(p, cfg, rowbits, rowbase, anyb, nquads, s);
+}
+
+cudaError_t launch_full_sweep(int mode, const SweepParams& p, const GatherCfg& cfg, const uint32_t* rowbits,
+                              const int32_t* rowbase, uint32_t* anyb, int32_t* done, cudaStream_t s) {
   const int64_t nquads = p.ntiles_host;   // quads of the in-CSR capacity
-  const int sms = num_sms();
   const bool pull = mode == SWEEP_PULL_DF || mode == SWEEP_PULL_DFP;
   if (pull) {
     cudaError_t e = cudaMemsetAsync(anyb, 0, sizeof(uint32_t) * (size_t)(cdiv(p.n, 32) + 1), s);
     if (e != cudaSuccess) return e;
   }
-  int qgrid = (int)std::min<int64_t>(cdiv(nquads, 32 * SW_QPT * 8) + 1, (int64_t)sms * 16);
-  note_launch();
-  if (pull)
-    k_gather_rows<true><<<qgrid, 256, 0, s>>>(p.icol, p.Ccur, p.X_cur, p.S_cur, rowbits, rowbase, nquads, p.n, p.gacc,
-                                               anyb);
-  else
-    k_gather_rows<false><<<qgrid, 256, 0, s>>>(p.icol, p.Ccur, nullptr, nullptr, rowbits, rowbase, nquads, p.n, p.gacc,
-                                                anyb);
+  if (cfg.fused) {
+    if (!gather_cfg_valid(cfg)) return cudaErrorInvalidValue;
+    switch (mode) {
+      case SWEEP_FULL: return sweep_rows_dispatch<SWEEP_FULL>(p, cfg, rowbits, rowbase, anyb, done, s);
+      case SWEEP_PULL_DF: return sweep_rows_dispatch<SWEEP_PULL_DF>(p, cfg, rowbits, rowbase, anyb, done, s);
+      case SWEEP_PULL_DFP: return sweep_rows_dispatch<SWEEP_PULL_DFP>(p, cfg, rowbits, rowbase, anyb, done, s);
+      default: return cudaErrorInvalidValue;
+    }
+  }
+  cudaError_t e = launch_gather(pull, p, cfg, rowbits, rowbase, anyb, nquads, s);
+  if (e != cudaSuccess) return e;
   int rgrid = grid_for(p.n, 256);
   switch (mode) {
     case SWEEP_FULL: note_launch(); k_finish_full<<<rgrid, 256, 0, s>>>(p, p.gacc); break;

@@ -65,12 +65,35 @@ struct SweepParams {
 
 cudaError_t launch_sweep(int mode, const SweepParams& p, cudaStream_t s);
 
-// every-vertex sweep (FULL, PULL_DF, PULL_DFP) in two phases; p.ntiles_host is
-// the number of quads of the in-CSR capacity, p.gacc the all-zero per-vertex
-// accumulators (left zero), rowbits / rowbase the row-start index of the
-// in-CSR (launch_row_start_index), anyb an n-bit scratch bitset
-cudaError_t launch_full_sweep(int mode, const SweepParams& p, const uint32_t* rowbits, const int32_t* rowbase,
-                              uint32_t* anyb, cudaStream_t s);
+// Launch configuration of the every-vertex gather (k_gather_rows): threads per
+// block (256, 512 or 1024), quads per lane per warp step (2, 4 or 8), and the
+// number of hub contributions staged in shared memory by every block (0: none;
+// internal ids are ordered by decreasing out-degree, so the hub set is the
+// vertices whose out-degree is at least that of vertex hub - 1), and whether
+// the epilogue runs inside the gather kernel (k_sweep_rows) or as a second
+// launch (k_finish_full / k_finish_pull).  The defaults are the configuration
+// used before any tuning.
+struct GatherCfg {
+  int32_t threads = 256;
+  int32_t qpt = SW_QPT;
+  int32_t hub = 0;
+  int32_t fused = 0;
+};
+constexpr int GATHER_SMEM_MAX = 227 * 1024;   // dynamic shared memory of one block on sm_103
+size_t gather_hub_bytes(int32_t hub_k, int32_t hub_kx);
+bool gather_cfg_valid(const GatherCfg& c);
+cudaError_t gather_occupancy(const void* fn, int threads, size_t smem, int* bps);
+// the gather alone: adds every row's sum to p.gacc (and, if pull, sets anyb)
+cudaError_t launch_gather(bool pull, const SweepParams& p, const GatherCfg& cfg, const uint32_t* rowbits,
+                          const int32_t* rowbase, uint32_t* anyb, int64_t nquads, cudaStream_t s);
+
+// every-vertex sweep (FULL, PULL_DF, PULL_DFP); p.ntiles_host is the number of
+// quads of the in-CSR capacity, p.gacc the all-zero per-vertex accumulators
+// (left zero), rowbits / rowbase the row-start index of the in-CSR
+// (launch_row_start_index), anyb an n-bit scratch bitset, done the all-zero
+// per-chunk unit counts of the one-launch form (cdiv(n, 128) int32, left zero)
+cudaError_t launch_full_sweep(int mode, const SweepParams& p, const GatherCfg& cfg, const uint32_t* rowbits,
+                              const int32_t* rowbase, uint32_t* anyb, int32_t* done, cudaStream_t s);
 // row-start index of the in-CSR: rowbits (nquads/32 + 1 words), rowbase (as
 // many int32 + 1); tmp: scan_tmp_elems(nquads/32 + 1) int32
 cudaError_t launch_row_start_index(const int64_t* off, int32_t n, int64_t nquads, uint32_t* rowbits, int32_t* rowbase,

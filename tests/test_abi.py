@@ -58,6 +58,10 @@ def test_argument_errors_are_reported_before_any_device_work(lib):
     assert lib.pr_graph_create_edges(4, 2, src, dst, 0, 0, None, ctypes.byref(h)) == 2        # id out of range
     lib.pr_update.argtypes = [P, ctypes.c_int, ctypes.c_double, ctypes.c_double, P, P]
     assert lib.pr_update(None, 0, 0.85, 1e-10, None, None) == 1
+    lib.pr_autotune.argtypes = [P, ctypes.c_int, ctypes.c_double, ctypes.c_double, ctypes.c_int32, P]
+    assert lib.pr_autotune(None, 1, 0.85, 1e-10, 3, None) == 1
+    lib.pr_set_tuning.argtypes = [P, P]
+    assert lib.pr_set_tuning(None, None) == 1
 
 
 def test_product_path_has_no_oracle_or_cpu_fallback():
@@ -80,7 +84,7 @@ def test_binding_structs_match_the_header(tmp_path):
         pytest.skip("gcc not found")
     import paper_2401_15870_gb300 as pr
     structs = {"pr_options": pr.pr_options, "pr_stats": pr.pr_stats, "pr_server_options": pr.pr_server_options,
-               "pr_request_info": pr.pr_request_info}
+               "pr_request_info": pr.pr_request_info, "pr_tuning": pr.pr_tuning}
     lines = ['#include <stdio.h>', '#include <stddef.h>', '#include "dfpr.h"', "int main(void) {"]
     for name, cls in structs.items():
         lines.append('printf("%s %%zu\\n", sizeof(%s));' % (name, name))

@@ -363,3 +363,84 @@ def test_deterministic_across_runs(lib):
         G.update("dfp")
         outs.append(G.ranks())
     assert np.array_equal(outs[0], outs[1]) and np.array_equal(outs[1], outs[2])
+
+
+# ------------------------------------------------------------- gather settings (pr_autotune)
+
+SETTINGS = [(256, 4, 0, 0), (256, 4, 0, 1), (1024, 4, 27648, 1), (512, 2, 13824, 0), (256, 8, 3072, 1),
+            (1024, 8, 100, 0), (512, 4, 1, 1), (1024, 2, 6656, 1), (512, 8, 0, 1), (1024, 2, 0, 0)]
+
+
+@pytest.mark.parametrize("method,direction", [("static", None), ("nd", None), ("df", "pull"), ("dfp", "pull")])
+@pytest.mark.parametrize("scale,bsize", [(12, 40), (14, 262)])
+def test_every_gather_setting_gives_the_same_bits(lib, method, direction, scale, bsize):
+    """Threads per block, quads per lane, the hub staged in shared memory
+    (none, a ragged count, a count above n that covers every vertex and the
+    sentinel) and the epilogue inside or after the gather kernel change only
+    the schedule of exact integer sums: ranks and statistics are bit-identical
+    across settings, and within 1e-9 of the oracle."""
+    G, O, r0 = rank_case(lib, scale, 16, bsize, 90 + scale)
+    out = []
+    for t, q, hub, fused in SETTINGS:
+        G.set_tuning(t, q, hub, fused)
+        tu = G.tuning()
+        assert (tu.threads, tu.quads_per_lane, tu.hub_vertices, tu.fused_epilogue) == (t, q, min(hub, G.n), fused)
+        G.set_ranks(r0)
+        st = G.update(method, direction=direction, loop="host")
+        out.append((G.ranks(), st.iterations, st.vertices_ever_affected, st.vertices_processed, st.edges_processed))
+    for r, *rest in out[1:]:
+        assert np.array_equal(r, out[0][0])
+        assert rest == list(out[0][1:])
+    ref, _ = O.update(method, r_prev=r0)
+    assert np.max(np.abs(out[0][0] - ref)) < TOL
+
+
+def test_autotune_on_sweeps_keeps_the_graph_and_the_results(lib):
+    G, O, r0 = rank_case(lib, 14, 16, 262, 97)
+    G.set_ranks(r0)
+    st0 = G.update("dfp", direction="pull", loop="host")
+    r_default = G.ranks()
+    tu = G.autotune("nd", reps=2)
+    assert np.array_equal(G.ranks(), r_default)          # the trials leave the ranks as they were
+    assert tu.threads in (256, 512, 1024) and tu.quads_per_lane in (2, 4, 8)
+    assert 0 <= tu.hub_vertices <= G.n and tu.candidates >= 18 and tu.ms_gather > 0
+    assert tu.fused_epilogue in (0, 1)
+    # the staged hub is every vertex of out-degree >= hub_min_degree
+    if tu.hub_vertices:
+        deg = np.diff(G.rows(0, np.arange(G.n, dtype=np.int32), degrees_only=True))
+        assert tu.hub_min_degree >= 1
+        assert np.sum(deg > tu.hub_min_degree) <= tu.hub_vertices <= np.sum(deg >= tu.hub_min_degree)
+    assert G.tuning() == tu
+    G.set_ranks(r0)
+    st1 = G.update("dfp", direction="pull", loop="host")
+    assert np.array_equal(G.ranks(), r_default)
+    assert (st1.iterations, st1.vertices_processed) == (st0.iterations, st0.vertices_processed)
+
+
+@pytest.mark.parametrize("method", ["df", "dfp"])
+def test_autotune_on_updates_leaves_one_update(lib, method):
+    """Tuning on whole updates runs them from the entry ranks with the last
+    batch; the graph ends with the ranks of one update, equal to the oracle's."""
+    G, O, r0 = rank_case(lib, 13, 16, 200, 98)
+    G.set_ranks(r0)
+    tu = G.autotune(method)
+    assert tu.candidates >= 18
+    got = G.ranks()
+    G.set_ranks(r0)
+    G.update(method, loop="host")
+    assert np.array_equal(got, G.ranks())
+    ref, _ = O.update(method, r_prev=r0)
+    assert np.max(np.abs(got - ref)) < TOL
+    with pytest.raises(lib.PRError):
+        G.autotune("dt")
+
+
+def test_invalid_gather_settings_are_rejected(lib):
+    G, _, _ = rank_case(lib, 10, 8, 20, 5)
+    before = G.tuning()
+    # a hub of 40000 vertices is above n here, but no block's shared memory holds it
+    for t, q, hub, f in ((128, 4, 0, 1), (256, 3, 0, 1), (256, 4, -1, 1), (256, 4, 40000, 1), (2048, 4, 0, 1),
+                         (256, 4, 0, 2)):
+        with pytest.raises(lib.PRError):
+            G.set_tuning(t, q, hub, f)
+    assert G.tuning() == before
