@@ -39,8 +39,8 @@ SWEEP_BYTES_PER_VERTEX = 60
 SAMPLE_SCALE = 18
 # DRAM bytes (read + write) of one pull-form DF-P sweep (k_gather_rows + k_finish_pull) on the
 # default workload, from the one-pass ncu captures under profiles/, keyed by the gather setting
-# (threads, quads per lane, hub vertices); a setting without a capture reports null
-SWEEP_DRAM_BYTES_RMAT25 = {(256, 4, 0): 11.42e9}
+# (threads, quads per lane, hub vertices, fused epilogue); a setting without a capture reports null
+SWEEP_DRAM_BYTES_RMAT25 = {(256, 4, 0, 0): 11.42e9, (512, 4, 0, 0): 11.28e9}
 
 
 def parse():
@@ -293,7 +293,8 @@ def run_gpu(a, rank, world, local_rank):
         "roofline": {"bound": "hbm", "kernel": "DF-P rank sweep (k_gather_rows + k_finish_pull in pull form, "
                                "k_sweep<DFP> in push form)", "achieved": achieved, "peak": peak,
                      "unit": "GB/s", "frac": achieved / peak,
-                     "traffic": SWEEP_DRAM_BYTES_RMAT25.get((tuning.threads, tuning.quads_per_lane, tuning.hub_vertices))
+                     "traffic": SWEEP_DRAM_BYTES_RMAT25.get((tuning.threads, tuning.quads_per_lane, tuning.hub_vertices,
+                                                             tuning.fused_epilogue))
                      if (a.scale, a.edge_factor, a.batch_frac) == (25, 32, 1e-4) else None,
                      "peak_source": peak_src + " (MEASURED_PEAKS.json hbm_gbs)" if peak_src == "measured" else
                      "fallback 6800 GB/s"},
@@ -358,8 +359,9 @@ def run_batched(a, rank, world, local_rank):
         src, dst = sg.rmat(scale, ef << scale, seed + 7919 * rank)
         G = pr.Graph.from_edges(n, src, dst, device=True, stream=stream)
         size = max(1, int(round(a.batch_frac * G.m)))
-        # batches for the group steps, then as many for the plain steps
-        batches.append([sg.batch(n, src, dst, size, seed + 1 + i) for i in range(2 * nb)])
+        # batches for the group steps, then as many for the plain steps, then
+        # one for tuning
+        batches.append([sg.batch(n, src, dst, size, seed + 1 + i) for i in range(2 * nb + 1)])
         host_batches.append([[t.cpu().pin_memory() for t in sg.batch(n, src, dst, size, seed + 50001 + i)]
                              for i in range(a.e2e_steps)])
         graphs.append(G)
@@ -368,6 +370,16 @@ def run_batched(a, rank, world, local_rank):
     torch.cuda.synchronize()
     grp = pr.Group(graphs, stream=stream)
     grp.update("static", alpha=ALPHA, tau=TAU)
+    # tuning, before anything is timed: the group's unit sizes on group DF-P
+    # updates, and every graph's own settings on its DF-P updates (for the
+    # per-graph baseline), all on one extra batch per graph
+    gtune, ptune = grp.tuning(), []
+    if a.tune != "default":
+        for G, b in zip(graphs, batches):
+            G.apply_batch_device(*b[2 * nb])
+        gtune = grp.autotune("dfp", alpha=ALPHA, tau=TAU)
+        ptune = [G.autotune("dfp", alpha=ALPHA, tau=TAU) for G in graphs]
+        grp.update("dfp", alpha=ALPHA, tau=TAU)
 
     def group_step(i):
         for G, b in zip(graphs, batches):
@@ -454,6 +466,11 @@ def run_batched(a, rank, world, local_rank):
         "gpu_launches": launches_g,
         "clocks": clk,
         "detail": {
+            "group_unit_sizes": dataclasses.asdict(gtune),
+            "per_graph_settings": {"threads": sorted(set(t.threads for t in ptune)),
+                                   "quads_per_lane": sorted(set(t.quads_per_lane for t in ptune)),
+                                   "hub_vertices": sorted(set(t.hub_vertices for t in ptune)),
+                                   "fused_epilogue": sorted(set(t.fused_epilogue for t in ptune))},
             "group_update_ms_mean": upd_ms / a.steps,
             "iterations_max_mean": statistics.mean(max(s.iterations for s in step) for step in st_g),
             "iterations_mean": statistics.mean(s.iterations for s in flat),

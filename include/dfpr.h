@@ -286,6 +286,35 @@ pr_status pr_group_update_members(pr_group* grp, pr_method method, double alpha,
 void pr_group_destroy(pr_group* grp);
 
 /*
+ * Unit sizes of the group kernels: a gather unit is one warp step over 32 x
+ * quads_per_lane in-CSR quads (2, 4 or 8), an epilogue unit is
+ * chunks_per_unit 32-vertex chunks (1, 2 or 4) whose loads a warp issues
+ * together.  Smaller units spread small graphs over more warps; larger ones
+ * keep more loads in flight per warp.  Defaults 4 / 4.  The setting changes no
+ * result (the sums are exact).
+ * pr_group_autotune: runs reps (0: 1) group updates of the method per
+ *   candidate (the device loop, CUDA-event time of the whole update), every
+ *   graph starting from its ranks on entry (with its last batch for DF / DF-P),
+ *   keeps the fastest, and puts the ranks on entry back at the end (a graph
+ *   without ranks keeps those of the last Static trial).  Dynamic methods need
+ *   ranks on every graph (PR_ENORANKS).  Errors: PR_EINVAL (Dynamic
+ *   Traversal, bad alpha / tau / reps, an update in flight), PR_ENORANKS,
+ *   PR_ENOMEM, PR_ECUDA.
+ * pr_group_set_tuning: quads_per_lane and chunks_per_unit (the other fields
+ *   are ignored); other values give PR_EINVAL and no change.
+ */
+typedef struct {
+  int32_t quads_per_lane;
+  int32_t chunks_per_unit;
+  float ms_update;          /* pr_group_autotune: the chosen setting's update time, ms */
+  int32_t candidates;       /* pr_group_autotune: settings timed                      */
+} pr_group_tuning;
+pr_status pr_group_autotune(pr_group* grp, pr_method method, double alpha, double tau, int32_t reps,
+                            pr_group_tuning* out);
+pr_status pr_group_get_tuning(const pr_group* grp, pr_group_tuning* out);
+pr_status pr_group_set_tuning(pr_group* grp, const pr_group_tuning* in);
+
+/*
  * Serving: a request loop over resident graphs.  The paper updates one graph
  * per batch; a server accepts update batches for many graphs as they arrive
  * (from any thread) and turns them into DF / DF-P updates on one worker
@@ -376,10 +405,13 @@ void pr_server_destroy(pr_server* srv);
  *   the graph's ranks and edges are left as they were.  method PR_DF or
  *   PR_DFP: reps (0: 1) whole updates per candidate (the iteration loop on the
  *   host, options at their defaults), each from the ranks the graph has on
- *   entry and with its last batch; the rank-sweep kernel time decides.  Every
- *   setting gives the same bits, so the graph is left as after one
- *   pr_update(method, alpha, tau).  Needs ranks (PR_ENORANKS).  The trials
- *   allocate one n-vector of device memory for the duration of the call.
+ *   entry and with its last batch; the rank-sweep kernel time decides, and the
+ *   ranks on entry are put back at the end.  Needs ranks (PR_ENORANKS).  A
+ *   graph with ranks below PR_DEVICE_LOOP_SLOTS in-CSR slots, whose pr_update
+ *   runs the loop on the device with the group kernels, also has the unit
+ *   sizes of those kernels tuned (pr_group_autotune on its one-graph group,
+ *   same method, ranks put back).  The trials allocate one n-vector of device memory for the
+ *   duration of the call.
  *   Errors: PR_EINVAL (method PR_DYNAMIC_TRAVERSAL, whose sweeps are list
  *   sweeps, or bad alpha / tau / reps), PR_ENORANKS, PR_ENOMEM, PR_ECUDA.
  * pr_get_tuning: the graph's current setting (the defaults 256 / 4 / 0 / 0

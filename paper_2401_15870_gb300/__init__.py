@@ -60,6 +60,19 @@ class Tuning:
     candidates: int
 
 
+class pr_group_tuning(ctypes.Structure):
+    _fields_ = [("quads_per_lane", ctypes.c_int32), ("chunks_per_unit", ctypes.c_int32), ("ms_update", ctypes.c_float),
+                ("candidates", ctypes.c_int32)]
+
+
+@dataclass
+class GroupTuning:
+    quads_per_lane: int
+    chunks_per_unit: int
+    ms_update: float
+    candidates: int
+
+
 @dataclass
 class Stats:
     iterations: int
@@ -124,6 +137,9 @@ def load():
         "pr_autotune": ([_P, ctypes.c_int, f64, f64, i32, _P], ctypes.c_int),
         "pr_get_tuning": ([_P, _P], ctypes.c_int),
         "pr_set_tuning": ([_P, _P], ctypes.c_int),
+        "pr_group_autotune": ([_P, ctypes.c_int, f64, f64, i32, _P], ctypes.c_int),
+        "pr_group_get_tuning": ([_P, _P], ctypes.c_int),
+        "pr_group_set_tuning": ([_P, _P], ctypes.c_int),
     }
     for name, (args, res) in sig.items():
         f = getattr(lib, name)
@@ -408,9 +424,33 @@ def pr_get_tuning(h):
     return _tuning(t)
 
 
-def pr_set_tuning(h, threads=256, quads_per_lane=4, hub_vertices=0, fused_epilogue=1):
+def pr_set_tuning(h, threads=256, quads_per_lane=4, hub_vertices=0, fused_epilogue=0):
     t = pr_tuning(int(threads), int(quads_per_lane), int(hub_vertices), int(fused_epilogue), 0, 0.0, 0)
     _check(load().pr_set_tuning(h, ctypes.byref(t)), h)
+
+
+def _group_tuning(t):
+    return GroupTuning(*(getattr(t, f) for f, _ in pr_group_tuning._fields_))
+
+
+def pr_group_autotune(q, method="dfp", alpha=0.85, tau=1e-10, reps=0):
+    """Time the group kernels' unit sizes on whole group updates and keep the
+    fastest; every graph's ranks on entry are put back."""
+    m = METHODS[method] if isinstance(method, str) else int(method)
+    t = pr_group_tuning()
+    _check(load().pr_group_autotune(q, m, float(alpha), float(tau), int(reps), ctypes.byref(t)))
+    return _group_tuning(t)
+
+
+def pr_group_get_tuning(q):
+    t = pr_group_tuning()
+    _check(load().pr_group_get_tuning(q, ctypes.byref(t)))
+    return _group_tuning(t)
+
+
+def pr_group_set_tuning(q, quads_per_lane=4, chunks_per_unit=4):
+    t = pr_group_tuning(int(quads_per_lane), int(chunks_per_unit), 0.0, 0)
+    _check(load().pr_group_set_tuning(q, ctypes.byref(t)))
 
 
 def pr_kernel_launches() -> int:
@@ -501,7 +541,7 @@ class Graph:
     def tuning(self) -> Tuning:
         return pr_get_tuning(self._h)
 
-    def set_tuning(self, threads=256, quads_per_lane=4, hub_vertices=0, fused_epilogue=1):
+    def set_tuning(self, threads=256, quads_per_lane=4, hub_vertices=0, fused_epilogue=0):
         pr_set_tuning(self._h, threads, quads_per_lane, hub_vertices, fused_epilogue)
 
 
@@ -517,6 +557,15 @@ class Group:
 
     def update_members(self, members, method, **kw):
         return pr_group_update_members(self._q, members, method, **kw)
+
+    def autotune(self, method="dfp", alpha=0.85, tau=1e-10, reps=0) -> GroupTuning:
+        return pr_group_autotune(self._q, method, alpha, tau, reps)
+
+    def tuning(self) -> GroupTuning:
+        return pr_group_get_tuning(self._q)
+
+    def set_tuning(self, quads_per_lane=4, chunks_per_unit=4):
+        pr_group_set_tuning(self._q, quads_per_lane, chunks_per_unit)
 
     def close(self):
         if self._q:

@@ -35,7 +35,10 @@ using namespace dfpr;
 namespace {
 
 constexpr int GR_THREADS = 256;
-constexpr int64_t GR_GATHER_QUADS = 32 * SW_QPT;   // quads per gather work unit (one warp step)
+// the unit sizes a group can be set to: quads per lane of a gather unit (one
+// warp step of 32 x QPT quads) and 32-vertex chunks of an epilogue unit
+constexpr int GR_QPT[3] = {2, 4, 8};
+constexpr int GR_FU[3] = {1, 2, 4};
 
 // per graph, fixed during one update
 struct GDesc {
@@ -167,7 +170,8 @@ __global__ void __launch_bounds__(GR_THREADS) k_g_mark(const GRun* __restrict__ 
   }
 }
 
-// gather phase of one iteration, every live graph
+// gather phase of one iteration, every live graph (units of 32 x QPT quads)
+template <int QPT>
 __global__ void __launch_bounds__(GR_THREADS) k_g_gather(const GRun* __restrict__ run, const GDesc* __restrict__ desc,
                                                          const GState* __restrict__ st) {
   __shared__ int64_t pre[PR_GROUP_MAX + 1];
@@ -182,8 +186,8 @@ __global__ void __launch_bounds__(GR_THREADS) k_g_gather(const GRun* __restrict_
     if (st[g].done) continue;
     const GDesc& d = desc[g];
     const int c = st[g].cur;
-    gather_step<true>(d.icol, d.C[c], d.X[c], d.S[c], d.rowbits, d.rowbase, d.nquads, d.n, d.acc, d.anyb,
-                      (u - pre[g]) * GR_GATHER_QUADS, pol_stream, pol_keep);
+    gather_step<true, QPT>(d.icol, d.C[c], d.X[c], d.S[c], d.rowbits, d.rowbase, d.nquads, d.n, d.acc, d.anyb,
+                           (u - pre[g]) * (32 * QPT), pol_stream, pol_keep);
   }
 }
 
@@ -224,9 +228,9 @@ __device__ __forceinline__ void flush_totals(PullTotals& t, GState* s) {
   t = PullTotals();
 }
 
-// epilogue phase of one iteration, every live graph
+// epilogue phase of one iteration, every live graph, units of FU chunks
 // (Eq. 2 for DF-P when CLOSED, else Eq. 1)
-template <bool CLOSED>
+template <bool CLOSED, int FU>
 __global__ void __launch_bounds__(GR_THREADS, 2) k_g_finish(const GRun* __restrict__ run,
                                                             const GDesc* __restrict__ desc, GState* __restrict__ st) {
   __shared__ int64_t pre[PR_GROUP_MAX + 1];
@@ -263,8 +267,8 @@ __global__ void __launch_bounds__(GR_THREADS, 2) k_g_finish(const GRun* __restri
     p.tau_f = run->tau_f;
     p.tau_p = run->tau_p;
     const int64_t nchunks = cdiv(d.n, 32);
-    const int64_t ch0 = (u - pre[g]) * FIN_U;
-    finish_pull_step<CLOSED>(p, d.acc, d.anyb, ch0, nchunks, t);
+    const int64_t ch0 = (u - pre[g]) * FU;
+    finish_pull_step<CLOSED, GView, false, FU>(p, d.acc, d.anyb, ch0, nchunks, t);
   }
   if (tg >= 0) flush_totals(t, st + tg);
 }
@@ -323,9 +327,16 @@ struct pr_group {
   GDesc* h_desc = nullptr;
   GState* h_state = nullptr;
   int64_t* h_pre = nullptr;
-  // one CUDA graph per epilogue form (index 1: DF-P), built on first use
+  // unit sizes (indices into GR_QPT / GR_FU), set by pr_group_set_tuning or
+  // pr_group_autotune
+  int qi = 1, fi = 2;
+  float tune_ms = 0.f;
+  int32_t tune_trials = 0;
+  // one CUDA graph per epilogue form (index 1: DF-P), built on first use with
+  // the unit sizes of exec_q / exec_f
   cudaGraph_t graph[2] = {nullptr, nullptr};
   cudaGraphExec_t exec[2] = {nullptr, nullptr};
+  int exec_q[2] = {-1, -1}, exec_f[2] = {-1, -1};
   cudaGraphConditionalHandle cond[2] = {0, 0};
   cudaEvent_t ev[3] = {nullptr, nullptr, nullptr};
   // the update in flight: its members (group indices) and method
@@ -334,13 +345,12 @@ struct pr_group {
   pr_method cur_method = PR_DFP;
 };
 
+static void drop_exec(pr_group* q, int k);
+
 static void group_free(pr_group* q) {
   if (!q) return;
   if (q->stream) cudaStreamSynchronize(q->stream);
-  for (int k = 0; k < 2; k++) {
-    if (q->exec[k]) cudaGraphExecDestroy(q->exec[k]);
-    if (q->graph[k]) cudaGraphDestroy(q->graph[k]);
-  }
+  for (int k = 0; k < 2; k++) drop_exec(q, k);
   for (void* p : {(void*)q->d_run, (void*)q->d_desc, (void*)q->d_state, (void*)q->d_pre, (void*)q->tab_sc,
                   (void*)q->tab_cl})
     if (p) cudaFree(p);
@@ -368,16 +378,46 @@ static cudaError_t add_kernel(cudaGraph_t graph, cudaGraphNode_t* node, const cu
   return cudaGraphAddKernelNode(node, graph, dep, ndep, &kp);
 }
 
+static const void* gather_fn(int qi) {
+  switch (qi) {
+    case 0: return (const void*)k_g_gather<2>;
+    case 1: return (const void*)k_g_gather<4>;
+    default: return (const void*)k_g_gather<8>;
+  }
+}
+
+static const void* finish_fn(int k, int fi) {
+  switch (fi * 2 + k) {
+    case 0: return (const void*)k_g_finish<false, 1>;
+    case 1: return (const void*)k_g_finish<true, 1>;
+    case 2: return (const void*)k_g_finish<false, 2>;
+    case 3: return (const void*)k_g_finish<true, 2>;
+    case 4: return (const void*)k_g_finish<false, 4>;
+    default: return (const void*)k_g_finish<true, 4>;
+  }
+}
+
+static void drop_exec(pr_group* q, int k) {
+  if (q->exec[k]) cudaGraphExecDestroy(q->exec[k]);
+  if (q->graph[k]) cudaGraphDestroy(q->graph[k]);
+  q->exec[k] = nullptr;
+  q->graph[k] = nullptr;
+  q->exec_q[k] = q->exec_f[k] = -1;
+}
+
 // init -> mark -> WHILE (gather -> finish -> control); k = 1 for the DF-P epilogue
 static cudaError_t build_exec(pr_group* q, int k) {
   cudaError_t e;
   cudaGraph_t& graph = q->graph[k];
   if ((e = cudaGraphCreate(&graph, 0)) != cudaSuccess) return e;
   if ((e = cudaGraphConditionalHandleCreate(&q->cond[k], graph, 0, 0)) != cudaSuccess) return e;
-  const void* fin = k ? (const void*)k_g_finish<true> : (const void*)k_g_finish<false>;
+  const void* fin = finish_fn(k, q->fi);
+  const void* gat = gather_fn(q->qi);
+  q->exec_q[k] = q->qi;
+  q->exec_f[k] = q->fi;
   const int sms = num_sms();
   const int g_init = sms * blocks_per_sm((const void*)k_g_init, GR_THREADS);
-  const int g_gather = sms * blocks_per_sm((const void*)k_g_gather, GR_THREADS);
+  const int g_gather = sms * blocks_per_sm(gat, GR_THREADS);
   const int g_finish = sms * blocks_per_sm(fin, GR_THREADS);
   cudaGraphNode_t n_init, n_mark, n_loop, n_gather, n_finish, n_ctl;
   void* a_init[] = {&q->d_run, &q->d_desc, &q->d_state, &q->cond[k]};
@@ -394,8 +434,7 @@ static cudaError_t build_exec(pr_group* q, int k) {
   cp.conditional.size = 1;
   if ((e = cudaGraphAddNode(&n_loop, graph, &n_mark, nullptr, 1, &cp)) != cudaSuccess) return e;
   cudaGraph_t body = cp.conditional.phGraph_out[0];
-  if ((e = add_kernel(body, &n_gather, nullptr, 0, (const void*)k_g_gather, g_gather, a_gather)) != cudaSuccess)
-    return e;
+  if ((e = add_kernel(body, &n_gather, nullptr, 0, gat, g_gather, a_gather)) != cudaSuccess) return e;
   if ((e = add_kernel(body, &n_finish, &n_gather, 1, fin, g_finish, a_finish)) != cudaSuccess) return e;
   cudaKernelNodeParams kp;
   memset(&kp, 0, sizeof(kp));
@@ -460,21 +499,24 @@ void pr_group_destroy(pr_group* q) { group_free(q); }
 static cudaError_t host_loop(pr_group* q, int k, int32_t max_iter) {
   cudaStream_t s = q->stream;
   const int sms = num_sms();
-  const void* fin = k ? (const void*)k_g_finish<true> : (const void*)k_g_finish<false>;
+  const void* fin = finish_fn(k, q->fi);
+  const void* gat = gather_fn(q->qi);
   const int g_init = sms * blocks_per_sm((const void*)k_g_init, GR_THREADS);
-  const int g_gather = sms * blocks_per_sm((const void*)k_g_gather, GR_THREADS);
+  const int g_gather = sms * blocks_per_sm(gat, GR_THREADS);
   const int g_finish = sms * blocks_per_sm(fin, GR_THREADS);
   const cudaGraphConditionalHandle none = 0;
+  void* a3[] = {&q->d_run, &q->d_desc, &q->d_state};
   note_launch();
   k_g_init<<<g_init, GR_THREADS, 0, s>>>(q->d_run, q->d_desc, q->d_state, none);
   note_launch();
   k_g_mark<<<g_init, GR_THREADS, 0, s>>>(q->d_run, q->d_desc);
   for (int32_t it = 0; it < max_iter; it++) {
     note_launch();
-    k_g_gather<<<g_gather, GR_THREADS, 0, s>>>(q->d_run, q->d_desc, q->d_state);
+    cudaError_t le = cudaLaunchKernel(gat, dim3(g_gather), dim3(GR_THREADS), a3, 0, s);
+    if (le != cudaSuccess) return le;
     note_launch();
-    if (k) k_g_finish<true><<<g_finish, GR_THREADS, 0, s>>>(q->d_run, q->d_desc, q->d_state);
-    else k_g_finish<false><<<g_finish, GR_THREADS, 0, s>>>(q->d_run, q->d_desc, q->d_state);
+    le = cudaLaunchKernel(fin, dim3(g_finish), dim3(GR_THREADS), a3, 0, s);
+    if (le != cudaSuccess) return le;
     note_launch();
     k_g_control<<<1, GR_THREADS, 0, s>>>(q->d_run, q->d_state, none);
     cudaError_t e = cudaMemcpyAsync(&q->h_run->live, &q->d_run->live, sizeof(int32_t), cudaMemcpyDeviceToHost, s);
@@ -547,8 +589,8 @@ pr_status group_launch(pr_group* q, pr_method method, double alpha, double tau, 
     d.n = g->n;
     d.id_bits = g->id_bits;
     d.C0 = (1.0 - alpha) / (double)g->n;
-    wpre[i + 1] = wpre[i] + cdiv(d.nquads, GR_GATHER_QUADS);
-    fpre[i + 1] = fpre[i] + cdiv(cdiv((int64_t)g->n, 32), FIN_U);
+    wpre[i + 1] = wpre[i] + cdiv(d.nquads, 32 * GR_QPT[q->qi]);
+    fpre[i + 1] = fpre[i] + cdiv(cdiv((int64_t)g->n, 32), GR_FU[q->fi]);
     bpre[i + 1] = bpre[i] + cdiv((int64_t)g->n, 32);
     dpre[i + 1] = dpre[i] + ((method == PR_DF || method == PR_DFP) ? g->n_dmin + g->n_dplus : 0);
   }
@@ -589,6 +631,7 @@ pr_status group_launch(pr_group* q, pr_method method, double alpha, double tau, 
     return PR_ECUDA;
   const int k = method == PR_DFP ? 1 : 0;
   if (r.use_graph) {
+    if (q->exec[k] && (q->exec_q[k] != q->qi || q->exec_f[k] != q->fi)) drop_exec(q, k);
     if (!q->exec[k] && build_exec(q, k) != cudaSuccess) {
       cudaGetLastError();
       return PR_ECUDA;
@@ -667,3 +710,100 @@ pr_status pr_group_update_members(pr_group* q, pr_method method, double alpha, d
 
 }  // extern "C"
 
+// ------------------------------------------------------------------ unit sizes
+
+extern "C" {
+
+pr_status pr_group_get_tuning(const pr_group* q, pr_group_tuning* out) {
+  if (!q || !out) return PR_EINVAL;
+  out->quads_per_lane = GR_QPT[q->qi];
+  out->chunks_per_unit = GR_FU[q->fi];
+  out->ms_update = q->tune_ms;
+  out->candidates = q->tune_trials;
+  return PR_OK;
+}
+
+pr_status pr_group_set_tuning(pr_group* q, const pr_group_tuning* in) {
+  if (!q || !in || q->in_flight) return PR_EINVAL;
+  int qi = -1, fi = -1;
+  for (int i = 0; i < 3; i++) {
+    if (GR_QPT[i] == in->quads_per_lane) qi = i;
+    if (GR_FU[i] == in->chunks_per_unit) fi = i;
+  }
+  if (qi < 0 || fi < 0) return PR_EINVAL;
+  q->qi = qi;
+  q->fi = fi;
+  q->tune_ms = 0.f;
+  q->tune_trials = 0;
+  return PR_OK;
+}
+
+pr_status pr_group_autotune(pr_group* q, pr_method method, double alpha, double tau, int32_t reps,
+                            pr_group_tuning* out) {
+  if (!q || q->in_flight || reps < 0 || reps > 100) return PR_EINVAL;
+  if (method != PR_STATIC && method != PR_NAIVE_DYNAMIC && method != PR_DF && method != PR_DFP) return PR_EINVAL;
+  if (!(alpha >= 0.0 && alpha < 1.0) || !(tau >= 0.0)) return PR_EINVAL;
+  if (reps == 0) reps = 1;
+  const int G = q->G;
+  if (method != PR_STATIC)
+    for (int i = 0; i < G; i++)
+      if (!q->graphs[i]->g.has_ranks) return PR_ENORANKS;
+  // the ranks of every graph on entry, put back before every trial and at the end
+  std::vector<int64_t> off(G + 1, 0);
+  for (int i = 0; i < G; i++) off[i + 1] = off[i] + (q->graphs[i]->g.has_ranks ? q->graphs[i]->g.n : 0);
+  double* saved = nullptr;
+  if (off[G] > 0 && cudaMalloc((void**)&saved, sizeof(double) * (size_t)off[G]) != cudaSuccess) {
+    cudaGetLastError();
+    return PR_ENOMEM;
+  }
+  auto copy_ranks = [&](bool back) -> cudaError_t {
+    for (int i = 0; i < G; i++) {
+      Graph* g = &q->graphs[i]->g;
+      if (off[i + 1] == off[i]) continue;
+      double* dst = back ? g->R : saved + off[i];
+      const double* src = back ? saved + off[i] : g->R;
+      cudaError_t e = cudaMemcpyAsync(dst, src, sizeof(double) * (size_t)g->n, cudaMemcpyDeviceToDevice, g->stream);
+      if (e == cudaSuccess && back) e = launch_contrib_all(g->R, g->C[g->ccur], g->out.deg, g->tab_sc, g->n, g->stream);
+      if (e == cudaSuccess) e = cudaStreamSynchronize(g->stream);
+      if (e != cudaSuccess) return e;
+    }
+    return cudaSuccess;
+  };
+  pr_status st = copy_ranks(false) == cudaSuccess ? PR_OK : PR_ECUDA;
+  const int qi0 = q->qi, fi0 = q->fi;
+  int bq = qi0, bf = fi0, trials = 0;
+  float best = -1.f;
+  std::vector<pr_stats> stats(G);
+  for (int qi = 0; qi < 3 && st == PR_OK; qi++)
+    for (int fi = 0; fi < 3 && st == PR_OK; fi++) {
+      q->qi = qi;
+      q->fi = fi;
+      double ms = 0.0;
+      for (int r = 0; r < reps && st == PR_OK; r++) {
+        if (copy_ranks(true) != cudaSuccess) {
+          st = PR_ECUDA;
+          break;
+        }
+        st = group_launch(q, method, alpha, tau, nullptr, nullptr, 0);
+        if (st == PR_OK) st = group_complete(q, stats.data());
+        ms += stats[0].ms_update;
+      }
+      if (st != PR_OK) break;
+      trials++;
+      if (best < 0.f || ms / reps < best) {
+        best = (float)(ms / reps);
+        bq = qi;
+        bf = fi;
+      }
+    }
+  if (st == PR_OK && copy_ranks(true) != cudaSuccess) st = PR_ECUDA;
+  if (saved) cudaFree(saved);
+  q->qi = st == PR_OK ? bq : qi0;
+  q->fi = st == PR_OK ? bf : fi0;
+  if (st != PR_OK) return st;
+  q->tune_ms = best;
+  q->tune_trials = trials;
+  return out ? pr_group_get_tuning(q, out) : PR_OK;
+}
+
+}  // extern "C"

@@ -128,8 +128,8 @@ pr_status tune_sweeps(pr_graph* h, double alpha, int32_t reps, GatherCfg* best, 
 }
 
 // DF / DF-P: reps whole updates per trial (host loop, sweep kernels timed with
-// events), each from the ranks the graph had on entry and with its last batch.
-// Every setting gives the same bits, so the graph ends as after one update.
+// events), each from the ranks the graph had on entry and with its last batch;
+// those ranks are put back at the end.
 pr_status tune_updates(pr_graph* h, int method, double alpha, double tau, int32_t reps, GatherCfg* best,
                        float* best_ms, int32_t* trials) {
   Graph* g = &h->g;
@@ -163,6 +163,11 @@ pr_status tune_updates(pr_graph* h, int method, double alpha, double tau, int32_
     }
   }
   h->gcfg = keep;
+  if (st == PR_OK) {
+    e = cudaMemcpyAsync(g->R, saved, sizeof(double) * (size_t)g->n, cudaMemcpyDeviceToDevice, s);
+    if (e == cudaSuccess) e = launch_contrib_all(g->R, g->C[g->ccur], g->out.deg, g->tab_sc, g->n, s);
+    if (e != cudaSuccess) st = (pr_status)cuda_fail(g, e, "pr_autotune");
+  }
   cudaStreamSynchronize(s);
   cudaFree(saved);
   return st;
@@ -192,6 +197,17 @@ pr_status pr_autotune(pr_graph* h, pr_method method, double alpha, double tau, i
   h->gcfg = best;
   h->gcfg_ms = best_ms;
   h->gcfg_trials = trials;
+  // graphs that pr_update runs with the loop on the device use the group
+  // kernels of a one-graph group: tune its unit sizes too
+  if (g->in.cap < PR_DEVICE_LOOP_SLOTS && g->has_ranks) {
+    if (!h->solo) {
+      pr_graph* one[1] = {h};
+      st = pr_group_create(1, one, g->stream, &h->solo);
+      if (st != PR_OK) return st;
+    }
+    st = pr_group_autotune(h->solo, method, alpha, tau, 1, nullptr);
+    if (st != PR_OK) return st;
+  }
   return out ? read_tuning(h, out) : PR_OK;
 }
 

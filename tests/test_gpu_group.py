@@ -180,3 +180,60 @@ def test_group_errors(lib):
         grp.update("dfp")
     finally:
         grp.close()
+
+
+@pytest.mark.parametrize("method", ["dfp", "df", "nd"])
+def test_every_unit_size_gives_the_same_bits(lib, cases, method):
+    """Gather units of 32 x 2/4/8 quads and epilogue units of 1/2/4 chunks
+    change only how the group's work is cut: ranks and statistics are
+    bit-identical across all nine settings (and to the oracle within 1e-9)."""
+    graphs = [c[0] for c in cases]
+    grp = lib.Group(graphs)
+    try:
+        out = []
+        for q in (2, 4, 8):
+            for f in (1, 2, 4):
+                grp.set_tuning(q, f)
+                assert (grp.tuning().quads_per_lane, grp.tuning().chunks_per_unit) == (q, f)
+                for G, O, r0 in cases:
+                    G.set_ranks(r0)
+                for loop in ("device", "host"):
+                    if loop == "host":
+                        for G, O, r0 in cases:
+                            G.set_ranks(r0)
+                    st = grp.update(method, loop=loop)
+                    out.append(([G.ranks() for G in graphs], [(s.iterations, s.vertices_processed) for s in st]))
+        for ranks, its in out[1:]:
+            assert all(np.array_equal(a, b) for a, b in zip(ranks, out[0][0]))
+            assert its == out[0][1]
+        for (G, O, r0), got in zip(cases, out[0][0]):
+            ref, _ = O.update(method, r_prev=r0)
+            assert np.max(np.abs(got - ref)) < TOL
+    finally:
+        grp.close()
+
+
+def test_group_autotune_keeps_the_ranks(lib, cases):
+    graphs = [c[0] for c in cases]
+    for G, O, r0 in cases:
+        G.set_ranks(r0)
+    grp = lib.Group(graphs)
+    try:
+        tu = grp.autotune("dfp")
+        assert tu.candidates == 9 and tu.ms_update > 0
+        assert tu.quads_per_lane in (2, 4, 8) and tu.chunks_per_unit in (1, 2, 4)
+        assert grp.tuning() == tu
+        for G, O, r0 in cases:
+            assert np.array_equal(G.ranks(), r0)
+        st = grp.update("dfp")
+        for (G, O, r0), s in zip(cases, st):
+            ref, _ = O.update("dfp", r_prev=r0)
+            assert np.max(np.abs(G.ranks() - ref)) < TOL
+        for bad in ((3, 4), (4, 3), (16, 4), (4, 8)):
+            with pytest.raises(lib.PRError):
+                grp.set_tuning(*bad)
+        assert grp.tuning() == tu
+        with pytest.raises(lib.PRError):
+            grp.autotune("dt")
+    finally:
+        grp.close()

@@ -418,19 +418,22 @@ def test_autotune_on_sweeps_keeps_the_graph_and_the_results(lib):
 
 
 @pytest.mark.parametrize("method", ["df", "dfp"])
-def test_autotune_on_updates_leaves_one_update(lib, method):
+@pytest.mark.parametrize("scale", [13, 12])
+def test_autotune_on_updates_keeps_the_ranks(lib, method, scale):
     """Tuning on whole updates runs them from the entry ranks with the last
-    batch; the graph ends with the ranks of one update, equal to the oracle's."""
-    G, O, r0 = rank_case(lib, 13, 16, 200, 98)
+    batch and puts those ranks back; a graph small enough for the device loop
+    also gets its one-graph group tuned.  The update that follows, with the
+    device loop or the host loop, equals the oracle's."""
+    G, O, r0 = rank_case(lib, scale, 16, 200, 98)
     G.set_ranks(r0)
     tu = G.autotune(method)
     assert tu.candidates >= 18
-    got = G.ranks()
-    G.set_ranks(r0)
-    G.update(method, loop="host")
-    assert np.array_equal(got, G.ranks())
+    assert np.array_equal(G.ranks(), r0)
     ref, _ = O.update(method, r_prev=r0)
-    assert np.max(np.abs(got - ref)) < TOL
+    for loop in ("device", "host"):
+        G.set_ranks(r0)
+        G.update(method, loop=loop)
+        assert np.max(np.abs(G.ranks() - ref)) < TOL
     with pytest.raises(lib.PRError):
         G.autotune("dt")
 
