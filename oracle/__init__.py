@@ -10,7 +10,9 @@ the CUDA library and never imports it.
 Every function follows a passage of the paper:
   * ``Graph``            -- edge set with one self-loop per vertex (Sec. 5.1.3)
   * ``Graph.apply_batch`` -- E_t = (E_{t-1} \\ D) u I, effective deltas (Sec. 3.2)
-  * ``Graph.update``      -- Static / ND / DT / DF / DF-P (Sec. 3.1, 2.3, Alg. 1)
+  * ``Graph.update``      -- Static / ND / DT / DF / DF-P (Sec. 3.1, 2.3, Alg. 1),
+                             with the expansion measures of Sec. 4.3 and the
+                             asynchronous order of Alg. 1 (Sec. 4.4) as options
   * ``Graph.initial_affected`` -- initial marking of Alg. 1
   * ``Graph.dt_affected`` -- reachability of Dynamic Traversal (Sec. 3.3.2)
   * ``rank_plain`` / ``rank_closed_loop`` -- Eq. 1 and Eq. 2
@@ -37,6 +39,9 @@ _LIB = os.path.join(_HERE, "liboracle.so")
 
 STATIC, NAIVE_DYNAMIC, DYNAMIC_TRAVERSAL, DF, DFP = 0, 1, 2, 3, 4
 METHODS = {"static": STATIC, "nd": NAIVE_DYNAMIC, "dt": DYNAMIC_TRAVERSAL, "df": DF, "dfp": DFP}
+# the DF / DF-P measures of Sec. 4.3: dr / max(r, R[v]) (Alg. 1), dr, dr / d
+METRICS = {"relative": 0, "absolute": 1, "contrib": 2}
+ORDERS = {"sync": 0, "async": 1}
 _ERR = {1: "invalid argument", 2: "vertex id out of range", 3: "out of memory", 4: "no previous ranks"}
 
 
@@ -80,6 +85,8 @@ def _load():
         lib.or_rank_closed_loop.restype = f64
         lib.or_update.argtypes = [P, ctypes.c_int, f64, f64, f64, f64, i32, P, P, P]
         lib.or_update.restype = ctypes.c_int
+        lib.or_update_ex.argtypes = [P, ctypes.c_int, f64, f64, f64, f64, i32, ctypes.c_int, ctypes.c_int, P, P, P]
+        lib.or_update_ex.restype = ctypes.c_int
         _lib = lib
     return _lib
 
@@ -194,16 +201,20 @@ class Graph:
             raise OracleError("out of memory")
         return f.astype(bool)
 
-    def update(self, method, alpha=0.85, tau=1e-10, tau_f=1e-6, tau_p=1e-6, max_iter=500, r_prev=None):
-        """Run one method; returns (ranks, Stats)."""
+    def update(self, method, alpha=0.85, tau=1e-10, tau_f=1e-6, tau_p=1e-6, max_iter=500, r_prev=None,
+               metric="relative", order="sync"):
+        """Run one method; returns (ranks, Stats).  metric: the DF / DF-P
+        measure of Sec. 4.3 ("relative", "absolute", "contrib"); order: "sync"
+        or "async" (Alg. 1 with one rank vector, ascending vertex id)."""
         m = METHODS[method] if isinstance(method, str) else int(method)
         out = np.zeros(self.n, np.float64)
         prev = None if r_prev is None else np.ascontiguousarray(np.asarray(r_prev, dtype=np.float64))
         if prev is not None and prev.size != self.n:
             raise ValueError("r_prev has the wrong length")
         st = _Stats()
-        rc = _load().or_update(self._h, m, alpha, tau, tau_f, tau_p, int(max_iter),
-                               None if prev is None else prev.ctypes.data, out.ctypes.data, ctypes.byref(st))
+        rc = _load().or_update_ex(self._h, m, alpha, tau, tau_f, tau_p, int(max_iter), METRICS[metric],
+                                  ORDERS[order], None if prev is None else prev.ctypes.data, out.ctypes.data,
+                                  ctypes.byref(st))
         if rc:
             raise OracleError(_ERR.get(rc, str(rc)))
         return out, Stats(st.iterations, bool(st.converged), st.delta_R, st.vertices_ever_affected,

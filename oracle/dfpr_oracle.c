@@ -36,7 +36,10 @@
  *   - when a vertex is pruned and also re-marked by an expansion in the same
  *     iteration, the mark wins: F_{i+1} = M_i u (F_i \ P_i);
  *   - Dynamic Traversal marks the union of the vertices reachable from the
- *     updated sources in G_{t-1} and those reachable in G_t (Sec. 3.3.2).
+ *     updated sources in G_{t-1} and those reachable in G_t (Sec. 3.3.2);
+ *   - the other expansion measures of Sec. 4.3 (dr, dr / d) are compared with
+ *     tau_p for pruning too, and the asynchronous order (or_update_ex) visits
+ *     vertices in ascending id with the flags of Alg. 1 taking effect at once.
  *
  * Build: gcc -O2 -std=c11 -shared -fPIC dfpr_oracle.c -o liboracle.so
  * (no -ffast-math: IEEE round-to-nearest FP64 throughout).
@@ -340,15 +343,40 @@ double or_rank_closed_loop(double alpha, int32_t n, double c, double Rv, int64_t
 }
 
 /*
- * One method run (Sec. 3.1, Sec. 3.3, Alg. 1), synchronous order.
+ * The measure a DF / DF-P vertex compares with tau_f (expand) and tau_p
+ * (prune).  Sec. 4.3 tries three: the rank change dr, the change of the
+ * contribution factor dr / d, and the relative change dr / max(r, R[v]); Alg. 1
+ * and every later experiment use the relative change.
+ */
+enum { OR_METRIC_RELATIVE = 0, OR_METRIC_ABSOLUTE = 1, OR_METRIC_CONTRIB = 2 };
+/* Order of the sweeps: synchronous (every vertex of an iteration reads the
+ * ranks of the start of the iteration), or asynchronous as Alg. 1 reads with
+ * one rank vector and one flag vector, visited in ascending vertex id: a rank
+ * written earlier in the iteration is read by later vertices, a vertex marked
+ * affected later in the id order is processed in the same iteration, and a
+ * vertex marked behind the current id waits for the next one (Sec. 4.4 runs
+ * the loop in parallel; ascending id is one of its schedules). */
+enum { OR_ORDER_SYNC = 0, OR_ORDER_ASYNC = 1 };
+
+static double frontier_measure(int metric, double dr, double r, double Rv, int64_t d) {
+  if (metric == OR_METRIC_ABSOLUTE) return dr;
+  if (metric == OR_METRIC_CONTRIB) return dr / (double)d;
+  return dr / fmax(r, Rv);
+}
+
+/*
+ * One method run (Sec. 3.1, Sec. 3.3, Alg. 1).
  * r_prev: ranks of the previous snapshot (ignored by Static, required by the
- * others).  r_out: the updated ranks.  Returns OR_ENORANKS when a dynamic
+ * others).  r_out: the updated ranks.  metric: the DF / DF-P measure above.
+ * order: OR_ORDER_SYNC or OR_ORDER_ASYNC.  Returns OR_ENORANKS when a dynamic
  * method has no r_prev.
  */
-int or_update(const or_graph *g, int method, double alpha, double tau, double tau_f, double tau_p,
-              int32_t max_iter, const double *r_prev, double *r_out, or_stats *st) {
+int or_update_ex(const or_graph *g, int method, double alpha, double tau, double tau_f, double tau_p,
+                 int32_t max_iter, int metric, int order, const double *r_prev, double *r_out, or_stats *st) {
   int32_t n = g->n;
   if (method < OR_STATIC || method > OR_DFP || max_iter < 0 || !(alpha >= 0.0 && alpha < 1.0)) return OR_EINVAL;
+  if (metric < OR_METRIC_RELATIVE || metric > OR_METRIC_CONTRIB || order < OR_ORDER_SYNC || order > OR_ORDER_ASYNC)
+    return OR_EINVAL;
   if (method != OR_STATIC && !r_prev) return OR_ENORANKS;
   double *R = (double *)malloc(sizeof(double) * (size_t)n);
   double *Rn = (double *)malloc(sizeof(double) * (size_t)n);
@@ -367,12 +395,19 @@ int or_update(const or_graph *g, int method, double alpha, double tau, double ta
 
   int frontier = (method == OR_DF || method == OR_DFP);
   int prune = (method == OR_DFP);
+  int async = (order == OR_ORDER_ASYNC);
   or_stats s;
   memset(&s, 0, sizeof(s));
   for (int32_t i = 0; i < max_iter; i++) {
     double dR = 0.0;
-    memcpy(Rn, R, sizeof(double) * (size_t)n);
-    if (frontier) memset(Fn, 0, (size_t)n);
+    /* synchronous: new ranks and flags go to Rn / Fn and are committed after
+     * the sweep; asynchronous: R and F themselves are written */
+    double *Rw = async ? R : Rn;
+    uint8_t *Fw = async ? F : Fn;
+    if (!async) {
+      memcpy(Rn, R, sizeof(double) * (size_t)n);
+      if (frontier) memset(Fn, 0, (size_t)n);
+    }
     for (int32_t v = 0; v < n; v++) {
       if (!F[v]) continue;
       ever[v] = 1;                                          /* processed in some sweep */
@@ -381,18 +416,24 @@ int or_update(const or_graph *g, int method, double alpha, double tau, double ta
       double r = prune ? or_rank_closed_loop(alpha, n, c, R[v], d) : or_rank_plain(alpha, n, c);
       double dr = fabs(r - R[v]);
       if (dr > dR) dR = dr;
-      Rn[v] = r;
       s.vertices_processed++;
       s.edges_processed += g->in_off[v + 1] - g->in_off[v];
       if (frontier) {
-        double rel = dr / fmax(r, R[v]);
-        if (!(prune && rel <= tau_p)) Fn[v] = 1;          /* v stays unless pruned */
-        if (rel > tau_f)                                    /* expand: mark G_t.out(v) */
-          for (int64_t j = g->out_off[v]; j < g->out_off[v + 1]; j++) Fn[g->out_adj[j]] = 1;
+        double mv = frontier_measure(metric, dr, r, R[v], d);
+        if (async) {
+          if (prune && mv <= tau_p) Fw[v] = 0;              /* mark v as not affected */
+        } else if (!(prune && mv <= tau_p)) {
+          Fw[v] = 1;                                        /* v stays unless pruned */
+        }
+        if (mv > tau_f)                                     /* expand: mark G_t.out(v) */
+          for (int64_t j = g->out_off[v]; j < g->out_off[v + 1]; j++) Fw[g->out_adj[j]] = 1;
       }
+      Rw[v] = r;
     }
-    memcpy(R, Rn, sizeof(double) * (size_t)n);
-    if (frontier) memcpy(F, Fn, (size_t)n);
+    if (!async) {
+      memcpy(R, Rn, sizeof(double) * (size_t)n);
+      if (frontier) memcpy(F, Fn, (size_t)n);
+    }
     s.iterations = i + 1;
     s.delta_R = dR;
     if (dR <= tau) { s.converged = 1; break; }
@@ -402,4 +443,11 @@ int or_update(const or_graph *g, int method, double alpha, double tau, double ta
   if (st) *st = s;
   free(R); free(Rn); free(F); free(Fn); free(ever);
   return OR_OK;
+}
+
+/* The synchronous run with the relative measure of Alg. 1. */
+int or_update(const or_graph *g, int method, double alpha, double tau, double tau_f, double tau_p,
+              int32_t max_iter, const double *r_prev, double *r_out, or_stats *st) {
+  return or_update_ex(g, method, alpha, tau, tau_f, tau_p, max_iter, OR_METRIC_RELATIVE, OR_ORDER_SYNC, r_prev,
+                      r_out, st);
 }

@@ -341,3 +341,138 @@ def test_error_ordering_soft_claim():
     assert err["df"] < err["static"]
     assert err["nd"] <= err["df"] * 1.0001
     assert err["dfp"] < 10 * 1e-6 / (1 - ALPHA)
+
+
+# ---------------------------------------------------------------- Sec. 4.3 measures, asynchronous order
+
+
+@pytest.mark.parametrize("metric", ["relative", "absolute", "contrib"])
+@pytest.mark.parametrize("order", ["sync", "async"])
+@pytest.mark.parametrize("method", ["df", "dfp"])
+def test_every_measure_and_order_reaches_fixed_point_at_zero_tolerance(metric, order, method):
+    """With tau_f = tau_p = 0 every measure expands on any change and prunes
+    nothing that changes, in either order, so DF and DF-P reach the fixed
+    point of G_t (the linear solve)."""
+    n = 150
+    src, dst = random_graph(n, 700, 31)
+    g = oracle.Graph(n, src, dst)
+    E0 = edge_set(n, src, dst)
+    r0 = pagerank_solve(n, E0)
+    (ds, dd), (is_, id_) = random_batch(n, E0, 10, 40, 32)
+    g.apply_batch(ds, dd, is_, id_)
+    E1 = (E0 - {(int(a), int(b)) for a, b in zip(ds, dd) if a != b}) | {(int(a), int(b)) for a, b in zip(is_, id_)}
+    r, st = g.update(method, tau=1e-15, tau_f=0.0, tau_p=0.0, max_iter=5000, r_prev=r0, metric=metric, order=order)
+    assert st.converged
+    assert np.max(np.abs(r - pagerank_solve(n, E1))) < 1e-12
+
+
+@pytest.mark.parametrize("method", ["static", "nd"])
+def test_async_sweeps_reach_fixed_point(method):
+    """Gauss-Seidel sweeps (one rank vector, ascending id) converge to the
+    same linear-system solution as the synchronous ones.  (Not necessarily in
+    fewer sweeps: on a well-mixing random graph the power iteration's error
+    shrinks by about alpha |lambda_2| per sweep, with nothing along the Perron
+    vector, and beats Gauss-Seidel; the DAG test below shows the opposite.)"""
+    n = 120
+    src, dst = random_graph(n, 900, 41)
+    g = oracle.Graph(n, src, dst)
+    ref = pagerank_solve(n, edge_set(n, src, dst))
+    start = np.full(n, 1.0 / n) if method == "nd" else None
+    ra, sa = g.update(method, tau=1e-15, max_iter=5000, r_prev=start, order="async")
+    assert sa.converged and np.max(np.abs(ra - ref)) < 1e-12
+
+
+def test_async_closed_loop_solves_a_dag_in_one_sweep():
+    """On a graph whose edges all go from a lower to a higher id (plus the
+    self-loops), Eq. 2 visited in ascending id reads only final in-neighbour
+    ranks and removes the self term exactly: one asynchronous DF-P sweep over
+    every vertex gives the fixed point, and the second one only confirms it.
+    The synchronous order needs one sweep per level of the DAG at least."""
+    n = 60
+    rng = np.random.default_rng(51)
+    u = rng.integers(0, n - 1, 200)
+    v = u + 1 + (rng.integers(0, n, 200) % (n - 1 - u))
+    g = oracle.Graph(n, u, v)
+    E0 = edge_set(n, u, v)
+    r0 = pagerank_solve(n, E0)
+    # insert (k, k+1) for every k: every vertex becomes a source, so all are marked
+    ins = [(k, k + 1) for k in range(n - 1) if (k, k + 1) not in E0]
+    ins += [(0, 1)] if not ins else []
+    g.apply_batch([], [], [a for a, _ in ins], [b for _, b in ins])
+    E1 = E0 | set(ins)
+    ref = pagerank_solve(n, E1)
+    assert g.initial_affected().all()
+    r1, s1 = g.update("dfp", tau=1e-14, tau_f=0.0, tau_p=0.0, max_iter=1, r_prev=r0, order="async")
+    assert np.max(np.abs(r1 - ref)) < 1e-14
+    r2, s2 = g.update("dfp", tau=1e-14, tau_f=0.0, tau_p=0.0, max_iter=50, r_prev=r0, order="async")
+    assert s2.converged and s2.iterations == 2
+    _, s3 = g.update("dfp", tau=1e-14, tau_f=0.0, tau_p=0.0, max_iter=500, r_prev=r0, order="sync")
+    assert s3.iterations > 2
+
+
+def test_contribution_measure_on_constant_out_degree():
+    """dr / d > tau_f with every out-degree equal to d is dr > d * tau_f: on
+    such a graph DF with the contribution measure at tau_f takes the same steps
+    as DF with the rank-change measure at d * tau_f (tau_f a power of two,
+    so both thresholds are exact)."""
+    n, k = 300, 6   # out-degree k with the self-loop
+    rng = np.random.default_rng(61)
+    src, dst = [], []
+    for a in range(n):
+        others = rng.choice(np.delete(np.arange(n), a), k - 1, replace=False)
+        src += [a] * (k - 1)
+        dst += list(others)
+    g = oracle.Graph(n, src, dst)
+    off, _ = g.out_csr()
+    assert np.all(np.diff(off) == k)
+    r0, _ = g.update("static", tau=1e-14)
+    # a batch that keeps every out-degree at k: move one edge of each of a few sources
+    E = edge_set(n, src, dst)
+    dels, ins = [], []
+    for a in rng.choice(n, 8, replace=False):
+        old = next(w for (x, w) in sorted(E) if x == a and w != a)
+        new = next(w for w in rng.permutation(n) if w != a and (int(a), int(w)) not in E)
+        dels.append((int(a), int(old)))
+        ins.append((int(a), int(new)))
+    g.apply_batch([a for a, _ in dels], [b for _, b in dels], [a for a, _ in ins], [b for _, b in ins])
+    assert np.all(np.diff(g.out_csr()[0]) == k)
+    t = 2.0 ** -30   # d * t ~ 5.6e-9: inside the range the rank changes pass through before tau = 1e-10
+    for method in ("df", "dfp"):
+        rc, sc = g.update(method, tau_f=t, tau_p=t, r_prev=r0, metric="contrib")
+        ra, sa = g.update(method, tau_f=t * k, tau_p=t * k, r_prev=r0, metric="absolute")
+        assert np.array_equal(rc, ra)
+        assert (sc.iterations, sc.vertices_processed) == (sa.iterations, sa.vertices_processed)
+        rr, sr = g.update(method, tau_f=t, tau_p=t, r_prev=r0, metric="absolute")
+        assert sr.vertices_processed >= sc.vertices_processed   # a lower threshold processes at least as much here
+
+
+@pytest.mark.parametrize("metric", ["relative", "absolute", "contrib"])
+@pytest.mark.parametrize("order", ["sync", "async"])
+def test_prune_everything_expand_nothing(metric, order):
+    """Every measure is at most 1 here (dr <= max(r, R[v]) for non-negative
+    ranks, and dr <= 1, dr / d <= 1 for ranks below 1), so DF-P with
+    tau_f = tau_p = 1 expands nothing and prunes every vertex at its first
+    visit: each initially affected vertex is processed exactly once, with one
+    step of Eq. 2 from R_{t-1}, and the second iteration finds an empty
+    frontier."""
+    n = 200
+    src, dst = random_graph(n, 1200, 71)
+    g = oracle.Graph(n, src, dst)
+    r0, _ = g.update("static", tau=1e-14)
+    E0 = edge_set(n, src, dst)
+    (ds, dd), (is_, id_) = random_batch(n, E0, 3, 6, 72, with_noise=False)
+    g.apply_batch(ds, dd, is_, id_)
+    F0 = g.initial_affected()
+    r, st = g.update("dfp", tau_f=1.0, tau_p=1.0, r_prev=r0, metric=metric, order=order)
+    assert st.vertices_processed == F0.sum() == st.vertices_ever_affected
+    assert st.iterations == 2 and st.converged
+    assert np.array_equal(r[~F0], r0[~F0])
+    # the processed vertices moved by one Eq. 2 step from R_{t-1} (in the
+    # synchronous order every in-neighbour still has its R_{t-1} rank)
+    if order == "sync":
+        off, adj = g.in_csr()
+        oo, _ = g.out_csr()
+        d = np.diff(oo)
+        for v in np.flatnonzero(F0)[:20]:
+            c = sum(r0[u] / d[u] for u in adj[off[v]:off[v + 1]])
+            assert r[v] == oracle.rank_closed_loop(ALPHA, n, c, r0[v], int(d[v]))
