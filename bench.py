@@ -55,7 +55,8 @@ def parse():
     ap.add_argument("--seed", type=int, default=2000)
     ap.add_argument("--e2e-steps", type=int, default=5)
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--workload", default="large", choices=["large", "batched", "serving", "methods", "temporal"],
+    ap.add_argument("--workload", default="large",
+                    choices=["large", "batched", "serving", "methods", "temporal", "tolerances"],
                     help="large: one R-MAT scale-25 graph (default); batched: a group of R-MAT graphs updated "
                          "together; serving: Poisson request arrivals for resident graphs")
     ap.add_argument("--rates", default="50,200,500,1000,2000", help="serving: arrival rates (requests/s)")
@@ -64,6 +65,7 @@ def parse():
                     help="methods: batch sizes as fractions of |E|")
     ap.add_argument("--reps", type=int, default=1, help="methods: batches per size")
     ap.add_argument("--temporal-batches", type=int, default=100, help="temporal: consecutive batches per size")
+    ap.add_argument("--tolerance-batches", type=int, default=10, help="tolerances: consecutive batches")
     ap.add_argument("--graphs", type=int, default=64, help="batched: graphs in the group")
     ap.add_argument("--tune", default="auto",
                     help="large: setting of the every-vertex sweeps: auto (pr_autotune on the first warm-up "
@@ -757,6 +759,82 @@ def run_temporal(a, rank, world, local_rank):
     print(json.dumps(line), flush=True)
 
 
+def run_tolerances(a, rank, world, local_rank):
+    """The experiments of Sec. 4.3 and Sec. 4.4 (figures adjust-frontier and
+    adjust-prune) on the temporal stream: consecutive insertion-only batches of
+    1e-5 |E_T| after a base of the first 90%.  For every batch, every setting
+    runs from the same previous ranks (a Static solve of G_{t-1} to its exact
+    fixed point) and is timed against Static at tau = 1e-10; the error is the
+    L1 distance to the exact fixed point of G_t.
+      frontier: DF with each measure -- relative change at tau_f = 0.1 ...
+        1e-6, rank change and contribution-factor change at tau_f = tau ...
+        tau / 1e5;
+      prune: DF-P with the relative change, tau_f in {1e-6, 1e-7, 1e-8},
+        tau_p = tau_f ... tau_f / 1e4."""
+    import numpy as np
+    import torch
+
+    import paper_2401_15870_gb300 as pr
+    import synth
+
+    torch.cuda.set_device(local_rank)
+    n, m_t = 2_600_000, 63_000_000
+    src, dst = synth.temporal(n, m_t, a.seed + 77)
+    base = int(0.9 * m_t)
+    size = int(round(1e-5 * m_t))
+    settings = [("df", "relative", 10.0 ** -k, 10.0 ** -k) for k in range(1, 7)]
+    settings += [("df", ms, TAU / 10.0 ** k, TAU / 10.0 ** k) for ms in ("absolute", "contrib") for k in range(0, 6)]
+    settings += [("dfp", "relative", tf, tf / 10.0 ** k) for tf in (1e-6, 1e-7, 1e-8) for k in range(0, 5)]
+    G = pr.Graph.from_edges(n, src[:base], dst[:base])
+    G.update("static", alpha=ALPHA, tau=0.0, max_iter=500)
+    r_prev = G.ranks()
+    acc = {i: {"ms": [], "l1": [], "share": [], "iters": []} for i in range(len(settings))}
+    static = {"ms": [], "l1": [], "iters": []}
+    pos = base
+    for k in range(a.tolerance_batches):
+        G.apply_batch(ins_src=src[pos:pos + size], ins_dst=dst[pos:pos + size])
+        pos += size
+        G.update("static", alpha=ALPHA, tau=0.0, max_iter=500)
+        r_ref = G.ranks()
+        s0 = G.update("static", alpha=ALPHA, tau=TAU)
+        static["ms"].append(s0.ms_update)
+        static["iters"].append(s0.iterations)
+        static["l1"].append(float(np.abs(G.ranks() - r_ref).sum()))
+        for i, (method, measure, tf, tp) in enumerate(settings):
+            G.set_ranks(r_prev)
+            st = G.update(method, alpha=ALPHA, tau=TAU, tau_f=tf, tau_p=tp, measure=measure)
+            acc[i]["ms"].append(st.ms_update)
+            acc[i]["iters"].append(st.iterations)
+            acc[i]["share"].append(st.vertices_ever_affected / n)
+            acc[i]["l1"].append(float(np.abs(G.ranks() - r_ref).sum()))
+        G.set_ranks(r_ref)
+        r_prev = r_ref
+    if rank != 0:
+        return
+    rows = []
+    for i, (method, measure, tf, tp) in enumerate(settings):
+        speed = [s / m for s, m in zip(static["ms"], acc[i]["ms"])]
+        rows.append({"method": method, "measure": measure, "tau_f": tf, "tau_p": tp,
+                     "speedup_vs_static_mean": statistics.mean(speed),
+                     "ms_mean": statistics.mean(acc[i]["ms"]), "iterations_mean": statistics.mean(acc[i]["iters"]),
+                     "affected_share_mean": statistics.mean(acc[i]["share"]),
+                     "l1_error_mean": statistics.mean(acc[i]["l1"])})
+    best = min((r for r in rows if r["l1_error_mean"] <= statistics.mean(static["l1"])),
+               key=lambda r: r["ms_mean"], default=None)
+    line = {"metric": METRIC, "value": best["speedup_vs_static_mean"] if best else None,
+            "unit": "mean speedup over Static of the fastest setting whose error stays at or below Static's",
+            "n_gpus": world, "higher_is_better": True, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": "temporal stream (copying / preferential attachment with repeats), %d vertices, "
+                       "%d timestamped edges, base = first 90%%, %d consecutive insertion-only batches of "
+                       "1e-5 |E_T| (%d edges); every setting from the exact fixed point of G_{t-1}"
+                       % (n, m_t, a.tolerance_batches, size)},
+            "best": best,
+            "static": {"ms_mean": statistics.mean(static["ms"]), "iterations_mean": statistics.mean(static["iters"]),
+                       "l1_error_mean": statistics.mean(static["l1"])},
+            "settings": rows}
+    print(json.dumps(line), flush=True)
+
+
 def main():
     a = parse()
     rank = int(os.environ.get("RANK", "0"))
@@ -778,6 +856,8 @@ def main():
             run_methods(a, rank, world, local_rank)
         elif a.workload == "temporal":
             run_temporal(a, rank, world, local_rank)
+        elif a.workload == "tolerances":
+            run_tolerances(a, rank, world, local_rank)
         else:
             run_gpu(a, rank, world, local_rank)
     finally:

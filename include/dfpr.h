@@ -86,6 +86,17 @@ typedef struct {
  * above).  The result is the same either way. */
 #define PR_OPT_DEVICE_LOOP 8
 #define PR_OPT_HOST_LOOP 16
+/* pr_options.flags for DF / DF-P: the measure a processed vertex compares
+ * with tau_f (expand its out-neighbours when above) and tau_p (DF-P: prune it
+ * when at or below).  Sec. 4.3 tries three: the relative rank change
+ * dr / max(r, R[v]) (the default; Alg. 1 and every later experiment), the rank
+ * change dr (PR_OPT_MEASURE_ABSOLUTE) and the change of the contribution
+ * factor dr / |out(v)| (PR_OPT_MEASURE_CONTRIB).  At most one of the two may
+ * be set; they work with either iteration loop and with groups.  The
+ * comparisons are made without a division: dr > tau * max(r, R[v]), dr > tau,
+ * dr > tau * |out(v)|. */
+#define PR_OPT_MEASURE_ABSOLUTE 32
+#define PR_OPT_MEASURE_CONTRIB 64
 #define PR_DEVICE_LOOP_SLOTS (1ll << 24)
 
 /* Outcome of one pr_update (Sec. 5.1.5 measures time and affected vertices). */
@@ -262,11 +273,12 @@ pr_status pr_sweep_noalloc(int32_t n, const int64_t* in_off, const int32_t* in_s
  *   of its graphs.  stream: the CUDA stream of the group's work (NULL: the
  *   legacy default stream).  Errors: PR_EINVAL, PR_ENOMEM, PR_ECUDA.
  * pr_group_update: method PR_STATIC, PR_NAIVE_DYNAMIC, PR_DF or PR_DFP (Dynamic
- *   Traversal is not offered), alpha / tau / opts as in pr_update; the only
- *   flag accepted is PR_OPT_HOST_LOOP (or PR_OPT_DEVICE_LOOP, the default):
- *   the same kernels launched one by one with the loop condition read back
- *   after every iteration, for profilers that cannot look into a CUDA graph
- *   with conditional nodes and for drivers without them.  The update runs after the work already queued on
+ *   Traversal is not offered), alpha / tau / opts as in pr_update; the flags
+ *   accepted are PR_OPT_MEASURE_* and PR_OPT_HOST_LOOP (or
+ *   PR_OPT_DEVICE_LOOP, the default): the same kernels launched one by one
+ *   with the loop condition read back after every iteration, for profilers
+ *   that cannot look into a CUDA graph with conditional nodes and for drivers
+ *   without them.  The update runs after the work already queued on
  *   every graph's stream and is complete on return.  stats: NULL or count
  *   entries, one per graph in creation order; ms_update is the time of the
  *   whole group, ms_sweep is 0.  Errors: PR_EINVAL, PR_ENORANKS (a dynamic

@@ -244,14 +244,20 @@ PR_OPT_DEVICE_LOOP, PR_OPT_HOST_LOOP = 8, 16
 PR_DEVICE_LOOP_SLOTS = 1 << 24
 
 
+MEASURES = {None: 0, "relative": 0, "absolute": 32, "contrib": 64}   # PR_OPT_MEASURE_* (Sec. 4.3)
+
+
 def pr_update(h, method, alpha=0.85, tau=1e-10, tau_f=1e-6, tau_p=1e-6, max_iter=500, time_sweeps=False,
-              direction=None, loop=None) -> Stats:
+              direction=None, loop=None, measure=None) -> Stats:
     """direction: None (chosen per iteration), "pull" or "push" (DF / DF-P, host loop).
-    loop: None (by graph size), "device" or "host"."""
+    loop: None (by graph size), "device" or "host".  measure: the DF / DF-P
+    measure compared with tau_f / tau_p: "relative" (default), "absolute" or
+    "contrib"."""
     m = METHODS[method] if isinstance(method, str) else int(method)
     flags = (PR_OPT_TIME_SWEEPS if time_sweeps else 0) | {None: 0, "pull": PR_OPT_FORCE_PULL,
                                                           "push": PR_OPT_FORCE_PUSH}[direction]
     flags |= {None: 0, "device": PR_OPT_DEVICE_LOOP, "host": PR_OPT_HOST_LOOP}[loop]
+    flags |= MEASURES[measure]
     opts = pr_options(tau_f, tau_p, int(max_iter), flags)
     st = pr_stats()
     _check(load().pr_update(h, m, float(alpha), float(tau), ctypes.byref(opts), ctypes.byref(st)), h)
@@ -374,11 +380,14 @@ def pr_group_create(handles, stream=None):
     return out
 
 
-def pr_group_update(q, method, alpha=0.85, tau=1e-10, tau_f=1e-6, tau_p=1e-6, max_iter=500, loop=None):
+def pr_group_update(q, method, alpha=0.85, tau=1e-10, tau_f=1e-6, tau_p=1e-6, max_iter=500, loop=None,
+                    measure=None):
     """One update of every graph of the group; returns one Stats per graph.
-    loop: None / "device" (CUDA graph) or "host" (kernels launched one by one)."""
+    loop: None / "device" (CUDA graph) or "host" (kernels launched one by one).
+    measure: as in pr_update."""
     m = METHODS[method] if isinstance(method, str) else int(method)
-    opts = pr_options(tau_f, tau_p, int(max_iter), {None: 0, "device": 0, "host": PR_OPT_HOST_LOOP}[loop])
+    opts = pr_options(tau_f, tau_p, int(max_iter),
+                      {None: 0, "device": 0, "host": PR_OPT_HOST_LOOP}[loop] | MEASURES[measure])
     n = _group_sizes[q.value]
     st = (pr_stats * n)()
     _check(load().pr_group_update(q, m, float(alpha), float(tau), ctypes.byref(opts), st))

@@ -392,6 +392,9 @@ pr_status dfpr::run_update(pr_graph* h, int method, double alpha, double tau, do
     g->tab_alpha = alpha;
   }
   SweepParams p = base_params(g, alpha, tau_f, tau_p);
+  p.metric = (flags & PR_OPT_MEASURE_ABSOLUTE) ? METRIC_ABSOLUTE
+             : (flags & PR_OPT_MEASURE_CONTRIB) ? METRIC_CONTRIB
+                                                : METRIC_RELATIVE;
   int64_t ever = 0;
   int32_t iters = 0;
   double dR = 0.0;
@@ -781,8 +784,10 @@ pr_status pr_update(pr_graph* h, pr_method method, double alpha, double tau, con
     tau_p = opts->tau_p;
     max_iter = opts->max_iter;
     flags = opts->flags;
-    if (flags & ~(PR_OPT_TIME_SWEEPS | PR_OPT_FORCE_PULL | PR_OPT_FORCE_PUSH | PR_OPT_DEVICE_LOOP | PR_OPT_HOST_LOOP))
+    if (flags & ~(PR_OPT_TIME_SWEEPS | PR_OPT_FORCE_PULL | PR_OPT_FORCE_PUSH | PR_OPT_DEVICE_LOOP | PR_OPT_HOST_LOOP |
+                  PR_OPT_MEASURE_ABSOLUTE | PR_OPT_MEASURE_CONTRIB))
       return PR_EINVAL;
+    if ((flags & PR_OPT_MEASURE_ABSOLUTE) && (flags & PR_OPT_MEASURE_CONTRIB)) return PR_EINVAL;
     if ((flags & PR_OPT_FORCE_PULL) && (flags & PR_OPT_FORCE_PUSH)) return PR_EINVAL;
     if ((flags & PR_OPT_DEVICE_LOOP) &&
         (flags & (PR_OPT_HOST_LOOP | PR_OPT_TIME_SWEEPS | PR_OPT_FORCE_PULL | PR_OPT_FORCE_PUSH)))
@@ -802,7 +807,7 @@ pr_status pr_update(pr_graph* h, pr_method method, double alpha, double tau, con
       pr_status st = pr_group_create(1, one, g->stream, &h->solo);
       if (st != PR_OK) return st;
     }
-    pr_options o = {tau_f, tau_p, max_iter, 0};
+    pr_options o = {tau_f, tau_p, max_iter, flags & (PR_OPT_MEASURE_ABSOLUTE | PR_OPT_MEASURE_CONTRIB)};
     return pr_group_update(h->solo, method, alpha, tau, &o, stats);
   }
   return run_update(h, (int)method, alpha, tau, tau_f, tau_p, max_iter, flags, stats);

@@ -74,6 +74,7 @@ struct GState {
 struct GRun {
   double alpha, tau, tau_f, tau_p;
   int32_t max_iter, method, G, loops;
+  int32_t metric, pad;
   int32_t live, use_graph;   // loop condition, written to `live` instead of the WHILE node when use_graph is 0
   const int64_t* wpre;   // gather units
   const int64_t* fpre;   // epilogue units (FIN_U chunks)
@@ -206,6 +207,7 @@ struct GView {
   const double* tab_sc;
   const double* tab_cl;
   double alpha, C0, tau_f, tau_p;
+  int32_t metric;
 };
 
 __device__ __forceinline__ void flush_totals(PullTotals& t, GState* s) {
@@ -266,6 +268,7 @@ __global__ void __launch_bounds__(GR_THREADS, 2) k_g_finish(const GRun* __restri
     p.C0 = d.C0;
     p.tau_f = run->tau_f;
     p.tau_p = run->tau_p;
+    p.metric = run->metric;
     const int64_t nchunks = cdiv(d.n, 32);
     const int64_t ch0 = (u - pre[g]) * FU;
     finish_pull_step<CLOSED, GView, false, FU>(p, d.acc, d.anyb, ch0, nchunks, t);
@@ -537,8 +540,10 @@ pr_status group_launch(pr_group* q, pr_method method, double alpha, double tau, 
   pr_options o = {1e-6, 1e-6, 500, 0};
   if (opts) o = *opts;
   if (!(o.tau_f >= 0.0) || !(o.tau_p >= 0.0) || o.max_iter < 0) return PR_EINVAL;
-  if (o.flags & ~(PR_OPT_HOST_LOOP | PR_OPT_DEVICE_LOOP)) return PR_EINVAL;
+  if (o.flags & ~(PR_OPT_HOST_LOOP | PR_OPT_DEVICE_LOOP | PR_OPT_MEASURE_ABSOLUTE | PR_OPT_MEASURE_CONTRIB))
+    return PR_EINVAL;
   if ((o.flags & PR_OPT_HOST_LOOP) && (o.flags & PR_OPT_DEVICE_LOOP)) return PR_EINVAL;
+  if ((o.flags & PR_OPT_MEASURE_ABSOLUTE) && (o.flags & PR_OPT_MEASURE_CONTRIB)) return PR_EINVAL;
   std::vector<int32_t>& mem = q->members;
   mem.clear();
   if (members) {
@@ -611,6 +616,9 @@ pr_status group_launch(pr_group* q, pr_method method, double alpha, double tau, 
   r.tab_sc = q->tab_sc;
   r.tab_cl = q->tab_cl;
   r.use_graph = (o.flags & PR_OPT_HOST_LOOP) ? 0 : 1;
+  r.metric = (o.flags & PR_OPT_MEASURE_ABSOLUTE) ? METRIC_ABSOLUTE
+             : (o.flags & PR_OPT_MEASURE_CONTRIB) ? METRIC_CONTRIB
+                                                  : METRIC_RELATIVE;
 
   // order after the work already queued on the members' streams
   for (int i = 0; i < G; i++) {

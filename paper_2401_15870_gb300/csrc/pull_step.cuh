@@ -159,7 +159,8 @@ struct PullTotals {
 };
 
 // chunks [ch0, ch0 + U) of one graph.  P provides n, odeg, ideg, R, Ccur,
-// Cnext, S_cur, S_next, X_next, ever, tab_sc, tab_cl, alpha, C0, tau_f, tau_p.
+// Cnext, S_cur, S_next, X_next, ever, tab_sc, tab_cl, alpha, C0, tau_f, tau_p,
+// metric.
 // The accumulators and the expanded-source words it reads are left zero for
 // the next sweep.  L2: read them from L2 (they were written by other SMs in
 // the same launch).
@@ -210,8 +211,9 @@ __device__ __forceinline__ void finish_pull_step(const P& p, long long* __restri
       const double sc = d[u] < TAB ? p.tab_sc[d[u]] : FIX_ONE / (double)d[u];
       p.Cnext[v] = __double2ll_rn(r * sc);
       // Alg. 1: prune when dr / max(r, R[v]) <= tau_p (DF-P), expand when it
-      // is > tau_f; compared without the division
-      const double mr = dbits(r) > dbits(Rv[u]) ? r : Rv[u];
+      // is > tau_f (or the other measures of Sec. 4.3); compared without the
+      // division
+      const double mr = measure_base(p.metric, dbits(r) > dbits(Rv[u]) ? r : Rv[u], d[u]);
       const unsigned long long tf = dbits(p.tau_f * mr);
       const unsigned long long tp = same_tau ? tf : dbits(p.tau_p * mr);
       stay = !CLOSED || drb > tp;

@@ -211,8 +211,9 @@ __device__ __forceinline__ void finalize(const SweepParams& p, int32_t k, int32_
     p.Cnext[v] = cn;
     if (pull) {
       // Alg. 1: prune when dr / max(r, R[v]) <= tau_p (DF-P), expand when it
-      // is > tau_f; both compared without the division, in FP64
-      double mr = fmax(r, Rv);
+      // is > tau_f (or the other measures of Sec. 4.3); both compared
+      // without the division, in FP64
+      double mr = measure_base(p.metric, fmax(r, Rv), d);
       bool stay = member && (MODE == SWEEP_PULL_DF || !(dr <= p.tau_p * mr));
       bool expand = member && dr > p.tau_f * mr;
       agg_set_bit(p.S_next, v, stay);
@@ -225,7 +226,7 @@ __device__ __forceinline__ void finalize(const SweepParams& p, int32_t k, int32_
   }
   p.rnew[k] = r;
   if (MODE == SWEEP_DF || MODE == SWEEP_DFP) {
-    double mr = fmax(r, Rv);
+    double mr = measure_base(p.metric, fmax(r, Rv), d);
     bool stay = (MODE == SWEEP_DF) || !(dr <= p.tau_p * mr);
     bool expand = dr > p.tau_f * mr;
     agg_set_bit(p.ever, v, true);

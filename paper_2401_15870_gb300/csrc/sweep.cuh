@@ -18,6 +18,14 @@ enum SweepMode : int {
   SWEEP_PULL_DFP = 5, // the same for DF-P
 };
 
+// The measure of Sec. 4.3 that a DF / DF-P vertex compares with tau_f and
+// tau_p, as the factor of the tolerance: dr > tau * measure_base (relative
+// change: max(r, R[v]); rank change: 1; contribution factor dr / d: d).
+enum Metric : int { METRIC_RELATIVE = 0, METRIC_ABSOLUTE = 1, METRIC_CONTRIB = 2 };
+__device__ __forceinline__ double measure_base(int metric, double mr, int32_t d) {
+  return metric == METRIC_RELATIVE ? mr : (metric == METRIC_ABSOLUTE ? 1.0 : (double)d);
+}
+
 struct SweepParams {
   int32_t n;
   const int64_t* ioff;
@@ -35,6 +43,7 @@ struct SweepParams {
   // policy and the rest with evict-first, so the most-read contributions
   // (internal ids are ordered by decreasing out-degree) stay in L2
   int32_t hot;
+  int32_t metric;            // Metric (DF / DF-P)
   // the swept list: identity (list == nullptr) over in-CSR capacity quads, or
   // list[0..*count) with quad prefix qs
   const int32_t* list;

@@ -447,3 +447,50 @@ def test_invalid_gather_settings_are_rejected(lib):
         with pytest.raises(lib.PRError):
             G.set_tuning(t, q, hub, f)
     assert G.tuning() == before
+
+
+# ------------------------------------------------------------- frontier measures of Sec. 4.3
+
+
+@pytest.mark.parametrize("measure,tol_f", [("absolute", 1e-12), ("contrib", 1e-13), ("relative", 1e-5)])
+@pytest.mark.parametrize("method", ["df", "dfp"])
+@pytest.mark.parametrize("scale,bsize", [(12, 40), (14, 262)])
+def test_frontier_measures_match_oracle_in_every_form(lib, measure, tol_f, method, scale, bsize):
+    """DF / DF-P with each measure of Sec. 4.3 (rank change, change of the
+    contribution factor, relative change) against the oracle with the same
+    measure, within 1e-9; pull, push, the automatic choice, the device loop
+    and a group give bit-identical ranks and statistics."""
+    G, O, r0 = rank_case(lib, scale, 16, bsize, 110 + scale)
+    ref, ost = O.update(method, tau_f=tol_f, tau_p=tol_f, r_prev=r0, metric=measure)
+    out = []
+    for direction, loop in (("pull", "host"), ("push", "host"), (None, "host"), (None, "device")):
+        G.set_ranks(r0)
+        st = G.update(method, tau_f=tol_f, tau_p=tol_f, direction=direction, loop=loop, measure=measure)
+        out.append((G.ranks(), st.iterations, st.vertices_ever_affected, st.vertices_processed))
+    G.set_ranks(r0)
+    grp = lib.Group([G])
+    try:
+        st = grp.update(method, tau_f=tol_f, tau_p=tol_f, measure=measure)[0]
+        out.append((G.ranks(), st.iterations, st.vertices_ever_affected, st.vertices_processed))
+    finally:
+        grp.close()
+    for r, *rest in out[1:]:
+        assert np.array_equal(r, out[0][0])
+        assert rest == list(out[0][1:])
+    assert np.max(np.abs(out[0][0] - ref)) < TOL
+    assert abs(out[0][1] - ost.iterations) <= 1
+    assert out[0][2] == pytest.approx(ost.vertices_ever_affected, rel=0.01)
+
+
+def test_measure_flags_are_exclusive(lib):
+    G, _, r0 = rank_case(lib, 10, 8, 20, 5)
+    G.set_ranks(r0)
+    import ctypes
+    opts = lib.pr_options(1e-6, 1e-6, 500, 32 | 64)
+    assert lib.load().pr_update(G.handle, 4, 0.85, 1e-10, ctypes.byref(opts), None) == 1
+    # the measures change the frontier, not Eq. 1 / Eq. 2: ND ignores them
+    a = G.update("nd", measure="absolute")
+    ra = G.ranks()
+    G.set_ranks(r0)
+    b = G.update("nd")
+    assert np.array_equal(ra, G.ranks()) and a.iterations == b.iterations
