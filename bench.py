@@ -164,6 +164,28 @@ def cpu_baseline_entry(times, m_sample, sc, full_scale):
                        "2^%d to the full workload" % (sc, m_sample, len(times), per, sc - full_scale))}
 
 
+def replica_seed(seed, rank):
+    """Seed of rank `rank`'s replica: every rank draws its own graph and batches."""
+    return seed + 7919 * rank
+
+
+def max_over_ranks(x, world, device):
+    """The largest of every rank's x (a time): the job is as slow as its
+    slowest replica.  With one rank, x itself."""
+    if world <= 1:
+        return float(x)
+    import torch
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_rate(world, units_per_rank, ms):
+    """Whole-job throughput: the units all ranks processed over the slowest
+    rank's time."""
+    return world * units_per_rank / (ms / 1000.0)
+
+
 def run_reference(a, rank, world):
     if rank != 0:
         return
@@ -193,7 +215,7 @@ def run_gpu(a, rank, world, local_rank):
     dev = torch.device("cuda", local_rank)
     stream = torch.cuda.current_stream()
     n = 1 << a.scale
-    seed = a.seed + 7919 * rank          # independent replica per rank
+    seed = replica_seed(a.seed, rank)    # independent replica per rank
     src, dst = sg.rmat(a.scale, a.edge_factor << a.scale, seed)
     G = pr.Graph.from_edges(n, src, dst, device=True, stream=stream)
     m0 = G.m
@@ -240,12 +262,8 @@ def run_gpu(a, rank, world, local_rank):
     torch.cuda.synchronize()
     launches = pr.pr_kernel_launches() - l0
     clk = clocks.stop()
-    ms = ev0.elapsed_time(ev1)
-    if world > 1:
-        t = torch.tensor([ms], device=dev)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        ms = float(t.item())
-    value = world * a.steps / (ms / 1000.0)
+    ms = max_over_ranks(ev0.elapsed_time(ev1), world, dev)
+    value = job_rate(world, a.steps, ms)
 
     sweep_ms = sum(s.ms_sweep for s in stats)
     sweep_bytes = sum(SWEEP_BYTES_PER_EDGE * s.edges_processed + SWEEP_BYTES_PER_VERTEX * s.vertices_processed
@@ -277,10 +295,7 @@ def run_gpu(a, rank, world, local_rank):
         e2e_ms = (time.perf_counter() - t0) * 1000.0
         h2d = sum(t.numel() * 4 for t in host_batches[0])
         d2h = n * 8
-        if world > 1:
-            t = torch.tensor([e2e_ms], device=dev)
-            torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-            e2e_ms = float(t.item())
+        e2e_ms = max_over_ranks(e2e_ms, world, dev)
     # one every-vertex sweep with the tuned setting (after everything timed)
     st_nd = G.update("nd", alpha=ALPHA, tau=TAU, max_iter=2, time_sweeps=True, loop="host")
     if rank != 0:
@@ -300,7 +315,7 @@ def run_gpu(a, rank, world, local_rank):
                      if (a.scale, a.edge_factor, a.batch_frac) == (25, 32, 1e-4) else None,
                      "peak_source": peak_src + " (MEASURED_PEAKS.json hbm_gbs)" if peak_src == "measured" else
                      "fallback 6800 GB/s"},
-        "e2e": {"value": (a.e2e_steps / (e2e_ms / 1000.0) * world) if e2e_ms else None, "unit": "updates/s",
+        "e2e": {"value": job_rate(world, a.e2e_steps, e2e_ms) if e2e_ms else None, "unit": "updates/s",
                 "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
         "gpu_launches": launches,
         "clocks": clk,
@@ -358,7 +373,7 @@ def run_batched(a, rank, world, local_rank):
     nb = a.warmup + a.steps
     for scale, ef, seed in specs:
         n = 1 << scale
-        src, dst = sg.rmat(scale, ef << scale, seed + 7919 * rank)
+        src, dst = sg.rmat(scale, ef << scale, replica_seed(seed, rank))
         G = pr.Graph.from_edges(n, src, dst, device=True, stream=stream)
         size = max(1, int(round(a.batch_frac * G.m)))
         # batches for the group steps, then as many for the plain steps, then
