@@ -283,13 +283,22 @@ __global__ void k_row_degrees(const uint64_t* __restrict__ rows, const int64_t* 
 // temporal stream -- and geometric slack makes their repacks rare), an eighth
 // more for every row of degree >= 64 once the direction has been repacked
 // before (the graph keeps growing), and never less than the row had
+// (also each row's first deletion and insertion, dstart / istart[0..n], for
+// pass 2)
 __global__ void k_repack_plan(const int64_t* __restrict__ off, const int32_t* __restrict__ deg, int32_t n,
                               const uint64_t* __restrict__ dl, int64_t nd, const uint64_t* __restrict__ il, int64_t ni,
-                              int bits, bool growing, int32_t* __restrict__ newdeg, int64_t* __restrict__ cap) {
+                              int bits, bool growing, int32_t* __restrict__ newdeg, int64_t* __restrict__ cap,
+                              int64_t* __restrict__ dstart, int64_t* __restrict__ istart) {
   GRID_STRIDE(r, n) {
     const uint64_t rk = (uint64_t)r << bits, rk1 = (uint64_t)(r + 1) << bits;
     const int64_t d0 = lower_key(dl, 0, nd, rk), d1 = lower_key(dl, d0, nd, rk1);
     const int64_t i0 = lower_key(il, 0, ni, rk), i1 = lower_key(il, i0, ni, rk1);
+    dstart[r] = d0;
+    istart[r] = i0;
+    if (r == n - 1) {
+      dstart[n] = nd;
+      istart[n] = ni;
+    }
     const int64_t d = deg[r] - (d1 - d0) + (i1 - i0);
     newdeg[r] = (int32_t)d;
     const int64_t extra = i1 > i0 ? round4(d >> 2) : (growing && d >= 64 ? round4(d >> 3) : 0);
@@ -304,16 +313,17 @@ __global__ void k_repack_plan(const int64_t* __restrict__ off, const int32_t* __
 // below x, insertion y -> k + #old below y - #deletions below y), then the
 // padding slots get the sentinel
 __global__ void k_repack_rows(const int64_t* __restrict__ off, const int32_t* __restrict__ deg,
-                              const int32_t* __restrict__ col, int32_t n, const uint64_t* __restrict__ dl, int64_t nd,
-                              const uint64_t* __restrict__ il, int64_t ni, int bits, const int64_t* __restrict__ noff,
+                              const int32_t* __restrict__ col, int32_t n, const uint64_t* __restrict__ dl,
+                              const uint64_t* __restrict__ il, const int64_t* __restrict__ dstart,
+                              const int64_t* __restrict__ istart, int bits, const int64_t* __restrict__ noff,
                               const int32_t* __restrict__ ndeg, int32_t* __restrict__ ncol) {
   const int lane = threadIdx.x & 31;
   const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
   const uint64_t mask = (1ull << bits) - 1;
   for (int64_t r = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5; r < n; r += nw) {
-    const uint64_t rk = (uint64_t)r << bits, rk1 = (uint64_t)(r + 1) << bits;
-    const int64_t d0 = lower_key(dl, 0, nd, rk), d1 = lower_key(dl, d0, nd, rk1);
-    const int64_t i0 = lower_key(il, 0, ni, rk), i1 = lower_key(il, i0, ni, rk1);
+    const uint64_t rk = (uint64_t)r << bits;
+    const int64_t d0 = dstart[r], d1 = dstart[r + 1];
+    const int64_t i0 = istart[r], i1 = istart[r + 1];
     const int64_t base = off[r], nbase = noff[r], dg = deg[r];
     const int32_t* row = col + base;
     for (int64_t x = lane; x < dg; x += 32) {
@@ -352,24 +362,28 @@ static int repack_direction(Graph* g, Csr* c, const uint64_t* dl, int64_t nd, co
   const int bits = g->id_bits;
   const int32_t n = g->n;
   int32_t* ndeg = nullptr;
-  int64_t *cap = nullptr, *noff = nullptr, *scr = nullptr;
+  int64_t *cap = nullptr, *noff = nullptr, *scr = nullptr, *dstart = nullptr, *istart = nullptr;
   int32_t* ncol = nullptr;
   auto release = [&] {
     cudaFree(ndeg);
     cudaFree(cap);
     cudaFree(noff);
     cudaFree(scr);
+    cudaFree(dstart);
+    cudaFree(istart);
   };
   cudaError_t e;
   if ((e = cudaMalloc(&ndeg, sizeof(int32_t) * n)) != cudaSuccess ||
       (e = cudaMalloc(&cap, sizeof(int64_t) * (n + 1))) != cudaSuccess ||
       (e = cudaMalloc(&noff, sizeof(int64_t) * (n + 1))) != cudaSuccess ||
-      (e = cudaMalloc(&scr, sizeof(int64_t) * scan_tmp_elems(n))) != cudaSuccess) {
+      (e = cudaMalloc(&scr, sizeof(int64_t) * scan_tmp_elems(n))) != cudaSuccess ||
+      (e = cudaMalloc(&dstart, sizeof(int64_t) * (n + 1))) != cudaSuccess ||
+      (e = cudaMalloc(&istart, sizeof(int64_t) * (n + 1))) != cudaSuccess) {
     release();
     return cuda_fail(g, e, "cudaMalloc(repack)");
   }
   note_launch(); k_repack_plan<<<grid_for(n, 256), 256, 0, s>>>(c->off, c->deg, n, dl, nd, il, ni, bits, c->repacks > 0,
-                                                                 ndeg, cap);
+                                                                 ndeg, cap, dstart, istart);
   e = scan_excl<int64_t>(cap, noff, n, scr, s);
   int64_t total = 0;
   if (e == cudaSuccess) e = cudaMemcpyAsync(&total, noff + n, sizeof(int64_t), cudaMemcpyDeviceToHost, s);
@@ -379,8 +393,8 @@ static int repack_direction(Graph* g, Csr* c, const uint64_t* dl, int64_t nd, co
     release();
     return cuda_fail(g, e, "repack");
   }
-  note_launch(); k_repack_rows<<<num_sms() * 16, 256, 0, s>>>(c->off, c->deg, c->col, n, dl, nd, il, ni, bits, noff,
-                                                              ndeg, ncol);
+  note_launch(); k_repack_rows<<<num_sms() * 16, 256, 0, s>>>(c->off, c->deg, c->col, n, dl, il, dstart, istart, bits,
+                                                              noff, ndeg, ncol);
   e = cudaMemcpyAsync(c->off, noff, sizeof(int64_t) * (n + 1), cudaMemcpyDeviceToDevice, s);
   if (e == cudaSuccess) e = cudaMemcpyAsync(c->deg, ndeg, sizeof(int32_t) * n, cudaMemcpyDeviceToDevice, s);
   if (e == cudaSuccess) e = cudaStreamSynchronize(s);
