@@ -277,19 +277,31 @@ __global__ void k_row_degrees(const uint64_t* __restrict__ rows, const int64_t* 
   }
 }
 
+constexpr int32_t REPACK_SHORT = 64;     // rows of at most this degree are rewritten by one thread
+constexpr int32_t REPACK_HUB = 16384;    // rows above this degree are spread over many blocks
+constexpr int64_t REPACK_CHUNK = 8192;   // elements of a hub row per block
+
 // repack of a direction, pass 1: per row the new degree and the new capacity:
 // round4(degree) + 8 slots of slack, a quarter of the degree more for a row
 // that received insertions (rows that grew tend to grow again -- a hub of a
 // temporal stream -- and geometric slack makes their repacks rare), an eighth
 // more for every row of degree >= 64 once the direction has been repacked
 // before (the graph keeps growing), and never less than the row had
-// (also each row's first deletion and insertion, dstart / istart[0..n], for
-// pass 2)
+// (also each row's first deletion and insertion, dstart / istart[0..n], and
+// the list of rows above REPACK_HUB with their count and largest degree in
+// hinfo[0..1], for pass 2)
 __global__ void k_repack_plan(const int64_t* __restrict__ off, const int32_t* __restrict__ deg, int32_t n,
                               const uint64_t* __restrict__ dl, int64_t nd, const uint64_t* __restrict__ il, int64_t ni,
                               int bits, bool growing, int32_t* __restrict__ newdeg, int64_t* __restrict__ cap,
-                              int64_t* __restrict__ dstart, int64_t* __restrict__ istart) {
+                              int64_t* __restrict__ dstart, int64_t* __restrict__ istart, int32_t* __restrict__ hubs,
+                              int32_t* __restrict__ hinfo) {
   GRID_STRIDE(r, n) {
+    const int32_t od = deg[r];
+    const int slot = warp_append(hinfo, od > REPACK_HUB);
+    if (od > REPACK_HUB) {
+      hubs[slot] = (int32_t)r;
+      atomicMax(hinfo + 1, od);
+    }
     const uint64_t rk = (uint64_t)r << bits, rk1 = (uint64_t)(r + 1) << bits;
     const int64_t d0 = lower_key(dl, 0, nd, rk), d1 = lower_key(dl, d0, nd, rk1);
     const int64_t i0 = lower_key(il, 0, ni, rk), i1 = lower_key(il, i0, ni, rk1);
@@ -307,11 +319,56 @@ __global__ void k_repack_plan(const int64_t* __restrict__ off, const int32_t* __
   }
 }
 
-// pass 2, one warp per row: the surviving old elements and the insertions
-// merged into the new column array (both are sorted, so each element's output
-// position is its rank: survivors x -> i - #deletions below x + #insertions
-// below x, insertion y -> k + #old below y - #deletions below y), then the
-// padding slots get the sentinel
+// pass 2 for the rows longer than REPACK_SHORT: the surviving old elements
+// and the insertions merged into the new column array (both are sorted, so
+// each element's output position is its rank: survivors x -> i - #deletions
+// below x + #insertions below x, insertion y -> k + #old below y - #deletions
+// below y), then the padding slots get the sentinel.  part / nparts: this
+// call's share of the row -- elements [part * chunk, (part + 1) * chunk) and
+// the same share of its insertions and of its padding -- worked by `step`
+// threads from t0.
+__device__ __forceinline__ void repack_row_part(int64_t r, int64_t part, int64_t nparts, int64_t chunk, int64_t t0,
+                                                int64_t step, const int64_t* __restrict__ off,
+                                                const int32_t* __restrict__ deg, const int32_t* __restrict__ col,
+                                                int32_t n, const uint64_t* __restrict__ dl,
+                                                const uint64_t* __restrict__ il, const int64_t* __restrict__ dstart,
+                                                const int64_t* __restrict__ istart, int bits,
+                                                const int64_t* __restrict__ noff, const int32_t* __restrict__ ndeg,
+                                                int32_t* __restrict__ ncol) {
+  const uint64_t mask = (1ull << bits) - 1;
+  const int64_t dg = deg[r];
+  const uint64_t rk = (uint64_t)r << bits;
+  const int64_t d0 = dstart[r], d1 = dstart[r + 1];
+  const int64_t i0 = istart[r], i1 = istart[r + 1];
+  const int64_t base = off[r], nbase = noff[r];
+  const int32_t* row = col + base;
+  const int64_t x1 = min(dg, (part + 1) * chunk);
+  for (int64_t x = part * chunk + t0; x < x1; x += step) {
+    const int32_t v = row[x];
+    const uint64_t key = rk | (uint64_t)v;
+    const int64_t dlt = lower_key(dl, d0, d1, key);
+    if (dlt < d1 && dl[dlt] == key) continue;   // deleted
+    ncol[nbase + x - (dlt - d0) + (lower_key(il, i0, i1, key) - i0)] = v;
+  }
+  const int64_t ish = cdiv(i1 - i0, nparts);
+  const int64_t k1 = min(i1, i0 + (part + 1) * ish);
+  for (int64_t k = i0 + part * ish + t0; k < k1; k += step) {
+    const int32_t y = (int32_t)(il[k] & mask);
+    int64_t a = 0, b = dg;   // old elements below y
+    while (a < b) {
+      const int64_t mid = (a + b) >> 1;
+      if (row[mid] < y) a = mid + 1;
+      else b = mid;
+    }
+    ncol[nbase + (k - i0) + a - (lower_key(dl, d0, d1, rk | (uint64_t)y) - d0)] = y;
+  }
+  const int64_t f0 = ndeg[r], f1 = noff[r + 1] - nbase;
+  const int64_t fsh = cdiv(f1 - f0, nparts);
+  const int64_t e1 = min(f1, f0 + (part + 1) * fsh);
+  for (int64_t x = f0 + part * fsh + t0; x < e1; x += step) ncol[nbase + x] = n;
+}
+
+// rows of degree in (REPACK_SHORT, REPACK_HUB], one warp per row
 __global__ void k_repack_rows(const int64_t* __restrict__ off, const int32_t* __restrict__ deg,
                               const int32_t* __restrict__ col, int32_t n, const uint64_t* __restrict__ dl,
                               const uint64_t* __restrict__ il, const int64_t* __restrict__ dstart,
@@ -319,31 +376,70 @@ __global__ void k_repack_rows(const int64_t* __restrict__ off, const int32_t* __
                               const int32_t* __restrict__ ndeg, int32_t* __restrict__ ncol) {
   const int lane = threadIdx.x & 31;
   const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
-  const uint64_t mask = (1ull << bits) - 1;
   for (int64_t r = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5; r < n; r += nw) {
-    const uint64_t rk = (uint64_t)r << bits;
-    const int64_t d0 = dstart[r], d1 = dstart[r + 1];
-    const int64_t i0 = istart[r], i1 = istart[r + 1];
-    const int64_t base = off[r], nbase = noff[r], dg = deg[r];
-    const int32_t* row = col + base;
-    for (int64_t x = lane; x < dg; x += 32) {
-      const int32_t v = row[x];
-      const uint64_t key = rk | (uint64_t)v;
-      const int64_t dlt = lower_key(dl, d0, d1, key);
-      if (dlt < d1 && dl[dlt] == key) continue;   // deleted
-      ncol[nbase + x - (dlt - d0) + (lower_key(il, i0, i1, key) - i0)] = v;
-    }
-    for (int64_t k = i0 + lane; k < i1; k += 32) {
-      const int32_t y = (int32_t)(il[k] & mask);
-      int64_t a = 0, b = dg;   // old elements below y
-      while (a < b) {
-        const int64_t mid = (a + b) >> 1;
-        if (row[mid] < y) a = mid + 1;
-        else b = mid;
+    const int64_t dg = deg[r];
+    if (dg <= REPACK_SHORT || dg > REPACK_HUB) continue;   // k_repack_short / k_repack_hub
+    repack_row_part(r, 0, 1, dg, lane, 32, off, deg, col, n, dl, il, dstart, istart, bits, noff, ndeg, ncol);
+  }
+}
+
+// rows of degree above REPACK_HUB (listed by k_repack_plan): block (x, y)
+// works share x of hub row hubs[y], REPACK_CHUNK elements each, so a row of
+// a million edges is spread over the grid instead of one warp
+__global__ void k_repack_hub(const int32_t* __restrict__ hubs, const int64_t* __restrict__ off,
+                             const int32_t* __restrict__ deg, const int32_t* __restrict__ col, int32_t n,
+                             const uint64_t* __restrict__ dl, const uint64_t* __restrict__ il,
+                             const int64_t* __restrict__ dstart, const int64_t* __restrict__ istart, int bits,
+                             const int64_t* __restrict__ noff, const int32_t* __restrict__ ndeg,
+                             int32_t* __restrict__ ncol) {
+  const int64_t r = hubs[blockIdx.y];
+  const int64_t nparts = cdiv((int64_t)deg[r], REPACK_CHUNK);
+  if ((int64_t)blockIdx.x >= nparts) return;
+  repack_row_part(r, blockIdx.x, nparts, REPACK_CHUNK, threadIdx.x, blockDim.x, off, deg, col, n, dl, il, dstart,
+                  istart, bits, noff, ndeg, ncol);
+}
+
+// pass 2 for the short rows (degree <= REPACK_SHORT), one thread per row: an
+// untouched row is copied as whole quads (both offsets are multiples of four
+// slots, so the copies are aligned 16-byte moves), a touched one is merged
+// element by element (old elements ascending, deletions skipped, insertions
+// placed in order: the effective deletions are present and the effective
+// insertions absent, so the merge never meets an equal pair).  The rest of the
+// new capacity gets the sentinel.  Longer rows are left to k_repack_rows.
+__global__ void k_repack_short(const int64_t* __restrict__ off, const int32_t* __restrict__ deg,
+                               const int32_t* __restrict__ col, int32_t n, const uint64_t* __restrict__ dl,
+                               const uint64_t* __restrict__ il, const int64_t* __restrict__ dstart,
+                               const int64_t* __restrict__ istart, int bits, const int64_t* __restrict__ noff,
+                               int32_t* __restrict__ ncol) {
+  const uint64_t mask = (1ull << bits) - 1;
+  GRID_STRIDE(r, n) {
+    const int32_t dg = deg[r];
+    if (dg > REPACK_SHORT) continue;
+    const int64_t d0 = dstart[r], d1 = dstart[r + 1], i0 = istart[r], i1 = istart[r + 1];
+    const int32_t* row = col + off[r];
+    int32_t* out = ncol + noff[r];
+    const int64_t ncap = noff[r + 1] - noff[r];
+    int64_t o = 0;
+    if (d0 == d1 && i0 == i1) {
+      const int64_t q = round4(dg);   // the last quad's slack slots already hold the sentinel
+      for (int64_t k = 0; k < q; k += 4)
+        *reinterpret_cast<int4*>(out + k) = *reinterpret_cast<const int4*>(row + k);
+      o = q;
+    } else {
+      int64_t di = d0, ii = i0;
+      for (int32_t x = 0; x < dg; x++) {
+        const int32_t v = row[x];
+        while (ii < i1 && (int32_t)(il[ii] & mask) < v) out[o++] = (int32_t)(il[ii++] & mask);
+        while (di < d1 && (int32_t)(dl[di] & mask) < v) di++;
+        if (di < d1 && (int32_t)(dl[di] & mask) == v) {
+          di++;
+          continue;
+        }
+        out[o++] = v;
       }
-      ncol[nbase + (k - i0) + a - (lower_key(dl, d0, d1, rk | (uint64_t)y) - d0)] = y;
+      while (ii < i1) out[o++] = (int32_t)(il[ii++] & mask);
     }
-    for (int64_t x = ndeg[r] + lane; x < noff[r + 1] - nbase; x += 32) ncol[nbase + x] = n;
+    for (; o < ncap; o++) out[o] = n;
   }
 }
 
@@ -363,7 +459,7 @@ static int repack_direction(Graph* g, Csr* c, const uint64_t* dl, int64_t nd, co
   const int32_t n = g->n;
   int32_t* ndeg = nullptr;
   int64_t *cap = nullptr, *noff = nullptr, *scr = nullptr, *dstart = nullptr, *istart = nullptr;
-  int32_t* ncol = nullptr;
+  int32_t *ncol = nullptr, *hubs = nullptr, *hinfo = nullptr;
   auto release = [&] {
     cudaFree(ndeg);
     cudaFree(cap);
@@ -371,30 +467,47 @@ static int repack_direction(Graph* g, Csr* c, const uint64_t* dl, int64_t nd, co
     cudaFree(scr);
     cudaFree(dstart);
     cudaFree(istart);
+    cudaFree(hubs);
+    cudaFree(hinfo);
   };
+  // rows above REPACK_HUB, each holding more than REPACK_HUB of the old edges
+  const int64_t hub_cap = std::min<int64_t>(n, c->cap / REPACK_HUB + 1);
   cudaError_t e;
   if ((e = cudaMalloc(&ndeg, sizeof(int32_t) * n)) != cudaSuccess ||
       (e = cudaMalloc(&cap, sizeof(int64_t) * (n + 1))) != cudaSuccess ||
       (e = cudaMalloc(&noff, sizeof(int64_t) * (n + 1))) != cudaSuccess ||
       (e = cudaMalloc(&scr, sizeof(int64_t) * scan_tmp_elems(n))) != cudaSuccess ||
       (e = cudaMalloc(&dstart, sizeof(int64_t) * (n + 1))) != cudaSuccess ||
-      (e = cudaMalloc(&istart, sizeof(int64_t) * (n + 1))) != cudaSuccess) {
+      (e = cudaMalloc(&istart, sizeof(int64_t) * (n + 1))) != cudaSuccess ||
+      (e = cudaMalloc(&hubs, sizeof(int32_t) * hub_cap)) != cudaSuccess ||
+      (e = cudaMalloc(&hinfo, sizeof(int32_t) * 2)) != cudaSuccess ||
+      (e = cudaMemsetAsync(hinfo, 0, sizeof(int32_t) * 2, s)) != cudaSuccess) {
     release();
     return cuda_fail(g, e, "cudaMalloc(repack)");
   }
   note_launch(); k_repack_plan<<<grid_for(n, 256), 256, 0, s>>>(c->off, c->deg, n, dl, nd, il, ni, bits, c->repacks > 0,
-                                                                 ndeg, cap, dstart, istart);
+                                                                 ndeg, cap, dstart, istart, hubs, hinfo);
   e = scan_excl<int64_t>(cap, noff, n, scr, s);
   int64_t total = 0;
+  int32_t hinfo_h[2] = {0, 0};
   if (e == cudaSuccess) e = cudaMemcpyAsync(&total, noff + n, sizeof(int64_t), cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(hinfo_h, hinfo, sizeof(hinfo_h), cudaMemcpyDeviceToHost, s);
   if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  if (e == cudaSuccess && (hinfo_h[0] < 0 || hinfo_h[0] > hub_cap || hinfo_h[0] > 65535)) e = cudaErrorUnknown;
   if (e == cudaSuccess) e = cudaMalloc(&ncol, sizeof(int32_t) * (size_t)total);
   if (e != cudaSuccess) {
     release();
     return cuda_fail(g, e, "repack");
   }
+  note_launch(); k_repack_short<<<grid_for(n, 256), 256, 0, s>>>(c->off, c->deg, c->col, n, dl, il, dstart, istart,
+                                                                  bits, noff, ncol);
   note_launch(); k_repack_rows<<<num_sms() * 16, 256, 0, s>>>(c->off, c->deg, c->col, n, dl, il, dstart, istart, bits,
                                                               noff, ndeg, ncol);
+  if (hinfo_h[0] > 0) {
+    const dim3 hgrid((unsigned)cdiv(hinfo_h[1], REPACK_CHUNK), (unsigned)hinfo_h[0]);
+    note_launch(); k_repack_hub<<<hgrid, 256, 0, s>>>(hubs, c->off, c->deg, c->col, n, dl, il, dstart, istart, bits, noff,
+                                                       ndeg, ncol);
+  }
   e = cudaMemcpyAsync(c->off, noff, sizeof(int64_t) * (n + 1), cudaMemcpyDeviceToDevice, s);
   if (e == cudaSuccess) e = cudaMemcpyAsync(c->deg, ndeg, sizeof(int32_t) * n, cudaMemcpyDeviceToDevice, s);
   if (e == cudaSuccess) e = cudaStreamSynchronize(s);
