@@ -232,7 +232,7 @@ __device__ __forceinline__ void flush_totals(PullTotals& t, GState* s) {
 
 // epilogue phase of one iteration, every live graph, units of FU chunks
 // (Eq. 2 for DF-P when CLOSED, else Eq. 1)
-template <bool CLOSED, int FU>
+template <bool CLOSED, int FU, bool REL>
 __global__ void __launch_bounds__(GR_THREADS, 2) k_g_finish(const GRun* __restrict__ run,
                                                             const GDesc* __restrict__ desc, GState* __restrict__ st) {
   __shared__ int64_t pre[PR_GROUP_MAX + 1];
@@ -271,7 +271,7 @@ __global__ void __launch_bounds__(GR_THREADS, 2) k_g_finish(const GRun* __restri
     p.metric = run->metric;
     const int64_t nchunks = cdiv(d.n, 32);
     const int64_t ch0 = (u - pre[g]) * FU;
-    finish_pull_step<CLOSED, GView, false, FU>(p, d.acc, d.anyb, ch0, nchunks, t);
+    finish_pull_step<CLOSED, GView, false, FU, REL>(p, d.acc, d.anyb, ch0, nchunks, t);
   }
   if (tg >= 0) flush_totals(t, st + tg);
 }
@@ -339,7 +339,7 @@ struct pr_group {
   // the unit sizes of exec_q / exec_f
   cudaGraph_t graph[2] = {nullptr, nullptr};
   cudaGraphExec_t exec[2] = {nullptr, nullptr};
-  int exec_q[2] = {-1, -1}, exec_f[2] = {-1, -1};
+  int exec_q[2] = {-1, -1}, exec_f[2] = {-1, -1}, exec_rel[2] = {-1, -1};
   cudaGraphConditionalHandle cond[2] = {0, 0};
   cudaEvent_t ev[3] = {nullptr, nullptr, nullptr};
   // the update in flight: its members (group indices) and method
@@ -389,14 +389,26 @@ static const void* gather_fn(int qi) {
   }
 }
 
-static const void* finish_fn(int k, int fi) {
+// epilogue kernel for form k (1: DF-P), unit-size index fi, and whether the
+// measure is the relative change of Alg. 1 (compiled in) or chosen at run time
+static const void* finish_fn(int k, int fi, bool rel) {
+  if (rel) {
+    switch (fi * 2 + k) {
+      case 0: return (const void*)k_g_finish<false, 1, true>;
+      case 1: return (const void*)k_g_finish<true, 1, true>;
+      case 2: return (const void*)k_g_finish<false, 2, true>;
+      case 3: return (const void*)k_g_finish<true, 2, true>;
+      case 4: return (const void*)k_g_finish<false, 4, true>;
+      default: return (const void*)k_g_finish<true, 4, true>;
+    }
+  }
   switch (fi * 2 + k) {
-    case 0: return (const void*)k_g_finish<false, 1>;
-    case 1: return (const void*)k_g_finish<true, 1>;
-    case 2: return (const void*)k_g_finish<false, 2>;
-    case 3: return (const void*)k_g_finish<true, 2>;
-    case 4: return (const void*)k_g_finish<false, 4>;
-    default: return (const void*)k_g_finish<true, 4>;
+    case 0: return (const void*)k_g_finish<false, 1, false>;
+    case 1: return (const void*)k_g_finish<true, 1, false>;
+    case 2: return (const void*)k_g_finish<false, 2, false>;
+    case 3: return (const void*)k_g_finish<true, 2, false>;
+    case 4: return (const void*)k_g_finish<false, 4, false>;
+    default: return (const void*)k_g_finish<true, 4, false>;
   }
 }
 
@@ -405,19 +417,20 @@ static void drop_exec(pr_group* q, int k) {
   if (q->graph[k]) cudaGraphDestroy(q->graph[k]);
   q->exec[k] = nullptr;
   q->graph[k] = nullptr;
-  q->exec_q[k] = q->exec_f[k] = -1;
+  q->exec_q[k] = q->exec_f[k] = q->exec_rel[k] = -1;
 }
 
 // init -> mark -> WHILE (gather -> finish -> control); k = 1 for the DF-P epilogue
-static cudaError_t build_exec(pr_group* q, int k) {
+static cudaError_t build_exec(pr_group* q, int k, bool rel) {
   cudaError_t e;
   cudaGraph_t& graph = q->graph[k];
   if ((e = cudaGraphCreate(&graph, 0)) != cudaSuccess) return e;
   if ((e = cudaGraphConditionalHandleCreate(&q->cond[k], graph, 0, 0)) != cudaSuccess) return e;
-  const void* fin = finish_fn(k, q->fi);
+  const void* fin = finish_fn(k, q->fi, rel);
   const void* gat = gather_fn(q->qi);
   q->exec_q[k] = q->qi;
   q->exec_f[k] = q->fi;
+  q->exec_rel[k] = rel ? 1 : 0;
   const int sms = num_sms();
   const int g_init = sms * blocks_per_sm((const void*)k_g_init, GR_THREADS);
   const int g_gather = sms * blocks_per_sm(gat, GR_THREADS);
@@ -499,10 +512,10 @@ void pr_group_destroy(pr_group* q) { group_free(q); }
 // the same kernels launched one by one, the loop condition read back after
 // every iteration (PR_OPT_HOST_LOOP): for profilers that cannot see into a
 // CUDA graph with conditional nodes, and for drivers without them
-static cudaError_t host_loop(pr_group* q, int k, int32_t max_iter) {
+static cudaError_t host_loop(pr_group* q, int k, int32_t max_iter, bool rel) {
   cudaStream_t s = q->stream;
   const int sms = num_sms();
-  const void* fin = finish_fn(k, q->fi);
+  const void* fin = finish_fn(k, q->fi, rel);
   const void* gat = gather_fn(q->qi);
   const int g_init = sms * blocks_per_sm((const void*)k_g_init, GR_THREADS);
   const int g_gather = sms * blocks_per_sm(gat, GR_THREADS);
@@ -639,13 +652,14 @@ pr_status group_launch(pr_group* q, pr_method method, double alpha, double tau, 
     return PR_ECUDA;
   const int k = method == PR_DFP ? 1 : 0;
   if (r.use_graph) {
-    if (q->exec[k] && (q->exec_q[k] != q->qi || q->exec_f[k] != q->fi)) drop_exec(q, k);
-    if (!q->exec[k] && build_exec(q, k) != cudaSuccess) {
+    const int rel = r.metric == METRIC_RELATIVE ? 1 : 0;
+    if (q->exec[k] && (q->exec_q[k] != q->qi || q->exec_f[k] != q->fi || q->exec_rel[k] != rel)) drop_exec(q, k);
+    if (!q->exec[k] && build_exec(q, k, rel != 0) != cudaSuccess) {
       cudaGetLastError();
       return PR_ECUDA;
     }
     if (cudaGraphLaunch(q->exec[k], s) != cudaSuccess) return PR_ECUDA;
-  } else if (host_loop(q, k, o.max_iter) != cudaSuccess) {
+  } else if (host_loop(q, k, o.max_iter, r.metric == METRIC_RELATIVE) != cudaSuccess) {
     return PR_ECUDA;
   }
   if (cudaMemcpyAsync(q->h_state, q->d_state, sizeof(GState) * G, cudaMemcpyDeviceToHost, s) != cudaSuccess ||

@@ -71,8 +71,10 @@ struct GatherSpan {
   bool wrote;
 };
 
-// quads [base, base + 32 * QPT) of one in-CSR; S / X / anyb only in pull form
-template <bool PULL, int QPT = SW_QPT, bool HUB = false>
+// quads [base, base + 32 * QPT) of one in-CSR; S / X / anyb only in pull form.
+// SPAN: also report what the step touched (the one-launch sweep needs it; the
+// other callers skip the extra warp operations)
+template <bool PULL, int QPT = SW_QPT, bool HUB = false, bool SPAN = false>
 __device__ __forceinline__ GatherSpan gather_step(const int32_t* __restrict__ icol, const long long* __restrict__ C,
                                                   const uint32_t* __restrict__ X, const uint32_t* __restrict__ S,
                                                   const uint32_t* __restrict__ rowbits,
@@ -116,13 +118,14 @@ __device__ __forceinline__ GatherSpan gather_step(const int32_t* __restrict__ ic
     if (PULL && owner[j] >= 0 && !((__ldg(S + (owner[j] >> 5)) >> (owner[j] & 31)) & 1u))
       x[j] = (expanded(c[j].x) | expanded(c[j].y) | expanded(c[j].z) | expanded(c[j].w)) & 1u;
   }
-  GatherSpan span;
-  span.first = __shfl_sync(0xffffffffu, owner[0], 0);
-  int hi = owner[0];
+  GatherSpan span{0, 0, false};
+  if (SPAN) {
+    span.first = __shfl_sync(0xffffffffu, owner[0], 0);
+    int hi = owner[0];
 #pragma unroll
-  for (int j = 1; j < QPT; j++) hi = max(hi, owner[j]);
-  span.last = __reduce_max_sync(0xffffffffu, hi);
-  span.wrote = false;
+    for (int j = 1; j < QPT; j++) hi = max(hi, owner[j]);
+    span.last = __reduce_max_sync(0xffffffffu, hi);
+  }
 #pragma unroll
   for (int j = 0; j < QPT; j++) {
     const int own = owner[j];
@@ -142,7 +145,7 @@ __device__ __forceinline__ GatherSpan gather_step(const int32_t* __restrict__ ic
     if (own >= 0 && (lane == 0 || prev != own)) {
       if (sum) atomicAdd(reinterpret_cast<unsigned long long*>(acc + own), (unsigned long long)sum);
       if (PULL && any) atomicOr(anyb + (own >> 5), 1u << (own & 31));
-      span.wrote = span.wrote || sum != 0 || (PULL && any);
+      if (SPAN) span.wrote = span.wrote || sum != 0 || (PULL && any);
     }
   }
   return span;
@@ -160,11 +163,13 @@ struct PullTotals {
 
 // chunks [ch0, ch0 + U) of one graph.  P provides n, odeg, ideg, R, Ccur,
 // Cnext, S_cur, S_next, X_next, ever, tab_sc, tab_cl, alpha, C0, tau_f, tau_p,
-// metric.
+// metric (unless REL).
 // The accumulators and the expanded-source words it reads are left zero for
 // the next sweep.  L2: read them from L2 (they were written by other SMs in
 // the same launch).
-template <bool CLOSED, class P, bool L2 = false, int U = FIN_U>
+// REL: the relative measure of Alg. 1 fixed at compile time (the default);
+// otherwise p.metric chooses
+template <bool CLOSED, class P, bool L2 = false, int U = FIN_U, bool REL = false>
 __device__ __forceinline__ void finish_pull_step(const P& p, long long* __restrict__ acc, uint32_t* __restrict__ anyb,
                                                  int64_t ch0, int64_t nchunks, PullTotals& t) {
   const int lane = threadIdx.x & 31;
@@ -213,7 +218,8 @@ __device__ __forceinline__ void finish_pull_step(const P& p, long long* __restri
       // Alg. 1: prune when dr / max(r, R[v]) <= tau_p (DF-P), expand when it
       // is > tau_f (or the other measures of Sec. 4.3); compared without the
       // division
-      const double mr = measure_base(p.metric, dbits(r) > dbits(Rv[u]) ? r : Rv[u], d[u]);
+      const double mx = dbits(r) > dbits(Rv[u]) ? r : Rv[u];
+      const double mr = REL ? mx : measure_base(p.metric, mx, d[u]);
       const unsigned long long tf = dbits(p.tau_f * mr);
       const unsigned long long tp = same_tau ? tf : dbits(p.tau_p * mr);
       stay = !CLOSED || drb > tp;

@@ -384,7 +384,7 @@ __global__ void __launch_bounds__(1024) k_gather_rows(const int32_t* __restrict_
                                 hub);
 }
 
-template <bool CLOSED>
+template <bool CLOSED, bool REL>
 __global__ void __launch_bounds__(256, 4) k_finish_pull(SweepParams p, long long* __restrict__ acc,
                                                         uint32_t* __restrict__ anyb) {
   const int lane = threadIdx.x & 31;
@@ -392,7 +392,7 @@ __global__ void __launch_bounds__(256, 4) k_finish_pull(SweepParams p, long long
   const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
   PullTotals t;
   for (int64_t ch0 = ((blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5) * FIN_U; ch0 < nchunks; ch0 += nw * FIN_U)
-    finish_pull_step<CLOSED>(p, acc, anyb, ch0, nchunks, t);
+    finish_pull_step<CLOSED, SweepParams, false, FIN_U, REL>(p, acc, anyb, ch0, nchunks, t);
   if (lane == 0) {
     if (t.stays) atomicAdd(p.cnt_next, t.stays);
     if (t.exps) atomicAdd(p.cnt_x, t.exps);
@@ -562,7 +562,7 @@ __global__ void __launch_bounds__(1024) k_sweep_rows(SweepParams p, const uint32
     for (int r = 0; r < RU; r++) {
       const int64_t u = tk * RU + r;
       if (u >= nunits) break;
-      const GatherSpan sp = gather_step<PULL, QPT, HUB>(p.icol, p.Ccur, p.X_cur, p.S_cur, rowbits, rowbase, nquads,
+      const GatherSpan sp = gather_step<PULL, QPT, HUB, true>(p.icol, p.Ccur, p.X_cur, p.S_cur, rowbits, rowbase, nquads,
                                                         p.n, p.gacc, anyb, u * UQ, pol_stream, pol_keep, hub);
       first = min(first, sp.first);
       last = max(last, sp.last);
@@ -743,8 +743,16 @@ cudaError_t launch_full_sweep(int mode, const SweepParams& p, const GatherCfg& c
   int rgrid = grid_for(p.n, 256);
   switch (mode) {
     case SWEEP_FULL: note_launch(); k_finish_full<<<rgrid, 256, 0, s>>>(p, p.gacc); break;
-    case SWEEP_PULL_DF: note_launch(); k_finish_pull<false><<<rgrid, 256, 0, s>>>(p, p.gacc, anyb); break;
-    case SWEEP_PULL_DFP: note_launch(); k_finish_pull<true><<<rgrid, 256, 0, s>>>(p, p.gacc, anyb); break;
+    case SWEEP_PULL_DF:
+      note_launch();
+      if (p.metric == METRIC_RELATIVE) k_finish_pull<false, true><<<rgrid, 256, 0, s>>>(p, p.gacc, anyb);
+      else k_finish_pull<false, false><<<rgrid, 256, 0, s>>>(p, p.gacc, anyb);
+      break;
+    case SWEEP_PULL_DFP:
+      note_launch();
+      if (p.metric == METRIC_RELATIVE) k_finish_pull<true, true><<<rgrid, 256, 0, s>>>(p, p.gacc, anyb);
+      else k_finish_pull<true, false><<<rgrid, 256, 0, s>>>(p, p.gacc, anyb);
+      break;
     default: return cudaErrorInvalidValue;
   }
   return cudaGetLastError();

@@ -22,8 +22,18 @@ enum SweepMode : int {
 // tau_p, as the factor of the tolerance: dr > tau * measure_base (relative
 // change: max(r, R[v]); rank change: 1; contribution factor dr / d: d).
 enum Metric : int { METRIC_RELATIVE = 0, METRIC_ABSOLUTE = 1, METRIC_CONTRIB = 2 };
+// d >= 1 as a double, assembled from its bits with integer instructions
+// (exact: a 31-bit integer fits the 53-bit significand), so the default
+// relative measure pays no FP64 conversion even where the compiler evaluates
+// both arms of the choice below
+__device__ __forceinline__ double degree_as_double(int32_t d) {
+  const uint32_t u = (uint32_t)d;
+  const int msb = 31 - __clz(u);
+  const unsigned long long frac = ((unsigned long long)u << (52 - msb)) & ((1ull << 52) - 1);
+  return __longlong_as_double((long long)(((unsigned long long)(1023 + msb) << 52) | frac));
+}
 __device__ __forceinline__ double measure_base(int metric, double mr, int32_t d) {
-  return metric == METRIC_RELATIVE ? mr : (metric == METRIC_ABSOLUTE ? 1.0 : (double)d);
+  return metric == METRIC_RELATIVE ? mr : (metric == METRIC_ABSOLUTE ? 1.0 : degree_as_double(d));
 }
 
 struct SweepParams {
