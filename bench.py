@@ -39,8 +39,9 @@ SWEEP_BYTES_PER_VERTEX = 60
 SAMPLE_SCALE = 18
 # DRAM bytes (read + write) of one pull-form DF-P sweep (k_gather_rows + k_finish_pull) on the
 # default workload, from the one-pass ncu captures under profiles/, keyed by the gather setting
-# (threads, quads per lane, hub vertices, fused epilogue); a setting without a capture reports null
-SWEEP_DRAM_BYTES_RMAT25 = {(256, 4, 0, 0): 11.42e9, (512, 4, 0, 0): 11.28e9}
+# (threads, quads per lane, hub vertices, fused epilogue, ranges); a setting without a capture reports
+# null
+SWEEP_DRAM_BYTES_RMAT25 = {(256, 4, 0, 0, 1): 11.42e9, (512, 4, 0, 0, 1): 11.28e9}
 
 
 def parse():
@@ -69,7 +70,7 @@ def parse():
     ap.add_argument("--graphs", type=int, default=64, help="batched: graphs in the group")
     ap.add_argument("--tune", default="auto",
                     help="large: setting of the every-vertex sweeps: auto (pr_autotune on the first warm-up "
-                         "update), default, or threads,quads_per_lane,hub_vertices,fused_epilogue")
+                         "update), default, or threads,quads_per_lane,hub_vertices,fused_epilogue[,ranges]")
     ap.add_argument("--group-loop", default="device", choices=["device", "host"],
                     help="batched: iteration loop of the group update (host: kernels launched one by one)")
     return ap.parse_args()
@@ -311,7 +312,7 @@ def run_gpu(a, rank, world, local_rank):
                                "k_sweep<DFP> in push form)", "achieved": achieved, "peak": peak,
                      "unit": "GB/s", "frac": achieved / peak,
                      "traffic": SWEEP_DRAM_BYTES_RMAT25.get((tuning.threads, tuning.quads_per_lane, tuning.hub_vertices,
-                                                             tuning.fused_epilogue))
+                                                             tuning.fused_epilogue, tuning.ranges))
                      if (a.scale, a.edge_factor, a.batch_frac) == (25, 32, 1e-4) else None,
                      "peak_source": peak_src + " (MEASURED_PEAKS.json hbm_gbs)" if peak_src == "measured" else
                      "fallback 6800 GB/s"},
@@ -487,7 +488,8 @@ def run_batched(a, rank, world, local_rank):
             "per_graph_settings": {"threads": sorted(set(t.threads for t in ptune)),
                                    "quads_per_lane": sorted(set(t.quads_per_lane for t in ptune)),
                                    "hub_vertices": sorted(set(t.hub_vertices for t in ptune)),
-                                   "fused_epilogue": sorted(set(t.fused_epilogue for t in ptune))},
+                                   "fused_epilogue": sorted(set(t.fused_epilogue for t in ptune)),
+                                   "ranges": sorted(set(t.ranges for t in ptune))},
             "group_update_ms_mean": upd_ms / a.steps,
             "iterations_max_mean": statistics.mean(max(s.iterations for s in step) for step in st_g),
             "iterations_mean": statistics.mean(s.iterations for s in flat),

@@ -406,7 +406,11 @@ void pr_server_destroy(pr_server* srv);
  *                    of out-degree >= hub_min_degree is staged;
  *   fused_epilogue   1: Eq. 1 / Eq. 2 and the frontier tests run inside the
  *                    gather kernel, for each 128-vertex chunk as soon as its
- *                    rows are summed; 0: in a second kernel after the gather.
+ *                    rows are summed; 0: in a second kernel after the gather;
+ *   ranges           1, 2, 4 or 8: the sweep cut into as many vertex ranges; the
+ *                    epilogue of a range runs on a second, high-priority
+ *                    stream while the next range is gathered (fused_epilogue 0
+ *                    only).
  * The setting changes no result: contribution sums are exact (see the
  * conventions above), so every setting gives the same bits.  It belongs to
  * the graph and survives batches.
@@ -426,10 +430,10 @@ void pr_server_destroy(pr_server* srv);
  *   duration of the call.
  *   Errors: PR_EINVAL (method PR_DYNAMIC_TRAVERSAL, whose sweeps are list
  *   sweeps, or bad alpha / tau / reps), PR_ENORANKS, PR_ENOMEM, PR_ECUDA.
- * pr_get_tuning: the graph's current setting (the defaults 256 / 4 / 0 / 0
+ * pr_get_tuning: the graph's current setting (the defaults 256 / 4 / 0 / 0 / 1
  *   until tuned or set).  ms_gather and candidates are 0 unless pr_autotune chose it.
- * pr_set_tuning: sets threads, quads_per_lane, hub_vertices and
- *   fused_epilogue (the other fields are ignored).  hub_vertices above n is clamped; a setting outside
+ * pr_set_tuning: sets threads, quads_per_lane, hub_vertices, fused_epilogue
+ *   and ranges (the other fields are ignored).  hub_vertices above n is clamped; a setting outside
  *   the values above, or a hub too large for one block's shared memory
  *   (about 27.9K vertices), gives PR_EINVAL and no change.
  */
@@ -438,6 +442,7 @@ typedef struct {
   int32_t quads_per_lane;
   int32_t hub_vertices;
   int32_t fused_epilogue;
+  int32_t ranges;
   int32_t hub_min_degree;   /* out-degree of the last staged vertex (0: none)   */
   float ms_gather;          /* pr_autotune: the chosen setting's time per trial (ms): one sweep, or
                                the rank sweeps of one update                        */

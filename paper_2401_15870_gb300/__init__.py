@@ -45,7 +45,8 @@ class pr_stats(ctypes.Structure):
 
 class pr_tuning(ctypes.Structure):
     _fields_ = [("threads", ctypes.c_int32), ("quads_per_lane", ctypes.c_int32), ("hub_vertices", ctypes.c_int32),
-                ("fused_epilogue", ctypes.c_int32), ("hub_min_degree", ctypes.c_int32), ("ms_gather", ctypes.c_float),
+                ("fused_epilogue", ctypes.c_int32), ("ranges", ctypes.c_int32), ("hub_min_degree", ctypes.c_int32),
+                ("ms_gather", ctypes.c_float),
                 ("candidates", ctypes.c_int32)]
 
 
@@ -55,6 +56,7 @@ class Tuning:
     quads_per_lane: int
     hub_vertices: int
     fused_epilogue: int
+    ranges: int
     hub_min_degree: int
     ms_gather: float
     candidates: int
@@ -433,8 +435,8 @@ def pr_get_tuning(h):
     return _tuning(t)
 
 
-def pr_set_tuning(h, threads=256, quads_per_lane=4, hub_vertices=0, fused_epilogue=0):
-    t = pr_tuning(int(threads), int(quads_per_lane), int(hub_vertices), int(fused_epilogue), 0, 0.0, 0)
+def pr_set_tuning(h, threads=256, quads_per_lane=4, hub_vertices=0, fused_epilogue=0, ranges=1):
+    t = pr_tuning(int(threads), int(quads_per_lane), int(hub_vertices), int(fused_epilogue), int(ranges), 0, 0.0, 0)
     _check(load().pr_set_tuning(h, ctypes.byref(t)), h)
 
 
@@ -550,8 +552,8 @@ class Graph:
     def tuning(self) -> Tuning:
         return pr_get_tuning(self._h)
 
-    def set_tuning(self, threads=256, quads_per_lane=4, hub_vertices=0, fused_epilogue=0):
-        pr_set_tuning(self._h, threads, quads_per_lane, hub_vertices, fused_epilogue)
+    def set_tuning(self, threads=256, quads_per_lane=4, hub_vertices=0, fused_epilogue=0, ranges=1):
+        pr_set_tuning(self._h, threads, quads_per_lane, hub_vertices, fused_epilogue, ranges)
 
 
 class Group:

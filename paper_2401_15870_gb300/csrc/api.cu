@@ -217,7 +217,27 @@ static void destroy_handle(pr_graph* h) {
   if (g->small_h) cudaFreeHost(g->small_h);
   for (int i = 0; i < 6; i++)
     if (h->ev[i]) cudaEventDestroy(h->ev[i]);
+  for (cudaEvent_t e : h->saux.ev)
+    if (e) cudaEventDestroy(e);
+  if (h->saux.stream) cudaStreamDestroy(h->saux.stream);
   delete h;
+}
+
+// a non-blocking stream at the highest priority, so that the epilogue blocks
+// of one range are scheduled as soon as the gather of the next leaves room
+cudaError_t dfpr::sweep_aux(pr_graph* h, const GatherCfg& c, const SweepAux** out) {
+  *out = nullptr;
+  if (c.parts <= 1) return cudaSuccess;
+  SweepAux& a = h->saux;
+  if (!a.stream) {
+    int least = 0, greatest = 0;
+    cudaError_t e = cudaDeviceGetStreamPriorityRange(&least, &greatest);
+    if (e == cudaSuccess) e = cudaStreamCreateWithPriority(&a.stream, cudaStreamNonBlocking, greatest);
+    for (int i = 0; e == cudaSuccess && i < 9; i++) e = cudaEventCreateWithFlags(&a.ev[i], cudaEventDisableTiming);
+    if (e != cudaSuccess) return e;
+  }
+  *out = &a;
+  return cudaSuccess;
 }
 
 // ------------------------------------------------------------------ drivers
@@ -365,7 +385,9 @@ struct SweepTimer {
       Graph* g = &h->g;
       SweepParams q = p;
       q.ntiles_host = g->in.cap >> 2;
-      e = launch_full_sweep(mode, q, h->gcfg, g->rowbits, g->rowbase, g->anyb, g->done, s);
+      const SweepAux* aux = nullptr;
+      e = sweep_aux(h, h->gcfg, &aux);
+      if (e == cudaSuccess) e = launch_full_sweep(mode, q, h->gcfg, g->rowbits, g->rowbase, g->anyb, g->done, aux, s);
     } else {
       e = launch_sweep(mode, p, s);
     }

@@ -15,6 +15,7 @@ struct pr_graph {
   double* vec_tmp = nullptr;      // n doubles (rank import / export)
   struct pr_group* solo = nullptr;  // one-graph group behind the device loop of pr_update
   dfpr::GatherCfg gcfg;            // gather configuration of every-vertex sweeps (pr_autotune)
+  dfpr::SweepAux saux;             // second stream and events of sweeps in several ranges (made on first use)
   float gcfg_ms = 0.f;              // its measured gather time (0: not measured)
   int32_t gcfg_trials = 0;          // configurations the last pr_autotune timed
 };
@@ -22,6 +23,9 @@ struct pr_graph {
 namespace dfpr {
 // sweep parameters of a graph's current state (api.cu)
 SweepParams base_params(Graph* g, double alpha, double tau_f, double tau_p);
+// the graph's sweep auxiliary, created on first use for a setting with
+// several ranges (api.cu); NULL when the setting has one range
+cudaError_t sweep_aux(pr_graph* h, const GatherCfg& c, const SweepAux** out);
 // one update with the iteration loop on the host (api.cu); the arguments are
 // validated by the caller
 pr_status run_update(pr_graph* h, int method, double alpha, double tau, double tau_f, double tau_p, int32_t max_iter,

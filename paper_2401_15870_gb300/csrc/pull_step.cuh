@@ -71,7 +71,8 @@ struct GatherSpan {
   bool wrote;
 };
 
-// quads [base, base + 32 * QPT) of one in-CSR; S / X / anyb only in pull form.
+// quads [base, base + 32 * QPT) of one in-CSR, those below qlo or from nquads
+// on left out; S / X / anyb only in pull form.
 // SPAN: also report what the step touched (the one-launch sweep needs it; the
 // other callers skip the extra warp operations)
 template <bool PULL, int QPT = SW_QPT, bool HUB = false, bool SPAN = false>
@@ -81,7 +82,7 @@ __device__ __forceinline__ GatherSpan gather_step(const int32_t* __restrict__ ic
                                                   const int32_t* __restrict__ rowbase, int64_t nquads, int32_t sent,
                                                   long long* __restrict__ acc, uint32_t* __restrict__ anyb,
                                                   int64_t base, uint64_t pol_stream, uint64_t pol_keep,
-                                                  const HubView& hub = HubView()) {
+                                                  const HubView& hub = HubView(), int64_t qlo = 0) {
   const int lane = threadIdx.x & 31;
   const unsigned upto = lane == 31 ? 0xffffffffu : ((2u << lane) - 1u);
   // sentinel slots (row slack) contribute 0 and issue no load; a hub cache
@@ -100,7 +101,7 @@ __device__ __forceinline__ GatherSpan gather_step(const int32_t* __restrict__ ic
 #pragma unroll
   for (int j = 0; j < QPT; j++) {
     const int64_t q = base + 32 * j + lane;
-    const bool valid = q < nquads;
+    const bool valid = q >= qlo && q < nquads;
     c[j] = valid ? ld_stream4(icol + 4 * q, pol_stream) : make_int4(sent, sent, sent, sent);
     const int64_t w = (base >> 5) + j;
     const uint32_t bits = w * 32 < nquads ? __ldg(rowbits + w) : 0u;

@@ -360,7 +360,8 @@ __global__ void __launch_bounds__(1024) k_gather_rows(const int32_t* __restrict_
                                                       const uint32_t* __restrict__ rowbits,
                                                       const int32_t* __restrict__ rowbase, int64_t nquads, int32_t sent,
                                                       long long* __restrict__ acc, uint32_t* __restrict__ anyb,
-                                                      int32_t hub_k, int32_t hub_kx) {
+                                                      int32_t hub_k, int32_t hub_kx, const int64_t* __restrict__ ioff,
+                                                      int32_t v_lo, int32_t v_hi) {
   extern __shared__ __align__(16) unsigned char hub_smem[];
   const int64_t warp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
   const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
@@ -379,20 +380,26 @@ __global__ void __launch_bounds__(1024) k_gather_rows(const int32_t* __restrict_
     hub.k = hub_k;
     hub.kx = PULL ? hub_kx : 0;
   }
-  for (int64_t base = warp * 32 * QPT; base < nquads; base += nw * 32 * QPT)
-    gather_step<PULL, QPT, HUB>(icol, C, X, S, rowbits, rowbase, nquads, sent, acc, anyb, base, pol_stream, pol_keep,
-                                hub);
+  // the rows of vertices [v_lo, v_hi): quads [qlo, qhi), walked in steps
+  // aligned to 32 x QPT quads (the row-start index is per 32-quad word)
+  const int64_t qlo = v_lo > 0 ? __ldg(ioff + v_lo) >> 2 : 0;
+  const int64_t qhi = v_hi < sent ? __ldg(ioff + v_hi) >> 2 : nquads;
+  const int64_t q0 = qlo / (32 * QPT) * (32 * QPT);
+  for (int64_t base = q0 + warp * 32 * QPT; base < qhi; base += nw * 32 * QPT)
+    gather_step<PULL, QPT, HUB>(icol, C, X, S, rowbits, rowbase, qhi, sent, acc, anyb, base, pol_stream, pol_keep,
+                                hub, qlo);
 }
 
+// (the 32-vertex chunks [ch_lo, ch_hi); ch_lo a multiple of FIN_U)
 template <bool CLOSED, bool REL>
 __global__ void __launch_bounds__(256, 4) k_finish_pull(SweepParams p, long long* __restrict__ acc,
-                                                        uint32_t* __restrict__ anyb) {
+                                                        uint32_t* __restrict__ anyb, int64_t ch_lo, int64_t ch_hi) {
   const int lane = threadIdx.x & 31;
-  const int64_t nchunks = cdiv(p.n, 32);
   const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
   PullTotals t;
-  for (int64_t ch0 = ((blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5) * FIN_U; ch0 < nchunks; ch0 += nw * FIN_U)
-    finish_pull_step<CLOSED, SweepParams, false, FIN_U, REL>(p, acc, anyb, ch0, nchunks, t);
+  for (int64_t ch0 = ch_lo + ((blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5) * FIN_U; ch0 < ch_hi;
+       ch0 += nw * FIN_U)
+    finish_pull_step<CLOSED, SweepParams, false, FIN_U, REL>(p, acc, anyb, ch0, ch_hi, t);
   if (lane == 0) {
     if (t.stays) atomicAdd(p.cnt_next, t.stays);
     if (t.exps) atomicAdd(p.cnt_x, t.exps);
@@ -402,20 +409,22 @@ __global__ void __launch_bounds__(256, 4) k_finish_pull(SweepParams p, long long
 
 // Epilogue of a sweep over every vertex with Eq. 1 (Static, ND): all vertices
 // are processed; loads of U vertices per lane are issued together.
-__global__ void __launch_bounds__(256, 4) k_finish_full(SweepParams p, long long* __restrict__ acc) {
+// (vertices [v_lo, v_hi))
+__global__ void __launch_bounds__(256, 4) k_finish_full(SweepParams p, long long* __restrict__ acc, int64_t v_lo,
+                                                        int64_t v_hi) {
   constexpr int U = 4;
   const double alpha_fix = p.alpha * FIX_INV;
   unsigned long long dmax = 0ull;
   long long edges = 0, verts = 0;
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-  for (int64_t v0 = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; v0 < p.n; v0 += stride * U) {
+  for (int64_t v0 = v_lo + blockIdx.x * (int64_t)blockDim.x + threadIdx.x; v0 < v_hi; v0 += stride * U) {
     long long sum[U];
     double Rv[U];
     int32_t d[U];
 #pragma unroll
     for (int u = 0; u < U; u++) {
       const int64_t v = v0 + u * stride;
-      const bool ok = v < p.n;
+      const bool ok = v < v_hi;
       sum[u] = ok ? acc[v] : 0;
       Rv[u] = ok ? p.R[v] : 0.0;
       d[u] = ok ? p.odeg[v] : 1;
@@ -423,7 +432,7 @@ __global__ void __launch_bounds__(256, 4) k_finish_full(SweepParams p, long long
 #pragma unroll
     for (int u = 0; u < U; u++) {
       const int64_t v = v0 + u * stride;
-      if (v >= p.n) continue;
+      if (v >= v_hi) continue;
       acc[v] = 0;
       const double r = fma(alpha_fix, (double)sum[u], p.C0);   // Eq. 1
       const unsigned long long drb = dbits(fabs(r - Rv[u]));
@@ -639,7 +648,8 @@ static cudaError_t sweep_rows_dispatch(const SweepParams& p, const GatherCfg& cf
 
 template <bool PULL, int QPT, bool HUB>
 static cudaError_t gather_launch(const SweepParams& p, const uint32_t* rowbits, const int32_t* rowbase, uint32_t* anyb,
-                                 int64_t nquads, int threads, int32_t hub_k, int32_t hub_kx, cudaStream_t s) {
+                                 int64_t nquads, int threads, int32_t hub_k, int32_t hub_kx, int32_t v_lo, int32_t v_hi,
+                                 bool one_wave, cudaStream_t s) {
   const void* fn = (const void*)k_gather_rows<PULL, QPT, HUB>;
   const size_t smem = HUB ? gather_hub_bytes(hub_k, hub_kx) : 0;
   int bps = 1;
@@ -648,29 +658,31 @@ static cudaError_t gather_launch(const SweepParams& p, const uint32_t* rowbits, 
   // one wave of resident blocks when each block stages a hub cache, else up
   // to 16 blocks of 256 threads per SM; never more warps than work units
   const int64_t units = cdiv(nquads, 32 * QPT);
-  const int64_t cap = HUB ? (int64_t)num_sms() * bps : (int64_t)num_sms() * 16 * 256 / threads;
+  const int64_t cap = HUB || one_wave ? (int64_t)num_sms() * bps : (int64_t)num_sms() * 16 * 256 / threads;
   const int grid = (int)std::max<int64_t>(1, std::min<int64_t>(cdiv(units, threads / 32), cap));
   note_launch();
   k_gather_rows<PULL, QPT, HUB><<<grid, threads, smem, s>>>(p.icol, p.Ccur, PULL ? p.X_cur : nullptr,
                                                           PULL ? p.S_cur : nullptr, rowbits, rowbase, nquads, p.n,
-                                                          p.gacc, anyb, hub_k, hub_kx);
+                                                          p.gacc, anyb, hub_k, hub_kx, p.ioff, v_lo, v_hi);
   return cudaGetLastError();
 }
 
 template <bool PULL>
 static cudaError_t gather_dispatch(const SweepParams& p, const GatherCfg& cfg, const uint32_t* rowbits,
-                                   const int32_t* rowbase, uint32_t* anyb, int64_t nquads, cudaStream_t s) {
+                                   const int32_t* rowbase, uint32_t* anyb, int64_t nquads, int32_t v_lo, int32_t v_hi,
+                                   cudaStream_t s) {
+  const bool ow = cfg.parts > 1;
   const int32_t hub_k = std::min<int32_t>(cfg.hub, p.n + 1);
   const int32_t hub_kx = PULL ? (int32_t)cdiv(std::min<int32_t>(hub_k, p.n), 32) : 0;
   const bool hub = hub_k > 0;
   const int t = cfg.threads;
   switch (cfg.qpt * 2 + (hub ? 1 : 0)) {
-    case 4: return gather_launch<PULL, 2, false>(p, rowbits, rowbase, anyb, nquads, t, 0, 0, s);
-    case 5: return gather_launch<PULL, 2, true>(p, rowbits, rowbase, anyb, nquads, t, hub_k, hub_kx, s);
-    case 8: return gather_launch<PULL, 4, false>(p, rowbits, rowbase, anyb, nquads, t, 0, 0, s);
-    case 9: return gather_launch<PULL, 4, true>(p, rowbits, rowbase, anyb, nquads, t, hub_k, hub_kx, s);
-    case 16: return gather_launch<PULL, 8, false>(p, rowbits, rowbase, anyb, nquads, t, 0, 0, s);
-    case 17: return gather_launch<PULL, 8, true>(p, rowbits, rowbase, anyb, nquads, t, hub_k, hub_kx, s);
+    case 4: return gather_launch<PULL, 2, false>(p, rowbits, rowbase, anyb, nquads, t, 0, 0, v_lo, v_hi, ow, s);
+    case 5: return gather_launch<PULL, 2, true>(p, rowbits, rowbase, anyb, nquads, t, hub_k, hub_kx, v_lo, v_hi, ow, s);
+    case 8: return gather_launch<PULL, 4, false>(p, rowbits, rowbase, anyb, nquads, t, 0, 0, v_lo, v_hi, ow, s);
+    case 9: return gather_launch<PULL, 4, true>(p, rowbits, rowbase, anyb, nquads, t, hub_k, hub_kx, v_lo, v_hi, ow, s);
+    case 16: return gather_launch<PULL, 8, false>(p, rowbits, rowbase, anyb, nquads, t, 0, 0, v_lo, v_hi, ow, s);
+    case 17: return gather_launch<PULL, 8, true>(p, rowbits, rowbase, anyb, nquads, t, hub_k, hub_kx, v_lo, v_hi, ow, s);
     default: return cudaErrorInvalidValue;
   }
 }
@@ -711,18 +723,21 @@ bool gather_cfg_valid(const GatherCfg& c) {
   if (c.threads != 256 && c.threads != 512 && c.threads != 1024) return false;
   if (c.qpt != 2 && c.qpt != 4 && c.qpt != 8) return false;
   if (c.fused != 0 && c.fused != 1) return false;
+  if (c.parts != 1 && c.parts != 2 && c.parts != 4 && c.parts != 8) return false;
+  if (c.parts > 1 && c.fused) return false;
   return c.hub >= 0 && gather_hub_bytes(c.hub, (int32_t)cdiv(c.hub, 32)) <= (size_t)GATHER_SMEM_MAX;
 }
 
 cudaError_t launch_gather(bool pull, const SweepParams& p, const GatherCfg& cfg, const uint32_t* rowbits,
                           const int32_t* rowbase, uint32_t* anyb, int64_t nquads, cudaStream_t s) {
   if (!gather_cfg_valid(cfg)) return cudaErrorInvalidValue;
-  return pull ? gather_dispatch<true>(p, cfg, rowbits, rowbase, anyb, nquads, s)
-              : gather_dispatch<false>(p, cfg, rowbits, rowbase, anyb, nquads, s);
+  return pull ? gather_dispatch<true>(p, cfg, rowbits, rowbase, anyb, nquads, 0, p.n, s)
+              : gather_dispatch<false>(p, cfg, rowbits, rowbase, anyb, nquads, 0, p.n, s);
 }
 
 cudaError_t launch_full_sweep(int mode, const SweepParams& p, const GatherCfg& cfg, const uint32_t* rowbits,
-                              const int32_t* rowbase, uint32_t* anyb, int32_t* done, cudaStream_t s) {
+                              const int32_t* rowbase, uint32_t* anyb, int32_t* done, const SweepAux* aux,
+                              cudaStream_t s) {
   const int64_t nquads = p.ntiles_host;   // quads of the in-CSR capacity
   const bool pull = mode == SWEEP_PULL_DF || mode == SWEEP_PULL_DFP;
   if (pull) {
@@ -738,22 +753,44 @@ cudaError_t launch_full_sweep(int mode, const SweepParams& p, const GatherCfg& c
       default: return cudaErrorInvalidValue;
     }
   }
-  cudaError_t e = launch_gather(pull, p, cfg, rowbits, rowbase, anyb, nquads, s);
-  if (e != cudaSuccess) return e;
-  int rgrid = grid_for(p.n, 256);
-  switch (mode) {
-    case SWEEP_FULL: note_launch(); k_finish_full<<<rgrid, 256, 0, s>>>(p, p.gacc); break;
-    case SWEEP_PULL_DF:
-      note_launch();
-      if (p.metric == METRIC_RELATIVE) k_finish_pull<false, true><<<rgrid, 256, 0, s>>>(p, p.gacc, anyb);
-      else k_finish_pull<false, false><<<rgrid, 256, 0, s>>>(p, p.gacc, anyb);
-      break;
-    case SWEEP_PULL_DFP:
-      note_launch();
-      if (p.metric == METRIC_RELATIVE) k_finish_pull<true, true><<<rgrid, 256, 0, s>>>(p, p.gacc, anyb);
-      else k_finish_pull<true, false><<<rgrid, 256, 0, s>>>(p, p.gacc, anyb);
-      break;
-    default: return cudaErrorInvalidValue;
+  if (!gather_cfg_valid(cfg)) return cudaErrorInvalidValue;
+  // P vertex ranges cut at multiples of 128: the gather of range k + 1 runs on
+  // s while the epilogue of range k runs on the auxiliary stream, so the
+  // FP64-bound epilogue overlaps the L1TEX-bound gather; the epilogues join s
+  // at the end.  P = 1: gather then epilogue on s.
+  const int P = (aux && cfg.parts > 1 && p.n >= 128 * cfg.parts) ? cfg.parts : 1;
+  cudaStream_t fs = P > 1 ? aux->stream : s;
+  for (int k = 0; k < P; k++) {
+    const int32_t v_lo = (int32_t)((int64_t)p.n * k / P / 128 * 128);
+    const int32_t v_hi = k + 1 == P ? p.n : (int32_t)((int64_t)p.n * (k + 1) / P / 128 * 128);
+    cudaError_t e = pull ? gather_dispatch<true>(p, cfg, rowbits, rowbase, anyb, nquads, v_lo, v_hi, s)
+                         : gather_dispatch<false>(p, cfg, rowbits, rowbase, anyb, nquads, v_lo, v_hi, s);
+    if (e != cudaSuccess) return e;
+    if (P > 1) {
+      if ((e = cudaEventRecord(aux->ev[k], s)) != cudaSuccess) return e;
+      if ((e = cudaStreamWaitEvent(fs, aux->ev[k], 0)) != cudaSuccess) return e;
+    }
+    const int64_t ch_lo = v_lo / 32, ch_hi = cdiv(v_hi, 32);
+    const int rgrid = grid_for(v_hi - v_lo, 256);
+    switch (mode) {
+      case SWEEP_FULL: note_launch(); k_finish_full<<<rgrid, 256, 0, fs>>>(p, p.gacc, v_lo, v_hi); break;
+      case SWEEP_PULL_DF:
+        note_launch();
+        if (p.metric == METRIC_RELATIVE) k_finish_pull<false, true><<<rgrid, 256, 0, fs>>>(p, p.gacc, anyb, ch_lo, ch_hi);
+        else k_finish_pull<false, false><<<rgrid, 256, 0, fs>>>(p, p.gacc, anyb, ch_lo, ch_hi);
+        break;
+      case SWEEP_PULL_DFP:
+        note_launch();
+        if (p.metric == METRIC_RELATIVE) k_finish_pull<true, true><<<rgrid, 256, 0, fs>>>(p, p.gacc, anyb, ch_lo, ch_hi);
+        else k_finish_pull<true, false><<<rgrid, 256, 0, fs>>>(p, p.gacc, anyb, ch_lo, ch_hi);
+        break;
+      default: return cudaErrorInvalidValue;
+    }
+  }
+  if (P > 1) {
+    cudaError_t e = cudaEventRecord(aux->ev[P], fs);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(s, aux->ev[P], 0);
+    if (e != cudaSuccess) return e;
   }
   return cudaGetLastError();
 }

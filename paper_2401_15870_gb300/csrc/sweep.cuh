@@ -90,13 +90,20 @@ cudaError_t launch_sweep(int mode, const SweepParams& p, cudaStream_t s);
 // internal ids are ordered by decreasing out-degree, so the hub set is the
 // vertices whose out-degree is at least that of vertex hub - 1), and whether
 // the epilogue runs inside the gather kernel (k_sweep_rows) or as a second
-// launch (k_finish_full / k_finish_pull).  The defaults are the configuration
-// used before any tuning.
+// launch (k_finish_full / k_finish_pull), and in how many vertex ranges the
+// sweep runs.  The defaults are the configuration used before any tuning.
 struct GatherCfg {
   int32_t threads = 256;
   int32_t qpt = SW_QPT;
   int32_t hub = 0;
   int32_t fused = 0;
+  int32_t parts = 1;   // vertex ranges whose epilogue overlaps the next range's gather (1, 2, 4, 8)
+};
+
+// the second stream and the events of a sweep cut into vertex ranges
+struct SweepAux {
+  cudaStream_t stream = nullptr;
+  cudaEvent_t ev[9] = {};
 };
 constexpr int GATHER_SMEM_MAX = 227 * 1024;   // dynamic shared memory of one block on sm_103
 size_t gather_hub_bytes(int32_t hub_k, int32_t hub_kx);
@@ -111,8 +118,10 @@ cudaError_t launch_gather(bool pull, const SweepParams& p, const GatherCfg& cfg,
 // (left zero), rowbits / rowbase the row-start index of the in-CSR
 // (launch_row_start_index), anyb an n-bit scratch bitset, done the all-zero
 // per-chunk unit counts of the one-launch form (cdiv(n, 128) int32, left zero)
+// aux: the second stream of a sweep in several ranges (NULL: one range)
 cudaError_t launch_full_sweep(int mode, const SweepParams& p, const GatherCfg& cfg, const uint32_t* rowbits,
-                              const int32_t* rowbase, uint32_t* anyb, int32_t* done, cudaStream_t s);
+                              const int32_t* rowbase, uint32_t* anyb, int32_t* done, const SweepAux* aux,
+                              cudaStream_t s);
 // row-start index of the in-CSR: rowbits (nquads/32 + 1 words), rowbase (as
 // many int32 + 1); tmp: scan_tmp_elems(nquads/32 + 1) int32
 cudaError_t launch_row_start_index(const int64_t* off, int32_t n, int64_t nquads, uint32_t* rowbits, int32_t* rowbase,

@@ -34,7 +34,7 @@ namespace {
 constexpr int32_t HUB_CANDIDATES[] = {0, 3072, 13824};
 
 bool same_cfg(const GatherCfg& a, const GatherCfg& b) {
-  return a.threads == b.threads && a.qpt == b.qpt && a.hub == b.hub && a.fused == b.fused;
+  return a.threads == b.threads && a.qpt == b.qpt && a.hub == b.hub && a.fused == b.fused && a.parts == b.parts;
 }
 
 pr_status read_tuning(pr_graph* h, pr_tuning* out) {
@@ -43,6 +43,7 @@ pr_status read_tuning(pr_graph* h, pr_tuning* out) {
   out->quads_per_lane = h->gcfg.qpt;
   out->hub_vertices = std::min<int32_t>(h->gcfg.hub, g->n);
   out->fused_epilogue = h->gcfg.fused;
+  out->ranges = h->gcfg.parts;
   out->hub_min_degree = 0;
   if (out->hub_vertices > 0) {
     int32_t d = 0;
@@ -58,22 +59,25 @@ pr_status read_tuning(pr_graph* h, pr_tuning* out) {
 }
 
 // candidate settings: every thread count, quads per lane and hub size in
-// HUB_CANDIDATES (clamped to n + 1), epilogue inside or after the gather
+// HUB_CANDIDATES (clamped to n + 1), epilogue inside or after the gather, and
+// 1, 2, 4 or 8 vertex ranges (separate epilogue only)
 std::vector<GatherCfg> candidates(int32_t n) {
   std::vector<GatherCfg> cands;
   for (int t : {256, 512, 1024})
     for (int q : {2, 4, 8})
       for (int32_t hb : HUB_CANDIDATES)
-        for (int f : {0, 1}) {
-          GatherCfg c;
-          c.threads = t;
-          c.qpt = q;
-          c.hub = std::min<int32_t>(hb, n + 1);
-          c.fused = f;
-          bool dup = false;
-          for (const GatherCfg& o : cands) dup = dup || same_cfg(o, c);
-          if (!dup && gather_cfg_valid(c)) cands.push_back(c);
-        }
+        for (int f : {0, 1})
+          for (int pt : {1, 2, 4, 8}) {
+            GatherCfg c;
+            c.threads = t;
+            c.qpt = q;
+            c.hub = std::min<int32_t>(hb, n + 1);
+            c.fused = f;
+            c.parts = pt;
+            bool dup = false;
+            for (const GatherCfg& o : cands) dup = dup || same_cfg(o, c);
+            if (!dup && gather_cfg_valid(c)) cands.push_back(c);
+          }
   return cands;
 }
 
@@ -97,7 +101,10 @@ pr_status tune_sweeps(pr_graph* h, double alpha, int32_t reps, GatherCfg* best, 
   if (e != cudaSuccess) return (pr_status)cuda_fail(g, e, "pr_autotune");
   cudaEvent_t e0 = h->ev[4], e1 = h->ev[5];
   auto sweep = [&](const GatherCfg& c) {
-    return launch_full_sweep(SWEEP_FULL, p, c, g->rowbits, g->rowbase, g->anyb, g->done, s);
+    const SweepAux* aux = nullptr;
+    cudaError_t ae = sweep_aux(h, c, &aux);
+    return ae == cudaSuccess ? launch_full_sweep(SWEEP_FULL, p, c, g->rowbits, g->rowbase, g->anyb, g->done, aux, s)
+                             : ae;
   };
   for (const GatherCfg& c : candidates(g->n)) {
     // one untimed sweep (also raises the kernel's shared memory limit), then
@@ -223,6 +230,7 @@ pr_status pr_set_tuning(pr_graph* h, const pr_tuning* in) {
   c.qpt = in->quads_per_lane;
   c.hub = in->hub_vertices;
   c.fused = in->fused_epilogue;
+  c.parts = in->ranges;
   if (c.hub < 0 || !gather_cfg_valid(c)) return PR_EINVAL;
   c.hub = std::min<int32_t>(c.hub, h->g.n + 1);
   h->gcfg = c;

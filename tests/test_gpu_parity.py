@@ -403,8 +403,10 @@ def test_deterministic_across_runs(lib):
 
 # ------------------------------------------------------------- gather settings (pr_autotune)
 
-SETTINGS = [(256, 4, 0, 0), (256, 4, 0, 1), (1024, 4, 27648, 1), (512, 2, 13824, 0), (256, 8, 3072, 1),
-            (1024, 8, 100, 0), (512, 4, 1, 1), (1024, 2, 6656, 1), (512, 8, 0, 1), (1024, 2, 0, 0)]
+SETTINGS = [(256, 4, 0, 0, 1), (256, 4, 0, 1, 1), (1024, 4, 27648, 1, 1), (512, 2, 13824, 0, 1),
+            (256, 8, 3072, 1, 1), (1024, 8, 100, 0, 1), (512, 4, 1, 1, 1), (1024, 2, 6656, 1, 1), (512, 8, 0, 1, 1),
+            (1024, 2, 0, 0, 1), (512, 4, 0, 0, 2), (256, 4, 0, 0, 4), (1024, 2, 3072, 0, 4), (256, 8, 0, 0, 2),
+            (1024, 2, 0, 0, 8)]
 
 
 @pytest.mark.parametrize("method,direction", [("static", None), ("nd", None), ("df", "pull"), ("dfp", "pull")])
@@ -412,15 +414,17 @@ SETTINGS = [(256, 4, 0, 0), (256, 4, 0, 1), (1024, 4, 27648, 1), (512, 2, 13824,
 def test_every_gather_setting_gives_the_same_bits(lib, method, direction, scale, bsize):
     """Threads per block, quads per lane, the hub staged in shared memory
     (none, a ragged count, a count above n that covers every vertex and the
-    sentinel) and the epilogue inside or after the gather kernel change only
-    the schedule of exact integer sums: ranks and statistics are bit-identical
-    across settings, and within 1e-9 of the oracle."""
+    sentinel), the epilogue inside or after the gather kernel and the sweep cut
+    into vertex ranges on two streams change only the schedule of exact integer
+    sums: ranks and statistics are bit-identical across settings, and within
+    1e-9 of the oracle."""
     G, O, r0 = rank_case(lib, scale, 16, bsize, 90 + scale)
     out = []
-    for t, q, hub, fused in SETTINGS:
-        G.set_tuning(t, q, hub, fused)
+    for t, q, hub, fused, ranges in SETTINGS:
+        G.set_tuning(t, q, hub, fused, ranges)
         tu = G.tuning()
-        assert (tu.threads, tu.quads_per_lane, tu.hub_vertices, tu.fused_epilogue) == (t, q, min(hub, G.n), fused)
+        assert (tu.threads, tu.quads_per_lane, tu.hub_vertices, tu.fused_epilogue, tu.ranges) == \
+            (t, q, min(hub, G.n), fused, ranges)
         G.set_ranks(r0)
         st = G.update(method, direction=direction, loop="host")
         out.append((G.ranks(), st.iterations, st.vertices_ever_affected, st.vertices_processed, st.edges_processed))
@@ -478,10 +482,11 @@ def test_invalid_gather_settings_are_rejected(lib):
     G, _, _ = rank_case(lib, 10, 8, 20, 5)
     before = G.tuning()
     # a hub of 40000 vertices is above n here, but no block's shared memory holds it
-    for t, q, hub, f in ((128, 4, 0, 1), (256, 3, 0, 1), (256, 4, -1, 1), (256, 4, 40000, 1), (2048, 4, 0, 1),
-                         (256, 4, 0, 2)):
+    for t, q, hub, f, r in ((128, 4, 0, 1, 1), (256, 3, 0, 1, 1), (256, 4, -1, 1, 1), (256, 4, 40000, 1, 1),
+                            (2048, 4, 0, 1, 1), (256, 4, 0, 2, 1), (256, 4, 0, 1, 2), (256, 4, 0, 0, 3),
+                            (256, 4, 0, 0, 0)):
         with pytest.raises(lib.PRError):
-            G.set_tuning(t, q, hub, f)
+            G.set_tuning(t, q, hub, f, r)
     assert G.tuning() == before
 
 
