@@ -41,7 +41,7 @@ SAMPLE_SCALE = 18
 # default workload, from the one-pass ncu captures under profiles/, keyed by the gather setting
 # (threads, quads per lane, hub vertices, fused epilogue, ranges); a setting without a capture reports
 # null
-SWEEP_DRAM_BYTES_RMAT25 = {(256, 4, 0, 0, 1): 11.42e9, (512, 4, 0, 0, 1): 11.28e9}
+SWEEP_DRAM_BYTES_RMAT25 = {(256, 4, 0, 0, 1): 11.42e9, (512, 4, 0, 0, 1): 11.28e9, (1024, 2, 0, 0, 1): 11.44e9}
 
 
 def parse():
