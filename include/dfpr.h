@@ -430,7 +430,7 @@ void pr_server_destroy(pr_server* srv);
  *   duration of the call.
  *   Errors: PR_EINVAL (method PR_DYNAMIC_TRAVERSAL, whose sweeps are list
  *   sweeps, or bad alpha / tau / reps), PR_ENORANKS, PR_ENOMEM, PR_ECUDA.
- * pr_get_tuning: the graph's current setting (the defaults 256 / 4 / 0 / 0 / 1
+ * pr_get_tuning: the graph's current setting (the defaults 1024 / 2 / 0 / 0 / 1
  *   until tuned or set).  ms_gather and candidates are 0 unless pr_autotune chose it.
  * pr_set_tuning: sets threads, quads_per_lane, hub_vertices, fused_epilogue
  *   and ranges (the other fields are ignored).  hub_vertices above n is clamped; a setting outside

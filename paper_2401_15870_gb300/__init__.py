@@ -435,7 +435,7 @@ def pr_get_tuning(h):
     return _tuning(t)
 
 
-def pr_set_tuning(h, threads=256, quads_per_lane=4, hub_vertices=0, fused_epilogue=0, ranges=1):
+def pr_set_tuning(h, threads=1024, quads_per_lane=2, hub_vertices=0, fused_epilogue=0, ranges=1):
     t = pr_tuning(int(threads), int(quads_per_lane), int(hub_vertices), int(fused_epilogue), int(ranges), 0, 0.0, 0)
     _check(load().pr_set_tuning(h, ctypes.byref(t)), h)
 
@@ -552,7 +552,7 @@ class Graph:
     def tuning(self) -> Tuning:
         return pr_get_tuning(self._h)
 
-    def set_tuning(self, threads=256, quads_per_lane=4, hub_vertices=0, fused_epilogue=0, ranges=1):
+    def set_tuning(self, threads=1024, quads_per_lane=2, hub_vertices=0, fused_epilogue=0, ranges=1):
         pr_set_tuning(self._h, threads, quads_per_lane, hub_vertices, fused_epilogue, ranges)
 
 

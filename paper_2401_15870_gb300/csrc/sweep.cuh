@@ -91,10 +91,11 @@ cudaError_t launch_sweep(int mode, const SweepParams& p, cudaStream_t s);
 // vertices whose out-degree is at least that of vertex hub - 1), and whether
 // the epilogue runs inside the gather kernel (k_sweep_rows) or as a second
 // launch (k_finish_full / k_finish_pull), and in how many vertex ranges the
-// sweep runs.  The defaults are the configuration used before any tuning.
+// sweep runs.  The defaults are the setting the tuner picks for DF-P on
+// R-MAT scale 25 (the pull gather in 32 registers, 64 warps per SM).
 struct GatherCfg {
-  int32_t threads = 256;
-  int32_t qpt = SW_QPT;
+  int32_t threads = 1024;
+  int32_t qpt = 2;
   int32_t hub = 0;
   int32_t fused = 0;
   int32_t parts = 1;   // vertex ranges whose epilogue overlaps the next range's gather (1, 2, 4, 8)
