@@ -298,25 +298,27 @@ pr_status pr_group_update_members(pr_group* grp, pr_method method, double alpha,
 void pr_group_destroy(pr_group* grp);
 
 /*
- * Unit sizes of the group kernels: a gather unit is one warp step over 32 x
- * quads_per_lane in-CSR quads (2, 4 or 8), an epilogue unit is
- * chunks_per_unit 32-vertex chunks (1, 2 or 4) whose loads a warp issues
- * together.  Smaller units spread small graphs over more warps; larger ones
- * keep more loads in flight per warp.  Defaults 4 / 4.  The setting changes no
+ * Unit sizes of the group kernels: a gather unit is steps_per_unit warp steps,
+ * each over 32 x quads_per_lane in-CSR quads ((quads, steps) one of (2, 1),
+ * (4, 1), (8, 1), (2, 4)), an epilogue unit is chunks_per_unit 32-vertex chunks
+ * (1, 2 or 4) whose loads a warp issues together.  Smaller units spread small
+ * graphs over more warps; larger ones keep more loads in flight per warp or
+ * look the graph up less often.  Defaults 4 / 1 / 4.  The setting changes no
  * result (the sums are exact).
  * pr_group_autotune: runs reps (0: 1) group updates of the method per
- *   candidate (the device loop, CUDA-event time of the whole update), every
+ *   candidate (12 settings; the device loop, CUDA-event time of the whole update), every
  *   graph starting from its ranks on entry (with its last batch for DF / DF-P),
  *   keeps the fastest, and puts the ranks on entry back at the end (a graph
  *   without ranks keeps those of the last Static trial).  Dynamic methods need
  *   ranks on every graph (PR_ENORANKS).  Errors: PR_EINVAL (Dynamic
  *   Traversal, bad alpha / tau / reps, an update in flight), PR_ENORANKS,
  *   PR_ENOMEM, PR_ECUDA.
- * pr_group_set_tuning: quads_per_lane and chunks_per_unit (the other fields
- *   are ignored); other values give PR_EINVAL and no change.
+ * pr_group_set_tuning: quads_per_lane, steps_per_unit and chunks_per_unit (the
+ *   other fields are ignored); other values give PR_EINVAL and no change.
  */
 typedef struct {
   int32_t quads_per_lane;
+  int32_t steps_per_unit;
   int32_t chunks_per_unit;
   float ms_update;          /* pr_group_autotune: the chosen setting's update time, ms */
   int32_t candidates;       /* pr_group_autotune: settings timed                      */

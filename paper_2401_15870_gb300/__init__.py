@@ -63,13 +63,14 @@ class Tuning:
 
 
 class pr_group_tuning(ctypes.Structure):
-    _fields_ = [("quads_per_lane", ctypes.c_int32), ("chunks_per_unit", ctypes.c_int32), ("ms_update", ctypes.c_float),
-                ("candidates", ctypes.c_int32)]
+    _fields_ = [("quads_per_lane", ctypes.c_int32), ("steps_per_unit", ctypes.c_int32),
+                ("chunks_per_unit", ctypes.c_int32), ("ms_update", ctypes.c_float), ("candidates", ctypes.c_int32)]
 
 
 @dataclass
 class GroupTuning:
     quads_per_lane: int
+    steps_per_unit: int
     chunks_per_unit: int
     ms_update: float
     candidates: int
@@ -459,8 +460,8 @@ def pr_group_get_tuning(q):
     return _group_tuning(t)
 
 
-def pr_group_set_tuning(q, quads_per_lane=4, chunks_per_unit=4):
-    t = pr_group_tuning(int(quads_per_lane), int(chunks_per_unit), 0.0, 0)
+def pr_group_set_tuning(q, quads_per_lane=4, chunks_per_unit=4, steps_per_unit=1):
+    t = pr_group_tuning(int(quads_per_lane), int(steps_per_unit), int(chunks_per_unit), 0.0, 0)
     _check(load().pr_group_set_tuning(q, ctypes.byref(t)))
 
 
@@ -575,8 +576,8 @@ class Group:
     def tuning(self) -> GroupTuning:
         return pr_group_get_tuning(self._q)
 
-    def set_tuning(self, quads_per_lane=4, chunks_per_unit=4):
-        pr_group_set_tuning(self._q, quads_per_lane, chunks_per_unit)
+    def set_tuning(self, quads_per_lane=4, chunks_per_unit=4, steps_per_unit=1):
+        pr_group_set_tuning(self._q, quads_per_lane, chunks_per_unit, steps_per_unit)
 
     def close(self):
         if self._q:

@@ -35,9 +35,12 @@ using namespace dfpr;
 namespace {
 
 constexpr int GR_THREADS = 256;
-// the unit sizes a group can be set to: quads per lane of a gather unit (one
-// warp step of 32 x QPT quads) and 32-vertex chunks of an epilogue unit
-constexpr int GR_QPT[3] = {2, 4, 8};
+// the unit sizes a group can be set to: quads per lane of a gather warp step
+// (32 x QPT quads) and warp steps per gather unit, and 32-vertex chunks of an
+// epilogue unit
+constexpr int GR_QPT[4] = {2, 4, 8, 2};
+constexpr int GR_STEPS[4] = {1, 1, 1, 4};   // warp steps per gather unit (same graph, looked up once)
+constexpr int GR_NQ = 4;
 constexpr int GR_FU[3] = {1, 2, 4};
 
 // per graph, fixed during one update
@@ -171,8 +174,9 @@ __global__ void __launch_bounds__(GR_THREADS) k_g_mark(const GRun* __restrict__ 
   }
 }
 
-// gather phase of one iteration, every live graph (units of 32 x QPT quads)
-template <int QPT>
+// gather phase of one iteration, every live graph (units of STEPS x 32 x QPT
+// quads: STEPS warp steps on one graph per lookup of the graph)
+template <int QPT, int STEPS>
 __global__ void __launch_bounds__(GR_THREADS) k_g_gather(const GRun* __restrict__ run, const GDesc* __restrict__ desc,
                                                          const GState* __restrict__ st) {
   __shared__ int64_t pre[PR_GROUP_MAX + 1];
@@ -187,8 +191,14 @@ __global__ void __launch_bounds__(GR_THREADS) k_g_gather(const GRun* __restrict_
     if (st[g].done) continue;
     const GDesc& d = desc[g];
     const int c = st[g].cur;
-    gather_step<true, QPT>(d.icol, d.C[c], d.X[c], d.S[c], d.rowbits, d.rowbase, d.nquads, d.n, d.acc, d.anyb,
-                           (u - pre[g]) * (32 * QPT), pol_stream, pol_keep);
+    const int64_t ub = (u - pre[g]) * (STEPS * 32 * QPT);
+#pragma unroll 1
+    for (int k = 0; k < STEPS; k++) {
+      const int64_t base = ub + k * (32 * QPT);
+      if (base >= d.nquads) break;
+      gather_step<true, QPT>(d.icol, d.C[c], d.X[c], d.S[c], d.rowbits, d.rowbase, d.nquads, d.n, d.acc, d.anyb, base,
+                             pol_stream, pol_keep);
+    }
   }
 }
 
@@ -330,7 +340,7 @@ struct pr_group {
   GDesc* h_desc = nullptr;
   GState* h_state = nullptr;
   int64_t* h_pre = nullptr;
-  // unit sizes (indices into GR_QPT / GR_FU), set by pr_group_set_tuning or
+  // unit sizes (indices into GR_QPT and GR_STEPS / GR_FU), set by pr_group_set_tuning or
   // pr_group_autotune
   int qi = 1, fi = 2;
   float tune_ms = 0.f;
@@ -383,9 +393,10 @@ static cudaError_t add_kernel(cudaGraph_t graph, cudaGraphNode_t* node, const cu
 
 static const void* gather_fn(int qi) {
   switch (qi) {
-    case 0: return (const void*)k_g_gather<2>;
-    case 1: return (const void*)k_g_gather<4>;
-    default: return (const void*)k_g_gather<8>;
+    case 0: return (const void*)k_g_gather<2, 1>;
+    case 1: return (const void*)k_g_gather<4, 1>;
+    case 2: return (const void*)k_g_gather<8, 1>;
+    default: return (const void*)k_g_gather<2, 4>;
   }
 }
 
@@ -607,7 +618,7 @@ pr_status group_launch(pr_group* q, pr_method method, double alpha, double tau, 
     d.n = g->n;
     d.id_bits = g->id_bits;
     d.C0 = (1.0 - alpha) / (double)g->n;
-    wpre[i + 1] = wpre[i] + cdiv(d.nquads, 32 * GR_QPT[q->qi]);
+    wpre[i + 1] = wpre[i] + cdiv(d.nquads, 32 * GR_QPT[q->qi] * GR_STEPS[q->qi]);
     fpre[i + 1] = fpre[i] + cdiv(cdiv((int64_t)g->n, 32), GR_FU[q->fi]);
     bpre[i + 1] = bpre[i] + cdiv((int64_t)g->n, 32);
     dpre[i + 1] = dpre[i] + ((method == PR_DF || method == PR_DFP) ? g->n_dmin + g->n_dplus : 0);
@@ -739,6 +750,7 @@ extern "C" {
 pr_status pr_group_get_tuning(const pr_group* q, pr_group_tuning* out) {
   if (!q || !out) return PR_EINVAL;
   out->quads_per_lane = GR_QPT[q->qi];
+  out->steps_per_unit = GR_STEPS[q->qi];
   out->chunks_per_unit = GR_FU[q->fi];
   out->ms_update = q->tune_ms;
   out->candidates = q->tune_trials;
@@ -748,10 +760,10 @@ pr_status pr_group_get_tuning(const pr_group* q, pr_group_tuning* out) {
 pr_status pr_group_set_tuning(pr_group* q, const pr_group_tuning* in) {
   if (!q || !in || q->in_flight) return PR_EINVAL;
   int qi = -1, fi = -1;
-  for (int i = 0; i < 3; i++) {
-    if (GR_QPT[i] == in->quads_per_lane) qi = i;
+  for (int i = 0; i < GR_NQ; i++)
+    if (GR_QPT[i] == in->quads_per_lane && GR_STEPS[i] == in->steps_per_unit) qi = i;
+  for (int i = 0; i < 3; i++)
     if (GR_FU[i] == in->chunks_per_unit) fi = i;
-  }
   if (qi < 0 || fi < 0) return PR_EINVAL;
   q->qi = qi;
   q->fi = fi;
@@ -796,7 +808,7 @@ pr_status pr_group_autotune(pr_group* q, pr_method method, double alpha, double 
   int bq = qi0, bf = fi0, trials = 0;
   float best = -1.f;
   std::vector<pr_stats> stats(G);
-  for (int qi = 0; qi < 3 && st == PR_OK; qi++)
+  for (int qi = 0; qi < GR_NQ && st == PR_OK; qi++)
     for (int fi = 0; fi < 3 && st == PR_OK; fi++) {
       q->qi = qi;
       q->fi = fi;

@@ -184,17 +184,19 @@ def test_group_errors(lib):
 
 @pytest.mark.parametrize("method", ["dfp", "df", "nd"])
 def test_every_unit_size_gives_the_same_bits(lib, cases, method):
-    """Gather units of 32 x 2/4/8 quads and epilogue units of 1/2/4 chunks
-    change only how the group's work is cut: ranks and statistics are
-    bit-identical across all nine settings (and to the oracle within 1e-9)."""
+    """Gather units of 32 x 2/4/8 quads (or four steps of 32 x 2) and epilogue
+    units of 1/2/4 chunks change only how the group's work is cut: ranks and
+    statistics are bit-identical across all twelve settings (and to the oracle
+    within 1e-9)."""
     graphs = [c[0] for c in cases]
     grp = lib.Group(graphs)
     try:
         out = []
-        for q in (2, 4, 8):
+        for q, k in ((2, 1), (4, 1), (8, 1), (2, 4)):
             for f in (1, 2, 4):
-                grp.set_tuning(q, f)
-                assert (grp.tuning().quads_per_lane, grp.tuning().chunks_per_unit) == (q, f)
+                grp.set_tuning(q, f, k)
+                tu = grp.tuning()
+                assert (tu.quads_per_lane, tu.steps_per_unit, tu.chunks_per_unit) == (q, k, f)
                 for G, O, r0 in cases:
                     G.set_ranks(r0)
                 for loop in ("device", "host"):
@@ -220,7 +222,7 @@ def test_group_autotune_keeps_the_ranks(lib, cases):
     grp = lib.Group(graphs)
     try:
         tu = grp.autotune("dfp")
-        assert tu.candidates == 9 and tu.ms_update > 0
+        assert tu.candidates == 12 and tu.ms_update > 0
         assert tu.quads_per_lane in (2, 4, 8) and tu.chunks_per_unit in (1, 2, 4)
         assert grp.tuning() == tu
         for G, O, r0 in cases:
@@ -229,7 +231,7 @@ def test_group_autotune_keeps_the_ranks(lib, cases):
         for (G, O, r0), s in zip(cases, st):
             ref, _ = O.update("dfp", r_prev=r0)
             assert np.max(np.abs(G.ranks() - ref)) < TOL
-        for bad in ((3, 4), (4, 3), (16, 4), (4, 8)):
+        for bad in ((3, 4, 1), (4, 3, 1), (16, 4, 1), (4, 8, 1), (4, 4, 4), (8, 4, 2)):
             with pytest.raises(lib.PRError):
                 grp.set_tuning(*bad)
         assert grp.tuning() == tu
