@@ -454,6 +454,16 @@ pr_status pr_autotune(pr_graph* g, pr_method method, double alpha, double tau, i
 pr_status pr_get_tuning(const pr_graph* g, pr_tuning* out);
 pr_status pr_set_tuning(pr_graph* g, const pr_tuning* in);
 
+/*
+ * Testing aid for failure handling (the paper has no counterpart): the k-th
+ * device memory allocation the library makes from now on (k >= 1, counted
+ * over all graphs, groups and servers of the process) fails as if the device
+ * were out of memory, so callers can test their handling of PR_ENOMEM without
+ * exhausting a real GPU.  k = 0 disarms.  Nothing is launched or faulted on
+ * the device.
+ */
+void pr_debug_fail_alloc(int64_t k);
+
 /* Number of CUDA kernels this library has launched in this process so far
  * (all graphs); the difference across a region counts its launches. */
 unsigned long long pr_kernel_launches(void);

@@ -138,6 +138,7 @@ def load():
         "pr_server_clock": ([], f64),
         "pr_server_destroy": ([_P], None),
         "pr_autotune": ([_P, ctypes.c_int, f64, f64, i32, _P], ctypes.c_int),
+        "pr_debug_fail_alloc": ([i64], None),
         "pr_get_tuning": ([_P, _P], ctypes.c_int),
         "pr_set_tuning": ([_P, _P], ctypes.c_int),
         "pr_group_autotune": ([_P, ctypes.c_int, f64, f64, i32, _P], ctypes.c_int),
@@ -465,6 +466,11 @@ def pr_group_set_tuning(q, quads_per_lane=4, chunks_per_unit=4, steps_per_unit=1
     _check(load().pr_group_set_tuning(q, ctypes.byref(t)))
 
 
+def pr_debug_fail_alloc(k):
+    """Make the k-th device allocation of the library from now fail (0: disarm)."""
+    load().pr_debug_fail_alloc(int(k))
+
+
 def pr_kernel_launches() -> int:
     return int(load().pr_kernel_launches())
 
@@ -546,6 +552,31 @@ class Graph:
 
     def dt_affected(self):
         return pr_affected(self._h, 1)
+
+    def save(self, path):
+        """Checkpoint: the out-CSR (user ids, sorted rows, self-loops included),
+        the ranks (if any) and the sweep setting, as one .npz file.  Graph.load
+        rebuilds an equivalent graph: the same edge set and ranks, so every
+        later update gives the same results as on this graph."""
+        off, adj = self.out_csr()
+        tu = self.tuning()
+        extra = {}
+        try:
+            extra["ranks"] = self.ranks()
+        except PRError:
+            pass
+        np.savez(path, off=off, adj=adj, tuning=np.array([tu.threads, tu.quads_per_lane, tu.hub_vertices,
+                                                          tu.fused_epilogue, tu.ranges], np.int32), **extra)
+
+    @classmethod
+    def load(cls, path, stream=None):
+        with np.load(path) as z:
+            off, adj = z["off"], z["adj"]
+            g = cls.from_csr(len(off) - 1, off, adj, stream)
+            g.set_tuning(*[int(x) for x in z["tuning"]])
+            if "ranks" in z:
+                g.set_ranks(z["ranks"])
+        return g
 
     def autotune(self, method="nd", alpha=0.85, tau=1e-10, reps=0) -> Tuning:
         return pr_autotune(self._h, method, alpha, tau, reps)

@@ -9,6 +9,7 @@
 #include <cstring>
 #include <new>
 #include <vector>
+#include <nvtx3/nvToolsExt.h>
 #include "dfpr.h"
 #include "batch.cuh"
 #include "frontier.cuh"
@@ -45,7 +46,7 @@ constexpr double HOT_L2_FRACTION = 0.5;
 template <typename T>
 struct DevBuf {
   T* p = nullptr;
-  cudaError_t alloc(int64_t count) { return cudaMalloc((void**)&p, sizeof(T) * (size_t)(count > 0 ? count : 1)); }
+  cudaError_t alloc(int64_t count) { return dev_malloc((void**)&p, sizeof(T) * (size_t)(count > 0 ? count : 1)); }
   ~DevBuf() {
     if (p) cudaFree(p);
   }
@@ -628,12 +629,12 @@ static pr_status create_from_keys_host_edges(int32_t n, int64_t m, const int32_t
   int32_t *ds = nullptr, *dd = nullptr;
   pr_status st = PR_OK;
   do {
-    cudaError_t e = cudaMalloc(&keys, sizeof(uint64_t) * (size_t)(m + n));
+    cudaError_t e = dev_malloc(&keys, sizeof(uint64_t) * (size_t)(m + n));
     if (e != cudaSuccess) { st = (pr_status)cuda_fail(g, e, "cudaMalloc(keys)"); break; }
     const int32_t *s_dev = src, *d_dev = dst;
     if (!dev_ptrs && m > 0) {
-      if ((e = cudaMalloc(&ds, sizeof(int32_t) * m)) != cudaSuccess ||
-          (e = cudaMalloc(&dd, sizeof(int32_t) * m)) != cudaSuccess ||
+      if ((e = dev_malloc(&ds, sizeof(int32_t) * m)) != cudaSuccess ||
+          (e = dev_malloc(&dd, sizeof(int32_t) * m)) != cudaSuccess ||
           (e = cudaMemcpyAsync(ds, src, sizeof(int32_t) * m, cudaMemcpyHostToDevice, g->stream)) != cudaSuccess ||
           (e = cudaMemcpyAsync(dd, dst, sizeof(int32_t) * m, cudaMemcpyHostToDevice, g->stream)) != cudaSuccess) {
         st = (pr_status)cuda_fail(g, e, "copy edge list");
@@ -644,7 +645,7 @@ static pr_status create_from_keys_host_edges(int32_t n, int64_t m, const int32_t
     }
     if (dev_ptrs && m > 0) {
       unsigned long long* bad;
-      if ((e = cudaMalloc(&bad, sizeof(*bad))) != cudaSuccess) { st = (pr_status)cuda_fail(g, e, "cudaMalloc"); break; }
+      if ((e = dev_malloc(&bad, sizeof(*bad))) != cudaSuccess) { st = (pr_status)cuda_fail(g, e, "cudaMalloc"); break; }
       cudaMemsetAsync(bad, 0, sizeof(*bad), g->stream);
       note_launch(); k_validate_ids<<<grid_for(m, 256), 256, 0, g->stream>>>(src, m, n, bad);
       note_launch(); k_validate_ids<<<grid_for(m, 256), 256, 0, g->stream>>>(dst, m, n, bad);
@@ -703,9 +704,9 @@ pr_status pr_graph_create(int32_t n, int64_t m, const int64_t* row_off, const in
   int32_t* dcol = nullptr;
   pr_status st = PR_OK;
   cudaError_t e;
-  if ((e = cudaMalloc(&keys, sizeof(uint64_t) * (size_t)(m + n))) != cudaSuccess ||
-      (e = cudaMalloc(&doff, sizeof(int64_t) * (size_t)(n + 1))) != cudaSuccess ||
-      (e = cudaMalloc(&dcol, sizeof(int32_t) * (size_t)(m > 0 ? m : 1))) != cudaSuccess ||
+  if ((e = dev_malloc(&keys, sizeof(uint64_t) * (size_t)(m + n))) != cudaSuccess ||
+      (e = dev_malloc(&doff, sizeof(int64_t) * (size_t)(n + 1))) != cudaSuccess ||
+      (e = dev_malloc(&dcol, sizeof(int32_t) * (size_t)(m > 0 ? m : 1))) != cudaSuccess ||
       (e = cudaMemcpyAsync(doff, row_off, sizeof(int64_t) * (n + 1), cudaMemcpyHostToDevice, g->stream)) != cudaSuccess ||
       (m > 0 && (e = cudaMemcpyAsync(dcol, col, sizeof(int32_t) * m, cudaMemcpyHostToDevice, g->stream)) != cudaSuccess)) {
     st = (pr_status)cuda_fail(g, e, "pr_graph_create copy");
@@ -784,18 +785,27 @@ static pr_status apply_common(pr_graph* h, const int32_t* ds, const int32_t* dd,
   return PR_OK;
 }
 
+// NVTX ranges name the library's phases for profilers (no cost without one)
+struct NvtxRange {
+  explicit NvtxRange(const char* name) { nvtxRangePushA(name); }
+  ~NvtxRange() { nvtxRangePop(); }
+};
+
 pr_status pr_apply_batch(pr_graph* h, const int32_t* del_src, const int32_t* del_dst, int64_t n_del,
                          const int32_t* ins_src, const int32_t* ins_dst, int64_t n_ins) {
+  NvtxRange r("pr_apply_batch");
   return apply_common(h, del_src, del_dst, n_del, ins_src, ins_dst, n_ins, false);
 }
 
 pr_status pr_apply_batch_device(pr_graph* h, const int32_t* del_src, const int32_t* del_dst, int64_t n_del,
                                 const int32_t* ins_src, const int32_t* ins_dst, int64_t n_ins) {
+  NvtxRange r("pr_apply_batch_device");
   return apply_common(h, del_src, del_dst, n_del, ins_src, ins_dst, n_ins, true);
 }
 
 pr_status pr_update(pr_graph* h, pr_method method, double alpha, double tau, const pr_options* opts,
                     pr_stats* stats) {
+  NvtxRange r("pr_update");
   if (!h) return PR_EINVAL;
   Graph* g = &h->g;
   g->err.clear();
@@ -1017,6 +1027,8 @@ pr_status pr_affected(pr_graph* h, int32_t which, uint8_t* flags) {
 unsigned long long pr_kernel_launches(void) { return launches_so_far(); }
 
 const char* pr_last_error(const pr_graph* h) { return h ? h->g.err.c_str() : ""; }
+
+void pr_debug_fail_alloc(int64_t k) { arm_alloc_failure(k); }
 
 const char* pr_status_string(pr_status s) {
   switch (s) {

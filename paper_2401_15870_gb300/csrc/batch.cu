@@ -473,14 +473,14 @@ static int repack_direction(Graph* g, Csr* c, const uint64_t* dl, int64_t nd, co
   // rows above REPACK_HUB, each holding more than REPACK_HUB of the old edges
   const int64_t hub_cap = std::min<int64_t>(n, c->cap / REPACK_HUB + 1);
   cudaError_t e;
-  if ((e = cudaMalloc(&ndeg, sizeof(int32_t) * n)) != cudaSuccess ||
-      (e = cudaMalloc(&cap, sizeof(int64_t) * (n + 1))) != cudaSuccess ||
-      (e = cudaMalloc(&noff, sizeof(int64_t) * (n + 1))) != cudaSuccess ||
-      (e = cudaMalloc(&scr, sizeof(int64_t) * scan_tmp_elems(n))) != cudaSuccess ||
-      (e = cudaMalloc(&dstart, sizeof(int64_t) * (n + 1))) != cudaSuccess ||
-      (e = cudaMalloc(&istart, sizeof(int64_t) * (n + 1))) != cudaSuccess ||
-      (e = cudaMalloc(&hubs, sizeof(int32_t) * hub_cap)) != cudaSuccess ||
-      (e = cudaMalloc(&hinfo, sizeof(int32_t) * 2)) != cudaSuccess ||
+  if ((e = dev_malloc(&ndeg, sizeof(int32_t) * n)) != cudaSuccess ||
+      (e = dev_malloc(&cap, sizeof(int64_t) * (n + 1))) != cudaSuccess ||
+      (e = dev_malloc(&noff, sizeof(int64_t) * (n + 1))) != cudaSuccess ||
+      (e = dev_malloc(&scr, sizeof(int64_t) * scan_tmp_elems(n))) != cudaSuccess ||
+      (e = dev_malloc(&dstart, sizeof(int64_t) * (n + 1))) != cudaSuccess ||
+      (e = dev_malloc(&istart, sizeof(int64_t) * (n + 1))) != cudaSuccess ||
+      (e = dev_malloc(&hubs, sizeof(int32_t) * hub_cap)) != cudaSuccess ||
+      (e = dev_malloc(&hinfo, sizeof(int32_t) * 2)) != cudaSuccess ||
       (e = cudaMemsetAsync(hinfo, 0, sizeof(int32_t) * 2, s)) != cudaSuccess) {
     release();
     return cuda_fail(g, e, "cudaMalloc(repack)");
@@ -494,7 +494,7 @@ static int repack_direction(Graph* g, Csr* c, const uint64_t* dl, int64_t nd, co
   if (e == cudaSuccess) e = cudaMemcpyAsync(hinfo_h, hinfo, sizeof(hinfo_h), cudaMemcpyDeviceToHost, s);
   if (e == cudaSuccess) e = cudaStreamSynchronize(s);
   if (e == cudaSuccess && (hinfo_h[0] < 0 || hinfo_h[0] > hub_cap || hinfo_h[0] > 65535)) e = cudaErrorUnknown;
-  if (e == cudaSuccess) e = cudaMalloc(&ncol, sizeof(int32_t) * (size_t)total);
+  if (e == cudaSuccess) e = dev_malloc(&ncol, sizeof(int32_t) * (size_t)total);
   if (e != cudaSuccess) {
     release();
     return cuda_fail(g, e, "repack");
@@ -964,14 +964,14 @@ static int apply_small(Graph* g, const int32_t* ds, const int32_t* dd, int64_t n
     if (g->dmin) cudaFree(g->dmin);
     g->dmin = nullptr;
     g->cap_dmin = 0;
-    TRY(cudaMalloc(&g->dmin, sizeof(uint64_t) * (a + 1)));
+    TRY(dev_malloc(&g->dmin, sizeof(uint64_t) * (a + 1)));
     g->cap_dmin = a;
   }
   if (g->cap_dplus < b) {
     if (g->dplus) cudaFree(g->dplus);
     g->dplus = nullptr;
     g->cap_dplus = 0;
-    TRY(cudaMalloc(&g->dplus, sizeof(uint64_t) * (b + 1)));
+    TRY(dev_malloc(&g->dplus, sizeof(uint64_t) * (b + 1)));
     g->cap_dplus = b;
   }
   if (a) TRY(cudaMemcpyAsync(g->dmin, B->edl, sizeof(uint64_t) * a, cudaMemcpyDeviceToDevice, s));
@@ -1051,14 +1051,14 @@ int apply_batch_device(Graph* g, const int32_t* ds, const int32_t* dd, int64_t n
     if (g->dmin) cudaFree(g->dmin);
     g->dmin = nullptr;
     g->cap_dmin = 0;
-    TRY(cudaMalloc(&g->dmin, sizeof(uint64_t) * (nd + 1)));
+    TRY(dev_malloc(&g->dmin, sizeof(uint64_t) * (nd + 1)));
     g->cap_dmin = nd;
   }
   if (g->cap_dplus < ni) {
     if (g->dplus) cudaFree(g->dplus);
     g->dplus = nullptr;
     g->cap_dplus = 0;
-    TRY(cudaMalloc(&g->dplus, sizeof(uint64_t) * (ni + 1)));
+    TRY(dev_malloc(&g->dplus, sizeof(uint64_t) * (ni + 1)));
     g->cap_dplus = ni;
   }
   if (nd) {

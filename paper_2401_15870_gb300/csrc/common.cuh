@@ -18,6 +18,16 @@
 
 namespace dfpr {
 
+// Device allocations of the library go through dev_malloc so that a test can
+// make the k-th one fail as if the device were out of memory
+// (pr_debug_fail_alloc), with no fault on the GPU.
+cudaError_t dev_malloc_raw(void** p, size_t bytes);
+void arm_alloc_failure(long long k);
+template <class T>
+inline cudaError_t dev_malloc(T** p, size_t bytes) {
+  return dev_malloc_raw(reinterpret_cast<void**>(p), bytes);
+}
+
 // process-wide count of kernel launches made by this library (pr_kernel_launches)
 void note_launch();
 void note_launches(unsigned long long k);   // kernels run by a CUDA graph launch

@@ -30,7 +30,7 @@ int cuda_fail(Graph* g, cudaError_t e, const char* where) {
 }
 
 cudaError_t dalloc(Graph* g, void** p, size_t bytes) {
-  cudaError_t e = cudaMalloc(p, bytes > 0 ? bytes : 16);
+  cudaError_t e = dev_malloc(p, bytes > 0 ? bytes : 16);
   if (e == cudaSuccess) g->allocs.push_back(*p);
   return e;
 }
@@ -55,7 +55,7 @@ cudaError_t scratch_get(Graph* g, int slot, size_t bytes, void** out) {
       s.bytes = 0;
     }
     size_t want = bytes + bytes / 4 + 256;
-    cudaError_t e = cudaMalloc(&s.p, want);
+    cudaError_t e = dev_malloc(&s.p, want);
     if (e != cudaSuccess) return e;
     s.bytes = want;
   }
@@ -145,7 +145,7 @@ struct Tmp {
   }
   template <typename T>
   cudaError_t get(T** p, size_t elems) {
-    cudaError_t e = cudaMalloc((void**)p, sizeof(T) * (elems > 0 ? elems : 1));
+    cudaError_t e = dev_malloc((void**)p, sizeof(T) * (elems > 0 ? elems : 1));
     if (e == cudaSuccess) ptrs.push_back(*p);
     return e;
   }
@@ -206,7 +206,7 @@ int refresh_full_tiles(Graph* g) {
   TRY(dalloc(g, (void**)&g->rowbase, sizeof(int32_t) * (words + 1)));
   {
     int32_t* tmp;
-    TRY(cudaMalloc(&tmp, sizeof(int32_t) * scan_tmp_elems(words)));
+    TRY(dev_malloc(&tmp, sizeof(int32_t) * scan_tmp_elems(words)));
     cudaError_t e = launch_row_start_index(g->in.off, g->n, quads, g->rowbits, g->rowbase, tmp, g->stream);
     cudaStreamSynchronize(g->stream);
     cudaFree(tmp);

@@ -496,12 +496,12 @@ pr_status pr_group_create(int32_t count, pr_graph* const* graphs, void* stream, 
   q->dev = dev;
   q->stream = (cudaStream_t)stream;
   const size_t pre_elems = 4 * (size_t)(count + 1);
-  bool ok = cudaMalloc((void**)&q->d_run, sizeof(GRun)) == cudaSuccess &&
-            cudaMalloc((void**)&q->d_desc, sizeof(GDesc) * count) == cudaSuccess &&
-            cudaMalloc((void**)&q->d_state, sizeof(GState) * count) == cudaSuccess &&
-            cudaMalloc((void**)&q->d_pre, sizeof(int64_t) * pre_elems) == cudaSuccess &&
-            cudaMalloc((void**)&q->tab_sc, sizeof(double) * TAB) == cudaSuccess &&
-            cudaMalloc((void**)&q->tab_cl, sizeof(double) * TAB) == cudaSuccess &&
+  bool ok = dev_malloc((void**)&q->d_run, sizeof(GRun)) == cudaSuccess &&
+            dev_malloc((void**)&q->d_desc, sizeof(GDesc) * count) == cudaSuccess &&
+            dev_malloc((void**)&q->d_state, sizeof(GState) * count) == cudaSuccess &&
+            dev_malloc((void**)&q->d_pre, sizeof(int64_t) * pre_elems) == cudaSuccess &&
+            dev_malloc((void**)&q->tab_sc, sizeof(double) * TAB) == cudaSuccess &&
+            dev_malloc((void**)&q->tab_cl, sizeof(double) * TAB) == cudaSuccess &&
             cudaMallocHost((void**)&q->h_run, sizeof(GRun)) == cudaSuccess &&
             cudaMallocHost((void**)&q->h_desc, sizeof(GDesc) * count) == cudaSuccess &&
             cudaMallocHost((void**)&q->h_state, sizeof(GState) * count) == cudaSuccess &&
@@ -786,7 +786,7 @@ pr_status pr_group_autotune(pr_group* q, pr_method method, double alpha, double 
   std::vector<int64_t> off(G + 1, 0);
   for (int i = 0; i < G; i++) off[i + 1] = off[i] + (q->graphs[i]->g.has_ranks ? q->graphs[i]->g.n : 0);
   double* saved = nullptr;
-  if (off[G] > 0 && cudaMalloc((void**)&saved, sizeof(double) * (size_t)off[G]) != cudaSuccess) {
+  if (off[G] > 0 && dev_malloc((void**)&saved, sizeof(double) * (size_t)off[G]) != cudaSuccess) {
     cudaGetLastError();
     return PR_ENOMEM;
   }

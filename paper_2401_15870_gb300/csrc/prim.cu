@@ -9,6 +9,19 @@ void note_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
 void note_launches(unsigned long long k) { g_launches.fetch_add(k, std::memory_order_relaxed); }
 unsigned long long launches_so_far() { return g_launches.load(std::memory_order_relaxed); }
 
+// allocations until the injected failure (0: none armed)
+static std::atomic<long long> g_fail_in{0};
+
+void arm_alloc_failure(long long k) { g_fail_in.store(k > 0 ? k : 0); }
+
+cudaError_t dev_malloc_raw(void** p, size_t bytes) {
+  if (g_fail_in.load(std::memory_order_relaxed) > 0 && g_fail_in.fetch_sub(1) == 1) {
+    *p = nullptr;
+    return cudaErrorMemoryAllocation;
+  }
+  return cudaMalloc(p, bytes);
+}
+
 static int g_sms = 0;
 
 int num_sms() {

@@ -142,7 +142,7 @@ pr_status tune_updates(pr_graph* h, int method, double alpha, double tau, int32_
   Graph* g = &h->g;
   cudaStream_t s = g->stream;
   double* saved = nullptr;
-  cudaError_t e = cudaMalloc((void**)&saved, sizeof(double) * (size_t)g->n);
+  cudaError_t e = dev_malloc((void**)&saved, sizeof(double) * (size_t)g->n);
   if (e != cudaSuccess) return (pr_status)cuda_fail(g, e, "pr_autotune");
   e = cudaMemcpyAsync(saved, g->R, sizeof(double) * (size_t)g->n, cudaMemcpyDeviceToDevice, s);
   const GatherCfg keep = h->gcfg;
