@@ -21,6 +21,7 @@
 // the threshold tests of non-negative doubles compare their bit patterns as
 // integers, which orders them the same way.
 #pragma once
+#include "fixconv.cuh"
 #include "sweep.cuh"
 
 namespace dfpr {
@@ -215,7 +216,7 @@ __device__ __forceinline__ void finish_pull_step(const P& p, long long* __restri
       t.verts += 1;
       p.R[v] = r;
       const double sc = d[u] < TAB ? p.tab_sc[d[u]] : FIX_ONE / (double)d[u];
-      p.Cnext[v] = __double2ll_rn(r * sc);
+      p.Cnext[v] = fixconv::f64_to_i64_rn(r * sc);   // the FP64 pipe bounds this epilogue
       // Alg. 1: prune when dr / max(r, R[v]) <= tau_p (DF-P), expand when it
       // is > tau_f (or the other measures of Sec. 4.3); compared without the
       // division
