@@ -400,8 +400,7 @@ def run_batched(a, rank, world, local_rank):
         grp.update("dfp", alpha=ALPHA, tau=TAU)
 
     def group_step(i):
-        for G, b in zip(graphs, batches):
-            G.apply_batch_device(*b[i])
+        grp.apply_batches_device([b[i] for b in batches])
         return grp.update("dfp", alpha=ALPHA, tau=TAU, loop=a.group_loop)
 
     def plain_step(i):
@@ -484,6 +483,7 @@ def run_batched(a, rank, world, local_rank):
         "gpu_launches": launches_g,
         "clocks": clk,
         "detail": {
+            "apply": "pr_apply_batches_device: every graph's batch queued before the host waits",
             "group_unit_sizes": dataclasses.asdict(gtune),
             "per_graph_settings": {"threads": sorted(set(t.threads for t in ptune)),
                                    "quads_per_lane": sorted(set(t.quads_per_lane for t in ptune)),

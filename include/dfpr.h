@@ -167,6 +167,26 @@ pr_status pr_apply_batch_device(pr_graph* g, const int32_t* del_src, const int32
                                 const int32_t* ins_src, const int32_t* ins_dst, int64_t n_ins);
 
 /*
+ * The batches of many graphs at once (one per graph, device arrays as in
+ * pr_apply_batch_device; graphs[i] gets del_src[i] .. n_ins[i]).  Each batch
+ * has the effect of pr_apply_batch_device on its graph; the difference is
+ * scheduling: every graph's work is queued before the host waits for any, so
+ * the host round trips of many small batches overlap, and the batches run side
+ * by side on a pool of library streams (each first waits for its graph's
+ * stream, and the graph's stream waits for its end, so work queued on the
+ * graph's stream before and after the call stays ordered with it; graphs of
+ * another device than the current one run on their own stream).  A group
+ * update of the same graphs usually follows (pr_group_update).  The graphs
+ * must be distinct.  The call returns when every batch is applied.
+ * Returns the first error; a graph whose batch failed is left as
+ * pr_apply_batch_device leaves it on that error, the others are applied.
+ * Errors: PR_EINVAL, PR_ERANGE, PR_ENOMEM, PR_ECUDA.
+ */
+pr_status pr_apply_batches_device(int32_t count, pr_graph* const* graphs, const int32_t* const* del_src,
+                                  const int32_t* const* del_dst, const int64_t* n_del, const int32_t* const* ins_src,
+                                  const int32_t* const* ins_dst, const int64_t* n_ins);
+
+/*
  * Update the ranks with one method (Sec. 3.1, 2.3, Alg. 1) after the last
  * batch, iterating until the L-inf change of a sweep is <= tau or
  * opts->max_iter sweeps have run.  alpha in [0, 1) is the damping factor

@@ -139,6 +139,7 @@ def load():
         "pr_server_destroy": ([_P], None),
         "pr_autotune": ([_P, ctypes.c_int, f64, f64, i32, _P], ctypes.c_int),
         "pr_debug_fail_alloc": ([i64], None),
+        "pr_apply_batches_device": ([i32, _P, _P, _P, _P, _P, _P, _P], ctypes.c_int),
         "pr_get_tuning": ([_P, _P], ctypes.c_int),
         "pr_set_tuning": ([_P, _P], ctypes.c_int),
         "pr_group_autotune": ([_P, ctypes.c_int, f64, f64, i32, _P], ctypes.c_int),
@@ -241,6 +242,29 @@ def pr_apply_batch_device(h, del_src=None, del_dst=None, ins_src=None, ins_dst=N
     if nd != nd2 or ni != ni2:
         raise ValueError("endpoint arrays differ in length")
     _check(load().pr_apply_batch_device(h, dsp, ddp, nd, isp, idp, ni), h)
+
+
+def pr_apply_batches_device(handles, batches):
+    """One batch per graph (each (del_src, del_dst, ins_src, ins_dst) device
+    int32 tensors or None), every graph's work queued before the host waits."""
+    k = len(handles)
+    if len(batches) != k:
+        raise ValueError("one batch per graph")
+    P = ctypes.c_void_p
+    ptr = [(P * k)() for _ in range(4)]
+    cnt = [(ctypes.c_int64 * k)() for _ in range(2)]
+    for i, b in enumerate(batches):
+        ds, dd, is_, id_ = b
+        dsp, nd = _dev_ptr(ds, "int32")
+        ddp, nd2 = _dev_ptr(dd, "int32")
+        isp, ni = _dev_ptr(is_, "int32")
+        idp, ni2 = _dev_ptr(id_, "int32")
+        if nd != nd2 or ni != ni2:
+            raise ValueError("endpoint arrays differ in length")
+        ptr[0][i], ptr[1][i], ptr[2][i], ptr[3][i] = dsp, ddp, isp, idp
+        cnt[0][i], cnt[1][i] = nd, ni
+    hs = (P * k)(*handles)
+    _check(load().pr_apply_batches_device(k, hs, ptr[0], ptr[1], cnt[0], ptr[2], ptr[3], cnt[1]))
 
 
 PR_OPT_TIME_SWEEPS, PR_OPT_FORCE_PULL, PR_OPT_FORCE_PUSH = 1, 2, 4
@@ -600,6 +624,10 @@ class Group:
 
     def update_members(self, members, method, **kw):
         return pr_group_update_members(self._q, members, method, **kw)
+
+    def apply_batches_device(self, batches):
+        """One device batch per graph of the group, in group order."""
+        pr_apply_batches_device([g.handle for g in self.graphs], batches)
 
     def autotune(self, method="dfp", alpha=0.85, tau=1e-10, reps=0) -> GroupTuning:
         return pr_group_autotune(self._q, method, alpha, tau, reps)

@@ -7,6 +7,7 @@
 #include <cmath>
 #include <cstdio>
 #include <cstring>
+#include <mutex>
 #include <new>
 #include <vector>
 #include <nvtx3/nvToolsExt.h>
@@ -741,6 +742,8 @@ pr_status pr_set_stream(pr_graph* h, void* stream) {
   return PR_OK;
 }
 
+static pr_status apply_finish(pr_graph* h, bool wait);
+
 static pr_status apply_common(pr_graph* h, const int32_t* ds, const int32_t* dd, int64_t nd, const int32_t* is,
                               const int32_t* id, int64_t ni, bool device) {
   if (!h || nd < 0 || ni < 0 || (nd > 0 && (!ds || !dd)) || (ni > 0 && (!is || !id))) return PR_EINVAL;
@@ -774,10 +777,18 @@ static pr_status apply_common(pr_graph* h, const int32_t* ds, const int32_t* dd,
     rc = apply_batch_device(g, b, b + nd, nd, b + 2 * nd, b + 2 * nd + ni, ni, true);
   }
   if (rc != OK) return (pr_status)rc;
+  return apply_finish(h, true);
+}
+
+// after a batch: the edge count, the tile tables, the end event and (when
+// `wait`) the apply time
+static pr_status apply_finish(pr_graph* h, bool wait) {
+  Graph* g = &h->g;
   g->m += g->n_dplus - g->n_dmin;
   pr_status st = ensure_tiles(h);
   if (st != PR_OK) return st;
-  TRY(cudaEventRecord(h->ev[1], s));
+  TRY(cudaEventRecord(h->ev[1], g->stream));
+  if (!wait) return PR_OK;
   TRY(cudaEventSynchronize(h->ev[1]));
   float ms = 0.f;
   TRY(cudaEventElapsedTime(&ms, h->ev[0], h->ev[1]));
@@ -801,6 +812,123 @@ pr_status pr_apply_batch_device(pr_graph* h, const int32_t* del_src, const int32
                                 const int32_t* ins_src, const int32_t* ins_dst, int64_t n_ins) {
   NvtxRange r("pr_apply_batch_device");
   return apply_common(h, del_src, del_dst, n_del, ins_src, ins_dst, n_ins, true);
+}
+
+// streams on which pr_apply_batches_device runs the graphs' batches side by
+// side: a small batch is a chain of short kernels, one of them a single block,
+// so one graph's chain leaves the GPU nearly idle (made on first use, one set
+// per device, kept for the life of the process)
+constexpr int APPLY_STREAMS = 16;
+
+static cudaError_t apply_streams(int dev, cudaStream_t** out) {
+  static std::mutex mu;
+  static cudaStream_t pool[64][APPLY_STREAMS];
+  static bool made[64] = {false};
+  *out = nullptr;
+  if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
+  std::lock_guard<std::mutex> lock(mu);
+  if (!made[dev]) {
+    for (int i = 0; i < APPLY_STREAMS; i++) {
+      cudaError_t e = cudaStreamCreateWithFlags(&pool[dev][i], cudaStreamNonBlocking);
+      if (e != cudaSuccess) {
+        for (int j = 0; j < i; j++) cudaStreamDestroy(pool[dev][j]);
+        return e;
+      }
+    }
+    made[dev] = true;
+  }
+  *out = pool[dev];
+  return cudaSuccess;
+}
+
+pr_status pr_apply_batches_device(int32_t count, pr_graph* const* graphs, const int32_t* const* del_src,
+                                  const int32_t* const* del_dst, const int64_t* n_del, const int32_t* const* ins_src,
+                                  const int32_t* const* ins_dst, const int64_t* n_ins) {
+  NvtxRange r("pr_apply_batches_device");
+  if (count < 0 || (count > 0 && (!graphs || !n_del || !n_ins || !del_src || !del_dst || !ins_src || !ins_dst)))
+    return PR_EINVAL;
+  for (int32_t i = 0; i < count; i++) {
+    if (!graphs[i] || n_del[i] < 0 || n_ins[i] < 0 || (n_del[i] > 0 && (!del_src[i] || !del_dst[i])) ||
+        (n_ins[i] > 0 && (!ins_src[i] || !ins_dst[i])))
+      return PR_EINVAL;
+    for (int32_t j = 0; j < i; j++)
+      if (graphs[j] == graphs[i]) return PR_EINVAL;
+  }
+  if (count == 0) return PR_OK;
+  // each graph's batch runs on a stream of the pool that first waits for the
+  // graph's own stream (h->ev[0]); the graph's stream waits for the batch's
+  // end (h->ev[1]) before the call returns.  Graphs on another device than the
+  // current one stay on their own stream.
+  int cur = -1;
+  cudaStream_t* pool = nullptr;
+  if (cudaGetDevice(&cur) != cudaSuccess || apply_streams(cur, &pool) != cudaSuccess) pool = nullptr;
+  std::vector<cudaStream_t> home((size_t)count);
+  std::vector<SmallApply> pend((size_t)count);
+  std::vector<char> queued((size_t)count, 0), done((size_t)count, 0);
+  pr_status first = PR_OK;
+  auto fail = [&](pr_status st) {
+    if (first == PR_OK) first = st;
+  };
+  // every graph's work queued first, then each finished: the host waits for
+  // the device once per graph, when its work is already under way
+  for (int32_t i = 0; i < count; i++) {
+    pr_graph* h = graphs[i];
+    Graph* g = &h->g;
+    g->err.clear();
+    home[i] = g->stream;
+    if (cudaEventRecord(h->ev[0], g->stream) != cudaSuccess) {
+      fail((pr_status)cuda_fail(g, cudaGetLastError(), "pr_apply_batches_device"));
+      continue;
+    }
+    if (pool && g->dev == cur) {
+      cudaStream_t aux = pool[i % APPLY_STREAMS];
+      if (cudaStreamWaitEvent(aux, h->ev[0], 0) != cudaSuccess) {
+        fail((pr_status)cuda_fail(g, cudaGetLastError(), "pr_apply_batches_device"));
+        continue;
+      }
+      g->stream = aux;
+    }
+    queued[i] = 1;
+    int rc = apply_batch_launch(g, del_src[i], del_dst[i], n_del[i], ins_src[i], ins_dst[i], n_ins[i], false, &pend[i]);
+    if (rc != OK) {
+      fail((pr_status)rc);
+      continue;
+    }
+    done[i] = 1;
+  }
+  for (int32_t i = 0; i < count; i++) {
+    if (!done[i]) continue;
+    pr_graph* h = graphs[i];
+    int rc = apply_batch_complete(&h->g, &pend[i]);
+    pr_status st = rc == OK ? apply_finish(h, false) : (pr_status)rc;
+    if (st != PR_OK) {
+      done[i] = 0;
+      fail(st);
+    }
+  }
+  // back to each graph's own stream: it waits for everything the batch queued
+  for (int32_t i = 0; i < count; i++) {
+    if (!queued[i]) continue;
+    pr_graph* h = graphs[i];
+    Graph* g = &h->g;
+    if (g->stream != home[i]) {
+      cudaError_t e = done[i] ? cudaSuccess : cudaEventRecord(h->ev[1], g->stream);
+      if (e == cudaSuccess) e = cudaStreamWaitEvent(home[i], h->ev[1], 0);
+      if (e != cudaSuccess) {
+        cudaStreamSynchronize(g->stream);   // the ordering the event could not give
+        fail((pr_status)cuda_fail(g, e, "pr_apply_batches_device"));
+      }
+      g->stream = home[i];
+    }
+  }
+  for (int32_t i = 0; i < count; i++) {
+    if (!done[i]) continue;
+    pr_graph* h = graphs[i];
+    float ms = 0.f;
+    if (cudaEventSynchronize(h->ev[1]) == cudaSuccess && cudaEventElapsedTime(&ms, h->ev[0], h->ev[1]) == cudaSuccess)
+      h->ms_apply = ms;
+  }
+  return first;
 }
 
 pr_status pr_update(pr_graph* h, pr_method method, double alpha, double tau, const pr_options* opts,

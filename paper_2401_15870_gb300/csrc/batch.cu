@@ -922,8 +922,10 @@ static cudaError_t small_staging(Graph* g, int dir, int64_t elems, int32_t** out
   return cudaSuccess;
 }
 
-static int apply_small(Graph* g, const int32_t* ds, const int32_t* dd, int64_t nd, const int32_t* is,
-                       const int32_t* id, int64_t ni) {
+// phase 1 of a small batch: everything up to the status copy to the host,
+// queued on the graph's stream without waiting
+static int small_launch(Graph* g, const int32_t* ds, const int32_t* dd, int64_t nd, const int32_t* is,
+                        const int32_t* id, int64_t ni, SmallApply* A) {
   cudaStream_t s = g->stream;
   const int32_t n = g->n;
   const int64_t nk = nd + ni;
@@ -932,8 +934,8 @@ static int apply_small(Graph* g, const int32_t* ds, const int32_t* dd, int64_t n
   SmallBufs* B = (SmallBufs*)bp;
   if (!g->small_h) TRY(cudaMallocHost(&g->small_h, sizeof(SmallStatus)));
   SmallStatus* h = (SmallStatus*)g->small_h;
-  int32_t* S[2];
-  int64_t cap[2];
+  int32_t** S = A->S;
+  int64_t* cap = A->cap;
   // staging of at least 64K elements per direction; larger rows are handled by growing it
   TRY(small_staging(g, 0, 65536, &S[0], &cap[0]));
   TRY(small_staging(g, 1, 65536, &S[1], &cap[1]));
@@ -956,6 +958,21 @@ static int apply_small(Graph* g, const int32_t* ds, const int32_t* dd, int64_t n
                                                       g->out.deg, g->tab_sc);
   }
   TRY(cudaMemcpyAsync(h, &B->st, sizeof(SmallStatus), cudaMemcpyDeviceToHost, s));
+  A->B = B;
+  A->nk = nk;
+  return OK;
+}
+
+// phase 2: wait for the status, keep the effective change, and finish on the
+// host what the device left (a larger staging buffer, or a repack)
+static int small_complete(Graph* g, SmallApply* A) {
+  cudaStream_t s = g->stream;
+  const int32_t n = g->n;
+  SmallBufs* B = A->B;
+  SmallStatus* h = (SmallStatus*)g->small_h;
+  int32_t** S = A->S;
+  int64_t* cap = A->cap;
+  const int64_t nk = A->nk;
   TRY(cudaStreamSynchronize(s));
   if (h->bad) return set_error(g, ERANGE_, "pr_apply_batch: vertex id out of range");
   const int64_t a = h->n_del, b = h->n_ins;
@@ -1010,13 +1027,30 @@ static int apply_small(Graph* g, const int32_t* ds, const int32_t* dd, int64_t n
   return OK;
 }
 
+int apply_batch_launch(Graph* g, const int32_t* ds, const int32_t* dd, int64_t nd, const int32_t* is,
+                       const int32_t* id, int64_t ni, bool validated, SmallApply* pending) {
+  const int64_t nk = nd + ni;
+  pending->B = nullptr;
+  if (nk > 0 && nk <= SMALL_MAX) return small_launch(g, ds, dd, nd, is, id, ni, pending);
+  return apply_batch_device(g, ds, dd, nd, is, id, ni, validated);
+}
+
+int apply_batch_complete(Graph* g, SmallApply* pending) {
+  if (!pending->B) return OK;
+  return small_complete(g, pending);
+}
+
 int apply_batch_device(Graph* g, const int32_t* ds, const int32_t* dd, int64_t nd, const int32_t* is,
                        const int32_t* id, int64_t ni, bool validated) {
   cudaStream_t s = g->stream;
   int bits = g->id_bits;
   int32_t n = g->n;
   int64_t nk = nd + ni;
-  if (nk > 0 && nk <= SMALL_MAX) return apply_small(g, ds, dd, nd, is, id, ni);
+  if (nk > 0 && nk <= SMALL_MAX) {
+    SmallApply A;
+    const int rc = small_launch(g, ds, dd, nd, is, id, ni, &A);
+    return rc != OK ? rc : small_complete(g, &A);
+  }
   size_t need;
   {
     Carve probe(nullptr);

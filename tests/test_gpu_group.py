@@ -239,3 +239,56 @@ def test_group_autotune_keeps_the_ranks(lib, cases):
             grp.autotune("dt")
     finally:
         grp.close()
+
+
+def test_batches_of_many_graphs_at_once(lib):
+    """pr_apply_batches_device gives every graph the edges, effective change
+    and ranks that pr_apply_batch_device on each graph gives: small and large
+    batches, an empty one, a graph with a repack; a batch with a bad id fails
+    with PR_ERANGE and leaves only its own graph unchanged."""
+    torch = pytest.importorskip("torch")
+    specs = [(10, 8, 40), (12, 16, 3000), (11, 4, 0), (13, 16, 9000), (9, 8, 120)]
+    pairs, batches = [], []
+    for k, (scale, ef, bsize) in enumerate(specs):
+        n = 1 << scale
+        src, dst = synth.rmat(scale, ef * n, 300 + k)
+        A = lib.Graph.from_edges(n, src, dst)
+        B = lib.Graph.from_edges(n, src, dst)
+        for G in (A, B):
+            G.update("static")
+        cs, cd = synth.unique_edges(src, dst)
+        b = synth.batch(n, cs, cd, bsize, 400 + k) if bsize else tuple(np.zeros(0, np.int32) for _ in range(4))
+        if k == 4:   # overflow one row: a repack inside the multi-graph call
+            b = (b[0], b[1], np.concatenate([b[2], np.full(300, 5, np.int32)]),
+                 np.concatenate([b[3], np.arange(300, dtype=np.int32) % n]))
+        pairs.append((A, B))
+        batches.append(tuple(torch.from_numpy(np.ascontiguousarray(x, np.int32)).cuda() for x in b))
+    lib.pr_apply_batches_device([A.handle for A, _ in pairs], batches)
+    for (A, B), b in zip(pairs, batches):
+        B.apply_batch_device(*b)
+        for x, y in ((A.out_csr(), B.out_csr()), (A.in_csr(), B.in_csr())):
+            assert np.array_equal(x[0], y[0]) and np.array_equal(x[1], y[1])
+        da, db = A.effective_delta(), B.effective_delta()
+        assert all(np.array_equal(p, q) for p, q in zip(da, db))
+    grp = lib.Group([A for A, _ in pairs])
+    try:
+        st = grp.update("dfp")
+    finally:
+        grp.close()
+    for (A, B), s in zip(pairs, st):
+        sb = B.update("dfp")
+        assert np.array_equal(A.ranks(), B.ranks())
+        assert (s.iterations, s.vertices_processed) == (sb.iterations, sb.vertices_processed)
+    # a bad id in one batch
+    n0 = 1 << specs[0][0]
+    bad = (None, None, torch.tensor([1, n0 + 5], dtype=torch.int32, device="cuda"),
+           torch.tensor([2, 3], dtype=torch.int32, device="cuda"))
+    good = tuple(torch.tensor(x, dtype=torch.int32, device="cuda") for x in ([], [], [7], [8]))
+    before = pairs[0][0].out_csr()
+    m1 = pairs[1][0].m
+    with pytest.raises(lib.PRError) as e:
+        lib.pr_apply_batches_device([pairs[0][0].handle, pairs[1][0].handle], [bad, good])
+    assert e.value.status == 2
+    after = pairs[0][0].out_csr()
+    assert np.array_equal(before[0], after[0]) and np.array_equal(before[1], after[1])
+    assert pairs[1][0].m in (m1, m1 + 1)                 # the other graph's batch was applied
