@@ -438,8 +438,7 @@ def run_batched(a, rank, world, local_rank):
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         for i in range(a.e2e_steps):
-            for G, hb in zip(graphs, host_batches):
-                G.apply_batch(*[t.numpy() for t in hb[i]])
+            grp.apply_batches([[t.numpy() for t in hb[i]] for hb in host_batches])
             grp.update("dfp", alpha=ALPHA, tau=TAU)
             for G, r in zip(graphs, r_host):
                 G.ranks(r.numpy())

@@ -186,6 +186,13 @@ pr_status pr_apply_batches_device(int32_t count, pr_graph* const* graphs, const 
                                   const int32_t* const* del_dst, const int64_t* n_del, const int32_t* const* ins_src,
                                   const int32_t* const* ins_dst, const int64_t* n_ins);
 
+/* As pr_apply_batches_device with every endpoint array in host memory (ids
+ * are checked on the host before anything of that graph is queued; each
+ * batch is staged into its graph's device scratch on the pool's stream). */
+pr_status pr_apply_batches(int32_t count, pr_graph* const* graphs, const int32_t* const* del_src,
+                           const int32_t* const* del_dst, const int64_t* n_del, const int32_t* const* ins_src,
+                           const int32_t* const* ins_dst, const int64_t* n_ins);
+
 /*
  * Update the ranks with one method (Sec. 3.1, 2.3, Alg. 1) after the last
  * batch, iterating until the L-inf change of a sweep is <= tau or

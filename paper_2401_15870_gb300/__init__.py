@@ -140,6 +140,7 @@ def load():
         "pr_autotune": ([_P, ctypes.c_int, f64, f64, i32, _P], ctypes.c_int),
         "pr_debug_fail_alloc": ([i64], None),
         "pr_apply_batches_device": ([i32, _P, _P, _P, _P, _P, _P, _P], ctypes.c_int),
+        "pr_apply_batches": ([i32, _P, _P, _P, _P, _P, _P, _P], ctypes.c_int),
         "pr_get_tuning": ([_P, _P], ctypes.c_int),
         "pr_set_tuning": ([_P, _P], ctypes.c_int),
         "pr_group_autotune": ([_P, ctypes.c_int, f64, f64, i32, _P], ctypes.c_int),
@@ -265,6 +266,28 @@ def pr_apply_batches_device(handles, batches):
         cnt[0][i], cnt[1][i] = nd, ni
     hs = (P * k)(*handles)
     _check(load().pr_apply_batches_device(k, hs, ptr[0], ptr[1], cnt[0], ptr[2], ptr[3], cnt[1]))
+
+
+def pr_apply_batches(handles, batches):
+    """As pr_apply_batches_device with host arrays (anything numpy can view as
+    int32; each batch (del_src, del_dst, ins_src, ins_dst))."""
+    k = len(handles)
+    if len(batches) != k:
+        raise ValueError("one batch per graph")
+    P = ctypes.c_void_p
+    ptr = [(P * k)() for _ in range(4)]
+    cnt = [(ctypes.c_int64 * k)() for _ in range(2)]
+    keep = []
+    for i, b in enumerate(batches):
+        arrs = [_host_i32(x if x is not None else ()) for x in b]
+        keep.append(arrs)
+        if arrs[0][0].size != arrs[1][0].size or arrs[2][0].size != arrs[3][0].size:
+            raise ValueError("endpoint arrays differ in length")
+        for j in range(4):
+            ptr[j][i] = arrs[j][1]
+        cnt[0][i], cnt[1][i] = arrs[0][0].size, arrs[2][0].size
+    hs = (P * k)(*handles)
+    _check(load().pr_apply_batches(k, hs, ptr[0], ptr[1], cnt[0], ptr[2], ptr[3], cnt[1]))
 
 
 PR_OPT_TIME_SWEEPS, PR_OPT_FORCE_PULL, PR_OPT_FORCE_PUSH = 1, 2, 4
@@ -628,6 +651,10 @@ class Group:
     def apply_batches_device(self, batches):
         """One device batch per graph of the group, in group order."""
         pr_apply_batches_device([g.handle for g in self.graphs], batches)
+
+    def apply_batches(self, batches):
+        """One host batch per graph of the group, in group order."""
+        pr_apply_batches([g.handle for g in self.graphs], batches)
 
     def autotune(self, method="dfp", alpha=0.85, tau=1e-10, reps=0) -> GroupTuning:
         return pr_group_autotune(self._q, method, alpha, tau, reps)

@@ -841,10 +841,11 @@ static cudaError_t apply_streams(int dev, cudaStream_t** out) {
   return cudaSuccess;
 }
 
-pr_status pr_apply_batches_device(int32_t count, pr_graph* const* graphs, const int32_t* const* del_src,
-                                  const int32_t* const* del_dst, const int64_t* n_del, const int32_t* const* ins_src,
-                                  const int32_t* const* ins_dst, const int64_t* n_ins) {
-  NvtxRange r("pr_apply_batches_device");
+// the batches of many graphs (host or device endpoint arrays), side by side on
+// the pool's streams
+static pr_status apply_many(int32_t count, pr_graph* const* graphs, const int32_t* const* del_src,
+                            const int32_t* const* del_dst, const int64_t* n_del, const int32_t* const* ins_src,
+                            const int32_t* const* ins_dst, const int64_t* n_ins, bool device) {
   if (count < 0 || (count > 0 && (!graphs || !n_del || !n_ins || !del_src || !del_dst || !ins_src || !ins_dst)))
     return PR_EINVAL;
   for (int32_t i = 0; i < count; i++) {
@@ -875,21 +876,53 @@ pr_status pr_apply_batches_device(int32_t count, pr_graph* const* graphs, const 
     pr_graph* h = graphs[i];
     Graph* g = &h->g;
     g->err.clear();
+    const int32_t *ds = del_src[i], *dd = del_dst[i], *is = ins_src[i], *id = ins_dst[i];
+    const int64_t nd = n_del[i], ni = n_ins[i];
+    if (!device) {   // host arrays: ids checked here, before anything is queued
+      const int32_t n = g->n;
+      bool bad = false;
+      for (int64_t k = 0; k < nd && !bad; k++) bad = ds[k] < 0 || ds[k] >= n || dd[k] < 0 || dd[k] >= n;
+      for (int64_t k = 0; k < ni && !bad; k++) bad = is[k] < 0 || is[k] >= n || id[k] < 0 || id[k] >= n;
+      if (bad) {
+        fail((pr_status)set_error(g, ERANGE_, "pr_apply_batches: vertex id out of range"));
+        continue;
+      }
+    }
     home[i] = g->stream;
     if (cudaEventRecord(h->ev[0], g->stream) != cudaSuccess) {
-      fail((pr_status)cuda_fail(g, cudaGetLastError(), "pr_apply_batches_device"));
+      fail((pr_status)cuda_fail(g, cudaGetLastError(), "pr_apply_batches"));
       continue;
     }
     if (pool && g->dev == cur) {
       cudaStream_t aux = pool[i % APPLY_STREAMS];
       if (cudaStreamWaitEvent(aux, h->ev[0], 0) != cudaSuccess) {
-        fail((pr_status)cuda_fail(g, cudaGetLastError(), "pr_apply_batches_device"));
+        fail((pr_status)cuda_fail(g, cudaGetLastError(), "pr_apply_batches"));
         continue;
       }
       g->stream = aux;
     }
     queued[i] = 1;
-    int rc = apply_batch_launch(g, del_src[i], del_dst[i], n_del[i], ins_src[i], ins_dst[i], n_ins[i], false, &pend[i]);
+    if (!device && nd + ni > 0) {   // staged in the graph's scratch (slot 0), as pr_apply_batch does
+      void* stage;
+      cudaError_t e = scratch_get(g, 0, sizeof(int32_t) * (size_t)(2 * (nd + ni) + 4) + 1024, &stage);
+      int32_t* b = (int32_t*)stage;
+      if (e == cudaSuccess && nd) e = cudaMemcpyAsync(b, ds, sizeof(int32_t) * nd, cudaMemcpyHostToDevice, g->stream);
+      if (e == cudaSuccess && nd)
+        e = cudaMemcpyAsync(b + nd, dd, sizeof(int32_t) * nd, cudaMemcpyHostToDevice, g->stream);
+      if (e == cudaSuccess && ni)
+        e = cudaMemcpyAsync(b + 2 * nd, is, sizeof(int32_t) * ni, cudaMemcpyHostToDevice, g->stream);
+      if (e == cudaSuccess && ni)
+        e = cudaMemcpyAsync(b + 2 * nd + ni, id, sizeof(int32_t) * ni, cudaMemcpyHostToDevice, g->stream);
+      if (e != cudaSuccess) {
+        fail((pr_status)cuda_fail(g, e, "pr_apply_batches"));
+        continue;
+      }
+      ds = b;
+      dd = b + nd;
+      is = b + 2 * nd;
+      id = b + 2 * nd + ni;
+    }
+    int rc = apply_batch_launch(g, ds, dd, nd, is, id, ni, !device, &pend[i]);
     if (rc != OK) {
       fail((pr_status)rc);
       continue;
@@ -916,7 +949,7 @@ pr_status pr_apply_batches_device(int32_t count, pr_graph* const* graphs, const 
       if (e == cudaSuccess) e = cudaStreamWaitEvent(home[i], h->ev[1], 0);
       if (e != cudaSuccess) {
         cudaStreamSynchronize(g->stream);   // the ordering the event could not give
-        fail((pr_status)cuda_fail(g, e, "pr_apply_batches_device"));
+        fail((pr_status)cuda_fail(g, e, "pr_apply_batches"));
       }
       g->stream = home[i];
     }
@@ -929,6 +962,20 @@ pr_status pr_apply_batches_device(int32_t count, pr_graph* const* graphs, const 
       h->ms_apply = ms;
   }
   return first;
+}
+
+pr_status pr_apply_batches(int32_t count, pr_graph* const* graphs, const int32_t* const* del_src,
+                           const int32_t* const* del_dst, const int64_t* n_del, const int32_t* const* ins_src,
+                           const int32_t* const* ins_dst, const int64_t* n_ins) {
+  NvtxRange r("pr_apply_batches");
+  return apply_many(count, graphs, del_src, del_dst, n_del, ins_src, ins_dst, n_ins, false);
+}
+
+pr_status pr_apply_batches_device(int32_t count, pr_graph* const* graphs, const int32_t* const* del_src,
+                                  const int32_t* const* del_dst, const int64_t* n_del, const int32_t* const* ins_src,
+                                  const int32_t* const* ins_dst, const int64_t* n_ins) {
+  NvtxRange r("pr_apply_batches_device");
+  return apply_many(count, graphs, del_src, del_dst, n_del, ins_src, ins_dst, n_ins, true);
 }
 
 pr_status pr_update(pr_graph* h, pr_method method, double alpha, double tau, const pr_options* opts,

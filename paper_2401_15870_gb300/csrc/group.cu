@@ -108,7 +108,7 @@ __device__ __forceinline__ void load_prefix(int64_t* sm, const int64_t* pre, int
 // Static ranks set to 1/n; the loop condition set from max_iter
 __global__ void __launch_bounds__(GR_THREADS) k_g_init(const GRun* __restrict__ run, const GDesc* __restrict__ desc,
                                                        GState* __restrict__ st, cudaGraphConditionalHandle cond) {
-  __shared__ int64_t pre[PR_GROUP_MAX + 1];
+  extern __shared__ int64_t pre[];   // G + 1 prefix entries
   const int G = run->G;
   const int method = run->method;
   load_prefix(pre, run->bpre, G);
@@ -154,7 +154,7 @@ __global__ void __launch_bounds__(GR_THREADS) k_g_init(const GRun* __restrict__ 
 // DF / DF-P initial frontier: X <- sources of the effective change, S <-
 // targets of deleted edges
 __global__ void __launch_bounds__(GR_THREADS) k_g_mark(const GRun* __restrict__ run, const GDesc* __restrict__ desc) {
-  __shared__ int64_t pre[PR_GROUP_MAX + 1];
+  extern __shared__ int64_t pre[];   // G + 1 prefix entries
   const int G = run->G;
   if (run->method != PR_DF && run->method != PR_DFP) return;
   load_prefix(pre, run->dpre, G);
@@ -179,7 +179,7 @@ __global__ void __launch_bounds__(GR_THREADS) k_g_mark(const GRun* __restrict__ 
 template <int QPT, int STEPS>
 __global__ void __launch_bounds__(GR_THREADS) k_g_gather(const GRun* __restrict__ run, const GDesc* __restrict__ desc,
                                                          const GState* __restrict__ st) {
-  __shared__ int64_t pre[PR_GROUP_MAX + 1];
+  extern __shared__ int64_t pre[];   // G + 1 prefix entries
   const int G = run->G;
   load_prefix(pre, run->wpre, G);
   const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
@@ -245,7 +245,7 @@ __device__ __forceinline__ void flush_totals(PullTotals& t, GState* s) {
 template <bool CLOSED, int FU, bool REL>
 __global__ void __launch_bounds__(GR_THREADS, 2) k_g_finish(const GRun* __restrict__ run,
                                                             const GDesc* __restrict__ desc, GState* __restrict__ st) {
-  __shared__ int64_t pre[PR_GROUP_MAX + 1];
+  extern __shared__ int64_t pre[];   // G + 1 prefix entries
   const int G = run->G;
   load_prefix(pre, run->fpre, G);
   const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
@@ -374,19 +374,24 @@ static void group_free(pr_group* q) {
   delete q;
 }
 
-static int blocks_per_sm(const void* fn, int threads) {
+static int blocks_per_sm(const void* fn, int threads, size_t smem) {
   int b = 0;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, fn, threads, 0) != cudaSuccess || b < 1) b = 1;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, fn, threads, smem) != cudaSuccess || b < 1) b = 1;
   return b;
 }
 
+// shared memory of the kernels that look a unit's graph up: the prefix of
+// per-graph unit counts of at most the group's G graphs
+static size_t prefix_bytes(const pr_group* q) { return sizeof(int64_t) * (size_t)(q->G + 1); }
+
 static cudaError_t add_kernel(cudaGraph_t graph, cudaGraphNode_t* node, const cudaGraphNode_t* dep, size_t ndep,
-                              const void* fn, int grid, void** args) {
+                              const void* fn, int grid, void** args, size_t smem) {
   cudaKernelNodeParams kp;
   memset(&kp, 0, sizeof(kp));
   kp.func = const_cast<void*>(fn);
   kp.gridDim = dim3(grid);
   kp.blockDim = dim3(GR_THREADS);
+  kp.sharedMemBytes = (unsigned)smem;
   kp.kernelParams = args;
   return cudaGraphAddKernelNode(node, graph, dep, ndep, &kp);
 }
@@ -443,17 +448,18 @@ static cudaError_t build_exec(pr_group* q, int k, bool rel) {
   q->exec_f[k] = q->fi;
   q->exec_rel[k] = rel ? 1 : 0;
   const int sms = num_sms();
-  const int g_init = sms * blocks_per_sm((const void*)k_g_init, GR_THREADS);
-  const int g_gather = sms * blocks_per_sm(gat, GR_THREADS);
-  const int g_finish = sms * blocks_per_sm(fin, GR_THREADS);
+  const size_t sm = prefix_bytes(q);
+  const int g_init = sms * blocks_per_sm((const void*)k_g_init, GR_THREADS, sm);
+  const int g_gather = sms * blocks_per_sm(gat, GR_THREADS, sm);
+  const int g_finish = sms * blocks_per_sm(fin, GR_THREADS, sm);
   cudaGraphNode_t n_init, n_mark, n_loop, n_gather, n_finish, n_ctl;
   void* a_init[] = {&q->d_run, &q->d_desc, &q->d_state, &q->cond[k]};
   void* a_mark[] = {&q->d_run, &q->d_desc};
   void* a_gather[] = {&q->d_run, &q->d_desc, &q->d_state};
   void* a_finish[] = {&q->d_run, &q->d_desc, &q->d_state};
   void* a_ctl[] = {&q->d_run, &q->d_state, &q->cond[k]};
-  if ((e = add_kernel(graph, &n_init, nullptr, 0, (const void*)k_g_init, g_init, a_init)) != cudaSuccess) return e;
-  if ((e = add_kernel(graph, &n_mark, &n_init, 1, (const void*)k_g_mark, g_init, a_mark)) != cudaSuccess) return e;
+  if ((e = add_kernel(graph, &n_init, nullptr, 0, (const void*)k_g_init, g_init, a_init, sm)) != cudaSuccess) return e;
+  if ((e = add_kernel(graph, &n_mark, &n_init, 1, (const void*)k_g_mark, g_init, a_mark, sm)) != cudaSuccess) return e;
   cudaGraphNodeParams cp = {};
   cp.type = cudaGraphNodeTypeConditional;
   cp.conditional.handle = q->cond[k];
@@ -461,8 +467,8 @@ static cudaError_t build_exec(pr_group* q, int k, bool rel) {
   cp.conditional.size = 1;
   if ((e = cudaGraphAddNode(&n_loop, graph, &n_mark, nullptr, 1, &cp)) != cudaSuccess) return e;
   cudaGraph_t body = cp.conditional.phGraph_out[0];
-  if ((e = add_kernel(body, &n_gather, nullptr, 0, gat, g_gather, a_gather)) != cudaSuccess) return e;
-  if ((e = add_kernel(body, &n_finish, &n_gather, 1, fin, g_finish, a_finish)) != cudaSuccess) return e;
+  if ((e = add_kernel(body, &n_gather, nullptr, 0, gat, g_gather, a_gather, sm)) != cudaSuccess) return e;
+  if ((e = add_kernel(body, &n_finish, &n_gather, 1, fin, g_finish, a_finish, sm)) != cudaSuccess) return e;
   cudaKernelNodeParams kp;
   memset(&kp, 0, sizeof(kp));
   kp.func = (void*)k_g_control;
@@ -528,21 +534,22 @@ static cudaError_t host_loop(pr_group* q, int k, int32_t max_iter, bool rel) {
   const int sms = num_sms();
   const void* fin = finish_fn(k, q->fi, rel);
   const void* gat = gather_fn(q->qi);
-  const int g_init = sms * blocks_per_sm((const void*)k_g_init, GR_THREADS);
-  const int g_gather = sms * blocks_per_sm(gat, GR_THREADS);
-  const int g_finish = sms * blocks_per_sm(fin, GR_THREADS);
+  const size_t sm = prefix_bytes(q);
+  const int g_init = sms * blocks_per_sm((const void*)k_g_init, GR_THREADS, sm);
+  const int g_gather = sms * blocks_per_sm(gat, GR_THREADS, sm);
+  const int g_finish = sms * blocks_per_sm(fin, GR_THREADS, sm);
   const cudaGraphConditionalHandle none = 0;
   void* a3[] = {&q->d_run, &q->d_desc, &q->d_state};
   note_launch();
-  k_g_init<<<g_init, GR_THREADS, 0, s>>>(q->d_run, q->d_desc, q->d_state, none);
+  k_g_init<<<g_init, GR_THREADS, sm, s>>>(q->d_run, q->d_desc, q->d_state, none);
   note_launch();
-  k_g_mark<<<g_init, GR_THREADS, 0, s>>>(q->d_run, q->d_desc);
+  k_g_mark<<<g_init, GR_THREADS, sm, s>>>(q->d_run, q->d_desc);
   for (int32_t it = 0; it < max_iter; it++) {
     note_launch();
-    cudaError_t le = cudaLaunchKernel(gat, dim3(g_gather), dim3(GR_THREADS), a3, 0, s);
+    cudaError_t le = cudaLaunchKernel(gat, dim3(g_gather), dim3(GR_THREADS), a3, sm, s);
     if (le != cudaSuccess) return le;
     note_launch();
-    le = cudaLaunchKernel(fin, dim3(g_finish), dim3(GR_THREADS), a3, 0, s);
+    le = cudaLaunchKernel(fin, dim3(g_finish), dim3(GR_THREADS), a3, sm, s);
     if (le != cudaSuccess) return le;
     note_launch();
     k_g_control<<<1, GR_THREADS, 0, s>>>(q->d_run, q->d_state, none);

@@ -242,53 +242,62 @@ def test_group_autotune_keeps_the_ranks(lib, cases):
 
 
 def test_batches_of_many_graphs_at_once(lib):
-    """pr_apply_batches_device gives every graph the edges, effective change
-    and ranks that pr_apply_batch_device on each graph gives: small and large
-    batches, an empty one, a graph with a repack; a batch with a bad id fails
-    with PR_ERANGE and leaves only its own graph unchanged."""
+    """pr_apply_batches_device and pr_apply_batches (host arrays) give every
+    graph the edges, effective change and ranks that pr_apply_batch_device on
+    each graph gives: small and large batches, an empty one, a graph with a
+    repack; a batch with a bad id fails with PR_ERANGE and leaves only its own
+    graph unchanged."""
     torch = pytest.importorskip("torch")
     specs = [(10, 8, 40), (12, 16, 3000), (11, 4, 0), (13, 16, 9000), (9, 8, 120)]
-    pairs, batches = [], []
+    trios, dev_batches, host_batches = [], [], []
     for k, (scale, ef, bsize) in enumerate(specs):
         n = 1 << scale
         src, dst = synth.rmat(scale, ef * n, 300 + k)
-        A = lib.Graph.from_edges(n, src, dst)
-        B = lib.Graph.from_edges(n, src, dst)
-        for G in (A, B):
+        trio = [lib.Graph.from_edges(n, src, dst) for _ in range(3)]
+        for G in trio:
             G.update("static")
         cs, cd = synth.unique_edges(src, dst)
         b = synth.batch(n, cs, cd, bsize, 400 + k) if bsize else tuple(np.zeros(0, np.int32) for _ in range(4))
         if k == 4:   # overflow one row: a repack inside the multi-graph call
             b = (b[0], b[1], np.concatenate([b[2], np.full(300, 5, np.int32)]),
                  np.concatenate([b[3], np.arange(300, dtype=np.int32) % n]))
-        pairs.append((A, B))
-        batches.append(tuple(torch.from_numpy(np.ascontiguousarray(x, np.int32)).cuda() for x in b))
-    lib.pr_apply_batches_device([A.handle for A, _ in pairs], batches)
-    for (A, B), b in zip(pairs, batches):
+        b = tuple(np.ascontiguousarray(x, np.int32) for x in b)
+        trios.append(trio)
+        host_batches.append(b)
+        dev_batches.append(tuple(torch.from_numpy(x).cuda() for x in b))
+    lib.pr_apply_batches_device([t[0].handle for t in trios], dev_batches)
+    lib.pr_apply_batches([t[2].handle for t in trios], host_batches)
+    for (A, B, C), b in zip(trios, dev_batches):
         B.apply_batch_device(*b)
-        for x, y in ((A.out_csr(), B.out_csr()), (A.in_csr(), B.in_csr())):
-            assert np.array_equal(x[0], y[0]) and np.array_equal(x[1], y[1])
-        da, db = A.effective_delta(), B.effective_delta()
-        assert all(np.array_equal(p, q) for p, q in zip(da, db))
-    grp = lib.Group([A for A, _ in pairs])
+        for G in (A, C):
+            for x, y in ((G.out_csr(), B.out_csr()), (G.in_csr(), B.in_csr())):
+                assert np.array_equal(x[0], y[0]) and np.array_equal(x[1], y[1])
+            assert all(np.array_equal(p, q) for p, q in zip(G.effective_delta(), B.effective_delta()))
+    grp = lib.Group([t[0] for t in trios])
     try:
         st = grp.update("dfp")
     finally:
         grp.close()
-    for (A, B), s in zip(pairs, st):
+    for (A, B, C), s in zip(trios, st):
         sb = B.update("dfp")
-        assert np.array_equal(A.ranks(), B.ranks())
+        sc = C.update("dfp")
+        assert np.array_equal(A.ranks(), B.ranks()) and np.array_equal(C.ranks(), B.ranks())
         assert (s.iterations, s.vertices_processed) == (sb.iterations, sb.vertices_processed)
-    # a bad id in one batch
+    # a bad id in one batch, host and device forms
     n0 = 1 << specs[0][0]
-    bad = (None, None, torch.tensor([1, n0 + 5], dtype=torch.int32, device="cuda"),
-           torch.tensor([2, 3], dtype=torch.int32, device="cuda"))
-    good = tuple(torch.tensor(x, dtype=torch.int32, device="cuda") for x in ([], [], [7], [8]))
-    before = pairs[0][0].out_csr()
-    m1 = pairs[1][0].m
-    with pytest.raises(lib.PRError) as e:
-        lib.pr_apply_batches_device([pairs[0][0].handle, pairs[1][0].handle], [bad, good])
-    assert e.value.status == 2
-    after = pairs[0][0].out_csr()
-    assert np.array_equal(before[0], after[0]) and np.array_equal(before[1], after[1])
-    assert pairs[1][0].m in (m1, m1 + 1)                 # the other graph's batch was applied
+    for form in ("device", "host"):
+        bad = (None, None, np.array([1, n0 + 5], np.int32), np.array([2, 3], np.int32))
+        good = (None, None, np.array([7], np.int32), np.array([8], np.int32))
+        if form == "device":
+            bad = (None, None) + tuple(torch.from_numpy(x).cuda() for x in bad[2:])
+            good = (None, None) + tuple(torch.from_numpy(x).cuda() for x in good[2:])
+        G0, G1 = trios[0][0], trios[1][0]
+        before = G0.out_csr()
+        m0, m1 = G0.m, G1.m
+        call = lib.pr_apply_batches_device if form == "device" else lib.pr_apply_batches
+        with pytest.raises(lib.PRError) as e:
+            call([G0.handle, G1.handle], [bad, good])
+        assert e.value.status == 2
+        after = G0.out_csr()
+        assert np.array_equal(before[0], after[0]) and np.array_equal(before[1], after[1]) and G0.m == m0
+        assert G1.m in (m1, m1 + 1)                    # the other graph's batch was applied
