@@ -70,7 +70,8 @@ def parse():
     ap.add_argument("--graphs", type=int, default=64, help="batched: graphs in the group")
     ap.add_argument("--tune", default="auto",
                     help="large: setting of the every-vertex sweeps: auto (pr_autotune on the first warm-up "
-                         "update), default, or threads,quads_per_lane,hub_vertices,fused_epilogue[,ranges]")
+                         "update), default, or threads,quads_per_lane,hub_vertices,fused_epilogue[,ranges]; "
+                         "batched: auto, default, or the group's quads_per_lane,steps_per_unit,chunks_per_unit")
     ap.add_argument("--group-loop", default="device", choices=["device", "host"],
                     help="batched: iteration loop of the group update (host: kernels launched one by one)")
     return ap.parse_args()
@@ -392,7 +393,12 @@ def run_batched(a, rank, world, local_rank):
     # updates, and every graph's own settings on its DF-P updates (for the
     # per-graph baseline), all on one extra batch per graph
     gtune, ptune = grp.tuning(), []
-    if a.tune != "default":
+    if a.tune not in ("auto", "default"):
+        # explicit group unit sizes (quads per lane, warp steps per unit, chunks per unit); graphs untuned
+        q, steps, chunks = (int(x) for x in a.tune.split(","))
+        grp.set_tuning(quads_per_lane=q, chunks_per_unit=chunks, steps_per_unit=steps)
+        gtune = grp.tuning()
+    elif a.tune == "auto":
         for G, b in zip(graphs, batches):
             G.apply_batch_device(*b[2 * nb])
         gtune = grp.autotune("dfp", alpha=ALPHA, tau=TAU)
