@@ -71,10 +71,11 @@ typedef struct {
 /* pr_options.flags: time every rank-sweep kernel with CUDA events on the
  * graph's stream and report the sum in pr_stats.ms_sweep. */
 #define PR_OPT_TIME_SWEEPS 1
-/* pr_options.flags for DF / DF-P: sweep the frontier only in pull form (every
- * vertex with a membership test) or only in push form (frontier lists with
- * explicit expansion).  By default the form is chosen per iteration from the
- * frontier's size; the result is the same in every form. */
+/* pr_options.flags for DF / DF-P and DT: sweep the frontier only in pull form
+ * (every vertex with a membership test) or only in push form (frontier lists
+ * with explicit expansion; DT: its affected set as a list).  By default the
+ * form is chosen per iteration (DT: once) from the frontier's size; the result
+ * is the same in every form. */
 #define PR_OPT_FORCE_PULL 2
 #define PR_OPT_FORCE_PUSH 4
 /* pr_options.flags for Static, ND, DF and DF-P: where the iteration loop runs.

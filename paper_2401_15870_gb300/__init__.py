@@ -300,7 +300,8 @@ MEASURES = {None: 0, "relative": 0, "absolute": 32, "contrib": 64}   # PR_OPT_ME
 
 def pr_update(h, method, alpha=0.85, tau=1e-10, tau_f=1e-6, tau_p=1e-6, max_iter=500, time_sweeps=False,
               direction=None, loop=None, measure=None) -> Stats:
-    """direction: None (chosen per iteration), "pull" or "push" (DF / DF-P, host loop).
+    """direction: None (chosen per iteration), "pull" or "push" (DF / DF-P and
+    DT, host loop).
     loop: None (by graph size), "device" or "host".  measure: the DF / DF-P
     measure compared with tau_f / tau_p: "relative" (default), "absolute" or
     "contrib"."""

@@ -450,32 +450,82 @@ pr_status dfpr::run_update(pr_graph* h, int method, double alpha, double tau, do
     if (st != PR_OK) return st;
     TRY(launch_list_scan(g->wl[0], &g->ctl->count[0], g->in.deg, n, g->qs, g->tfirst, &g->ctl->qtot, &g->ctl->ntiles,
                          h->ls_tmp, s));
-    p.list = g->wl[0];
-    p.count = &g->ctl->count[0];
-    p.qs = g->qs;
-    p.tfirst = g->tfirst;
-    p.ntiles_dev = &g->ctl->ntiles;
-    p.Ccur = g->C[g->ccur];
-    for (int32_t it = 0; it < max_iter; it++) {
-      TRY(timer.launch(SWEEP_LIST, p, s));
-      TRY(launch_commit(g->wl[0], &g->ctl->count[0], g->rnew, g->R, g->C[g->ccur], g->out.deg, g->tab_sc, nullptr, n,
-                        s));
-      TRY(launch_control(g->ctl, 0, s));
-      st = read_ctl(g);
-      if (st != PR_OK) return st;
-      timer.collect();
-      iters = it + 1;
-      dR = ctl_dR(g->ctl_h);
-      if (dR <= tau) {
-        conv = true;
-        break;
+    st = read_ctl(g);
+    if (st != PR_OK) return st;
+    const int64_t n_aff = g->ctl_h->count[0];
+    const bool pull = (flags & PR_OPT_FORCE_PULL) ||
+                      (!(flags & PR_OPT_FORCE_PUSH) && (double)(4 * g->ctl_h->qtot) > PULL_EDGE_FRACTION * (double)g->m);
+    if (pull) {
+      // the affected set holds most in-edges: sweep every row and update the
+      // members of A = aux | aux2 only.  This is the pull form of DF with no
+      // expansion (tau_f = +inf): the frontier stays A, every member is
+      // recomputed with Eq. 1 from the same sums as the list sweep, the other
+      // rows keep their ranks and contributions
+      const int64_t words = cdiv(n, 32) + 1;
+      const size_t wbytes = sizeof(uint32_t) * (size_t)words;
+      uint32_t* xb[2] = {g->aux, g->aux2};
+      TRY(launch_bits_or(g->aux, g->aux2, g->bits[0], words, s));
+      for (uint32_t* b : {g->bits[1], g->aux, g->aux2, g->ever}) TRY(cudaMemsetAsync(b, 0, wbytes, s));
+      p.tau_f = HUGE_VAL;
+      p.tau_p = HUGE_VAL;
+      int cur = 0;
+      for (int32_t it = 0; it < max_iter; it++) {
+        p.list = nullptr;
+        p.tfirst = g->full_tfirst;
+        p.ntiles_host = g->full_ntiles;
+        p.Ccur = g->C[g->ccur];
+        p.Cnext = g->C[1 - g->ccur];
+        p.S_cur = g->bits[cur];
+        p.X_cur = xb[cur];
+        p.S_next = g->bits[1 - cur];
+        p.X_next = xb[1 - cur];
+        p.gany = g->gany;
+        p.ever = g->ever;
+        p.cnt_next = &g->ctl->count[1 - cur];
+        p.cnt_x = &g->ctl->nexp;
+        TRY(timer.launch(SWEEP_PULL_DF, p, s));
+        TRY(launch_control(g->ctl, 1, s));
+        g->ccur ^= 1;
+        cur ^= 1;
+        st = read_ctl(g);
+        if (st != PR_OK) return st;
+        timer.collect();
+        iters = it + 1;
+        dR = ctl_dR(g->ctl_h);
+        if (dR <= tau) {
+          conv = true;
+          break;
+        }
       }
+      ever = iters > 0 ? n_aff : 0;
+    } else {
+      p.list = g->wl[0];
+      p.count = &g->ctl->count[0];
+      p.qs = g->qs;
+      p.tfirst = g->tfirst;
+      p.ntiles_dev = &g->ctl->ntiles;
+      p.Ccur = g->C[g->ccur];
+      for (int32_t it = 0; it < max_iter; it++) {
+        TRY(timer.launch(SWEEP_LIST, p, s));
+        TRY(launch_commit(g->wl[0], &g->ctl->count[0], g->rnew, g->R, g->C[g->ccur], g->out.deg, g->tab_sc, nullptr, n,
+                          s));
+        TRY(launch_control(g->ctl, 0, s));
+        st = read_ctl(g);
+        if (st != PR_OK) return st;
+        timer.collect();
+        iters = it + 1;
+        dR = ctl_dR(g->ctl_h);
+        if (dR <= tau) {
+          conv = true;
+          break;
+        }
+      }
+      if (max_iter == 0) {
+        st = read_ctl(g);
+        if (st != PR_OK) return st;
+      }
+      ever = iters > 0 ? g->ctl_h->count[0] : 0;
     }
-    if (max_iter == 0) {
-      st = read_ctl(g);
-      if (st != PR_OK) return st;
-    }
-    ever = iters > 0 ? g->ctl_h->count[0] : 0;
   } else {
     pr_status st = initial_marking(h);
     if (st != PR_OK) return st;

@@ -151,6 +151,18 @@ __global__ void k_popcount(const uint32_t* __restrict__ a, int64_t words, long l
   if ((threadIdx.x & 31) == 0 && c) atomicAdd((unsigned long long*)out, (unsigned long long)c);
 }
 
+// out = a | b, word by word
+__global__ void k_bits_or(const uint32_t* __restrict__ a, const uint32_t* __restrict__ b, uint32_t* __restrict__ out,
+                          int64_t words) {
+  GRID_STRIDE(w, words) out[w] = a[w] | b[w];
+}
+
+cudaError_t launch_bits_or(const uint32_t* a, const uint32_t* b, uint32_t* out, int64_t words, cudaStream_t s) {
+  if (words == 0) return cudaSuccess;
+  note_launch(); k_bits_or<<<grid_for(words, 256), 256, 0, s>>>(a, b, out, words);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_popcount(const uint32_t* a, int64_t words, long long* out, cudaStream_t s) {
   cudaError_t e = cudaMemsetAsync(out, 0, sizeof(long long), s);
   if (e != cudaSuccess) return e;

@@ -22,6 +22,8 @@ cudaError_t launch_bits_to_list(const uint32_t* a, const uint32_t* b, int32_t n,
 int64_t bits_to_list_tmp(int32_t n);
 // *out = number of set bits of a[0..words)
 cudaError_t launch_popcount(const uint32_t* a, int64_t words, long long* out, cudaStream_t s);
+// out = a | b over `words` 32-bit words
+cudaError_t launch_bits_or(const uint32_t* a, const uint32_t* b, uint32_t* out, int64_t words, cudaStream_t s);
 
 // end-of-iteration bookkeeping (one thread); frontier != 0 swaps the worklists
 cudaError_t launch_control(Ctl* ctl, int frontier, cudaStream_t s);

@@ -260,11 +260,12 @@ def test_ranks_with_hub_rows_spanning_many_tiles(lib):
 
 
 @pytest.mark.parametrize("direction", ["pull", "push", None])
-@pytest.mark.parametrize("method", ["df", "dfp"])
+@pytest.mark.parametrize("method", ["df", "dfp", "dt"])
 @pytest.mark.parametrize("scale,bsize", [(12, 40), (14, 262), (13, 3000)])
 def test_frontier_directions_agree_with_oracle(lib, method, direction, scale, bsize):
     """Pull sweeps (every vertex, membership test), push sweeps (frontier lists)
-    and the automatic choice give the oracle's ranks and processed sets."""
+    and the automatic choice give the oracle's ranks and processed sets (DT:
+    its affected set swept as a list or as the members of every-row sweeps)."""
     G, O, r0 = rank_case(lib, scale, 16, bsize, 50 + scale)
     G.set_ranks(r0)
     st = G.update(method, direction=direction)
@@ -292,7 +293,7 @@ def test_device_and_host_loops_agree_bitwise(lib, method, scale, bsize):
     assert np.max(np.abs(out[0][0] - ref)) < TOL
 
 
-@pytest.mark.parametrize("method", ["df", "dfp"])
+@pytest.mark.parametrize("method", ["df", "dfp", "dt"])
 @pytest.mark.parametrize("scale,bsize", [(12, 40), (14, 262), (13, 3000)])
 def test_frontier_directions_agree_bitwise(lib, method, scale, bsize):
     """Both sweep forms sum the same fixed-point contributions exactly and
@@ -304,10 +305,11 @@ def test_frontier_directions_agree_bitwise(lib, method, scale, bsize):
     for direction in ("pull", "push", None):
         G.set_ranks(r0)
         st = G.update(method, direction=direction)
-        out.append((G.ranks(), st.iterations, st.vertices_ever_affected, st.vertices_processed))
-    for r, it, ev, vp in out[1:]:
+        out.append((G.ranks(), st.iterations, st.vertices_ever_affected, st.vertices_processed,
+                    st.edges_processed if method == "dt" else 0))
+    for r, *rest in out[1:]:
         assert np.array_equal(r, out[0][0])
-        assert (it, ev, vp) == out[0][1:]
+        assert tuple(rest) == out[0][1:]
 
 
 def test_successive_batches_and_methods_from_same_ranks(lib):
