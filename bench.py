@@ -496,6 +496,10 @@ def run_batched(a, rank, world, local_rank):
                                    "fused_epilogue": sorted(set(t.fused_epilogue for t in ptune)),
                                    "ranges": sorted(set(t.ranges for t in ptune))},
             "group_update_ms_mean": upd_ms / a.steps,
+            # in-edges of frontier rows over the in-edges the group's pull sweeps walk
+            # (every slot of a live graph per pass)
+            "processed_share_of_walked": sum(s.edges_processed for s in flat) /
+            max(1, sum(s.iterations * m for step in st_g for s, (_, m, _) in zip(step, sizes))),
             "iterations_max_mean": statistics.mean(max(s.iterations for s in step) for step in st_g),
             "iterations_mean": statistics.mean(s.iterations for s in flat),
             "ms_apply_sum_mean": statistics.mean(sum(s.ms_apply for s in step) for step in st_g),
