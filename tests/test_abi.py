@@ -62,6 +62,15 @@ def test_argument_errors_are_reported_before_any_device_work(lib):
     assert lib.pr_autotune(None, 1, 0.85, 1e-10, 3, None) == 1
     lib.pr_set_tuning.argtypes = [P, P]
     assert lib.pr_set_tuning(None, None) == 1
+    for name in ("pr_apply_batches", "pr_apply_batches_device"):
+        fn = getattr(lib, name)
+        fn.argtypes = [ctypes.c_int32, P, P, P, P, P, P, P]
+        counts = (ctypes.c_int64 * 1)(0)
+        nulls = (P * 1)()
+        assert fn(0, None, None, None, None, None, None, None) == 0                   # nothing to apply
+        assert fn(-1, None, None, None, None, None, None, None) == 1                  # count < 0
+        assert fn(1, None, nulls, nulls, counts, nulls, nulls, counts) == 1           # no graph array
+        assert fn(1, nulls, nulls, nulls, counts, nulls, nulls, counts) == 1          # a null graph
 
 
 def test_product_path_has_no_oracle_or_cpu_fallback():
