@@ -240,3 +240,39 @@ def test_dfp_full_run_full_size(full):
     r_static = G.ranks()
     assert np.max(np.abs(r - r_static)) < 10 * TAU_P / (1 - ALPHA)
     assert abs(float(np.sum(r)) - 1.0) < 1e-5          # sanity: pruning moves little mass
+
+
+def test_dt_full_run_full_size(full):
+    """Dynamic Traversal at full size: its affected set (reachable from the
+    changed sources in G_{t-1} or G_t) holds most in-edges here, so the
+    automatic choice sweeps every row and updates the members; the list form
+    gives the same bits.  Converged; every vertex outside the set keeps
+    R_{t-1} bitwise; on sampled members the residual of Eq. 1 is within the
+    bound a last change of at most tau allows (as for Static)."""
+    G, r_prev, n = full["G"], full["r_prev"], full["n"]
+    DT = G.dt_affected()
+    res = {}
+    for direction in (None, "push"):
+        G.set_ranks(r_prev)
+        st = G.update("dt", alpha=ALPHA, tau=TAU, direction=direction)
+        assert st.converged and st.delta_R <= TAU
+        assert st.vertices_ever_affected == int(DT.sum())
+        res[direction] = (G.ranks(), st)
+    r, st = res[None]
+    assert np.array_equal(res["push"][0], r)
+    assert (res["push"][1].iterations, res["push"][1].edges_processed) == (st.iterations, st.edges_processed)
+    assert np.array_equal(r[~DT], r_prev[~DT])
+    snap = full["after"]
+    c = in_sums(snap.in_rows, snap.outdeg_of, r)
+    off, adj = snap.in_rows
+    checked = 0
+    for k, v in enumerate(snap.sample):
+        if not DT[v]:
+            continue
+        u = adj[off[k]:off[k + 1]]
+        expect = oracle.rank_plain(ALPHA, n, c[k])
+        bound = (ALPHA * TAU * float(np.sum(1.0 / snap.outdeg_of(u))) + ALPHA * (u.size + 1) * 2.0 ** -61
+                 + 8 * np.spacing(expect))
+        assert abs(r[v] - expect) <= bound, (v, r[v], expect, bound)
+        checked += 1
+    assert checked > 0
