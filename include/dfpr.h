@@ -367,7 +367,9 @@ pr_status pr_group_set_tuning(pr_group* grp, const pr_group_tuning* in);
  *     set is the one the requests give one after another, Sec. 3.2).  Batches
  *     are applied while the previous group update runs, and every graph with
  *     an applied batch joins the next group update (one launch pair per
- *     iteration for all of them, the loop on the device).  A round admits
+ *     iteration for all of them, the loop on the device); a round of one or
+ *     two graphs with no request waiting for an idle graph runs pr_update on
+ *     each instead.  A round admits
  *     graphs while their estimated batch scratch leaves hbm_reserve bytes of
  *     device memory free and the round's edges stay within max_round_edges
  *     (0: no cap); the first graph of a round is always admitted.

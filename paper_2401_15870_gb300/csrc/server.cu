@@ -15,8 +15,9 @@
 //      on the graphs' stream -- this overlaps with the group update already
 //      running on the group stream;
 //   3. when no update is running, launch one group update (pr_group machinery)
-//      over every READY graph (a lone READY graph with nothing else queued
-//      runs pr_update instead, whose host loop may pick the push form);
+//      over every READY graph (one or two READY graphs, with no request
+//      waiting for an idle graph, run pr_update each instead, whose host loop
+//      may pick the push form);
 //   4. when the running update has finished, complete its requests.
 // A request that arrives for a READY or IN_FLIGHT graph waits for the next
 // round of that graph, so the batches of a graph are applied in arrival order.
@@ -55,6 +56,9 @@ enum GraphState { IDLE = 0, READY = 1, IN_FLIGHT = 2 };
 // sort buffers, flags, row staging), for admission
 constexpr int64_t BYTES_PER_BATCH_EDGE = 160;
 constexpr int64_t BYTES_PER_BATCH = 4 << 20;
+// rounds of at most this many graphs, with no request waiting for an idle
+// graph, run one pr_update per graph instead of a group update
+constexpr size_t SOLO_MAX_GRAPHS = 2;
 
 }  // namespace
 
@@ -274,25 +278,29 @@ void run_grouped(pr_server* S) {
       S->members.clear();
       for (int i = 0; i < G; i++)
         if (S->state[i] == READY) S->members.push_back(i);
-      bool alone = false;
-      if (S->members.size() == 1) {
+      bool solo = !S->members.empty() && S->members.size() <= SOLO_MAX_GRAPHS;
+      if (solo) {
+        // only when no request waits for an idle graph: otherwise the group
+        // update runs asynchronously while the worker applies those batches
         std::lock_guard<std::mutex> lk(S->mu);
-        alone = S->pending.empty();
+        for (const Request& r : S->pending) solo = solo && S->state[r.graph] != IDLE;
       }
-      if (alone) {
-        // one graph and no other work: its own update, with the direction
-        // choice of pr_update (cheaper than the pull-only group form on a
-        // large graph whose frontier starts small)
-        const int32_t gi = S->members[0];
-        pr_stats st;
-        memset(&st, 0, sizeof(st));
-        pr_status rc = pr_update(S->graphs[gi], (pr_method)S->opt.method, S->opt.alpha, S->opt.tau, &S->opt.opts,
-                                 &st);
-        finish_requests(S, S->ready_reqs[gi], rc, S->round++, S->t_start[gi], &st);
+      if (solo) {
+        // few graphs: each its own update in turn, with the direction choice
+        // of pr_update (cheaper than the pull-only group form on a large graph
+        // whose frontier starts small); same ranks and statistics as the group
+        for (int32_t gi : S->members) {
+          pr_stats st;
+          memset(&st, 0, sizeof(st));
+          pr_status rc = pr_update(S->graphs[gi], (pr_method)S->opt.method, S->opt.alpha, S->opt.tau, &S->opt.opts,
+                                   &st);
+          finish_requests(S, S->ready_reqs[gi], rc, S->round++, S->t_start[gi], &st);
+          std::lock_guard<std::mutex> lk(S->mu);
+          S->state[gi] = IDLE;
+        }
         S->ready_bytes = 0;
         S->ready_edges = 0;
-        std::lock_guard<std::mutex> lk(S->mu);
-        S->state[gi] = IDLE;
+        S->cv_work.notify_all();
       } else if (!S->members.empty()) {
         pr_status rc = group_launch(S->group, (pr_method)S->opt.method, S->opt.alpha, S->opt.tau, &S->opt.opts,
                                     S->members.data(), (int32_t)S->members.size());
