@@ -202,8 +202,13 @@ int refresh_full_tiles(Graph* g) {
       p = nullptr;
     }
   int64_t words = cdiv(quads, 32) + 1;
-  TRY(dalloc(g, (void**)&g->rowbits, sizeof(uint32_t) * words));
-  TRY(dalloc(g, (void**)&g->rowbase, sizeof(int32_t) * (words + 1)));
+  // padded to a multiple of 8 words, plus 8: a sweep step reads the words of
+  // its quads (up to 8) with vector loads from a multiple of its width
+  const int64_t padded = (cdiv(quads, 32) + 7) / 8 * 8 + 8;
+  TRY(dalloc(g, (void**)&g->rowbits, sizeof(uint32_t) * padded));
+  TRY(dalloc(g, (void**)&g->rowbase, sizeof(int32_t) * padded));
+  TRY(cudaMemsetAsync(g->rowbits, 0, sizeof(uint32_t) * padded, g->stream));
+  TRY(cudaMemsetAsync(g->rowbase, 0, sizeof(int32_t) * padded, g->stream));
   {
     int32_t* tmp;
     TRY(dev_malloc(&tmp, sizeof(int32_t) * scan_tmp_elems(words)));

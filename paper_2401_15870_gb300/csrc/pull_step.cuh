@@ -99,15 +99,44 @@ __device__ __forceinline__ GatherSpan gather_step(const int32_t* __restrict__ ic
   };
   int4 c[QPT];
   int owner[QPT];
+  // the row-start words of the step's QPT 32-quad words in one vector load
+  // each: a step starts at a multiple of 32 x QPT quads, and both arrays are
+  // padded to a multiple of 8 words, so the loads are aligned and in bounds
+  // (words past the last quad are read but not used)
+  static_assert(QPT == 2 || QPT % 4 == 0, "quads per lane: 2 or a multiple of 4");
+  uint32_t wb[QPT];
+  int32_t wr[QPT];
+  {
+    const int64_t w0 = base >> 5;
+    if constexpr (QPT == 2) {
+      const uint2 b = __ldg(reinterpret_cast<const uint2*>(rowbits + w0));
+      const int2 r = __ldg(reinterpret_cast<const int2*>(rowbase + w0));
+      wb[0] = b.x;
+      wb[1] = b.y;
+      wr[0] = r.x;
+      wr[1] = r.y;
+    } else {
+#pragma unroll
+      for (int j = 0; j < QPT; j += 4) {
+        const uint4 b = __ldg(reinterpret_cast<const uint4*>(rowbits + w0 + j));
+        const int4 r = __ldg(reinterpret_cast<const int4*>(rowbase + w0 + j));
+        wb[j] = b.x;
+        wb[j + 1] = b.y;
+        wb[j + 2] = b.z;
+        wb[j + 3] = b.w;
+        wr[j] = r.x;
+        wr[j + 1] = r.y;
+        wr[j + 2] = r.z;
+        wr[j + 3] = r.w;
+      }
+    }
+  }
 #pragma unroll
   for (int j = 0; j < QPT; j++) {
     const int64_t q = base + 32 * j + lane;
     const bool valid = q >= qlo && q < nquads;
     c[j] = valid ? ld_stream4(icol + 4 * q, pol_stream) : make_int4(sent, sent, sent, sent);
-    const int64_t w = (base >> 5) + j;
-    const uint32_t bits = w * 32 < nquads ? __ldg(rowbits + w) : 0u;
-    const int32_t rb = w * 32 < nquads ? __ldg(rowbase + w) : 0;
-    owner[j] = valid ? rb + __popc(bits & upto) - 1 : -1;
+    owner[j] = valid ? wr[j] + __popc(wb[j] & upto) - 1 : -1;
   }
   long long s[QPT];
   unsigned x[QPT];
