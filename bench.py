@@ -39,9 +39,9 @@ SWEEP_BYTES_PER_VERTEX = 60
 SAMPLE_SCALE = 18
 # DRAM bytes (read + write) of one pull-form DF-P sweep (k_gather_rows + k_finish_pull) on the
 # default workload, from the one-pass ncu captures under profiles/, keyed by the gather setting
-# (threads, quads per lane, hub vertices, fused epilogue, ranges); a setting without a capture reports
-# null
-SWEEP_DRAM_BYTES_RMAT25 = {(256, 4, 0, 0, 1): 11.42e9, (512, 4, 0, 0, 1): 11.28e9, (1024, 2, 0, 0, 1): 11.44e9}
+# (threads, quads per lane, hub vertices, fused epilogue, ranges); a setting without a capture of the
+# current kernels reports null
+SWEEP_DRAM_BYTES_RMAT25 = {(1024, 2, 0, 0, 1): 11.44e9}
 
 
 def parse():

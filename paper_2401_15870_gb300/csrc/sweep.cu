@@ -22,6 +22,7 @@
 #include <tuple>
 #include "sweep.cuh"
 #include "pull_step.cuh"
+#include "fixconv.cuh"
 #include "prim.cuh"
 
 namespace dfpr {
@@ -441,7 +442,7 @@ __global__ void __launch_bounds__(256, 4) k_finish_full(SweepParams p, long long
       verts += 1;
       p.R[v] = r;
       const double sc = d[u] < TAB ? p.tab_sc[d[u]] : FIX_ONE / (double)d[u];
-      p.Cnext[v] = __double2ll_rn(r * sc);
+      p.Cnext[v] = fixconv::f64_to_i64_rn(r * sc);   // integer pipes: the FP64 pipe bounds this epilogue
     }
   }
   block_flush_stats(__longlong_as_double((long long)dmax), edges, verts, p.ctl);
@@ -489,7 +490,7 @@ __device__ __forceinline__ void finish_full_step(const SweepParams& p, long long
     t.verts += 1;
     p.R[v] = r;
     const double sc = d[u] < TAB ? p.tab_sc[d[u]] : FIX_ONE / (double)d[u];
-    p.Cnext[v] = __double2ll_rn(r * sc);
+    p.Cnext[v] = fixconv::f64_to_i64_rn(r * sc);
   }
 }
 
