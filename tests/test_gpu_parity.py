@@ -537,3 +537,20 @@ def test_measure_flags_are_exclusive(lib):
     G.set_ranks(r0)
     b = G.update("nd")
     assert np.array_equal(ra, G.ranks()) and a.iterations == b.iterations
+
+
+@pytest.mark.parametrize("method", ["df", "dfp"])
+@pytest.mark.parametrize("direction", ["pull", "push", None])
+def test_frontier_without_expansion_matches_oracle(lib, method, direction):
+    """tau_f = inf, tau_p = 0: only the initially affected set is swept, every
+    other vertex keeps R_{t-1} bitwise (the case the oracle pins to the linear
+    system restricted to that set)."""
+    G, O, r0 = rank_case(lib, 12, 16, 40, 91)
+    G.set_ranks(r0)
+    st = G.update(method, tau_f=float("inf"), tau_p=0.0, direction=direction)
+    ref, ost = O.update(method, tau_f=float("inf"), tau_p=0.0, r_prev=r0)
+    A = G.initial_affected()
+    got = G.ranks()
+    assert np.max(np.abs(got - ref)) < TOL
+    assert np.array_equal(got[~A], r0[~A])
+    assert st.vertices_ever_affected == ost.vertices_ever_affected == int(A.sum())

@@ -476,3 +476,39 @@ def test_prune_everything_expand_nothing(metric, order):
         for v in np.flatnonzero(F0)[:20]:
             c = sum(r0[u] / d[u] for u in adj[off[v]:off[v + 1]])
             assert r[v] == oracle.rank_closed_loop(ALPHA, n, c, r0[v], int(d[v]))
+
+
+@pytest.mark.parametrize("method", ["df", "dfp"])
+@pytest.mark.parametrize("seed", [81, 82])
+def test_frontier_without_expansion_solves_the_restricted_system(method, seed):
+    """With expansion switched off (tau_f = inf) and no pruning (tau_p = 0),
+    DF and DF-P sweep exactly the initially affected set F_0 (Alg. 1) with every
+    other vertex held at R_{t-1}.  Their limit is then the solution of the
+    linear system restricted to F_0: x_v = (1-alpha)/n + alpha sum_{u in in(v)}
+    x_u / |out(u)| for v in F_0, with x_u = R_{t-1}[u] outside F_0 (Eq. 1; Eq. 2
+    has the same fixed point), solved here with numpy's LAPACK solver."""
+    n = 150
+    src, dst = random_graph(n, 700, seed)
+    g = oracle.Graph(n, src, dst)
+    r0, _ = g.update("static", tau=1e-15, max_iter=5000)
+    E0 = edge_set(n, src, dst)
+    (ds, dd), (is_, id_) = random_batch(n, E0, 2, 4, seed + 100, with_noise=False)
+    g.apply_batch(ds, dd, is_, id_)
+    F0 = g.initial_affected().astype(bool)
+    assert 0 < F0.sum() < n
+    E1 = (E0 - set(zip(ds.tolist(), dd.tolist()))) | set(zip(is_.tolist(), id_.tolist()))
+    E1 |= {(v, v) for v in range(n)}
+    outdeg = np.zeros(n)
+    for u, _ in E1:
+        outdeg[u] += 1
+    A = np.eye(n)
+    for u, w in E1:
+        A[w, u] -= ALPHA / outdeg[u]
+    b = np.full(n, (1 - ALPHA) / n)
+    F, O = np.flatnonzero(F0), np.flatnonzero(~F0)
+    x = np.linalg.solve(A[np.ix_(F, F)], b[F] - A[np.ix_(F, O)] @ r0[O])
+    r, st = g.update(method, tau=1e-15, tau_f=np.inf, tau_p=0.0, max_iter=5000, r_prev=r0)
+    assert st.converged
+    assert st.vertices_ever_affected == F0.sum()
+    assert np.array_equal(r[O], r0[O])
+    assert np.max(np.abs(r[F] - x)) < 1e-12
