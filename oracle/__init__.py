@@ -21,8 +21,9 @@ Parity status: Static / ND / DT ranks are pinned to the linear-system
 solution, to closed forms and to mass conservation; the marking and
 reachability sets to brute force and to the worked example of Sec. 4.1.3.
 DF / DF-P ranks on general inputs are pinned only by their invariants and
-by their limits (tau_f = tau_p = 0 gives the linear-system solution):
-parity unpinned beyond those.
+by their limits (tau_f = tau_p = 0 gives the linear-system solution;
+tau_f = inf with tau_p = 0 gives the solution of the system restricted to
+the initial marking): parity unpinned beyond those.
 """
 from __future__ import annotations
 
