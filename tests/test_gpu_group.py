@@ -301,3 +301,50 @@ def test_batches_of_many_graphs_at_once(lib):
         after = G0.out_csr()
         assert np.array_equal(before[0], after[0]) and np.array_equal(before[1], after[1]) and G0.m == m0
         assert G1.m in (m1, m1 + 1)                    # the other graph's batch was applied
+
+
+def test_batches_of_graphs_on_their_own_streams(lib):
+    """Graphs on different streams: pr_apply_batches_device orders each graph's
+    batch after the work already queued on the graph's stream and before the
+    work queued after the call.  A rank import is queued on each stream just
+    before the call, a rank export just after, and the applied edges, the
+    effective change and the DF-P ranks equal those of the same graph applied
+    alone."""
+    torch = pytest.importorskip("torch")
+    streams = [torch.cuda.Stream() for _ in range(3)]
+    graphs, twins, batches, r0s = [], [], [], []
+    for k, (scale, bsize) in enumerate([(11, 50), (12, 2500), (10, 9)]):
+        n = 1 << scale
+        src, dst = synth.rmat(scale, 8 * n, 500 + k)
+        G = lib.Graph.from_edges(n, src, dst, stream=streams[k])
+        T = lib.Graph.from_edges(n, src, dst)
+        T.update("static")
+        r0 = torch.from_numpy(T.ranks()).cuda()
+        cs, cd = synth.unique_edges(src, dst)
+        b = synth.batch(n, cs, cd, bsize, 600 + k)
+        graphs.append(G)
+        twins.append(T)
+        batches.append(tuple(torch.from_numpy(np.ascontiguousarray(x, np.int32)).cuda() for x in b))
+        r0s.append(r0)
+    torch.cuda.synchronize()
+    outs = []
+    for G, r0, s in zip(graphs, r0s, streams):
+        with torch.cuda.stream(s):
+            G.set_ranks_device(r0)
+    lib.pr_apply_batches_device([G.handle for G in graphs], batches)
+    for G, r0, s in zip(graphs, r0s, streams):
+        with torch.cuda.stream(s):
+            out = torch.empty_like(r0)
+            G.ranks_device(out)
+            outs.append(out)
+    torch.cuda.synchronize()
+    for G, T, b, r0, out in zip(graphs, twins, batches, r0s, outs):
+        assert torch.equal(out, r0)                    # the import landed before the batch, the export after
+        T.apply_batch_device(*b)
+        for x, y in ((G.out_csr(), T.out_csr()), (G.in_csr(), T.in_csr())):
+            assert np.array_equal(x[0], y[0]) and np.array_equal(x[1], y[1])
+        assert all(np.array_equal(p, q) for p, q in zip(G.effective_delta(), T.effective_delta()))
+        sg_ = G.update("dfp")
+        st_ = T.update("dfp")
+        assert np.array_equal(G.ranks(), T.ranks())
+        assert (sg_.iterations, sg_.vertices_processed) == (st_.iterations, st_.vertices_processed)
