@@ -199,8 +199,9 @@ struct PullTotals {
 // the next sweep.  L2: read them from L2 (they were written by other SMs in
 // the same launch).
 // REL: the relative measure of Alg. 1 fixed at compile time (the default);
-// otherwise p.metric chooses
-template <bool CLOSED, class P, bool L2 = false, int U = FIN_U, bool REL = false>
+// otherwise p.metric chooses.  SAME: tau_p == tau_f known at compile time (the
+// default tolerances), which saves the FP64 product of the prune threshold
+template <bool CLOSED, class P, bool L2 = false, int U = FIN_U, bool REL = false, bool SAME = false>
 __device__ __forceinline__ void finish_pull_step(const P& p, long long* __restrict__ acc, uint32_t* __restrict__ anyb,
                                                  int64_t ch0, int64_t nchunks, PullTotals& t) {
   const int lane = threadIdx.x & 31;
@@ -252,7 +253,7 @@ __device__ __forceinline__ void finish_pull_step(const P& p, long long* __restri
       const double mx = dbits(r) > dbits(Rv[u]) ? r : Rv[u];
       const double mr = REL ? mx : measure_base(p.metric, mx, d[u]);
       const unsigned long long tf = dbits(p.tau_f * mr);
-      const unsigned long long tp = same_tau ? tf : dbits(p.tau_p * mr);
+      const unsigned long long tp = SAME || same_tau ? tf : dbits(p.tau_p * mr);
       stay = !CLOSED || drb > tp;
       expand = drb > tf;
     } else if (valid[u]) {

@@ -392,7 +392,7 @@ __global__ void __launch_bounds__(1024) k_gather_rows(const int32_t* __restrict_
 }
 
 // (the 32-vertex chunks [ch_lo, ch_hi); ch_lo a multiple of FIN_U)
-template <bool CLOSED, bool REL>
+template <bool CLOSED, bool REL, bool SAME = false>
 __global__ void __launch_bounds__(256, 4) k_finish_pull(SweepParams p, long long* __restrict__ acc,
                                                         uint32_t* __restrict__ anyb, int64_t ch_lo, int64_t ch_hi) {
   const int lane = threadIdx.x & 31;
@@ -400,7 +400,7 @@ __global__ void __launch_bounds__(256, 4) k_finish_pull(SweepParams p, long long
   PullTotals t;
   for (int64_t ch0 = ch_lo + ((blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5) * FIN_U; ch0 < ch_hi;
        ch0 += nw * FIN_U)
-    finish_pull_step<CLOSED, SweepParams, false, FIN_U, REL>(p, acc, anyb, ch0, ch_hi, t);
+    finish_pull_step<CLOSED, SweepParams, false, FIN_U, REL, SAME>(p, acc, anyb, ch0, ch_hi, t);
   if (lane == 0) {
     if (t.stays) atomicAdd(p.cnt_next, t.stays);
     if (t.exps) atomicAdd(p.cnt_x, t.exps);
@@ -782,7 +782,10 @@ cudaError_t launch_full_sweep(int mode, const SweepParams& p, const GatherCfg& c
         break;
       case SWEEP_PULL_DFP:
         note_launch();
-        if (p.metric == METRIC_RELATIVE) k_finish_pull<true, true><<<rgrid, 256, 0, fs>>>(p, p.gacc, anyb, ch_lo, ch_hi);
+        if (p.metric == METRIC_RELATIVE && p.tau_f == p.tau_p)
+          k_finish_pull<true, true, true><<<rgrid, 256, 0, fs>>>(p, p.gacc, anyb, ch_lo, ch_hi);
+        else if (p.metric == METRIC_RELATIVE)
+          k_finish_pull<true, true><<<rgrid, 256, 0, fs>>>(p, p.gacc, anyb, ch_lo, ch_hi);
         else k_finish_pull<true, false><<<rgrid, 256, 0, fs>>>(p, p.gacc, anyb, ch_lo, ch_hi);
         break;
       default: return cudaErrorInvalidValue;
