@@ -272,13 +272,16 @@ pr_status pr_affected(pr_graph* g, int32_t which, uint8_t* flags);
  *     summed exactly in 2^-61 fixed point like pr_update's sweeps;
  *   *delta_out: receives max_v |r_out[v] - r_in[v]|.
  * Work is enqueued on `stream`; the call returns before it completes.  Its
- * scratch memory (n + 2 int64 values) is a fixed array inside the library,
- * present on every GPU that loads it until the process exits; n above
- * PR_NOALLOC_MAX_N is rejected with PR_EINVAL before any device work.  The
+ * scratch memory is a fixed array of PR_NOALLOC_MAX_N + 2 int64 values
+ * (about 4 MB) inside the library, whatever n is, present on every GPU that
+ * loads it until the process exits; n above PR_NOALLOC_MAX_N is rejected with
+ * PR_EINVAL before any device work.  r_out must not overlap r_in (the change
+ * of every vertex is measured against r_in): overlapping buffers are rejected
+ * with PR_EINVAL.  The
  * first call on a device looks up that array's address (cudaGetSymbolAddress):
  * make it before any stream capture.  All calls share the array, so calls
  * that overlap on the GPU race and must be serialized.  Errors: PR_EINVAL
- * (size, null pointer, alpha), PR_ECUDA.
+ * (size, null pointer, r_out overlapping r_in, alpha), PR_ECUDA.
  */
 #define PR_NOALLOC_MAX_N 524288
 pr_status pr_sweep_noalloc(int32_t n, const int64_t* in_off, const int32_t* in_src, const int32_t* out_deg,

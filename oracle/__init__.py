@@ -95,7 +95,8 @@ def _load():
 class _Stats(ctypes.Structure):
     _fields_ = [("iterations", ctypes.c_int32), ("converged", ctypes.c_int32),
                 ("delta_R", ctypes.c_double), ("vertices_ever_affected", ctypes.c_int64),
-                ("edges_processed", ctypes.c_int64), ("vertices_processed", ctypes.c_int64)]
+                ("edges_processed", ctypes.c_int64), ("vertices_processed", ctypes.c_int64),
+                ("tie_rel", ctypes.c_double)]
 
 
 @dataclass
@@ -106,6 +107,9 @@ class Stats:
     vertices_ever_affected: int
     edges_processed: int
     vertices_processed: int
+    # smallest |x / t - 1| between a compared quantity x and its threshold t
+    # over every expand / prune / stop decision of the run (near-ties)
+    tie_rel: float = float("inf")
 
 
 class OracleError(RuntimeError):
@@ -219,4 +223,4 @@ class Graph:
         if rc:
             raise OracleError(_ERR.get(rc, str(rc)))
         return out, Stats(st.iterations, bool(st.converged), st.delta_R, st.vertices_ever_affected,
-                          st.edges_processed, st.vertices_processed)
+                          st.edges_processed, st.vertices_processed, st.tie_rel)

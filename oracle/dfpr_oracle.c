@@ -72,6 +72,14 @@ typedef struct {
   int64_t vertices_ever_affected;
   int64_t edges_processed;
   int64_t vertices_processed;
+  /* the smallest relative distance |x / t - 1| between a compared quantity x
+   * and its threshold t over every decision of the run: the frontier measure
+   * against tau_f (expand) and tau_p (prune), and Delta R against tau (stop).
+   * A second implementation whose ranks differ slightly from these can take a
+   * decision the other way only where this is small; the tests use it to tell
+   * a genuine near-tie from a different frontier.  Thresholds of 0 or
+   * infinity take no part; INFINITY when nothing was compared. */
+  double tie_rel;
 } or_stats;
 
 static uint64_t key_of(int32_t u, int32_t v) { return ((uint64_t)(uint32_t)u << 32) | (uint32_t)v; }
@@ -364,6 +372,12 @@ static double frontier_measure(int metric, double dr, double r, double Rv, int64
   return dr / fmax(r, Rv);
 }
 
+/* relative distance of x from the threshold t (see tie_rel) */
+static double tie_to(double x, double t) {
+  if (!(t > 0.0) || !isfinite(t)) return INFINITY;
+  return fabs(x / t - 1.0);
+}
+
 /*
  * One method run (Sec. 3.1, Sec. 3.3, Alg. 1).
  * r_prev: ranks of the previous snapshot (ignored by Static, required by the
@@ -398,6 +412,7 @@ int or_update_ex(const or_graph *g, int method, double alpha, double tau, double
   int async = (order == OR_ORDER_ASYNC);
   or_stats s;
   memset(&s, 0, sizeof(s));
+  s.tie_rel = INFINITY;
   for (int32_t i = 0; i < max_iter; i++) {
     double dR = 0.0;
     /* synchronous: new ranks and flags go to Rn / Fn and are committed after
@@ -420,6 +435,8 @@ int or_update_ex(const or_graph *g, int method, double alpha, double tau, double
       s.edges_processed += g->in_off[v + 1] - g->in_off[v];
       if (frontier) {
         double mv = frontier_measure(metric, dr, r, R[v], d);
+        s.tie_rel = fmin(s.tie_rel, tie_to(mv, tau_f));
+        if (prune) s.tie_rel = fmin(s.tie_rel, tie_to(mv, tau_p));
         if (async) {
           if (prune && mv <= tau_p) Fw[v] = 0;              /* mark v as not affected */
         } else if (!(prune && mv <= tau_p)) {
@@ -436,6 +453,7 @@ int or_update_ex(const or_graph *g, int method, double alpha, double tau, double
     }
     s.iterations = i + 1;
     s.delta_R = dR;
+    s.tie_rel = fmin(s.tie_rel, tie_to(dR, tau));
     if (dR <= tau) { s.converged = 1; break; }
   }
   for (int32_t v = 0; v < n; v++) s.vertices_ever_affected += ever[v];

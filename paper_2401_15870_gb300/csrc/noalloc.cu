@@ -15,7 +15,10 @@
 //
 // Properties a caller must know:
 //   * Size limit: n <= PR_NOALLOC_MAX_N (header); larger n is rejected with
-//     PR_EINVAL before any device work.
+//     PR_EINVAL before any device work.  The array holds PR_NOALLOC_MAX_N + 2
+//     int64 values (about 4 MB) whatever n is.
+//   * r_out must not overlap r_in: each vertex's change is measured against
+//     r_in after r_out is written, so overlapping buffers are rejected.
 //   * The first call on a device looks up the array's device address with
 //     cudaGetSymbolAddress (once per device, with that device current).  Make
 //     that first call before any stream capture on the device.
@@ -106,6 +109,8 @@ extern "C" pr_status pr_sweep_noalloc(int32_t n, const int64_t* in_off, const in
                                       void* stream) {
   if (n < 1 || n > NA_MAX_N) return PR_EINVAL;
   if (!in_off || !in_src || !out_deg || !r_in || !r_out || !delta_out) return PR_EINVAL;
+  // the sweep measures each vertex's change against r_in after writing r_out
+  if ((const void*)r_out < (const void*)(r_in + n) && (const void*)r_in < (const void*)(r_out + n)) return PR_EINVAL;
   if (!(alpha >= 0.0 && alpha < 1.0)) return PR_EINVAL;
   NoAllocScratch* s = nullptr;
   if (na_scratch_ptr(&s) != cudaSuccess) return PR_ECUDA;

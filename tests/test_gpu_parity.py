@@ -13,6 +13,7 @@ import synth
 pytestmark = pytest.mark.gpu
 
 TOL = 1e-9
+from cases import TIE_REL, assert_same_run  # noqa: E402
 
 
 @pytest.fixture(scope="module")
@@ -217,10 +218,7 @@ def test_ranks_tiny_config(lib, method):
     got = G.ranks()
     assert np.max(np.abs(got - ref)) < TOL
     assert st.converged and ost.converged
-    assert abs(st.iterations - ost.iterations) <= 1
-    if method in ("static", "nd", "dt"):
-        assert st.vertices_ever_affected == ost.vertices_ever_affected
-        assert st.edges_processed == pytest.approx(ost.edges_processed, rel=0.02)
+    assert_same_run(st, ost, method)
 
 
 @pytest.mark.parametrize("method", ["static", "nd", "dt", "df", "dfp"])
@@ -228,9 +226,10 @@ def test_ranks_tiny_config(lib, method):
 def test_ranks_ragged_and_small(lib, method, scale, ef, bsize, keep):
     G, O, r0 = rank_case(lib, scale, ef, bsize, 20 + scale, keep)
     G.set_ranks(r0)
-    G.update(method)
-    ref, _ = O.update(method, r_prev=r0)
+    st = G.update(method)
+    ref, ost = O.update(method, r_prev=r0)
     assert np.max(np.abs(G.ranks() - ref)) < TOL
+    assert_same_run(st, ost, method)
 
 
 def test_ranks_with_hub_rows_spanning_many_tiles(lib):
@@ -271,8 +270,7 @@ def test_frontier_directions_agree_with_oracle(lib, method, direction, scale, bs
     st = G.update(method, direction=direction)
     ref, ost = O.update(method, r_prev=r0)
     assert np.max(np.abs(G.ranks() - ref)) < TOL
-    assert abs(st.iterations - ost.iterations) <= 1
-    assert st.vertices_ever_affected == pytest.approx(ost.vertices_ever_affected, rel=0.01)
+    assert_same_run(st, ost, (method, direction))
 
 
 @pytest.mark.parametrize("method", ["static", "nd", "df", "dfp"])
@@ -289,8 +287,10 @@ def test_device_and_host_loops_agree_bitwise(lib, method, scale, bsize):
                     st.edges_processed))
     assert np.array_equal(out[0][0], out[1][0])
     assert out[0][1:] == out[1][1:]
-    ref, _ = O.update(method, r_prev=r0)
+    ref, ost = O.update(method, r_prev=r0)
     assert np.max(np.abs(out[0][0] - ref)) < TOL
+    assert (out[0][1], out[0][3], out[0][4]) == (ost.iterations, ost.vertices_ever_affected,
+                                                 ost.vertices_processed) or ost.tie_rel < TIE_REL
 
 
 @pytest.mark.parametrize("method", ["df", "dfp", "dt"])
@@ -324,9 +324,10 @@ def test_successive_batches_and_methods_from_same_ranks(lib):
         O.apply_batch(*b)
         for method in ("dfp", "df", "dt", "nd"):
             G.set_ranks(r_cpu)
-            G.update(method)
-            ref, _ = O.update(method, r_prev=r_cpu)
+            st = G.update(method)
+            ref, ost = O.update(method, r_prev=r_cpu)
             assert np.max(np.abs(G.ranks() - ref)) < TOL, (i, method)
+            assert_same_run(st, ost, (i, method))
         # chain DF-P results on both sides
         G.set_ranks(r_cpu)
         G.update("dfp")
@@ -505,11 +506,12 @@ def test_frontier_measures_match_oracle_in_every_form(lib, measure, tol_f, metho
     and a group give bit-identical ranks and statistics."""
     G, O, r0 = rank_case(lib, scale, 16, bsize, 110 + scale)
     ref, ost = O.update(method, tau_f=tol_f, tau_p=tol_f, r_prev=r0, metric=measure)
-    out = []
+    out, first = [], None
     for direction, loop in (("pull", "host"), ("push", "host"), (None, "host"), (None, "device")):
         G.set_ranks(r0)
         st = G.update(method, tau_f=tol_f, tau_p=tol_f, direction=direction, loop=loop, measure=measure)
         out.append((G.ranks(), st.iterations, st.vertices_ever_affected, st.vertices_processed))
+        first = first or st
     G.set_ranks(r0)
     grp = lib.Group([G])
     try:
@@ -521,8 +523,7 @@ def test_frontier_measures_match_oracle_in_every_form(lib, measure, tol_f, metho
         assert np.array_equal(r, out[0][0])
         assert rest == list(out[0][1:])
     assert np.max(np.abs(out[0][0] - ref)) < TOL
-    assert abs(out[0][1] - ost.iterations) <= 1
-    assert out[0][2] == pytest.approx(ost.vertices_ever_affected, rel=0.01)
+    assert_same_run(first, ost, measure)
 
 
 def test_measure_flags_are_exclusive(lib):
@@ -554,3 +555,28 @@ def test_frontier_without_expansion_matches_oracle(lib, method, direction):
     assert np.max(np.abs(got - ref)) < TOL
     assert np.array_equal(got[~A], r0[~A])
     assert st.vertices_ever_affected == ost.vertices_ever_affected == int(A.sum())
+
+
+# ------------------------------------------------------------- prune against re-mark (reading C2)
+
+
+@pytest.mark.parametrize("direction,loop", [("pull", "host"), ("push", "host"), (None, "device")])
+def test_pruned_vertex_re_marked_matches_oracle(lib, direction, loop):
+    """The hand-made case of tests/golden/prune_vs_mark_6v.txt: vertex 2 is
+    pruned in iteration 0 while its in-neighbour 1 expands into it, so it is
+    swept again in iteration 1 (F_1 = M_0 u (F_0 \\ P_0) = {1, 2, 3}).  Every
+    sweep form gives the oracle's ranks and the same vertex updates after
+    one, two and three iterations."""
+    from cases import load_prune_vs_mark, prune_vs_mark_case
+    edges, _ = load_prune_vs_mark()
+    O, r, meta = prune_vs_mark_case()
+    G = lib.Graph.from_edges(6, [a for a, _ in edges], [b for _, b in edges])
+    G.apply_batch(ins_src=[meta["insert"][0]], ins_dst=[meta["insert"][1]])
+    for k in (1, 2, 3):
+        G.set_ranks(r)
+        st = G.update("dfp", tau=0.0, max_iter=k, direction=direction, loop=loop)
+        ref, ost = O.update("dfp", tau=0.0, max_iter=k, r_prev=r)
+        assert np.max(np.abs(G.ranks() - ref)) < TOL, k
+        assert (st.vertices_processed, st.vertices_ever_affected) == (ost.vertices_processed,
+                                                                      ost.vertices_ever_affected), k
+    assert ost.vertices_processed >= meta["processed_after2"][0]

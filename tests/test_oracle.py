@@ -512,3 +512,40 @@ def test_frontier_without_expansion_solves_the_restricted_system(method, seed):
     assert st.vertices_ever_affected == F0.sum()
     assert np.array_equal(r[O], r0[O])
     assert np.max(np.abs(r[F] - x)) < 1e-12
+
+
+# ------------------------------------------------------------ prune against re-mark (reading C2)
+
+
+from cases import prune_vs_mark_case  # noqa: E402
+
+
+def test_pruned_vertex_re_marked_by_expanding_in_neighbour():
+    """Alg. 1, Sec. 4.1.2: a vertex pruned in iteration i but marked by an
+    expanding in-neighbour in the same iteration is swept in iteration i + 1
+    (F_{i+1} = M_i u (F_i \\ P_i)).  The expected sets are derived by hand in
+    the fixture; a 'prune wins' order would drop vertex 2 from F_1 (5 vertices
+    processed in two iterations instead of 6, R[2] unchanged in iteration 1)."""
+    g, r, meta = prune_vs_mark_case()
+    assert set(np.flatnonzero(g.initial_affected()).tolist()) == set(meta["initial"])
+    r1, s1 = g.update("dfp", tau=0.0, max_iter=1, r_prev=r)
+    r2, s2 = g.update("dfp", tau=0.0, max_iter=2, r_prev=r)
+    # iteration 0: 0 and 2 keep their ranks (pruned), 1 moves (expands)
+    for v in meta["pruned0"]:
+        assert abs(r1[v] - r[v]) <= 1e-6 * r[v]
+    for v in meta["expanders0"]:
+        assert abs(r1[v] - r[v]) > 1e-6 * max(r1[v], r[v])
+    assert s1.vertices_processed == len(meta["initial"])
+    # F_1 = {1, 2, 3} is swept in iteration 1.  2 and 3 change (they read the
+    # new R[1]); 1 is swept but Eq. 2 gives it the same value, since its only
+    # other in-neighbour, 0, did not change; 0 is not swept and keeps its bits
+    f1 = set(meta["frontier1"])
+    assert s2.vertices_processed - s1.vertices_processed == len(f1) == meta["processed_after2"][0] - 3
+    changed = set(np.flatnonzero(r2 != r1).tolist())
+    assert changed == f1 - {1}
+    assert r2[0] == r1[0]
+    assert s2.vertices_ever_affected == meta["ever_after2"][0]
+    # Eq. 2 for vertex 2 in iteration 1 reads the new R[1]
+    C0 = (1 - ALPHA) / 6
+    expect2 = (C0 + ALPHA * (r1[0] / 3 + r1[1] / 3)) / (1 - ALPHA)
+    assert r2[2] == pytest.approx(expect2, rel=1e-14)
