@@ -14,8 +14,14 @@ e2e    = the same through host buffers: pinned host batches in, ranks of all
 roofline: the DF-P rank-sweep kernel, algorithmic bytes (12 B per processed
          in-edge + 60 B per processed vertex) over its CUDA-event time.
 
---impl reference times the CPU oracle (the plain C reference of the method)
-on a bounded sample of the same workload on the host cores.
+cpu_baseline / parity: before the timed steps, the CPU oracle (the plain C
+reference of the method, built with OpenMP over the host cores) runs one
+apply + DF-P update of the same workload at full size from its own Static
+ranks, which the GPU also takes; the GPU's ranks are compared with it
+element by element and the oracle's update is timed.
+
+--impl reference times the same oracle on a bounded sample of the workload
+(1/16 of the drawn edges per step) on the host cores.
 """
 from __future__ import annotations
 
@@ -36,7 +42,6 @@ METRIC = "DF-P batch-update time & HBM GB/s; served updates/s, p50/p99 vs plain 
 ALPHA, TAU = 0.85, 1e-10
 SWEEP_BYTES_PER_EDGE = 12
 SWEEP_BYTES_PER_VERTEX = 60
-SAMPLE_SCALE = 18
 # DRAM bytes (read + write) of one pull-form DF-P sweep (k_gather_rows + k_finish_pull) on the
 # default workload, from the one-pass ncu captures under profiles/, keyed by the gather setting
 # (threads, quads per lane, hub vertices, fused epilogue, ranges); a setting without a capture of the
@@ -132,18 +137,97 @@ class ClockSampler:
                 "reasons": reasons, "samples": len(rows)}
 
 
-# ------------------------------------------------------------------ CPU oracle sample
+# ------------------------------------------------------------------ CPU oracle
 
-def oracle_sample(a, steps=1):
-    """The oracle as it stands, single-threaded, on R-MAT scale SAMPLE_SCALE with
-    the same edge factor and batch fraction; returns (seconds per update, m)."""
+REF_SAMPLE_SCALE_DROP = 4   # the reference arm's per-step sample: 1/16 of the drawn edges
+
+
+def cpu_model():
+    """The host CPU's model name (lscpu, else /proc/cpuinfo)."""
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=20).stdout
+        for line in out.splitlines():
+            if line.lower().startswith("model name"):
+                return line.split(":", 1)[1].strip()
+    except (OSError, subprocess.SubprocessError):
+        pass
+    try:
+        for line in open("/proc/cpuinfo"):
+            if line.lower().startswith("model name"):
+                return line.split(":", 1)[1].strip()
+    except OSError:
+        pass
+    return "unknown"
+
+
+def full_size_parity(a, G, n, src_host, dst_host, batch_host):
+    """Parity and CPU baseline on the benchmark workload itself.
+
+    The oracle (the same C source built with OpenMP, every host core, the
+    same bits as its single-threaded build) builds the graph from the same
+    drawn edges and computes R_{t-1} by Static at tau = 1e-10.  Both sides take
+    those ranks (the GPU through pr_set_ranks), apply the same batch and run
+    DF-P; the GPU's ranks are compared with the oracle's element by element.
+    The oracle's apply + DF-P is the timed CPU baseline."""
+    import numpy as np
+
+    import oracle
+    t0 = time.perf_counter()
+    O = oracle.Graph(n, src_host, dst_host, parallel=True)
+    t_create = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    r0, st_static = O.update("static", alpha=ALPHA, tau=TAU)
+    t_static = time.perf_counter() - t0
+    G.set_ranks(r0)
+    G.apply_batch(*batch_host)
+    gst = G.update("dfp", alpha=ALPHA, tau=TAU)
+    r_gpu = G.ranks()
+    t0 = time.perf_counter()
+    O.apply_batch(*batch_host)
+    t_apply = time.perf_counter() - t0
+    ref, ost = O.update("dfp", alpha=ALPHA, tau=TAU, r_prev=r0)
+    t_update = time.perf_counter() - t0
+    linf = float(np.max(np.abs(r_gpu - ref)))
+    m_graph = O.m
+    del O
+    threads = oracle.threads()
+    same = (gst.iterations, gst.vertices_ever_affected, gst.vertices_processed) == \
+        (ost.iterations, ost.vertices_ever_affected, ost.vertices_processed)
+    parity = {
+        "what": "DF-P ranks of the whole graph after one batch of the benchmark workload, GPU against the oracle "
+                "from the same R_{t-1} (the oracle's Static, tau=1e-10), element by element",
+        "linf": linf, "tol": 1e-9, "pass": linf < 1e-9 and gst.iterations == ost.iterations,
+        "iterations": [gst.iterations, ost.iterations],
+        "vertices_ever_affected": [gst.vertices_ever_affected, ost.vertices_ever_affected],
+        "vertex_updates": [gst.vertices_processed, ost.vertices_processed],
+        "same_decisions": same,
+        # the nearest expand / prune / stop decision to its threshold (relative): where it is far below
+        # the GPU's relative error on those quantities, a decision may go the other way
+        "oracle_nearest_tie_rel": ost.tie_rel,
+        "oracle_static_iterations": st_static.iterations,
+        "oracle_seconds": {"create": t_create, "static": t_static, "apply": t_apply, "apply_dfp": t_update},
+    }
+    cb = {"value": 1.0 / t_update, "unit": "updates/s", "cores": threads, "kind": "oracle",
+          "cpu_model": cpu_model(),
+          "sample": "the whole workload, one update: oracle (plain C, the same source built with OpenMP, %d threads) "
+                    "apply + DF-P of one %d-edge batch on the full graph (%d vertices, %d edges) from its own "
+                    "Static ranks; %.1f s (apply %.1f s), not scaled"
+                    % (threads, len(batch_host[0]) + len(batch_host[2]), n, m_graph, t_update, t_apply)}
+    return parity, cb
+
+
+def reference_sample(a, steps):
+    """The reference arm's steps: the oracle (OpenMP build, every host core)
+    on R-MAT scale a.scale - REF_SAMPLE_SCALE_DROP with the same edge factor
+    and batch fraction, one apply + DF-P per step on the evolving graph;
+    returns (seconds per step, edges, scale)."""
     import oracle
     import synth
-    sc = min(SAMPLE_SCALE, a.scale)
+    sc = max(1, a.scale - REF_SAMPLE_SCALE_DROP)
     n = 1 << sc
     src, dst = synth.rmat(sc, a.edge_factor << sc, a.seed)
-    g = oracle.Graph(n, src, dst)
-    r, _ = g.update("static")
+    g = oracle.Graph(n, src, dst, parallel=True)
+    r, _ = g.update("static", alpha=ALPHA, tau=TAU)
     size = max(1, int(round(a.batch_frac * g.m)))
     times = []
     for i in range(steps):
@@ -153,17 +237,6 @@ def oracle_sample(a, steps=1):
         r, _ = g.update("dfp", alpha=ALPHA, tau=TAU, r_prev=r)
         times.append(time.perf_counter() - t0)
     return times, g.m, sc
-
-
-def cpu_baseline_entry(times, m_sample, sc, full_scale):
-    """Updates/s of the sample, scaled to the full workload by the ratio of drawn
-    edges (2^(sc - full_scale)): the work of an update grows with the edges."""
-    per = statistics.median(times)
-    scale = 2.0 ** (sc - full_scale)
-    return {"value": (1.0 / per) * scale, "unit": "updates/s", "cores": 1, "kind": "oracle",
-            "sample": ("oracle (plain C, 1 thread) apply + DF-P on R-MAT scale %d (%d edges, same edge factor), %d "
-                       "batch(es) of the same fraction; median %.3f s per update, scaled by the drawn-edge ratio "
-                       "2^%d to the full workload" % (sc, m_sample, len(times), per, sc - full_scale))}
 
 
 def replica_seed(seed, rank):
@@ -191,16 +264,24 @@ def job_rate(world, units_per_rank, ms):
 def run_reference(a, rank, world):
     if rank != 0:
         return
-    times, m_sample, sc = oracle_sample(a, steps=a.warmup + a.steps)
+    import oracle
+    times, m_sample, sc = reference_sample(a, a.warmup + a.steps)
     timed = times[a.warmup:] or times
-    cb = cpu_baseline_entry(timed, m_sample, sc, a.scale)
-    total = sum(timed)
-    line = {"metric": METRIC, "value": cb["value"], "unit": "updates/s", "n_gpus": world, "steps": len(timed),
-            "warmup": a.warmup, "ms_per_step": 1000.0 * total / len(timed), "higher_is_better": True,
+    per = statistics.median(timed)
+    ratio = 2.0 ** (sc - a.scale)
+    value = ratio / per
+    cb = {"value": value, "unit": "updates/s", "cores": oracle.threads(), "kind": "oracle", "cpu_model": cpu_model(),
+          "sample": "oracle (plain C, the same source built with OpenMP, %d threads) apply + DF-P per step on R-MAT "
+                    "scale %d (%d edges, the same edge factor and batch fraction), %d timed steps; median %.3f s per "
+                    "update, scaled by the drawn-edge ratio 2^%d to the full workload (one full-size update is "
+                    "measured by the GPU arm's cpu_baseline)" % (oracle.threads(), sc, m_sample, len(timed), per,
+                                                                  sc - a.scale)}
+    line = {"metric": METRIC, "value": value, "unit": "updates/s", "n_gpus": world, "steps": len(timed),
+            "warmup": a.warmup, "ms_per_step": 1000.0 * per / ratio, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": {"workload": workload_name(a), "inputs": "larger than L2", "sample_scale": sc},
             "impl": "reference", "cpu_baseline": cb,
-            "e2e": {"value": cb["value"], "unit": "updates/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+            "e2e": {"value": value, "unit": "updates/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
 
@@ -230,8 +311,17 @@ def run_gpu(a, rank, world, local_rank):
     for i in range(a.e2e_steps):
         bt = sg.batch(n, src, dst, size, seed + 100001 + i)
         host_batches.append([t.cpu().pin_memory() for t in bt])
+    parity_inputs = None
+    if not a.no_cpu_baseline and world == 1:
+        # the same drawn edges and one more batch, for the oracle
+        parity_inputs = (src.cpu().numpy(), dst.cpu().numpy(),
+                         [t.cpu().numpy() for t in sg.batch(n, src, dst, size, seed + 200001)])
     torch.cuda.synchronize()
     del src, dst
+    parity = cpu_base = None
+    if parity_inputs is not None:
+        parity, cpu_base = full_size_parity(a, G, n, *parity_inputs)
+        del parity_inputs
 
     def step(b):
         G.apply_batch_device(*b)
@@ -339,9 +429,9 @@ def run_gpu(a, rank, world, local_rank):
             / (st_nd.ms_sweep / 1000.0) / 1e9 if st_nd.ms_sweep else None,
         },
     }
-    if not a.no_cpu_baseline and world == 1:
-        times, m_sample, sc = oracle_sample(a, steps=1)
-        line["cpu_baseline"] = cpu_baseline_entry(times, m_sample, sc, a.scale)
+    if cpu_base is not None:
+        line["cpu_baseline"] = cpu_base
+        line["parity"] = parity
     print(json.dumps(line), flush=True)
 
 

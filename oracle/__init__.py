@@ -1,9 +1,10 @@
 """CPU oracle for the DF / DF-P PageRank update (arXiv 2401.15870).
 
-TEST INFRASTRUCTURE ONLY: a plain, slow, single-threaded FP64 C
-implementation (``dfpr_oracle.c``) of Static, Naive-dynamic, Dynamic
-Traversal, DF and DF-P PageRank, in the synchronous order, with the batch
-update of Sec. 3.2.  Only the tests, the package smoke check and the
+TEST INFRASTRUCTURE ONLY: a plain, slow FP64 C implementation
+(``dfpr_oracle.c``) of Static, Naive-dynamic, Dynamic Traversal, DF and DF-P
+PageRank, in the synchronous order, with the batch update of Sec. 3.2.  It is
+built single-threaded, and from the same source with OpenMP for the large
+workloads (``Graph(..., parallel=True)``): both builds return the same bits.  Only the tests, the package smoke check and the
 benchmark's CPU-baseline leg may import this module.  It shares no code with
 the CUDA library and never imports it.
 
@@ -37,6 +38,9 @@ import numpy as np
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "dfpr_oracle.c")
 _LIB = os.path.join(_HERE, "liboracle.so")
+# the same source built with -fopenmp: synchronous sweeps, sorts and the
+# adjacency rebuild on every host core, bit-identical results
+_LIB_OMP = os.path.join(_HERE, "liboracle_omp.so")
 
 STATIC, NAIVE_DYNAMIC, DYNAMIC_TRAVERSAL, DF, DFP = 0, 1, 2, 3, 4
 METHODS = {"static": STATIC, "nd": NAIVE_DYNAMIC, "dt": DYNAMIC_TRAVERSAL, "df": DF, "dfp": DFP}
@@ -46,22 +50,40 @@ ORDERS = {"sync": 0, "async": 1}
 _ERR = {1: "invalid argument", 2: "vertex id out of range", 3: "out of memory", 4: "no previous ranks"}
 
 
-def build(force: bool = False) -> str:
-    """Compile the oracle with gcc (plain -O2, IEEE FP64)."""
-    if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
-        tmp = _LIB + ".tmp%d" % os.getpid()
-        subprocess.check_call(["gcc", "-O2", "-std=c11", "-shared", "-fPIC", _SRC, "-o", tmp, "-lm"])
-        os.replace(tmp, _LIB)
-    return _LIB
+def _compile(lib: str, extra, force: bool) -> str:
+    if force or not os.path.exists(lib) or os.path.getmtime(lib) < os.path.getmtime(_SRC):
+        tmp = lib + ".tmp%d" % os.getpid()
+        subprocess.check_call(["gcc", "-O2", "-std=c11", *extra, "-shared", "-fPIC", _SRC, "-o", tmp, "-lm"])
+        os.replace(tmp, lib)
+    return lib
 
 
-_lib = None
+def build(force: bool = False, parallel: bool = None) -> str:
+    """Compile the oracle with gcc (plain -O2, IEEE FP64): liboracle.so, and
+    liboracle_omp.so from the same source with -fopenmp.  parallel=None builds
+    both and returns the plain one's path."""
+    if parallel is None:
+        _compile(_LIB_OMP, ["-fopenmp"], force)
+        return _compile(_LIB, [], force)
+    return _compile(_LIB_OMP, ["-fopenmp"], force) if parallel else _compile(_LIB, [], force)
 
 
-def _load():
-    global _lib
-    if _lib is None:
-        lib = ctypes.CDLL(build())
+_libs = {}
+
+
+def set_threads(k: int) -> None:
+    """Threads of the OpenMP build (it uses every host core by default)."""
+    _load(True).or_set_threads(int(k))
+
+
+def threads(parallel: bool = True) -> int:
+    return _load(parallel).or_threads()
+
+
+def _load(parallel: bool = False):
+    lib = _libs.get(parallel)
+    if lib is None:
+        lib = ctypes.CDLL(build(parallel=parallel))
         P = ctypes.c_void_p
         i32, i64, f64 = ctypes.c_int32, ctypes.c_int64, ctypes.c_double
         lib.or_graph_create.argtypes = [i32, i64, P, P, ctypes.POINTER(P)]
@@ -88,8 +110,10 @@ def _load():
         lib.or_update.restype = ctypes.c_int
         lib.or_update_ex.argtypes = [P, ctypes.c_int, f64, f64, f64, f64, i32, ctypes.c_int, ctypes.c_int, P, P, P]
         lib.or_update_ex.restype = ctypes.c_int
-        _lib = lib
-    return _lib
+        lib.or_threads.restype = ctypes.c_int
+        lib.or_set_threads.argtypes = [ctypes.c_int]
+        _libs[parallel] = lib
+    return lib
 
 
 class _Stats(ctypes.Structure):
@@ -135,10 +159,11 @@ def rank_closed_loop(alpha: float, n: int, c: float, Rv: float, d: int) -> float
 
 
 class Graph:
-    """Edge set over [0, n) with one self-loop per vertex (Sec. 5.1.3)."""
+    """Edge set over [0, n) with one self-loop per vertex (Sec. 5.1.3).
+    parallel=True runs it on the OpenMP build (same results, bit for bit)."""
 
-    def __init__(self, n: int, src, dst):
-        lib = _load()
+    def __init__(self, n: int, src, dst, parallel: bool = False):
+        self._lib = lib = _load(bool(parallel))
         s, d = _i32(src), _i32(dst)
         if s.shape != d.shape:
             raise ValueError("src and dst differ in length")
@@ -150,42 +175,42 @@ class Graph:
 
     def __del__(self):
         h = getattr(self, "_h", None)
-        if h and _lib is not None:
-            _lib.or_graph_destroy(h)
+        if h and getattr(self, "_lib", None) is not None:
+            self._lib.or_graph_destroy(h)
             self._h = None
 
     @property
     def n(self) -> int:
-        return _load().or_num_vertices(self._h)
+        return self._lib.or_num_vertices(self._h)
 
     @property
     def m(self) -> int:
-        return _load().or_num_edges(self._h)
+        return self._lib.or_num_edges(self._h)
 
     def apply_batch(self, del_src=(), del_dst=(), ins_src=(), ins_dst=()):
         """Deletions, then insertions, set semantics (Sec. 3.2)."""
         ds, dd, is_, id_ = _i32(del_src), _i32(del_dst), _i32(ins_src), _i32(ins_dst)
         if ds.shape != dd.shape or is_.shape != id_.shape:
             raise ValueError("endpoint arrays differ in length")
-        rc = _load().or_apply_batch(self._h, _ptr(ds), _ptr(dd), ds.size, _ptr(is_), _ptr(id_), is_.size)
+        rc = self._lib.or_apply_batch(self._h, _ptr(ds), _ptr(dd), ds.size, _ptr(is_), _ptr(id_), is_.size)
         if rc:
             raise OracleError(_ERR.get(rc, str(rc)))
 
     def out_csr(self):
         off = np.zeros(self.n + 1, np.int64)
         adj = np.zeros(max(self.m, 1), np.int32)
-        _load().or_get_out_csr(self._h, off.ctypes.data, adj.ctypes.data)
+        self._lib.or_get_out_csr(self._h, off.ctypes.data, adj.ctypes.data)
         return off, adj[: self.m]
 
     def in_csr(self):
         off = np.zeros(self.n + 1, np.int64)
         adj = np.zeros(max(self.m, 1), np.int32)
-        _load().or_get_in_csr(self._h, off.ctypes.data, adj.ctypes.data)
+        self._lib.or_get_in_csr(self._h, off.ctypes.data, adj.ctypes.data)
         return off, adj[: self.m]
 
     def effective_delta(self):
         """(Delta-, Delta+) of the last batch as sorted (k, 2) int arrays of (src, dst)."""
-        lib = _load()
+        lib = self._lib
         nd, ni = lib.or_num_eff_del(self._h), lib.or_num_eff_ins(self._h)
         d = np.zeros(max(nd, 1), np.uint64)
         i = np.zeros(max(ni, 1), np.uint64)
@@ -197,12 +222,12 @@ class Graph:
 
     def initial_affected(self) -> np.ndarray:
         f = np.zeros(self.n, np.uint8)
-        _load().or_initial_affected(self._h, f.ctypes.data)
+        self._lib.or_initial_affected(self._h, f.ctypes.data)
         return f.astype(bool)
 
     def dt_affected(self) -> np.ndarray:
         f = np.zeros(self.n, np.uint8)
-        if _load().or_dt_affected(self._h, f.ctypes.data):
+        if self._lib.or_dt_affected(self._h, f.ctypes.data):
             raise OracleError("out of memory")
         return f.astype(bool)
 
@@ -217,7 +242,7 @@ class Graph:
         if prev is not None and prev.size != self.n:
             raise ValueError("r_prev has the wrong length")
         st = _Stats()
-        rc = _load().or_update_ex(self._h, m, alpha, tau, tau_f, tau_p, int(max_iter), METRICS[metric],
+        rc = self._lib.or_update_ex(self._h, m, alpha, tau, tau_f, tau_p, int(max_iter), METRICS[metric],
                                   ORDERS[order], None if prev is None else prev.ctypes.data, out.ctypes.data,
                                   ctypes.byref(st))
         if rc:

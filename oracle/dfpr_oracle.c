@@ -43,11 +43,24 @@
  *
  * Build: gcc -O2 -std=c11 -shared -fPIC dfpr_oracle.c -o liboracle.so
  * (no -ffast-math: IEEE round-to-nearest FP64 throughout).
+ *
+ * The same source built with -fopenmp (liboracle_omp.so) spreads the
+ * synchronous sweeps, the sorts and the adjacency rebuild over the host's
+ * cores, so that the oracle can also run the large workloads.  Each vertex of
+ * a synchronous sweep is still computed alone, by the same instructions on the
+ * same inputs (the ranks of the start of the iteration), and flags are only
+ * ever set to one value in an iteration; maxima, minima and counts do not
+ * depend on the order they are combined in.  The threaded build therefore
+ * returns bit for bit what the single-threaded build returns.  The
+ * asynchronous order stays sequential in both.
  */
 #include <stdint.h>
 #include <stdlib.h>
 #include <string.h>
 #include <math.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
 
 enum { OR_STATIC = 0, OR_NAIVE_DYNAMIC = 1, OR_DYNAMIC_TRAVERSAL = 2, OR_DF = 3, OR_DFP = 4 };
 enum { OR_OK = 0, OR_EINVAL = 1, OR_ERANGE = 2, OR_ENOMEM = 3, OR_ENORANKS = 4 };
@@ -91,10 +104,72 @@ static int cmp_u64(const void *a, const void *b) {
   return (x > y) - (x < y);
 }
 
+static int cmp_i32(const void *a, const void *b) {
+  int32_t x = *(const int32_t *)a, y = *(const int32_t *)b;
+  return (x > y) - (x < y);
+}
+
+/* threads of the OpenMP build (1 in the plain build) */
+static int n_threads(void) {
+#ifdef _OPENMP
+  return omp_get_max_threads();
+#else
+  return 1;
+#endif
+}
+int or_threads(void) { return n_threads(); }
+void or_set_threads(int t) {
+#ifdef _OPENMP
+  if (t > 0) omp_set_num_threads(t);
+#else
+  (void)t;
+#endif
+}
+
+/* merge the sorted runs a[0..la) and b[0..lb) into out */
+static void merge_u64(const uint64_t *a, int64_t la, const uint64_t *b, int64_t lb, uint64_t *out) {
+  int64_t i = 0, j = 0, w = 0;
+  while (i < la && j < lb) out[w++] = (b[j] < a[i]) ? b[j++] : a[i++];
+  while (i < la) out[w++] = a[i++];
+  while (j < lb) out[w++] = b[j++];
+}
+
+/* ascending sort of k[0..len): one qsort, or with several threads one qsort
+ * per thread over equal runs followed by rounds of pairwise merges */
+static void sort_u64(uint64_t *k, int64_t len) {
+  int T = n_threads();
+  if (T <= 1 || len < ((int64_t)1 << 22)) {
+    qsort(k, (size_t)len, sizeof(uint64_t), cmp_u64);
+    return;
+  }
+  int64_t *bnd = (int64_t *)malloc(sizeof(int64_t) * (size_t)(T + 1));
+  uint64_t *tmp = (uint64_t *)malloc(sizeof(uint64_t) * (size_t)len);
+  if (!bnd || !tmp) {
+    free(bnd); free(tmp);
+    qsort(k, (size_t)len, sizeof(uint64_t), cmp_u64);
+    return;
+  }
+  for (int i = 0; i <= T; i++) bnd[i] = len / T * i + (len % T) * i / T;
+  bnd[T] = len;
+#pragma omp parallel for schedule(static, 1)
+  for (int i = 0; i < T; i++) qsort(k + bnd[i], (size_t)(bnd[i + 1] - bnd[i]), sizeof(uint64_t), cmp_u64);
+  uint64_t *from = k, *to = tmp;
+  for (int w = 1; w < T; w *= 2) {
+#pragma omp parallel for schedule(dynamic, 1)
+    for (int i = 0; i < T; i += 2 * w) {
+      int mid = i + w < T ? i + w : T, hi = i + 2 * w < T ? i + 2 * w : T;
+      merge_u64(from + bnd[i], bnd[mid] - bnd[i], from + bnd[mid], bnd[hi] - bnd[mid], to + bnd[i]);
+    }
+    uint64_t *x = from; from = to; to = x;
+  }
+  if (from != k) memcpy(k, from, sizeof(uint64_t) * (size_t)len);
+  free(tmp); free(bnd);
+}
+
 /* sort and drop repeated keys in place; returns the new length */
 static int64_t sort_unique(uint64_t *k, int64_t len) {
   if (len == 0) return 0;
-  qsort(k, (size_t)len, sizeof(uint64_t), cmp_u64);
+  sort_u64(k, len);
   int64_t w = 1;
   for (int64_t i = 1; i < len; i++)
     if (k[i] != k[w - 1]) k[w++] = k[i];
@@ -152,24 +227,38 @@ static int rebuild_adjacency(or_graph *g) {
   g->out_adj = (int32_t *)malloc(sizeof(int32_t) * (size_t)(m > 0 ? m : 1));
   g->in_adj = (int32_t *)malloc(sizeof(int32_t) * (size_t)(m > 0 ? m : 1));
   if (!g->out_off || !g->in_off || !g->out_adj || !g->in_adj) return OR_ENOMEM;
+  /* keys are sorted by (src, dst): out-row u is the key range of source u,
+   * already sorted by dst */
+#pragma omp parallel for schedule(static)
+  for (int64_t v = 0; v <= (int64_t)n; v++)
+    g->out_off[v] = v == n ? m : lower_bound(g->keys, m, key_of((int32_t)v, 0));
+#pragma omp parallel for schedule(static)
   for (int64_t i = 0; i < m; i++) {
-    g->out_off[key_src(g->keys[i]) + 1]++;
-    g->in_off[key_dst(g->keys[i]) + 1]++;
+    g->out_adj[i] = key_dst(g->keys[i]);
+    int32_t d = key_dst(g->keys[i]);
+#pragma omp atomic
+    g->in_off[d + 1]++;
   }
-  for (int32_t v = 0; v < n; v++) {
-    g->out_off[v + 1] += g->out_off[v];
-    g->in_off[v + 1] += g->in_off[v];
-  }
-  /* keys are sorted by (src, dst): a linear pass gives out-rows sorted by dst
-   * and, bucketing by dst in that order, in-rows sorted by src */
+  for (int32_t v = 0; v < n; v++) g->in_off[v + 1] += g->in_off[v];
+  /* bucket by dst: in key order this gives in-rows sorted by src; threads
+   * fill the buckets in any order, and each in-row is sorted afterwards */
   int64_t *fill = (int64_t *)malloc(sizeof(int64_t) * (size_t)(n > 0 ? n : 1));
   if (!fill) return OR_ENOMEM;
   for (int32_t v = 0; v < n; v++) fill[v] = g->in_off[v];
+#pragma omp parallel for schedule(static)
   for (int64_t i = 0; i < m; i++) {
-    g->out_adj[i] = key_dst(g->keys[i]);
-    g->in_adj[fill[key_dst(g->keys[i])]++] = key_src(g->keys[i]);
+    int32_t d = key_dst(g->keys[i]);
+    int64_t at;
+#pragma omp atomic capture
+    at = fill[d]++;
+    g->in_adj[at] = key_src(g->keys[i]);
   }
   free(fill);
+  if (n_threads() > 1) {
+#pragma omp parallel for schedule(dynamic, 4096)
+    for (int32_t v = 0; v < n; v++)
+      qsort(g->in_adj + g->in_off[v], (size_t)(g->in_off[v + 1] - g->in_off[v]), sizeof(int32_t), cmp_i32);
+  }
   return OR_OK;
 }
 
@@ -192,10 +281,10 @@ int or_graph_create(int32_t n, int64_t m, const int32_t *src, const int32_t *dst
   g->n = n;
   g->keys = (uint64_t *)malloc(sizeof(uint64_t) * (size_t)(m + n));
   if (!g->keys) { free(g); return OR_ENOMEM; }
-  int64_t len = 0;
-  for (int64_t i = 0; i < m; i++) g->keys[len++] = key_of(src[i], dst[i]);
-  for (int32_t v = 0; v < n; v++) g->keys[len++] = key_of(v, v);
-  g->m = sort_unique(g->keys, len);
+#pragma omp parallel for schedule(static)
+  for (int64_t i = 0; i < m; i++) g->keys[i] = key_of(src[i], dst[i]);
+  for (int32_t v = 0; v < n; v++) g->keys[m + v] = key_of(v, v);
+  g->m = sort_unique(g->keys, m + n);
   int rc = rebuild_adjacency(g);
   if (rc != OR_OK) { or_graph_destroy(g); return rc; }
   *out = g;
@@ -326,13 +415,14 @@ int or_dt_affected(const or_graph *g, uint8_t *flag) {
 
 /* ---- rank update ---- */
 
-/* c = sum over u in G_t.in(v) of R[u] / |G_t.out(u)|, in ascending u (Eq. 1) */
-static double in_sum(const or_graph *g, const double *R, int32_t v) {
+/* |G_t.out(u)| */
+static int64_t out_degree(const or_graph *g, int32_t u) { return g->out_off[u + 1] - g->out_off[u]; }
+
+/* c = sum over u in G_t.in(v) of R[u] / |G_t.out(u)|, in ascending u (Eq. 1);
+ * K[u] holds R[u] / |G_t.out(u)|, the quotient taken once per vertex */
+static double in_sum(const or_graph *g, const double *K, int32_t v) {
   double c = 0.0;
-  for (int64_t j = g->in_off[v]; j < g->in_off[v + 1]; j++) {
-    int32_t u = g->in_adj[j];
-    c += R[u] / (double)(g->out_off[u + 1] - g->out_off[u]);
-  }
+  for (int64_t j = g->in_off[v]; j < g->in_off[v + 1]; j++) c += K[g->in_adj[j]];
   return c;
 }
 
@@ -378,6 +468,59 @@ static double tie_to(double x, double t) {
   return fabs(x / t - 1.0);
 }
 
+/* What one sweep over the processed vertices gathers for the statistics. */
+typedef struct {
+  double dR, tie;
+  int64_t vertices, edges;
+} sweep_sum;
+
+/* The fixed arguments of one method run. */
+typedef struct {
+  double alpha, tau_f, tau_p;
+  int metric, frontier, prune, async;
+} run_args;
+
+/*
+ * Process vertex v in one iteration of Alg. 1 (Eq. 1, or Eq. 2 for DF-P),
+ * reading the ranks R and their quotients K.  Writes the new rank to Rw[v] and
+ * the flags of the next frontier to Fw.  Synchronous order: R, K are the
+ * ranks of the start of the iteration and Fw is F_{i+1} (v stays unless
+ * pruned; expansion marks G_t.out(v)).  Asynchronous order: Rw == R,
+ * Fw is the one flag vector (pruning clears v, expansion sets G_t.out(v)),
+ * and K[v] follows the new rank at once.
+ */
+static void visit(const or_graph *g, const run_args *a, int32_t v, const double *R, double *K, double *Rw,
+                  uint8_t *Fw, uint8_t *ever, sweep_sum *acc) {
+  int32_t n = g->n;
+  ever[v] = 1;                                              /* processed in some sweep */
+  double c = in_sum(g, K, v);
+  int64_t d = out_degree(g, v);
+  double Rv = R[v];
+  double r = a->prune ? or_rank_closed_loop(a->alpha, n, c, Rv, d) : or_rank_plain(a->alpha, n, c);
+  double dr = fabs(r - Rv);
+  if (dr > acc->dR) acc->dR = dr;
+  acc->vertices++;
+  acc->edges += g->in_off[v + 1] - g->in_off[v];
+  if (a->frontier) {
+    double mv = frontier_measure(a->metric, dr, r, Rv, d);
+    acc->tie = fmin(acc->tie, tie_to(mv, a->tau_f));
+    if (a->prune) acc->tie = fmin(acc->tie, tie_to(mv, a->tau_p));
+    if (a->async) {
+      if (a->prune && mv <= a->tau_p) Fw[v] = 0;            /* mark v as not affected */
+    } else if (!(a->prune && mv <= a->tau_p)) {
+#pragma omp atomic write
+      Fw[v] = 1;                                            /* v stays unless pruned */
+    }
+    if (mv > a->tau_f)                                      /* expand: mark G_t.out(v) */
+      for (int64_t j = g->out_off[v]; j < g->out_off[v + 1]; j++) {
+#pragma omp atomic write
+        Fw[g->out_adj[j]] = 1;
+      }
+  }
+  Rw[v] = r;
+  if (a->async) K[v] = r / (double)d;
+}
+
 /*
  * One method run (Sec. 3.1, Sec. 3.3, Alg. 1).
  * r_prev: ranks of the previous snapshot (ignored by Static, required by the
@@ -394,72 +537,72 @@ int or_update_ex(const or_graph *g, int method, double alpha, double tau, double
   if (method != OR_STATIC && !r_prev) return OR_ENORANKS;
   double *R = (double *)malloc(sizeof(double) * (size_t)n);
   double *Rn = (double *)malloc(sizeof(double) * (size_t)n);
+  double *K = (double *)malloc(sizeof(double) * (size_t)n);  /* R[u] / |G_t.out(u)| */
   uint8_t *F = (uint8_t *)calloc((size_t)n, 1);      /* vertices processed in this iteration */
   uint8_t *Fn = (uint8_t *)calloc((size_t)n, 1);     /* F_{i+1} */
   uint8_t *ever = (uint8_t *)calloc((size_t)n, 1);
-  if (!R || !Rn || !F || !Fn || !ever) { free(R); free(Rn); free(F); free(Fn); free(ever); return OR_ENOMEM; }
+  if (!R || !Rn || !K || !F || !Fn || !ever) {
+    free(R); free(Rn); free(K); free(F); free(Fn); free(ever);
+    return OR_ENOMEM;
+  }
 
   if (method == OR_STATIC) for (int32_t v = 0; v < n; v++) R[v] = 1.0 / (double)n;
   else memcpy(R, r_prev, sizeof(double) * (size_t)n);
 
   if (method == OR_STATIC || method == OR_NAIVE_DYNAMIC) memset(F, 1, (size_t)n);
   else if (method == OR_DYNAMIC_TRAVERSAL) {
-    if (or_dt_affected(g, F) != OR_OK) { free(R); free(Rn); free(F); free(Fn); free(ever); return OR_ENOMEM; }
+    if (or_dt_affected(g, F) != OR_OK) {
+      free(R); free(Rn); free(K); free(F); free(Fn); free(ever);
+      return OR_ENOMEM;
+    }
   } else or_initial_affected(g, F);
 
-  int frontier = (method == OR_DF || method == OR_DFP);
-  int prune = (method == OR_DFP);
-  int async = (order == OR_ORDER_ASYNC);
+  run_args a = {alpha, tau_f, tau_p, metric, method == OR_DF || method == OR_DFP, method == OR_DFP,
+                order == OR_ORDER_ASYNC};
   or_stats s;
   memset(&s, 0, sizeof(s));
   s.tie_rel = INFINITY;
   for (int32_t i = 0; i < max_iter; i++) {
-    double dR = 0.0;
-    /* synchronous: new ranks and flags go to Rn / Fn and are committed after
-     * the sweep; asynchronous: R and F themselves are written */
-    double *Rw = async ? R : Rn;
-    uint8_t *Fw = async ? F : Fn;
-    if (!async) {
+#pragma omp parallel for schedule(static)
+    for (int32_t u = 0; u < n; u++) K[u] = R[u] / (double)out_degree(g, u);
+    sweep_sum tot = {0.0, INFINITY, 0, 0};
+    if (a.async) {
+      /* one rank vector and one flag vector, ascending vertex id */
+      for (int32_t v = 0; v < n; v++)
+        if (F[v]) visit(g, &a, v, R, K, R, F, ever, &tot);
+    } else {
+      /* new ranks and flags go to Rn / Fn and are committed after the sweep */
       memcpy(Rn, R, sizeof(double) * (size_t)n);
-      if (frontier) memset(Fn, 0, (size_t)n);
-    }
-    for (int32_t v = 0; v < n; v++) {
-      if (!F[v]) continue;
-      ever[v] = 1;                                          /* processed in some sweep */
-      double c = in_sum(g, R, v);
-      int64_t d = g->out_off[v + 1] - g->out_off[v];
-      double r = prune ? or_rank_closed_loop(alpha, n, c, R[v], d) : or_rank_plain(alpha, n, c);
-      double dr = fabs(r - R[v]);
-      if (dr > dR) dR = dr;
-      s.vertices_processed++;
-      s.edges_processed += g->in_off[v + 1] - g->in_off[v];
-      if (frontier) {
-        double mv = frontier_measure(metric, dr, r, R[v], d);
-        s.tie_rel = fmin(s.tie_rel, tie_to(mv, tau_f));
-        if (prune) s.tie_rel = fmin(s.tie_rel, tie_to(mv, tau_p));
-        if (async) {
-          if (prune && mv <= tau_p) Fw[v] = 0;              /* mark v as not affected */
-        } else if (!(prune && mv <= tau_p)) {
-          Fw[v] = 1;                                        /* v stays unless pruned */
+      if (a.frontier) memset(Fn, 0, (size_t)n);
+#pragma omp parallel
+      {
+        sweep_sum part = {0.0, INFINITY, 0, 0};
+#pragma omp for schedule(dynamic, 1024)
+        for (int32_t v = 0; v < n; v++)
+          if (F[v]) visit(g, &a, v, R, K, Rn, Fn, ever, &part);
+#pragma omp critical
+        {
+          if (part.dR > tot.dR) tot.dR = part.dR;
+          tot.tie = fmin(tot.tie, part.tie);
+          tot.vertices += part.vertices;
+          tot.edges += part.edges;
         }
-        if (mv > tau_f)                                     /* expand: mark G_t.out(v) */
-          for (int64_t j = g->out_off[v]; j < g->out_off[v + 1]; j++) Fw[g->out_adj[j]] = 1;
       }
-      Rw[v] = r;
-    }
-    if (!async) {
       memcpy(R, Rn, sizeof(double) * (size_t)n);
-      if (frontier) memcpy(F, Fn, (size_t)n);
+      if (a.frontier) memcpy(F, Fn, (size_t)n);
     }
+    s.vertices_processed += tot.vertices;
+    s.edges_processed += tot.edges;
+    s.tie_rel = fmin(s.tie_rel, tot.tie);
     s.iterations = i + 1;
-    s.delta_R = dR;
-    s.tie_rel = fmin(s.tie_rel, tie_to(dR, tau));
-    if (dR <= tau) { s.converged = 1; break; }
+    s.delta_R = tot.dR;
+    s.tie_rel = fmin(s.tie_rel, tie_to(tot.dR, tau));
+    if (tot.dR <= tau) { s.converged = 1; break; }
   }
   for (int32_t v = 0; v < n; v++) s.vertices_ever_affected += ever[v];
   memcpy(r_out, R, sizeof(double) * (size_t)n);
   if (st) *st = s;
-  free(R); free(Rn); free(F); free(Fn); free(ever);
+  free(R); free(Rn); free(K); free(F); free(Fn); free(ever);
   return OR_OK;
 }
 

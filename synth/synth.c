@@ -26,6 +26,9 @@
 #include <stdint.h>
 #include <stdlib.h>
 
+/* Built with -fopenmp; the draws are counter-based, so the output does not
+ * depend on the number of threads. */
+
 static uint64_t mix64(uint64_t z) {
   z = (z ^ (z >> 30)) * 0xbf58476d1ce4e5b9ULL;
   z = (z ^ (z >> 27)) * 0x94d049bb133111ebULL;
@@ -70,6 +73,9 @@ void sy_rmat(int scale, int64_t m, uint64_t seed, int32_t a, int32_t b, int32_t 
   uint64_t t1 = ((uint64_t)a << 32) / 10000;
   uint64_t t2 = ((uint64_t)(a + b) << 32) / 10000;
   uint64_t t3 = ((uint64_t)(a + b + c) << 32) / 10000;
+  /* every edge depends only on its own counter: the threads of an OpenMP
+   * build draw the same list */
+#pragma omp parallel for schedule(static)
   for (int64_t e = 0; e < m; e++) {
     uint32_t u = 0, v = 0;
     uint64_t w = 0;

@@ -549,3 +549,53 @@ def test_pruned_vertex_re_marked_by_expanding_in_neighbour():
     C0 = (1 - ALPHA) / 6
     expect2 = (C0 + ALPHA * (r1[0] / 3 + r1[1] / 3)) / (1 - ALPHA)
     assert r2[2] == pytest.approx(expect2, rel=1e-14)
+
+
+# ------------------------------------------------------------ the OpenMP build of the oracle
+
+
+@pytest.mark.parametrize("seed", [1, 2])
+def test_openmp_build_gives_the_same_bits(seed):
+    """The oracle built with -fopenmp (threaded sweeps, sorts and adjacency
+    rebuild) returns exactly what the single-threaded build returns: the same
+    edge sets, effective changes, affected sets, ranks and statistics for every
+    method, measure and order, over a chain of batches."""
+    oracle.set_threads(4)
+    assert oracle.threads() == 4
+    scale = 12
+    n = 1 << scale
+    src, dst = synth.rmat(scale, 16 * n, 600 + seed)
+    A, B = oracle.Graph(n, src, dst), oracle.Graph(n, src, dst, parallel=True)
+    for x, y in zip(A.out_csr() + A.in_csr(), B.out_csr() + B.in_csr()):
+        assert np.array_equal(x, y)
+    ra, sa = A.update("static")
+    rb, sb = B.update("static")
+    assert np.array_equal(ra, rb) and sa == sb
+    cs, cd = synth.unique_edges(src, dst)
+    for step in range(3):
+        b = synth.batch(n, cs, cd, 50 + 400 * step, 700 + seed * 10 + step)
+        A.apply_batch(*b)
+        B.apply_batch(*b)
+        for x, y in zip(A.out_csr() + A.in_csr() + A.effective_delta(), B.out_csr() + B.in_csr() + B.effective_delta()):
+            assert np.array_equal(x, y)
+        assert np.array_equal(A.initial_affected(), B.initial_affected())
+        for method in ("static", "nd", "dt", "df", "dfp"):
+            for metric, order in (("relative", "sync"), ("absolute", "sync"), ("relative", "async")):
+                tf = 1e-12 if metric == "absolute" else 1e-6
+                x, s1 = A.update(method, r_prev=ra, metric=metric, order=order, tau_f=tf, tau_p=tf)
+                y, s2 = B.update(method, r_prev=ra, metric=metric, order=order, tau_f=tf, tau_p=tf)
+                assert np.array_equal(x, y), (step, method, metric, order)
+                assert s1 == s2, (step, method, metric, order)
+        ra, _ = A.update("dfp", r_prev=ra)
+
+
+def test_openmp_build_sorts_large_edge_lists():
+    """Edge lists long enough for the threaded sort (runs sorted per thread,
+    then merged) build the same graph as the single-threaded build."""
+    oracle.set_threads(3)
+    n = 1 << 16
+    src, dst = synth.rmat(16, 5_000_000, 77)
+    A, B = oracle.Graph(n, src, dst), oracle.Graph(n, src, dst, parallel=True)
+    assert A.m == B.m
+    for x, y in zip(A.out_csr() + A.in_csr(), B.out_csr() + B.in_csr()):
+        assert np.array_equal(x, y)
