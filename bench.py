@@ -46,7 +46,7 @@ SWEEP_BYTES_PER_VERTEX = 60
 # default workload, from the one-pass ncu captures under profiles/, keyed by the gather setting
 # (threads, quads per lane, hub vertices, fused epilogue, ranges); a setting without a capture of the
 # current kernels reports null
-SWEEP_DRAM_BYTES_RMAT25 = {(1024, 2, 0, 0, 1): 11.44e9}
+SWEEP_DRAM_BYTES_RMAT25 = {}
 
 
 def parse():
@@ -62,7 +62,7 @@ def parse():
     ap.add_argument("--e2e-steps", type=int, default=5)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--workload", default="large",
-                    choices=["large", "batched", "serving", "methods", "temporal", "tolerances"],
+                    choices=["large", "batched", "serving", "methods", "temporal", "tolerances", "orders", "settings"],
                     help="large: one R-MAT scale-25 graph (default); batched: a group of R-MAT graphs updated "
                          "together; serving: Poisson request arrivals for resident graphs")
     ap.add_argument("--rates", default="50,200,500,1000,2000", help="serving: arrival rates (requests/s)")
@@ -323,9 +323,14 @@ def run_gpu(a, rank, world, local_rank):
         parity, cpu_base = full_size_parity(a, G, n, *parity_inputs)
         del parity_inputs
 
-    def step(b):
+    sweep_records = []
+
+    def step(b, log=False):
         G.apply_batch_device(*b)
-        return G.update("dfp", alpha=ALPHA, tau=TAU, time_sweeps=True)
+        st = G.update("dfp", alpha=ALPHA, tau=TAU, time_sweeps=True)
+        if log:
+            sweep_records.extend(G.sweep_log())
+        return st
 
     # the first warm-up step tunes the sweep setting on its own update: every
     # candidate runs that DF-P update from the same ranks (same bits each time)
@@ -349,7 +354,7 @@ def run_gpu(a, rank, world, local_rank):
     ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     torch.cuda.synchronize()
     ev0.record(stream)
-    stats = [step(dev_batches[a.warmup + i]) for i in range(a.steps)]
+    stats = [step(dev_batches[a.warmup + i], log=True) for i in range(a.steps)]
     ev1.record(stream)
     torch.cuda.synchronize()
     launches = pr.pr_kernel_launches() - l0
@@ -358,10 +363,17 @@ def run_gpu(a, rank, world, local_rank):
     value = job_rate(world, a.steps, ms)
 
     sweep_ms = sum(s.ms_sweep for s in stats)
-    sweep_bytes = sum(SWEEP_BYTES_PER_EDGE * s.edges_processed + SWEEP_BYTES_PER_VERTEX * s.vertices_processed
-                      for s in stats)
     sweeps = sum(s.sweeps for s in stats)
-    achieved = sweep_bytes / (sweep_ms / 1000.0) / 1e9 if sweep_ms > 0 else 0.0
+    # the dominant kernel: the every-vertex (pull) sweep, k_gather_rows + k_finish_pull; the list (push)
+    # sweeps of the first iterations are another kernel, reported beside it
+    def alg_bytes(recs):
+        return sum(SWEEP_BYTES_PER_EDGE * r[3] + SWEEP_BYTES_PER_VERTEX * r[4] for r in recs)
+    pull = [r for r in sweep_records if r[1] == pr.PR_SWEEP_EVERY_VERTEX]
+    push = [r for r in sweep_records if r[1] == pr.PR_SWEEP_LIST]
+    pull_ms = sum(r[2] for r in pull)
+    push_ms = sum(r[2] for r in push)
+    achieved = alg_bytes(pull) / (pull_ms / 1000.0) / 1e9 if pull_ms > 0 else 0.0
+    all_gbs = (alg_bytes(sweep_records) / ((pull_ms + push_ms) / 1000.0) / 1e9) if pull_ms + push_ms > 0 else 0.0
     peaks = {}
     try:
         peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
@@ -399,8 +411,9 @@ def run_gpu(a, rank, world, local_rank):
         "config": {"workload": workload_name(a), "vertices": n, "edges": m0, "batch_edges": size,
                    "inputs": "larger than L2 (graph ~%.0f GB resident)" % (m0 * 8 * 1.2 / 1e9),
                    "parallelism": "replicas" if world > 1 else "single GPU"},
-        "roofline": {"bound": "hbm", "kernel": "DF-P rank sweep (k_gather_rows + k_finish_pull in pull form, "
-                               "k_sweep<DFP> in push form)", "achieved": achieved, "peak": peak,
+        "roofline": {"bound": "hbm", "kernel": "DF-P every-vertex (pull) rank sweep: k_gather_rows + k_finish_pull, "
+                               "one launch pair per iteration", "launches": len(pull),
+                     "ms_per_launch": pull_ms / max(len(pull), 1), "achieved": achieved, "peak": peak,
                      "unit": "GB/s", "frac": achieved / peak,
                      "traffic": SWEEP_DRAM_BYTES_RMAT25.get((tuning.threads, tuning.quads_per_lane, tuning.hub_vertices,
                                                              tuning.fused_epilogue, tuning.ranges))
@@ -417,6 +430,10 @@ def run_gpu(a, rank, world, local_rank):
             "ms_update_mean": statistics.mean(s.ms_update for s in stats),
             "sweep_ms_mean_per_launch": sweep_ms / max(sweeps, 1),
             "sweep_share_of_step": sweep_ms / ms if ms else None,
+            "list_sweeps": {"launches": len(push), "ms": push_ms,
+                            "gbs": alg_bytes(push) / (push_ms / 1000.0) / 1e9 if push_ms > 0 else None},
+            "all_sweeps_gbs": all_gbs,
+            "pull_sweep_edges_share": (sum(r[3] for r in pull) / len(pull) / m0) if pull else None,
             "vertices_ever_affected_mean": statistics.mean(s.vertices_ever_affected for s in stats),
             "edges_processed_mean": statistics.mean(s.edges_processed for s in stats),
             "eff_ins_mean": statistics.mean(s.eff_insertions for s in stats),
@@ -602,10 +619,16 @@ def run_batched(a, rank, world, local_rank):
 
 # ------------------------------------------------------------------ serving workload
 
+# scales of the 16 resident graphs of the serving workload: 18..24 with edge
+# factor 16, 16 x sum(2^s) = 2.56e9 drawn edges in all
+SERVING_SCALES = [24] * 8 + [23, 23, 22, 21, 20, 19, 18, 18]
+
+
 def serving_name(a):
-    return ("16 resident R-MAT graphs (scales 18..24 uniform, edge factor 16), requests with Poisson arrivals, "
-            "batch sizes log-uniform in 10..1e5 edges (80/20), DF-P; server (pr_server, grouped: coalescing + "
-            "group updates overlapping batch edits) vs one pr_apply_batch + pr_update per request")
+    return ("16 resident R-MAT graphs (scales 18..24, edge factor 16, 2.56e9 drawn edges in all), requests with "
+            "Poisson arrivals for a uniformly drawn graph, batch sizes log-uniform in 10..1e5 edges (80/20), DF-P; "
+            "server (pr_server, grouped: coalescing, solo updates and group updates overlapping batch edits) vs one "
+            "pr_apply_batch + pr_update per request")
 
 
 def run_serving(a, rank, world, local_rank):
@@ -619,7 +642,7 @@ def run_serving(a, rank, world, local_rank):
 
     torch.cuda.set_device(local_rank)
     rng = np.random.default_rng(a.seed + 5)
-    specs = [(int(rng.integers(18, 25)), 16, a.seed + 3000 + 17 * i) for i in range(16)]
+    specs = [(int(sc), 16, a.seed + 3000 + 17 * i) for i, sc in enumerate(rng.permutation(SERVING_SCALES))]
     graphs, cands = [], []
     for scale, ef, seed in specs:
         n = 1 << scale
@@ -951,6 +974,139 @@ def run_tolerances(a, rank, world, local_rank):
     print(json.dumps(line), flush=True)
 
 
+# ------------------------------------------------------------------ sweep settings
+
+SETTINGS_TABLE = [(256, 4, 0, 0, 1), (512, 4, 0, 0, 1), (1024, 2, 0, 0, 1), (512, 2, 0, 0, 1), (1024, 4, 0, 0, 1),
+                  (1024, 4, 13824, 0, 1), (1024, 4, 0, 1, 1), (1024, 2, 0, 1, 1), (1024, 2, 0, 0, 2),
+                  (1024, 2, 0, 0, 4)]
+
+
+def run_settings(a, rank, world, local_rank):
+    """Time the every-vertex sweep under fixed settings of pr_set_tuning
+    (threads per block, quads per lane, hub vertices, epilogue in the gather
+    kernel, vertex ranges) on the benchmark graph: ND sweeps (mean of 3) and the
+    pull-form sweeps of one DF-P update (per-sweep trace) after one random
+    batch, the same batch and previous ranks for every setting."""
+    import numpy as np
+    import torch
+
+    import paper_2401_15870_gb300 as pr
+    import synth.gpu as sg
+
+    torch.cuda.set_device(local_rank)
+    n = 1 << a.scale
+    src, dst = sg.rmat(a.scale, a.edge_factor << a.scale, a.seed)
+    G = pr.Graph.from_edges(n, src, dst, device=True)
+    G.update("static", alpha=ALPHA, tau=TAU)
+    size = max(1, int(round(a.batch_frac * G.m)))
+    G.apply_batch_device(*sg.batch(n, src, dst, size, a.seed + 1))
+    del src, dst
+    r0 = torch.empty(n, dtype=torch.float64, device="cuda")
+    G.ranks_device(r0)
+    rows = []
+    for t, q, hub, fused, ranges in SETTINGS_TABLE:
+        G.set_tuning(t, q, hub, fused, ranges)
+        G.set_ranks_device(r0)
+        G.update("nd", alpha=ALPHA, tau=TAU, max_iter=1, time_sweeps=True, loop="host")   # warm-up
+        G.set_ranks_device(r0)
+        st = G.update("nd", alpha=ALPHA, tau=0.0, max_iter=3, time_sweeps=True, loop="host")
+        nd_ms = st.ms_sweep / max(st.sweeps, 1)
+        G.set_ranks_device(r0)
+        G.update("dfp", alpha=ALPHA, tau=TAU, time_sweeps=True, direction="pull")
+        pull = [r[2] for r in G.sweep_log() if r[1] == pr.PR_SWEEP_EVERY_VERTEX and r[3] > 0]
+        rows.append({"threads": t, "quads_per_lane": q, "hub_vertices": hub, "fused_epilogue": fused,
+                     "ranges": ranges, "nd_sweep_ms": nd_ms, "dfp_pull_sweep_ms": float(np.mean(pull)),
+                     "dfp_sweeps": len(pull)})
+    if rank != 0:
+        return
+    best = min(rows, key=lambda r: r["dfp_pull_sweep_ms"])
+    line = {"metric": METRIC, "value": best["dfp_pull_sweep_ms"], "unit": "ms per DF-P pull sweep, best setting",
+            "n_gpus": world, "higher_is_better": False, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": workload_name(a), "edges": G.m}, "settings": rows}
+    print(json.dumps(line), flush=True)
+
+
+# ------------------------------------------------------------------ synchronous and asynchronous order
+
+def run_orders(a, rank, world, local_rank):
+    """Sec. 4.4: the synchronous order (every vertex of a sweep reads the ranks
+    of the start of the sweep) against the asynchronous one (PR_OPT_ASYNC: one
+    contribution vector updated in place while the sweep runs) on the temporal
+    stream: 2.6M vertices, 63M timestamped edges, base = first 90%, then
+    a.reps consecutive insertion-only batches of each size 1e-5, 1e-4, 1e-3
+    |E_T|.  Every method starts from the exact fixed point of G_{t-1} (Static at
+    tau = 0, 500 iterations) and is compared in L1 with the exact fixed point
+    of G_t.  Beside it, the oracle's two orders (the asynchronous one visits
+    vertices in ascending id) on a 20,000-vertex, 400,000-edge stream of the
+    same kind, three batches of 400 insertions."""
+    import numpy as np
+    import torch
+
+    import oracle
+    import paper_2401_15870_gb300 as pr
+    import synth
+
+    torch.cuda.set_device(local_rank)
+    n, m_t = 2_600_000, 63_000_000
+    src, dst = synth.temporal(n, m_t, a.seed + 77)
+    base = int(0.9 * m_t)
+    G = pr.Graph.from_edges(n, src[:base], dst[:base])
+    G.update("static", alpha=ALPHA, tau=0.0, max_iter=500)
+    r_prev = G.ranks()
+    methods = ("static", "nd", "df", "dfp")
+    rows = []
+    pos = base
+    for frac in (1e-5, 1e-4, 1e-3):
+        size = int(round(frac * m_t))
+        acc = {(mth, o): {"ms": [], "l1": [], "iters": []} for mth in methods for o in ("sync", "async")}
+        for k in range(a.reps):
+            G.apply_batch(ins_src=src[pos:pos + size], ins_dst=dst[pos:pos + size])
+            pos += size
+            G.update("static", alpha=ALPHA, tau=0.0, max_iter=500)
+            r_ref = G.ranks()
+            for mth in methods:
+                for o in ("sync", "async"):
+                    G.set_ranks(r_prev)
+                    st = G.update(mth, alpha=ALPHA, tau=TAU, loop="host", order=o)
+                    acc[(mth, o)]["ms"].append(st.ms_update)
+                    acc[(mth, o)]["iters"].append(st.iterations)
+                    acc[(mth, o)]["l1"].append(float(np.abs(G.ranks() - r_ref).sum()))
+            G.set_ranks(r_ref)
+            r_prev = r_ref
+        for (mth, o), v in acc.items():
+            rows.append({"batch_frac": frac, "batch": size, "method": mth, "order": o,
+                         "ms_mean": statistics.mean(v["ms"]), "iterations_mean": statistics.mean(v["iters"]),
+                         "l1_error_mean": statistics.mean(v["l1"])})
+    # the oracle's orders on a small stream of the same kind
+    on, om = 20000, 400000
+    s_, d_ = synth.temporal(on, om, 5)
+    ob = int(0.9 * om)
+    og = oracle.Graph(on, s_[:ob], d_[:ob])
+    orp, _ = og.update("static", tau=0.0, max_iter=500)
+    orows = []
+    opos = ob
+    for k in range(3):
+        og.apply_batch([], [], s_[opos:opos + 400], d_[opos:opos + 400])
+        opos += 400
+        oref, _ = og.update("static", tau=0.0, max_iter=500)
+        for mth in ("nd", "df", "dfp"):
+            for o in ("sync", "async"):
+                r, st = og.update(mth, r_prev=orp, order=o)
+                orows.append({"batch": k, "method": mth, "order": o, "l1_error": float(np.abs(r - oref).sum()),
+                              "iterations": st.iterations, "vertex_updates": st.vertices_processed})
+        orp = oref
+    if rank != 0:
+        return
+    dfp = {r["order"]: r for r in rows if r["method"] == "dfp" and r["batch_frac"] == 1e-4}
+    line = {"metric": METRIC, "value": dfp["async"]["l1_error_mean"], "unit": "DF-P L1 error, asynchronous order, "
+            "1e-4 |E_T| batches", "n_gpus": world, "higher_is_better": False, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": "temporal stream (copying / preferential attachment with repeats), %d vertices, "
+                       "%d timestamped edges, base = first 90%%, %d consecutive insertion-only batches per size; "
+                       "every method from the exact fixed point of G_{t-1}" % (n, m_t, a.reps)},
+            "gpu": rows, "oracle_20k": orows}
+    print(json.dumps(line), flush=True)
+
+
 def main():
     a = parse()
     rank = int(os.environ.get("RANK", "0"))
@@ -974,6 +1130,10 @@ def main():
             run_temporal(a, rank, world, local_rank)
         elif a.workload == "tolerances":
             run_tolerances(a, rank, world, local_rank)
+        elif a.workload == "orders":
+            run_orders(a, rank, world, local_rank)
+        elif a.workload == "settings":
+            run_settings(a, rank, world, local_rank)
         else:
             run_gpu(a, rank, world, local_rank)
     finally:

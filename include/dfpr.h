@@ -98,6 +98,19 @@ typedef struct {
  * dr > tau * |out(v)|. */
 #define PR_OPT_MEASURE_ABSOLUTE 32
 #define PR_OPT_MEASURE_CONTRIB 64
+/* pr_options.flags for Static, ND, DF and DF-P: the asynchronous order of
+ * Alg. 1 (Sec. 4.4: one rank vector, updated in place while the sweep runs).
+ * Every sweep is an every-vertex sweep whose epilogue writes a vertex's new
+ * contribution R[v]/|out(v)| as soon as its row is summed, into the vector the
+ * sweep gathers from: rows summed later read the new value, rows summed
+ * earlier or at the same time the old one, as the GPU schedules them.  The
+ * frontier flags of an iteration still take effect in the next one.  The
+ * result depends on that schedule and is not reproducible bit for bit; it
+ * converges to the same fixed point (Eq. 1), and from the paper's setting
+ * (Sec. 4.4) it usually needs fewer iterations.  Runs on the host loop; not
+ * with PR_OPT_DEVICE_LOOP, PR_OPT_FORCE_PUSH, Dynamic Traversal or groups
+ * (PR_EINVAL). */
+#define PR_OPT_ASYNC 128
 #define PR_DEVICE_LOOP_SLOTS (1ll << 24)
 
 /* Outcome of one pr_update (Sec. 5.1.5 measures time and affected vertices). */
@@ -147,6 +160,32 @@ void pr_graph_destroy(pr_graph* g);
 
 /* Rebind the graph to another CUDA stream of the same device. */
 pr_status pr_set_stream(pr_graph* g, void* stream);
+
+/*
+ * Vertex insertion and deletion: change |V| to n_new.  The paper keeps |V|
+ * fixed in its experiments (Sec. 5.2.2) while its temporal graphs gain
+ * vertices over time (Sec. 5.1.4); this call adds or removes vertices at the
+ * end of the id range.
+ *   n_new > n: vertices n .. n_new-1 are added with their self-loop only
+ *     (Sec. 5.1.3), and no other edge.
+ *   n_new < n: vertices n_new .. n-1 are removed; each must have no edge but
+ *     its self-loop (delete its edges with pr_apply_batch first), else
+ *     PR_EINVAL and nothing changes.
+ * Ranks (if the graph has them) are carried over by a closed form.  With
+ * C0 = (1 - alpha)/|V| in Eq. 1, scaling a solution of Eq. 1 on the old graph
+ * by n / n_new solves Eq. 1 on the new graph (the sums over in-neighbours
+ * scale with it), and a vertex whose only edge is its self-loop solves
+ * r = (1 - alpha)/n_new + alpha r, i.e. r = 1/n_new.  So r'[v] = r[v] n/n_new
+ * for the vertices kept and 1/n_new for the new ones: a converged graph stays
+ * converged, to the rounding of that product.  The last batch's effective
+ * change is cleared, so a DF / DF-P update right after the call processes
+ * nothing; edges of the new vertices come in later batches.  The tuning
+ * settings are kept; the handle stays valid (its device memory is rebuilt:
+ * the call costs a graph creation).  Errors: PR_EINVAL (n_new < 1, n_new + m
+ * >= 2^31, a removed vertex with edges), PR_ENOMEM, PR_ECUDA; on error the
+ * graph is unchanged.
+ */
+pr_status pr_graph_resize(pr_graph* g, int32_t n_new);
 
 /*
  * Apply one batch update (Sec. 3.2): E_t = (E_{t-1} \ D) u I, deletions
@@ -500,6 +539,27 @@ void pr_debug_fail_alloc(int64_t k);
 /* Number of CUDA kernels this library has launched in this process so far
  * (all graphs); the difference across a region counts its launches. */
 unsigned long long pr_kernel_launches(void);
+
+/*
+ * Per-sweep trace of the last pr_update of a graph that ran with
+ * PR_OPT_TIME_SWEEPS and its host loop (the device loop and groups keep no
+ * per-sweep times): one record per iteration of Alg. 1, in order.  The paper
+ * reports whole-update times (Sec. 5.1.5); the trace splits them into the
+ * list (push) sweeps over a frontier and the every-vertex (pull) sweeps, so
+ * that each kernel form can be held against its own roofline.
+ */
+typedef struct {
+  int32_t iteration;   /* 0-based                                                  */
+  int32_t form;        /* PR_SWEEP_LIST or PR_SWEEP_EVERY_VERTEX                   */
+  double ms;           /* CUDA-event time of the sweep's launches on the stream    */
+  int64_t edges;       /* in-edges summed by the sweep (vertices processed only)   */
+  int64_t vertices;    /* vertices the sweep processed                             */
+} pr_sweep_record;
+#define PR_SWEEP_LIST 0
+#define PR_SWEEP_EVERY_VERTEX 1
+/* Copies min(cap, count) records to out (host) and sets *count to the number
+ * of records of that update (0 if it kept none).  Errors: PR_EINVAL. */
+pr_status pr_sweep_log(const pr_graph* g, pr_sweep_record* out, int32_t cap, int32_t* count);
 
 /* Text of the last error on this graph ("" if none); valid until the next call. */
 const char* pr_last_error(const pr_graph* g);

@@ -110,6 +110,9 @@ def _load(parallel: bool = False):
         lib.or_update.restype = ctypes.c_int
         lib.or_update_ex.argtypes = [P, ctypes.c_int, f64, f64, f64, f64, i32, ctypes.c_int, ctypes.c_int, P, P, P]
         lib.or_update_ex.restype = ctypes.c_int
+        lib.or_graph_resize.argtypes = [P, i32]
+        lib.or_graph_resize.restype = ctypes.c_int
+        lib.or_resize_ranks.argtypes = [i32, P, i32, P]
         lib.or_threads.restype = ctypes.c_int
         lib.or_set_threads.argtypes = [ctypes.c_int]
         _libs[parallel] = lib
@@ -146,6 +149,15 @@ def _i32(a):
 
 def _ptr(a):
     return a.ctypes.data if a.size else None
+
+
+def resize_ranks(r_old, n_new: int) -> np.ndarray:
+    """Ranks carried over a resize: r * n / n_new for the kept vertices,
+    1 / n_new for added ones (closed form from Eq. 1)."""
+    r = np.ascontiguousarray(np.asarray(r_old, dtype=np.float64))
+    out = np.zeros(int(n_new), np.float64)
+    _load().or_resize_ranks(r.size, r.ctypes.data, int(n_new), out.ctypes.data)
+    return out
 
 
 def rank_plain(alpha: float, n: int, c: float) -> float:
@@ -193,6 +205,14 @@ class Graph:
         if ds.shape != dd.shape or is_.shape != id_.shape:
             raise ValueError("endpoint arrays differ in length")
         rc = self._lib.or_apply_batch(self._h, _ptr(ds), _ptr(dd), ds.size, _ptr(is_), _ptr(id_), is_.size)
+        if rc:
+            raise OracleError(_ERR.get(rc, str(rc)))
+
+    def resize(self, n_new: int):
+        """Vertex insertion / deletion at the end of the id range: added
+        vertices carry their self-loop only; removed ones must have no other
+        edge.  Clears the last batch's effective change."""
+        rc = self._lib.or_graph_resize(self._h, int(n_new))
         if rc:
             raise OracleError(_ERR.get(rc, str(rc)))
 

@@ -334,6 +334,47 @@ int or_apply_batch(or_graph *g, const int32_t *del_src, const int32_t *del_dst, 
   return rebuild_adjacency(g);
 }
 
+/* Vertex insertion and deletion at the end of the id range (|V| fixed in the
+ * paper's experiments, Sec. 5.2.2; its temporal graphs gain vertices over
+ * time, Sec. 5.1.4): |V| becomes n_new.  Added vertices get their self-loop
+ * only (Sec. 5.1.3); removed vertices must have no edge but their self-loop.
+ * The last batch's effective change is cleared. */
+int or_graph_resize(or_graph *g, int32_t n_new) {
+  if (n_new < 1) return OR_EINVAL;
+  int32_t n = g->n;
+  for (int32_t v = n_new; v < n; v++)
+    if (g->out_off[v + 1] - g->out_off[v] != 1 || g->in_off[v + 1] - g->in_off[v] != 1) return OR_EINVAL;
+  /* keys are sorted by source: the edges of the removed vertices (their
+   * self-loops) are the tail, and self-loops of added vertices sort after
+   * every existing key */
+  int64_t keep = n_new < n ? lower_bound(g->keys, g->m, key_of(n_new, 0)) : g->m;
+  int64_t m_new = keep + (n_new > n ? (int64_t)(n_new - n) : 0);
+  uint64_t *k = (uint64_t *)malloc(sizeof(uint64_t) * (size_t)m_new);
+  uint64_t *kp = (uint64_t *)malloc(sizeof(uint64_t) * (size_t)m_new);
+  if (!k || !kp) { free(k); free(kp); return OR_ENOMEM; }
+  memcpy(k, g->keys, sizeof(uint64_t) * (size_t)keep);
+  for (int32_t v = n; v < n_new; v++) k[keep + (v - n)] = key_of(v, v);
+  memcpy(kp, k, sizeof(uint64_t) * (size_t)m_new);
+  free(g->keys); free(g->keys_prev);
+  g->keys = k; g->m = m_new;
+  g->keys_prev = kp; g->m_prev = m_new;   /* no batch since: Delta- = Delta+ = {} */
+  g->n_del = g->n_ins = 0;
+  g->n = n_new;
+  return rebuild_adjacency(g);
+}
+
+/* The previous snapshot's ranks carried over a resize.  Eq. 1 on n vertices
+ * is r = (1 - alpha)/n + alpha P^T r; multiplying a solution by n / n_new
+ * gives (1 - alpha)/n_new + alpha P^T r', the same equation on n_new vertices
+ * (adding or removing isolated vertices leaves P of the others unchanged), and
+ * a vertex with only its self-loop solves r = (1 - alpha)/n_new + alpha r,
+ * r = 1/n_new.  So r'[v] = r[v] n / n_new for the kept vertices and 1/n_new for
+ * the added ones. */
+void or_resize_ranks(int32_t n_old, const double *r_old, int32_t n_new, double *r_new) {
+  double ratio = (double)n_old / (double)n_new;
+  for (int32_t v = 0; v < n_new; v++) r_new[v] = v < n_old ? r_old[v] * ratio : 1.0 / (double)n_new;
+}
+
 /* ---- read-only accessors (tests) ---- */
 int32_t or_num_vertices(const or_graph *g) { return g->n; }
 int64_t or_num_edges(const or_graph *g) { return g->m; }

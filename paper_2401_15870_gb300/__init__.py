@@ -146,6 +146,8 @@ def load():
         "pr_group_autotune": ([_P, ctypes.c_int, f64, f64, i32, _P], ctypes.c_int),
         "pr_group_get_tuning": ([_P, _P], ctypes.c_int),
         "pr_group_set_tuning": ([_P, _P], ctypes.c_int),
+        "pr_graph_resize": ([_P, i32], ctypes.c_int),
+        "pr_sweep_log": ([_P, _P, i32, ctypes.POINTER(i32)], ctypes.c_int),
     }
     for name, (args, res) in sig.items():
         f = getattr(lib, name)
@@ -292,6 +294,7 @@ def pr_apply_batches(handles, batches):
 
 PR_OPT_TIME_SWEEPS, PR_OPT_FORCE_PULL, PR_OPT_FORCE_PUSH = 1, 2, 4
 PR_OPT_DEVICE_LOOP, PR_OPT_HOST_LOOP = 8, 16
+PR_OPT_ASYNC = 128   # asynchronous order (Sec. 4.4): one contribution vector, updated in place
 PR_DEVICE_LOOP_SLOTS = 1 << 24
 
 
@@ -299,17 +302,19 @@ MEASURES = {None: 0, "relative": 0, "absolute": 32, "contrib": 64}   # PR_OPT_ME
 
 
 def pr_update(h, method, alpha=0.85, tau=1e-10, tau_f=1e-6, tau_p=1e-6, max_iter=500, time_sweeps=False,
-              direction=None, loop=None, measure=None) -> Stats:
+              direction=None, loop=None, measure=None, order="sync") -> Stats:
     """direction: None (chosen per iteration), "pull" or "push" (DF / DF-P and
     DT, host loop).
     loop: None (by graph size), "device" or "host".  measure: the DF / DF-P
     measure compared with tau_f / tau_p: "relative" (default), "absolute" or
-    "contrib"."""
+    "contrib".  order: "sync" (every vertex of a sweep reads the ranks of its
+    start) or "async" (one contribution vector updated in place, Sec. 4.4)."""
     m = METHODS[method] if isinstance(method, str) else int(method)
     flags = (PR_OPT_TIME_SWEEPS if time_sweeps else 0) | {None: 0, "pull": PR_OPT_FORCE_PULL,
                                                           "push": PR_OPT_FORCE_PUSH}[direction]
     flags |= {None: 0, "device": PR_OPT_DEVICE_LOOP, "host": PR_OPT_HOST_LOOP}[loop]
     flags |= MEASURES[measure]
+    flags |= {"sync": 0, "async": PR_OPT_ASYNC}[order]
     opts = pr_options(tau_f, tau_p, int(max_iter), flags)
     st = pr_stats()
     _check(load().pr_update(h, m, float(alpha), float(tau), ctypes.byref(opts), ctypes.byref(st)), h)
@@ -407,6 +412,31 @@ def pr_affected(h, which):
 
 def pr_last_error(h) -> str:
     return load().pr_last_error(h).decode()
+
+
+class pr_sweep_record(ctypes.Structure):
+    _fields_ = [("iteration", ctypes.c_int32), ("form", ctypes.c_int32), ("ms", ctypes.c_double),
+                ("edges", ctypes.c_int64), ("vertices", ctypes.c_int64)]
+
+
+PR_SWEEP_LIST, PR_SWEEP_EVERY_VERTEX = 0, 1
+
+
+def pr_sweep_log(h):
+    """Per-sweep records of the graph's last timed host-loop update, as a list
+    of (iteration, form, ms, edges, vertices); form 0 = list (push) sweep,
+    1 = every-vertex (pull) sweep."""
+    cnt = ctypes.c_int32(0)
+    _check(load().pr_sweep_log(h, None, 0, ctypes.byref(cnt)), h)
+    recs = (pr_sweep_record * max(cnt.value, 1))()
+    _check(load().pr_sweep_log(h, recs, cnt.value, ctypes.byref(cnt)), h)
+    return [(r.iteration, r.form, r.ms, r.edges, r.vertices) for r in recs[:cnt.value]]
+
+
+def pr_graph_resize(h, n_new):
+    """Vertex insertion / deletion at the end of the id range; ranks carried
+    over by the closed form r * n / n_new (new vertices 1 / n_new)."""
+    _check(load().pr_graph_resize(h, int(n_new)), h)
 
 
 PR_NOALLOC_MAX_N = 524288
@@ -594,6 +624,12 @@ class Graph:
 
     def effective_delta(self):
         return pr_last_delta(self._h)
+
+    def resize(self, n_new):
+        pr_graph_resize(self._h, n_new)
+
+    def sweep_log(self):
+        return pr_sweep_log(self._h)
 
     def initial_affected(self):
         return pr_affected(self._h, 0)

@@ -380,16 +380,27 @@ struct SweepTimer {
   bool on;
   double ms = 0.0;
   int32_t launches = 0;
+  int last_mode = 0;
+  long long edges0 = 0, verts0 = 0;   // the control block's totals at the previous record
+  // asynchronous order: every-vertex sweeps in the one-launch form (gather and
+  // epilogue in one kernel) with the contributions updated in place
+  bool async = false;
   cudaError_t launch(int mode, const SweepParams& p, cudaStream_t s) {
+    last_mode = mode;
     if (on) cudaEventRecord(h->ev[4], s);
     cudaError_t e;
     if (mode == SWEEP_FULL || mode == SWEEP_PULL_DF || mode == SWEEP_PULL_DFP) {
       Graph* g = &h->g;
       SweepParams q = p;
       q.ntiles_host = g->in.cap >> 2;
+      GatherCfg cfg = h->gcfg;
+      if (async) {
+        cfg.fused = 1;
+        cfg.parts = 1;
+      }
       const SweepAux* aux = nullptr;
-      e = sweep_aux(h, h->gcfg, &aux);
-      if (e == cudaSuccess) e = launch_full_sweep(mode, q, h->gcfg, g->rowbits, g->rowbase, g->anyb, g->done, aux, s);
+      e = sweep_aux(h, cfg, &aux);
+      if (e == cudaSuccess) e = launch_full_sweep(mode, q, cfg, g->rowbits, g->rowbase, g->anyb, g->done, aux, s);
     } else {
       e = launch_sweep(mode, p, s);
     }
@@ -397,16 +408,33 @@ struct SweepTimer {
     launches++;
     return e;
   }
+  // after read_ctl: the sweep's time and, from the control block's running
+  // totals, the edges and vertices it processed, as one trace record
   void collect() {
     if (!on) return;
     float t = 0.f;
     if (cudaEventElapsedTime(&t, h->ev[4], h->ev[5]) == cudaSuccess) ms += t;
+    const Ctl* c = h->g.ctl_h;
+    pr_sweep_record r;
+    r.iteration = (int32_t)h->sweep_log.size();
+    r.form = last_mode == SWEEP_FULL || last_mode == SWEEP_PULL_DF || last_mode == SWEEP_PULL_DFP
+                 ? PR_SWEEP_EVERY_VERTEX : PR_SWEEP_LIST;
+    r.ms = t;
+    r.edges = c->edges - edges0;
+    r.vertices = c->verts - verts0;
+    edges0 = c->edges;
+    verts0 = c->verts;
+    h->sweep_log.push_back(r);
   }
 };
 
 pr_status dfpr::run_update(pr_graph* h, int method, double alpha, double tau, double tau_f, double tau_p,
                            int32_t max_iter, int32_t flags, pr_stats* out) {
   SweepTimer timer{h, (flags & PR_OPT_TIME_SWEEPS) != 0};
+  const bool async = (flags & PR_OPT_ASYNC) != 0;
+  timer.async = async;
+  if (async) flags |= PR_OPT_FORCE_PULL;
+  h->sweep_log.clear();
   Graph* g = &h->g;
   cudaStream_t s = g->stream;
   int32_t n = g->n;
@@ -430,10 +458,10 @@ pr_status dfpr::run_update(pr_graph* h, int method, double alpha, double tau, do
     p.ntiles_host = g->full_ntiles;
     for (int32_t it = 0; it < max_iter; it++) {
       p.Ccur = g->C[g->ccur];
-      p.Cnext = g->C[1 - g->ccur];
+      p.Cnext = g->C[async ? g->ccur : 1 - g->ccur];   // one vector, updated in place, when asynchronous
       TRY(timer.launch(SWEEP_FULL, p, s));
       TRY(launch_control(g->ctl, 0, s));
-      g->ccur ^= 1;
+      if (!async) g->ccur ^= 1;
       pr_status st = read_ctl(g);
       if (st != PR_OK) return st;
       timer.collect();
@@ -556,8 +584,13 @@ pr_status dfpr::run_update(pr_graph* h, int method, double alpha, double tau, do
         p.list = nullptr;
         p.tfirst = g->full_tfirst;
         p.ntiles_host = g->full_ntiles;
+        // with the gather and the epilogue in separate launches over one
+        // range, the epilogue updates the contributions in place (the gather
+        // that reads them has finished); otherwise into the other buffer.
+        // Asynchronous order: in place within the one launch, on purpose
+        const bool inplace = async || (!h->gcfg.fused && h->gcfg.parts == 1);
         p.Ccur = g->C[g->ccur];
-        p.Cnext = g->C[1 - g->ccur];
+        p.Cnext = g->C[inplace ? g->ccur : 1 - g->ccur];
         p.S_cur = g->bits[cur];
         p.X_cur = xb[cur];
         p.S_next = g->bits[1 - cur];
@@ -568,7 +601,7 @@ pr_status dfpr::run_update(pr_graph* h, int method, double alpha, double tau, do
         p.cnt_x = &g->ctl->nexp;
         TRY(timer.launch(pull_mode, p, s));
         TRY(launch_control(g->ctl, 1, s));
-        g->ccur ^= 1;
+        if (!inplace) g->ccur ^= 1;
         cur ^= 1;
         st = read_ctl(g);
         if (st != PR_OK) return st;
@@ -1042,7 +1075,10 @@ pr_status pr_update(pr_graph* h, pr_method method, double alpha, double tau, con
     max_iter = opts->max_iter;
     flags = opts->flags;
     if (flags & ~(PR_OPT_TIME_SWEEPS | PR_OPT_FORCE_PULL | PR_OPT_FORCE_PUSH | PR_OPT_DEVICE_LOOP | PR_OPT_HOST_LOOP |
-                  PR_OPT_MEASURE_ABSOLUTE | PR_OPT_MEASURE_CONTRIB))
+                  PR_OPT_MEASURE_ABSOLUTE | PR_OPT_MEASURE_CONTRIB | PR_OPT_ASYNC))
+      return PR_EINVAL;
+    if ((flags & PR_OPT_ASYNC) &&
+        ((flags & (PR_OPT_DEVICE_LOOP | PR_OPT_FORCE_PUSH)) || method == PR_DYNAMIC_TRAVERSAL))
       return PR_EINVAL;
     if ((flags & PR_OPT_MEASURE_ABSOLUTE) && (flags & PR_OPT_MEASURE_CONTRIB)) return PR_EINVAL;
     if ((flags & PR_OPT_FORCE_PULL) && (flags & PR_OPT_FORCE_PUSH)) return PR_EINVAL;
@@ -1055,7 +1091,8 @@ pr_status pr_update(pr_graph* h, pr_method method, double alpha, double tau, con
     return PR_EINVAL;
   if (method != PR_STATIC && !g->has_ranks)
     return (pr_status)set_error(g, ENORANKS_, "pr_update: a dynamic method needs ranks (pr_set_ranks or a previous update)");
-  const bool host_flags = flags & (PR_OPT_HOST_LOOP | PR_OPT_TIME_SWEEPS | PR_OPT_FORCE_PULL | PR_OPT_FORCE_PUSH);
+  const bool host_flags =
+      flags & (PR_OPT_HOST_LOOP | PR_OPT_TIME_SWEEPS | PR_OPT_FORCE_PULL | PR_OPT_FORCE_PUSH | PR_OPT_ASYNC);
   const bool loopable = method != PR_DYNAMIC_TRAVERSAL;
   if (loopable && ((flags & PR_OPT_DEVICE_LOOP) || (!host_flags && g->in.cap < PR_DEVICE_LOOP_SLOTS))) {
     // the iteration loop on the device: a group of this one graph, on its stream
@@ -1128,6 +1165,149 @@ pr_status pr_set_ranks_device(pr_graph* h, const double* r) {
   TRY(cudaStreamSynchronize(s));
   if (hv.bad || hv.sum > 2.0) return (pr_status)set_error(g, EINVAL_, "pr_set_ranks_device: bad ranks");
   return set_ranks_from_device(h, r);
+}
+
+// Vertex insertion / deletion (pr_graph_resize): the edge set in user ids,
+// rebuilt with the new vertex count.
+}  // extern "C"
+
+// any user id at or above n_new that has an edge besides its self-loop
+__global__ void k_removed_isolated(const int32_t* __restrict__ iperm, const int32_t* __restrict__ odeg,
+                                   const int32_t* __restrict__ ideg, int32_t n, int32_t n_new, int32_t* bad) {
+  for (int64_t u = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; u < n; u += (int64_t)gridDim.x * blockDim.x)
+    if (iperm[u] >= n_new && (odeg[u] != 1 || ideg[u] != 1)) *bad = 1;
+}
+
+__global__ void k_degrees_i64(const int32_t* __restrict__ deg, int32_t n, int64_t* __restrict__ out) {
+  for (int64_t u = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; u < n; u += (int64_t)gridDim.x * blockDim.x)
+    out[u] = deg[u];
+}
+
+// one warp per internal out-row: its edges as user-id keys packed with `bits`
+// (the new graph's id width) at pos[u]..; an edge with an end at or above
+// n_new (the self-loop of a removed vertex) becomes the key of vertex 0's
+// self-loop, which the build collapses.  Then one self-loop key per vertex of
+// the new graph.
+__global__ void k_export_keys(const int64_t* __restrict__ off, const int32_t* __restrict__ deg,
+                              const int32_t* __restrict__ col, const int32_t* __restrict__ iperm,
+                              const int64_t* __restrict__ pos, int32_t n, int32_t n_new, int bits,
+                              uint64_t* __restrict__ keys) {
+  const int lane = threadIdx.x & 31;
+  const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  for (int64_t u = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5; u < n; u += nw) {
+    const int32_t su = iperm[u];
+    for (int64_t x = lane; x < deg[u]; x += 32) {
+      const int32_t sv = iperm[col[off[u] + x]];
+      keys[pos[u] + x] = su < n_new && sv < n_new ? ((uint64_t)su << bits) | (uint64_t)sv : 0ull;
+    }
+  }
+}
+
+__global__ void k_self_loop_keys(int32_t n_new, int bits, uint64_t* __restrict__ keys) {
+  for (int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; v < n_new; v += (int64_t)gridDim.x * blockDim.x)
+    keys[v] = ((uint64_t)v << bits) | (uint64_t)v;
+}
+
+// r'[v] = r[v] * ratio for the vertices kept, 1/n_new for the new ones (user ids)
+__global__ void k_resize_ranks(const double* __restrict__ r, int32_t n, int32_t n_new, double ratio,
+                               double* __restrict__ out) {
+  for (int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; v < n_new; v += (int64_t)gridDim.x * blockDim.x)
+    out[v] = v < n ? r[v] * ratio : 1.0 / (double)n_new;
+}
+
+extern "C" {
+
+pr_status pr_graph_resize(pr_graph* h, int32_t n_new) {
+  if (!h) return PR_EINVAL;
+  Graph* g = &h->g;
+  const int32_t n = g->n;
+  if (n_new < 1) return (pr_status)set_error(g, EINVAL_, "pr_graph_resize: n_new < 1");
+  if ((int64_t)n_new + g->m >= (int64_t(1) << 31))
+    return (pr_status)set_error(g, EINVAL_, "pr_graph_resize: too many vertices and edges");
+  if (n_new == n) return PR_OK;
+  cudaStream_t s = g->stream;
+  if (n_new < n) {
+    DevBuf<int32_t> bad;
+    TRY(bad.alloc(1));
+    TRY(cudaMemsetAsync(bad.p, 0, sizeof(int32_t), s));
+    note_launch();
+    k_removed_isolated<<<grid_for(n, 256), 256, 0, s>>>(g->iperm, g->out.deg, g->in.deg, n, n_new, bad.p);
+    int32_t hb = 0;
+    TRY(cudaMemcpyAsync(&hb, bad.p, sizeof(hb), cudaMemcpyDeviceToHost, s));
+    TRY(cudaStreamSynchronize(s));
+    if (hb) return (pr_status)set_error(g, EINVAL_, "pr_graph_resize: a removed vertex still has edges");
+  }
+  // the edges in user ids, then the self-loops of the new vertex set
+  const int64_t m = g->m;
+  const int nb = bits_for(n_new);
+  DevBuf<int64_t> pos, stmp;
+  uint64_t* keys = nullptr;
+  TRY(pos.alloc(n + 1));
+  TRY(stmp.alloc(scan_tmp_elems(n)));
+  note_launch();
+  k_degrees_i64<<<grid_for(n, 256), 256, 0, s>>>(g->out.deg, n, pos.p);
+  TRY(scan_excl<int64_t>(pos.p, pos.p, n, stmp.p, s));
+  TRY(dev_malloc(&keys, sizeof(uint64_t) * (size_t)(m + n_new)));
+  note_launch();
+  k_export_keys<<<grid_for((int64_t)n * 32, 256), 256, 0, s>>>(g->out.off, g->out.deg, g->out.col, g->iperm, pos.p,
+                                                                n, n_new, nb, keys);
+  note_launch();
+  k_self_loop_keys<<<grid_for(n_new, 256), 256, 0, s>>>(n_new, nb, keys + m);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) {
+    cudaFree(keys);
+    return (pr_status)cuda_fail(g, e, "pr_graph_resize: keys");
+  }
+  pr_graph* h2 = new (std::nothrow) pr_graph();
+  if (!h2) {
+    cudaFree(keys);
+    return PR_ENOMEM;
+  }
+  Graph* g2 = &h2->g;
+  g2->n = n_new;
+  g2->id_bits = nb;
+  g2->stream = s;
+  g2->relabel = g->relabel;
+  g2->dev = g->dev;
+  pr_graph* made = nullptr;
+  pr_status st = finish_create(h2, keys, m + n_new, &made);
+  cudaFree(keys);
+  if (st == PR_OK && g->has_ranks) {
+    // ranks in user order, carried over to the new vertex set
+    e = launch_gather_f64(g->R, g->perm, h->vec_tmp, n, s);
+    if (e == cudaSuccess) {
+      note_launch();
+      k_resize_ranks<<<grid_for(n_new, 256), 256, 0, s>>>(h->vec_tmp, n, n_new, (double)n / (double)n_new,
+                                                           h2->vec_tmp);
+      e = cudaGetLastError();
+    }
+    st = e == cudaSuccess ? set_ranks_from_device(h2, h2->vec_tmp) : (pr_status)cuda_fail(g, e, "pr_graph_resize");
+  }
+  if (st != PR_OK) {
+    if (st != PR_ENOMEM && st != PR_ECUDA) g->err = g2->err;
+    destroy_handle(h2);
+    return st;
+  }
+  // the new state moves into the caller's handle; the old one is freed with h2
+  if (h->solo) {
+    pr_group_destroy(h->solo);
+    h->solo = nullptr;
+  }
+  std::swap(h->g, h2->g);
+  std::swap(h->lbits_tmp, h2->lbits_tmp);
+  std::swap(h->ls_tmp, h2->ls_tmp);
+  std::swap(h->vec_tmp, h2->vec_tmp);
+  std::swap(h->tiles_cap, h2->tiles_cap);
+  destroy_handle(h2);
+  return PR_OK;
+}
+
+pr_status pr_sweep_log(const pr_graph* h, pr_sweep_record* out, int32_t cap, int32_t* count) {
+  if (!h || !count || cap < 0 || (cap > 0 && !out)) return PR_EINVAL;
+  const int32_t k = (int32_t)h->sweep_log.size();
+  for (int32_t i = 0; i < k && i < cap; i++) out[i] = h->sweep_log[i];
+  *count = k;
+  return PR_OK;
 }
 
 pr_status pr_graph_info(const pr_graph* h, int32_t* n, int64_t* m) {

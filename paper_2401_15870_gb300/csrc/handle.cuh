@@ -1,6 +1,7 @@
 // handle.cuh -- the opaque pr_graph handle of the C ABI: one graph and the
 // host-side scratch of its drivers.
 #pragma once
+#include <vector>
 #include "dfpr.h"
 #include "graph.cuh"
 #include "sweep.cuh"
@@ -18,6 +19,7 @@ struct pr_graph {
   dfpr::SweepAux saux;             // second stream and events of sweeps in several ranges (made on first use)
   float gcfg_ms = 0.f;              // its measured gather time (0: not measured)
   int32_t gcfg_trials = 0;          // configurations the last pr_autotune timed
+  std::vector<pr_sweep_record> sweep_log;   // per-sweep trace of the last timed host-loop update
 };
 
 namespace dfpr {

@@ -53,6 +53,20 @@ __device__ __forceinline__ long long ld_hint(const long long* p, uint64_t pol) {
 
 __device__ __forceinline__ unsigned long long dbits(double x) { return (unsigned long long)__double_as_longlong(x); }
 
+// The asynchronous order (one contribution vector, written by the epilogue of
+// a one-launch sweep while other warps of the same launch gather from it):
+// coherent relaxed loads and stores at GPU scope, so a gather reads either
+// the old or the new value of a contribution, never a stale cached line
+// beyond the launch's own writes, and the accesses do not race.
+__device__ __forceinline__ long long ld_relaxed_hint(const long long* p, uint64_t pol) {
+  long long v;
+  asm volatile("ld.relaxed.gpu.global.L2::cache_hint.b64 %0, [%1], %2;" : "=l"(v) : "l"(p), "l"(pol) : "memory");
+  return v;
+}
+__device__ __forceinline__ void st_relaxed(long long* p, long long v) {
+  asm volatile("st.relaxed.gpu.global.b64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
+}
+
 // Contributions (and, in pull form, expanded-source bits) of the hub vertices
 // [0, k) staged in shared memory by the kernel.  Internal ids are ordered by
 // decreasing out-degree, so [0, k) are the vertices of out-degree at least
@@ -76,7 +90,9 @@ struct GatherSpan {
 // on left out; S / X / anyb only in pull form.
 // SPAN: also report what the step touched (the one-launch sweep needs it; the
 // other callers skip the extra warp operations)
-template <bool PULL, int QPT = SW_QPT, bool HUB = false, bool SPAN = false>
+// ASYNC: the contributions are being updated in place during the launch
+// (asynchronous order): they are read with coherent relaxed loads
+template <bool PULL, int QPT = SW_QPT, bool HUB = false, bool SPAN = false, bool ASYNC = false>
 __device__ __forceinline__ GatherSpan gather_step(const int32_t* __restrict__ icol, const long long* __restrict__ C,
                                                   const uint32_t* __restrict__ X, const uint32_t* __restrict__ S,
                                                   const uint32_t* __restrict__ rowbits,
@@ -90,6 +106,7 @@ __device__ __forceinline__ GatherSpan gather_step(const int32_t* __restrict__ ic
   // that covers the sentinel id holds C[sent] = 0
   auto contrib = [&](int32_t c) -> long long {
     if (HUB && c < hub.k) return hub.c[c];
+    if (ASYNC) return c != sent ? ld_relaxed_hint(C + c, pol_keep) : 0ll;
     return c != sent ? ld_hint(C + c, pol_keep) : 0ll;
   };
   auto expanded = [&](int32_t c) -> unsigned {
@@ -207,6 +224,9 @@ __device__ __forceinline__ void finish_pull_step(const P& p, long long* __restri
   const int lane = threadIdx.x & 31;
   const double alpha_fix = p.alpha * FIX_INV;
   const bool same_tau = p.tau_f == p.tau_p;
+  // contributions updated in place (the gather that read them has finished):
+  // a vertex outside F_i keeps its entry and copies nothing
+  const bool inplace = p.Cnext == p.Ccur;
   long long sum[U], cself[U];
   double Rv[U];
   int32_t d[U];
@@ -220,7 +240,8 @@ __device__ __forceinline__ void finish_pull_step(const P& p, long long* __restri
     const uint32_t in_f = ch < nchunks ? (ab | __ldg(p.S_cur + ch)) : 0u;
     member[u] = valid[u] && ((in_f >> lane) & 1u);
     sum[u] = valid[u] ? (L2 ? __ldcg(acc + v) : acc[v]) : 0;
-    cself[u] = valid[u] ? p.Ccur[v] : 0;
+    // the own contribution: Eq. 2's self term, or the entry a non-member copies
+    cself[u] = (CLOSED ? member[u] : false) || (valid[u] && !member[u] && !inplace) ? p.Ccur[v] : 0;
     Rv[u] = member[u] ? p.R[v] : 0.0;
     d[u] = member[u] ? p.odeg[v] : 1;
   }
@@ -246,7 +267,9 @@ __device__ __forceinline__ void finish_pull_step(const P& p, long long* __restri
       t.verts += 1;
       p.R[v] = r;
       const double sc = d[u] < TAB ? p.tab_sc[d[u]] : FIX_ONE / (double)d[u];
-      p.Cnext[v] = fixconv::f64_to_i64_rn(r * sc);   // the FP64 pipe bounds this epilogue
+      const long long cn = fixconv::f64_to_i64_rn(r * sc);   // the FP64 pipe bounds this epilogue
+      if (inplace) st_relaxed(p.Cnext + v, cn);
+      else p.Cnext[v] = cn;
       // Alg. 1: prune when dr / max(r, R[v]) <= tau_p (DF-P), expand when it
       // is > tau_f (or the other measures of Sec. 4.3); compared without the
       // division
@@ -256,7 +279,7 @@ __device__ __forceinline__ void finish_pull_step(const P& p, long long* __restri
       const unsigned long long tp = SAME || same_tau ? tf : dbits(p.tau_p * mr);
       stay = !CLOSED || drb > tp;
       expand = drb > tf;
-    } else if (valid[u]) {
+    } else if (valid[u] && !inplace) {
       p.Cnext[v] = cself[u];
     }
     const unsigned ms = __ballot_sync(0xffffffffu, stay);

@@ -14,13 +14,19 @@
 //      set as applying the requests one after another, Sec. 3.2) and apply it
 //      on the graphs' stream -- this overlaps with the group update already
 //      running on the group stream;
-//   3. when no update is running, launch one group update (pr_group machinery)
-//      over every READY graph (one or two READY graphs, with no request
-//      waiting for an idle graph, run pr_update each instead, whose host loop
-//      may pick the push form);
-//   4. when the running update has finished, complete its requests.
-// A request that arrives for a READY or IN_FLIGHT graph waits for the next
-// round of that graph, so the batches of a graph are applied in arrival order.
+//   3. hand the READY graphs to the device: while few graphs are READY
+//      (at most SOLO_MAX_GRAPHS) and a solo thread is free, each goes to a
+//      solo thread that runs pr_update on it (its host loop picks the push or
+//      pull form per iteration, cheaper than the pull-only group form when a
+//      frontier starts small on a large graph); otherwise, when no group
+//      update is running, one group update (pr_group machinery) takes every
+//      READY graph;
+//   4. when the running group update has finished, complete its requests.
+// Every graph has its own stream while the server runs, so a solo update, the
+// group update and the batch edits of other graphs overlap on the device; the
+// worker never waits for a solo update.  A request that arrives for a READY or
+// IN_FLIGHT graph waits for the next round of that graph, so the batches of a
+// graph are applied in arrival order.
 //
 // Plain mode: one pr_apply_batch + pr_update per request, in arrival order --
 // the baseline the grouped mode is measured against.
@@ -56,9 +62,11 @@ enum GraphState { IDLE = 0, READY = 1, IN_FLIGHT = 2 };
 // sort buffers, flags, row staging), for admission
 constexpr int64_t BYTES_PER_BATCH_EDGE = 160;
 constexpr int64_t BYTES_PER_BATCH = 4 << 20;
-// rounds of at most this many graphs, with no request waiting for an idle
-// graph, run one pr_update per graph instead of a group update
+// rounds of at most this many READY graphs go to the solo threads (one
+// pr_update per graph) instead of a group update
 constexpr size_t SOLO_MAX_GRAPHS = 2;
+// threads that run solo updates, each on its graph's own stream
+constexpr int SOLO_THREADS = 2;
 
 }  // namespace
 
@@ -67,7 +75,8 @@ struct pr_server {
   int32_t G = 0;
   std::vector<pr_graph*> graphs;
   std::vector<void*> old_streams;
-  cudaStream_t apply_stream = nullptr, group_stream = nullptr;
+  std::vector<cudaStream_t> streams;   // one per graph while the server runs
+  cudaStream_t group_stream = nullptr;
   pr_group* group = nullptr;
 
   std::mutex mu;
@@ -78,6 +87,12 @@ struct pr_server {
   int64_t outstanding = 0;
   bool stop = false;
   std::thread worker;
+  // solo updates: graphs queued by the worker, run by the solo threads
+  std::vector<std::thread> solo;
+  std::condition_variable cv_solo;
+  std::deque<std::pair<int32_t, int64_t>> solo_q;   // (graph, round)
+  int solo_busy = 0;                                 // queued or running
+  bool solo_stop = false;
 
   // worker-only state
   std::vector<int> state;
@@ -186,6 +201,31 @@ void run_plain(pr_server* S) {
   }
 }
 
+// a solo thread: one pr_update per queued graph, on the graph's own stream
+void run_solo(pr_server* S) {
+  for (;;) {
+    std::pair<int32_t, int64_t> job;
+    {
+      std::unique_lock<std::mutex> lk(S->mu);
+      S->cv_solo.wait(lk, [&] { return S->solo_stop || !S->solo_q.empty(); });
+      if (S->solo_q.empty()) return;
+      job = S->solo_q.front();
+      S->solo_q.pop_front();
+    }
+    const int32_t gi = job.first;
+    pr_stats st;
+    memset(&st, 0, sizeof(st));
+    pr_status rc = pr_update(S->graphs[gi], (pr_method)S->opt.method, S->opt.alpha, S->opt.tau, &S->opt.opts, &st);
+    finish_requests(S, S->ready_reqs[gi], rc, job.second, S->t_start[gi], &st);
+    {
+      std::lock_guard<std::mutex> lk(S->mu);
+      S->state[gi] = IDLE;
+      S->solo_busy--;
+    }
+    S->cv_work.notify_all();
+  }
+}
+
 void run_grouped(pr_server* S) {
   const int G = S->G;
   bool in_flight = false;
@@ -201,14 +241,22 @@ void run_grouped(pr_server* S) {
           if (S->state[r.graph] == IDLE) return true;
         return false;
       };
-      if (in_flight) {
-        if (!has_work()) S->cv_work.wait_for(lk, std::chrono::microseconds(50));
-      } else if (!has_work()) {
+      // READY graphs that step 3 could hand to the device now
+      auto can_launch = [&] {
         bool ready = false;
         for (int i = 0; i < G; i++) ready = ready || S->state[i] == READY;
-        if (!ready) {
-          S->cv_work.wait(lk, [&] { return S->stop || has_work(); });
-          if (S->stop && !has_work() && S->pending.empty()) return;
+        return ready && (!in_flight || S->solo_busy < SOLO_THREADS);
+      };
+      if (!has_work() && !can_launch()) {
+        if (in_flight) {
+          S->cv_work.wait_for(lk, std::chrono::microseconds(50));   // poll the group update
+        } else if (S->stop) {
+          bool busy = S->solo_busy > 0 || !S->pending.empty();
+          for (int i = 0; i < G; i++) busy = busy || S->state[i] != IDLE;
+          if (!busy) return;                                          // every request is done
+          S->cv_work.wait_for(lk, std::chrono::milliseconds(1));
+        } else {
+          S->cv_work.wait(lk, [&] { return S->stop || has_work() || can_launch(); });
         }
       }
       // the next round holds the READY graphs and those admitted now
@@ -244,7 +292,7 @@ void run_grouped(pr_server* S) {
       }
       S->pending.swap(keep);
     }
-    // 2. merge and apply, overlapping the running update
+    // 2. merge and apply on each graph's stream, overlapping the running updates
     for (int32_t gi : order) {
       std::vector<int32_t> ds, dd, is, id;
       merge_requests(take[gi], &ds, &dd, &is, &id);
@@ -262,7 +310,7 @@ void run_grouped(pr_server* S) {
       S->t_start[gi] = t0;
       S->ready_reqs[gi] = std::move(take[gi]);
     }
-    // 3. complete the running update
+    // 3. complete the running group update
     if (in_flight && group_done(S->group)) {
       pr_status rc = group_complete(S->group, S->stats.data());
       for (int32_t gi : S->members) {
@@ -273,52 +321,47 @@ void run_grouped(pr_server* S) {
       in_flight = false;
       S->cv_work.notify_all();
     }
-    // 4. launch the next one over every READY graph
-    if (!in_flight) {
-      S->members.clear();
+    // 4. hand the READY graphs to the solo threads or to one group update
+    std::vector<int32_t> ready;
+    int solo_free = 0;
+    {
+      std::lock_guard<std::mutex> lk(S->mu);
       for (int i = 0; i < G; i++)
-        if (S->state[i] == READY) S->members.push_back(i);
-      bool solo = !S->members.empty() && S->members.size() <= SOLO_MAX_GRAPHS;
-      if (solo) {
-        // only when no request waits for an idle graph: otherwise the group
-        // update runs asynchronously while the worker applies those batches
+        if (S->state[i] == READY) ready.push_back(i);
+      solo_free = SOLO_THREADS - S->solo_busy;
+    }
+    if (ready.empty()) continue;
+    const bool solo = ready.size() <= SOLO_MAX_GRAPHS && (int)ready.size() <= solo_free;
+    if (solo) {
+      {
         std::lock_guard<std::mutex> lk(S->mu);
-        for (const Request& r : S->pending) solo = solo && S->state[r.graph] != IDLE;
+        for (int32_t gi : ready) {
+          S->state[gi] = IN_FLIGHT;
+          S->solo_q.emplace_back(gi, S->round++);
+          S->solo_busy++;
+        }
       }
-      if (solo) {
-        // few graphs: each its own update in turn, with the direction choice
-        // of pr_update (cheaper than the pull-only group form on a large graph
-        // whose frontier starts small); same ranks and statistics as the group
+      S->cv_solo.notify_all();
+      S->ready_bytes = 0;
+      S->ready_edges = 0;
+    } else if (!in_flight) {
+      S->members = ready;
+      pr_status rc = group_launch(S->group, (pr_method)S->opt.method, S->opt.alpha, S->opt.tau, &S->opt.opts,
+                                  S->members.data(), (int32_t)S->members.size());
+      if (rc != PR_OK) {
         for (int32_t gi : S->members) {
-          pr_stats st;
-          memset(&st, 0, sizeof(st));
-          pr_status rc = pr_update(S->graphs[gi], (pr_method)S->opt.method, S->opt.alpha, S->opt.tau, &S->opt.opts,
-                                   &st);
-          finish_requests(S, S->ready_reqs[gi], rc, S->round++, S->t_start[gi], &st);
+          finish_requests(S, S->ready_reqs[gi], rc, -1, S->t_start[gi], nullptr);
           std::lock_guard<std::mutex> lk(S->mu);
           S->state[gi] = IDLE;
         }
-        S->ready_bytes = 0;
-        S->ready_edges = 0;
-        S->cv_work.notify_all();
-      } else if (!S->members.empty()) {
-        pr_status rc = group_launch(S->group, (pr_method)S->opt.method, S->opt.alpha, S->opt.tau, &S->opt.opts,
-                                    S->members.data(), (int32_t)S->members.size());
-        if (rc != PR_OK) {
-          for (int32_t gi : S->members) {
-            finish_requests(S, S->ready_reqs[gi], rc, -1, S->t_start[gi], nullptr);
-            std::lock_guard<std::mutex> lk(S->mu);
-            S->state[gi] = IDLE;
-          }
-        } else {
-          std::lock_guard<std::mutex> lk(S->mu);
-          for (int32_t gi : S->members) S->state[gi] = IN_FLIGHT;
-          in_flight = true;
-          flight_round = S->round++;
-        }
-        S->ready_bytes = 0;
-        S->ready_edges = 0;
+      } else {
+        std::lock_guard<std::mutex> lk(S->mu);
+        for (int32_t gi : S->members) S->state[gi] = IN_FLIGHT;
+        in_flight = true;
+        flight_round = S->round++;
       }
+      S->ready_bytes = 0;
+      S->ready_edges = 0;
     }
   }
 }
@@ -333,9 +376,17 @@ void server_free(pr_server* S) {
     S->cv_work.notify_all();
     S->worker.join();
   }
+  {
+    std::lock_guard<std::mutex> lk(S->mu);
+    S->solo_stop = true;
+  }
+  S->cv_solo.notify_all();
+  for (std::thread& t : S->solo)
+    if (t.joinable()) t.join();
   if (S->group) pr_group_destroy(S->group);
   for (size_t i = 0; i < S->old_streams.size(); i++) pr_set_stream(S->graphs[i], S->old_streams[i]);
-  if (S->apply_stream) cudaStreamDestroy(S->apply_stream);
+  for (cudaStream_t st : S->streams)
+    if (st) cudaStreamDestroy(st);
   if (S->group_stream) cudaStreamDestroy(S->group_stream);
   delete S;
 }
@@ -365,15 +416,20 @@ pr_status pr_server_create(int32_t count, pr_graph* const* graphs, const pr_serv
   S->ready_reqs.resize(count);
   S->t_start.assign(count, 0.0);
   S->stats.resize(count);
-  if (cudaStreamCreateWithFlags(&S->apply_stream, cudaStreamNonBlocking) != cudaSuccess ||
-      cudaStreamCreateWithFlags(&S->group_stream, cudaStreamNonBlocking) != cudaSuccess) {
+  if (cudaStreamCreateWithFlags(&S->group_stream, cudaStreamNonBlocking) != cudaSuccess) {
     server_free(S);
     return PR_ECUDA;
   }
-  // the graphs work on the server's apply stream while it runs
+  // every graph works on a stream of its own while the server runs
+  // (pr_set_stream finishes the work queued on its old stream first)
+  S->streams.assign(count, nullptr);
   for (int32_t i = 0; i < count; i++) {
+    if (cudaStreamCreateWithFlags(&S->streams[i], cudaStreamNonBlocking) != cudaSuccess) {
+      server_free(S);
+      return PR_ECUDA;
+    }
     S->old_streams.push_back((void*)graphs[i]->g.stream);
-    pr_status rc = pr_set_stream(graphs[i], S->apply_stream);
+    pr_status rc = pr_set_stream(graphs[i], S->streams[i]);
     if (rc != PR_OK) {
       server_free(S);
       return rc;
@@ -393,6 +449,12 @@ pr_status pr_server_create(int32_t count, pr_graph* const* graphs, const pr_serv
     if (S->opt.mode == PR_SERVE_PLAIN) run_plain(S);
     else run_grouped(S);
   });
+  if (opts->mode == PR_SERVE_GROUPED)
+    for (int k = 0; k < SOLO_THREADS; k++)
+      S->solo.emplace_back([S, dev] {
+        cudaSetDevice(dev);
+        run_solo(S);
+      });
   *out = S;
   return PR_OK;
 }

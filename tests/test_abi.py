@@ -94,7 +94,7 @@ def test_binding_structs_match_the_header(tmp_path):
     import paper_2401_15870_gb300 as pr
     structs = {"pr_options": pr.pr_options, "pr_stats": pr.pr_stats, "pr_server_options": pr.pr_server_options,
                "pr_request_info": pr.pr_request_info, "pr_tuning": pr.pr_tuning,
-               "pr_group_tuning": pr.pr_group_tuning}
+               "pr_group_tuning": pr.pr_group_tuning, "pr_sweep_record": pr.pr_sweep_record}
     lines = ['#include <stdio.h>', '#include <stddef.h>', '#include "dfpr.h"', "int main(void) {"]
     for name, cls in structs.items():
         lines.append('printf("%s %%zu\\n", sizeof(%s));' % (name, name))

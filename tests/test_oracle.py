@@ -599,3 +599,66 @@ def test_openmp_build_sorts_large_edge_lists():
     assert A.m == B.m
     for x, y in zip(A.out_csr() + A.in_csr(), B.out_csr() + B.in_csr()):
         assert np.array_equal(x, y)
+
+
+# ------------------------------------------------------------ vertex insertion and deletion
+
+
+@pytest.mark.parametrize("seed", [1, 2, 3])
+def test_resize_carries_the_fixed_point_over(seed):
+    """Adding isolated vertices (self-loop only) to a graph: the linear-system
+    solution of the grown graph equals the old solution times n / n_new, with
+    1 / n_new on the new vertices (numpy LAPACK on both graphs), and the
+    oracle's resize gives the grown edge set."""
+    n, n_new = 40, 57
+    src, dst = random_graph(n, 160, 80 + seed)
+    g = oracle.Graph(n, src, dst)
+    r_old = pagerank_solve(n, edge_set(n, src, dst))
+    g.resize(n_new)
+    assert g.n == n_new
+    off, adj = g.out_csr()
+    grown = {(u, int(w)) for u in range(n_new) for w in adj[off[u]:off[u + 1]]}
+    assert grown == edge_set(n_new, src, dst)
+    exact_new = pagerank_solve(n_new, grown)
+    carried = oracle.resize_ranks(r_old, n_new)
+    assert np.max(np.abs(carried - exact_new)) < 1e-14
+    assert np.all(carried[n:] == 1.0 / n_new)
+    # the carried ranks are a fixed point: ND stops after one sweep
+    r, st = g.update("nd", tau=1e-13, r_prev=carried)
+    assert st.iterations == 1 and np.max(np.abs(r - exact_new)) < 1e-14
+    # the last batch is cleared: DF-P processes nothing
+    r, st = g.update("dfp", r_prev=carried)
+    assert st.vertices_processed == 0 and np.array_equal(r, carried)
+
+
+def test_resize_removes_isolated_tail_only():
+    """Removing vertices: allowed only once their edges are deleted; the
+    solution of the smaller graph is the isolated-tail solution times
+    n / n_new, and DF-P after a batch that connects a grown graph's new
+    vertices reaches the linear-system solution at zero tolerance."""
+    n = 30
+    src, dst = random_graph(n, 120, 7)
+    g = oracle.Graph(n, src, dst)
+    before = (g.out_csr(), g.in_csr())
+    with pytest.raises(oracle.OracleError):
+        g.resize(20)                     # vertices 20..29 still have edges
+    assert all(np.array_equal(a, b) for a, b in zip(g.out_csr() + g.in_csr(), before[0] + before[1]))
+    # delete every edge touching 20..29, then remove them
+    E = edge_set(n, src, dst)
+    gone = [(u, v) for u, v in E if u != v and (u >= 20 or v >= 20)]
+    g.apply_batch(del_src=[u for u, _ in gone], del_dst=[v for _, v in gone])
+    E2 = E - set(gone)
+    r_iso = pagerank_solve(n, E2)
+    g.resize(20)
+    E3 = {(u, v) for u, v in E2 if u < 20 and v < 20}
+    exact = pagerank_solve(20, E3)
+    assert np.max(np.abs(oracle.resize_ranks(r_iso, 20) - exact)) < 1e-14
+    # grow again and connect the new vertices with a batch: DF-P at zero
+    # tolerance from the carried ranks reaches the new fixed point
+    g.resize(26)
+    carried = oracle.resize_ranks(exact, 26)
+    ins = [(20, 3), (3, 21), (22, 20), (25, 0), (24, 24), (5, 23)]
+    g.apply_batch(ins_src=[u for u, _ in ins], ins_dst=[v for _, v in ins])
+    E4 = edge_set(26, [u for u, _ in E3] + [u for u, _ in ins], [v for _, v in E3] + [v for _, v in ins])
+    r, _ = g.update("dfp", tau=1e-15, tau_f=0.0, tau_p=0.0, r_prev=carried)
+    assert np.max(np.abs(r - pagerank_solve(26, E4))) < 1e-12
