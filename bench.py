@@ -660,7 +660,7 @@ def run_serving(a, rank, world, local_rank):
         times, graphs and sizes depend on the rate only; the edges on k0, so each
         arm gets batches of its own (a batch applied twice changes nothing)."""
         r2 = np.random.default_rng(a.seed + int(rate))
-        count = max(20, min(a.max_requests, int(rate * 1.0)))
+        count = min(a.max_requests, max(200, int(rate * 1.0)))
         t = np.cumsum(r2.exponential(1.0 / rate, count))
         out = []
         for i in range(count):
@@ -1030,14 +1030,15 @@ def run_settings(a, rank, world, local_rank):
 
 def run_orders(a, rank, world, local_rank):
     """Sec. 4.4: the synchronous order (every vertex of a sweep reads the ranks
-    of the start of the sweep) against the asynchronous one (PR_OPT_ASYNC: one
-    contribution vector updated in place while the sweep runs) on the temporal
-    stream: 2.6M vertices, 63M timestamped edges, base = first 90%, then
-    a.reps consecutive insertion-only batches of each size 1e-5, 1e-4, 1e-3
-    |E_T|.  Every method starts from the exact fixed point of G_{t-1} (Static at
-    tau = 0, 500 iterations) and is compared in L1 with the exact fixed point
-    of G_t.  Beside it, the oracle's two orders (the asynchronous one visits
-    vertices in ascending id) on a 20,000-vertex, 400,000-edge stream of the
+    of the start of the sweep) against the asynchronous one (PR_OPT_ASYNC: eight
+    vertex ranges swept in turn, each reading the ranks of the ranges before it
+    as updated in the sweep) on the temporal stream: 2.6M vertices, 63M
+    timestamped edges, base = first 90%, then a.reps consecutive insertion-only
+    batches of each size 1e-5, 1e-4, 1e-3 |E_T|.  Every method starts from the
+    exact fixed point of G_{t-1} (Static at tau = 0, 500 iterations) and is
+    compared in L1 with the exact fixed point of G_t.  Beside it, the oracle's
+    three orders (sync; async: ascending id, one vertex at a time; ranges: the
+    GPU's asynchronous schedule) on a 20,000-vertex, 400,000-edge stream of the
     same kind, three batches of 400 insertions."""
     import numpy as np
     import torch
@@ -1090,7 +1091,7 @@ def run_orders(a, rank, world, local_rank):
         opos += 400
         oref, _ = og.update("static", tau=0.0, max_iter=500)
         for mth in ("nd", "df", "dfp"):
-            for o in ("sync", "async"):
+            for o in ("sync", "async", "ranges"):
                 r, st = og.update(mth, r_prev=orp, order=o)
                 orows.append({"batch": k, "method": mth, "order": o, "l1_error": float(np.abs(r - oref).sum()),
                               "iterations": st.iterations, "vertex_updates": st.vertices_processed})

@@ -98,17 +98,19 @@ typedef struct {
  * dr > tau * |out(v)|. */
 #define PR_OPT_MEASURE_ABSOLUTE 32
 #define PR_OPT_MEASURE_CONTRIB 64
-/* pr_options.flags for Static, ND, DF and DF-P: the asynchronous order of
- * Alg. 1 (Sec. 4.4: one rank vector, updated in place while the sweep runs).
- * Every sweep is an every-vertex sweep whose epilogue writes a vertex's new
- * contribution R[v]/|out(v)| as soon as its row is summed, into the vector the
- * sweep gathers from: rows summed later read the new value, rows summed
- * earlier or at the same time the old one, as the GPU schedules them.  The
- * frontier flags of an iteration still take effect in the next one.  The
- * result depends on that schedule and is not reproducible bit for bit; it
- * converges to the same fixed point (Eq. 1), and from the paper's setting
- * (Sec. 4.4) it usually needs fewer iterations.  Runs on the host loop; not
- * with PR_OPT_DEVICE_LOOP, PR_OPT_FORCE_PUSH, Dynamic Traversal or groups
+/* pr_options.flags for Static, ND, DF and DF-P: an asynchronous order of
+ * Alg. 1 (Sec. 4.4 runs it with one rank vector updated in place).  The
+ * library's vertex order is cut into 8 consecutive ranges at multiples of 128
+ * (range k starts at floor(n k / 8 / 128) * 128; one range below 1024
+ * vertices), every sweep visits the ranges one after another, and a vertex
+ * reads the ranks of the ranges before its own as updated in this sweep and
+ * the others as of the start of the sweep.  Frontier flags take effect in the
+ * next iteration, as in the synchronous order.  The schedule is fixed, so the
+ * result is reproducible; it converges to the same fixed point of Eq. 1,
+ * usually in fewer iterations.  The library's vertex order is the caller's
+ * when the graph was created keeping it (pr_graph_create_edges flags bit 0),
+ * else the internal order by out-degree.  Runs on the host loop; not with
+ * PR_OPT_DEVICE_LOOP, PR_OPT_FORCE_PUSH, Dynamic Traversal or groups
  * (PR_EINVAL). */
 #define PR_OPT_ASYNC 128
 #define PR_DEVICE_LOOP_SLOTS (1ll << 24)

@@ -46,7 +46,7 @@ STATIC, NAIVE_DYNAMIC, DYNAMIC_TRAVERSAL, DF, DFP = 0, 1, 2, 3, 4
 METHODS = {"static": STATIC, "nd": NAIVE_DYNAMIC, "dt": DYNAMIC_TRAVERSAL, "df": DF, "dfp": DFP}
 # the DF / DF-P measures of Sec. 4.3: dr / max(r, R[v]) (Alg. 1), dr, dr / d
 METRICS = {"relative": 0, "absolute": 1, "contrib": 2}
-ORDERS = {"sync": 0, "async": 1}
+ORDERS = {"sync": 0, "async": 1, "ranges": 2}
 _ERR = {1: "invalid argument", 2: "vertex id out of range", 3: "out of memory", 4: "no previous ranks"}
 
 
@@ -254,8 +254,10 @@ class Graph:
     def update(self, method, alpha=0.85, tau=1e-10, tau_f=1e-6, tau_p=1e-6, max_iter=500, r_prev=None,
                metric="relative", order="sync"):
         """Run one method; returns (ranks, Stats).  metric: the DF / DF-P
-        measure of Sec. 4.3 ("relative", "absolute", "contrib"); order: "sync"
-        or "async" (Alg. 1 with one rank vector, ascending vertex id)."""
+        measure of Sec. 4.3 ("relative", "absolute", "contrib"); order: "sync",
+        "async" (Alg. 1 with one rank vector, ascending vertex id) or "ranges"
+        (eight consecutive id ranges swept in order, each reading the ranks of
+        the ranges before it as updated in this sweep)."""
         m = METHODS[method] if isinstance(method, str) else int(method)
         out = np.zeros(self.n, np.float64)
         prev = None if r_prev is None else np.ascontiguousarray(np.asarray(r_prev, dtype=np.float64))

@@ -495,7 +495,15 @@ enum { OR_METRIC_RELATIVE = 0, OR_METRIC_ABSOLUTE = 1, OR_METRIC_CONTRIB = 2 };
  * affected later in the id order is processed in the same iteration, and a
  * vertex marked behind the current id waits for the next one (Sec. 4.4 runs
  * the loop in parallel; ascending id is one of its schedules). */
-enum { OR_ORDER_SYNC = 0, OR_ORDER_ASYNC = 1 };
+enum { OR_ORDER_SYNC = 0, OR_ORDER_ASYNC = 1, OR_ORDER_RANGES = 2 };
+/* The ranges order is another schedule of Alg. 1's one rank vector: the
+ * vertex ids are cut into OR_RANGES consecutive ranges at multiples of 128
+ * (range k starts at floor(n k / OR_RANGES / 128) * 128; one range when n <
+ * 128 OR_RANGES), the ranges are swept one after another, and a vertex reads
+ * the ranks of the ranges before its own as updated in this sweep and all
+ * others as of the start of the sweep.  Flags take effect in the next
+ * iteration, as in the synchronous order. */
+enum { OR_RANGES = 8 };
 
 static double frontier_measure(int metric, double dr, double r, double Rv, int64_t d) {
   if (metric == OR_METRIC_ABSOLUTE) return dr;
@@ -573,7 +581,7 @@ int or_update_ex(const or_graph *g, int method, double alpha, double tau, double
                  int32_t max_iter, int metric, int order, const double *r_prev, double *r_out, or_stats *st) {
   int32_t n = g->n;
   if (method < OR_STATIC || method > OR_DFP || max_iter < 0 || !(alpha >= 0.0 && alpha < 1.0)) return OR_EINVAL;
-  if (metric < OR_METRIC_RELATIVE || metric > OR_METRIC_CONTRIB || order < OR_ORDER_SYNC || order > OR_ORDER_ASYNC)
+  if (metric < OR_METRIC_RELATIVE || metric > OR_METRIC_CONTRIB || order < OR_ORDER_SYNC || order > OR_ORDER_RANGES)
     return OR_EINVAL;
   if (method != OR_STATIC && !r_prev) return OR_ENORANKS;
   double *R = (double *)malloc(sizeof(double) * (size_t)n);
@@ -600,6 +608,11 @@ int or_update_ex(const or_graph *g, int method, double alpha, double tau, double
 
   run_args a = {alpha, tau_f, tau_p, metric, method == OR_DF || method == OR_DFP, method == OR_DFP,
                 order == OR_ORDER_ASYNC};
+  /* range bounds: one range for the synchronous order */
+  int P = order == OR_ORDER_RANGES && n >= 128 * OR_RANGES ? OR_RANGES : 1;
+  int32_t bound[OR_RANGES + 1];
+  for (int k = 0; k < P; k++) bound[k] = (int32_t)((int64_t)n * k / P / 128 * 128);
+  bound[P] = n;
   or_stats s;
   memset(&s, 0, sizeof(s));
   s.tie_rel = INFINITY;
@@ -612,21 +625,30 @@ int or_update_ex(const or_graph *g, int method, double alpha, double tau, double
       for (int32_t v = 0; v < n; v++)
         if (F[v]) visit(g, &a, v, R, K, R, F, ever, &tot);
     } else {
-      /* new ranks and flags go to Rn / Fn and are committed after the sweep */
+      /* new ranks and flags go to Rn / Fn and are committed after the sweep;
+       * in the ranges order the quotients of a range follow its new ranks
+       * before the next range is swept */
       memcpy(Rn, R, sizeof(double) * (size_t)n);
       if (a.frontier) memset(Fn, 0, (size_t)n);
+      for (int k = 0; k < P; k++) {
 #pragma omp parallel
-      {
-        sweep_sum part = {0.0, INFINITY, 0, 0};
-#pragma omp for schedule(dynamic, 1024)
-        for (int32_t v = 0; v < n; v++)
-          if (F[v]) visit(g, &a, v, R, K, Rn, Fn, ever, &part);
-#pragma omp critical
         {
-          if (part.dR > tot.dR) tot.dR = part.dR;
-          tot.tie = fmin(tot.tie, part.tie);
-          tot.vertices += part.vertices;
-          tot.edges += part.edges;
+          sweep_sum part = {0.0, INFINITY, 0, 0};
+#pragma omp for schedule(dynamic, 1024)
+          for (int32_t v = bound[k]; v < bound[k + 1]; v++)
+            if (F[v]) visit(g, &a, v, R, K, Rn, Fn, ever, &part);
+#pragma omp critical
+          {
+            if (part.dR > tot.dR) tot.dR = part.dR;
+            tot.tie = fmin(tot.tie, part.tie);
+            tot.vertices += part.vertices;
+            tot.edges += part.edges;
+          }
+        }
+        if (P > 1) {
+#pragma omp parallel for schedule(static)
+          for (int32_t v = bound[k]; v < bound[k + 1]; v++)
+            if (F[v]) K[v] = Rn[v] / (double)out_degree(g, v);
         }
       }
       memcpy(R, Rn, sizeof(double) * (size_t)n);

@@ -382,8 +382,8 @@ struct SweepTimer {
   int32_t launches = 0;
   int last_mode = 0;
   long long edges0 = 0, verts0 = 0;   // the control block's totals at the previous record
-  // asynchronous order: every-vertex sweeps in the one-launch form (gather and
-  // epilogue in one kernel) with the contributions updated in place
+  // asynchronous order: every-vertex sweeps over ASYNC_RANGES vertex ranges in
+  // order, the contributions updated in place after each range
   bool async = false;
   cudaError_t launch(int mode, const SweepParams& p, cudaStream_t s) {
     last_mode = mode;
@@ -394,13 +394,16 @@ struct SweepTimer {
       SweepParams q = p;
       q.ntiles_host = g->in.cap >> 2;
       GatherCfg cfg = h->gcfg;
-      if (async) {
-        cfg.fused = 1;
-        cfg.parts = 1;
-      }
       const SweepAux* aux = nullptr;
-      e = sweep_aux(h, cfg, &aux);
-      if (e == cudaSuccess) e = launch_full_sweep(mode, q, cfg, g->rowbits, g->rowbase, g->anyb, g->done, aux, s);
+      if (async) {
+        cfg.fused = 0;
+        cfg.parts = ASYNC_RANGES;
+        e = cudaSuccess;
+      } else {
+        e = sweep_aux(h, cfg, &aux);
+      }
+      if (e == cudaSuccess)
+        e = launch_full_sweep(mode, q, cfg, g->rowbits, g->rowbase, g->anyb, g->done, aux, s, async);
     } else {
       e = launch_sweep(mode, p, s);
     }
@@ -587,7 +590,7 @@ pr_status dfpr::run_update(pr_graph* h, int method, double alpha, double tau, do
         // with the gather and the epilogue in separate launches over one
         // range, the epilogue updates the contributions in place (the gather
         // that reads them has finished); otherwise into the other buffer.
-        // Asynchronous order: in place within the one launch, on purpose
+        // Asynchronous order: in place after every range, on purpose
         const bool inplace = async || (!h->gcfg.fused && h->gcfg.parts == 1);
         p.Ccur = g->C[g->ccur];
         p.Cnext = g->C[inplace ? g->ccur : 1 - g->ccur];

@@ -53,20 +53,6 @@ __device__ __forceinline__ long long ld_hint(const long long* p, uint64_t pol) {
 
 __device__ __forceinline__ unsigned long long dbits(double x) { return (unsigned long long)__double_as_longlong(x); }
 
-// The asynchronous order (one contribution vector, written by the epilogue of
-// a one-launch sweep while other warps of the same launch gather from it):
-// coherent relaxed loads and stores at GPU scope, so a gather reads either
-// the old or the new value of a contribution, never a stale cached line
-// beyond the launch's own writes, and the accesses do not race.
-__device__ __forceinline__ long long ld_relaxed_hint(const long long* p, uint64_t pol) {
-  long long v;
-  asm volatile("ld.relaxed.gpu.global.L2::cache_hint.b64 %0, [%1], %2;" : "=l"(v) : "l"(p), "l"(pol) : "memory");
-  return v;
-}
-__device__ __forceinline__ void st_relaxed(long long* p, long long v) {
-  asm volatile("st.relaxed.gpu.global.b64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
-}
-
 // Contributions (and, in pull form, expanded-source bits) of the hub vertices
 // [0, k) staged in shared memory by the kernel.  Internal ids are ordered by
 // decreasing out-degree, so [0, k) are the vertices of out-degree at least
@@ -90,9 +76,7 @@ struct GatherSpan {
 // on left out; S / X / anyb only in pull form.
 // SPAN: also report what the step touched (the one-launch sweep needs it; the
 // other callers skip the extra warp operations)
-// ASYNC: the contributions are being updated in place during the launch
-// (asynchronous order): they are read with coherent relaxed loads
-template <bool PULL, int QPT = SW_QPT, bool HUB = false, bool SPAN = false, bool ASYNC = false>
+template <bool PULL, int QPT = SW_QPT, bool HUB = false, bool SPAN = false>
 __device__ __forceinline__ GatherSpan gather_step(const int32_t* __restrict__ icol, const long long* __restrict__ C,
                                                   const uint32_t* __restrict__ X, const uint32_t* __restrict__ S,
                                                   const uint32_t* __restrict__ rowbits,
@@ -106,7 +90,6 @@ __device__ __forceinline__ GatherSpan gather_step(const int32_t* __restrict__ ic
   // that covers the sentinel id holds C[sent] = 0
   auto contrib = [&](int32_t c) -> long long {
     if (HUB && c < hub.k) return hub.c[c];
-    if (ASYNC) return c != sent ? ld_relaxed_hint(C + c, pol_keep) : 0ll;
     return c != sent ? ld_hint(C + c, pol_keep) : 0ll;
   };
   auto expanded = [&](int32_t c) -> unsigned {
@@ -267,9 +250,7 @@ __device__ __forceinline__ void finish_pull_step(const P& p, long long* __restri
       t.verts += 1;
       p.R[v] = r;
       const double sc = d[u] < TAB ? p.tab_sc[d[u]] : FIX_ONE / (double)d[u];
-      const long long cn = fixconv::f64_to_i64_rn(r * sc);   // the FP64 pipe bounds this epilogue
-      if (inplace) st_relaxed(p.Cnext + v, cn);
-      else p.Cnext[v] = cn;
+      p.Cnext[v] = fixconv::f64_to_i64_rn(r * sc);   // the FP64 pipe bounds this epilogue
       // Alg. 1: prune when dr / max(r, R[v]) <= tau_p (DF-P), expand when it
       // is > tau_f (or the other measures of Sec. 4.3); compared without the
       // division

@@ -14,13 +14,15 @@
 //      set as applying the requests one after another, Sec. 3.2) and apply it
 //      on the graphs' stream -- this overlaps with the group update already
 //      running on the group stream;
-//   3. hand the READY graphs to the device: while few graphs are READY
-//      (at most SOLO_MAX_GRAPHS) and a solo thread is free, each goes to a
-//      solo thread that runs pr_update on it (its host loop picks the push or
-//      pull form per iteration, cheaper than the pull-only group form when a
-//      frontier starts small on a large graph); otherwise, when no group
-//      update is running, one group update (pr_group machinery) takes every
-//      READY graph;
+//   3. hand the READY graphs to the device: while few graphs are READY (at
+//      most SOLO_MAX_GRAPHS), they go, once the solo thread is free, to the
+//      solo thread, which runs pr_update on each in turn (its host loop picks
+//      the push or pull form per iteration, cheaper than the pull-only group
+//      form when a frontier starts small on a large graph; updates of large
+//      graphs that ran side by side would each take about as long as both in
+//      turn, which only lengthens the first one's latency); when more are
+//      READY and no group update is running, one group update (pr_group
+//      machinery) takes them all;
 //   4. when the running group update has finished, complete its requests.
 // Every graph has its own stream while the server runs, so a solo update, the
 // group update and the batch edits of other graphs overlap on the device; the
@@ -62,11 +64,11 @@ enum GraphState { IDLE = 0, READY = 1, IN_FLIGHT = 2 };
 // sort buffers, flags, row staging), for admission
 constexpr int64_t BYTES_PER_BATCH_EDGE = 160;
 constexpr int64_t BYTES_PER_BATCH = 4 << 20;
-// rounds of at most this many READY graphs go to the solo threads (one
-// pr_update per graph) instead of a group update
+// rounds of at most this many READY graphs go to the solo thread (one
+// pr_update per graph, in turn) instead of a group update
 constexpr size_t SOLO_MAX_GRAPHS = 2;
 // threads that run solo updates, each on its graph's own stream
-constexpr int SOLO_THREADS = 2;
+constexpr int SOLO_THREADS = 1;
 
 }  // namespace
 
@@ -241,11 +243,12 @@ void run_grouped(pr_server* S) {
           if (S->state[r.graph] == IDLE) return true;
         return false;
       };
-      // READY graphs that step 3 could hand to the device now
+      // READY graphs that step 4 would hand to the device now
       auto can_launch = [&] {
-        bool ready = false;
-        for (int i = 0; i < G; i++) ready = ready || S->state[i] == READY;
-        return ready && (!in_flight || S->solo_busy < SOLO_THREADS);
+        size_t ready = 0;
+        for (int i = 0; i < G; i++) ready += S->state[i] == READY;
+        if (ready == 0) return false;
+        return ready <= SOLO_MAX_GRAPHS ? S->solo_busy < SOLO_THREADS : !in_flight;
       };
       if (!has_work() && !can_launch()) {
         if (in_flight) {
@@ -331,8 +334,8 @@ void run_grouped(pr_server* S) {
       solo_free = SOLO_THREADS - S->solo_busy;
     }
     if (ready.empty()) continue;
-    const bool solo = ready.size() <= SOLO_MAX_GRAPHS && (int)ready.size() <= solo_free;
-    if (solo) {
+    const bool few = ready.size() <= SOLO_MAX_GRAPHS;
+    if (few && solo_free > 0) {
       {
         std::lock_guard<std::mutex> lk(S->mu);
         for (int32_t gi : ready) {
@@ -344,7 +347,7 @@ void run_grouped(pr_server* S) {
       S->cv_solo.notify_all();
       S->ready_bytes = 0;
       S->ready_edges = 0;
-    } else if (!in_flight) {
+    } else if (!few && !in_flight) {
       S->members = ready;
       pr_status rc = group_launch(S->group, (pr_method)S->opt.method, S->opt.alpha, S->opt.tau, &S->opt.opts,
                                   S->members.data(), (int32_t)S->members.size());

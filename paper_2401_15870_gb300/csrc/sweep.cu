@@ -490,9 +490,7 @@ __device__ __forceinline__ void finish_full_step(const SweepParams& p, long long
     t.verts += 1;
     p.R[v] = r;
     const double sc = d[u] < TAB ? p.tab_sc[d[u]] : FIX_ONE / (double)d[u];
-    const long long cn = fixconv::f64_to_i64_rn(r * sc);
-    if (p.Cnext == p.Ccur) st_relaxed(p.Cnext + v, cn);   // asynchronous order: one vector, in place
-    else p.Cnext[v] = cn;
+    p.Cnext[v] = fixconv::f64_to_i64_rn(r * sc);
   }
 }
 
@@ -534,10 +532,7 @@ __device__ __forceinline__ void block_flush_totals(const PullTotals& t, Ctl* ctl
 
 constexpr int64_t TASK_Q = 1024;   // quads per task of k_sweep_rows (a multiple of 32 x QPT)
 
-// ASYNC: the asynchronous order of Alg. 1 -- the epilogue writes the new
-// contributions into the vector the gather reads (p.Cnext == p.Ccur), so rows
-// summed later in the launch read them (no hub cache: it would freeze them)
-template <int MODE, int QPT, bool HUB, bool ASYNC = false>
+template <int MODE, int QPT, bool HUB>
 __global__ void __launch_bounds__(1024) k_sweep_rows(SweepParams p, const uint32_t* __restrict__ rowbits,
                                                      const int32_t* __restrict__ rowbase, uint32_t* __restrict__ anyb,
                                                      int32_t* __restrict__ done, int32_t hub_k, int32_t hub_kx) {
@@ -577,9 +572,8 @@ __global__ void __launch_bounds__(1024) k_sweep_rows(SweepParams p, const uint32
     for (int r = 0; r < RU; r++) {
       const int64_t u = tk * RU + r;
       if (u >= nunits) break;
-      const GatherSpan sp = gather_step<PULL, QPT, HUB, true, ASYNC>(p.icol, p.Ccur, p.X_cur, p.S_cur, rowbits, rowbase,
-                                                               nquads, p.n, p.gacc, anyb, u * UQ, pol_stream, pol_keep,
-                                                               hub);
+      const GatherSpan sp = gather_step<PULL, QPT, HUB, true>(p.icol, p.Ccur, p.X_cur, p.S_cur, rowbits, rowbase, nquads,
+                                                        p.n, p.gacc, anyb, u * UQ, pol_stream, pol_keep, hub);
       first = min(first, sp.first);
       last = max(last, sp.last);
       wrote = wrote || sp.wrote;
@@ -618,12 +612,11 @@ __global__ void __launch_bounds__(1024) k_sweep_rows(SweepParams p, const uint32
   block_flush_totals(t, p.ctl, p.cnt_next, p.cnt_x);
 }
 
-template <int MODE, int QPT, bool HUB, bool ASYNC = false>
+template <int MODE, int QPT, bool HUB>
 static cudaError_t sweep_rows_launch(const SweepParams& p, const uint32_t* rowbits, const int32_t* rowbase,
                                      uint32_t* anyb, int32_t* done, int threads, int32_t hub_k, int32_t hub_kx,
                                      cudaStream_t s) {
-  static_assert(!(ASYNC && HUB), "the asynchronous order runs without a hub cache");
-  const void* fn = (const void*)k_sweep_rows<MODE, QPT, HUB, ASYNC>;
+  const void* fn = (const void*)k_sweep_rows<MODE, QPT, HUB>;
   const size_t smem = HUB ? gather_hub_bytes(hub_k, hub_kx) : 0;
   int bps = 1;
   cudaError_t e = gather_occupancy(fn, threads, smem, &bps);
@@ -632,7 +625,7 @@ static cudaError_t sweep_rows_launch(const SweepParams& p, const uint32_t* rowbi
   const int64_t cap = (int64_t)num_sms() * bps;
   const int grid = (int)std::max<int64_t>(1, std::min<int64_t>(cdiv(tasks, threads / 32), cap));
   note_launch();
-  k_sweep_rows<MODE, QPT, HUB, ASYNC><<<grid, threads, smem, s>>>(p, rowbits, rowbase, anyb, done, hub_k, hub_kx);
+  k_sweep_rows<MODE, QPT, HUB><<<grid, threads, smem, s>>>(p, rowbits, rowbase, anyb, done, hub_k, hub_kx);
   return cudaGetLastError();
 }
 
@@ -643,14 +636,6 @@ static cudaError_t sweep_rows_dispatch(const SweepParams& p, const GatherCfg& cf
   const int32_t hub_k = std::min<int32_t>(cfg.hub, p.n + 1);
   const int32_t hub_kx = PULL ? (int32_t)cdiv(std::min<int32_t>(hub_k, p.n), 32) : 0;
   const int t = cfg.threads;
-  if (p.Cnext == p.Ccur) {   // asynchronous order
-    switch (cfg.qpt) {
-      case 2: return sweep_rows_launch<MODE, 2, false, true>(p, rowbits, rowbase, anyb, done, t, 0, 0, s);
-      case 4: return sweep_rows_launch<MODE, 4, false, true>(p, rowbits, rowbase, anyb, done, t, 0, 0, s);
-      case 8: return sweep_rows_launch<MODE, 8, false, true>(p, rowbits, rowbase, anyb, done, t, 0, 0, s);
-      default: return cudaErrorInvalidValue;
-    }
-  }
   switch (cfg.qpt * 2 + (hub_k > 0 ? 1 : 0)) {
     case 4: return sweep_rows_launch<MODE, 2, false>(p, rowbits, rowbase, anyb, done, t, 0, 0, s);
     case 5: return sweep_rows_launch<MODE, 2, true>(p, rowbits, rowbase, anyb, done, t, hub_k, hub_kx, s);
@@ -753,14 +738,14 @@ cudaError_t launch_gather(bool pull, const SweepParams& p, const GatherCfg& cfg,
 
 cudaError_t launch_full_sweep(int mode, const SweepParams& p, const GatherCfg& cfg, const uint32_t* rowbits,
                               const int32_t* rowbase, uint32_t* anyb, int32_t* done, const SweepAux* aux,
-                              cudaStream_t s) {
+                              cudaStream_t s, bool ordered) {
   const int64_t nquads = p.ntiles_host;   // quads of the in-CSR capacity
   const bool pull = mode == SWEEP_PULL_DF || mode == SWEEP_PULL_DFP;
   if (pull) {
     cudaError_t e = cudaMemsetAsync(anyb, 0, sizeof(uint32_t) * (size_t)(cdiv(p.n, 32) + 1), s);
     if (e != cudaSuccess) return e;
   }
-  if (cfg.fused) {
+  if (cfg.fused && !ordered) {
     if (!gather_cfg_valid(cfg)) return cudaErrorInvalidValue;
     switch (mode) {
       case SWEEP_FULL: return sweep_rows_dispatch<SWEEP_FULL>(p, cfg, rowbits, rowbase, anyb, done, s);
@@ -769,20 +754,23 @@ cudaError_t launch_full_sweep(int mode, const SweepParams& p, const GatherCfg& c
       default: return cudaErrorInvalidValue;
     }
   }
-  if (!gather_cfg_valid(cfg)) return cudaErrorInvalidValue;
+  if (!ordered && !gather_cfg_valid(cfg)) return cudaErrorInvalidValue;
   // P vertex ranges cut at multiples of 128: the gather of range k + 1 runs on
   // s while the epilogue of range k runs on the auxiliary stream, so the
   // FP64-bound epilogue overlaps the L1TEX-bound gather; the epilogues join s
-  // at the end.  P = 1: gather then epilogue on s.
-  const int P = (aux && cfg.parts > 1 && p.n >= 128 * cfg.parts) ? cfg.parts : 1;
-  cudaStream_t fs = P > 1 ? aux->stream : s;
+  // at the end.  P = 1: gather then epilogue on s.  Ordered (asynchronous
+  // order): every range's gather and epilogue on s, one range after another.
+  const int P = ordered ? (p.n >= 128 * cfg.parts ? cfg.parts : 1)
+                        : ((aux && cfg.parts > 1 && p.n >= 128 * cfg.parts) ? cfg.parts : 1);
+  if (ordered) aux = nullptr;
+  cudaStream_t fs = P > 1 && !ordered ? aux->stream : s;
   for (int k = 0; k < P; k++) {
     const int32_t v_lo = (int32_t)((int64_t)p.n * k / P / 128 * 128);
     const int32_t v_hi = k + 1 == P ? p.n : (int32_t)((int64_t)p.n * (k + 1) / P / 128 * 128);
     cudaError_t e = pull ? gather_dispatch<true>(p, cfg, rowbits, rowbase, anyb, nquads, v_lo, v_hi, s)
                          : gather_dispatch<false>(p, cfg, rowbits, rowbase, anyb, nquads, v_lo, v_hi, s);
     if (e != cudaSuccess) return e;
-    if (P > 1) {
+    if (P > 1 && !ordered) {
       if ((e = cudaEventRecord(aux->ev[k], s)) != cudaSuccess) return e;
       if ((e = cudaStreamWaitEvent(fs, aux->ev[k], 0)) != cudaSuccess) return e;
     }
@@ -806,7 +794,7 @@ cudaError_t launch_full_sweep(int mode, const SweepParams& p, const GatherCfg& c
       default: return cudaErrorInvalidValue;
     }
   }
-  if (P > 1) {
+  if (P > 1 && !ordered) {
     cudaError_t e = cudaEventRecord(aux->ev[P], fs);
     if (e == cudaSuccess) e = cudaStreamWaitEvent(s, aux->ev[P], 0);
     if (e != cudaSuccess) return e;

@@ -120,9 +120,17 @@ cudaError_t launch_gather(bool pull, const SweepParams& p, const GatherCfg& cfg,
 // (launch_row_start_index), anyb an n-bit scratch bitset, done the all-zero
 // per-chunk unit counts of the one-launch form (cdiv(n, 128) int32, left zero)
 // aux: the second stream of a sweep in several ranges (NULL: one range)
+// ordered: the asynchronous order -- the cfg.parts vertex ranges are swept one
+// after another on s, each gather followed by its epilogue, and the epilogue
+// writes the new contributions in place (p.Cnext == p.Ccur), so every range
+// gathers the contributions of the ranges before it as updated in this sweep
 cudaError_t launch_full_sweep(int mode, const SweepParams& p, const GatherCfg& cfg, const uint32_t* rowbits,
                               const int32_t* rowbase, uint32_t* anyb, int32_t* done, const SweepAux* aux,
-                              cudaStream_t s);
+                              cudaStream_t s, bool ordered = false);
+// ranges of the asynchronous order (PR_OPT_ASYNC): the vertex set cut at
+// multiples of 128 into this many consecutive ranges (one range below 128 x
+// this many vertices)
+constexpr int ASYNC_RANGES = 8;
 // row-start index of the in-CSR: rowbits (nquads/32 + 1 words), rowbase (as
 // many int32 + 1); tmp: scan_tmp_elems(nquads/32 + 1) int32
 cudaError_t launch_row_start_index(const int64_t* off, int32_t n, int64_t nquads, uint32_t* rowbits, int32_t* rowbase,

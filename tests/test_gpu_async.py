@@ -1,17 +1,20 @@
-"""The asynchronous order of Alg. 1 on the GPU (PR_OPT_ASYNC, Sec. 4.4): one
-contribution vector, updated in place while the sweep runs.  Its results
-depend on the GPU's schedule, so they are checked against what holds for any
-schedule: at zero tolerances every method reaches the linear-system solution
-of Eq. 1 (the oracle's Static at tau = 1e-15 is pinned to numpy's LAPACK
-solve), and at the default tolerances DF / DF-P stay as close to that
-solution as the synchronous order does (the convergence bound of the
-tolerances).  Vertices outside every frontier keep their previous ranks bit
-for bit, as in the synchronous order."""
+"""The asynchronous order of Alg. 1 on the GPU (PR_OPT_ASYNC, Sec. 4.4): eight
+consecutive vertex ranges swept in turn, each reading the ranks of the
+ranges before it as updated in the sweep.  On graphs that keep the caller's
+vertex order the ranges are the oracle's ranges order, so ranks must agree
+within 1e-9 with the same decisions of Alg. 1; on relabelled graphs (ranges
+of the internal order) the checks are what holds for any such schedule: at
+zero tolerances every method reaches the linear-system solution of Eq. 1
+(the oracle's Static at tau = 1e-15 is pinned to numpy's LAPACK solve), and
+at the default tolerances DF / DF-P stay as close to that solution as the
+synchronous order does.  Vertices outside every frontier keep their previous
+ranks bit for bit."""
 import numpy as np
 import pytest
 
 import oracle
 import synth
+from cases import assert_same_run
 
 pytestmark = pytest.mark.gpu
 
@@ -23,10 +26,10 @@ def lib():
     return pr
 
 
-def case(lib, scale, ef, bsize, seed):
+def case(lib, scale, ef, bsize, seed, keep_order=False):
     n = 1 << scale
     src, dst = synth.rmat(scale, ef * n, seed)
-    G = lib.Graph.from_edges(n, src, dst)
+    G = lib.Graph.from_edges(n, src, dst, keep_order=keep_order)
     O = oracle.Graph(n, src, dst)
     r0, _ = O.update("static")
     cs, cd = synth.unique_edges(src, dst)
@@ -98,3 +101,27 @@ def test_async_argument_errors(lib):
         assert lib.load().pr_group_update(grp._q, 4, 0.85, 1e-10, ctypes.byref(opts), None) == 1
     finally:
         grp.close()
+
+
+@pytest.mark.parametrize("method", ["static", "nd", "df", "dfp"])
+@pytest.mark.parametrize("scale,bsize", [(9, 30), (12, 120), (14, 262)])
+def test_async_matches_the_oracle_ranges_order(lib, method, scale, bsize):
+    """Graphs that keep the caller's vertex order: the GPU's asynchronous
+    order is the oracle's ranges order (one range below 1024 vertices, eight
+    above), so ranks agree within 1e-9 and Alg. 1 takes the same decisions."""
+    G, O, r0, _ = case(lib, scale, 16, bsize, 60 + scale, keep_order=True)
+    G.set_ranks(r0)
+    st = G.update(method, order="async")
+    ref, ost = O.update(method, r_prev=r0, order="ranges")
+    assert np.max(np.abs(G.ranks() - ref)) < 1e-9
+    assert_same_run(st, ost, method)
+
+
+def test_async_is_reproducible(lib):
+    G, O, r0, _ = case(lib, 13, 16, 200, 14)
+    out = []
+    for _ in range(2):
+        G.set_ranks(r0)
+        st = G.update("dfp", order="async")
+        out.append((G.ranks(), st.iterations, st.vertices_processed))
+    assert np.array_equal(out[0][0], out[1][0]) and out[0][1:] == out[1][1:]

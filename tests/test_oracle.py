@@ -662,3 +662,73 @@ def test_resize_removes_isolated_tail_only():
     E4 = edge_set(26, [u for u, _ in E3] + [u for u, _ in ins], [v for _, v in E3] + [v for _, v in ins])
     r, _ = g.update("dfp", tau=1e-15, tau_f=0.0, tau_p=0.0, r_prev=carried)
     assert np.max(np.abs(r - pagerank_solve(26, E4))) < 1e-12
+
+
+# ------------------------------------------------------------ the ranges order (Alg. 1, one rank vector, eight id ranges in turn)
+
+
+def range_bounds(n, P=8):
+    P = P if n >= 128 * P else 1
+    return [n * k // P // 128 * 128 for k in range(P)] + [n]
+
+
+@pytest.mark.parametrize("method", ["static", "nd", "df", "dfp"])
+def test_ranges_order_reaches_fixed_point_at_zero_tolerance(method):
+    """Eight ranges of 1280 vertices: every method in the ranges order reaches
+    the linear-system solution of G_t (numpy LAPACK) at zero tolerances."""
+    n = 1280
+    src, dst = random_graph(n, 6000, 41)
+    g = oracle.Graph(n, src, dst)
+    E0 = edge_set(n, src, dst)
+    r0 = pagerank_solve(n, E0)
+    (ds, dd), (is_, id_) = random_batch(n, E0, 30, 120, 42)
+    g.apply_batch(ds, dd, is_, id_)
+    off, adj = g.out_csr()
+    E1 = {(u, int(w)) for u in range(n) for w in adj[off[u]:off[u + 1]]}
+    r, st = g.update(method, tau=1e-15, tau_f=0.0, tau_p=0.0, max_iter=5000, r_prev=r0, order="ranges")
+    assert st.converged
+    assert np.max(np.abs(r - pagerank_solve(n, E1))) < 1e-12
+
+
+def test_ranges_order_reads_earlier_ranges_only():
+    """What sets the ranges order apart, checked against the synchronous order:
+    (a) one sweep gives range 0 exactly the synchronous values (it reads only
+    start-of-sweep ranks) and gives a later vertex the synchronous value
+    whenever none of its in-neighbours lies in an earlier range;
+    (b) a later vertex with an in-neighbour in an earlier range gets Eq. 1
+    evaluated on the updated ranks of that range;
+    (c) a graph with no edge between ranges, and any graph below 1024
+    vertices (one range), gives the synchronous result bit for bit."""
+    n = 1280
+    b = range_bounds(n)
+    src, dst = random_graph(n, 5000, 43)
+    g = oracle.Graph(n, src, dst)
+    r0 = np.random.default_rng(44).random(n)
+    r0 /= r0.sum()
+    rs, _ = g.update("nd", tau=0.0, max_iter=1, r_prev=r0)
+    rr, _ = g.update("nd", tau=0.0, max_iter=1, r_prev=r0, order="ranges")
+    rng_of = np.searchsorted(b, np.arange(n), side="right") - 1
+    off, adj = g.in_csr()
+    ooff, _ = g.out_csr()
+    deg = np.diff(ooff)
+    for v in range(n):
+        ins = adj[off[v]:off[v + 1]]
+        early = ins[rng_of[ins] < rng_of[v]]
+        if early.size == 0:
+            assert rr[v] == rs[v], v
+        else:
+            mixed = np.where(rng_of[ins] < rng_of[v], rr[ins], r0[ins]) / deg[ins]
+            expect = (1 - ALPHA) / n + ALPHA * mixed.sum()
+            assert rr[v] == pytest.approx(expect, rel=1e-12, abs=0), v
+    # (c) no edge between ranges
+    keep = rng_of[src] == rng_of[dst]
+    g2 = oracle.Graph(n, src[keep], dst[keep])
+    for m in ("static", "dfp"):
+        x, sx = g2.update(m, r_prev=r0)
+        y, sy = g2.update(m, r_prev=r0, order="ranges")
+        assert np.array_equal(x, y) and sx == sy
+    s3, d3 = random_graph(900, 4000, 45)
+    g3 = oracle.Graph(900, s3, d3)
+    x, sx = g3.update("static")
+    y, sy = g3.update("static", order="ranges")
+    assert np.array_equal(x, y) and sx == sy
