@@ -409,17 +409,19 @@ pr_status pr_group_set_tuning(pr_group* grp, const pr_group_tuning* in);
  *     are merged in arrival order into one batch (per edge the last operation
  *     wins, deletions of a request before its insertions; the resulting edge
  *     set is the one the requests give one after another, Sec. 3.2).  Batches
- *     are applied while the previous group update runs, and every graph with
- *     an applied batch joins the next group update (one launch pair per
- *     iteration for all of them, the loop on the device); a round of one or
- *     two graphs with no request waiting for an idle graph runs pr_update on
- *     each instead.  A round admits
+ *     are applied while the updates of other graphs run.  A small graph
+ *     (below PR_DEVICE_LOOP_SLOTS in-CSR slots) with an applied batch joins
+ *     the next group update (one launch pair per iteration for all of them,
+ *     the loop on the device); a large graph is updated with pr_update by a
+ *     second server thread, large graphs one after another (pr_update picks
+ *     the push or pull form per iteration), while group updates and batch
+ *     edits of other graphs go on.  A round admits
  *     graphs while their estimated batch scratch leaves hbm_reserve bytes of
  *     device memory free and the round's edges stay within max_round_edges
  *     (0: no cap); the first graph of a round is always admitted.
  *   PR_SERVE_PLAIN: one pr_apply_batch + pr_update per request, in arrival
  *     order (the baseline).
- * While the server runs, the graphs' work is on a stream of the server's
+ * While the server runs, each graph's work is on a stream of the server's
  * (pr_set_stream; the previous streams are restored by pr_server_destroy) and
  * the caller must not use the graphs.  Every graph needs ranks.
  */

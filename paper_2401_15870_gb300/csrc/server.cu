@@ -14,15 +14,16 @@
 //      set as applying the requests one after another, Sec. 3.2) and apply it
 //      on the graphs' stream -- this overlaps with the group update already
 //      running on the group stream;
-//   3. hand the READY graphs to the device: while few graphs are READY (at
-//      most SOLO_MAX_GRAPHS), they go, once the solo thread is free, to the
-//      solo thread, which runs pr_update on each in turn (its host loop picks
-//      the push or pull form per iteration, cheaper than the pull-only group
-//      form when a frontier starts small on a large graph; updates of large
-//      graphs that ran side by side would each take about as long as both in
-//      turn, which only lengthens the first one's latency); when more are
-//      READY and no group update is running, one group update (pr_group
-//      machinery) takes them all;
+//   3. hand the READY graphs to the device: a large graph (at least
+//      PR_DEVICE_LOOP_SLOTS in-CSR slots) goes to the solo thread, which runs
+//      pr_update on such graphs one after another (its host loop picks the
+//      push or pull form per iteration, much cheaper than the pull-only group
+//      form when a batch's frontier starts small on a large graph; large
+//      updates run side by side would each take about as long as both in
+//      turn, which only lengthens the first one's latency); the small graphs
+//      -- those pr_update itself runs as a one-graph group -- go, when no
+//      group update is running, into one group update (pr_group machinery)
+//      together;
 //   4. when the running group update has finished, complete its requests.
 // Every graph has its own stream while the server runs, so a solo update, the
 // group update and the batch edits of other graphs overlap on the device; the
@@ -64,11 +65,9 @@ enum GraphState { IDLE = 0, READY = 1, IN_FLIGHT = 2 };
 // sort buffers, flags, row staging), for admission
 constexpr int64_t BYTES_PER_BATCH_EDGE = 160;
 constexpr int64_t BYTES_PER_BATCH = 4 << 20;
-// rounds of at most this many READY graphs go to the solo thread (one
-// pr_update per graph, in turn) instead of a group update
-constexpr size_t SOLO_MAX_GRAPHS = 2;
-// threads that run solo updates, each on its graph's own stream
-constexpr int SOLO_THREADS = 1;
+// a graph with at least this many in-CSR slots is updated by the solo thread
+// (pr_update), the others by group updates
+bool large_graph(const pr_graph* g) { return g->g.in.cap >= PR_DEVICE_LOOP_SLOTS; }
 
 }  // namespace
 
@@ -89,7 +88,7 @@ struct pr_server {
   int64_t outstanding = 0;
   bool stop = false;
   std::thread worker;
-  // solo updates: graphs queued by the worker, run by the solo threads
+  // solo updates: large graphs queued by the worker, run by the solo thread
   std::vector<std::thread> solo;
   std::condition_variable cv_solo;
   std::deque<std::pair<int32_t, int64_t>> solo_q;   // (graph, round)
@@ -203,7 +202,8 @@ void run_plain(pr_server* S) {
   }
 }
 
-// a solo thread: one pr_update per queued graph, on the graph's own stream
+// the solo thread: one pr_update per queued graph, in turn, each on the
+// graph's own stream
 void run_solo(pr_server* S) {
   for (;;) {
     std::pair<int32_t, int64_t> job;
@@ -245,10 +245,9 @@ void run_grouped(pr_server* S) {
       };
       // READY graphs that step 4 would hand to the device now
       auto can_launch = [&] {
-        size_t ready = 0;
-        for (int i = 0; i < G; i++) ready += S->state[i] == READY;
-        if (ready == 0) return false;
-        return ready <= SOLO_MAX_GRAPHS ? S->solo_busy < SOLO_THREADS : !in_flight;
+        for (int i = 0; i < G; i++)
+          if (S->state[i] == READY && (large_graph(S->graphs[i]) || !in_flight)) return true;
+        return false;
       };
       if (!has_work() && !can_launch()) {
         if (in_flight) {
@@ -324,31 +323,27 @@ void run_grouped(pr_server* S) {
       in_flight = false;
       S->cv_work.notify_all();
     }
-    // 4. hand the READY graphs to the solo threads or to one group update
-    std::vector<int32_t> ready;
-    int solo_free = 0;
+    // 4. hand the READY graphs to the solo thread (large) or to one group
+    //    update (small)
+    std::vector<int32_t> big, small;
     {
       std::lock_guard<std::mutex> lk(S->mu);
       for (int i = 0; i < G; i++)
-        if (S->state[i] == READY) ready.push_back(i);
-      solo_free = SOLO_THREADS - S->solo_busy;
-    }
-    if (ready.empty()) continue;
-    const bool few = ready.size() <= SOLO_MAX_GRAPHS;
-    if (few && solo_free > 0) {
-      {
-        std::lock_guard<std::mutex> lk(S->mu);
-        for (int32_t gi : ready) {
-          S->state[gi] = IN_FLIGHT;
-          S->solo_q.emplace_back(gi, S->round++);
-          S->solo_busy++;
-        }
+        if (S->state[i] == READY) (large_graph(S->graphs[i]) ? big : small).push_back(i);
+      for (int32_t gi : big) {
+        S->state[gi] = IN_FLIGHT;
+        S->solo_q.emplace_back(gi, S->round++);
+        S->solo_busy++;
       }
-      S->cv_solo.notify_all();
+    }
+    if (!big.empty()) S->cv_solo.notify_all();
+    if (big.empty() && small.empty()) continue;
+    if (small.empty() || !in_flight) {
       S->ready_bytes = 0;
       S->ready_edges = 0;
-    } else if (!few && !in_flight) {
-      S->members = ready;
+    }
+    if (!small.empty() && !in_flight) {
+      S->members = small;
       pr_status rc = group_launch(S->group, (pr_method)S->opt.method, S->opt.alpha, S->opt.tau, &S->opt.opts,
                                   S->members.data(), (int32_t)S->members.size());
       if (rc != PR_OK) {
@@ -363,8 +358,6 @@ void run_grouped(pr_server* S) {
         in_flight = true;
         flight_round = S->round++;
       }
-      S->ready_bytes = 0;
-      S->ready_edges = 0;
     }
   }
 }
@@ -453,11 +446,10 @@ pr_status pr_server_create(int32_t count, pr_graph* const* graphs, const pr_serv
     else run_grouped(S);
   });
   if (opts->mode == PR_SERVE_GROUPED)
-    for (int k = 0; k < SOLO_THREADS; k++)
-      S->solo.emplace_back([S, dev] {
-        cudaSetDevice(dev);
-        run_solo(S);
-      });
+    S->solo.emplace_back([S, dev] {
+      cudaSetDevice(dev);
+      run_solo(S);
+    });
   *out = S;
   return PR_OK;
 }

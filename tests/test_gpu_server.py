@@ -34,7 +34,7 @@ def build(pr, specs):
         src, dst = synth.rmat(scale, ef * n, seed)
         A = pr.Graph.from_edges(n, src, dst)
         B = pr.Graph.from_edges(n, src, dst)
-        O = oracle.Graph(n, src, dst)
+        O = oracle.Graph(n, src, dst, parallel=scale >= 18)
         A.update("static")
         B.set_ranks(A.ranks())
         out.append(dict(n=n, src=src, dst=dst, A=A, B=B, O=O, r0=A.ranks()))
@@ -177,3 +177,19 @@ def test_server_errors(lib):
     finally:
         srv.close()
     G.update("dfp")                                  # the graph is usable again afterwards
+
+
+def test_large_graph_is_served_beside_group_updates(lib):
+    """A graph of at least PR_DEVICE_LOOP_SLOTS in-CSR slots is updated by the
+    server's solo thread (pr_update, one large graph after another) while the
+    small graphs go through group updates; every round still equals its
+    replay with plain calls bit for bit and the oracle's DF-P within 1e-9."""
+    cases = build(lib, [(20, 16, 41), (10, 8, 42), (12, 16, 43)])
+    reqs = make_requests(cases, 30, 8, max_size=2000)
+    infos = run_server(lib, cases, reqs, mode="grouped")
+    by = replay(cases, reqs, infos)
+    big_rounds = {i.round for i in infos if i.graph == 0}
+    small_rounds = {i.round for i in infos if i.graph != 0}
+    assert not (big_rounds & small_rounds)               # the large graph never joins a group update
+    for c in cases:
+        assert np.array_equal(c["A"].ranks(), c["B"].ranks())
