@@ -165,14 +165,14 @@ static pr_status alloc_state(pr_graph* h) {
   TRY(dalloc(g, (void**)&g->done, sizeof(int32_t) * (cdiv(n, 128) + 1)));
   TRY(cudaMemsetAsync(g->done, 0, sizeof(int32_t) * (cdiv(n, 128) + 1), g->stream));
   TRY(dalloc(g, (void**)&g->tab_sc, sizeof(double) * TAB));
-  TRY(dalloc(g, (void**)&g->tab_cl, sizeof(double) * TAB));
+  TRY(dalloc(g, (void**)&g->tab_ab, sizeof(double2) * TAB));
   TRY(dalloc(g, (void**)&g->ctl, sizeof(Ctl)));
   TRY(cudaMemsetAsync(g->ctl, 0, sizeof(Ctl), g->stream));
   TRY(cudaMallocHost((void**)&g->ctl_h, sizeof(Ctl)));
   TRY(dalloc(g, (void**)&h->lbits_tmp, sizeof(int32_t) * bits_to_list_tmp(n)));
   TRY(dalloc(g, (void**)&h->ls_tmp, sizeof(int64_t) * list_scan_tmp(n)));
   TRY(dalloc(g, (void**)&h->vec_tmp, sizeof(double) * (n > 4 ? n : 4)));
-  TRY(launch_tables(g->tab_sc, g->tab_cl, 0.85, g->stream));
+  TRY(launch_tables(g->tab_sc, g->tab_ab, 0.85, g->n, g->stream));
   g->tab_alpha = 0.85;
   for (int i = 0; i < 6; i++) TRY(cudaEventCreate(&h->ev[i]));
   return PR_OK;
@@ -277,7 +277,7 @@ SweepParams dfpr::base_params(Graph* g, double alpha, double tau_f, double tau_p
   p.R = g->R;
   p.rnew = g->rnew;
   p.tab_sc = g->tab_sc;
-  p.tab_cl = g->tab_cl;
+  p.tab_ab = g->tab_ab;
   p.alpha = alpha;
   p.C0 = (1.0 - alpha) / (double)g->n;
   p.tau_f = tau_f;
@@ -443,7 +443,7 @@ pr_status dfpr::run_update(pr_graph* h, int method, double alpha, double tau, do
   int32_t n = g->n;
   TRY(cudaEventRecord(h->ev[2], s));
   if (g->tab_alpha != alpha) {
-    TRY(launch_tables(g->tab_sc, g->tab_cl, alpha, s));
+    TRY(launch_tables(g->tab_sc, g->tab_ab, alpha, n, s));
     g->tab_alpha = alpha;
   }
   SweepParams p = base_params(g, alpha, tau_f, tau_p);

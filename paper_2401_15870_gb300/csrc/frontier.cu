@@ -1,6 +1,7 @@
 // frontier.cu -- initial marking (Alg. 1), reachability helpers (Sec. 3.3.2),
 // per-iteration bookkeeping, contribution refresh.
 #include "frontier.cuh"
+#include "sweep.cuh"
 #include "prim.cuh"
 
 namespace dfpr {
@@ -191,21 +192,20 @@ cudaError_t launch_control(Ctl* ctl, int frontier, cudaStream_t s) {
   return cudaGetLastError();
 }
 
-__global__ void k_tables(double* tab_sc, double* tab_cl, double alpha) {
+__global__ void k_tables(double* tab_sc, double2* tab_ab, double alpha, int32_t n) {
   GRID_STRIDE(d, TAB) {
     if (d == 0) {
       tab_sc[0] = 0.0;
-      tab_cl[0] = 0.0;
+      if (tab_ab) tab_ab[0] = make_double2(0.0, 0.0);
     } else {
-      double dd = (double)d;
-      tab_sc[d] = FIX_ONE / dd;
-      tab_cl[d] = 1.0 / (1.0 - alpha / dd);
+      tab_sc[d] = FIX_ONE / (double)d;
+      if (tab_ab) tab_ab[d] = closed_coeffs(alpha, n, (int32_t)d);
     }
   }
 }
 
-cudaError_t launch_tables(double* tab_sc, double* tab_cl, double alpha, cudaStream_t s) {
-  note_launch(); k_tables<<<cdiv(TAB, 256), 256, 0, s>>>(tab_sc, tab_cl, alpha);
+cudaError_t launch_tables(double* tab_sc, double2* tab_ab, double alpha, int32_t n, cudaStream_t s) {
+  note_launch(); k_tables<<<cdiv(TAB, 256), 256, 0, s>>>(tab_sc, tab_ab, alpha, n);
   return cudaGetLastError();
 }
 

@@ -28,8 +28,9 @@ cudaError_t launch_bits_or(const uint32_t* a, const uint32_t* b, uint32_t* out, 
 // end-of-iteration bookkeeping (one thread); frontier != 0 swaps the worklists
 cudaError_t launch_control(Ctl* ctl, int frontier, cudaStream_t s);
 
-// tables: tab_sc[d] = 2^61 / d, tab_cl[d] = 1 / (1 - alpha/d) for d in [1, TAB)
-cudaError_t launch_tables(double* tab_sc, double* tab_cl, double alpha, cudaStream_t s);
+// tables for d in [1, TAB): tab_sc[d] = 2^61 / d and, unless tab_ab is NULL,
+// tab_ab[d] = closed_coeffs(alpha, n, d) (the coefficients of Eq. 2 as one FMA)
+cudaError_t launch_tables(double* tab_sc, double2* tab_ab, double alpha, int32_t n, cudaStream_t s);
 // R = 1/n for all v; C from R
 cudaError_t launch_init_uniform(double* R, long long* C, const int32_t* odeg, const double* tab_sc, int32_t n,
                                 cudaStream_t s);

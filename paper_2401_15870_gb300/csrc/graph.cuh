@@ -57,9 +57,10 @@ struct Graph {
   int ccur = 0;                 // which C buffer is current
   bool has_ranks = false;
 
-  // tables indexed by out-degree d in [0, TAB): 2^61/d and 1/(1 - alpha/d)
+  // tables indexed by out-degree d in [0, TAB): 2^61/d, and the coefficients
+  // of Eq. 2 as one FMA (closed_coeffs, for this graph's n and tab_alpha)
   double* tab_sc = nullptr;
-  double* tab_cl = nullptr;
+  double2* tab_ab = nullptr;
   double tab_alpha = -1.0;
 
   // frontier state

@@ -63,6 +63,7 @@ struct GDesc {
   int64_t n_dmin, n_dplus;
   int32_t n, id_bits;
   double C0;
+  const double2* tab_ab;   // the graph's own Eq. 2 coefficients (its n, the group's alpha)
 };
 
 // per graph, written by the loop
@@ -84,7 +85,6 @@ struct GRun {
   const int64_t* bpre;   // bitset words
   const int64_t* dpre;   // changed edges (deletions then insertions)
   const double* tab_sc;
-  const double* tab_cl;
 };
 
 // the largest g in [0, G) with pre[g] <= u (pre[0] = 0 <= u < pre[G]); graphs
@@ -215,7 +215,7 @@ struct GView {
   uint32_t* X_next;
   uint32_t* ever;
   const double* tab_sc;
-  const double* tab_cl;
+  const double2* tab_ab;
   double alpha, C0, tau_f, tau_p;
   int32_t metric;
 };
@@ -273,7 +273,7 @@ __global__ void __launch_bounds__(GR_THREADS, 2) k_g_finish(const GRun* __restri
     p.X_next = d.X[c ^ 1];
     p.ever = d.ever;
     p.tab_sc = run->tab_sc;
-    p.tab_cl = run->tab_cl;
+    p.tab_ab = d.tab_ab;
     p.alpha = run->alpha;
     p.C0 = d.C0;
     p.tau_f = run->tau_f;
@@ -333,7 +333,6 @@ struct pr_group {
   GState* d_state = nullptr;
   int64_t* d_pre = nullptr;
   double* tab_sc = nullptr;
-  double* tab_cl = nullptr;
   double tab_alpha = -1.0;
   // pinned host staging
   GRun* h_run = nullptr;
@@ -364,8 +363,7 @@ static void group_free(pr_group* q) {
   if (!q) return;
   if (q->stream) cudaStreamSynchronize(q->stream);
   for (int k = 0; k < 2; k++) drop_exec(q, k);
-  for (void* p : {(void*)q->d_run, (void*)q->d_desc, (void*)q->d_state, (void*)q->d_pre, (void*)q->tab_sc,
-                  (void*)q->tab_cl})
+  for (void* p : {(void*)q->d_run, (void*)q->d_desc, (void*)q->d_state, (void*)q->d_pre, (void*)q->tab_sc})
     if (p) cudaFree(p);
   for (void* p : {(void*)q->h_run, (void*)q->h_desc, (void*)q->h_state, (void*)q->h_pre})
     if (p) cudaFreeHost(p);
@@ -507,7 +505,6 @@ pr_status pr_group_create(int32_t count, pr_graph* const* graphs, void* stream, 
             dev_malloc((void**)&q->d_state, sizeof(GState) * count) == cudaSuccess &&
             dev_malloc((void**)&q->d_pre, sizeof(int64_t) * pre_elems) == cudaSuccess &&
             dev_malloc((void**)&q->tab_sc, sizeof(double) * TAB) == cudaSuccess &&
-            dev_malloc((void**)&q->tab_cl, sizeof(double) * TAB) == cudaSuccess &&
             cudaMallocHost((void**)&q->h_run, sizeof(GRun)) == cudaSuccess &&
             cudaMallocHost((void**)&q->h_desc, sizeof(GDesc) * count) == cudaSuccess &&
             cudaMallocHost((void**)&q->h_state, sizeof(GState) * count) == cudaSuccess &&
@@ -625,6 +622,7 @@ pr_status group_launch(pr_group* q, pr_method method, double alpha, double tau, 
     d.n = g->n;
     d.id_bits = g->id_bits;
     d.C0 = (1.0 - alpha) / (double)g->n;
+    d.tab_ab = g->tab_ab;
     wpre[i + 1] = wpre[i] + cdiv(d.nquads, 32 * GR_QPT[q->qi] * GR_STEPS[q->qi]);
     fpre[i + 1] = fpre[i] + cdiv(cdiv((int64_t)g->n, 32), GR_FU[q->fi]);
     bpre[i + 1] = bpre[i] + cdiv((int64_t)g->n, 32);
@@ -645,7 +643,6 @@ pr_status group_launch(pr_group* q, pr_method method, double alpha, double tau, 
   r.bpre = q->d_pre + 2 * (G + 1);
   r.dpre = q->d_pre + 3 * (G + 1);
   r.tab_sc = q->tab_sc;
-  r.tab_cl = q->tab_cl;
   r.use_graph = (o.flags & PR_OPT_HOST_LOOP) ? 0 : 1;
   r.metric = (o.flags & PR_OPT_MEASURE_ABSOLUTE) ? METRIC_ABSOLUTE
              : (o.flags & PR_OPT_MEASURE_CONTRIB) ? METRIC_CONTRIB
@@ -660,8 +657,17 @@ pr_status group_launch(pr_group* q, pr_method method, double alpha, double tau, 
   }
   if (cudaEventRecord(q->ev[0], s) != cudaSuccess) return PR_ECUDA;
   if (q->tab_alpha != alpha) {
-    if (launch_tables(q->tab_sc, q->tab_cl, alpha, s) != cudaSuccess) return PR_ECUDA;
+    if (launch_tables(q->tab_sc, nullptr, alpha, 1, s) != cudaSuccess) return PR_ECUDA;
     q->tab_alpha = alpha;
+  }
+  // each member's own Eq. 2 coefficients for this alpha (after the work
+  // already queued on its stream, which the waits above order before s)
+  for (int i = 0; i < G; i++) {
+    Graph* g = &q->graphs[mem[i]]->g;
+    if (g->tab_alpha != alpha) {
+      if (launch_tables(g->tab_sc, g->tab_ab, alpha, g->n, s) != cudaSuccess) return PR_ECUDA;
+      g->tab_alpha = alpha;
+    }
   }
   if (cudaMemcpyAsync(q->d_pre, q->h_pre, sizeof(int64_t) * 4 * (size_t)(G + 1), cudaMemcpyHostToDevice, s) !=
           cudaSuccess ||

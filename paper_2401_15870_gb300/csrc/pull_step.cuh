@@ -193,7 +193,7 @@ struct PullTotals {
 };
 
 // chunks [ch0, ch0 + U) of one graph.  P provides n, odeg, ideg, R, Ccur,
-// Cnext, S_cur, S_next, X_next, ever, tab_sc, tab_cl, alpha, C0, tau_f, tau_p,
+// Cnext, S_cur, S_next, X_next, ever, tab_sc, tab_ab, alpha, C0, tau_f, tau_p,
 // metric (unless REL).
 // The accumulators and the expanded-source words it reads are left zero for
 // the next sweep.  L2: read them from L2 (they were written by other SMs in
@@ -237,10 +237,10 @@ __device__ __forceinline__ void finish_pull_step(const P& p, long long* __restri
     if (member[u]) {
       double r;
       if (CLOSED) {
-        // Eq. 2, the self term removed exactly in fixed point
+        // Eq. 2, the self term removed exactly in fixed point, as one FMA
         const long long K = sum[u] - cself[u];
-        const double f = d[u] < TAB ? p.tab_cl[d[u]] : 1.0 / (1.0 - p.alpha / (double)d[u]);
-        r = f * fma(alpha_fix, (double)K, p.C0);
+        const double2 ab = d[u] < TAB ? p.tab_ab[d[u]] : closed_coeffs(p.alpha, p.n, d[u]);
+        r = fma(ab.x, (double)K, ab.y);
       } else {
         r = fma(alpha_fix, (double)sum[u], p.C0);   // Eq. 1
       }

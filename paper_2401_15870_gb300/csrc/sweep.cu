@@ -184,12 +184,12 @@ __device__ __forceinline__ void finalize(const SweepParams& p, int32_t k, int32_
   if (closed) {
     // Eq. 2: K = sum over in-neighbours minus the vertex's own self-loop term,
     // r = (C0 + alpha K) / (1 - alpha/d); the self term is removed exactly in
-    // fixed point
-    // (one rounding for C0 + alpha K, as in the every-vertex epilogues, so
-    // that push and pull forms give bit-identical ranks)
+    // fixed point, and the expression is one FMA with the coefficients of
+    // closed_coeffs, as in the every-vertex epilogues, so that push and pull
+    // forms give bit-identical ranks
     long long K = sum - p.Ccur[v];
-    double f = d < TAB ? p.tab_cl[d] : 1.0 / (1.0 - p.alpha / (double)d);
-    r = f * fma(p.alpha * FIX_INV, (double)K, p.C0);
+    const double2 ab = d < TAB ? p.tab_ab[d] : closed_coeffs(p.alpha, p.n, d);
+    r = fma(ab.x, (double)K, ab.y);
   } else {
     // Eq. 1: r = C0 + alpha c
     r = fma(p.alpha * FIX_INV, (double)sum, p.C0);

@@ -36,6 +36,16 @@ __device__ __forceinline__ double measure_base(int metric, double mr, int32_t d)
   return metric == METRIC_RELATIVE ? mr : (metric == METRIC_ABSOLUTE ? 1.0 : degree_as_double(d));
 }
 
+// Eq. 2 as one FMA: r = f (C0 + alpha K 2^-61) with f = 1 / (1 - alpha/d) is
+// evaluated as fma(a, K, b), a = f alpha 2^-61, b = f C0, C0 = (1 - alpha)/n;
+// the tables hold (a, b) for d < TAB, and larger degrees compute them here
+// with the same operations, so both give the same bits
+__device__ __forceinline__ double2 closed_coeffs(double alpha, int32_t n, int32_t d) {
+  const double f = 1.0 / (1.0 - alpha / (double)d);
+  const double C0 = (1.0 - alpha) / (double)n;
+  return make_double2(f * (alpha * FIX_INV), f * C0);
+}
+
 struct SweepParams {
   int32_t n;
   const int64_t* ioff;
@@ -47,7 +57,7 @@ struct SweepParams {
   double* R;
   double* rnew;              // LIST / DF / DFP
   const double* tab_sc;      // 2^61 / d
-  const double* tab_cl;      // 1 / (1 - alpha/d)
+  const double2* tab_ab;     // closed_coeffs(alpha, n, d): Eq. 2 as fma(a, K, b)
   double alpha, C0, tau_f, tau_p;
   // contributions of vertices below `hot` are gathered with an L2 evict-last
   // policy and the rest with evict-first, so the most-read contributions

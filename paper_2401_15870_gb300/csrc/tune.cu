@@ -89,7 +89,7 @@ pr_status tune_sweeps(pr_graph* h, double alpha, int32_t reps, GatherCfg* best, 
   Graph* g = &h->g;
   cudaStream_t s = g->stream;
   if (g->tab_alpha != alpha) {
-    cudaError_t e = launch_tables(g->tab_sc, g->tab_cl, alpha, s);
+    cudaError_t e = launch_tables(g->tab_sc, g->tab_ab, alpha, g->n, s);
     if (e != cudaSuccess) return (pr_status)cuda_fail(g, e, "pr_autotune");
     g->tab_alpha = alpha;
   }
