@@ -212,8 +212,12 @@ __device__ __forceinline__ void finish_pull_step(const P& p, long long* __restri
   const bool inplace = p.Cnext == p.Ccur;
   long long sum[U], cself[U];
   double Rv[U];
-  int32_t d[U];
+  int32_t d[U], din[U];
   bool member[U], valid[U];
+  // every load of a vertex is issued up front, whether or not it turns out
+  // to be a member: waiting for the membership words before loading the
+  // members' data would chain two global-memory latencies, which is what
+  // bounds this epilogue (long scoreboard stalls), not the extra bytes
 #pragma unroll
   for (int u = 0; u < U; u++) {
     const int64_t ch = ch0 + u;
@@ -224,9 +228,10 @@ __device__ __forceinline__ void finish_pull_step(const P& p, long long* __restri
     member[u] = valid[u] && ((in_f >> lane) & 1u);
     sum[u] = valid[u] ? (L2 ? __ldcg(acc + v) : acc[v]) : 0;
     // the own contribution: Eq. 2's self term, or the entry a non-member copies
-    cself[u] = (CLOSED ? member[u] : false) || (valid[u] && !member[u] && !inplace) ? p.Ccur[v] : 0;
-    Rv[u] = member[u] ? p.R[v] : 0.0;
-    d[u] = member[u] ? p.odeg[v] : 1;
+    cself[u] = (CLOSED || !inplace) && valid[u] ? p.Ccur[v] : 0;
+    Rv[u] = valid[u] ? p.R[v] : 0.0;
+    d[u] = valid[u] ? p.odeg[v] : 1;
+    din[u] = valid[u] ? p.ideg[v] : 0;
   }
 #pragma unroll
   for (int u = 0; u < U; u++) {
@@ -246,7 +251,7 @@ __device__ __forceinline__ void finish_pull_step(const P& p, long long* __restri
       }
       const unsigned long long drb = dbits(fabs(r - Rv[u]));
       t.dmax = drb > t.dmax ? drb : t.dmax;
-      t.edges += p.ideg[v];
+      t.edges += din[u];
       t.verts += 1;
       p.R[v] = r;
       const double sc = d[u] < TAB ? p.tab_sc[d[u]] : FIX_ONE / (double)d[u];

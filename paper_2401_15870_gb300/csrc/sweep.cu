@@ -393,7 +393,7 @@ __global__ void __launch_bounds__(1024) k_gather_rows(const int32_t* __restrict_
 
 // (the 32-vertex chunks [ch_lo, ch_hi); ch_lo a multiple of FIN_U)
 template <bool CLOSED, bool REL, bool SAME = false>
-__global__ void __launch_bounds__(256, 4) k_finish_pull(SweepParams p, long long* __restrict__ acc,
+__global__ void __launch_bounds__(256, 3) k_finish_pull(SweepParams p, long long* __restrict__ acc,
                                                         uint32_t* __restrict__ anyb, int64_t ch_lo, int64_t ch_hi) {
   const int lane = threadIdx.x & 31;
   const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
