@@ -43,10 +43,10 @@ ALPHA, TAU = 0.85, 1e-10
 SWEEP_BYTES_PER_EDGE = 12
 SWEEP_BYTES_PER_VERTEX = 60
 # DRAM bytes (read + write) of one pull-form DF-P sweep (k_gather_rows + k_finish_pull) on the
-# default workload, from the one-pass ncu captures under profiles/, keyed by the gather setting
-# (threads, quads per lane, hub vertices, fused epilogue, ranges); a setting without a capture of the
-# current kernels reports null
-SWEEP_DRAM_BYTES_RMAT25 = {}
+# default workload, from the ncu capture of the current kernels under profiles/ (R-MAT scale 24,
+# scaled by the in-edges walked), keyed by the gather setting (threads, quads per lane, hub vertices,
+# fused epilogue, ranges); a setting without a capture of the current kernels reports null
+SWEEP_DRAM_BYTES_RMAT25 = {(1024, 2, 0, 0, 1): 11.3e9}
 
 
 def parse():
