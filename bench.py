@@ -60,6 +60,8 @@ def parse():
     ap.add_argument("--batch-frac", type=float, default=1e-4)
     ap.add_argument("--seed", type=int, default=2000)
     ap.add_argument("--e2e-steps", type=int, default=5)
+    ap.add_argument("--async-steps", type=int, default=5,
+                    help="large: DF-P steps in the asynchronous order after the timed ones (reported in detail)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--workload", default="large",
                     choices=["large", "batched", "serving", "methods", "temporal", "tolerances", "orders", "settings"],
@@ -307,6 +309,7 @@ def run_gpu(a, rank, world, local_rank):
     size = max(1, int(round(a.batch_frac * m0)))
     nb = a.warmup + a.steps
     dev_batches = [sg.batch(n, src, dst, size, seed + 1 + i) for i in range(nb)]
+    async_batches = [sg.batch(n, src, dst, size, seed + 300001 + i) for i in range(a.async_steps)]
     host_batches = []
     for i in range(a.e2e_steps):
         bt = sg.batch(n, src, dst, size, seed + 100001 + i)
@@ -400,6 +403,23 @@ def run_gpu(a, rank, world, local_rank):
         h2d = sum(t.numel() * 4 for t in host_batches[0])
         d2h = n * 8
         e2e_ms = max_over_ranks(e2e_ms, world, dev)
+    # the asynchronous order of Alg. 1 (PR_OPT_ASYNC: eight vertex ranges in turn) on the same kind of
+    # steps, after everything timed: a reported alternative, not the headline (the synchronous order
+    # is the library's canonical reading)
+    async_detail = None
+    if a.async_steps > 0:
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        ast = []
+        for b in async_batches:
+            G.apply_batch_device(*b)
+            ast.append(G.update("dfp", alpha=ALPHA, tau=TAU, order="async"))
+        e1.record(stream)
+        torch.cuda.synchronize()
+        async_detail = {"updates_per_s": a.async_steps / (e0.elapsed_time(e1) / 1000.0),
+                        "iterations_mean": statistics.mean(s.iterations for s in ast),
+                        "ms_update_mean": statistics.mean(s.ms_update for s in ast)}
     # one every-vertex sweep with the tuned setting (after everything timed)
     st_nd = G.update("nd", alpha=ALPHA, tau=TAU, max_iter=2, time_sweeps=True, loop="host")
     if rank != 0:
@@ -444,6 +464,7 @@ def run_gpu(a, rank, world, local_rank):
             "full_sweep_ms": st_nd.ms_sweep / max(st_nd.sweeps, 1),
             "full_sweep_gbs": (SWEEP_BYTES_PER_EDGE * st_nd.edges_processed + 40 * st_nd.vertices_processed)
             / (st_nd.ms_sweep / 1000.0) / 1e9 if st_nd.ms_sweep else None,
+            "async_order": async_detail,
         },
     }
     if cpu_base is not None:
@@ -609,7 +630,9 @@ def run_batched(a, rank, world, local_rank):
             max(1, sum(s.iterations * m for step in st_g for s, (_, m, _) in zip(step, sizes))),
             "iterations_max_mean": statistics.mean(max(s.iterations for s in step) for step in st_g),
             "iterations_mean": statistics.mean(s.iterations for s in flat),
-            "ms_apply_sum_mean": statistics.mean(sum(s.ms_apply for s in step) for step in st_g),
+            # the batch chains of the graphs overlap on the library's streams, so the
+            # edit time of a step is its time less the group update's
+            "ms_apply_step_mean": (ms_g - upd_ms) / a.steps,
             "plain_update_ms_sum_mean": statistics.mean(sum(s.ms_update for s in step) for step in st_p),
         },
     }

@@ -357,3 +357,34 @@ def test_batches_of_graphs_on_their_own_streams(lib):
         st_ = T.update("dfp")
         assert np.array_equal(G.ranks(), T.ranks())
         assert (sg_.iterations, sg_.vertices_processed) == (st_.iterations, st_.vertices_processed)
+
+
+def test_group_at_the_batched_workload_sizes(lib):
+    """The batched configuration's graph sizes (R-MAT scales 12 .. 21, edge
+    factors 8 .. 32, one 80/20 batch of 1e-4 |E| each): one group DF-P update
+    of ten graphs spanning that range equals, graph by graph, the oracle's
+    DF-P from the same previous ranks within 1e-9, with the same decisions of
+    Alg. 1."""
+    specs = [(12, 8), (13, 32), (14, 16), (15, 24), (16, 8), (17, 32), (18, 12), (19, 20), (20, 16), (21, 8)]
+    graphs, refs = [], []
+    for k, (scale, ef) in enumerate(specs):
+        n = 1 << scale
+        src, dst = synth.rmat(scale, ef * n, 7000 + k)
+        G = lib.Graph.from_edges(n, src, dst)
+        O = oracle.Graph(n, src, dst, parallel=True)
+        r0, _ = O.update("static")
+        cs, cd = synth.unique_edges(src, dst)
+        b = synth.batch(n, cs, cd, max(1, int(round(1e-4 * O.m))), 7100 + k)
+        G.apply_batch(*b)
+        O.apply_batch(*b)
+        G.set_ranks(r0)
+        graphs.append(G)
+        refs.append(O.update("dfp", r_prev=r0))
+    grp = lib.Group(graphs)
+    try:
+        stats = grp.update("dfp")
+    finally:
+        grp.close()
+    for k, (G, (ref, ost)) in enumerate(zip(graphs, refs)):
+        assert np.max(np.abs(G.ranks() - ref)) < TOL, specs[k]
+        assert_same_run(stats[k], ost, specs[k])
