@@ -657,9 +657,14 @@ static cudaError_t gather_launch(const SweepParams& p, const uint32_t* rowbits, 
   cudaError_t e = gather_occupancy(fn, threads, smem, &bps);
   if (e != cudaSuccess) return e;
   // one wave of resident blocks when each block stages a hub cache, else up
-  // to 16 blocks of 256 threads per SM; never more warps than work units
+  // to 64 blocks of 256 threads per SM (eight waves of 1024-thread blocks at
+  // two per SM: the blocks' uneven ends, from hub rows and their atomics,
+  // are spread over more, shorter blocks; DF-P pull sweeps at R-MAT 25 took
+  // 4.06 ms with two waves, 3.97 with eight, 3.99 with sixteen, 4.04 with
+  // thirty-two and 4.28 with sixty-four, and one wave 3.5% more than two);
+  // never more warps than work units
   const int64_t units = cdiv(nquads, 32 * QPT);
-  const int64_t cap = HUB || one_wave ? (int64_t)num_sms() * bps : (int64_t)num_sms() * 16 * 256 / threads;
+  const int64_t cap = HUB || one_wave ? (int64_t)num_sms() * bps : (int64_t)num_sms() * 64 * 256 / threads;
   const int grid = (int)std::max<int64_t>(1, std::min<int64_t>(cdiv(units, threads / 32), cap));
   note_launch();
   k_gather_rows<PULL, QPT, HUB><<<grid, threads, smem, s>>>(p.icol, p.Ccur, PULL ? p.X_cur : nullptr,
@@ -775,7 +780,18 @@ cudaError_t launch_full_sweep(int mode, const SweepParams& p, const GatherCfg& c
       if ((e = cudaStreamWaitEvent(fs, aux->ev[k], 0)) != cudaSuccess) return e;
     }
     const int64_t ch_lo = v_lo / 32, ch_hi = cdiv(v_hi, 32);
-    const int rgrid = grid_for(v_hi - v_lo, 256);
+    // one wave of resident epilogue blocks: every warp strides over the same
+    // number of chunks, and no partial last wave leaves most SMs idle
+    int bps = 1;
+    const bool rel = p.metric == METRIC_RELATIVE;
+    const void* fin = mode == SWEEP_FULL       ? (const void*)k_finish_full
+                      : mode == SWEEP_PULL_DF  ? (rel ? (const void*)k_finish_pull<false, true>
+                                                      : (const void*)k_finish_pull<false, false>)
+                      : rel && p.tau_f == p.tau_p ? (const void*)k_finish_pull<true, true, true>
+                      : rel                        ? (const void*)k_finish_pull<true, true>
+                                                   : (const void*)k_finish_pull<true, false>;
+    if ((e = gather_occupancy(fin, 256, 0, &bps)) != cudaSuccess) return e;
+    const int rgrid = (int)std::min<int64_t>(grid_for(v_hi - v_lo, 256), (int64_t)num_sms() * bps);
     switch (mode) {
       case SWEEP_FULL: note_launch(); k_finish_full<<<rgrid, 256, 0, fs>>>(p, p.gacc, v_lo, v_hi); break;
       case SWEEP_PULL_DF:
