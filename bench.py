@@ -46,7 +46,7 @@ SWEEP_BYTES_PER_VERTEX = 60
 # default workload, from the ncu capture of the current kernels under profiles/ (R-MAT scale 24,
 # scaled by the in-edges walked), keyed by the gather setting (threads, quads per lane, hub vertices,
 # fused epilogue, ranges); a setting without a capture of the current kernels reports null
-SWEEP_DRAM_BYTES_RMAT25 = {(1024, 2, 0, 0, 1): 11.3e9}
+SWEEP_DRAM_BYTES_RMAT25 = {(1024, 2, 0, 0, 1): 11.45e9, (512, 2, 0, 0, 1): 11.45e9}
 
 
 def parse():
