@@ -84,7 +84,8 @@ typedef struct {
  * WHILE node is driven by a control kernel (the pull form only, no host round
  * trip).  By default graphs below PR_DEVICE_LOOP_SLOTS in-CSR slots use the
  * device loop unless another flag asks for the host loop (any of the flags
- * above).  The result is the same either way. */
+ * above); the smallest run it in one kernel (PR_OPT_ONE_KERNEL below).  The
+ * result is the same either way. */
 #define PR_OPT_DEVICE_LOOP 8
 #define PR_OPT_HOST_LOOP 16
 /* pr_options.flags for DF / DF-P: the measure a processed vertex compares
@@ -114,6 +115,21 @@ typedef struct {
  * (PR_EINVAL). */
 #define PR_OPT_ASYNC 128
 #define PR_DEVICE_LOOP_SLOTS (1ll << 24)
+/* pr_options.flags for Static, ND, DF and DF-P, and for groups: the device
+ * loop in one cooperative kernel.  Initialisation, marking and every
+ * iteration's gather, epilogue and control run as phases of one launch whose
+ * blocks are all resident, separated by grid barriers, instead of three kernel
+ * launches per iteration in a CUDA graph: on graphs whose sweeps take
+ * microseconds the launches cost more than the work.  Without this flag,
+ * PR_OPT_DEVICE_LOOP or a host-loop flag, the device loop runs in one kernel
+ * when the graphs of the update hold fewer than PR_ONE_KERNEL_SLOTS in-CSR
+ * slots in all; PR_OPT_DEVICE_LOOP alone asks for the CUDA graph.  At most one
+ * of PR_OPT_HOST_LOOP, PR_OPT_DEVICE_LOOP and PR_OPT_ONE_KERNEL may be set.
+ * The result is the same bit for bit.  A barrier wait gives up after about a
+ * second (a block that never arrives); the update then returns PR_ETIMEOUT
+ * and its graphs are left without ranks. */
+#define PR_OPT_ONE_KERNEL 256
+#define PR_ONE_KERNEL_SLOTS (1ll << 20)
 
 /* Outcome of one pr_update (Sec. 5.1.5 measures time and affected vertices). */
 typedef struct {

@@ -294,6 +294,9 @@ def pr_apply_batches(handles, batches):
 
 PR_OPT_TIME_SWEEPS, PR_OPT_FORCE_PULL, PR_OPT_FORCE_PUSH = 1, 2, 4
 PR_OPT_DEVICE_LOOP, PR_OPT_HOST_LOOP = 8, 16
+PR_OPT_ONE_KERNEL = 256   # the device loop as one cooperative kernel
+PR_ONE_KERNEL_SLOTS = 1 << 20
+LOOPS = {None: 0, "device": PR_OPT_DEVICE_LOOP, "host": PR_OPT_HOST_LOOP, "one": PR_OPT_ONE_KERNEL}
 PR_OPT_ASYNC = 128   # asynchronous order (Sec. 4.4): one contribution vector, updated in place
 PR_DEVICE_LOOP_SLOTS = 1 << 24
 
@@ -305,14 +308,15 @@ def pr_update(h, method, alpha=0.85, tau=1e-10, tau_f=1e-6, tau_p=1e-6, max_iter
               direction=None, loop=None, measure=None, order="sync") -> Stats:
     """direction: None (chosen per iteration), "pull" or "push" (DF / DF-P and
     DT, host loop).
-    loop: None (by graph size), "device" or "host".  measure: the DF / DF-P
+    loop: None (by graph size), "device" (CUDA graph), "one" (one cooperative
+    kernel) or "host".  measure: the DF / DF-P
     measure compared with tau_f / tau_p: "relative" (default), "absolute" or
     "contrib".  order: "sync" (every vertex of a sweep reads the ranks of its
     start) or "async" (one contribution vector updated in place, Sec. 4.4)."""
     m = METHODS[method] if isinstance(method, str) else int(method)
     flags = (PR_OPT_TIME_SWEEPS if time_sweeps else 0) | {None: 0, "pull": PR_OPT_FORCE_PULL,
                                                           "push": PR_OPT_FORCE_PUSH}[direction]
-    flags |= {None: 0, "device": PR_OPT_DEVICE_LOOP, "host": PR_OPT_HOST_LOOP}[loop]
+    flags |= LOOPS[loop]
     flags |= MEASURES[measure]
     flags |= {"sync": 0, "async": PR_OPT_ASYNC}[order]
     opts = pr_options(tau_f, tau_p, int(max_iter), flags)
@@ -465,11 +469,11 @@ def pr_group_create(handles, stream=None):
 def pr_group_update(q, method, alpha=0.85, tau=1e-10, tau_f=1e-6, tau_p=1e-6, max_iter=500, loop=None,
                     measure=None):
     """One update of every graph of the group; returns one Stats per graph.
-    loop: None / "device" (CUDA graph) or "host" (kernels launched one by one).
-    measure: as in pr_update."""
+    loop: None (by size: one kernel below PR_ONE_KERNEL_SLOTS in-CSR slots in
+    all, else the CUDA graph), "device" (CUDA graph), "one" (one cooperative
+    kernel) or "host" (kernels launched one by one).  measure: as in pr_update."""
     m = METHODS[method] if isinstance(method, str) else int(method)
-    opts = pr_options(tau_f, tau_p, int(max_iter),
-                      {None: 0, "device": 0, "host": PR_OPT_HOST_LOOP}[loop] | MEASURES[measure])
+    opts = pr_options(tau_f, tau_p, int(max_iter), LOOPS[loop] | MEASURES[measure])
     n = _group_sizes[q.value]
     st = (pr_stats * n)()
     _check(load().pr_group_update(q, m, float(alpha), float(tau), ctypes.byref(opts), st))

@@ -1078,7 +1078,12 @@ pr_status pr_update(pr_graph* h, pr_method method, double alpha, double tau, con
     max_iter = opts->max_iter;
     flags = opts->flags;
     if (flags & ~(PR_OPT_TIME_SWEEPS | PR_OPT_FORCE_PULL | PR_OPT_FORCE_PUSH | PR_OPT_DEVICE_LOOP | PR_OPT_HOST_LOOP |
-                  PR_OPT_MEASURE_ABSOLUTE | PR_OPT_MEASURE_CONTRIB | PR_OPT_ASYNC))
+                  PR_OPT_MEASURE_ABSOLUTE | PR_OPT_MEASURE_CONTRIB | PR_OPT_ASYNC | PR_OPT_ONE_KERNEL))
+      return PR_EINVAL;
+    if ((flags & PR_OPT_ONE_KERNEL) &&
+        ((flags & (PR_OPT_DEVICE_LOOP | PR_OPT_HOST_LOOP | PR_OPT_TIME_SWEEPS | PR_OPT_FORCE_PULL | PR_OPT_FORCE_PUSH |
+                   PR_OPT_ASYNC)) ||
+         method == PR_DYNAMIC_TRAVERSAL))
       return PR_EINVAL;
     if ((flags & PR_OPT_ASYNC) &&
         ((flags & (PR_OPT_DEVICE_LOOP | PR_OPT_FORCE_PUSH)) || method == PR_DYNAMIC_TRAVERSAL))
@@ -1097,14 +1102,18 @@ pr_status pr_update(pr_graph* h, pr_method method, double alpha, double tau, con
   const bool host_flags =
       flags & (PR_OPT_HOST_LOOP | PR_OPT_TIME_SWEEPS | PR_OPT_FORCE_PULL | PR_OPT_FORCE_PUSH | PR_OPT_ASYNC);
   const bool loopable = method != PR_DYNAMIC_TRAVERSAL;
-  if (loopable && ((flags & PR_OPT_DEVICE_LOOP) || (!host_flags && g->in.cap < PR_DEVICE_LOOP_SLOTS))) {
+  if (loopable &&
+      ((flags & (PR_OPT_DEVICE_LOOP | PR_OPT_ONE_KERNEL)) || (!host_flags && g->in.cap < PR_DEVICE_LOOP_SLOTS))) {
     // the iteration loop on the device: a group of this one graph, on its stream
     if (!h->solo) {
       pr_graph* one[1] = {h};
       pr_status st = pr_group_create(1, one, g->stream, &h->solo);
       if (st != PR_OK) return st;
     }
-    pr_options o = {tau_f, tau_p, max_iter, flags & (PR_OPT_MEASURE_ABSOLUTE | PR_OPT_MEASURE_CONTRIB)};
+    // PR_OPT_DEVICE_LOOP keeps the CUDA graph, PR_OPT_ONE_KERNEL asks for one
+    // kernel, neither lets the group choose by size
+    pr_options o = {tau_f, tau_p, max_iter,
+                    flags & (PR_OPT_MEASURE_ABSOLUTE | PR_OPT_MEASURE_CONTRIB | PR_OPT_DEVICE_LOOP | PR_OPT_ONE_KERNEL)};
     return pr_group_update(h->solo, method, alpha, tau, &o, stats);
   }
   return run_update(h, (int)method, alpha, tau, tau_f, tau_p, max_iter, flags, stats);

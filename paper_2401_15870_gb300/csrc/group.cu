@@ -21,6 +21,8 @@
 // full sweep of Eq. 1.
 #include <algorithm>
 #include <cstring>
+#include <map>
+#include <mutex>
 #include <new>
 #include <vector>
 #include "dfpr.h"
@@ -42,6 +44,10 @@ constexpr int GR_QPT[4] = {2, 4, 8, 2};
 constexpr int GR_STEPS[4] = {1, 1, 1, 4};   // warp steps per gather unit (same graph, looked up once)
 constexpr int GR_NQ = 4;
 constexpr int GR_FU[3] = {1, 2, 4};
+// unit sizes of the one-kernel loop (k_g_loop): one gather warp step of 32 x 2
+// quads and one epilogue chunk per unit
+constexpr int LOOP_QPT = 2;
+constexpr int LOOP_FU = 1;
 
 // per graph, fixed during one update
 struct GDesc {
@@ -72,6 +78,7 @@ struct GState {
   unsigned long long dR_last;   // of the last finished iteration
   long long edges, verts, ever;
   int32_t cur, iter, done, converged;
+  unsigned long long dR_odd;    // the one-kernel loop: odd iterations' change (even ones in dR)
 };
 
 // the update: method, tolerances and the work-space prefixes (G + 1 each)
@@ -80,6 +87,11 @@ struct GRun {
   int32_t max_iter, method, G, loops;
   int32_t metric, pad;
   int32_t live, use_graph;   // loop condition, written to `live` instead of the WHILE node when use_graph is 0
+  // the one-kernel loop (k_g_loop): arrivals at its grid barriers (never
+  // reset: barrier k completes at k x blocks), the number of the last
+  // completed barrier, and 1 when a barrier wait ran out
+  uint32_t bar_count, bar_done;
+  int32_t err, pad2;
   const int64_t* wpre;   // gather units
   const int64_t* fpre;   // epilogue units (FIN_U chunks)
   const int64_t* bpre;   // bitset words
@@ -105,13 +117,13 @@ __device__ __forceinline__ void load_prefix(int64_t* sm, const int64_t* pre, int
 }
 
 // bitsets of every graph cleared, Static / ND frontiers set to every vertex,
-// Static ranks set to 1/n; the loop condition set from max_iter
-__global__ void __launch_bounds__(GR_THREADS) k_g_init(const GRun* __restrict__ run, const GDesc* __restrict__ desc,
-                                                       GState* __restrict__ st, cudaGraphConditionalHandle cond) {
-  extern __shared__ int64_t pre[];   // G + 1 prefix entries
+// Static ranks set to 1/n; the loop condition set from max_iter (pre: the
+// bitset-word prefix in shared memory)
+__device__ __forceinline__ void g_init_phase(const GRun* __restrict__ run, const GDesc* __restrict__ desc,
+                                             GState* __restrict__ st, cudaGraphConditionalHandle cond,
+                                             const int64_t* pre) {
   const int G = run->G;
   const int method = run->method;
-  load_prefix(pre, run->bpre, G);
   if (blockIdx.x == 0) {
     for (int g = threadIdx.x; g < G; g += blockDim.x) {
       GState z;
@@ -151,13 +163,18 @@ __global__ void __launch_bounds__(GR_THREADS) k_g_init(const GRun* __restrict__ 
   }
 }
 
+__global__ void __launch_bounds__(GR_THREADS) k_g_init(const GRun* __restrict__ run, const GDesc* __restrict__ desc,
+                                                       GState* __restrict__ st, cudaGraphConditionalHandle cond) {
+  extern __shared__ int64_t pre[];   // G + 1 prefix entries
+  load_prefix(pre, run->bpre, run->G);
+  g_init_phase(run, desc, st, cond, pre);
+}
+
 // DF / DF-P initial frontier: X <- sources of the effective change, S <-
 // targets of deleted edges
-__global__ void __launch_bounds__(GR_THREADS) k_g_mark(const GRun* __restrict__ run, const GDesc* __restrict__ desc) {
-  extern __shared__ int64_t pre[];   // G + 1 prefix entries
+__device__ __forceinline__ void g_mark_phase(const GRun* __restrict__ run, const GDesc* __restrict__ desc,
+                                             const int64_t* pre) {
   const int G = run->G;
-  if (run->method != PR_DF && run->method != PR_DFP) return;
-  load_prefix(pre, run->dpre, G);
   const int64_t total = pre[G];
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < total; i += (int64_t)gridDim.x * blockDim.x) {
     const int g = find_graph(pre, G, i);
@@ -174,32 +191,71 @@ __global__ void __launch_bounds__(GR_THREADS) k_g_mark(const GRun* __restrict__ 
   }
 }
 
+__global__ void __launch_bounds__(GR_THREADS) k_g_mark(const GRun* __restrict__ run, const GDesc* __restrict__ desc) {
+  extern __shared__ int64_t pre[];   // G + 1 prefix entries
+  if (run->method != PR_DF && run->method != PR_DFP) return;
+  load_prefix(pre, run->dpre, run->G);
+  g_mark_phase(run, desc, pre);
+}
+
 // gather phase of one iteration, every live graph (units of STEPS x 32 x QPT
 // quads: STEPS warp steps on one graph per lookup of the graph)
-template <int QPT, int STEPS>
-__global__ void __launch_bounds__(GR_THREADS) k_g_gather(const GRun* __restrict__ run, const GDesc* __restrict__ desc,
-                                                         const GState* __restrict__ st) {
-  extern __shared__ int64_t pre[];   // G + 1 prefix entries
+// Where a phase finds a graph's state: whether it is done, the parity of its
+// double buffers, and the word its epilogue adds this iteration's change to.
+// The kernels of the CUDA graph read the states in device memory, which the
+// control kernel writes between launches.
+struct StatesInMemory {
+  GState* st;
+  __device__ __forceinline__ bool done(int g) const { return st[g].done != 0; }
+  __device__ __forceinline__ int cur(int g) const { return st[g].cur; }
+  __device__ __forceinline__ unsigned long long* dR(int g) const { return &st[g].dR; }
+};
+// The one-kernel loop: every block keeps each graph's state in shared memory
+// (bit 0 done, bit 1 parity, bit 2 converged, iteration count from bit 3) and
+// closes each iteration itself from the same changes, so no barrier separates
+// the control step from the next gather; the changes of consecutive
+// iterations go to two words, so one can be read while the next is cleared.
+struct StatesInBlock {
+  GState* st;
+  const uint32_t* sm;
+  int odd;   // parity of the iteration
+  __device__ __forceinline__ bool done(int g) const { return sm[g] & 1u; }
+  __device__ __forceinline__ int cur(int g) const { return (sm[g] >> 1) & 1u; }
+  __device__ __forceinline__ unsigned long long* dR(int g) const { return odd ? &st[g].dR_odd : &st[g].dR; }
+};
+
+// COH: inside the one-kernel loop, where contributions and frontier words
+// were written earlier in the same launch
+template <int QPT, int STEPS, bool COH, class SV>
+__device__ __forceinline__ void g_gather_phase(const GRun* __restrict__ run, const GDesc* __restrict__ desc,
+                                               const SV& sv, const int64_t* pre) {
   const int G = run->G;
-  load_prefix(pre, run->wpre, G);
   const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
   const int64_t total = pre[G];
   const uint64_t pol_stream = policy_evict_first();
   const uint64_t pol_keep = policy_evict_last();
   for (int64_t u = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5; u < total; u += nw) {
     const int g = find_graph(pre, G, u);
-    if (st[g].done) continue;
+    if (sv.done(g)) continue;
     const GDesc& d = desc[g];
-    const int c = st[g].cur;
+    const int c = sv.cur(g);
     const int64_t ub = (u - pre[g]) * (STEPS * 32 * QPT);
 #pragma unroll 1
     for (int k = 0; k < STEPS; k++) {
       const int64_t base = ub + k * (32 * QPT);
       if (base >= d.nquads) break;
-      gather_step<true, QPT>(d.icol, d.C[c], d.X[c], d.S[c], d.rowbits, d.rowbase, d.nquads, d.n, d.acc, d.anyb, base,
-                             pol_stream, pol_keep);
+      gather_step<true, QPT, false, false, COH>(d.icol, d.C[c], d.X[c], d.S[c], d.rowbits, d.rowbase, d.nquads, d.n,
+                                                d.acc, d.anyb, base, pol_stream, pol_keep);
     }
   }
+}
+
+template <int QPT, int STEPS>
+__global__ void __launch_bounds__(GR_THREADS) k_g_gather(const GRun* __restrict__ run, const GDesc* __restrict__ desc,
+                                                         const GState* __restrict__ st) {
+  extern __shared__ int64_t pre[];   // G + 1 prefix entries
+  load_prefix(pre, run->wpre, run->G);
+  g_gather_phase<QPT, STEPS, false>(run, desc, StatesInMemory{const_cast<GState*>(st)}, pre);
 }
 
 // the fields finish_pull_step reads, for one graph and one parity
@@ -220,7 +276,7 @@ struct GView {
   int32_t metric;
 };
 
-__device__ __forceinline__ void flush_totals(PullTotals& t, GState* s) {
+__device__ __forceinline__ void flush_totals(PullTotals& t, GState* s, unsigned long long* dRw) {
   const int lane = threadIdx.x & 31;
   unsigned long long dm = t.dmax;
   long long e = t.edges, v = t.verts;
@@ -232,7 +288,7 @@ __device__ __forceinline__ void flush_totals(PullTotals& t, GState* s) {
     v += __shfl_xor_sync(0xffffffffu, v, o);
   }
   if (lane == 0) {
-    if (dm) atomicMax(&s->dR, dm);
+    if (dm) atomicMax(dRw, dm);
     if (e) atomicAdd(reinterpret_cast<unsigned long long*>(&s->edges), (unsigned long long)e);
     if (v) atomicAdd(reinterpret_cast<unsigned long long*>(&s->verts), (unsigned long long)v);
     if (t.ever_new) atomicAdd(reinterpret_cast<unsigned long long*>(&s->ever), (unsigned long long)t.ever_new);
@@ -242,25 +298,23 @@ __device__ __forceinline__ void flush_totals(PullTotals& t, GState* s) {
 
 // epilogue phase of one iteration, every live graph, units of FU chunks
 // (Eq. 2 for DF-P when CLOSED, else Eq. 1)
-template <bool CLOSED, int FU, bool REL>
-__global__ void __launch_bounds__(GR_THREADS, 2) k_g_finish(const GRun* __restrict__ run,
-                                                            const GDesc* __restrict__ desc, GState* __restrict__ st) {
-  extern __shared__ int64_t pre[];   // G + 1 prefix entries
+template <bool CLOSED, int FU, bool REL, bool COH, class SV>
+__device__ __forceinline__ void g_finish_phase(const GRun* __restrict__ run, const GDesc* __restrict__ desc,
+                                               const SV& sv, const int64_t* pre) {
   const int G = run->G;
-  load_prefix(pre, run->fpre, G);
   const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
   const int64_t total = pre[G];
   PullTotals t;
   int tg = -1;   // graph the totals belong to
   for (int64_t u = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5; u < total; u += nw) {
     const int g = find_graph(pre, G, u);
-    if (st[g].done) continue;
+    if (sv.done(g)) continue;
     if (g != tg) {
-      if (tg >= 0) flush_totals(t, st + tg);
+      if (tg >= 0) flush_totals(t, sv.st + tg, sv.dR(tg));
       tg = g;
     }
     const GDesc& d = desc[g];
-    const int c = st[g].cur;
+    const int c = sv.cur(g);
     GView p;
     p.n = d.n;
     p.odeg = d.odeg;
@@ -281,12 +335,20 @@ __global__ void __launch_bounds__(GR_THREADS, 2) k_g_finish(const GRun* __restri
     p.metric = run->metric;
     const int64_t nchunks = cdiv(d.n, 32);
     const int64_t ch0 = (u - pre[g]) * FU;
-    finish_pull_step<CLOSED, GView, false, FU, REL>(p, d.acc, d.anyb, ch0, nchunks, t);
+    finish_pull_step<CLOSED, GView, false, FU, REL, false, COH>(p, d.acc, d.anyb, ch0, nchunks, t);
   }
-  if (tg >= 0) flush_totals(t, st + tg);
+  if (tg >= 0) flush_totals(t, sv.st + tg, sv.dR(tg));
 }
 
-// close the iteration of every live graph; loop while any is live
+template <bool CLOSED, int FU, bool REL>
+__global__ void __launch_bounds__(GR_THREADS, 2) k_g_finish(const GRun* __restrict__ run,
+                                                            const GDesc* __restrict__ desc, GState* __restrict__ st) {
+  extern __shared__ int64_t pre[];   // G + 1 prefix entries
+  load_prefix(pre, run->fpre, run->G);
+  g_finish_phase<CLOSED, FU, REL, false>(run, desc, StatesInMemory{st}, pre);
+}
+
+// close the iteration of every live graph; loop while any is live (one block)
 __global__ void k_g_control(GRun* run, GState* st, cudaGraphConditionalHandle cond) {
   __shared__ int live;
   if (threadIdx.x == 0) live = 0;
@@ -317,6 +379,153 @@ __global__ void k_g_control(GRun* run, GState* st, cudaGraphConditionalHandle co
     const unsigned go = (live && run->loops < run->max_iter) ? 1u : 0u;
     run->live = (int32_t)go;
     if (run->use_graph) cudaGraphSetConditional(cond, go);
+  }
+}
+
+
+// ------------------------------------------------------------------ the whole loop in one kernel
+//
+// For groups whose sweeps take a few microseconds, the launches of the CUDA
+// graph (three kernels per iteration) cost more than the work.  k_g_loop runs
+// init, mark and every iteration's gather, epilogue and control in one
+// cooperative launch (every block resident), the phases separated by grid
+// barriers.  Same phase code, same arithmetic: the ranks and statistics are
+// bit-identical to the CUDA graph's.  Data written in an earlier phase is read
+// from L2 (COH), never through the read-only path.
+
+// iterations of a barrier wait before it gives up (after the first 4096 each
+// with a short sleep: about a second in all, against microseconds when every
+// block runs)
+constexpr long long BAR_SPINS = 1ll << 24;
+// resident blocks per SM of the one-kernel loop, at most: fewer blocks make
+// the barriers cheaper (one arrival each), more make the phases of larger
+// graphs faster.  One per SM: R-MAT graphs of 2^8 to 2^14 vertices update
+// 4-8% faster than with two, and the loop is the default only below
+// PR_ONE_KERNEL_SLOTS, where it beats the CUDA graph (equal at about 2^20)
+constexpr int LOOP_BPS = 1;
+
+__device__ __forceinline__ uint32_t ld_acquire_u32(const uint32_t* p) {
+  uint32_t v;
+  asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+
+// barrier number `k` (1, 2, ...) over the grid's blocks.  False when a wait
+// ran out, here or in another block (run->err set): the caller returns.
+__device__ __forceinline__ bool grid_barrier(GRun* run, uint32_t k) {
+  __shared__ int ok;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    int good = 1;
+    __threadfence();   // this block's writes before the arrival
+    const uint32_t arrived = atomicAdd(&run->bar_count, 1u) + 1u;
+    if (arrived == k * gridDim.x) {
+      __threadfence();
+      atomicExch(&run->bar_done, k);
+    } else {
+      long long spins = 0;
+      while (ld_acquire_u32(&run->bar_done) < k) {
+        if (*(volatile int32_t*)&run->err) {
+          good = 0;
+          break;
+        }
+        if (++spins > BAR_SPINS) {
+          atomicExch(&run->err, 1);
+          good = 0;
+          break;
+        }
+        if (spins > 4096) __nanosleep(64);   // poll at full rate for the first few microseconds
+      }
+    }
+    __threadfence();
+    ok = good;
+  }
+  __syncthreads();
+  return ok != 0;
+}
+
+// Every block closes iteration `it` of every live graph from the changes in
+// the word of its parity, with the same arithmetic as k_g_control, so all
+// blocks hold the same states; block 0 also writes them to device memory for
+// the host.  Returns whether any graph is still live.
+__device__ __forceinline__ bool loop_control(GRun* run, GState* st, uint32_t* sm, int it) {
+  __shared__ int live;
+  if (threadIdx.x == 0) live = 0;
+  __syncthreads();
+  const double tau = run->tau;
+  for (int g = threadIdx.x; g < run->G; g += blockDim.x) {
+    uint32_t w = sm[g];
+    if (w & 1u) continue;
+    const unsigned long long dRb = __ldcg((it & 1) ? &st[g].dR_odd : &st[g].dR);
+    const uint32_t iter = (w >> 3) + 1;
+    uint32_t cur = ((w >> 1) & 1u) ^ 1u, done = 0, conv = 0;
+    const double dR = __longlong_as_double((long long)dRb);
+    if (dR <= tau) {
+      conv = 1;
+      done = 1;
+    } else if ((int32_t)iter >= run->max_iter) {
+      done = 1;
+    } else {
+      live = 1;
+    }
+    sm[g] = (iter << 3) | (conv << 2) | (cur << 1) | done;
+    if (blockIdx.x == 0) {
+      GState& s = st[g];
+      s.iter = (int32_t)iter;
+      s.cur = (int32_t)cur;
+      s.done = (int32_t)done;
+      s.converged = (int32_t)conv;
+      s.dR_last = dRb;
+    }
+  }
+  __syncthreads();
+  return live != 0;
+}
+
+// shared memory: the four prefixes (gather units, epilogue units, bitset
+// words, changed edges; G + 1 entries each), then the G packed states
+template <bool CLOSED, bool REL>
+__global__ void __launch_bounds__(GR_THREADS, 2) k_g_loop(GRun* run, const GDesc* __restrict__ desc, GState* st) {
+  extern __shared__ int64_t pre[];
+  const int G = run->G;
+  uint32_t* sm = reinterpret_cast<uint32_t*>(pre + 4 * (G + 1));
+  for (int i = threadIdx.x; i <= G; i += blockDim.x) {
+    pre[i] = run->wpre[i];
+    pre[(G + 1) + i] = run->fpre[i];
+    pre[2 * (G + 1) + i] = run->bpre[i];
+    pre[3 * (G + 1) + i] = run->dpre[i];
+    if (i < G) sm[i] = 0u;
+  }
+  __syncthreads();
+  uint32_t k = 0;
+  g_init_phase(run, desc, st, 0, pre + 2 * (G + 1));   // zeroes every state, both change words included
+  if (!grid_barrier(run, ++k)) return;
+  if (run->method == PR_DF || run->method == PR_DFP) {
+    g_mark_phase(run, desc, pre + 3 * (G + 1));
+    if (!grid_barrier(run, ++k)) return;
+  }
+  int32_t loops = 0;
+  bool live = run->max_iter > 0;
+  for (int32_t it = 0; live; it++) {
+    const StatesInBlock sv{st, sm, it & 1};
+    g_gather_phase<LOOP_QPT, 1, true>(run, desc, sv, pre);
+    if (!grid_barrier(run, ++k)) return;
+    // the word of the next iteration's changes was last read by every block's
+    // control step of the iteration before this one, which the barrier above
+    // follows: clear it for the next epilogue
+    if (blockIdx.x == 0)
+      for (int g = threadIdx.x; g < G; g += blockDim.x) *((it & 1) ? &st[g].dR : &st[g].dR_odd) = 0ull;
+    g_finish_phase<CLOSED, LOOP_FU, REL, true>(run, desc, sv, pre + (G + 1));
+    if (!grid_barrier(run, ++k)) return;
+    live = loop_control(run, st, sm, it);
+    loops += 1;
+    // every graph is done after max_iter iterations; the guard bounds the
+    // loop even if a state were corrupted
+    if (loops >= run->max_iter) live = false;
+  }
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    run->loops = loops;
+    run->live = 0;
   }
 }
 
@@ -351,6 +560,8 @@ struct pr_group {
   int exec_q[2] = {-1, -1}, exec_f[2] = {-1, -1}, exec_rel[2] = {-1, -1};
   cudaGraphConditionalHandle cond[2] = {0, 0};
   cudaEvent_t ev[3] = {nullptr, nullptr, nullptr};
+  // resident blocks per SM of the one-kernel loop [form][relative measure], 0 until asked
+  int loop_bps[2][2] = {{0, 0}, {0, 0}};
   // the update in flight: its members (group indices) and method
   std::vector<int32_t> members;
   bool in_flight = false;
@@ -523,6 +734,41 @@ void pr_group_destroy(pr_group* q) { group_free(q); }
 
 }  // extern "C"
 
+static const void* loop_fn(int k, bool rel) {
+  if (rel) return k ? (const void*)k_g_loop<true, true> : (const void*)k_g_loop<false, true>;
+  return k ? (const void*)k_g_loop<true, false> : (const void*)k_g_loop<false, false>;
+}
+
+// the whole update as one cooperative launch of every resident block.  Two
+// such grids launched from different streams at once could each hold part of
+// the SMs while waiting at a barrier for blocks that the other keeps out, so
+// every launch of the process is ordered after the previous one on the
+// device (an event per device; the host does not wait)
+static cudaError_t launch_one_kernel(pr_group* q, int k, bool rel) {
+  static std::mutex mu;
+  static std::map<int, cudaEvent_t> last;
+  const void* fn = loop_fn(k, rel);
+  const size_t smem = 4 * prefix_bytes(q) + sizeof(uint32_t) * (size_t)q->G;
+  int& bps = q->loop_bps[k][rel ? 1 : 0];
+  if (bps == 0) {
+    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, fn, GR_THREADS, smem);
+    if (e != cudaSuccess) return e;
+    if (bps < 1) return cudaErrorInvalidConfiguration;
+    bps = std::min(bps, LOOP_BPS);
+  }
+  void* args[] = {&q->d_run, &q->d_desc, &q->d_state};
+  std::lock_guard<std::mutex> lock(mu);
+  cudaEvent_t& ev = last[q->dev];
+  cudaError_t e = cudaSuccess;
+  if (!ev) e = cudaEventCreateWithFlags(&ev, cudaEventDisableTiming);
+  else e = cudaStreamWaitEvent(q->stream, ev, 0);
+  if (e != cudaSuccess) return e;
+  note_launch();
+  e = cudaLaunchCooperativeKernel(fn, dim3(num_sms() * bps), dim3(GR_THREADS), args, smem, q->stream);
+  if (e != cudaSuccess) return e;
+  return cudaEventRecord(ev, q->stream);
+}
+
 // the same kernels launched one by one, the loop condition read back after
 // every iteration (PR_OPT_HOST_LOOP): for profilers that cannot see into a
 // CUDA graph with conditional nodes, and for drivers without them
@@ -568,9 +814,11 @@ pr_status group_launch(pr_group* q, pr_method method, double alpha, double tau, 
   pr_options o = {1e-6, 1e-6, 500, 0};
   if (opts) o = *opts;
   if (!(o.tau_f >= 0.0) || !(o.tau_p >= 0.0) || o.max_iter < 0) return PR_EINVAL;
-  if (o.flags & ~(PR_OPT_HOST_LOOP | PR_OPT_DEVICE_LOOP | PR_OPT_MEASURE_ABSOLUTE | PR_OPT_MEASURE_CONTRIB))
+  if (o.flags &
+      ~(PR_OPT_HOST_LOOP | PR_OPT_DEVICE_LOOP | PR_OPT_ONE_KERNEL | PR_OPT_MEASURE_ABSOLUTE | PR_OPT_MEASURE_CONTRIB))
     return PR_EINVAL;
-  if ((o.flags & PR_OPT_HOST_LOOP) && (o.flags & PR_OPT_DEVICE_LOOP)) return PR_EINVAL;
+  const int loops_asked = !!(o.flags & PR_OPT_HOST_LOOP) + !!(o.flags & PR_OPT_DEVICE_LOOP) + !!(o.flags & PR_OPT_ONE_KERNEL);
+  if (loops_asked > 1) return PR_EINVAL;
   if ((o.flags & PR_OPT_MEASURE_ABSOLUTE) && (o.flags & PR_OPT_MEASURE_CONTRIB)) return PR_EINVAL;
   std::vector<int32_t>& mem = q->members;
   mem.clear();
@@ -590,6 +838,12 @@ pr_status group_launch(pr_group* q, pr_method method, double alpha, double tau, 
     for (int i = 0; i < G; i++)
       if (!q->graphs[mem[i]]->g.has_ranks) return PR_ENORANKS;
   cudaStream_t s = q->stream;
+  // the loop in one kernel when asked, or by default when the sweeps are short
+  int64_t slots = 0;
+  for (int i = 0; i < G; i++) slots += q->graphs[mem[i]]->g.in.cap;
+  const bool one = (o.flags & PR_OPT_ONE_KERNEL) || (loops_asked == 0 && slots < PR_ONE_KERNEL_SLOTS);
+  const int64_t gq = one ? 32 * LOOP_QPT : 32 * GR_QPT[q->qi] * GR_STEPS[q->qi];   // quads per gather unit
+  const int64_t fu = one ? LOOP_FU : GR_FU[q->fi];                                 // chunks per epilogue unit
   int64_t* wpre = q->h_pre;
   int64_t* fpre = wpre + (G + 1);
   int64_t* bpre = fpre + (G + 1);
@@ -623,8 +877,8 @@ pr_status group_launch(pr_group* q, pr_method method, double alpha, double tau, 
     d.id_bits = g->id_bits;
     d.C0 = (1.0 - alpha) / (double)g->n;
     d.tab_ab = g->tab_ab;
-    wpre[i + 1] = wpre[i] + cdiv(d.nquads, 32 * GR_QPT[q->qi] * GR_STEPS[q->qi]);
-    fpre[i + 1] = fpre[i] + cdiv(cdiv((int64_t)g->n, 32), GR_FU[q->fi]);
+    wpre[i + 1] = wpre[i] + cdiv(d.nquads, gq);
+    fpre[i + 1] = fpre[i] + cdiv(cdiv((int64_t)g->n, 32), fu);
     bpre[i + 1] = bpre[i] + cdiv((int64_t)g->n, 32);
     dpre[i + 1] = dpre[i] + ((method == PR_DF || method == PR_DFP) ? g->n_dmin + g->n_dplus : 0);
   }
@@ -643,7 +897,7 @@ pr_status group_launch(pr_group* q, pr_method method, double alpha, double tau, 
   r.bpre = q->d_pre + 2 * (G + 1);
   r.dpre = q->d_pre + 3 * (G + 1);
   r.tab_sc = q->tab_sc;
-  r.use_graph = (o.flags & PR_OPT_HOST_LOOP) ? 0 : 1;
+  r.use_graph = (o.flags & PR_OPT_HOST_LOOP) || one ? 0 : 1;
   r.metric = (o.flags & PR_OPT_MEASURE_ABSOLUTE) ? METRIC_ABSOLUTE
              : (o.flags & PR_OPT_MEASURE_CONTRIB) ? METRIC_CONTRIB
                                                   : METRIC_RELATIVE;
@@ -675,7 +929,12 @@ pr_status group_launch(pr_group* q, pr_method method, double alpha, double tau, 
       cudaMemcpyAsync(q->d_run, q->h_run, sizeof(GRun), cudaMemcpyHostToDevice, s) != cudaSuccess)
     return PR_ECUDA;
   const int k = method == PR_DFP ? 1 : 0;
-  if (r.use_graph) {
+  if (one) {
+    if (launch_one_kernel(q, k, r.metric == METRIC_RELATIVE) != cudaSuccess) {
+      cudaGetLastError();
+      return PR_ECUDA;
+    }
+  } else if (r.use_graph) {
     const int rel = r.metric == METRIC_RELATIVE ? 1 : 0;
     if (q->exec[k] && (q->exec_q[k] != q->qi || q->exec_f[k] != q->fi || q->exec_rel[k] != rel)) drop_exec(q, k);
     if (!q->exec[k] && build_exec(q, k, rel != 0) != cudaSuccess) {
@@ -705,6 +964,11 @@ pr_status group_complete(pr_group* q, pr_stats* stats) {
   q->in_flight = false;
   if (cudaEventSynchronize(q->ev[1]) != cudaSuccess) return PR_ECUDA;
   const pr_method method = q->cur_method;
+  if (q->h_run->err) {
+    // a grid barrier of the one-kernel loop gave up: the ranks are partial
+    for (int32_t gi : q->members) q->graphs[gi]->g.has_ranks = false;
+    return PR_ETIMEOUT;
+  }
   float ms = 0.f;
   cudaEventElapsedTime(&ms, q->ev[0], q->ev[1]);
   // kernels the CUDA graph ran: init, mark, and three per loop pass (the host

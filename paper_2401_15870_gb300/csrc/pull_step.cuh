@@ -50,6 +50,29 @@ __device__ __forceinline__ long long ld_hint(const long long* p, uint64_t pol) {
   asm volatile("ld.global.nc.L2::cache_hint.b64 %0, [%1], %2;" : "=l"(v) : "l"(p), "l"(pol));
   return v;
 }
+// ordinary (weak) loads, for data written earlier in the same launch: the
+// read-only path may hold stale lines then, while an ordinary load after the
+// grid barrier's acquire sees every write made before the barrier
+__device__ __forceinline__ long long ld_weak_hint(const long long* p, uint64_t pol) {
+  long long v;
+  asm volatile("ld.global.L2::cache_hint.b64 %0, [%1], %2;" : "=l"(v) : "l"(p), "l"(pol) : "memory");
+  return v;
+}
+__device__ __forceinline__ uint32_t ld_weak(const uint32_t* p) {
+  uint32_t v;
+  asm volatile("ld.global.b32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+__device__ __forceinline__ long long ld_weak(const long long* p) {
+  long long v;
+  asm volatile("ld.global.b64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+  return v;
+}
+__device__ __forceinline__ double ld_weak(const double* p) {
+  double v;
+  asm volatile("ld.global.f64 %0, [%1];" : "=d"(v) : "l"(p) : "memory");
+  return v;
+}
 
 __device__ __forceinline__ unsigned long long dbits(double x) { return (unsigned long long)__double_as_longlong(x); }
 
@@ -75,8 +98,11 @@ struct GatherSpan {
 // quads [base, base + 32 * QPT) of one in-CSR, those below qlo or from nquads
 // on left out; S / X / anyb only in pull form.
 // SPAN: also report what the step touched (the one-launch sweep needs it; the
-// other callers skip the extra warp operations)
-template <bool PULL, int QPT = SW_QPT, bool HUB = false, bool SPAN = false>
+// other callers skip the extra warp operations).
+// COH: the contributions and the S / X words were written earlier in the same
+// launch (a kernel that runs the whole iteration loop): they are read with
+// ordinary loads, not through the read-only path
+template <bool PULL, int QPT = SW_QPT, bool HUB = false, bool SPAN = false, bool COH = false>
 __device__ __forceinline__ GatherSpan gather_step(const int32_t* __restrict__ icol, const long long* __restrict__ C,
                                                   const uint32_t* __restrict__ X, const uint32_t* __restrict__ S,
                                                   const uint32_t* __restrict__ rowbits,
@@ -90,11 +116,12 @@ __device__ __forceinline__ GatherSpan gather_step(const int32_t* __restrict__ ic
   // that covers the sentinel id holds C[sent] = 0
   auto contrib = [&](int32_t c) -> long long {
     if (HUB && c < hub.k) return hub.c[c];
-    return c != sent ? ld_hint(C + c, pol_keep) : 0ll;
+    if (c == sent) return 0ll;
+    return COH ? ld_weak_hint(C + c, pol_keep) : ld_hint(C + c, pol_keep);
   };
   auto expanded = [&](int32_t c) -> unsigned {
     if (c == sent) return 0u;
-    const uint32_t w = HUB && (c >> 5) < hub.kx ? hub.x[c >> 5] : __ldg(X + (c >> 5));
+    const uint32_t w = HUB && (c >> 5) < hub.kx ? hub.x[c >> 5] : (COH ? ld_weak(X + (c >> 5)) : __ldg(X + (c >> 5)));
     return w >> (c & 31);
   };
   int4 c[QPT];
@@ -146,7 +173,8 @@ __device__ __forceinline__ GatherSpan gather_step(const int32_t* __restrict__ ic
     x[j] = 0;
     // a row whose vertex stays in the frontier is processed anyway: its
     // sources' expanded bits are not needed
-    if (PULL && owner[j] >= 0 && !((__ldg(S + (owner[j] >> 5)) >> (owner[j] & 31)) & 1u))
+    if (PULL && owner[j] >= 0 &&
+        !(((COH ? ld_weak(S + (owner[j] >> 5)) : __ldg(S + (owner[j] >> 5))) >> (owner[j] & 31)) & 1u))
       x[j] = (expanded(c[j].x) | expanded(c[j].y) | expanded(c[j].z) | expanded(c[j].w)) & 1u;
   }
   GatherSpan span{0, 0, false};
@@ -197,11 +225,14 @@ struct PullTotals {
 // metric (unless REL).
 // The accumulators and the expanded-source words it reads are left zero for
 // the next sweep.  L2: read them from L2 (they were written by other SMs in
-// the same launch).
+// the same launch).  COH: also the frontier words, ranks, own contributions
+// and ever-affected words, which earlier phases of the same launch wrote
+// (a kernel that runs the whole iteration loop).
 // REL: the relative measure of Alg. 1 fixed at compile time (the default);
 // otherwise p.metric chooses.  SAME: tau_p == tau_f known at compile time (the
 // default tolerances), which saves the FP64 product of the prune threshold
-template <bool CLOSED, class P, bool L2 = false, int U = FIN_U, bool REL = false, bool SAME = false>
+template <bool CLOSED, class P, bool L2 = false, int U = FIN_U, bool REL = false, bool SAME = false,
+          bool COH = false>
 __device__ __forceinline__ void finish_pull_step(const P& p, long long* __restrict__ acc, uint32_t* __restrict__ anyb,
                                                  int64_t ch0, int64_t nchunks, PullTotals& t) {
   const int lane = threadIdx.x & 31;
@@ -223,13 +254,14 @@ __device__ __forceinline__ void finish_pull_step(const P& p, long long* __restri
     const int64_t ch = ch0 + u;
     const int64_t v = ch * 32 + lane;
     valid[u] = ch < nchunks && v < p.n;
-    const uint32_t ab = ch < nchunks ? (L2 ? __ldcg(anyb + ch) : anyb[ch]) : 0u;
-    const uint32_t in_f = ch < nchunks ? (ab | __ldg(p.S_cur + ch)) : 0u;
+    const uint32_t ab = ch < nchunks ? (L2 || COH ? __ldcg(anyb + ch) : anyb[ch]) : 0u;
+    const uint32_t sw = ch < nchunks ? (COH ? ld_weak(p.S_cur + ch) : __ldg(p.S_cur + ch)) : 0u;
+    const uint32_t in_f = ab | sw;
     member[u] = valid[u] && ((in_f >> lane) & 1u);
-    sum[u] = valid[u] ? (L2 ? __ldcg(acc + v) : acc[v]) : 0;
+    sum[u] = valid[u] ? (L2 || COH ? __ldcg(acc + v) : acc[v]) : 0;
     // the own contribution: Eq. 2's self term, or the entry a non-member copies
-    cself[u] = (CLOSED || !inplace) && valid[u] ? p.Ccur[v] : 0;
-    Rv[u] = valid[u] ? p.R[v] : 0.0;
+    cself[u] = (CLOSED || !inplace) && valid[u] ? (COH ? ld_weak(p.Ccur + v) : p.Ccur[v]) : 0;
+    Rv[u] = valid[u] ? (COH ? ld_weak(p.R + v) : p.R[v]) : 0.0;
     d[u] = valid[u] ? p.odeg[v] : 1;
     din[u] = valid[u] ? p.ideg[v] : 0;
   }
@@ -276,7 +308,7 @@ __device__ __forceinline__ void finish_pull_step(const P& p, long long* __restri
       p.S_next[ch] = ms;
       p.X_next[ch] = mx;
       if (mm) {
-        const uint32_t old = p.ever[ch];
+        const uint32_t old = COH ? ld_weak(p.ever + ch) : p.ever[ch];
         if (mm & ~old) {
           p.ever[ch] = old | mm;
           t.ever_new += __popc(mm & ~old);

@@ -110,3 +110,20 @@ def test_binding_structs_match_the_header(tmp_path):
         assert int(got[name]) == ctypes.sizeof(cls), name
         for field, _ in cls._fields_:
             assert int(got[name + "." + field]) == getattr(cls, field).offset, (name, field)
+
+
+def test_binding_constants_match_the_header():
+    """Every PR_OPT_* flag and size limit the Python binding passes through has
+    the header's value."""
+    import paper_2401_15870_gb300 as pr
+    text = open(os.path.join(ROOT, "include", "dfpr.h")).read()
+    defs = {}
+    for name, val in re.findall(r"#define\s+(PR_[A-Z_0-9]+)\s+\(?([0-9]+(?:ll)?(?:\s*<<\s*[0-9]+)?)\)?", text):
+        defs[name] = eval(val.replace("ll", ""))
+    checked = 0
+    for name in dir(pr):
+        if name.startswith(("PR_OPT_", "PR_ONE_", "PR_DEVICE_")) and name in defs:
+            assert getattr(pr, name) == defs[name], name
+            checked += 1
+    assert checked >= 8
+    assert pr.LOOPS["one"] == defs["PR_OPT_ONE_KERNEL"] and pr.LOOPS["device"] == defs["PR_OPT_DEVICE_LOOP"]

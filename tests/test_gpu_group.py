@@ -85,18 +85,20 @@ def test_group_matches_oracle_and_solo_runs(lib, cases, method):
 @pytest.mark.parametrize("method", ["dfp", "static"])
 def test_group_host_loop_equals_device_loop(lib, cases, method):
     """The kernels launched one by one with the condition read back on the host
-    give the same bits as the CUDA graph with its WHILE node."""
+    and the whole loop in one cooperative kernel give the same bits as the
+    CUDA graph with its WHILE node."""
     graphs = [c[0] for c in cases]
     grp = lib.Group(graphs)
     try:
         out = []
-        for loop in ("device", "host"):
+        for loop in ("device", "one", "host"):
             for G, O, r0 in cases:
                 G.set_ranks(r0)
             st = grp.update(method, loop=loop)
             out.append(([G.ranks() for G in graphs], [(s.iterations, s.vertices_ever_affected) for s in st]))
-        assert all(np.array_equal(a, b) for a, b in zip(out[0][0], out[1][0]))
-        assert out[0][1] == out[1][1]
+        for o in out[1:]:
+            assert all(np.array_equal(a, b) for a, b in zip(out[0][0], o[0]))
+            assert out[0][1] == o[1]
     finally:
         grp.close()
 

@@ -276,17 +276,19 @@ def test_frontier_directions_agree_with_oracle(lib, method, direction, scale, bs
 @pytest.mark.parametrize("method", ["static", "nd", "df", "dfp"])
 @pytest.mark.parametrize("scale,bsize", [(12, 40), (14, 262), (13, 3000)])
 def test_device_and_host_loops_agree_bitwise(lib, method, scale, bsize):
-    """The iteration loop on the device (CUDA graph, pull form) and on the host
-    give bit-identical ranks and statistics."""
+    """The iteration loop on the device (CUDA graph, pull form), in one
+    cooperative kernel and on the host give bit-identical ranks and
+    statistics."""
     G, O, r0 = rank_case(lib, scale, 16, bsize, 70 + scale)
     out = []
-    for loop in ("device", "host"):
+    for loop in ("device", "one", "host"):
         G.set_ranks(r0)
         st = G.update(method, loop=loop)
         out.append((G.ranks(), st.iterations, st.converged, st.vertices_ever_affected, st.vertices_processed,
                     st.edges_processed))
-    assert np.array_equal(out[0][0], out[1][0])
-    assert out[0][1:] == out[1][1:]
+    for o in out[1:]:
+        assert np.array_equal(out[0][0], o[0])
+        assert out[0][1:] == o[1:]
     ref, ost = O.update(method, r_prev=r0)
     assert np.max(np.abs(out[0][0] - ref)) < TOL
     assert (out[0][1], out[0][3], out[0][4]) == (ost.iterations, ost.vertices_ever_affected,
@@ -473,7 +475,7 @@ def test_autotune_on_updates_keeps_the_ranks(lib, method, scale):
     assert tu.candidates >= 18
     assert np.array_equal(G.ranks(), r0)
     ref, _ = O.update(method, r_prev=r0)
-    for loop in ("device", "host"):
+    for loop in ("device", "one", "host"):
         G.set_ranks(r0)
         G.update(method, loop=loop)
         assert np.max(np.abs(G.ranks() - ref)) < TOL
@@ -560,7 +562,7 @@ def test_frontier_without_expansion_matches_oracle(lib, method, direction):
 # ------------------------------------------------------------- prune against re-mark (reading C2)
 
 
-@pytest.mark.parametrize("direction,loop", [("pull", "host"), ("push", "host"), (None, "device")])
+@pytest.mark.parametrize("direction,loop", [("pull", "host"), ("push", "host"), (None, "device"), (None, "one")])
 def test_pruned_vertex_re_marked_matches_oracle(lib, direction, loop):
     """The hand-made case of tests/golden/prune_vs_mark_6v.txt: vertex 2 is
     pruned in iteration 0 while its in-neighbour 1 expands into it, so it is
