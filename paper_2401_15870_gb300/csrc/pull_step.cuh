@@ -185,23 +185,34 @@ __device__ __forceinline__ GatherSpan gather_step(const int32_t* __restrict__ ic
     for (int j = 1; j < QPT; j++) hi = max(hi, owner[j]);
     span.last = __reduce_max_sync(0xffffffffu, hi);
   }
+  // Segmented reduction of each 32-quad word: a row piece's sum ends up in its
+  // first lane.  Warp shuffles move data through the same L1TEX data pipe as
+  // the gathers, so only the sums are shuffled: whether two lanes hold the same
+  // row follows from the word's row-start bits (and the edges of the valid
+  // quads), and whether any source of a row piece expanded from one ballot.
 #pragma unroll
   for (int j = 0; j < QPT; j++) {
     const int own = owner[j];
     long long sum = s[j];
-    unsigned any = x[j];
+    // segment starts: lane 0, the row starts, and where the valid quads
+    // ([qlo, nquads), owner >= 0) begin and end
+    const unsigned vm = __ballot_sync(0xffffffffu, own >= 0);
+    const unsigned long long st = (unsigned long long)(wb[j] | 1u | (vm ^ (vm << 1)));
 #pragma unroll
     for (int o = 1; o < 32; o <<= 1) {
-      long long os = __shfl_down_sync(0xffffffffu, sum, o);
-      unsigned ox = __shfl_down_sync(0xffffffffu, any, o);
-      int oo = __shfl_down_sync(0xffffffffu, own, o);
-      if (lane + o < 32 && oo == own) {
-        sum += os;
-        any |= ox;
-      }
+      const long long os = __shfl_down_sync(0xffffffffu, sum, o);
+      // lane + o holds the same row piece when no segment starts in (lane, lane + o]
+      if (lane + o < 32 && ((st >> (lane + 1)) & ((1ull << o) - 1ull)) == 0) sum += os;
     }
-    const int prev = __shfl_up_sync(0xffffffffu, own, 1);
-    if (own >= 0 && (lane == 0 || prev != own)) {
+    unsigned any = 0u;
+    if (PULL) {
+      const unsigned xm = __ballot_sync(0xffffffffu, x[j] != 0u);
+      const unsigned long long later = (st >> (lane + 1)) << (lane + 1);   // starts after this lane
+      const int end = later ? __ffsll((long long)later) - 1 : 32;         // this lane's segment ends before it
+      const unsigned seg = (unsigned)(((1ull << end) - 1ull) & ~((1ull << lane) - 1ull));
+      any = (xm & seg) != 0u;
+    }
+    if (own >= 0 && ((st >> lane) & 1ull)) {
       if (sum) atomicAdd(reinterpret_cast<unsigned long long*>(acc + own), (unsigned long long)sum);
       if (PULL && any) atomicOr(anyb + (own >> 5), 1u << (own & 31));
       if (SPAN) span.wrote = span.wrote || sum != 0 || (PULL && any);
