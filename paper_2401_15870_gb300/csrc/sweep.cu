@@ -355,8 +355,9 @@ __global__ void __launch_bounds__(SW_THREADS) k_sweep(SweepParams p) {
 //   [0, hub_k) (and, in pull form, the expanded bits of their words) in
 //   shared memory; the grid is then one wave of resident blocks, so the
 //   staging is paid once per block and sweep.
+// (2 quads per lane: held to 32 registers, two 1024-thread blocks per SM)
 template <bool PULL, int QPT, bool HUB>
-__global__ void __launch_bounds__(1024) k_gather_rows(const int32_t* __restrict__ icol, const long long* __restrict__ C,
+__global__ void __launch_bounds__(1024, QPT == 2 ? 2 : 1) k_gather_rows(const int32_t* __restrict__ icol, const long long* __restrict__ C,
                                                       const uint32_t* __restrict__ X, const uint32_t* __restrict__ S,
                                                       const uint32_t* __restrict__ rowbits,
                                                       const int32_t* __restrict__ rowbase, int64_t nquads, int32_t sent,
