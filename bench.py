@@ -683,7 +683,7 @@ def run_serving(a, rank, world, local_rank):
         times, graphs and sizes depend on the rate only; the edges on k0, so each
         arm gets batches of its own (a batch applied twice changes nothing)."""
         r2 = np.random.default_rng(a.seed + int(rate))
-        count = min(a.max_requests, max(200, int(rate * 1.0)))
+        count = min(a.max_requests, max(400, int(rate * 1.0)))
         t = np.cumsum(r2.exponential(1.0 / rate, count))
         out = []
         for i in range(count):

@@ -131,14 +131,15 @@ void finish_requests(pr_server* S, std::vector<Request>& reqs, int32_t status, i
 }
 
 // the requests of one graph merged in arrival order: per edge the last
-// operation wins (deletions of a request before its insertions)
-void merge_requests(const std::vector<Request>& reqs, std::vector<int32_t>* ds, std::vector<int32_t>* dd,
+// operation wins (deletions of a request before its insertions).  The
+// requests' edge lists are not needed afterwards; a lone request's are moved.
+void merge_requests(std::vector<Request>& reqs, std::vector<int32_t>* ds, std::vector<int32_t>* dd,
                     std::vector<int32_t>* is, std::vector<int32_t>* id) {
   if (reqs.size() == 1) {
-    *ds = reqs[0].ds;
-    *dd = reqs[0].dd;
-    *is = reqs[0].is;
-    *id = reqs[0].id;
+    *ds = std::move(reqs[0].ds);
+    *dd = std::move(reqs[0].dd);
+    *is = std::move(reqs[0].is);
+    *id = std::move(reqs[0].id);
     return;
   }
   size_t total = 0;
@@ -261,8 +262,11 @@ void run_grouped(pr_server* S) {
           S->cv_work.wait(lk, [&] { return S->stop || has_work() || can_launch(); });
         }
       }
-      // the next round holds the READY graphs and those admitted now
-      int64_t free_b = S->pending.empty() ? 0 : free_device_bytes() - S->opt.hbm_reserve - S->ready_bytes;
+      // the next round holds the READY graphs and those admitted now; the
+      // free device memory is asked for (a driver call) only when a request
+      // after the round's first one is weighed
+      bool have_free = false;
+      int64_t free_b = 0;
       int64_t edges = S->ready_edges;
       bool any_ready = false;
       for (int i = 0; i < G; i++) any_ready = any_ready || S->state[i] == READY;
@@ -278,7 +282,11 @@ void run_grouped(pr_server* S) {
         const bool first = order.empty() && !any_ready;
         const bool new_graph = take[gi].empty();
         const int64_t need = (new_graph ? BYTES_PER_BATCH : 0) + BYTES_PER_BATCH_EDGE * e;
-        const bool fits_mem = need <= free_b;
+        if (!first && !have_free) {
+          free_b = free_device_bytes() - S->opt.hbm_reserve - S->ready_bytes;
+          have_free = true;
+        }
+        const bool fits_mem = first || need <= free_b;
         const bool fits_edges = S->opt.max_round_edges <= 0 || edges + e <= S->opt.max_round_edges;
         if (!first && (!fits_mem || !fits_edges)) {
           refused[gi] = 1;   // later requests of this graph wait too: arrival order
@@ -286,7 +294,7 @@ void run_grouped(pr_server* S) {
           continue;
         }
         if (new_graph) order.push_back(gi);
-        free_b -= need;
+        if (have_free) free_b -= need;
         edges += e;
         S->ready_bytes += need;
         S->ready_edges += e;
