@@ -261,7 +261,8 @@ pr_status pr_apply_batches(int32_t count, pr_graph* const* graphs, const int32_t
  * 1/|V|; the others from the current ranks (pr_set_ranks or a previous
  * update; PR_ENORANKS if none).  Not converging is not an error
  * (stats->converged = 0).  opts and stats may be NULL.  Errors: PR_EINVAL,
- * PR_ENORANKS, PR_ECUDA.
+ * PR_ENORANKS, PR_ECUDA, PR_ETIMEOUT (the one-kernel loop's grid barrier gave
+ * up, PR_OPT_ONE_KERNEL; the graph is left without ranks).
  */
 pr_status pr_update(pr_graph* g, pr_method method, double alpha, double tau, const pr_options* opts,
                     pr_stats* stats);
@@ -362,15 +363,19 @@ pr_status pr_sweep_noalloc(int32_t n, const int64_t* in_off, const int32_t* in_s
  *   legacy default stream).  Errors: PR_EINVAL, PR_ENOMEM, PR_ECUDA.
  * pr_group_update: method PR_STATIC, PR_NAIVE_DYNAMIC, PR_DF or PR_DFP (Dynamic
  *   Traversal is not offered), alpha / tau / opts as in pr_update; the flags
- *   accepted are PR_OPT_MEASURE_* and PR_OPT_HOST_LOOP (or
- *   PR_OPT_DEVICE_LOOP, the default): the same kernels launched one by one
- *   with the loop condition read back after every iteration, for profilers
- *   that cannot look into a CUDA graph with conditional nodes and for drivers
- *   without them.  The update runs after the work already queued on
- *   every graph's stream and is complete on return.  stats: NULL or count
- *   entries, one per graph in creation order; ms_update is the time of the
- *   whole group, ms_sweep is 0.  Errors: PR_EINVAL, PR_ENORANKS (a dynamic
- *   method on a graph without ranks; nothing is changed), PR_ECUDA.
+ *   accepted are PR_OPT_MEASURE_* and at most one of PR_OPT_HOST_LOOP (the
+ *   same kernels launched one by one with the loop condition read back after
+ *   every iteration, for profilers that cannot look into a CUDA graph with
+ *   conditional nodes and for drivers without them), PR_OPT_DEVICE_LOOP (the
+ *   CUDA graph) and PR_OPT_ONE_KERNEL (one cooperative kernel); with none of
+ *   the three the group runs in one kernel below PR_ONE_KERNEL_SLOTS in-CSR
+ *   slots over its graphs and as the CUDA graph above.  The update runs after
+ *   the work already queued on every graph's stream and is complete on
+ *   return.  stats: NULL or count entries, one per graph in creation order;
+ *   ms_update is the time of the whole group, ms_sweep is 0.  Errors:
+ *   PR_EINVAL, PR_ENORANKS (a dynamic method on a graph without ranks;
+ *   nothing is changed), PR_ECUDA, PR_ETIMEOUT (a grid barrier of the
+ *   one-kernel loop gave up; the graphs are left without ranks).
  */
 #define PR_GROUP_MAX 1024
 typedef struct pr_group pr_group;
