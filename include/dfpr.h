@@ -397,9 +397,11 @@ void pr_group_destroy(pr_group* grp);
  * (1, 2 or 4) whose loads a warp issues together.  Smaller units spread small
  * graphs over more warps; larger ones keep more loads in flight per warp or
  * look the graph up less often.  Defaults 4 / 1 / 4.  The setting changes no
- * result (the sums are exact).
+ * result (the sums are exact).  It applies to the CUDA-graph and host loops;
+ * the one-kernel loop (PR_OPT_ONE_KERNEL) uses units of one warp step of
+ * 32 x 2 quads and one chunk.
  * pr_group_autotune: runs reps (0: 1) group updates of the method per
- *   candidate (12 settings; the device loop, CUDA-event time of the whole update), every
+ *   candidate (12 settings; the CUDA-graph device loop, CUDA-event time of the whole update), every
  *   graph starting from its ranks on entry (with its last batch for DF / DF-P),
  *   keeps the fastest, and puts the ranks on entry back at the end (a graph
  *   without ranks keeps those of the last Static trial).  Dynamic methods need

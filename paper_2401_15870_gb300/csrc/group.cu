@@ -1095,7 +1095,10 @@ pr_status pr_group_autotune(pr_group* q, pr_method method, double alpha, double 
           st = PR_ECUDA;
           break;
         }
-        st = group_launch(q, method, alpha, tau, nullptr, nullptr, 0);
+        // timed on the CUDA-graph loop: the unit sizes are its (and the host
+        // loop's); the one-kernel loop of small groups has fixed ones
+        const pr_options graph_loop = {1e-6, 1e-6, 500, PR_OPT_DEVICE_LOOP};
+        st = group_launch(q, method, alpha, tau, &graph_loop, nullptr, 0);
         if (st == PR_OK) st = group_complete(q, stats.data());
         ms += stats[0].ms_update;
       }
