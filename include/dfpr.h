@@ -102,8 +102,10 @@ typedef struct {
 /* pr_options.flags for Static, ND, DF and DF-P: an asynchronous order of
  * Alg. 1 (Sec. 4.4 runs it with one rank vector updated in place).  The
  * library's vertex order is cut into 8 consecutive ranges at multiples of 128
- * (range k starts at floor(n k / 8 / 128) * 128; one range below 1024
- * vertices), every sweep visits the ranges one after another, and a vertex
+ * that hold about equal shares of the in-edges (range k starts at the first
+ * multiple of 128, v, where 8 times the in-edges of the vertices below v,
+ * self-loops included, reaches k times all in-edges, or at n; one range below
+ * 1024 vertices), every sweep visits the ranges one after another, and a vertex
  * reads the ranks of the ranges before its own as updated in this sweep and
  * the others as of the start of the sweep.  Frontier flags take effect in the
  * next iteration, as in the synchronous order.  The schedule is fixed, so the

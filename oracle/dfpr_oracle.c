@@ -498,12 +498,28 @@ enum { OR_METRIC_RELATIVE = 0, OR_METRIC_ABSOLUTE = 1, OR_METRIC_CONTRIB = 2 };
 enum { OR_ORDER_SYNC = 0, OR_ORDER_ASYNC = 1, OR_ORDER_RANGES = 2 };
 /* The ranges order is another schedule of Alg. 1's one rank vector: the
  * vertex ids are cut into OR_RANGES consecutive ranges at multiples of 128
- * (range k starts at floor(n k / OR_RANGES / 128) * 128; one range when n <
- * 128 OR_RANGES), the ranges are swept one after another, and a vertex reads
- * the ranks of the ranges before its own as updated in this sweep and all
- * others as of the start of the sweep.  Flags take effect in the next
- * iteration, as in the synchronous order. */
+ * that hold about equal shares of the in-edges (self-loops included): range k
+ * starts at the first multiple of 128, v, whose in-degree prefix (the in-edges
+ * of vertices below v) times OR_RANGES reaches k times all in-edges, or at n;
+ * one range when n < 128 OR_RANGES.  The ranges are swept one after another,
+ * and a vertex reads the ranks of the ranges before its own as updated in this
+ * sweep and all others as of the start of the sweep.  Flags take effect in
+ * the next iteration, as in the synchronous order. */
 enum { OR_RANGES = 8 };
+
+/* bound[0..P]: the ranges of the ranges order on the current in-rows */
+static void range_bounds(const or_graph *g, int P, int32_t *bound) {
+  const int32_t n = g->n;
+  const int64_t W = g->in_off[n];
+  const int64_t chunks = ((int64_t)n + 127) / 128;
+  bound[0] = 0;
+  for (int k = 1; k < P; k++) {
+    int64_t j = 0;
+    while (j < chunks && g->in_off[128 * j] * P < (int64_t)k * W) j++;
+    bound[k] = (int32_t)(128 * j < n ? 128 * j : n);
+  }
+  bound[P] = n;
+}
 
 static double frontier_measure(int metric, double dr, double r, double Rv, int64_t d) {
   if (metric == OR_METRIC_ABSOLUTE) return dr;
@@ -611,8 +627,7 @@ int or_update_ex(const or_graph *g, int method, double alpha, double tau, double
   /* range bounds: one range for the synchronous order */
   int P = order == OR_ORDER_RANGES && n >= 128 * OR_RANGES ? OR_RANGES : 1;
   int32_t bound[OR_RANGES + 1];
-  for (int k = 0; k < P; k++) bound[k] = (int32_t)((int64_t)n * k / P / 128 * 128);
-  bound[P] = n;
+  range_bounds(g, P, bound);
   or_stats s;
   memset(&s, 0, sizeof(s));
   s.tie_rel = INFINITY;

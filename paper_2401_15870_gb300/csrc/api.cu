@@ -383,8 +383,10 @@ struct SweepTimer {
   int last_mode = 0;
   long long edges0 = 0, verts0 = 0;   // the control block's totals at the previous record
   // asynchronous order: every-vertex sweeps over ASYNC_RANGES vertex ranges in
-  // order, the contributions updated in place after each range
+  // order (bounds: equal shares of the in-edges), the contributions updated in
+  // place after each range
   bool async = false;
+  int32_t bounds[ASYNC_RANGES + 1] = {};
   cudaError_t launch(int mode, const SweepParams& p, cudaStream_t s) {
     last_mode = mode;
     if (on) cudaEventRecord(h->ev[4], s);
@@ -403,7 +405,8 @@ struct SweepTimer {
         e = sweep_aux(h, cfg, &aux);
       }
       if (e == cudaSuccess)
-        e = launch_full_sweep(mode, q, cfg, g->rowbits, g->rowbase, g->anyb, g->done, aux, s, async);
+        e = launch_full_sweep(mode, q, cfg, g->rowbits, g->rowbase, g->anyb, g->done, aux, s, async,
+                              async ? bounds : nullptr);
     } else {
       e = launch_sweep(mode, p, s);
     }
@@ -446,6 +449,9 @@ pr_status dfpr::run_update(pr_graph* h, int method, double alpha, double tau, do
     TRY(launch_tables(g->tab_sc, g->tab_ab, alpha, n, s));
     g->tab_alpha = alpha;
   }
+  // the ranges of the asynchronous order from this graph's in-degrees (the
+  // rank-export buffer is free during an update and far larger than needed)
+  if (async) TRY(async_range_bounds(g->in.deg, n, ASYNC_RANGES, (int64_t*)h->vec_tmp, timer.bounds, s));
   SweepParams p = base_params(g, alpha, tau_f, tau_p);
   p.metric = (flags & PR_OPT_MEASURE_ABSOLUTE) ? METRIC_ABSOLUTE
              : (flags & PR_OPT_MEASURE_CONTRIB) ? METRIC_CONTRIB

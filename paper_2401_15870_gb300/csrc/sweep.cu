@@ -16,6 +16,7 @@
 // tiling, and integer adds run on GB300's integer pipes (FP64 adds are ~36x
 // slower there).
 #include <algorithm>
+#include <vector>
 #include <climits>
 #include <map>
 #include <mutex>
@@ -742,9 +743,56 @@ cudaError_t launch_gather(bool pull, const SweepParams& p, const GatherCfg& cfg,
               : gather_dispatch<false>(p, cfg, rowbits, rowbase, anyb, nquads, 0, p.n, s);
 }
 
+// in-degree sums of the 128-vertex chunks
+__global__ void k_chunk_degrees(const int32_t* __restrict__ ideg, int32_t n, int64_t chunks, int64_t* __restrict__ out) {
+  for (int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; c < chunks; c += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t v0 = c * 128, v1 = v0 + 128 < (int64_t)n ? v0 + 128 : (int64_t)n;
+    int64_t sum = 0;
+    for (int64_t v = v0; v < v1; v++) sum += ideg[v];
+    out[c] = sum;
+  }
+}
+
+// pre[0..chunks]: in-degree prefix before each chunk (pre[chunks] = all);
+// first[k - 1] = the first chunk j in [0, chunks] with P pre[j] >= k pre[chunks]
+__global__ void k_range_chunks(const int64_t* __restrict__ pre, int64_t chunks, int P, int64_t* __restrict__ first) {
+  const int64_t W = pre[chunks];
+  for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j <= chunks; j += (int64_t)gridDim.x * blockDim.x)
+    for (int k = 1; k < P; k++)
+      if (pre[j] * P >= (int64_t)k * W && (j == 0 || pre[j - 1] * P < (int64_t)k * W)) first[k - 1] = j;
+}
+
+int64_t async_range_scratch(int32_t n, int P) {
+  const int64_t chunks = cdiv((int64_t)n, 128);
+  return chunks + 1 + scan_tmp_elems(chunks) + P;
+}
+
+cudaError_t async_range_bounds(const int32_t* ideg, int32_t n, int P, int64_t* scratch, int32_t* bounds,
+                               cudaStream_t s) {
+  bounds[0] = 0;
+  bounds[P > 1 && n >= 128 * P ? P : 1] = n;
+  if (P <= 1 || n < 128 * P) return cudaSuccess;
+  const int64_t chunks = cdiv((int64_t)n, 128);
+  int64_t* pre = scratch;
+  int64_t* tmp = pre + chunks + 1;
+  int64_t* first = tmp + scan_tmp_elems(chunks);
+  note_launch();
+  k_chunk_degrees<<<grid_for(chunks, 256), 256, 0, s>>>(ideg, n, chunks, pre);
+  cudaError_t e = scan_excl<int64_t>(pre, pre, chunks, tmp, s);
+  if (e != cudaSuccess) return e;
+  note_launch();
+  k_range_chunks<<<grid_for(chunks + 1, 256), 256, 0, s>>>(pre, chunks, P, first);
+  std::vector<int64_t> h(P - 1);
+  if ((e = cudaMemcpyAsync(h.data(), first, sizeof(int64_t) * (P - 1), cudaMemcpyDeviceToHost, s)) != cudaSuccess ||
+      (e = cudaStreamSynchronize(s)) != cudaSuccess)
+    return e;
+  for (int k = 1; k < P; k++) bounds[k] = (int32_t)std::min<int64_t>(128 * h[k - 1], n);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_full_sweep(int mode, const SweepParams& p, const GatherCfg& cfg, const uint32_t* rowbits,
                               const int32_t* rowbase, uint32_t* anyb, int32_t* done, const SweepAux* aux,
-                              cudaStream_t s, bool ordered) {
+                              cudaStream_t s, bool ordered, const int32_t* bounds) {
   const int64_t nquads = p.ntiles_host;   // quads of the in-CSR capacity
   const bool pull = mode == SWEEP_PULL_DF || mode == SWEEP_PULL_DFP;
   if (pull) {
@@ -771,8 +819,12 @@ cudaError_t launch_full_sweep(int mode, const SweepParams& p, const GatherCfg& c
   if (ordered) aux = nullptr;
   cudaStream_t fs = P > 1 && !ordered ? aux->stream : s;
   for (int k = 0; k < P; k++) {
-    const int32_t v_lo = (int32_t)((int64_t)p.n * k / P / 128 * 128);
-    const int32_t v_hi = k + 1 == P ? p.n : (int32_t)((int64_t)p.n * (k + 1) / P / 128 * 128);
+    // the asynchronous order's ranges hold equal shares of the in-edges;
+    // ranges overlapping gather and epilogue are cut by vertex count
+    const int32_t v_lo = ordered && bounds ? bounds[k] : (int32_t)((int64_t)p.n * k / P / 128 * 128);
+    const int32_t v_hi = ordered && bounds ? bounds[k + 1]
+                                           : (k + 1 == P ? p.n : (int32_t)((int64_t)p.n * (k + 1) / P / 128 * 128));
+    if (ordered && v_hi <= v_lo) continue;   // an empty range (a hub range holding several shares)
     cudaError_t e = pull ? gather_dispatch<true>(p, cfg, rowbits, rowbase, anyb, nquads, v_lo, v_hi, s)
                          : gather_dispatch<false>(p, cfg, rowbits, rowbase, anyb, nquads, v_lo, v_hi, s);
     if (e != cudaSuccess) return e;

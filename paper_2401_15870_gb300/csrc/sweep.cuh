@@ -134,9 +134,20 @@ cudaError_t launch_gather(bool pull, const SweepParams& p, const GatherCfg& cfg,
 // after another on s, each gather followed by its epilogue, and the epilogue
 // writes the new contributions in place (p.Cnext == p.Ccur), so every range
 // gathers the contributions of the ranges before it as updated in this sweep
+// bounds (ordered only): the P + 1 range bounds on the host (P = cfg.parts;
+// async_range_bounds below)
 cudaError_t launch_full_sweep(int mode, const SweepParams& p, const GatherCfg& cfg, const uint32_t* rowbits,
                               const int32_t* rowbase, uint32_t* anyb, int32_t* done, const SweepAux* aux,
-                              cudaStream_t s, bool ordered = false);
+                              cudaStream_t s, bool ordered = false, const int32_t* bounds = nullptr);
+// The ranges of the asynchronous order: cut at multiples of 128 vertices
+// where the in-degree prefix (in-edges of the vertices below, self-loops
+// included) times P first reaches k times all in-edges, k = 1 .. P - 1; one
+// range below 128 P vertices.  ideg: n in-degrees on the device; scratch:
+// cdiv(n, 128) + 1 + scan_tmp_elems(cdiv(n, 128)) + P int64 on the device;
+// bounds: P + 1 host ints, written on return (the call waits for s).
+cudaError_t async_range_bounds(const int32_t* ideg, int32_t n, int P, int64_t* scratch, int32_t* bounds,
+                               cudaStream_t s);
+int64_t async_range_scratch(int32_t n, int P);
 // ranges of the asynchronous order (PR_OPT_ASYNC): the vertex set cut at
 // multiples of 128 into this many consecutive ranges (one range below 128 x
 // this many vertices)

@@ -667,9 +667,20 @@ def test_resize_removes_isolated_tail_only():
 # ------------------------------------------------------------ the ranges order (Alg. 1, one rank vector, eight id ranges in turn)
 
 
-def range_bounds(n, P=8):
+def range_bounds(in_off, P=8):
+    """The ranges of the ranges order on in-rows with offsets in_off: cut at
+    multiples of 128 where the in-degree prefix first reaches k / P of all
+    in-edges (one range below 128 P vertices)."""
+    n = len(in_off) - 1
     P = P if n >= 128 * P else 1
-    return [n * k // P // 128 * 128 for k in range(P)] + [n]
+    W = int(in_off[n])
+    b = [0]
+    for k in range(1, P):
+        j = 0
+        while 128 * j < n and int(in_off[128 * j]) * P < k * W:
+            j += 1
+        b.append(min(128 * j, n))
+    return b + [n]
 
 
 @pytest.mark.parametrize("method", ["static", "nd", "df", "dfp"])
@@ -690,7 +701,8 @@ def test_ranges_order_reaches_fixed_point_at_zero_tolerance(method):
     assert np.max(np.abs(r - pagerank_solve(n, E1))) < 1e-12
 
 
-def test_ranges_order_reads_earlier_ranges_only():
+@pytest.mark.parametrize("skewed", [False, True])
+def test_ranges_order_reads_earlier_ranges_only(skewed):
     """What sets the ranges order apart, checked against the synchronous order:
     (a) one sweep gives range 0 exactly the synchronous values (it reads only
     start-of-sweep ranks) and gives a later vertex the synchronous value
@@ -698,11 +710,17 @@ def test_ranges_order_reads_earlier_ranges_only():
     (b) a later vertex with an in-neighbour in an earlier range gets Eq. 1
     evaluated on the updated ranks of that range;
     (c) a graph with no edge between ranges, and any graph below 1024
-    vertices (one range), gives the synchronous result bit for bit."""
+    vertices (one range), gives the synchronous result bit for bit.
+    skewed: most in-edges go to low ids, so the ranges, which hold equal
+    shares of the in-edges, are far from equal in vertices."""
     n = 1280
-    b = range_bounds(n)
     src, dst = random_graph(n, 5000, 43)
+    if skewed:
+        dst = np.minimum(np.random.default_rng(46).geometric(1.0 / 150, dst.size) - 1, n - 1)
     g = oracle.Graph(n, src, dst)
+    b = range_bounds(g.in_csr()[0])
+    if skewed:
+        assert b[1] == 128 and b[-2] <= n // 2, b   # not the ranges of equal vertex counts
     r0 = np.random.default_rng(44).random(n)
     r0 /= r0.sum()
     rs, _ = g.update("nd", tau=0.0, max_iter=1, r_prev=r0)
@@ -720,8 +738,9 @@ def test_ranges_order_reads_earlier_ranges_only():
             mixed = np.where(rng_of[ins] < rng_of[v], rr[ins], r0[ins]) / deg[ins]
             expect = (1 - ALPHA) / n + ALPHA * mixed.sum()
             assert rr[v] == pytest.approx(expect, rel=1e-12, abs=0), v
-    # (c) no edge between ranges
-    keep = rng_of[src] == rng_of[dst]
+    # (c) no edge between ranges: none crosses a multiple of 128, where every
+    # range bound lies
+    keep = src // 128 == dst // 128
     g2 = oracle.Graph(n, src[keep], dst[keep])
     for m in ("static", "dfp"):
         x, sx = g2.update(m, r_prev=r0)
