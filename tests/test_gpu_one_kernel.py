@@ -143,3 +143,47 @@ def test_one_kernel_option_errors(lib):
     G.update("dfp", loop="one")
     ref, _ = O.update("dfp", r_prev=r0)
     assert np.max(np.abs(G.ranks() - ref)) < TOL
+
+
+def test_one_kernel_updates_from_two_threads(lib):
+    """Two graphs on streams of their own, updated at the same time from two
+    threads: the library orders their cooperative launches one after the
+    other on the device, and every result is the one of the update alone."""
+    import threading
+
+    torch = pytest.importorskip("torch")
+    specs = [(12, 16, 262, 61, None), (11, 12, 100, 62, 1500)]
+    streams = [torch.cuda.Stream() for _ in specs]
+    cases_ = []
+    for spec, s in zip(specs, streams):
+        scale, ef, bsize, seed, n = spec
+        n = n or (1 << scale)
+        src, dst = synth.rmat(scale, ef * n, seed)
+        src, dst = src % n, dst % n
+        G = lib.Graph.from_edges(n, src, dst, stream=s)
+        O = oracle.Graph(n, src, dst)
+        r0, _ = O.update("static")
+        cs, cd = synth.unique_edges(src, dst)
+        b = synth.batch(n, cs, cd, bsize, seed + 1)
+        G.apply_batch(*b)
+        cases_.append((G, r0))
+    alone = [run(G, r0, "dfp", loop="one") for G, r0 in cases_]
+    errors = []
+
+    def worker(k):
+        G, r0 = cases_[k]
+        try:
+            for _ in range(20):
+                got = run(G, r0, "dfp", loop="one")
+                if not (np.array_equal(got[0], alone[k][0]) and got[1] == alone[k][1]):
+                    errors.append((k, got[1], alone[k][1]))
+                    return
+        except Exception as e:   # a barrier that gave up would raise here (PR_ETIMEOUT)
+            errors.append((k, repr(e)))
+
+    threads = [threading.Thread(target=worker, args=(k,)) for k in range(len(cases_))]
+    for t in threads:
+        t.start()
+    for t in threads:
+        t.join()
+    assert not errors, errors
