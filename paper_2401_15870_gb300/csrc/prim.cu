@@ -1,5 +1,6 @@
 // prim.cu -- scan, radix sort, compaction and fills (see prim.cuh).
 #include <atomic>
+#include <mutex>
 #include "prim.cuh"
 
 namespace dfpr {
@@ -171,15 +172,24 @@ __global__ void __launch_bounds__(RS_THREADS) k_rs_hist(const uint64_t* __restri
 }
 
 // stable scatter: a warp owns a contiguous run of RS_KPW keys of the tile and
-// ranks its keys item by item, so (warp, item, lane) order is input order
+// ranks its keys item by item, so (warp, item, lane) order is input order.
+// The tile's keys are first placed in shared memory in digit order (each at
+// its position among the tile's keys of its digit), then written out by
+// consecutive threads, so the keys of one digit leave as one coalesced run
+// instead of each warp's 32 keys going to up to 32 places.
+constexpr size_t RS_STAGE_BYTES = sizeof(uint64_t) * RS_TILE;   // dynamic shared memory of k_rs_scatter
+
 __global__ void __launch_bounds__(RS_THREADS) k_rs_scatter(const uint64_t* __restrict__ keys, uint64_t* __restrict__ out,
                                                            int64_t n, int shift, const int32_t* __restrict__ offs,
                                                            int64_t ntiles) {
+  extern __shared__ uint64_t stage[];   // RS_TILE keys
   __shared__ int wcnt[RS_WARPS][256];
+  __shared__ int dstart[256];           // first position of each digit in the tile
   int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
   for (int i = threadIdx.x; i < RS_WARPS * 256; i += RS_THREADS) (&wcnt[0][0])[i] = 0;
   __syncthreads();
-  int64_t base = (int64_t)blockIdx.x * RS_TILE + (int64_t)w * RS_KPW;
+  const int64_t tile0 = (int64_t)blockIdx.x * RS_TILE;
+  int64_t base = tile0 + (int64_t)w * RS_KPW;
   uint64_t k[RS_ITEMS];
   int rank[RS_ITEMS];
   unsigned lt = lanemask_lt();
@@ -197,12 +207,37 @@ __global__ void __launch_bounds__(RS_THREADS) k_rs_scatter(const uint64_t* __res
     __syncwarp();
   }
   __syncthreads();
+  // per digit: the warps' counts turned into offsets within the digit, and
+  // the digit's total
   for (int d = threadIdx.x; d < 256; d += RS_THREADS) {
     int run = 0;
     for (int ww = 0; ww < RS_WARPS; ww++) {
       int t = wcnt[ww][d];
       wcnt[ww][d] = run;
       run += t;
+    }
+    dstart[d] = run;
+  }
+  __syncthreads();
+  // exclusive scan of the 256 digit totals by warp 0 (8 digits per lane)
+  if (w == 0) {
+    int v[8], sum = 0;
+#pragma unroll
+    for (int q = 0; q < 8; q++) {
+      v[q] = dstart[lane * 8 + q];
+      sum += v[q];
+    }
+    int incl = sum;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const int t = __shfl_up_sync(0xffffffffu, incl, o);
+      if (lane >= o) incl += t;
+    }
+    int run = incl - sum;
+#pragma unroll
+    for (int q = 0; q < 8; q++) {
+      dstart[lane * 8 + q] = run;
+      run += v[q];
     }
   }
   __syncthreads();
@@ -211,15 +246,27 @@ __global__ void __launch_bounds__(RS_THREADS) k_rs_scatter(const uint64_t* __res
     int64_t j = base + i * WARP + lane;
     if (j < n) {
       int d = (int)((k[i] >> shift) & 255u);
-      int64_t dst = (int64_t)offs[(int64_t)d * ntiles + blockIdx.x] + wcnt[w][d] + rank[i];
-      out[dst] = k[i];
+      stage[dstart[d] + wcnt[w][d] + rank[i]] = k[i];
     }
+  }
+  __syncthreads();
+  const int valid_keys = (int)(n - tile0 < RS_TILE ? n - tile0 : RS_TILE);
+  for (int t = threadIdx.x; t < valid_keys; t += RS_THREADS) {
+    const uint64_t key = stage[t];
+    const int d = (int)((key >> shift) & 255u);
+    out[(int64_t)offs[(int64_t)d * ntiles + blockIdx.x] + (t - dstart[d])] = key;
   }
 }
 
 cudaError_t radix_sort_u64(uint64_t* keys, uint64_t* alt, int64_t n, int nbits, void* tmp, cudaStream_t s) {
   if (n <= 1 || nbits <= 0) return cudaSuccess;
   if (n >= (int64_t(1) << 31)) return cudaErrorInvalidValue;
+  static std::once_flag smem_set;
+  static cudaError_t smem_err = cudaSuccess;
+  std::call_once(smem_set, [] {
+    smem_err = cudaFuncSetAttribute(k_rs_scatter, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)RS_STAGE_BYTES);
+  });
+  if (smem_err != cudaSuccess) return smem_err;
   int64_t ntiles = rs_tiles(n);
   int64_t cnt = 256 * ntiles;
   int32_t* counts = (int32_t*)tmp;
@@ -230,7 +277,7 @@ cudaError_t radix_sort_u64(uint64_t* keys, uint64_t* alt, int64_t n, int nbits, 
     note_launch(); k_rs_hist<<<(unsigned)ntiles, RS_THREADS, 0, s>>>(src, n, shift, counts, ntiles);
     cudaError_t e = scan_excl<int32_t>(counts, counts, cnt, scratch, s);
     if (e != cudaSuccess) return e;
-    note_launch(); k_rs_scatter<<<(unsigned)ntiles, RS_THREADS, 0, s>>>(src, dst, n, shift, counts, ntiles);
+    note_launch(); k_rs_scatter<<<(unsigned)ntiles, RS_THREADS, RS_STAGE_BYTES, s>>>(src, dst, n, shift, counts, ntiles);
     uint64_t* t = src;
     src = dst;
     dst = t;
