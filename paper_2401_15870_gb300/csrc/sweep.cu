@@ -459,7 +459,7 @@ __global__ void __launch_bounds__(256, 4) k_finish_full(SweepParams p, long long
 // task that brings the count to the number of tasks over the chunk's rows runs
 // the chunk's epilogue itself and resets the count.  Nothing waits on anything: a chunk
 // is finished by whichever warp completes it.  The epilogue is bound by the
-// FP64 pipe and the gather by the L1TEX data pipe, so in one launch the two
+// FP64 pipe and the gather by memory throughput, so in one launch the two
 // overlap across the warps of an SM.
 
 // Eq. 1 for every vertex of chunks [ch0, ch0 + U) (Static, ND): the
@@ -811,7 +811,7 @@ cudaError_t launch_full_sweep(int mode, const SweepParams& p, const GatherCfg& c
   if (!ordered && !gather_cfg_valid(cfg)) return cudaErrorInvalidValue;
   // P vertex ranges cut at multiples of 128: the gather of range k + 1 runs on
   // s while the epilogue of range k runs on the auxiliary stream, so the
-  // FP64-bound epilogue overlaps the L1TEX-bound gather; the epilogues join s
+  // FP64-bound epilogue overlaps the memory-bound gather; the epilogues join s
   // at the end.  P = 1: gather then epilogue on s.  Ordered (asynchronous
   // order): every range's gather and epilogue on s, one range after another.
   const int P = ordered ? (p.n >= 128 * cfg.parts ? cfg.parts : 1)

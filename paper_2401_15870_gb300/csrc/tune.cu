@@ -1,10 +1,11 @@
 // tune.cu -- the autotuner of the every-vertex rank sweep (pr_autotune).
 //
 // The gather phase of a sweep over every vertex (Static, ND, the pull form of
-// DF / DF-P) is bound by the L1TEX data pipe: each scattered 8-byte
-// contribution gather from global memory costs about one wavefront.  Three
-// knobs change how much of that pipe a sweep needs and how well its latency is
-// hidden, and the best setting depends on the graph's size and degree skew:
+// DF / DF-P) is bound by the memory system's throughput for scattered 8-byte
+// contribution reads: about one L1TEX wavefront each, and one 32-byte L2
+// sector each when it misses L1.  Three knobs change how much of that a sweep
+// needs and how well its latency is hidden, and the best setting depends on
+// the graph's size and degree skew:
 //   - threads per block (256, 512, 1024);
 //   - quads per lane per warp step (2, 4, 8: loads in flight per lane);
 //   - the hub threshold: the contributions of the vertices of highest
