@@ -69,3 +69,25 @@ def test_reference_arm_runs_on_rank_zero_only(capsys):
         sys.argv = old
     assert bench.run_reference(a, 1, 2) is None
     assert capsys.readouterr().out == ""
+
+
+def test_reference_arm_line_on_one_rank():
+    """The reference arm (the oracle, every host core) prints one JSON line
+    with the benchmark's metric and unit, impl "reference", a cpu_baseline
+    naming its sample and cores, and an e2e entry of its own value with no
+    host-device traffic (here on a small graph: R-MAT scale 12)."""
+    import json
+    import subprocess
+    out = subprocess.run([sys.executable, os.path.join(ROOT, "bench.py"), "--impl", "reference", "--scale", "12",
+                          "--steps", "2", "--warmup", "1"], capture_output=True, text=True, timeout=600, cwd=ROOT)
+    assert out.returncode == 0, out.stderr[-2000:]
+    lines = [l for l in out.stdout.splitlines() if l.startswith("{")]
+    assert len(lines) == 1
+    line = json.loads(lines[0])
+    assert line["impl"] == "reference"
+    assert line["unit"] == "updates/s" and line["higher_is_better"] is True
+    assert line["steps"] == 2 and line["warmup"] == 1 and line["value"] > 0
+    cb = line["cpu_baseline"]
+    assert cb["kind"] == "oracle" and cb["cores"] >= 1 and cb["value"] == line["value"] and cb["sample"]
+    assert line["e2e"] == {"value": line["value"], "unit": "updates/s", "h2d_bytes_per_step": 0,
+                           "d2h_bytes_per_step": 0}
