@@ -751,3 +751,35 @@ def test_ranges_order_reads_earlier_ranges_only(skewed):
     x, sx = g3.update("static")
     y, sy = g3.update("static", order="ranges")
     assert np.array_equal(x, y) and sx == sy
+
+
+@pytest.mark.parametrize("tau,stop_at_change", [(1e-6, False), (None, False), (1e-6, True)])
+def test_tie_distance_is_the_nearest_decision(tau, stop_at_change):
+    """The oracle's tie_rel (the relative distance of the nearest expand,
+    prune or stop decision from its threshold, which the GPU tests use to tell
+    a near-tie from a different frontier) equals a brute-force minimum over one
+    DF-P iteration: every processed vertex's relative change against tau_f and
+    tau_p, and the iteration's L-inf change against tau.  With tau_f = tau_p set
+    to one vertex's own relative change the nearest decision is exactly on its
+    threshold (0), and so it is with the iteration tolerance set to the
+    iteration's own L-inf change."""
+    n = 300
+    src, dst = random_graph(n, 1500, 91)
+    g = oracle.Graph(n, src, dst)
+    r0, _ = g.update("static")
+    E0 = edge_set(n, src, dst)
+    (ds, dd), (is_, id_) = random_batch(n, E0, 20, 60, 92, with_noise=False)
+    g.apply_batch(ds, dd, is_, id_)
+    F0 = np.nonzero(g.initial_affected())[0]
+    r1, _ = g.update("dfp", tau=1e-10, tau_f=1e-6, tau_p=1e-6, max_iter=1, r_prev=r0)
+    dr = np.abs(r1[F0] - r0[F0])
+    rel = dr / np.maximum(r1[F0], r0[F0])
+    if tau is None:                     # a threshold exactly at one vertex's change
+        tau = float(rel[len(rel) // 2])
+    tau_stop = float(dr.max()) if stop_at_change else 1e-10
+    r, st = g.update("dfp", tau=tau_stop, tau_f=tau, tau_p=tau, max_iter=1, r_prev=r0)
+    assert np.array_equal(r, r1)        # one iteration: the ranks do not depend on the tolerances
+    expect = min(float(np.min(np.abs(rel / tau - 1.0))), abs(float(dr.max()) / tau_stop - 1.0))
+    assert st.tie_rel == expect
+    if stop_at_change or tau == float(rel[len(rel) // 2]):
+        assert st.tie_rel == 0.0
