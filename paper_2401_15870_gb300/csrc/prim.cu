@@ -149,26 +149,30 @@ constexpr int RS_WARPS = RS_THREADS / WARP;
 constexpr int RS_ITEMS = 16;
 constexpr int RS_KPW = WARP * RS_ITEMS;       // keys per warp
 constexpr int RS_TILE = RS_WARPS * RS_KPW;    // 8192 keys per tile
+// digits of RS_BITS bits: the 2 x 25-bit edge keys of a 2^25-vertex graph
+// take 5 passes instead of the 7 of 8-bit digits
+constexpr int RS_BITS = 10;
+constexpr int RS_BINS = 1 << RS_BITS;
 
 static int64_t rs_tiles(int64_t n) { return cdiv(n > 0 ? n : 1, RS_TILE); }
 
 size_t radix_tmp_bytes(int64_t n) {
-  int64_t cnt = 256 * rs_tiles(n);
+  int64_t cnt = (int64_t)RS_BINS * rs_tiles(n);
   return sizeof(int32_t) * (size_t)(cnt + 1 + scan_tmp_elems(cnt));
 }
 
 __global__ void __launch_bounds__(RS_THREADS) k_rs_hist(const uint64_t* __restrict__ keys, int64_t n, int shift,
                                                         int32_t* __restrict__ counts, int64_t ntiles) {
-  __shared__ int hist[256];
-  for (int i = threadIdx.x; i < 256; i += RS_THREADS) hist[i] = 0;
+  __shared__ int hist[RS_BINS];
+  for (int i = threadIdx.x; i < RS_BINS; i += RS_THREADS) hist[i] = 0;
   __syncthreads();
   int64_t base = (int64_t)blockIdx.x * RS_TILE;
   for (int i = threadIdx.x; i < RS_TILE; i += RS_THREADS) {
     int64_t j = base + i;
-    if (j < n) atomicAdd(&hist[(int)((keys[j] >> shift) & 255u)], 1);
+    if (j < n) atomicAdd(&hist[(int)((keys[j] >> shift) & (RS_BINS - 1))], 1);
   }
   __syncthreads();
-  for (int d = threadIdx.x; d < 256; d += RS_THREADS) counts[(int64_t)d * ntiles + blockIdx.x] = hist[d];
+  for (int d = threadIdx.x; d < RS_BINS; d += RS_THREADS) counts[(int64_t)d * ntiles + blockIdx.x] = hist[d];
 }
 
 // stable scatter: a warp owns a contiguous run of RS_KPW keys of the tile and
@@ -177,16 +181,19 @@ __global__ void __launch_bounds__(RS_THREADS) k_rs_hist(const uint64_t* __restri
 // its position among the tile's keys of its digit), then written out by
 // consecutive threads, so the keys of one digit leave as one coalesced run
 // instead of each warp's 32 keys going to up to 32 places.
-constexpr size_t RS_STAGE_BYTES = sizeof(uint64_t) * RS_TILE;   // dynamic shared memory of k_rs_scatter
+// dynamic shared memory of k_rs_scatter: the staged tile, the per-warp digit
+// counts and the digit starts
+constexpr size_t RS_STAGE_BYTES =
+    sizeof(uint64_t) * RS_TILE + sizeof(int) * (size_t)RS_WARPS * RS_BINS + sizeof(int) * (size_t)RS_BINS;
 
 __global__ void __launch_bounds__(RS_THREADS) k_rs_scatter(const uint64_t* __restrict__ keys, uint64_t* __restrict__ out,
                                                            int64_t n, int shift, const int32_t* __restrict__ offs,
                                                            int64_t ntiles) {
-  extern __shared__ uint64_t stage[];   // RS_TILE keys
-  __shared__ int wcnt[RS_WARPS][256];
-  __shared__ int dstart[256];           // first position of each digit in the tile
+  extern __shared__ uint64_t stage[];   // RS_TILE keys, then wcnt and dstart
+  int (*wcnt)[RS_BINS] = reinterpret_cast<int (*)[RS_BINS]>(stage + RS_TILE);
+  int* dstart = reinterpret_cast<int*>(stage + RS_TILE) + RS_WARPS * RS_BINS;   // first position of each digit
   int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-  for (int i = threadIdx.x; i < RS_WARPS * 256; i += RS_THREADS) (&wcnt[0][0])[i] = 0;
+  for (int i = threadIdx.x; i < RS_WARPS * RS_BINS; i += RS_THREADS) (&wcnt[0][0])[i] = 0;
   __syncthreads();
   const int64_t tile0 = (int64_t)blockIdx.x * RS_TILE;
   int64_t base = tile0 + (int64_t)w * RS_KPW;
@@ -198,7 +205,7 @@ __global__ void __launch_bounds__(RS_THREADS) k_rs_scatter(const uint64_t* __res
     int64_t j = base + i * WARP + lane;
     bool valid = j < n;
     k[i] = valid ? keys[j] : 0;
-    int d = valid ? (int)((k[i] >> shift) & 255u) : 256;
+    int d = valid ? (int)((k[i] >> shift) & (RS_BINS - 1)) : RS_BINS;
     unsigned peers = __match_any_sync(0xffffffffu, d);
     int before = valid ? wcnt[w][d] : 0;
     rank[i] = before + __popc(peers & lt);
@@ -209,7 +216,7 @@ __global__ void __launch_bounds__(RS_THREADS) k_rs_scatter(const uint64_t* __res
   __syncthreads();
   // per digit: the warps' counts turned into offsets within the digit, and
   // the digit's total
-  for (int d = threadIdx.x; d < 256; d += RS_THREADS) {
+  for (int d = threadIdx.x; d < RS_BINS; d += RS_THREADS) {
     int run = 0;
     for (int ww = 0; ww < RS_WARPS; ww++) {
       int t = wcnt[ww][d];
@@ -219,14 +226,11 @@ __global__ void __launch_bounds__(RS_THREADS) k_rs_scatter(const uint64_t* __res
     dstart[d] = run;
   }
   __syncthreads();
-  // exclusive scan of the 256 digit totals by warp 0 (8 digits per lane)
+  // exclusive scan of the digit totals by warp 0 (RS_BINS / 32 digits per lane)
   if (w == 0) {
-    int v[8], sum = 0;
-#pragma unroll
-    for (int q = 0; q < 8; q++) {
-      v[q] = dstart[lane * 8 + q];
-      sum += v[q];
-    }
+    constexpr int PER = RS_BINS / WARP;
+    int sum = 0;
+    for (int q = 0; q < PER; q++) sum += dstart[lane * PER + q];
     int incl = sum;
 #pragma unroll
     for (int o = 1; o < 32; o <<= 1) {
@@ -234,10 +238,10 @@ __global__ void __launch_bounds__(RS_THREADS) k_rs_scatter(const uint64_t* __res
       if (lane >= o) incl += t;
     }
     int run = incl - sum;
-#pragma unroll
-    for (int q = 0; q < 8; q++) {
-      dstart[lane * 8 + q] = run;
-      run += v[q];
+    for (int q = 0; q < PER; q++) {
+      const int v = dstart[lane * PER + q];
+      dstart[lane * PER + q] = run;
+      run += v;
     }
   }
   __syncthreads();
@@ -245,7 +249,7 @@ __global__ void __launch_bounds__(RS_THREADS) k_rs_scatter(const uint64_t* __res
   for (int i = 0; i < RS_ITEMS; i++) {
     int64_t j = base + i * WARP + lane;
     if (j < n) {
-      int d = (int)((k[i] >> shift) & 255u);
+      int d = (int)((k[i] >> shift) & (RS_BINS - 1));
       stage[dstart[d] + wcnt[w][d] + rank[i]] = k[i];
     }
   }
@@ -253,7 +257,7 @@ __global__ void __launch_bounds__(RS_THREADS) k_rs_scatter(const uint64_t* __res
   const int valid_keys = (int)(n - tile0 < RS_TILE ? n - tile0 : RS_TILE);
   for (int t = threadIdx.x; t < valid_keys; t += RS_THREADS) {
     const uint64_t key = stage[t];
-    const int d = (int)((key >> shift) & 255u);
+    const int d = (int)((key >> shift) & (RS_BINS - 1));
     out[(int64_t)offs[(int64_t)d * ntiles + blockIdx.x] + (t - dstart[d])] = key;
   }
 }
@@ -268,12 +272,12 @@ cudaError_t radix_sort_u64(uint64_t* keys, uint64_t* alt, int64_t n, int nbits, 
   });
   if (smem_err != cudaSuccess) return smem_err;
   int64_t ntiles = rs_tiles(n);
-  int64_t cnt = 256 * ntiles;
+  int64_t cnt = (int64_t)RS_BINS * ntiles;
   int32_t* counts = (int32_t*)tmp;
   int32_t* scratch = counts + cnt + 1;
   uint64_t* src = keys;
   uint64_t* dst = alt;
-  for (int shift = 0; shift < nbits; shift += 8) {
+  for (int shift = 0; shift < nbits; shift += RS_BITS) {
     note_launch(); k_rs_hist<<<(unsigned)ntiles, RS_THREADS, 0, s>>>(src, n, shift, counts, ntiles);
     cudaError_t e = scan_excl<int32_t>(counts, counts, cnt, scratch, s);
     if (e != cudaSuccess) return e;
